@@ -1,0 +1,214 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+A ctypes binding over `glasso_oracle.c`, the plain, slow, obviously correct C
+implementation of the multilevel proximal-Newton solver for
+    min_{A > 0} -log det A + tr(S A) + lambda * sum_ij |A_ij|
+(Treister, Turek, Yavneh, Section 5 eq. MLE_l1_prior; Algorithm 1; Section 7).
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  It shares no code with the CUDA library and the CUDA
+library never calls it.  `build()` compiles the C file with gcc; nothing here
+depends on the GPU or on torch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glasso_oracle.c")
+_LIB = os.path.join(_HERE, "_glasso_oracle.so")
+_lib = None
+
+OK, EINVAL, ENOTPD, ELINESEARCH, EMAXITER = 0, 1, 3, 4, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared library (plain -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relaxations", C.c_int),
+                ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
+                ("max_kkt", C.c_double), ("logdet", C.c_double), ("nnz", C.c_int64),
+                ("ntrace", C.c_int64)]
+
+
+_d = C.POINTER(C.c_double)
+_i32 = C.POINTER(C.c_int32)
+_u8 = C.POINTER(C.c_uint8)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_form_S.argtypes = [_d, C.c_int64, C.c_int64, C.c_int, _d]
+        L.orc_cholesky.argtypes = [_d, C.c_int64, _d]
+        L.orc_cholesky.restype = C.c_int
+        L.orc_logdet_from_chol.argtypes = [_d, C.c_int64]
+        L.orc_logdet_from_chol.restype = C.c_double
+        L.orc_inverse_from_chol.argtypes = [_d, C.c_int64, _d]
+        L.orc_objective.argtypes = [_d, _d, C.c_int64, C.c_double, _d]
+        L.orc_objective.restype = C.c_int
+        L.orc_free_set.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64,
+                                   _i32, _i32]
+        L.orc_free_set.restype = C.c_int64
+        L.orc_rel_kkt.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _d]
+        L.orc_rel_kkt.restype = C.c_double
+        L.orc_hierarchy.argtypes = [_d, _u8, C.c_int64, _u8, C.POINTER(C.c_int)]
+        L.orc_hierarchy.restype = C.c_int
+        L.orc_cd_sweeps.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64,
+                                    C.c_int, _d, _d]
+        L.orc_line_search.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64,
+                                      _d, C.c_double, C.c_double, C.c_int, _d, _d,
+                                      C.POINTER(C.c_int)]
+        L.orc_line_search.restype = C.c_int
+        L.orc_solve.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d, _d,
+                                C.POINTER(Info), _d, C.c_int64]
+        L.orc_solve.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t=_d):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def form_S(X, center: bool = False) -> np.ndarray:
+    """a1: S = X^T X / m (optionally centred), eq. cov_estimate."""
+    X = _f64(X)
+    m, n = X.shape
+    S = np.empty((n, n))
+    lib().orc_form_S(_p(X), m, n, int(center), _p(S))
+    return S
+
+
+def cholesky(A):
+    """a2: (info, L) with A = L L^T; info = k+1 at the first non-positive pivot."""
+    A = _f64(A)
+    n = A.shape[0]
+    L = np.empty((n, n))
+    info = lib().orc_cholesky(_p(A), n, _p(L))
+    return info, L
+
+
+def logdet_from_chol(L) -> float:
+    L = _f64(L)
+    return lib().orc_logdet_from_chol(_p(L), L.shape[0])
+
+
+def inverse_from_chol(L) -> np.ndarray:
+    """a3: W = A^{-1} from the Cholesky factor."""
+    L = _f64(L)
+    n = L.shape[0]
+    W = np.empty((n, n))
+    lib().orc_inverse_from_chol(_p(L), n, _p(W))
+    return W
+
+
+def objective(S, A, lam):
+    """F(A) (eq. MLE_l1_prior); returns (info, F)."""
+    S, A = _f64(S), _f64(A)
+    F = C.c_double(0.0)
+    info = lib().orc_objective(_p(S), _p(A), A.shape[0], lam, C.byref(F))
+    return info, F.value
+
+
+def free_set(S, W, A, lam, cand=None):
+    """a4: free set (eq. active_set) restricted to candidate pairs; returns (i, j) arrays."""
+    S, W, A = _f64(S), _f64(W), _f64(A)
+    n = A.shape[0]
+    if cand is None:
+        cap = n * (n + 1) // 2
+        ci = cj = None
+        nc = 0
+    else:
+        ci = np.ascontiguousarray(cand[0], dtype=np.int32)
+        cj = np.ascontiguousarray(cand[1], dtype=np.int32)
+        nc = len(ci)
+        cap = max(nc, 1)
+    oi = np.empty(cap, dtype=np.int32)
+    oj = np.empty(cap, dtype=np.int32)
+    cnt = lib().orc_free_set(_p(S), _p(W), _p(A), n, lam,
+                             None if ci is None else _p(ci, _i32),
+                             None if cj is None else _p(cj, _i32), nc,
+                             _p(oi, _i32), _p(oj, _i32))
+    return oi[:cnt].copy(), oj[:cnt].copy()
+
+
+def rel_kkt(S, W, A, lam):
+    """Relative KKT residual and max-norm min-norm subgradient."""
+    S, W, A = _f64(S), _f64(W), _f64(A)
+    mx = C.c_double(0.0)
+    r = lib().orc_rel_kkt(_p(S), _p(W), _p(A), A.shape[0], lam, C.byref(mx))
+    return r, mx.value
+
+
+def hierarchy(absg, insupp):
+    """a5: per-pair level tags and the number of levels L."""
+    absg = _f64(absg)
+    insupp = np.ascontiguousarray(insupp, dtype=np.uint8)
+    nf = len(absg)
+    tag = np.empty(max(nf, 1), dtype=np.uint8)
+    L = C.c_int(0)
+    lib().orc_hierarchy(_p(absg), _p(insupp, _u8), nf, _p(tag, _u8), C.byref(L))
+    return tag[:nf].copy(), L.value
+
+
+def cd_sweeps(S, W, A, lam, pi, pj, nsweeps, D=None, U=None):
+    """a6: CD sweeps on the Newton LASSO; returns (Delta on pairs, U = Delta W)."""
+    S, W, A = _f64(S), _f64(W), _f64(A)
+    n = A.shape[0]
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    D = np.zeros(len(pi)) if D is None else _f64(D).copy()
+    U = np.zeros((n, n)) if U is None else _f64(U).copy()
+    lib().orc_cd_sweeps(_p(S), _p(W), _p(A), n, lam, _p(pi, _i32), _p(pj, _i32), len(pi),
+                        nsweeps, _p(D), _p(U))
+    return D, U
+
+
+def line_search(S, W, A, lam, pi, pj, D, F0, sigma=1e-4, beta=0.5, max_trials=30):
+    """a7: Armijo backtracking; returns (status, A_new, F_new, alpha, trials)."""
+    S, W = _f64(S), _f64(W)
+    A = _f64(A).copy()
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    D = _f64(D)
+    F = C.c_double(F0)
+    alpha = C.c_double(0.0)
+    trials = C.c_int(0)
+    rc = lib().orc_line_search(_p(S), _p(W), _p(A), A.shape[0], lam, _p(pi, _i32), _p(pj, _i32),
+                               len(pi), _p(D), sigma, beta, max_trials, C.byref(F),
+                               C.byref(alpha), C.byref(trials))
+    return rc, A, F.value, alpha.value, trials.value
+
+
+def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0):
+    """a8: the full ML-cycle solve.  Returns (A, W, info dict, trace array)."""
+    S = _f64(S)
+    n = S.shape[0]
+    A = np.empty((n, n))
+    W = np.empty((n, n))
+    info = Info()
+    tr = np.zeros((max(trace_cap, 1), 2))
+    a0 = None if A0 is None else _f64(A0)
+    lib().orc_solve(_p(S), n, lam, tol, max_cycles, None if a0 is None else _p(a0),
+                    _p(A), _p(W), C.byref(info), _p(tr), trace_cap)
+    d = {k: getattr(info, k) for k, _ in Info._fields_}
+    return A, W, d, tr[: info.ntrace].copy()

@@ -1,0 +1,512 @@
+/*
+ * FP64 CPU oracle for the multilevel proximal-Newton solver of the
+ * l1-regularised log-det problem (Treister, Turek, Yavneh, arXiv 1607.00315).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * reference against which the CUDA path is checked.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or helper with the CUDA library, and the CUDA library
+ * never calls it.
+ *
+ * Problem (Section 5, eq. MLE_l1_prior):
+ *     min_{A > 0}  F(A) = -log det A + tr(S A) + lambda * sum_ij |A_ij|
+ * The diagonal is penalised.  The minimiser is unique.
+ *
+ * All matrices are dense, row-major, n x n, double precision.  Pair lists hold
+ * upper-triangle index pairs (i <= j) in row-major order (i ascending, then j
+ * ascending); a pair (i, j) stands for both A_ij and A_ji.
+ *
+ * Readings of points the paper leaves open are marked READING.
+ * Parity pins: every function here is pinned by the CPU test suite against
+ * closed forms, library routines, brute force on tiny inputs or the paper's
+ * optimality conditions.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ENOTPD 3
+#define ORC_ELINESEARCH 4
+#define ORC_EMAXITER 5
+#define ORC_EINVAL 1
+
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+/* Soft shrinkage S_t(x) = sign(x) * max(0, |x| - t), eq. shrinkage (Section 2). */
+static double soft(double x, double t) {
+    double ax = fabs(x) - t;
+    return ax > 0.0 ? sgn(x) * ax : 0.0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* a1. Empirical covariance, eq. cov_estimate (Section 5):
+ *     S = (1/m) sum_k (y_k - mu)(y_k - mu)^T,  mu = mean of the samples when
+ *     `center` is set, else zero.  X is m x n (one sample per row).         */
+void orc_form_S(const double *X, int64_t m, int64_t n, int center, double *S) {
+    double *mu = (double *)calloc((size_t)n, sizeof(double));
+    if (center) {
+        for (int64_t k = 0; k < m; ++k)
+            for (int64_t i = 0; i < n; ++i) mu[i] += X[k * n + i];
+        for (int64_t i = 0; i < n; ++i) mu[i] /= (double)m;
+    }
+    /* the sum of outer products of eq. cov_estimate, one sample at a time */
+    memset(S, 0, (size_t)(n * n) * sizeof(double));
+    for (int64_t k = 0; k < m; ++k) {
+        const double *y = X + k * n;
+        for (int64_t i = 0; i < n; ++i) {
+            double yi = y[i] - mu[i];
+            for (int64_t j = 0; j <= i; ++j) S[i * n + j] += yi * (y[j] - mu[j]);
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j <= i; ++j) {
+            S[i * n + j] /= (double)m;
+            S[j * n + i] = S[i * n + j];
+        }
+    free(mu);
+}
+
+/* ---------------------------------------------------------------------- */
+/* a2. Cholesky factorisation A = L L^T (textbook column-by-column form).
+ * Returns 0 on success or k+1 when the k-th pivot is not positive (A is not
+ * positive definite; the line-search PD test of Section 6.1.2).  L is lower
+ * triangular with zeros above the diagonal.                                */
+int orc_cholesky(const double *A, int64_t n, double *L) {
+    memset(L, 0, (size_t)(n * n) * sizeof(double));
+    for (int64_t j = 0; j < n; ++j) {
+        double d = A[j * n + j];
+        for (int64_t k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > 0.0)) return (int)(j + 1);
+        double ljj = sqrt(d);
+        L[j * n + j] = ljj;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double s = A[i * n + j];
+            for (int64_t k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = s / ljj;
+        }
+    }
+    return 0;
+}
+
+/* log det A = 2 sum_i log L_ii for A = L L^T. */
+double orc_logdet_from_chol(const double *L, int64_t n) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += log(L[i * n + i]);
+    return 2.0 * s;
+}
+
+/* a3. W = A^{-1} = L^{-T} L^{-1} from the Cholesky factor (eq. gradHes needs
+ * A^{-1}).  X = L^{-1} is found column by column by forward substitution
+ * (L x_k = e_k, x_k zero above k); the columns are stored as rows of
+ * Y = X^T so that W_ij = sum_t X_ti X_tj = sum_t Y_it Y_jt runs along rows. */
+void orc_inverse_from_chol(const double *L, int64_t n, double *W) {
+    double *Y = (double *)calloc((size_t)(n * n), sizeof(double));
+    for (int64_t k = 0; k < n; ++k) {
+        double *y = Y + k * n; /* column k of L^{-1} */
+        for (int64_t i = k; i < n; ++i) {
+            double s = (i == k) ? 1.0 : 0.0;
+            for (int64_t t = k; t < i; ++t) s -= L[i * n + t] * y[t];
+            y[i] = s / L[i * n + i];
+        }
+    }
+    /* W = X^T X: entry (i, j) sums over t >= max(i, j) where both are nonzero */
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j <= i; ++j) {
+            double s = 0.0;
+            for (int64_t t = i; t < n; ++t) s += Y[i * n + t] * Y[j * n + t];
+            W[i * n + j] = s;
+            W[j * n + i] = s;
+        }
+    free(Y);
+}
+
+/* tr(S A) and ||A||_1 = sum_ij |A_ij| (eq. MLE_l1_prior). */
+static void trace_and_l1(const double *S, const double *A, int64_t n, double *tr, double *l1) {
+    double t = 0.0, a = 0.0;
+    for (int64_t i = 0; i < n * n; ++i) {
+        t += S[i] * A[i];
+        a += fabs(A[i]);
+    }
+    *tr = t;
+    *l1 = a;
+}
+
+/* F(A) = -log det A + tr(SA) + lambda ||A||_1 (eq. MLE_l1_prior).
+ * Returns 0, or the Cholesky info when A is not positive definite.         */
+int orc_objective(const double *S, const double *A, int64_t n, double lam, double *F) {
+    double *L = (double *)malloc((size_t)(n * n) * sizeof(double));
+    int info = orc_cholesky(A, n, L);
+    if (info == 0) {
+        double tr, l1;
+        trace_and_l1(S, A, n, &tr, &l1);
+        *F = -orc_logdet_from_chol(L, n) + tr + lam * l1;
+    }
+    free(L);
+    return info;
+}
+
+/* ---------------------------------------------------------------------- */
+/* a4. Free set, eq. active_set (Section 5.2):
+ *     F(A) = {(i,j) : A_ij != 0  or  |(S - A^{-1})_ij| > lambda}
+ * restricted to a candidate set C_l (Section 7, eq. MLE_l1_prior_C).
+ * When `cand` is NULL the candidates are all upper-triangle pairs.  The zero
+ * test is exact (READING: the soft-shrinkage step yields exact zeros).
+ * Writes the pairs in candidate order; returns their count.                */
+int64_t orc_free_set(const double *S, const double *W, const double *A, int64_t n, double lam,
+                     const int32_t *cand_i, const int32_t *cand_j, int64_t ncand,
+                     int32_t *out_i, int32_t *out_j) {
+    int64_t cnt = 0;
+    if (cand_i == NULL) {
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = i; j < n; ++j) {
+                double g = S[i * n + j] - W[i * n + j];
+                if (A[i * n + j] != 0.0 || fabs(g) > lam) {
+                    out_i[cnt] = (int32_t)i;
+                    out_j[cnt] = (int32_t)j;
+                    ++cnt;
+                }
+            }
+    } else {
+        for (int64_t p = 0; p < ncand; ++p) {
+            int64_t i = cand_i[p], j = cand_j[p];
+            double g = S[i * n + j] - W[i * n + j];
+            if (A[i * n + j] != 0.0 || fabs(g) > lam) {
+                out_i[cnt] = (int32_t)i;
+                out_j[cnt] = (int32_t)j;
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* Relative KKT residual (Section 8 stopping rule, with the subdifferential of
+ * eq. subgradient1): the minimum-norm subgradient
+ *     g_ij = G_ij + lambda sign(A_ij)                   if A_ij != 0
+ *     g_ij = sign(G_ij) max(|G_ij| - lambda, 0)         if A_ij == 0
+ * with G = S - W, summed in absolute value over all (i, j) and divided by
+ * ||A||_1.  Also returns max_ij |g_ij|.                                    */
+double orc_rel_kkt(const double *S, const double *W, const double *A, int64_t n, double lam,
+                   double *maxabs) {
+    double num = 0.0, den = 0.0, mx = 0.0;
+    for (int64_t i = 0; i < n * n; ++i) {
+        double g = S[i] - W[i];
+        double r = (A[i] != 0.0) ? g + lam * sgn(A[i]) : soft(g, lam);
+        num += fabs(r);
+        den += fabs(A[i]);
+        if (fabs(r) > mx) mx = fabs(r);
+    }
+    if (maxabs) *maxabs = mx;
+    return num / den;
+}
+
+/* ---------------------------------------------------------------------- */
+/* a5. Multilevel hierarchy (Section 3.2 and Section 7):
+ * Given the previous fine-level free set F_k (nf pairs), the absolute
+ * gradient |G| on those pairs and a flag telling which pairs are in
+ * supp(A^(k)), build nested C_1 > ... > C_L = supp with
+ *     |C_1| = max(ceil(|F_k| / 2), |supp|),
+ *     |C_{l+1}| = max(ceil(|C_l| / 2), |supp|), stop when |C_l| = |supp|.
+ * C_l = supp + the (|C_l| - |supp|) non-support pairs of largest |G|.
+ * READING: ties in |G| are broken by list position (row-major pair order),
+ * and when ceil(|F_k|/2) <= |supp| the hierarchy is C_1 = supp, L = 1.
+ * Output: tag[p] = the coarsest level containing pair p (0 if p is only in
+ * C_0), L via *levels.  Pairs outside F_k are in C_0 only.                  */
+static const double *g_rank_key;
+static int cmp_rank(const void *pa, const void *pb) {
+    int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
+    double ka = g_rank_key[a], kb = g_rank_key[b];
+    if (ka > kb) return -1; /* larger |G| first */
+    if (ka < kb) return 1;
+    return (a < b) ? -1 : (a > b); /* earlier pair first */
+}
+
+int orc_hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uint8_t *tag, int *levels) {
+    int64_t ns = 0;
+    for (int64_t p = 0; p < nf; ++p) ns += insupp[p] ? 1 : 0;
+    int64_t sizes[64];
+    int L = 1;
+    int64_t s = (nf + 1) / 2;
+    if (s < ns) s = ns;
+    sizes[1] = s;
+    while (sizes[L] > ns && L < 62) {
+        int64_t nxt = (sizes[L] + 1) / 2;
+        if (nxt < ns) nxt = ns;
+        sizes[++L] = nxt;
+    }
+    *levels = L;
+    int64_t nr = nf - ns;
+    int64_t *order = (int64_t *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int64_t));
+    int64_t q = 0;
+    for (int64_t p = 0; p < nf; ++p)
+        if (!insupp[p]) order[q++] = p;
+    g_rank_key = absg;
+    qsort(order, (size_t)nr, sizeof(int64_t), cmp_rank);
+    for (int64_t p = 0; p < nf; ++p) tag[p] = insupp[p] ? (uint8_t)L : 0;
+    for (int64_t r = 0; r < nr; ++r) {
+        int t = 0;
+        for (int l = 1; l <= L; ++l)
+            if (r < sizes[l] - ns) t = l;
+        tag[order[r]] = (uint8_t)t;
+    }
+    free(order);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* a6. Coordinate descent on the Newton LASSO, eq. Quad_MLE_l1_prior
+ *     min_Delta tr(Delta G) + 1/2 tr(Delta W Delta W) + lambda ||A + Delta||_1
+ * restricted to the given pairs (Section 5.2 free set, Section 7 restriction).
+ * For an off-diagonal pair, Delta <- Delta + mu (e_i e_j^T + e_j e_i^T)
+ * changes the model by 2 (b mu + a mu^2 / 2 + lambda |c + mu|) - 2 lambda |c|
+ * with a = W_ij^2 + W_ii W_jj, b = G_ij + (W Delta W)_ij, c = A_ij + Delta_ij;
+ * for a diagonal pair a = W_ii^2 and there is no factor 2.  In both cases
+ * the 1-D minimiser (eq. 1d_l1) is mu = -c + S_{lambda/a}(c - b/a).
+ * READING: the paper's printed closed form has the sign of (b -+ lambda)/a
+ * reversed; the minimiser of a z^2/2 + b z + lambda |z| is -(b - lambda)/a
+ * for b > lambda, which is what the formula above gives.
+ * U = Delta W is kept up to date: (W Delta W)_ij = W_i,: . U_:,j and the
+ * update adds mu W_j,: to row i of U and mu W_i,: to row j.
+ * D holds Delta on the pair list (in/out); U is n x n (in/out).           */
+void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n, double lam,
+                   const int32_t *pi, const int32_t *pj, int64_t np, int nsweeps,
+                   double *D, double *U) {
+    for (int sw = 0; sw < nsweeps; ++sw) {
+        for (int64_t p = 0; p < np; ++p) {
+            int64_t i = pi[p], j = pj[p];
+            double wij = W[i * n + j];
+            double a = (i == j) ? wij * wij : wij * wij + W[i * n + i] * W[j * n + j];
+            double wdw = 0.0;
+            for (int64_t k = 0; k < n; ++k) wdw += W[i * n + k] * U[k * n + j];
+            double b = (S[i * n + j] - wij) + wdw;
+            double c = A[i * n + j] + D[p];
+            double mu = -c + soft(c - b / a, lam / a);
+            if (mu != 0.0) {
+                D[p] += mu;
+                for (int64_t k = 0; k < n; ++k) U[i * n + k] += mu * W[j * n + k];
+                if (i != j)
+                    for (int64_t k = 0; k < n; ++k) U[j * n + k] += mu * W[i * n + k];
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* a7. Armijo backtracking line search (Section 2 eq. Line-search; Section
+ * 6.1.2 uses alpha_0 = 1, beta = 1/2 and positive definiteness).
+ * READING: accept the first alpha = beta^t (t = 0..max_trials-1) for which
+ * A + alpha Delta is positive definite and
+ *     F(A + alpha Delta) <= F(A) + sigma alpha delta + eps_F,
+ *     delta = tr(G Delta) + lambda (||A + Delta||_1 - ||A||_1),
+ * with sigma = 1e-4 and the rounding allowance eps_F = 1e-12 max(|F(A)|, n):
+ * near the optimum the predicted decrease falls below what an FP64 objective
+ * can resolve, and without the allowance the test would reject unit steps on
+ * rounding noise alone.  On success A is overwritten with A + alpha Delta and
+ * F_inout with its objective.  Returns 0, or ORC_ELINESEARCH.              */
+int orc_line_search(const double *S, const double *W, double *A, int64_t n, double lam,
+                    const int32_t *pi, const int32_t *pj, int64_t np, const double *D,
+                    double sigma, double beta, int max_trials, double *F_inout,
+                    double *alpha_out, int *trials_out) {
+    double delta = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        int64_t i = pi[p], j = pj[p];
+        double mult = (i == j) ? 1.0 : 2.0;
+        double aij = A[i * n + j];
+        delta += mult * ((S[i * n + j] - W[i * n + j]) * D[p] + lam * (fabs(aij + D[p]) - fabs(aij)));
+    }
+    double *T = (double *)malloc((size_t)(n * n) * sizeof(double));
+    double epsF = 1e-12 * (fabs(*F_inout) > (double)n ? fabs(*F_inout) : (double)n);
+    double alpha = 1.0;
+    int ok = 0, t;
+    for (t = 0; t < max_trials; ++t) {
+        memcpy(T, A, (size_t)(n * n) * sizeof(double));
+        for (int64_t p = 0; p < np; ++p) {
+            int64_t i = pi[p], j = pj[p];
+            T[i * n + j] = A[i * n + j] + alpha * D[p];
+            T[j * n + i] = T[i * n + j];
+        }
+        double Ft;
+        if (orc_objective(S, T, n, lam, &Ft) == 0 && Ft <= *F_inout + sigma * alpha * delta + epsF) {
+            memcpy(A, T, (size_t)(n * n) * sizeof(double));
+            *F_inout = Ft;
+            ok = 1;
+            break;
+        }
+        alpha *= beta;
+    }
+    free(T);
+    if (alpha_out) *alpha_out = ok ? alpha : 0.0;
+    if (trials_out) *trials_out = ok ? t + 1 : max_trials;
+    return ok ? ORC_OK : ORC_ELINESEARCH;
+}
+
+/* ---------------------------------------------------------------------- */
+/* a8. The ML-cycle, Algorithm 1 with nu = nu_c = 1 (Section 7), using the
+ * dense one-block proximal Newton relaxation (QUIC-type, Sections 5.1-5.2).
+ *
+ * Relax(A, C_l):
+ *   1. Cholesky of A, W = A^{-1}, G = S - W                   (eq. gradHes)
+ *   2. free set F(A) restricted to C_l                         (eq. active_set)
+ *   3. at l = 0: relative KKT of A; stop when <= tol (Section 3.2 last
+ *      paragraph: the finest relaxation monitors convergence); keep this free
+ *      set and |G| to define the next cycle's hierarchy (Section 7)
+ *   4. Newton direction by nsweeps CD sweeps from Delta = 0   (eq. Quad_MLE_l1_prior)
+ *   5. Armijo line search, A <- A + alpha Delta
+ * Initial iterate A0 = diag(1 / (S_ii + lambda)) unless given; initial free set
+ * {(i,j): |S_ij| > lambda} united with supp(A0) (Section 7 footnote) with
+ * |G| = |S - A0^{-1}|.
+ * READING: nsweeps = min(1 + floor(k/3), 10) for cycle k.
+ *
+ * trace (optional, capacity trace_cap): after every relaxation, the objective
+ * and the level, as (F, level) pairs.                                         */
+typedef struct {
+    int status;
+    int cycles;
+    int relaxations;
+    int ls_trials;
+    double objective;
+    double rel_kkt;
+    double max_kkt;
+    double logdet;
+    int64_t nnz;
+    int64_t ntrace;
+} orc_info;
+
+int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles,
+              const double *A0, double *A, double *W_out, orc_info *info,
+              double *trace, int64_t trace_cap) {
+    if (n < 1 || !(lam > 0.0)) return ORC_EINVAL;
+    size_t nn = (size_t)(n * n);
+    double *L = (double *)malloc(nn * sizeof(double));
+    double *W = (double *)malloc(nn * sizeof(double));
+    double *U = (double *)malloc(nn * sizeof(double));
+    int64_t maxp = n * (n + 1) / 2;
+    int32_t *fi = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *fj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *ci = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *cj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *pi = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *pj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    double *absg = (double *)malloc((size_t)maxp * sizeof(double));
+    uint8_t *insupp = (uint8_t *)malloc((size_t)maxp);
+    uint8_t *tag = (uint8_t *)malloc((size_t)maxp);
+    double *D = (double *)malloc((size_t)maxp * sizeof(double));
+    int status = ORC_EMAXITER;
+    int relax = 0, lstrials = 0, cycles = 0;
+    int64_t ntrace = 0;
+    double F = 0.0, relkkt = INFINITY, maxkkt = INFINITY, logdet = 0.0;
+
+    if (A0) {
+        memcpy(A, A0, nn * sizeof(double));
+    } else {
+        memset(A, 0, nn * sizeof(double));
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(S[i * n + i] + lam > 0.0)) { status = ORC_ENOTPD; goto done; }
+            A[i * n + i] = 1.0 / (S[i * n + i] + lam);
+        }
+    }
+    /* initial free set and gradient */
+    if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
+    orc_inverse_from_chol(L, n, W);
+    int64_t nf = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i; j < n; ++j)
+            if (fabs(S[i * n + j]) > lam || A[i * n + j] != 0.0) {
+                fi[nf] = (int32_t)i;
+                fj[nf] = (int32_t)j;
+                absg[nf] = fabs(S[i * n + j] - W[i * n + j]);
+                ++nf;
+            }
+
+    for (int k = 0; k < max_cycles; ++k) {
+        cycles = k + 1;
+        int nsweeps = 1 + k / 3;
+        if (nsweeps > 10) nsweeps = 10;
+        for (int64_t p = 0; p < nf; ++p) insupp[p] = A[fi[p] * n + fj[p]] != 0.0;
+        int L_levels = 1;
+        orc_hierarchy(absg, insupp, nf, tag, &L_levels);
+        for (int l = L_levels; l >= 0; --l) {
+            /* 1. factor, invert, objective */
+            if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
+            logdet = orc_logdet_from_chol(L, n);
+            orc_inverse_from_chol(L, n, W);
+            double tr, l1;
+            trace_and_l1(S, A, n, &tr, &l1);
+            F = -logdet + tr + lam * l1;
+            /* 2. free set restricted to C_l */
+            int64_t np;
+            if (l == 0) {
+                np = orc_free_set(S, W, A, n, lam, NULL, NULL, 0, pi, pj);
+                relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
+                /* 3. keep F_{k+1} and |G| for the next hierarchy */
+                for (int64_t p = 0; p < np; ++p) {
+                    fi[p] = pi[p];
+                    fj[p] = pj[p];
+                    absg[p] = fabs(S[pi[p] * n + pj[p]] - W[pi[p] * n + pj[p]]);
+                }
+                nf = np;
+                if (relkkt <= tol) { status = ORC_OK; goto done; }
+            } else {
+                int64_t nc = 0;
+                for (int64_t p = 0; p < nf; ++p)
+                    if (tag[p] >= l) { ci[nc] = fi[p]; cj[nc] = fj[p]; ++nc; }
+                np = orc_free_set(S, W, A, n, lam, ci, cj, nc, pi, pj);
+            }
+            /* 4. Newton direction */
+            memset(U, 0, nn * sizeof(double));
+            memset(D, 0, (size_t)np * sizeof(double));
+            orc_cd_sweeps(S, W, A, n, lam, pi, pj, np, nsweeps, D, U);
+            int moved = 0;
+            for (int64_t p = 0; p < np; ++p) moved |= (D[p] != 0.0);
+            /* 5. line search */
+            if (moved) {
+                double alpha;
+                int tr_used;
+                int rc = orc_line_search(S, W, A, n, lam, pi, pj, np, D, 1e-4, 0.5, 30, &F,
+                                         &alpha, &tr_used);
+                lstrials += tr_used;
+                if (rc != ORC_OK) { status = rc; goto done; }
+            }
+            ++relax;
+            if (trace && ntrace < trace_cap) {
+                trace[2 * ntrace] = F;
+                trace[2 * ntrace + 1] = (double)l;
+                ++ntrace;
+            }
+        }
+    }
+done:
+    if (status == ORC_OK || status == ORC_EMAXITER || status == ORC_ELINESEARCH) {
+        if (orc_cholesky(A, n, L) == 0) {
+            logdet = orc_logdet_from_chol(L, n);
+            orc_inverse_from_chol(L, n, W);
+            double tr, l1;
+            trace_and_l1(S, A, n, &tr, &l1);
+            F = -logdet + tr + lam * l1;
+            relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
+            if (W_out) memcpy(W_out, W, nn * sizeof(double));
+        }
+    }
+    if (info) {
+        int64_t nnz = 0;
+        for (size_t t = 0; t < nn; ++t) nnz += A[t] != 0.0;
+        info->status = status;
+        info->cycles = cycles;
+        info->relaxations = relax;
+        info->ls_trials = lstrials;
+        info->objective = F;
+        info->rel_kkt = relkkt;
+        info->max_kkt = maxkkt;
+        info->logdet = logdet;
+        info->nnz = nnz;
+        info->ntrace = ntrace;
+    }
+    free(L); free(W); free(U); free(fi); free(fj); free(ci); free(cj); free(pi); free(pj);
+    free(absg); free(insupp); free(tag); free(D);
+    return status;
+}
+
+/* Relaxation count of trace entries written (for callers sizing buffers). */
+int64_t orc_max_pairs(int64_t n) { return n * (n + 1) / 2; }

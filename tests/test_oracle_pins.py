@@ -1,0 +1,483 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks one oracle function against a closed form, a library routine,
+brute force on a tiny input, a hand-derived fixture (tests/golden) or an
+optimality condition of the paper, chosen so that a dropped term, a wrong sign
+or index, or a transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00315_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _spd(n, seed, cond=10.0):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.exp(rng.uniform(0, np.log(cond), n))
+    return (q * ev) @ q.T
+
+
+def _S(n, m, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, n)) @ np.linalg.cholesky(_spd(n, seed + 1)).T
+    return X.T @ X / m
+
+
+# ---------------------------------------------------------------- generators
+def test_sparse_theta_structure():
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 57
+    t = synth.sparse_theta(n, rng)
+    off = t - np.diag(np.diag(t))
+    assert np.array_equal(off, off.T)
+    assert np.count_nonzero(np.triu(off, 1)) == (5 * n) // 2
+    a = np.abs(off[off != 0])
+    assert a.min() >= 0.1 and a.max() <= 0.3
+    assert np.allclose(np.diag(t), np.abs(off).sum(1) + 0.5)
+    assert np.linalg.eigvalsh(t).min() > 0
+
+
+def test_gaussian_samples_covariance():
+    rng = np.random.Generator(np.random.PCG64(3))
+    t = synth.tridiag_theta(6)
+    X = synth.gaussian_samples(t, 200000, rng)
+    emp = X.T @ X / X.shape[0]
+    assert np.abs(emp - np.linalg.inv(t)).max() < 0.03
+
+
+# ---------------------------------------------------------------- a1: S
+def test_form_S_matches_library_product():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((37, 11))
+    assert np.allclose(oracle.form_S(X), X.T @ X / 37, rtol=0, atol=1e-14)
+    # centring: the biased sample covariance (denominator m), eq. cov_estimate
+    assert np.allclose(oracle.form_S(X, center=True), np.cov(X, rowvar=False, bias=True),
+                       rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- a2/a3
+@pytest.mark.parametrize("n", [1, 2, 7, 33])
+def test_cholesky_logdet_inverse_match_library(n):
+    A = _spd(n, n)
+    info, L = oracle.cholesky(A)
+    assert info == 0
+    assert np.allclose(L, np.linalg.cholesky(A), rtol=0, atol=1e-12)
+    assert np.allclose(np.triu(L, 1), 0)
+    assert abs(oracle.logdet_from_chol(L) - np.linalg.slogdet(A)[1]) < 1e-11
+    assert np.allclose(oracle.inverse_from_chol(L), np.linalg.inv(A), rtol=1e-10, atol=1e-12)
+
+
+def test_cholesky_info_is_first_nonpositive_leading_minor():
+    A = _spd(9, 5)
+    A[5, 5] -= 50.0  # makes some leading minor from index 5 on non-positive
+    info, _ = oracle.cholesky(A)
+    # Sylvester: the first k with det(A[:k+1, :k+1]) <= 0 is the failing pivot
+    k = next(k for k in range(9) if np.linalg.det(A[: k + 1, : k + 1]) <= 0)
+    assert info == k + 1
+
+
+# ---------------------------------------------------------------- objective
+def test_objective_diagonal_closed_form():
+    rng = np.random.default_rng(1)
+    n = 5
+    S = _S(n, 40, 2)
+    a = rng.uniform(0.5, 2.0, n)
+    lam = 0.3
+    info, F = oracle.objective(S, np.diag(a), lam)
+    assert info == 0
+    expect = np.sum(-np.log(a) + np.diag(S) * a + lam * a)
+    assert abs(F - expect) < 1e-12
+
+
+def test_objective_reports_not_pd():
+    info, _ = oracle.objective(np.eye(3), -np.eye(3), 0.1)
+    assert info == 1
+
+
+# ---------------------------------------------------------------- a4 free set
+def test_free_set_is_where_a_single_cd_step_moves():
+    """Section 5.2: variables outside the free set stay at zero when the Newton
+    LASSO is solved over them alone.  At Delta = 0 the 1-D model of pair
+    (i, j) is found by brute force (dense numpy model), independently of the
+    oracle's CD formula and of the free-set formula."""
+    n, lam = 8, 0.15
+    S = _S(n, 12, 3)
+    rng = np.random.default_rng(4)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    A[1, 2] = A[2, 1] = 0.05  # one off-diagonal nonzero
+    A += 0.0 * rng.standard_normal((n, n))
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    free = set(zip(fi.tolist(), fj.tolist()))
+    G = S - W
+    grid = np.linspace(-2, 2, 40001)
+    for i in range(n):
+        for j in range(i, n):
+            E = np.zeros((n, n))
+            E[i, j] = E[j, i] = 1.0
+            # model(mu) = tr(mu E G) + 1/2 mu^2 tr(E W E W) + lam ||A + mu E||_1
+            lin = np.trace(E @ G)
+            quad = 0.5 * np.trace(E @ W @ E @ W)
+            l1 = np.abs(A[None, :, :] + grid[:, None, None] * E[None]).sum(axis=(1, 2))
+            model = lin * grid + quad * grid ** 2 + lam * l1
+            mu = grid[np.argmin(model)]
+            moves = abs(mu) > 1e-3
+            if A[i, j] != 0:
+                assert (i, j) in free
+            else:
+                assert ((i, j) in free) == moves, (i, j, mu)
+
+
+def test_free_set_restricted_to_candidates_keeps_order():
+    n, lam = 6, 0.05
+    S = _S(n, 9, 5)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    cand = (fi[::-1].copy(), fj[::-1].copy())
+    ci, cj = oracle.free_set(S, W, A, lam, cand=cand)
+    assert np.array_equal(ci, cand[0]) and np.array_equal(cj, cand[1])
+    assert all(i <= j for i, j in zip(fi, fj))
+    # row-major order of the upper triangle
+    keys = fi.astype(np.int64) * n + fj
+    assert np.all(np.diff(keys) > 0)
+
+
+# ---------------------------------------------------------------- KKT residual
+def test_rel_kkt_hand_derived_fixture():
+    g = json.load(open(os.path.join(GOLD, "kkt_2x2.json")))
+    r, mx = oracle.rel_kkt(np.array(g["S"]), np.array(g["W"]), np.array(g["A"]), g["lambda"])
+    assert abs(r - g["rel_kkt"]) < 1e-15 and abs(mx - g["max_kkt"]) < 1e-15
+
+
+# ---------------------------------------------------------------- a5 hierarchy
+def test_hierarchy_hand_derived_sizes():
+    g = json.load(open(os.path.join(GOLD, "hierarchy_sizes.json")))
+    rng = np.random.default_rng(6)
+    for case in g["cases"]:
+        nf, ns = case["nf"], case["ns"]
+        insupp = np.zeros(nf, dtype=np.uint8)
+        insupp[rng.choice(nf, ns, replace=False)] = 1
+        absg = rng.uniform(0, 1, nf)
+        tag, L = oracle.hierarchy(absg, insupp)
+        assert L == case["L"]
+        counts = {str(t): int((tag == t).sum()) for t in np.unique(tag)}
+        assert counts == case["count_by_tag"]
+
+
+def test_hierarchy_ranking_matches_library_sort_with_ties():
+    rng = np.random.default_rng(8)
+    nf = 301
+    insupp = (rng.random(nf) < 0.2).astype(np.uint8)
+    absg = rng.integers(0, 25, nf).astype(np.float64) / 7.0  # many exact ties
+    tag, L = oracle.hierarchy(absg, insupp)
+    ns = int(insupp.sum())
+    # independent ranking: numpy lexsort by (-|G|, position)
+    idx = np.flatnonzero(insupp == 0)
+    order = idx[np.lexsort((idx, -absg[idx]))]
+    sizes = [None, max((nf + 1) // 2, ns)]
+    while sizes[-1] > ns:
+        sizes.append(max((sizes[-1] + 1) // 2, ns))
+    assert L == len(sizes) - 1
+    assert np.all(tag[insupp == 1] == L)
+    for l in range(1, L + 1):
+        in_l = set(np.flatnonzero(insupp).tolist()) | set(order[: sizes[l] - ns].tolist())
+        assert in_l == set(np.flatnonzero(tag >= l).tolist())
+        assert len(in_l) == sizes[l]
+
+
+# ---------------------------------------------------------------- a6 CD sweeps
+def _model(G, W, A, D, lam):
+    """Newton LASSO objective of eq. Quad_MLE_l1_prior without f(A)."""
+    return np.trace(D @ G) + 0.5 * np.trace(D @ W @ D @ W) + lam * np.abs(A + D).sum()
+
+
+def _dense(n, pi, pj, d):
+    D = np.zeros((n, n))
+    D[pi, pj] = d
+    D[pj, pi] = d
+    return D
+
+
+def test_cd_single_coordinate_is_exact_1d_minimiser():
+    n, lam = 7, 0.1
+    S = _S(n, 10, 9)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    A[0, 3] = A[3, 0] = -0.02
+    W = np.linalg.inv(A)
+    G = S - W
+    rng = np.random.default_rng(10)
+    pairs = [(0, 3), (1, 1), (2, 5), (4, 6)]
+    # start from a nonzero Delta so that b includes (W Delta W)_ij
+    pi0 = np.array([p[0] for p in pairs], dtype=np.int32)
+    pj0 = np.array([p[1] for p in pairs], dtype=np.int32)
+    d0 = rng.uniform(-0.05, 0.05, len(pairs))
+    U0 = _dense(n, pi0, pj0, d0) @ W
+    for k, (i, j) in enumerate(pairs):
+        d, U = oracle.cd_sweeps(S, W, A, lam, pi0[k:k + 1], pj0[k:k + 1], 1, D=d0[k:k + 1], U=U0)
+        D_before = _dense(n, pi0, pj0, d0)
+        E = np.zeros((n, n))
+        E[i, j] = E[j, i] = 1.0
+        grid = d0[k] + np.linspace(-1, 1, 200001)
+        vals = [_model(G, W, A, D_before + (g - d0[k]) * E, lam) for g in grid[::100]]
+        g0 = grid[::100][int(np.argmin(vals))]
+        fine = g0 + np.linspace(-1e-3, 1e-3, 2001)
+        vals = [_model(G, W, A, D_before + (g - d0[k]) * E, lam) for g in fine]
+        best = fine[int(np.argmin(vals))]
+        assert abs(d[0] - best) < 2e-6, (i, j, d[0], best)
+        # U stays Delta W (library matmul)
+        Dn = D_before + (d[0] - d0[k]) * E
+        assert np.allclose(U, Dn @ W, atol=1e-13)
+
+
+def test_cd_sweeps_converge_to_lasso_kkt():
+    """Many sweeps solve the restricted Newton LASSO: its subgradient
+    (G + W Delta W + lambda sign) vanishes on the pair list."""
+    n, lam = 12, 0.08
+    S = _S(n, 30, 11)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    d, U = oracle.cd_sweeps(S, W, A, lam, fi, fj, 400)
+    D = _dense(n, fi, fj, d)
+    assert np.allclose(U, D @ W, atol=1e-12)
+    R = (S - W) + W @ D @ W
+    T = A + D
+    for i, j in zip(fi, fj):
+        if T[i, j] != 0:
+            assert abs(R[i, j] + lam * np.sign(T[i, j])) < 1e-9
+        else:
+            assert abs(R[i, j]) <= lam + 1e-9
+
+
+def test_cd_decreases_model():
+    n, lam = 10, 0.1
+    S = _S(n, 15, 12)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    prev = _model(S - W, W, A, np.zeros((n, n)), lam)
+    d = None
+    U = None
+    for _ in range(5):
+        d, U = oracle.cd_sweeps(S, W, A, lam, fi, fj, 1, D=d, U=U)
+        cur = _model(S - W, W, A, _dense(n, fi, fj, d), lam)
+        assert cur <= prev + 1e-14
+        prev = cur
+
+
+# ---------------------------------------------------------------- a7 line search
+def test_line_search_first_armijo_alpha():
+    n, lam = 9, 0.05
+    S = _S(n, 20, 13)
+    A = np.diag(1.0 / (np.diag(S) + lam))
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    d, _ = oracle.cd_sweeps(S, W, A, lam, fi, fj, 3)
+    d = d * 40.0  # an overlong step forces backtracking
+    _, F0 = oracle.objective(S, A, lam)
+    rc, A1, F1, alpha, trials = oracle.line_search(S, W, A, lam, fi, fj, d, F0)
+    assert rc == 0 and trials > 1
+    D = _dense(n, fi, fj, d)
+    delta = np.sum((S - W) * D) + lam * (np.abs(A + D).sum() - np.abs(A).sum())
+
+    def F(M):
+        s, ld = np.linalg.slogdet(M)
+        if s <= 0 or np.linalg.eigvalsh(M).min() <= 0:
+            return None
+        return -ld + np.sum(S * M) + lam * np.abs(M).sum()
+
+    epsF = 1e-12 * max(abs(F0), n)  # the rounding allowance of the acceptance test
+    for t in range(trials):
+        a = 0.5 ** t
+        val = F(A + a * D)
+        ok = val is not None and val <= F0 + 1e-4 * a * delta + epsF
+        assert ok == (t == trials - 1)
+    assert abs(alpha - 0.5 ** (trials - 1)) == 0
+    assert np.allclose(A1, A + alpha * D, atol=1e-15)
+    assert abs(F1 - F(A1)) < 1e-10
+
+
+# ---------------------------------------------------------------- a8 solve
+def _kkt_ok(S, A, lam, tol):
+    W = np.linalg.inv(A)
+    G = S - W
+    on = A != 0
+    assert np.abs(G[on] + lam * np.sign(A[on])).max() < tol
+    if (~on).any():
+        assert np.abs(G[~on]).max() <= lam + tol
+    assert np.allclose(np.diag(W), np.diag(S) + lam, atol=tol)
+
+
+def test_solve_diagonal_S_closed_form():
+    d = np.array([0.5, 1.0, 2.0, 3.5])
+    lam = 0.2
+    A, W, info, _ = oracle.solve(np.diag(d), lam, tol=1e-12)
+    assert info["status"] == 0
+    assert np.allclose(A, np.diag(1.0 / (d + lam)), atol=1e-14)
+
+
+def test_solve_large_lambda_gives_diagonal():
+    S = _S(8, 20, 14)
+    lam = np.abs(S - np.diag(np.diag(S))).max() + 1e-3
+    A, W, info, _ = oracle.solve(S, lam, tol=1e-12)
+    assert np.count_nonzero(A - np.diag(np.diag(A))) == 0
+    assert np.allclose(np.diag(A), 1.0 / (np.diag(S) + lam), atol=1e-13)
+
+
+@pytest.mark.parametrize("s12", [0.7, -0.45, 0.05])
+def test_solve_n2_closed_form(s12):
+    S = np.array([[1.3, s12], [s12, 0.8]])
+    lam = 0.1
+    A, _, info, _ = oracle.solve(S, lam, tol=1e-13)
+    Wx = np.array([[1.3 + lam, np.sign(s12) * max(abs(s12) - lam, 0.0)],
+                   [0.0, 0.8 + lam]])
+    Wx[1, 0] = Wx[0, 1]
+    assert np.allclose(A, np.linalg.inv(Wx), atol=1e-11)
+
+
+def _brute_force(S, lam):
+    """Enumerate the sign patterns of the off-diagonal entries; for each, solve
+    the smooth restricted problem (fixed support, fixed signs) by Newton's
+    method and keep the patterns whose solution satisfies the optimality
+    conditions of eq. subgradient1.  Independent of the oracle's method."""
+    n = S.shape[0]
+    offs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    sols = []
+    for pat in itertools.product((-1, 0, 1), repeat=len(offs)):
+        act = [(i, i, 0) for i in range(n)] + [(i, j, s) for (i, j), s in zip(offs, pat) if s != 0]
+        Es = []
+        for i, j, _ in act:
+            E = np.zeros((n, n))
+            E[i, j] = E[j, i] = 1.0
+            Es.append(E)
+        lin = np.array([np.sum((S + lam * (np.eye(n) if i == j else s * (1 - np.eye(n)))) * E)
+                        for (i, j, s), E in zip(act, Es)])
+
+        def fval(x):
+            M = sum(xk * E for xk, E in zip(x, Es))
+            if np.linalg.eigvalsh(M).min() <= 0:
+                return np.inf
+            return -np.linalg.slogdet(M)[1] + lin @ x
+
+        x = np.array([1.0 / (S[i, i] + lam) if i == j else 0.0 for i, j, _ in act])
+        ok = False
+        for _ in range(200):
+            M = sum(xk * E for xk, E in zip(x, Es))
+            Wm = np.linalg.inv(M)
+            g = lin - np.array([np.sum(Wm * E) for E in Es])
+            H = np.array([[np.trace(Wm @ Ep @ Wm @ Eq) for Eq in Es] for Ep in Es])
+            step = np.linalg.solve(H, -g)
+            dec = -g @ step
+            if dec < 1e-26:
+                ok = True
+                break
+            t, f0 = 1.0, fval(x)
+            while fval(x + t * step) > f0 - 0.25 * t * dec and t > 1e-12:
+                t *= 0.5
+            x = x + t * step
+            if np.abs(x).max() > 1e8:
+                break
+        if not ok:
+            continue
+        M = sum(xk * E for xk, E in zip(x, Es))
+        Wm = np.linalg.inv(M)
+        G = S - Wm
+        good = True
+        for (i, j), s in zip(offs, pat):
+            if s == 0:
+                good &= abs(G[i, j]) <= lam + 1e-10
+            else:
+                good &= M[i, j] * s > -1e-12
+        if good:
+            sols.append(M)
+    return sols
+
+
+@pytest.mark.parametrize("n,seed", [(2, 21), (3, 22), (3, 23), (4, 24)])
+def test_solve_matches_brute_force(n, seed):
+    S = _S(n, 2 * n, seed)
+    off = np.abs(S - np.diag(np.diag(S)))
+    # some entries in, some out; kept off any |S_ij| so that no pair sits
+    # exactly on the free-set boundary |G_ij| = lambda at the optimum
+    lam = 0.97 * float(np.median(off[off > 0]))
+    sols = _brute_force(S, lam)
+    assert sols, "brute force found no optimum"
+    A, _, info, _ = oracle.solve(S, lam, tol=1e-12)
+    assert info["status"] == 0
+    for M in sols:  # all surviving patterns describe the same (unique) optimum
+        assert np.allclose(A, M, atol=1e-9), (A, M)
+
+
+@pytest.mark.parametrize("cfg_seed", [31, 32])
+def test_solve_kkt_and_duality_gap(cfg_seed):
+    p = synth.random_problem(40, 60, 0.12, cfg_seed, gen="sparse")
+    S = oracle.form_S(p.X)
+    A, W, info, _ = oracle.solve(S, p.lam, tol=1e-11)
+    assert info["status"] == 0 and info["rel_kkt"] <= 1e-11
+    _kkt_ok(S, A, p.lam, 1e-8)
+    # duality certificate: W~ = S + clip(A^{-1} - S, -lam, lam) is dual feasible
+    Wi = np.linalg.inv(A)
+    Wt = S + np.clip(Wi - S, -p.lam, p.lam)
+    primal = -np.linalg.slogdet(A)[1] + np.sum(S * A) + p.lam * np.abs(A).sum()
+    dual = np.linalg.slogdet(Wt)[1] + S.shape[0]
+    assert primal - dual >= -1e-12
+    assert primal - dual < 1e-8
+    assert abs(primal - info["objective"]) < 1e-9
+
+
+def test_solve_monotone_per_relaxation():
+    p = synth.config_problem(1)
+    S = oracle.form_S(p.X)
+    A, W, info, tr = oracle.solve(S, p.lam, tol=1e-8, trace_cap=500)
+    assert info["status"] == 0
+    F = tr[:, 0]
+    # monotone up to the line search's rounding allowance 1e-12 max(|F|, n)
+    assert np.all(np.diff(F) <= 1e-12 * max(abs(F).max(), S.shape[0]))
+    assert set(tr[:, 1].astype(int).tolist()) >= {0, 1}
+
+
+def test_solve_scaling_and_permutation_equivariance():
+    p = synth.random_problem(25, 40, 0.15, 41, gen="sparse")
+    S = oracle.form_S(p.X)
+    A, *_ = oracle.solve(S, p.lam, tol=1e-12)
+    c = 3.0
+    A2, *_ = oracle.solve(c * S, c * p.lam, tol=1e-12)
+    assert np.allclose(A2, A / c, atol=1e-9)
+    perm = np.random.default_rng(42).permutation(25)
+    A3, *_ = oracle.solve(S[np.ix_(perm, perm)], p.lam, tol=1e-12)
+    assert np.allclose(A3, A[np.ix_(perm, perm)], atol=1e-9)
+
+
+def test_solve_block_separability():
+    S1 = _S(6, 12, 51)
+    S2 = _S(5, 10, 52)
+    lam = 0.1
+    S = np.zeros((11, 11))
+    S[:6, :6] = S1
+    S[6:, 6:] = S2
+    S[0, 8] = S[8, 0] = 0.05  # below lambda: blocks stay separate
+    A, *_ = oracle.solve(S, lam, tol=1e-12)
+    A1, *_ = oracle.solve(S1, lam, tol=1e-12)
+    A2, *_ = oracle.solve(S2, lam, tol=1e-12)
+    assert np.count_nonzero(A[:6, 6:]) == 0
+    assert np.allclose(A[:6, :6], A1, atol=1e-9) and np.allclose(A[6:, 6:], A2, atol=1e-9)
+
+
+def test_warm_start_at_optimum_stops_immediately():
+    """Algorithm 1 maps x^(k) to x^(k+1); at the optimum the finest-level check
+    stops the solve without moving A (resume from a saved iterate)."""
+    p = synth.random_problem(20, 30, 0.15, 61, gen="tridiag")
+    S = oracle.form_S(p.X)
+    A, *_ = oracle.solve(S, p.lam, tol=1e-12)
+    A2, _, info, _ = oracle.solve(S, p.lam, tol=1e-9, A0=A)
+    assert info["status"] == 0 and info["cycles"] == 1
+    assert np.allclose(A2, A, atol=1e-12)
