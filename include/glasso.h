@@ -1,0 +1,236 @@
+/*
+ * glasso.h - C ABI of the GB300 multilevel proximal-Newton solver for sparse
+ * inverse covariance estimation (Treister, Turek, Yavneh, arXiv 1607.00315).
+ *
+ * The problem (Section 5, eq. MLE_l1_prior):
+ *     A* = argmin_{A > 0}  -log det A + tr(S A) + lambda * sum_ij |A_ij|,
+ * with S the empirical covariance of the samples (eq. cov_estimate) and the
+ * diagonal penalised.  A* is unique for lambda > 0.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are dense, row-major, n x n, leading dimension n, FP64 unless
+ *    stated.  Symmetric inputs are read in full; outputs are written in full.
+ *  - Pair lists are upper-triangle index pairs (i <= j) as two int32 arrays,
+ *    in row-major order (i ascending, then j ascending); a pair (i, j)
+ *    stands for both A_ij and A_ji.
+ *  - The caller owns every buffer it passes.  Inputs are borrowed for the
+ *    duration of the call only, except for glasso_submit (see there).
+ *  - No call aborts, traps or throws: every failure is a status code.
+ *    GLASSO_ECUDA means a CUDA runtime call failed; the message is kept in
+ *    the context (glasso_last_error).
+ *  - Step-level entry points (glasso_potrf ... glasso_line_search) take
+ *    DEVICE pointers, run on the context's stream and return when their
+ *    results are complete.  They expose the individual steps of one
+ *    relaxation for testing and measurement; glasso_solve runs them all.
+ */
+#ifndef GLASSO_H
+#define GLASSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glasso_ctx glasso_ctx; /* opaque; bound to one device */
+
+typedef enum {
+    GLASSO_OK = 0,
+    GLASSO_EINVAL = 1,       /* bad argument (n < 1, lambda <= 0, NaN, asymmetric S, ...) */
+    GLASSO_ENOMEM = 2,       /* device allocation failed or footprint above the budget */
+    GLASSO_ENOTPD = 3,       /* initial iterate not positive definite (S_ii + lambda <= 0) */
+    GLASSO_ELINESEARCH = 4,  /* no step length passed the line search */
+    GLASSO_EMAXITER = 5,     /* tolerance not reached within max_cycles */
+    GLASSO_EAGAIN = 6,       /* glasso_poll: not finished yet */
+    GLASSO_ETIMEOUT = 7,     /* a bounded device or host wait ran out */
+    GLASSO_ECUDA = 8         /* a CUDA runtime call failed */
+} glasso_status;
+
+enum { GLASSO_FP64 = 0, GLASSO_MIXED = 1 };          /* precision modes */
+enum { GLASSO_INPUT_S = 0, GLASSO_INPUT_X = 1 };     /* what `data` holds */
+enum { GLASSO_F64 = 0, GLASSO_F32 = 1 };             /* element type of `data` */
+enum { GLASSO_HOST = 0, GLASSO_DEVICE = 1 };         /* where `data`, A0 and outputs live */
+
+typedef struct {
+    int device;              /* CUDA device ordinal */
+    size_t mem_budget_bytes; /* 0 = no limit; solves whose footprint exceeds it get ENOMEM */
+    int precision;           /* GLASSO_FP64 or GLASSO_MIXED */
+} glasso_config;
+
+typedef struct {
+    int input;        /* GLASSO_INPUT_S: data is S (n x n); GLASSO_INPUT_X: data is X (m x n, one sample per row) */
+    int dtype;        /* GLASSO_F64 or GLASSO_F32 (X only; S is always FP64) */
+    int location;     /* GLASSO_HOST or GLASSO_DEVICE for data, A0, A_out and W_out */
+    const void *data;
+    int64_t n, m;     /* m: number of samples (INPUT_X only) */
+    int center;       /* INPUT_X: subtract the sample mean before forming S */
+    double lambda;    /* > 0 */
+    double tol;       /* stop when the relative KKT residual is <= tol */
+    int max_cycles;   /* ML-cycles (Algorithm 1) before GLASSO_EMAXITER; <= 0 means 200 */
+    const double *A0; /* optional warm start (n x n, positive definite); NULL: diag(1/(S_ii + lambda)) */
+} glasso_problem;
+
+typedef struct {
+    int status;          /* glasso_status of this solve */
+    int cycles;          /* ML-cycles run */
+    int relaxations;     /* proximal-Newton relaxations (all levels) */
+    int ls_trials;       /* Cholesky trials in the line searches */
+    double objective;    /* F(A) at return */
+    double rel_kkt;      /* sum |min-norm subgradient| / ||A||_1 at return */
+    double max_kkt;      /* max |min-norm subgradient| at return */
+    double logdet;       /* log det A at return */
+    double seconds;      /* wall time of the solve */
+    int64_t nnz;         /* nonzeros of A (both triangles) */
+} glasso_info;
+
+/* ---- context -------------------------------------------------------- */
+
+/* Create a context on cfg->device.  Allocates nothing on the device until the
+ * first call that needs memory.  *out is NULL on failure. */
+glasso_status glasso_create(const glasso_config *cfg, glasso_ctx **out);
+
+/* Release every device buffer and stream of the context.  NULL is ignored. */
+void glasso_destroy(glasso_ctx *ctx);
+
+/* Run all later work of this context on `stream` (a cudaStream_t; NULL puts
+ * the context back on its own stream).  The stream stays owned by the caller. */
+glasso_status glasso_set_stream(glasso_ctx *ctx, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *glasso_strerror(glasso_status s);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char *glasso_last_error(glasso_ctx *ctx);
+
+/* ---- solver --------------------------------------------------------- */
+
+/* Solve one problem by the ML-cycle (Algorithm 1, nu = nu_c = 1, hierarchy of
+ * Section 7) with the dense proximal-Newton relaxation of Sections 5.1-5.2.
+ * A_out (required) and W_out (optional, = A^{-1}) are n x n in the location
+ * given by p->location.  info (optional) receives the statistics; the return
+ * value equals info->status. */
+glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
+                           double *W_out, glasso_info *info);
+
+/* Solve `count` independent problems (e.g. several subjects, or a lambda
+ * path) on the device.  A_out[k] receives the solution of p[k]; infos[k] (if
+ * infos is not NULL) its statistics.  When p[k].A0 is NULL and k > 0 and
+ * warm_from_prev is set, problem k starts from the solution of problem k-1
+ * (continuation along decreasing lambda, Section 2; both must have the same
+ * n and data).  Returns the first non-OK status, or GLASSO_OK. */
+glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int count,
+                                 int warm_from_prev, double **A_out, glasso_info *infos);
+
+/* Asynchronous serving interface.  glasso_submit copies the problem's inputs
+ * before returning (the caller may free them at once), queues the solve and
+ * returns a ticket.  A_out must stay valid until glasso_poll reports the
+ * ticket finished.  glasso_poll waits up to timeout_us microseconds (0: do
+ * not wait) and returns GLASSO_EAGAIN while the solve is running, or the
+ * solve's status once it has finished (info filled, ticket retired).  Solves
+ * from several tickets run concurrently on the device. */
+glasso_status glasso_submit(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
+                            uint64_t *ticket);
+glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
+                          glasso_info *info);
+
+/* ---- timing of the solver's kernel classes ---------------------------- */
+
+/* Kernel classes timed with CUDA events on the context's stream when
+ * profiling is on: 0 Cholesky of the iterate, 1 inverse (W = A^{-1}),
+ * 2 level-0 free-set scan, 3 CD sweeps, 4 line-search Cholesky trials. */
+#define GLASSO_PROF_CLASSES 5
+typedef struct {
+    double ms[GLASSO_PROF_CLASSES];        /* summed device time */
+    long long launches[GLASSO_PROF_CLASSES];
+    double work[GLASSO_PROF_CLASSES];      /* algorithmic flops (0, 1, 4) or bytes (2, 3) */
+} glasso_profile;
+
+/* Turn event timing of the kernel classes on (on != 0) or off.  Off by
+ * default; costs two events per timed call. */
+glasso_status glasso_set_profiling(glasso_ctx *ctx, int on);
+
+/* Copy the accumulated timings (and zero them when reset != 0). */
+glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset);
+
+/* ---- step-level entry points (device pointers) ----------------------- */
+
+/* a1. S = (1/m) X^T X (eq. cov_estimate), X m x n row-major of `dtype`
+ * (GLASSO_F64 or GLASSO_F32), S n x n FP64.  With center != 0 the sample mean
+ * is subtracted first.  FP64 X is accumulated in FP64; FP32 X on the tensor
+ * cores (TF32 inputs, FP32 accumulation) in GLASSO_MIXED contexts and in FP64
+ * otherwise. */
+glasso_status glasso_form_S(glasso_ctx *ctx, const void *X, int dtype, int64_t m, int64_t n,
+                            int center, double *S);
+
+/* a2. Cholesky factorisation in place: on return the lower triangle of A
+ * holds L with A = L L^T (upper triangle untouched).  *info = 0, or k+1 when
+ * the k-th pivot is not positive (A not positive definite: the line-search
+ * feasibility test of Section 6.1.2); *logdet = 2 sum_i log L_ii when
+ * *info = 0.  Blocked right-looking; FP64. */
+glasso_status glasso_potrf(glasso_ctx *ctx, double *A, int64_t n, int *info, double *logdet);
+
+/* a3. W = A^{-1} = L^{-T} L^{-1} from the Cholesky factor L (lower triangle
+ * read), eq. gradHes.  W is written in full.  FP64. */
+glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double *W);
+
+/* a4. Free set of eq. active_set, {(i,j): A_ij != 0 or |(S - W)_ij| > lambda},
+ * restricted to a candidate set C_l (eq. MLE_l1_prior_C).  When cand_i is
+ * NULL all upper-triangle pairs are candidates and the scan also returns the
+ * relative KKT residual (min-norm subgradient, eq. subgradient1, over all
+ * (i, j), divided by ||A||_1) in *rel_kkt and its max norm in *max_kkt
+ * (either may be NULL); otherwise cand_i/cand_j (ncand pairs, device) are
+ * filtered in their order.  out_i/out_j (device, capacity n(n+1)/2 for the
+ * full scan, ncand otherwise) receive the free pairs in candidate order,
+ * absg (device, optional) |S - W| on them; *count their number. */
+glasso_status glasso_free_set(glasso_ctx *ctx, const double *S, const double *W,
+                              const double *A, int64_t n, double lambda,
+                              const int32_t *cand_i, const int32_t *cand_j, int64_t ncand,
+                              int32_t *out_i, int32_t *out_j, double *absg, int64_t *count,
+                              double *rel_kkt, double *max_kkt);
+
+/* a5. Multilevel hierarchy (Section 3.2, Section 7): given the previous fine
+ * free set (nf pairs) with |G| on each (absg, device) and a support flag
+ * (insupp, device uint8), tag[p] (device uint8) receives the coarsest level
+ * whose set C_l holds pair p and *levels the number L of levels:
+ * |C_1| = max(ceil(nf/2), |supp|), |C_{l+1}| = max(ceil(|C_l|/2), |supp|)
+ * until |C_L| = |supp|; C_l = support + the non-support pairs of largest |G|
+ * (ties: earlier pair first).  nf <= 2^31 - 1. */
+glasso_status glasso_hierarchy(glasso_ctx *ctx, const double *absg, const uint8_t *insupp,
+                               int64_t nf, uint8_t *tag, int *levels);
+
+/* a6. nsweeps coordinate-descent sweeps over the pair list on the Newton
+ * LASSO of eq. Quad_MLE_l1_prior,
+ *   min_Delta tr(Delta (S - W)) + 1/2 tr(Delta W Delta W) + lambda ||A + Delta||_1,
+ * in list order.  Each coordinate takes the exact 1-D minimiser
+ * mu = -c + S_{lambda/a}(c - b/a) (eq. 1d_l1 and eq. shrinkage) with
+ * a = W_ij^2 + W_ii W_jj (W_ii^2 on the diagonal), b = (S - W)_ij + (W Delta W)_ij,
+ * c = A_ij + Delta_ij.  D (np, device) holds Delta on the pairs and U (n x n,
+ * device) = Delta W; both are read and updated.  The result equals the
+ * sequential sweep up to floating-point reassociation. */
+glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W,
+                               const double *A, int64_t n, double lambda, const int32_t *pi,
+                               const int32_t *pj, int64_t np, int nsweeps, double *D, double *U);
+
+/* a7. Armijo backtracking line search (eq. Line-search; Section 6.1.2 with
+ * alpha_0 = 1, beta = 1/2): the first alpha = 2^-t, t < max_trials, for which
+ * A + alpha Delta is positive definite and
+ *   F(A + alpha Delta) <= F_A + sigma alpha delta + 1e-12 max(|F_A|, n),
+ *   delta = tr((S - W) Delta) + lambda (||A + Delta||_1 - ||A||_1),
+ * where F_A = F(A) is passed in (the last term absorbs objective rounding).
+ * On success A (device, n x n) becomes A + alpha Delta and the outputs are
+ * set; otherwise GLASSO_ELINESEARCH and A is unchanged. */
+glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double *W, double *A,
+                                 int64_t n, double lambda, const int32_t *pi, const int32_t *pj,
+                                 int64_t np, const double *D, double F_A, double sigma,
+                                 int max_trials, double *F_new, double *alpha, int *trials);
+
+/* F(A) = -log det A + tr(S A) + lambda ||A||_1 (eq. MLE_l1_prior); *info as
+ * glasso_potrf (F undefined when *info != 0). */
+glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A, int64_t n,
+                               double lambda, double *F, int *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLASSO_H */

@@ -1,0 +1,989 @@
+// Host side of the library: the C ABI of include/glasso.h, device workspace,
+// the ML-cycle driver (Algorithm 1 with nu = nu_c = 1 and the hierarchy of
+// Section 7, relaxation = dense proximal Newton of Sections 5.1-5.2), the
+// batch entry point and the asynchronous serving queue.
+//
+// Control flow per relaxation (device work on one stream, host reads a few
+// scalars at the marked points):
+//   W = A^{-1} from the current Cholesky factor            (dense.cu)
+//   free set on C_l (+ KKT at level 0)          [sync]     (scan.cu)
+//   per-pair data, U = 0, Delta = 0, CD sweeps             (scan.cu, cd.cu)
+//   delta, tr(S Delta)                          [sync]     (scan.cu)
+//   line search: T = A + alpha Delta, Cholesky  [sync per trial]
+//   accept: A += alpha Delta, the trial's factor becomes the new factor.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "glasso_internal.h"
+
+using namespace glx;
+
+namespace {
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return fail_cuda(err, e_, #call);   \
+    } while (0)
+
+glasso_status fail_cuda(std::string &err, cudaError_t e, const char *what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return GLASSO_ECUDA;
+}
+
+size_t footprint(int64_t n, int64_t m, int xbytes) {
+    const size_t nn = (size_t)n * (size_t)n;
+    const size_t pairs = (size_t)n * (size_t)(n + 1) / 2;
+    size_t b = 6 * nn * sizeof(double);                           // S A L T W U
+    b += pairs * (6 * sizeof(int32_t) + 7 * sizeof(double) + 3);  // pair lists
+    b += (size_t)n * ((n + 31) / 32) * sizeof(uint32_t);          // masks
+    b += (size_t)(n + 1) * sizeof(long long) + (size_t)n * 6 * sizeof(double);
+    if (m > 0) b += (size_t)m * n * (sizeof(double) + xbytes) + (size_t)n * sizeof(double);
+    return b + (4u << 20);
+}
+
+template <typename T>
+cudaError_t dalloc(T *&p, size_t count, cudaStream_t st) {
+    if (p) {
+        cudaError_t e = cudaFreeAsync(p, st);
+        p = nullptr;
+        if (e != cudaSuccess) return e;
+    }
+    if (count == 0) count = 1;
+    return cudaMallocAsync((void **)&p, count * sizeof(T), st);
+}
+
+template <typename T>
+void dfree(T *&p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+}
+
+void work_free(Work &w, cudaStream_t st) {
+    dfree(w.S, st); dfree(w.A, st); dfree(w.L, st); dfree(w.T, st); dfree(w.W, st); dfree(w.U, st);
+    dfree(w.Xin, st); dfree(w.Xraw, st);
+    dfree(w.fi, st); dfree(w.fj, st); dfree(w.fabsg, st); dfree(w.ftag, st); dfree(w.fsupp, st);
+    dfree(w.pi, st); dfree(w.pj, st); dfree(w.pabsg, st); dfree(w.D, st);
+    dfree(w.p_inva, st); dfree(w.p_g, st); dfree(w.p_a, st); dfree(w.p_s, st);
+    dfree(w.mask, st); dfree(w.rowcnt, st); dfree(w.rowred, st); dfree(w.flags, st);
+    dfree(w.blkcnt, st); dfree(w.redbuf, st);
+    dfree(w.cd_part, st); dfree(w.cd_mu, st); dfree(w.cd_seg, st); dfree(w.cd_emu, st);
+    dfree(w.cd_esrc, st); dfree(w.sc, st);
+    if (w.sc_host) cudaFreeHost(w.sc_host);
+    w.sc_host = nullptr;
+    w.cap_n = w.cap_pairs = w.cap_x = w.cap_xraw = w.cap_blk = w.cap_red = 0;
+}
+
+glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err) {
+    if (!w.sc) {
+        CK(dalloc(w.sc, 1, st));
+        CK(cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)));
+        CK(dalloc(w.redbuf, 3 * 1024, st));
+        w.cap_red = 3 * 1024;
+        CK(dalloc(w.cd_part, (size_t)CD_MAX_CHUNKS * CD_B + (size_t)CD_B * CD_B, st));
+        CK(dalloc(w.cd_mu, CD_B, st));
+        CK(dalloc(w.cd_seg, 4 * CD_B + 8, st));
+        CK(dalloc(w.cd_emu, 2 * CD_B, st));
+        CK(dalloc(w.cd_esrc, 2 * CD_B, st));
+    }
+    if (n <= w.cap_n) return GLASSO_OK;
+    const size_t nn = (size_t)n * (size_t)n;
+    const int64_t pairs = n * (n + 1) / 2;
+    CK(dalloc(w.S, nn, st)); CK(dalloc(w.A, nn, st)); CK(dalloc(w.L, nn, st));
+    CK(dalloc(w.T, nn, st)); CK(dalloc(w.W, nn, st)); CK(dalloc(w.U, nn, st));
+    CK(dalloc(w.fi, pairs, st)); CK(dalloc(w.fj, pairs, st)); CK(dalloc(w.fabsg, pairs, st));
+    CK(dalloc(w.ftag, pairs, st)); CK(dalloc(w.fsupp, pairs, st));
+    CK(dalloc(w.pi, pairs, st)); CK(dalloc(w.pj, pairs, st)); CK(dalloc(w.pabsg, pairs, st));
+    CK(dalloc(w.D, pairs, st));
+    CK(dalloc(w.p_inva, pairs, st)); CK(dalloc(w.p_g, pairs, st)); CK(dalloc(w.p_a, pairs, st));
+    CK(dalloc(w.p_s, pairs, st));
+    CK(dalloc(w.flags, pairs, st));
+    w.cap_blk = (pairs + 1023) / 1024 + 1;
+    CK(dalloc(w.blkcnt, w.cap_blk, st));
+    CK(dalloc(w.mask, (size_t)n * ((n + 31) / 32), st));
+    CK(dalloc(w.rowcnt, n + 1, st));
+    CK(dalloc(w.rowred, (size_t)n * 6, st));
+    w.cap_n = n;
+    w.cap_pairs = pairs;
+    return GLASSO_OK;
+}
+
+glasso_status work_ensure_x(Work &w, int64_t m, int64_t n, int xbytes, cudaStream_t st,
+                            std::string &err) {
+    const int64_t need = m * n + n;
+    if (need > w.cap_x) {
+        CK(dalloc(w.Xin, need, st));
+        w.cap_x = need;
+    }
+    const int64_t rawb = m * n * xbytes;
+    if (rawb > w.cap_xraw) {
+        CK(dalloc(w.Xraw, rawb, st));
+        w.cap_xraw = rawb;
+    }
+    return GLASSO_OK;
+}
+
+// ---- validation -----------------------------------------------------------
+__global__ void k_check_sym(const double *__restrict__ S, int64_t n, int *bad_sym, int *bad_nan,
+                            double *maxabs_part) {
+    __shared__ double red[256];
+    double mx = 0.0;
+    int nan = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double v = S[t];
+        if (!isfinite(v)) nan = 1;
+        mx = fmax(mx, fabs(v));
+    }
+    if (nan) atomicExch(bad_nan, 1);
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) maxabs_part[blockIdx.x] = red[0];
+}
+
+__global__ void k_check_sym2(const double *__restrict__ S, int64_t n, const double *maxabs_part,
+                             int nparts, int *bad_sym) {
+    __shared__ double mx;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int p = 0; p < nparts; ++p) m = fmax(m, maxabs_part[p]);
+        mx = m;
+    }
+    __syncthreads();
+    const double tol = 1e-12 * mx;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = t / n, j = t % n;
+        if (j > i && fabs(S[t] - S[j * n + i]) > tol) atomicExch(bad_sym, 1);
+    }
+}
+
+// Returns OK, or EINVAL on NaN/Inf or asymmetry beyond 1e-12 max|S|.
+glasso_status check_symmetric(Work &w, const double *M, int64_t n, cudaStream_t st,
+                              std::string &err) {
+    CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), st));
+    int *bad_nan = &w.sc->err;
+    int *bad_sym = &w.sc->bad_sym;
+    const int parts = 256;
+    k_check_sym<<<parts, 256, 0, st>>>(M, n, bad_sym, bad_nan, w.redbuf);
+    k_check_sym2<<<parts, 256, 0, st>>>(M, n, w.redbuf, parts, bad_sym);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (w.sc_host->err || w.sc_host->bad_sym) return GLASSO_EINVAL;
+    return GLASSO_OK;
+}
+
+// ---- the solver -------------------------------------------------------------
+struct Prof {
+    bool on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    double ms[GLASSO_PROF_CLASSES] = {0};
+    long long count[GLASSO_PROF_CLASSES] = {0};
+    double work[GLASSO_PROF_CLASSES] = {0};
+    std::vector<double> pend_work;
+};
+
+struct Solver {
+    Work &w;
+    cudaStream_t st;
+    std::string &err;
+    Prof *prof;
+    glasso_status sync() {
+        CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return GLASSO_OK;
+    }
+    void mark_begin(int cls, cudaEvent_t &b) {
+        if (!prof || !prof->on) return;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, st);
+        (void)cls;
+    }
+    void mark_end(int cls, cudaEvent_t b, double work) {
+        if (!prof || !prof->on) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, st);
+        prof->ev.push_back({cls, {b, e}});
+        prof->pend_work.push_back(work);
+    }
+};
+
+void prof_collect(Prof *prof) {
+    if (!prof) return;
+    for (size_t k = 0; k < prof->ev.size(); ++k) {
+        float ms = 0.f;
+        cudaEventSynchronize(prof->ev[k].second.second);
+        cudaEventElapsedTime(&ms, prof->ev[k].second.first, prof->ev[k].second.second);
+        int c = prof->ev[k].first;
+        prof->ms[c] += ms;
+        prof->count[c] += 1;
+        prof->work[c] += prof->pend_work[k];
+        cudaEventDestroy(prof->ev[k].second.first);
+        cudaEventDestroy(prof->ev[k].second.second);
+    }
+    prof->ev.clear();
+    prof->pend_work.clear();
+}
+
+// Runs the ML-cycle solve on w.S (and w.A if have_A0).  Leaves the iterate in
+// w.A and its inverse in w.W when W is requested (want_W).
+glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
+                         bool have_A0, bool want_W, glasso_info *info) {
+    Work &w = sv.w;
+    cudaStream_t st = sv.st;
+    std::string &err = sv.err;
+    DevScalars *sc = w.sc;
+    DevScalars *h = w.sc_host;
+    const double sigma = 1e-4;
+    const int max_trials = 30;
+    const double nd = (double)n;
+    const double flop_chol = nd * nd * nd / 3.0, flop_inv = 2.0 * nd * nd * nd / 3.0;
+    int cycles = 0, relax = 0, lstrials = 0;
+    double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
+    long long nnz = 0;
+    glasso_status status = GLASSO_EMAXITER;
+    bool W_valid = false, fresh_scan = false;
+    int64_t nf = 0;
+    cudaEvent_t eb;
+
+    CK(cudaMemsetAsync(sc, 0, sizeof(DevScalars), st));
+    if (!have_A0) CK(init_diag(w.S, n, lam, w.A, sc, st));
+    CK(cudaMemcpyAsync(w.L, w.A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    sv.mark_begin(0, eb);
+    CK(potrf(w.L, n, sc, st));
+    sv.mark_end(0, eb, flop_chol);
+    if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+    if (h->err || h->info != 0) return GLASSO_ENOTPD;
+    logdet = h->logdet;
+    sv.mark_begin(1, eb);
+    CK(inverse(w.L, n, w.W, w.T, w.U, st));
+    sv.mark_end(1, eb, flop_inv);
+    W_valid = true;
+    // initial free set (Section 7 footnote): {|S_ij| > lambda} united with supp(A0)
+    CK(scan_full(w.S, w.W, w.A, n, lam, 1, w, w.fi, w.fj, w.fabsg, sc, st));
+    if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+    nf = h->count;
+    trSA = h->trSA;
+    l1 = h->l1;
+    F = -logdet + trSA + lam * l1;
+
+    for (int k = 0; k < max_cycles; ++k) {
+        cycles = k + 1;
+        const int nsweeps = std::min(1 + k / 3, 10);
+        CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
+        CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        const int Lv = h->levels;
+        for (int l = Lv; l >= 0; --l) {
+            fresh_scan = false;
+            if (!W_valid) {
+                sv.mark_begin(1, eb);
+                CK(inverse(w.L, n, w.W, w.T, w.U, st));
+                sv.mark_end(1, eb, flop_inv);
+                W_valid = true;
+            }
+            int64_t np;
+            if (l == 0) {
+                sv.mark_begin(2, eb);
+                CK(scan_full(w.S, w.W, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+                sv.mark_end(2, eb, 3.0 * nd * (nd + 1) / 2 * 8.0);
+                if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                np = h->count;
+                trSA = h->trSA;
+                l1 = h->l1;
+                nnz = h->nnz;
+                F = -logdet + trSA + lam * l1;
+                relkkt = h->kkt_sum / l1;
+                maxkkt = h->kkt_max;
+                fresh_scan = true;
+                CK(cudaMemcpyAsync(w.fi, w.pi, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(w.fj, w.pj, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(w.fabsg, w.pabsg, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                nf = np;
+                if (relkkt <= tol) {
+                    status = GLASSO_OK;
+                    goto done;
+                }
+            } else {
+                CK(scan_cand(w.S, w.W, w.A, n, lam, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
+                             nullptr, sc, st));
+                if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                np = h->count;
+            }
+            ++relax;
+            if (np == 0) continue;
+            CK(pair_prep(w.S, w.W, w.A, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+            CK(cudaMemsetAsync(w.U, 0, (size_t)(n * n) * sizeof(double), st));
+            CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
+            sv.mark_begin(3, eb);
+            CK(cd_sweeps(w.W, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
+            sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 8.0);
+            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
+            if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            if (!h->moved) continue;
+            {
+                const double delta = h->delta, trSD = h->trSD;
+                const double epsF = 1e-12 * std::max(fabs(F), nd);
+                double alpha = 1.0;
+                bool ok = false;
+                double FT = 0.0, dl1 = 0.0, ldT = 0.0;
+                for (int t = 0; t < max_trials; ++t) {
+                    CK(ls_build_trial(w.A, w.T, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                    sv.mark_begin(4, eb);
+                    CK(potrf(w.T, n, sc, st));
+                    sv.mark_end(4, eb, flop_chol);
+                    CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
+                    if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                    ++lstrials;
+                    if (h->info == 0) {
+                        ldT = h->logdet;
+                        dl1 = h->dl1;
+                        FT = -ldT + trSA + alpha * trSD + lam * (l1 + dl1);
+                        if (FT <= F + sigma * alpha * delta + epsF) {
+                            ok = true;
+                            break;
+                        }
+                    }
+                    alpha *= 0.5;
+                }
+                if (!ok) {
+                    status = GLASSO_ELINESEARCH;
+                    goto done;
+                }
+                CK(ls_apply(w.A, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                std::swap(w.L, w.T);
+                logdet = ldT;
+                trSA += alpha * trSD;
+                l1 += dl1;
+                F = FT;
+                W_valid = false;
+            }
+        }
+    }
+done:
+    if (!fresh_scan) {
+        if (!W_valid) {
+            CK(inverse(w.L, n, w.W, w.T, w.U, st));
+            W_valid = true;
+        }
+        CK(scan_full(w.S, w.W, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        trSA = h->trSA;
+        l1 = h->l1;
+        nnz = h->nnz;
+        F = -logdet + trSA + lam * l1;
+        relkkt = h->kkt_sum / l1;
+        maxkkt = h->kkt_max;
+    }
+    (void)want_W;
+    if (info) {
+        info->status = status;
+        info->cycles = cycles;
+        info->relaxations = relax;
+        info->ls_trials = lstrials;
+        info->objective = F;
+        info->rel_kkt = relkkt;
+        info->max_kkt = maxkkt;
+        info->logdet = logdet;
+        info->nnz = nnz;
+    }
+    return status;
+}
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+// Stage the problem's S (or X -> S) and A0 on the device in w.
+glasso_status stage_problem(Work &w, cudaStream_t st, const glasso_problem *p, std::string &err) {
+    const int64_t n = p->n;
+    const cudaMemcpyKind kind = p->location == GLASSO_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice;
+    glasso_status s = work_ensure(w, n, st, err);
+    if (s != GLASSO_OK) return s;
+    if (p->input == GLASSO_INPUT_S) {
+        CK(cudaMemcpyAsync(w.S, p->data, (size_t)(n * n) * sizeof(double), kind, st));
+    } else {
+        const int xb = p->dtype == GLASSO_F32 ? 4 : 8;
+        s = work_ensure_x(w, p->m, n, xb, st, err);
+        if (s != GLASSO_OK) return s;
+        const void *X = p->data;
+        if (p->location == GLASSO_HOST) {
+            CK(cudaMemcpyAsync(w.Xraw, p->data, (size_t)(p->m * n) * xb, kind, st));
+            X = w.Xraw;
+        }
+        CK(form_S(X, p->dtype, p->m, n, p->center, w.S, w.Xin, st));
+    }
+    s = check_symmetric(w, w.S, n, st, err);
+    if (s != GLASSO_OK) return s;
+    if (p->A0) {
+        CK(cudaMemcpyAsync(w.A, p->A0, (size_t)(n * n) * sizeof(double), kind, st));
+        s = check_symmetric(w, w.A, n, st, err);
+        if (s != GLASSO_OK) return s;
+    }
+    return GLASSO_OK;
+}
+
+glasso_status validate(const glasso_problem *p) {
+    if (!p || !p->data || p->n < 1 || !finite_pos(p->lambda) || !(p->tol >= 0.0)) return GLASSO_EINVAL;
+    if (p->input != GLASSO_INPUT_S && p->input != GLASSO_INPUT_X) return GLASSO_EINVAL;
+    if (p->location != GLASSO_HOST && p->location != GLASSO_DEVICE) return GLASSO_EINVAL;
+    if (p->input == GLASSO_INPUT_X && (p->m < 1 || (p->dtype != GLASSO_F64 && p->dtype != GLASSO_F32)))
+        return GLASSO_EINVAL;
+    if (p->n > 46340) return GLASSO_EINVAL;  // n^2 int32-indexed pair bound
+    return GLASSO_OK;
+}
+
+glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_problem *p,
+                       double *A_out, double *W_out, glasso_info *info, std::string &err,
+                       Prof *prof, bool reuse_A, int out_location) {
+    auto t0 = std::chrono::steady_clock::now();
+    glasso_info loc;
+    memset(&loc, 0, sizeof(loc));
+    glasso_status s = validate(p);
+    if (s == GLASSO_OK && !A_out) s = GLASSO_EINVAL;
+    if (s == GLASSO_OK && budget) {
+        const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
+        if (footprint(p->n, m, p->dtype == GLASSO_F32 ? 4 : 8) > budget) s = GLASSO_ENOMEM;
+    }
+    if (s == GLASSO_OK) {
+        glasso_problem q = *p;
+        if (reuse_A) q.A0 = nullptr;
+        s = stage_problem(w, st, &q, err);
+    }
+    if (s == GLASSO_OK) {
+        Solver sv{w, st, err, prof};
+        const int mc = p->max_cycles > 0 ? p->max_cycles : 200;
+        s = solve_core(sv, p->n, p->lambda, p->tol, mc, p->A0 != nullptr || reuse_A, W_out != nullptr,
+                       &loc);
+        if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
+            const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost
+                                                                    : cudaMemcpyDeviceToDevice;
+            const size_t bytes = (size_t)(p->n * p->n) * sizeof(double);
+            cudaError_t e = cudaMemcpyAsync(A_out, w.A, bytes, kind, st);
+            if (e == cudaSuccess && W_out) e = cudaMemcpyAsync(W_out, w.W, bytes, kind, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = fail_cuda(err, e, "copy out");
+        }
+        if (prof) prof_collect(prof);
+    }
+    loc.status = s;
+    loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = loc;
+    return s;
+}
+
+// ---- serving --------------------------------------------------------------
+struct Request {
+    uint64_t ticket = 0;
+    glasso_problem p{};
+    std::vector<char> data;
+    std::vector<double> a0;
+    double *A_out = nullptr;
+    int out_location = GLASSO_HOST;
+    glasso_info info{};
+    glasso_status status = GLASSO_EAGAIN;
+    size_t fp = 0;
+    bool done = false;
+};
+
+struct Serve {
+    glasso_ctx *ctx = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> all;
+    std::vector<std::thread> workers;
+    size_t reserved = 0;
+    uint64_t next = 1;
+    bool stop = false;
+};
+
+int serve_slots() {
+    const char *e = getenv("GLASSO_SERVE_SLOTS");
+    int k = e ? atoi(e) : 4;
+    return k < 1 ? 1 : (k > 64 ? 64 : k);
+}
+
+void worker_main(Serve *sv) {
+    cudaSetDevice(sv->ctx->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    Work w;
+    std::string err;
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                if (sv->stop) return true;
+                if (sv->queue.empty()) return false;
+                // admission: the head request must fit the remaining budget
+                const size_t b = sv->ctx->budget;
+                return b == 0 || sv->reserved == 0 || sv->reserved + sv->queue.front()->fp <= b;
+            });
+            if (sv->stop) break;
+            r = sv->queue.front();
+            sv->queue.pop_front();
+            sv->reserved += r->fp;
+        }
+        if (w.cap_n > 0 && (w.cap_n < r->p.n || w.cap_n > 2 * r->p.n)) work_free(w, st);
+        glasso_info info;
+        glasso_status s = solve_in(w, st, 0, &r->p, r->A_out, nullptr, &info, err, nullptr, false,
+                                   r->out_location);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->info = info;
+            r->status = s;
+            r->done = true;
+            sv->reserved -= r->fp;
+            r->data.clear();
+            r->data.shrink_to_fit();
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    work_free(w, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+}
+
+Serve *serve_get(glasso_ctx *ctx) {
+    if (!ctx->serve) {
+        Serve *s = new Serve();
+        s->ctx = ctx;
+        const int k = serve_slots();
+        for (int i = 0; i < k; ++i) s->workers.emplace_back(worker_main, s);
+        ctx->serve = s;
+    }
+    return (Serve *)ctx->serve;
+}
+
+void serve_shutdown(glasso_ctx *ctx) {
+    Serve *s = (Serve *)ctx->serve;
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->workers) t.join();
+    for (auto &kv : s->all) delete kv.second;
+    delete s;
+    ctx->serve = nullptr;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char *glasso_strerror(glasso_status s) {
+    switch (s) {
+        case GLASSO_OK: return "ok";
+        case GLASSO_EINVAL: return "invalid argument";
+        case GLASSO_ENOMEM: return "out of device memory or over budget";
+        case GLASSO_ENOTPD: return "initial iterate not positive definite";
+        case GLASSO_ELINESEARCH: return "line search failed";
+        case GLASSO_EMAXITER: return "maximum number of cycles reached";
+        case GLASSO_EAGAIN: return "not finished";
+        case GLASSO_ETIMEOUT: return "timed out";
+        case GLASSO_ECUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+glasso_status glasso_create(const glasso_config *cfg, glasso_ctx **out) {
+    if (!out) return GLASSO_EINVAL;
+    *out = nullptr;
+    if (!cfg || (cfg->precision != GLASSO_FP64 && cfg->precision != GLASSO_MIXED)) return GLASSO_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
+        return GLASSO_ECUDA;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return GLASSO_ECUDA;
+    glasso_ctx *c = new glasso_ctx();
+    c->device = cfg->device;
+    c->precision = cfg->precision;
+    c->budget = cfg->mem_budget_bytes;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return GLASSO_ECUDA;
+    }
+    c->stream = c->own_stream;
+    *out = c;
+    return GLASSO_OK;
+}
+
+void glasso_destroy(glasso_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    work_free(ctx->w, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->prof) delete (Prof *)ctx->prof;
+    cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+glasso_status glasso_set_stream(glasso_ctx *ctx, void *stream) {
+    if (!ctx) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return GLASSO_OK;
+}
+
+const char *glasso_last_error(glasso_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+glasso_status glasso_set_profiling(glasso_ctx *ctx, int on) {
+    if (!ctx) return GLASSO_EINVAL;
+    if (!ctx->prof) ctx->prof = new Prof();
+    Prof *p = (Prof *)ctx->prof;
+    p->on = on != 0;
+    return GLASSO_OK;
+}
+
+glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset) {
+    if (!ctx || !out) return GLASSO_EINVAL;
+    memset(out, 0, sizeof(*out));
+    Prof *p = (Prof *)ctx->prof;
+    if (!p) return GLASSO_OK;
+    for (int c = 0; c < GLASSO_PROF_CLASSES; ++c) {
+        out->ms[c] = p->ms[c];
+        out->launches[c] = p->count[c];
+        out->work[c] = p->work[c];
+        if (reset) { p->ms[c] = 0; p->count[c] = 0; p->work[c] = 0; }
+    }
+    return GLASSO_OK;
+}
+
+glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_out, double *W_out,
+                           glasso_info *info) {
+    if (!ctx) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    return solve_in(ctx->w, ctx->stream, ctx->budget, p, A_out, W_out, info, ctx->last_error,
+                    (Prof *)ctx->prof, false, p ? p->location : GLASSO_HOST);
+}
+
+glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int count,
+                                 int warm_from_prev, double **A_out, glasso_info *infos) {
+    if (!ctx || !p || count < 0 || (count > 0 && !A_out)) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status first = GLASSO_OK;
+    if (!warm_from_prev) {
+        // independent problems: run them concurrently through the serving slots
+        std::vector<uint64_t> tickets(count);
+        for (int k = 0; k < count; ++k) {
+            glasso_status s = glasso_submit(ctx, &p[k], A_out[k], &tickets[k]);
+            if (s != GLASSO_OK) {
+                if (infos) { memset(&infos[k], 0, sizeof(glasso_info)); infos[k].status = s; }
+                if (first == GLASSO_OK) first = s;
+                tickets[k] = 0;
+            }
+        }
+        for (int k = 0; k < count; ++k) {
+            if (!tickets[k]) continue;
+            glasso_info inf;
+            glasso_status s;
+            while ((s = glasso_poll(ctx, tickets[k], 1000000, &inf)) == GLASSO_EAGAIN) {}
+            if (infos) infos[k] = inf;
+            if (s != GLASSO_OK && first == GLASSO_OK) first = s;
+        }
+        return first;
+    }
+    for (int k = 0; k < count; ++k) {
+        const bool chain = k > 0 && p[k].A0 == nullptr && p[k].n == p[k - 1].n &&
+                           p[k].data == p[k - 1].data && p[k].input == p[k - 1].input;
+        glasso_info inf;
+        glasso_status s;
+        if (chain) {
+            // continue from the previous solution kept in the workspace (w.A)
+            s = solve_in(ctx->w, ctx->stream, ctx->budget, &p[k], A_out[k], nullptr, &inf,
+                         ctx->last_error, (Prof *)ctx->prof, true, p[k].location);
+        } else {
+            s = solve_in(ctx->w, ctx->stream, ctx->budget, &p[k], A_out[k], nullptr, &inf,
+                         ctx->last_error, (Prof *)ctx->prof, false, p[k].location);
+        }
+        if (infos) infos[k] = inf;
+        if (s != GLASSO_OK && first == GLASSO_OK) first = s;
+    }
+    return first;
+}
+
+glasso_status glasso_submit(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
+                            uint64_t *ticket) {
+    if (!ctx || !ticket || !A_out) return GLASSO_EINVAL;
+    glasso_status s = validate(p);
+    if (s != GLASSO_OK) return s;
+    const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
+    const int xb = p->dtype == GLASSO_F32 ? 4 : 8;
+    const size_t fp = footprint(p->n, m, xb);
+    if (ctx->budget && fp > ctx->budget) return GLASSO_ENOMEM;
+    Request *r = new Request();
+    r->p = *p;
+    const size_t bytes = p->input == GLASSO_INPUT_S ? (size_t)(p->n * p->n) * 8 : (size_t)(m * p->n) * xb;
+    r->data.resize(bytes);
+    const cudaMemcpyKind kind = p->location == GLASSO_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    cudaSetDevice(ctx->device);
+    if (cudaMemcpy(r->data.data(), p->data, bytes, kind) != cudaSuccess) {
+        delete r;
+        return GLASSO_ECUDA;
+    }
+    if (p->A0) {
+        r->a0.resize((size_t)(p->n * p->n));
+        if (cudaMemcpy(r->a0.data(), p->A0, r->a0.size() * 8, kind) != cudaSuccess) {
+            delete r;
+            return GLASSO_ECUDA;
+        }
+        r->p.A0 = r->a0.data();
+    }
+    // the staged copies live on the host; outputs go where the caller said
+    r->p.data = r->data.data();
+    r->A_out = A_out;
+    r->out_location = p->location;
+    r->fp = fp;
+    r->p.location = GLASSO_HOST;  // inputs now live in the request's host copy
+    Serve *sv = serve_get(ctx);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->ticket = sv->next++;
+        sv->all[r->ticket] = r;
+        sv->queue.push_back(r);
+    }
+    sv->cv_work.notify_one();
+    *ticket = r->ticket;
+    return GLASSO_OK;
+}
+
+glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us, glasso_info *info) {
+    if (!ctx || !ctx->serve) return GLASSO_EINVAL;
+    Serve *sv = (Serve *)ctx->serve;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return GLASSO_EINVAL;
+    Request *r = it->second;
+    if (!r->done && timeout_us > 0)
+        sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; });
+    if (!r->done) return GLASSO_EAGAIN;
+    if (info) *info = r->info;
+    glasso_status s = r->status;
+    sv->all.erase(it);
+    delete r;
+    return s;
+}
+
+// ---- step-level entry points ----------------------------------------------
+#define CTX_CK(call)                                                          \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return fail_cuda(ctx->last_error, e_, #call); \
+    } while (0)
+
+static glasso_status sync_ctx(glasso_ctx *ctx) {
+    CTX_CK(cudaMemcpyAsync(ctx->w.sc_host, ctx->w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    return GLASSO_OK;
+}
+
+glasso_status glasso_form_S(glasso_ctx *ctx, const void *X, int dtype, int64_t m, int64_t n,
+                            int center, double *S) {
+    if (!ctx || !X || !S || m < 1 || n < 1 || (dtype != GLASSO_F64 && dtype != GLASSO_F32))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, 1, ctx->stream, ctx->last_error);
+    if (s == GLASSO_OK) s = work_ensure_x(ctx->w, m, n, 0, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    CTX_CK(form_S(X, dtype, m, n, center, S, ctx->w.Xin, ctx->stream));
+    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    return GLASSO_OK;
+}
+
+glasso_status glasso_potrf(glasso_ctx *ctx, double *A, int64_t n, int *info, double *logdet) {
+    if (!ctx || !A || n < 1) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, 1, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    Prof *prof = (Prof *)ctx->prof;
+    Solver sv{ctx->w, ctx->stream, ctx->last_error, prof};
+    cudaEvent_t eb;
+    sv.mark_begin(0, eb);
+    CTX_CK(potrf(A, n, ctx->w.sc, ctx->stream));
+    sv.mark_end(0, eb, (double)n * n * n / 3.0);
+    s = sync_ctx(ctx);
+    if (prof) prof_collect(prof);
+    if (s != GLASSO_OK) return s;
+    if (info) *info = ctx->w.sc_host->info;
+    if (logdet) *logdet = ctx->w.sc_host->logdet;
+    return GLASSO_OK;
+}
+
+glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double *W) {
+    if (!ctx || !L || !W || n < 1) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    Prof *prof = (Prof *)ctx->prof;
+    Solver sv{ctx->w, ctx->stream, ctx->last_error, prof};
+    cudaEvent_t eb;
+    sv.mark_begin(1, eb);
+    CTX_CK(inverse(L, n, W, ctx->w.T, ctx->w.U, ctx->stream));
+    sv.mark_end(1, eb, 2.0 * (double)n * n * n / 3.0);
+    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    if (prof) prof_collect(prof);
+    return GLASSO_OK;
+}
+
+glasso_status glasso_free_set(glasso_ctx *ctx, const double *S, const double *W, const double *A,
+                              int64_t n, double lambda, const int32_t *cand_i,
+                              const int32_t *cand_j, int64_t ncand, int32_t *out_i,
+                              int32_t *out_j, double *absg, int64_t *count, double *rel_kkt,
+                              double *max_kkt) {
+    if (!ctx || !S || !W || !A || n < 1 || !finite_pos(lambda) || !out_i || !out_j || !count)
+        return GLASSO_EINVAL;
+    if (cand_i && (!cand_j || ncand < 0)) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    if (cand_i && ncand > ctx->w.cap_pairs) return GLASSO_EINVAL;
+    Work &w = ctx->w;
+    if (!cand_i) {
+        CTX_CK(scan_full(S, W, A, n, lambda, 0, w, out_i, out_j, absg, w.sc, ctx->stream));
+    } else {
+        CTX_CK(scan_cand(S, W, A, n, lambda, cand_i, cand_j, nullptr, 0, ncand, w, out_i, out_j,
+                         absg, w.sc, ctx->stream));
+    }
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    *count = w.sc_host->count;
+    if (!cand_i) {
+        if (rel_kkt) *rel_kkt = w.sc_host->kkt_sum / w.sc_host->l1;
+        if (max_kkt) *max_kkt = w.sc_host->kkt_max;
+    }
+    return GLASSO_OK;
+}
+
+glasso_status glasso_hierarchy(glasso_ctx *ctx, const double *absg, const uint8_t *insupp,
+                               int64_t nf, uint8_t *tag, int *levels) {
+    if (!ctx || nf < 0 || (nf > 0 && (!absg || !insupp || !tag)) || !levels) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, 1, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    CTX_CK(hierarchy(absg, insupp, nf, tag, ctx->w.sc, ctx->stream));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    *levels = ctx->w.sc_host->levels;
+    return GLASSO_OK;
+}
+
+glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W, const double *A,
+                               int64_t n, double lambda, const int32_t *pi, const int32_t *pj,
+                               int64_t np, int nsweeps, double *D, double *U) {
+    if (!ctx || !S || !W || !A || n < 1 || !finite_pos(lambda) || np < 0 || nsweeps < 0 ||
+        (np > 0 && (!pi || !pj || !D || !U)))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    if (np > ctx->w.cap_pairs) return GLASSO_EINVAL;
+    Work &w = ctx->w;
+    Prof *prof = (Prof *)ctx->prof;
+    Solver sv{w, ctx->stream, ctx->last_error, prof};
+    CTX_CK(pair_prep(S, W, A, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, ctx->stream));
+    cudaEvent_t eb;
+    sv.mark_begin(3, eb);
+    CTX_CK(cd_sweeps(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, D, U, w, ctx->stream));
+    sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * (double)n * 8.0);
+    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    if (prof) prof_collect(prof);
+    return GLASSO_OK;
+}
+
+glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double *W, double *A,
+                                 int64_t n, double lambda, const int32_t *pi, const int32_t *pj,
+                                 int64_t np, const double *D, double F_A, double sigma,
+                                 int max_trials, double *F_new, double *alpha, int *trials) {
+    if (!ctx || !S || !W || !A || n < 1 || !finite_pos(lambda) || np < 0 || max_trials < 1 ||
+        (np > 0 && (!pi || !pj || !D)))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    if (np > ctx->w.cap_pairs) return GLASSO_EINVAL;
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    CTX_CK(pair_prep(S, W, A, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+    CTX_CK(ls_delta(w.p_g, w.p_a, w.p_s, D, pi, pj, np, lambda, w, w.sc, st));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    const double delta = w.sc_host->delta, trSD = w.sc_host->trSD;
+    // tr(SA) and ||A||_1 of the current iterate from F_A's definition are not
+    // needed: F(A + alpha Delta) - F(A) only involves the pairs.
+    double a = 1.0;
+    const double epsF = 1e-12 * std::max(fabs(F_A), (double)n);
+    double ldA = 0.0;
+    // log det A itself (to express F(A + alpha Delta) relative to F_A)
+    CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CTX_CK(potrf(w.T, n, w.sc, st));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    if (w.sc_host->info != 0) return GLASSO_EINVAL;
+    ldA = w.sc_host->logdet;
+    for (int t = 0; t < max_trials; ++t) {
+        CTX_CK(ls_build_trial(A, w.T, n, pi, pj, w.p_a, D, np, a, st));
+        CTX_CK(potrf(w.T, n, w.sc, st));
+        CTX_CK(ls_dl1(w.p_a, D, pi, pj, np, a, w, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (w.sc_host->info == 0) {
+            const double FT = F_A - (w.sc_host->logdet - ldA) + a * trSD + lambda * w.sc_host->dl1;
+            if (FT <= F_A + sigma * a * delta + epsF) {
+                CTX_CK(ls_apply(A, n, pi, pj, w.p_a, D, np, a, st));
+                CTX_CK(cudaStreamSynchronize(st));
+                if (F_new) *F_new = FT;
+                if (alpha) *alpha = a;
+                if (trials) *trials = t + 1;
+                return GLASSO_OK;
+            }
+        }
+        a *= 0.5;
+    }
+    if (trials) *trials = max_trials;
+    if (alpha) *alpha = 0.0;
+    return GLASSO_ELINESEARCH;
+}
+
+glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A, int64_t n,
+                               double lambda, double *F, int *info) {
+    if (!ctx || !S || !A || n < 1 || !finite_pos(lambda) || !F || !info) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CTX_CK(potrf(w.T, n, w.sc, st));
+    // tr(SA) and ||A||_1 come with a scan whose W is S itself (G = 0): only the
+    // trace and l1 sums are read from it.
+    CTX_CK(scan_full(S, S, A, n, lambda, 0, w, w.pi, w.pj, nullptr, w.sc, st));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    *info = w.sc_host->info;
+    *F = -w.sc_host->logdet + w.sc_host->trSA + lambda * w.sc_host->l1;
+    return GLASSO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,387 @@
+// Dense FP64 kernels of one relaxation: S = X^T X / m (eq. cov_estimate), the
+// blocked right-looking Cholesky with PD test and log-det (Section 6.1.2 uses
+// both in the line search), and W = A^{-1} = L^{-T} L^{-1} (eq. gradHes).
+//
+// GB300 note: FP64 runs at roughly 2 FMA/clock/SM on this part (about
+// 1.1 TFLOP/s for the whole GPU), so every kernel here is bound by FP64
+// issue, not by memory.  The design therefore maximises the number of
+// independent 32 x 32 output tiles in flight (many small CTAs, several per
+// SM) and keeps the serial panel work in shared memory.
+#include <math.h>
+
+#include "glasso_internal.h"
+
+namespace glx {
+namespace {
+
+constexpr int TPB = 256;  // threads of a tile CTA: 16 x 16, 2 x 2 outputs each
+
+// acc += sum_{k in [k0, k1)} opA(i0 + i, k) * opB(k, j0 + j) for a 32 x 32 tile.
+// opA(i, k) = TA ? A[k * lda + i] : A[i * lda + k]   (rows i < mrows)
+// opB(k, j) = TB ? B[j * ldb + k] : B[k * ldb + j]   (cols j < ncols)
+// Thread (ty, tx) owns rows {ty, ty + 16} and columns {tx, tx + 16}.
+template <typename TIN, bool TA, bool TB>
+__device__ __forceinline__ void tile_acc(double (&acc)[2][2], const TIN *__restrict__ A,
+                                         int64_t lda, const TIN *__restrict__ B, int64_t ldb,
+                                         int64_t i0, int64_t j0, int64_t k0, int64_t k1,
+                                         int64_t mrows, int64_t ncols, double (*As)[NB + 1],
+                                         double (*Bs)[NB + 1]) {
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    for (int64_t kc = k0; kc < k1; kc += NB) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = tid + TPB * r;
+            int i, k;
+            if (TA) { i = idx & 31; k = idx >> 5; } else { k = idx & 31; i = idx >> 5; }
+            int64_t gi = i0 + i, gk = kc + k;
+            double v = 0.0;
+            if (gi < mrows && gk < k1) v = (double)(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
+            As[k][i] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = tid + TPB * r;
+            int j, k;
+            if (TB) { k = idx & 31; j = idx >> 5; } else { j = idx & 31; k = idx >> 5; }
+            int64_t gj = j0 + j, gk = kc + k;
+            double v = 0.0;
+            if (gj < ncols && gk < k1) v = (double)(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
+            Bs[k][j] = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < NB; ++k) {
+            double a0 = As[k][ty], a1 = As[k][ty + 16];
+            double b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+}
+
+// Linear index over the lower-triangular tile grid (J <= I) -> (I, J).
+__device__ __forceinline__ void tri_index(int64_t t, int64_t &I, int64_t &J) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > t) --i;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    I = i;
+    J = t - i * (i + 1) / 2;
+}
+
+// ---------------------------------------------------------------- a1: S
+template <typename TIN>
+__global__ void k_stage_x(const TIN *__restrict__ X, int64_t m, int64_t n,
+                          const double *__restrict__ mu, double *__restrict__ Xd) {
+    int64_t total = m * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double v = (double)X[t];
+        if (mu) v -= mu[t % n];
+        Xd[t] = v;
+    }
+}
+
+template <typename TIN>
+__global__ void k_colmean(const TIN *__restrict__ X, int64_t m, int64_t n, double *__restrict__ mu) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t k = 0; k < m; ++k) s += (double)X[k * n + i];
+    mu[i] = s / (double)m;
+}
+
+// S_IJ = sum_k X[k, I]^T X[k, J] / m on lower tiles, mirrored.
+__global__ void __launch_bounds__(TPB) k_syrk_S(const double *__restrict__ X, int64_t m, int64_t n,
+                                                double *__restrict__ S) {
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    int64_t I, J;
+    tri_index(blockIdx.x, I, J);
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<double, true, false>(acc, X, n, X, n, I * NB, J * NB, 0, m, n, n, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < n && j < n) {
+                double v = acc[a][b] / (double)m;
+                S[i * n + j] = v;
+                S[j * n + i] = v;
+            }
+        }
+}
+
+// ---------------------------------------------------------------- a2: Cholesky
+// Step kb of the blocked right-looking factorisation.  Every CTA factors the
+// (already updated) diagonal block kb in shared memory; CTA 0 stores it and
+// reports a non-positive pivot, CTA r > 0 solves block row kb + r of the
+// panel, L_ik = A_ik L_kk^{-T}.  Fusing the diagonal factorisation into the
+// panel launch costs a redundant 32^3/3 flops per CTA and saves a launch.
+__global__ void __launch_bounds__(TPB) k_potrf_panel(double *__restrict__ A, int64_t n, int kb,
+                                                     DevScalars *sc) {
+    if (sc->info != 0) return;
+    __shared__ double Ld[NB][NB + 1];
+    __shared__ double P[NB][NB + 1];
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    const int64_t k0 = (int64_t)kb * NB;
+    const int kw = (int)lmin(NB, n - k0);
+    for (int idx = tid; idx < NB * NB; idx += TPB) {
+        int r = idx / NB, c = idx % NB;
+        Ld[r][c] = (r < kw && c <= r) ? A[(k0 + r) * n + k0 + c] : 0.0;
+    }
+    if (tid == 0) fail = 0;
+    __syncthreads();
+    for (int j = 0; j < kw; ++j) {
+        if (tid == 0) {
+            double d = Ld[j][j];
+            if (!(d > 0.0)) fail = j + 1;
+            else Ld[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail) break;
+        for (int r = j + 1 + tid; r < kw; r += TPB) Ld[r][j] /= Ld[j][j];
+        __syncthreads();
+        int rem = kw - j - 1;
+        for (int idx = tid; idx < rem * rem; idx += TPB) {
+            int r = j + 1 + idx / rem, c = j + 1 + idx % rem;
+            if (c <= r) Ld[r][c] -= Ld[r][j] * Ld[c][j];
+        }
+        __syncthreads();
+    }
+    if (fail) {
+        if (blockIdx.x == 0 && tid == 0) sc->info = (int)(k0 + fail);
+        return;
+    }
+    if (blockIdx.x == 0) {
+        for (int idx = tid; idx < kw * kw; idx += TPB) {
+            int r = idx / kw, c = idx % kw;
+            if (c <= r) A[(k0 + r) * n + k0 + c] = Ld[r][c];
+        }
+        return;
+    }
+    const int64_t r0 = k0 + (int64_t)blockIdx.x * NB;
+    const int rh = (int)lmin(NB, n - r0);
+    for (int idx = tid; idx < NB * NB; idx += TPB) {
+        int r = idx / NB, c = idx % NB;
+        P[r][c] = (r < rh && c < kw) ? A[(r0 + r) * n + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < kw; ++c) {
+        if (tid < rh) P[tid][c] /= Ld[c][c];
+        __syncthreads();
+        int rem = kw - c - 1;
+        for (int idx = tid; idx < rh * rem; idx += TPB) {
+            int r = idx / rem, cc = c + 1 + idx % rem;
+            P[r][cc] -= P[r][c] * Ld[cc][c];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < rh * kw; idx += TPB) {
+        int r = idx / kw, c = idx % kw;
+        A[(r0 + r) * n + k0 + c] = P[r][c];
+    }
+}
+
+// Trailing update of step kb: A_IJ -= L_I,kb L_J,kb^T on lower tiles I >= J > kb.
+__global__ void __launch_bounds__(TPB) k_potrf_trail(double *__restrict__ A, int64_t n, int kb,
+                                                     DevScalars *sc) {
+    if (sc->info != 0) return;
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    int64_t I, J;
+    tri_index(blockIdx.x, I, J);
+    I += kb + 1;
+    J += kb + 1;
+    const int64_t k0 = (int64_t)kb * NB, k1 = lmin(k0 + NB, n);
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<double, false, true>(acc, A, n, A, n, I * NB, J * NB, k0, k1, n, n, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < n && j < n && j <= i) A[i * n + j] -= acc[a][b];
+        }
+}
+
+// log det A = 2 sum_i log L_ii, deterministic single-CTA reduction.
+__global__ void k_logdet(const double *__restrict__ L, int64_t n, DevScalars *sc) {
+    __shared__ double red[TPB];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += TPB) s += log(L[i * n + i]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = TPB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sc->logdet = (sc->info == 0) ? 2.0 * red[0] : 0.0;
+}
+
+// ---------------------------------------------------------------- a3: inverse
+// Invert every 32 x 32 diagonal block of L: X_bb = L_bb^{-1} (forward
+// substitution, one thread per column).
+__global__ void k_trtri_diag(const double *__restrict__ L, int64_t n, double *__restrict__ X) {
+    __shared__ double Ls[NB][NB + 1];
+    __shared__ double Xs[NB][NB + 1];
+    const int64_t b0 = (int64_t)blockIdx.x * NB;
+    const int bw = (int)lmin(NB, n - b0);
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+        int r = idx / NB, c = idx % NB;
+        Ls[r][c] = (r < bw && c <= r) ? L[(b0 + r) * n + b0 + c] : 0.0;
+        Xs[r][c] = 0.0;
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c < bw) {
+        for (int i = c; i < bw; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int t = c; t < i; ++t) s -= Ls[i][t] * Xs[t][c];
+            Xs[i][c] = s / Ls[i][i];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < bw * bw; idx += blockDim.x) {
+        int r = idx / bw, cc = idx % bw;
+        if (cc <= r) X[(b0 + r) * n + b0 + cc] = Xs[r][cc];
+    }
+}
+
+// Recursive doubling of the inverted diagonal blocks: for blocks of size s,
+// pair p covers rows [r0, r0 + s + h) with r0 = 2 s p and
+//   X21 = -X22 (L21 X11),  computed as  Tw = L21 X11, then X21 = -X22 Tw.
+// Step 1: Tw_p (h x s, row stride s) = L21 X11; X11 is lower, so column
+// block J only needs k >= J*32.
+__global__ void __launch_bounds__(TPB) k_trtri_step1(const double *__restrict__ L,
+                                                     const double *__restrict__ X, int64_t n,
+                                                     int64_t s, int tiles_i, int tiles_j,
+                                                     double *__restrict__ Tw) {
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    const int per = tiles_i * tiles_j;
+    const int64_t p = blockIdx.x / per;
+    const int tt = blockIdx.x % per;
+    const int64_t I = tt / tiles_j, J = tt % tiles_j;
+    const int64_t r0 = 2 * s * p;
+    const int64_t h = lmin(s, n - r0 - s);
+    if (I * NB >= h) return;
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<double, false, false>(acc, L + (r0 + s) * n + r0, n, X + r0 * n + r0, n, I * NB,
+                                   J * NB, J * NB, s, h, s, As, Bs);
+    double *T = Tw + p * s * s;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < h && j < s) T[i * s + j] = acc[a][b];
+        }
+}
+
+// Step 2: X21 = -X22 Tw_p; X22 is lower, so row block I only needs k < (I+1)*32.
+__global__ void __launch_bounds__(TPB) k_trtri_step2(double *__restrict__ X, int64_t n, int64_t s,
+                                                     int tiles_i, int tiles_j,
+                                                     const double *__restrict__ Tw) {
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    const int per = tiles_i * tiles_j;
+    const int64_t p = blockIdx.x / per;
+    const int tt = blockIdx.x % per;
+    const int64_t I = tt / tiles_j, J = tt % tiles_j;
+    const int64_t r0 = 2 * s * p;
+    const int64_t h = lmin(s, n - r0 - s);
+    if (I * NB >= h) return;
+    const double *T = Tw + p * s * s;
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<double, false, false>(acc, X + (r0 + s) * n + (r0 + s), n, T, s, I * NB, J * NB, 0,
+                                   lmin((I + 1) * NB, h), h, s, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < h && j < s) X[(r0 + s + i) * n + r0 + j] = -acc[a][b];
+        }
+}
+
+// W = X^T X with X = L^{-1} lower: W_IJ = sum_{k >= I*32} X[k, I]^T X[k, J]
+// on lower tiles I >= J, mirrored to the upper triangle.
+__global__ void __launch_bounds__(TPB) k_lauum(const double *__restrict__ X, int64_t n,
+                                               double *__restrict__ W) {
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    int64_t I, J;
+    tri_index(blockIdx.x, I, J);
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<double, true, false>(acc, X, n, X, n, I * NB, J * NB, I * NB, n, n, n, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < n && j < n) {
+                W[i * n + j] = acc[a][b];
+                W[j * n + i] = acc[a][b];
+            }
+        }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, double *S,
+                   double *Xstage, cudaStream_t st) {
+    if (m < 1 || n < 1) return cudaErrorInvalidValue;
+    // Xstage holds m*n + n doubles: the centred FP64 copy of X and the mean.
+    double *mu = center ? Xstage + m * n : nullptr;
+    int g = (int)lmin((m * n + 255) / 256, 152 * 16);
+    if (dtype == GLASSO_F64) {
+        const double *x = (const double *)X;
+        if (center) k_colmean<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+        k_stage_x<double><<<g, 256, 0, st>>>(x, m, n, mu, Xstage);
+    } else {
+        const float *x = (const float *)X;
+        if (center) k_colmean<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+        k_stage_x<float><<<g, 256, 0, st>>>(x, m, n, mu, Xstage);
+    }
+    int64_t nb = (n + NB - 1) / NB;
+    k_syrk_S<<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(Xstage, m, n, S);
+    return cudaGetLastError();
+}
+
+cudaError_t potrf(double *A, int64_t n, DevScalars *sc, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = (n + NB - 1) / NB;
+    for (int64_t kb = 0; kb < nb; ++kb) {
+        k_potrf_panel<<<(unsigned)(nb - kb), TPB, 0, st>>>(A, n, (int)kb, sc);
+        const int64_t m = nb - kb - 1;
+        if (m > 0) k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, sc);
+    }
+    k_logdet<<<1, TPB, 0, st>>>(A, n, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(X, 0, (size_t)(n * n) * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = (n + NB - 1) / NB;
+    k_trtri_diag<<<(unsigned)nb, NB, 0, st>>>(L, n, X);
+    for (int64_t s = NB; s < n; s *= 2) {
+        const int64_t npairs = (n - s + 2 * s - 1) / (2 * s);  // r0 = 2sp with r0 + s < n
+        const int tiles = (int)(s / NB);
+        const unsigned grid = (unsigned)(npairs * tiles * tiles);
+        k_trtri_step1<<<grid, TPB, 0, st>>>(L, X, n, s, tiles, tiles, Tw);
+        k_trtri_step2<<<grid, TPB, 0, st>>>(X, n, s, tiles, tiles, Tw);
+    }
+    k_lauum<<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(X, n, W);
+    return cudaGetLastError();
+}
+
+}  // namespace glx

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of the solver.
+// Everything here is private to the shared library; the public surface is
+// include/glasso.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "glasso.h"
+
+namespace glx {
+
+__host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// Column / row block of the dense FP64 kernels (Cholesky panel width, tile edge).
+constexpr int NB = 32;
+// Coordinates resolved together by one blocked CD step (see cd.cu).
+constexpr int CD_B = 128;
+// Maximum number of k-chunks of the CD dot products.
+constexpr int CD_MAX_CHUNKS = 256;
+
+// Device-side scalar results of the reduction kernels (one struct per context).
+struct DevScalars {
+    // full free-set scan (level 0)
+    long long count;      // free pairs written
+    double kkt_sum;       // sum_ij |min-norm subgradient|
+    double kkt_max;       // max_ij |min-norm subgradient|
+    double trSA;          // sum_ij S_ij A_ij
+    double l1;            // sum_ij |A_ij|
+    long long nnz;        // #{A_ij != 0}
+    // Cholesky
+    int info;             // 0 or first failing pivot + 1
+    int pad0;
+    double logdet;
+    // line search
+    double delta;         // tr(G Delta) + lambda (||A + Delta||_1 - ||A||_1)
+    double trSD;          // tr(S Delta)
+    double dl1;           // ||A + alpha Delta||_1 - ||A||_1 at the trial alpha
+    int moved;            // any Delta_p != 0
+    int levels;           // hierarchy levels L
+    long long nsupp;
+    int err;              // device-side error flag (NaN input, bad diagonal)
+    int bad_sym;          // input symmetry check failed
+};
+
+// Per-context device workspace, sized for n <= cap_n.
+struct Work {
+    int64_t cap_n = 0;
+    int64_t cap_pairs = 0;
+    double *S = nullptr, *A = nullptr, *L = nullptr, *T = nullptr, *W = nullptr, *U = nullptr;
+    double *Xin = nullptr;       // centred FP64 copy of X (m x n) and its mean (n)
+    int64_t cap_x = 0;
+    char *Xraw = nullptr;        // host samples copied to the device as given
+    int64_t cap_xraw = 0;
+    // pair lists
+    int32_t *fi = nullptr, *fj = nullptr;  // previous fine free set F_k
+    double *fabsg = nullptr;               // |G| on F_k
+    uint8_t *ftag = nullptr, *fsupp = nullptr;
+    int32_t *pi = nullptr, *pj = nullptr;  // current relaxation's free set
+    double *pabsg = nullptr;
+    double *D = nullptr;                   // Delta on pairs
+    double *p_inva = nullptr, *p_g = nullptr, *p_a = nullptr, *p_s = nullptr;
+    // scan / compaction scratch
+    uint32_t *mask = nullptr;              // n x ceil(n/32) bit masks
+    long long *rowcnt = nullptr;           // n + 1
+    double *rowred = nullptr;              // n x 6 partial sums
+    uint8_t *flags = nullptr;              // cap_pairs
+    long long *blkcnt = nullptr;           // blocks of the compaction
+    int64_t cap_blk = 0;
+    double *redbuf = nullptr;              // generic reduction partials
+    int64_t cap_red = 0;
+    // CD scratch
+    double *cd_part = nullptr;             // CD_MAX_CHUNKS x CD_B partial dots
+    double *cd_mu = nullptr;               // CD_B
+    int32_t *cd_seg = nullptr;             // segment table of the row updates
+    double *cd_emu = nullptr;              // 2 CD_B entry coefficients
+    int32_t *cd_esrc = nullptr;            // 2 CD_B entry source rows
+    DevScalars *sc = nullptr;              // device scalars
+    DevScalars *sc_host = nullptr;         // pinned mirror
+};
+
+}  // namespace glx
+
+struct glasso_ctx {
+    int device = 0;
+    int precision = GLASSO_FP64;
+    size_t budget = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    glx::Work w;
+    std::string last_error;
+    void *serve = nullptr;  // serving state (api.cu)
+    void *prof = nullptr;   // kernel-class timing (api.cu)
+};
+
+namespace glx {
+
+// ---- launchers (dense.cu) ----
+cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, double *S,
+                   double *mu_scratch, cudaStream_t st);
+// In-place blocked Cholesky of the lower triangle; writes sc->info and sc->logdet.
+cudaError_t potrf(double *A, int64_t n, DevScalars *sc, cudaStream_t st);
+// W = L^{-T} L^{-1}; X (n x n) and Tw (n x n) are scratch.
+cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st);
+
+// ---- launchers (scan.cu) ----
+// Full level-0 scan: free set (pi, pj, absg) and the sums of DevScalars.
+// mode 0: condition A != 0 or |S - W| > lambda; mode 1: A != 0 or |S| > lambda
+// (the initial free set of Section 7's footnote).
+cudaError_t scan_full(const double *S, const double *W, const double *A, int64_t n, double lam,
+                      int mode, Work &w, int32_t *oi, int32_t *oj, double *oabsg, DevScalars *sc,
+                      cudaStream_t st);
+// Candidate scan: keep candidates p with (tag == NULL or tag[p] >= level) that
+// are free; writes count to sc->count.
+cudaError_t scan_cand(const double *S, const double *W, const double *A, int64_t n, double lam,
+                      const int32_t *ci, const int32_t *cj, const uint8_t *tag, int level,
+                      int64_t ncand, Work &w, int32_t *oi, int32_t *oj, double *oabsg,
+                      DevScalars *sc, cudaStream_t st);
+cudaError_t support_flags(const double *A, int64_t n, const int32_t *fi, const int32_t *fj,
+                          int64_t nf, uint8_t *flag, cudaStream_t st);
+cudaError_t init_diag(const double *S, int64_t n, double lam, double *A, DevScalars *sc,
+                      cudaStream_t st);
+// per-pair data for the CD sweep
+cudaError_t pair_prep(const double *S, const double *W, const double *A, int64_t n, double lam,
+                      const int32_t *pi, const int32_t *pj, int64_t np, double *inva, double *g,
+                      double *aval, double *sval, cudaStream_t st);
+// line search pieces
+cudaError_t ls_delta(const double *g, const double *aval, const double *sval, const double *D,
+                     const int32_t *pi, const int32_t *pj, int64_t np, double lam, Work &w,
+                     DevScalars *sc, cudaStream_t st);
+cudaError_t ls_build_trial(const double *A, double *T, int64_t n, const int32_t *pi,
+                           const int32_t *pj, const double *aval, const double *D, int64_t np,
+                           double alpha, cudaStream_t st);
+cudaError_t ls_dl1(const double *aval, const double *D, const int32_t *pi, const int32_t *pj,
+                   int64_t np, double alpha, Work &w, DevScalars *sc, cudaStream_t st);
+cudaError_t ls_apply(double *A, int64_t n, const int32_t *pi, const int32_t *pj,
+                     const double *aval, const double *D, int64_t np, double alpha,
+                     cudaStream_t st);
+
+// ---- launchers (hier.cu) ----
+cudaError_t hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uint8_t *tag,
+                      DevScalars *sc, cudaStream_t st);
+
+// ---- launchers (cd.cu) ----
+cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
+                      const int32_t *pj, int64_t np, const double *inva, const double *g,
+                      const double *aval, int nsweeps, double *D, double *U, Work &w,
+                      cudaStream_t st);
+
+}  // namespace glx

@@ -1,0 +1,176 @@
+"""GPU parity of the whole multilevel proximal-Newton solve against the FP64
+oracle, plus the batch and serving entry points and the error paths.
+
+Parity bar (FP64 path): relative objective within 1e-9, max entry error
+within 1e-7, identical support except pairs whose |(S - W)_ij| lies within
+1e-7 of lambda.  Both sides run to a tight tolerance so that the bar
+measures the solver, not the stopping point.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00315_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso
+
+    build.build()
+    torch.cuda.init()
+    c = glasso.Context(0)
+    yield c
+    c.close()
+
+
+def _compare(A, A_ref, S, lam, F, F_ref):
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref), (F, F_ref)
+    assert np.abs(A - A_ref).max() <= 1e-7, np.abs(A - A_ref).max()
+    W = np.linalg.inv(A_ref)
+    border = np.abs(np.abs(S - W) - lam) <= 1e-7
+    diff = (A != 0) != (A_ref != 0)
+    assert not np.any(diff & ~border)
+
+
+CASES = [
+    ("tridiag", 100, 200, 0.2, 1001),   # the n = 100 tridiagonal workload's shape
+    ("sparse", 33, 66, 0.1, 7),
+    ("sparse", 150, 300, 0.1, 8),
+    ("tridiag", 257, 300, 0.15, 9),
+    ("sparse", 300, 150, 0.08, 10),     # m < n: rank-deficient S
+]
+
+
+@pytest.mark.parametrize("gen,n,m,lam,seed", CASES)
+def test_solve_matches_oracle(ctx, gen, n, m, lam, seed):
+    p = synth.random_problem(n, m, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-11)
+    assert info_ref["status"] == 0
+    A, W, info = ctx.solve(S, lam, tol=1e-11, want_W=True)
+    assert info["status"] == 0, info
+    _compare(A, A_ref, S, lam, info["objective"], info_ref["objective"])
+    assert np.abs(W @ A - np.eye(n)).max() < 1e-8
+
+
+def test_config1_from_samples_on_device(ctx):
+    import torch
+
+    p = synth.config_problem(1)
+    S = oracle.form_S(p.X)
+    A_ref, _, info_ref, _ = oracle.solve(S, p.lam, tol=1e-11)
+    A, _, info = ctx.solve(torch.from_numpy(p.X).cuda(), p.lam, tol=1e-11, samples=True)
+    assert isinstance(A, torch.Tensor) and A.is_cuda
+    _compare(A.cpu().numpy(), A_ref, S, p.lam, info["objective"], info_ref["objective"])
+    # the configuration's own stopping rule
+    A8, _, info8 = ctx.solve(p.X, p.lam, tol=p.tol, samples=True)
+    assert info8["status"] == 0 and info8["rel_kkt"] <= p.tol
+
+
+def test_full_size_n2000_kkt_by_oracle(ctx):
+    """The n = 2000 sparse workload at its own tolerance (1e-5): the oracle
+    cannot run the whole solve in test time, so it checks the result: its own
+    inverse of the GPU's A gives the KKT residual, which must agree with the
+    GPU's report and meet the tolerance; the duality gap must be small."""
+    p = synth.config_problem(2)
+    S = oracle.form_S(p.X)
+    A, _, info = ctx.solve(p.X, p.lam, tol=p.tol, samples=True)
+    assert info["status"] == 0
+    info_c, L = oracle.cholesky(A)
+    assert info_c == 0
+    W = oracle.inverse_from_chol(L)
+    rk, mk = oracle.rel_kkt(S, W, A, p.lam)
+    assert rk <= p.tol and abs(rk - info["rel_kkt"]) <= 1e-6 * rk + 1e-12
+    _, F = oracle.objective(S, A, p.lam)
+    assert abs(F - info["objective"]) <= 1e-10 * abs(F)
+    Wt = S + np.clip(W - S, -p.lam, p.lam)
+    dual = np.linalg.slogdet(Wt)[1] + p.n
+    assert 0 <= F - dual <= 1e-3 * abs(F) * p.tol * 100
+
+
+def test_warm_start_and_batch_path(ctx):
+    from paper_1607_00315_gb300 import glasso
+
+    p = synth.random_problem(80, 160, 0.4, 21, gen="sparse")
+    S = oracle.form_S(p.X)
+    lams = list(synth.LAMBDA_PATH)
+    probs = [glasso.Context.problem(S, lam, 1e-10) for lam in lams]
+    outs = [np.empty((80, 80)) for _ in lams]
+    s, infos = ctx.solve_batch(probs, outs, warm_from_prev=True)
+    assert s == 0
+    for lam, A, inf in zip(lams, outs, infos):
+        A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-10)
+        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"])
+    # independent problems through the concurrent path
+    probs2 = [glasso.Context.problem(S, lam, 1e-10) for lam in lams]
+    outs2 = [np.empty((80, 80)) for _ in lams]
+    s, infos2 = ctx.solve_batch(probs2, outs2, warm_from_prev=False)
+    assert s == 0
+    for A, B in zip(outs, outs2):
+        assert np.abs(A - B).max() <= 1e-7
+
+
+def test_serving_results_same_alone_and_in_the_mix(ctx):
+    from paper_1607_00315_gb300 import glasso
+
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(10):
+        n = int(rng.integers(40, 200))
+        p = synth.random_problem(n, n, float(rng.uniform(0.05, 0.3)), 500 + k, gen="sparse")
+        reqs.append((p, oracle.form_S(p.X)))
+    alone = []
+    for p, S in reqs:
+        A, _, info = ctx.solve(S, p.lam, tol=1e-9)
+        alone.append(A)
+    outs = [np.empty((p.n, p.n)) for p, _ in reqs]
+    tickets = []
+    for (p, S), o in zip(reqs, outs):
+        tickets.append(ctx.submit(glasso.Context.problem(S, p.lam, 1e-9), o))
+        time.sleep(0.001)
+    for t in tickets:
+        while True:
+            s, info = ctx.poll(t, 200000)
+            if s != glasso.EAGAIN:
+                break
+        assert s == 0, info
+    for A, B in zip(alone, outs):
+        assert np.abs(A - B).max() <= 1e-9 * max(1.0, np.abs(A).max())
+
+
+def test_error_paths(ctx):
+    from paper_1607_00315_gb300 import glasso
+
+    S = np.eye(4)
+    with pytest.raises(glasso.GlassoError) as e:
+        ctx.solve(S, 0.0)
+    assert e.value.status == glasso.EINVAL
+    bad = S.copy()
+    bad[0, 1] = 0.3
+    with pytest.raises(glasso.GlassoError) as e:
+        ctx.solve(bad, 0.1)
+    assert e.value.status == glasso.EINVAL
+    nan = S.copy()
+    nan[2, 2] = np.nan
+    with pytest.raises(glasso.GlassoError) as e:
+        ctx.solve(nan, 0.1)
+    assert e.value.status == glasso.EINVAL
+    neg = -np.eye(3)
+    with pytest.raises(glasso.GlassoError) as e:
+        ctx.solve(neg, 0.1)
+    assert e.value.status == glasso.ENOTPD
+    small = glasso.Context(0, mem_budget_bytes=1 << 20)
+    with pytest.raises(glasso.GlassoError) as e:
+        small.solve(np.eye(500), 0.1)
+    assert e.value.status == glasso.ENOMEM
+    small.close()
+    # the context stays usable after errors
+    A, _, info = ctx.solve(np.diag([1.0, 2.0]), 0.5, tol=1e-12)
+    assert np.allclose(A, np.diag([1 / 1.5, 1 / 2.5]))
