@@ -144,13 +144,16 @@ typedef struct {
     double ms[GLASSO_PROF_CLASSES];        /* summed device time */
     long long launches[GLASSO_PROF_CLASSES];
     double work[GLASSO_PROF_CLASSES];      /* algorithmic flops (0, 1, 4) or bytes (2, 3) */
+    long long kernels;                     /* kernels launched by the library (all contexts,
+                                              counted always) since the last reset */
 } glasso_profile;
 
 /* Turn event timing of the kernel classes on (on != 0) or off.  Off by
  * default; costs two events per timed call. */
 glasso_status glasso_set_profiling(glasso_ctx *ctx, int on);
 
-/* Copy the accumulated timings (and zero them when reset != 0). */
+/* Copy the accumulated timings (and zero them when reset != 0).  The kernel
+ * count is kept whether or not profiling is on. */
 glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset);
 
 /* ---- step-level entry points (device pointers) ----------------------- */

@@ -27,6 +27,10 @@
 
 using namespace glx;
 
+namespace glx {
+std::atomic<long long> g_launches{0};
+}
+
 namespace {
 
 #define CK(call)                                                   \
@@ -179,7 +183,9 @@ glasso_status check_symmetric(Work &w, const double *M, int64_t n, cudaStream_t 
     int *bad_sym = &w.sc->bad_sym;
     const int parts = 256;
     k_check_sym<<<parts, 256, 0, st>>>(M, n, bad_sym, bad_nan, w.redbuf);
+    counted(1);
     k_check_sym2<<<parts, 256, 0, st>>>(M, n, w.redbuf, parts, bad_sym);
+    counted(1);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -195,6 +201,7 @@ struct Prof {
     long long count[GLASSO_PROF_CLASSES] = {0};
     double work[GLASSO_PROF_CLASSES] = {0};
     std::vector<double> pend_work;
+    long long kernels_base = 0;
 };
 
 struct Solver {
@@ -659,14 +666,16 @@ glasso_status glasso_set_profiling(glasso_ctx *ctx, int on) {
 glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset) {
     if (!ctx || !out) return GLASSO_EINVAL;
     memset(out, 0, sizeof(*out));
+    if (!ctx->prof) ctx->prof = new Prof();
     Prof *p = (Prof *)ctx->prof;
-    if (!p) return GLASSO_OK;
     for (int c = 0; c < GLASSO_PROF_CLASSES; ++c) {
         out->ms[c] = p->ms[c];
         out->launches[c] = p->count[c];
         out->work[c] = p->work[c];
         if (reset) { p->ms[c] = 0; p->count[c] = 0; p->work[c] = 0; }
     }
+    out->kernels = g_launches.load() - p->kernels_base;
+    if (reset) p->kernels_base = g_launches.load();
     return GLASSO_OK;
 }
 

@@ -240,9 +240,12 @@ cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
             const int nb = (int)lmin(CD_B, np - b0);
             k_cd_dots<<<nchunks + NKB, CD_B, 0, st>>>(W, U, n, pi, pj, b0, nb, KC, nchunks,
                                                       w.cd_part, Kt);
+            counted(1);
             k_cd_resolve<<<1, RT, kbytes, st>>>(n, lam, pi, pj, b0, nb, nchunks, w.cd_part, Kt,
                                                 inva, g, aval, D, w.cd_seg, w.cd_esrc, w.cd_emu);
+            counted(1);
             k_cd_rows<<<NE, RT, 0, st>>>(W, U, n, w.cd_seg, w.cd_esrc, w.cd_emu);
+            counted(1);
         }
     }
     return cudaGetLastError();

@@ -343,15 +343,24 @@ cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, d
     int g = (int)lmin((m * n + 255) / 256, 152 * 16);
     if (dtype == GLASSO_F64) {
         const double *x = (const double *)X;
-        if (center) k_colmean<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+        if (center) {
+            k_colmean<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+            counted(1);
+        }
         k_stage_x<double><<<g, 256, 0, st>>>(x, m, n, mu, Xstage);
+        counted(1);
     } else {
         const float *x = (const float *)X;
-        if (center) k_colmean<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+        if (center) {
+            k_colmean<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, m, n, mu);
+            counted(1);
+        }
         k_stage_x<float><<<g, 256, 0, st>>>(x, m, n, mu, Xstage);
+        counted(1);
     }
     int64_t nb = (n + NB - 1) / NB;
     k_syrk_S<<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(Xstage, m, n, S);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -361,10 +370,15 @@ cudaError_t potrf(double *A, int64_t n, DevScalars *sc, cudaStream_t st) {
     const int64_t nb = (n + NB - 1) / NB;
     for (int64_t kb = 0; kb < nb; ++kb) {
         k_potrf_panel<<<(unsigned)(nb - kb), TPB, 0, st>>>(A, n, (int)kb, sc);
+        counted(1);
         const int64_t m = nb - kb - 1;
-        if (m > 0) k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, sc);
+        if (m > 0) {
+            k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, sc);
+            counted(1);
+        }
     }
     k_logdet<<<1, TPB, 0, st>>>(A, n, sc);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -373,14 +387,18 @@ cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw
     if (e != cudaSuccess) return e;
     const int64_t nb = (n + NB - 1) / NB;
     k_trtri_diag<<<(unsigned)nb, NB, 0, st>>>(L, n, X);
+    counted(1);
     for (int64_t s = NB; s < n; s *= 2) {
         const int64_t npairs = (n - s + 2 * s - 1) / (2 * s);  // r0 = 2sp with r0 + s < n
         const int tiles = (int)(s / NB);
         const unsigned grid = (unsigned)(npairs * tiles * tiles);
         k_trtri_step1<<<grid, TPB, 0, st>>>(L, X, n, s, tiles, tiles, Tw);
+        counted(1);
         k_trtri_step2<<<grid, TPB, 0, st>>>(X, n, s, tiles, tiles, Tw);
+        counted(1);
     }
     k_lauum<<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(X, n, W);
+    counted(1);
     return cudaGetLastError();
 }
 

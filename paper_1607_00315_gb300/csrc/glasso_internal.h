@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "glasso.h"
@@ -14,6 +15,11 @@ namespace glx {
 
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// Number of kernels this library has launched (all contexts); read through
+// glasso_profile.kernels.
+extern std::atomic<long long> g_launches;
+inline void counted(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Column / row block of the dense FP64 kernels (Cholesky panel width, tile edge).
 constexpr int NB = 32;

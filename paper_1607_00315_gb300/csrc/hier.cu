@@ -174,6 +174,7 @@ cudaError_t hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uin
                       DevScalars *sc, cudaStream_t st) {
     if (nf < 0 || nf > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_hierarchy<<<1, HT, 0, st>>>(absg, insupp, nf, tag, sc);
+    counted(1);
     return cudaGetLastError();
 }
 

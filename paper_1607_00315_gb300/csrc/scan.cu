@@ -387,8 +387,11 @@ cudaError_t scan_full(const double *S, const double *W, const double *A, int64_t
                       cudaStream_t st) {
     const unsigned g = (unsigned)((n + SCAN_WARPS - 1) / SCAN_WARPS);
     k_scan_rows<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, A, n, lam, mode, w.mask, w.rowcnt, w.rowred);
+    counted(1);
     k_scan_finish<<<1, 1024, 0, st>>>(w.rowcnt, w.rowred, n, sc, 1);
+    counted(1);
     k_scan_write<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, n, w.mask, w.rowcnt, oi, oj, oabsg);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -401,15 +404,19 @@ cudaError_t scan_cand(const double *S, const double *W, const double *A, int64_t
     if (nb > w.cap_blk) return cudaErrorInvalidValue;
     k_cand_flags<<<(unsigned)nb, 256, 0, st>>>(S, W, A, n, lam, ci, cj, tag, level, ncand,
                                                w.flags, w.blkcnt);
+    counted(1);
     k_blk_scan<<<1, 1024, 0, st>>>(w.blkcnt, nb, sc);
+    counted(1);
     k_cand_write<<<(unsigned)nb, CBLK, 0, st>>>(S, W, n, ci, cj, ncand, w.flags, w.blkcnt, oi,
                                                 oj, oabsg);
+    counted(1);
     return cudaGetLastError();
 }
 
 cudaError_t support_flags(const double *A, int64_t n, const int32_t *fi, const int32_t *fj,
                           int64_t nf, uint8_t *flag, cudaStream_t st) {
     k_support<<<grid_for(nf), 256, 0, st>>>(A, n, fi, fj, nf, flag);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -418,6 +425,7 @@ cudaError_t init_diag(const double *S, int64_t n, double lam, double *A, DevScal
     cudaError_t e = cudaMemsetAsync(A, 0, (size_t)(n * n) * sizeof(double), st);
     if (e != cudaSuccess) return e;
     k_init_diag<<<grid_for(n), 256, 0, st>>>(S, n, lam, A, sc);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -427,6 +435,7 @@ cudaError_t pair_prep(const double *S, const double *W, const double *A, int64_t
     (void)lam;
     if (np <= 0) return cudaSuccess;
     k_pair_prep<<<grid_for(np), 256, 0, st>>>(S, W, A, n, pi, pj, np, inva, g, aval, sval);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -438,7 +447,9 @@ static cudaError_t pair_sums(const double *g, const double *aval, const double *
     if (nblk < 1) nblk = 1;
     if (3 * nblk > w.cap_red) return cudaErrorInvalidValue;
     k_pair_sums<<<nblk, RED_T, 0, st>>>(g, aval, sval, D, pi, pj, np, lam, alpha, what, w.redbuf);
+    counted(1);
     k_pair_sums_final<<<1, 32, 0, st>>>(w.redbuf, nblk, what, sc);
+    counted(1);
     return cudaGetLastError();
 }
 
@@ -459,14 +470,20 @@ cudaError_t ls_build_trial(const double *A, double *T, int64_t n, const int32_t 
     cudaError_t e = cudaMemcpyAsync(T, A, (size_t)(n * n) * sizeof(double),
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    if (np > 0) k_scatter_pairs<<<grid_for(np), 256, 0, st>>>(T, n, pi, pj, aval, D, np, alpha);
+    if (np > 0) {
+        k_scatter_pairs<<<grid_for(np), 256, 0, st>>>(T, n, pi, pj, aval, D, np, alpha);
+        counted(1);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t ls_apply(double *A, int64_t n, const int32_t *pi, const int32_t *pj,
                      const double *aval, const double *D, int64_t np, double alpha,
                      cudaStream_t st) {
-    if (np > 0) k_scatter_pairs<<<grid_for(np), 256, 0, st>>>(A, n, pi, pj, aval, D, np, alpha);
+    if (np > 0) {
+        k_scatter_pairs<<<grid_for(np), 256, 0, st>>>(A, n, pi, pj, aval, D, np, alpha);
+        counted(1);
+    }
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ class Info(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * PROF_CLASSES), ("launches", C.c_longlong * PROF_CLASSES),
-                ("work", C.c_double * PROF_CLASSES)]
+                ("work", C.c_double * PROF_CLASSES), ("kernels", C.c_longlong)]
 
 
 def load():
@@ -160,8 +160,10 @@ class Context:
     def get_profile(self, reset=False):
         p = Profile()
         self._check(self.L.glasso_get_profile(self.h, C.byref(p), int(reset)), "get_profile")
-        return {PROF_NAMES[c]: dict(ms=p.ms[c], launches=p.launches[c], work=p.work[c])
-                for c in range(PROF_CLASSES)}
+        d = {PROF_NAMES[c]: dict(ms=p.ms[c], launches=p.launches[c], work=p.work[c])
+             for c in range(PROF_CLASSES)}
+        d["kernels"] = p.kernels
+        return d
 
     # ---------------------------------------------------------------- solver
     @staticmethod
