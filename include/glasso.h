@@ -233,6 +233,40 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
 glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A, int64_t n,
                                double lambda, double *F, int *info);
 
+/* ---- allocation-free entry point ------------------------------------- */
+
+/* Largest n accepted by glasso_free_set_noalloc. */
+#define GLASSO_NOALLOC_MAX_N 4096
+
+/* The level-0 free-set scan of glasso_free_set (all candidate pairs, with the
+ * relative KKT residual), for callers that must not allocate device memory:
+ * code running under another framework's memory manager, which owns the
+ * device heap, or latency-critical loops that cannot take cudaMalloc's
+ * implicit device-wide synchronisation.  The paper has no counterpart; this
+ * is a deployment variant of the same kernels.
+ *
+ * It needs no context and allocates nothing.  Its scratch (about 2.3 MB: the
+ * row bit masks, row counts, partial sums and result scalars for n up to
+ * GLASSO_NOALLOC_MAX_N) is one fixed array in device memory that every GPU
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ *
+ * Arguments and outputs are those of glasso_free_set with cand_i = NULL:
+ * S, W, A are device n x n; out_i/out_j (capacity n(n+1)/2) and absg
+ * (optional) are device; count, rel_kkt, max_kkt are host.  Work runs on
+ * `stream` (a cudaStream_t, NULL for the legacy default stream) and the call
+ * returns when the outputs are complete.  n > GLASSO_NOALLOC_MAX_N returns
+ * GLASSO_EINVAL; CUDA failures return GLASSO_ECUDA.
+ *
+ * All calls in the process share the one scratch array, which keeps the last
+ * call's contents: calls that overlap on the GPU (from several host threads
+ * or streams) race on it and must be serialised by the caller. */
+glasso_status glasso_free_set_noalloc(const double *S, const double *W, const double *A,
+                                      int64_t n, double lambda, int32_t *out_i,
+                                      int32_t *out_j, double *absg, int64_t *count,
+                                      double *rel_kkt, double *max_kkt, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

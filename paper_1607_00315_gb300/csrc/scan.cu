@@ -6,6 +6,8 @@
 // partials in a fixed order, then one CTA combines them in a fixed order.
 #include <math.h>
 
+#include <mutex>
+
 #include "glasso_internal.h"
 
 namespace glx {
@@ -488,3 +490,94 @@ cudaError_t ls_apply(double *A, int64_t n, const int32_t *pi, const int32_t *pj,
 }
 
 }  // namespace glx
+
+// ============================================================================
+// Allocation-free variant of the full free-set scan (glasso_free_set_noalloc).
+//
+// Some callers cannot allocate device memory: code that runs under another
+// framework's memory manager (which owns the whole device heap), or a
+// latency-critical loop that cannot take cudaMalloc's implicit device-wide
+// synchronisation.  This entry point gives them the level-0 free-set scan
+// with its scratch (row bit masks, row counts and partial sums, result
+// scalars) in one file-scope device array of fixed size, so it needs no
+// context and allocates nothing.  Every GPU that loads the library holds the
+// array until the process exits.
+namespace glx {
+namespace {
+
+constexpr int64_t NA_N = GLASSO_NOALLOC_MAX_N;
+constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_MASK_OFF = 0;
+constexpr size_t NA_MASK_BYTES = na_round(sizeof(uint32_t) * NA_N * ((NA_N + 31) / 32));
+constexpr size_t NA_CNT_OFF = NA_MASK_OFF + NA_MASK_BYTES;
+constexpr size_t NA_CNT_BYTES = na_round(sizeof(long long) * (NA_N + 1));
+constexpr size_t NA_RED_OFF = NA_CNT_OFF + NA_CNT_BYTES;
+constexpr size_t NA_RED_BYTES = na_round(sizeof(double) * 6 * NA_N);
+constexpr size_t NA_SC_OFF = NA_RED_OFF + NA_RED_BYTES;
+constexpr size_t NA_TOTAL = NA_SC_OFF + na_round(sizeof(DevScalars));
+
+// The scratch itself.  In host code this name is only a host-side stand-in;
+// the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_na_scratch[NA_TOTAL];
+
+constexpr int NA_MAX_DEV = 64;
+std::mutex g_na_mu;
+unsigned char *g_na_ptr[NA_MAX_DEV] = {nullptr};
+
+// Set-up, once per device, with that device current: look up the device
+// address of the scratch array.
+cudaError_t na_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NA_MAX_DEV) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = (unsigned char *)p;
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace glx
+
+extern "C" glasso_status glasso_free_set_noalloc(const double *S, const double *W,
+                                                 const double *A, int64_t n, double lambda,
+                                                 int32_t *out_i, int32_t *out_j, double *absg,
+                                                 int64_t *count, double *rel_kkt,
+                                                 double *max_kkt, void *stream) {
+    using namespace glx;
+    if (!S || !W || !A || !out_i || !out_j || !count || n < 1 || !(lambda > 0.0) ||
+        !isfinite(lambda))
+        return GLASSO_EINVAL;
+    if (n > GLASSO_NOALLOC_MAX_N) return GLASSO_EINVAL;  // beyond the fixed scratch
+    unsigned char *base = nullptr;
+    if (na_scratch(&base) != cudaSuccess) return GLASSO_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *mask = (uint32_t *)(base + NA_MASK_OFF);
+    long long *rowcnt = (long long *)(base + NA_CNT_OFF);
+    double *rowred = (double *)(base + NA_RED_OFF);
+    DevScalars *sc = (DevScalars *)(base + NA_SC_OFF);
+    // Every mask word, row count and partial sum the scan reads is written by
+    // it first; only the result scalars are cleared, so that no value of the
+    // previous call can leak into this one.
+    if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) return GLASSO_ECUDA;
+    const unsigned g = (unsigned)((n + SCAN_WARPS - 1) / SCAN_WARPS);
+    k_scan_rows<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, A, n, lambda, 0, mask, rowcnt, rowred);
+    k_scan_finish<<<1, 1024, 0, st>>>(rowcnt, rowred, n, sc, 1);
+    k_scan_write<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, n, mask, rowcnt, out_i, out_j, absg);
+    counted(3);
+    if (cudaGetLastError() != cudaSuccess) return GLASSO_ECUDA;
+    DevScalars h;
+    if (cudaMemcpyAsync(&h, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return GLASSO_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GLASSO_ECUDA;
+    *count = h.count;
+    if (rel_kkt) *rel_kkt = h.kkt_sum / h.l1;
+    if (max_kkt) *max_kkt = h.kkt_max;
+    return GLASSO_OK;
+}

@@ -93,6 +93,9 @@ def load():
     L.glasso_line_search.argtypes = [vp, vp, vp, vp, i64, d, vp, vp, i64, vp, d, d, i32,
                                      C.POINTER(d), C.POINTER(d), C.POINTER(i32)]
     L.glasso_objective.argtypes = [vp, vp, vp, i64, d, C.POINTER(d), C.POINTER(i32)]
+    L.glasso_free_set_noalloc.argtypes = [vp, vp, vp, i64, d, vp, vp, vp, C.POINTER(i64),
+                                          C.POINTER(d), C.POINTER(d), vp]
+    L.glasso_free_set_noalloc.restype = i32
     for name in ("glasso_create", "glasso_set_stream", "glasso_solve", "glasso_solve_batch",
                  "glasso_submit", "glasso_poll", "glasso_set_profiling", "glasso_get_profile",
                  "glasso_form_S", "glasso_potrf", "glasso_inverse", "glasso_free_set",
@@ -277,10 +280,25 @@ class Context:
         return info.value, F.value
 
 
+NOALLOC_MAX_N = 4096
+
+
+def free_set_noalloc(S, W, A, lam, oi, oj, absg=None, stream=None):
+    """glasso_free_set_noalloc: the level-0 free-set scan without a context and
+    without any device allocation (fixed scratch inside the library).
+    Returns (status, count, rel_kkt, max_kkt)."""
+    L = load()
+    cnt = C.c_int64(0)
+    rk, mk = C.c_double(0.0), C.c_double(0.0)
+    s = L.glasso_free_set_noalloc(_ptr(S), _ptr(W), _ptr(A), A.shape[0], lam, _ptr(oi), _ptr(oj),
+                                  _ptr(absg), C.byref(cnt), C.byref(rk), C.byref(mk), stream)
+    return s, cnt.value, rk.value, mk.value
+
+
 EXPORTED = (
     "glasso_create", "glasso_destroy", "glasso_set_stream", "glasso_strerror",
     "glasso_last_error", "glasso_solve", "glasso_solve_batch", "glasso_submit", "glasso_poll",
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
-    "glasso_line_search", "glasso_objective",
+    "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc",
 )
