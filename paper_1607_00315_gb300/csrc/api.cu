@@ -81,7 +81,7 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.mask, st); dfree(w.rowcnt, st); dfree(w.rowred, st); dfree(w.flags, st);
     dfree(w.blkcnt, st); dfree(w.redbuf, st);
     dfree(w.cd_part, st); dfree(w.cd_mu, st); dfree(w.cd_seg, st); dfree(w.cd_emu, st);
-    dfree(w.cd_esrc, st); dfree(w.sc, st);
+    dfree(w.cd_esrc, st); dfree(w.xd, st); dfree(w.sc, st);
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
     w.cap_n = w.cap_pairs = w.cap_x = w.cap_xraw = w.cap_blk = w.cap_red = 0;
@@ -98,6 +98,7 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
         CK(dalloc(w.cd_seg, 4 * CD_B + 8, st));
         CK(dalloc(w.cd_emu, 2 * CD_B, st));
         CK(dalloc(w.cd_esrc, 2 * CD_B, st));
+        CK(dalloc(w.xd, 2 * NB * NB, st));
     }
     if (n <= w.cap_n) return GLASSO_OK;
     const size_t nn = (size_t)n * (size_t)n;
@@ -272,7 +273,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     if (!have_A0) CK(init_diag(w.S, n, lam, w.A, sc, st));
     CK(cudaMemcpyAsync(w.L, w.A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     sv.mark_begin(0, eb);
-    CK(potrf(w.L, n, sc, st));
+    CK(potrf(w.L, n, w.xd, sc, st));
     sv.mark_end(0, eb, flop_chol);
     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
     if (h->err || h->info != 0) return GLASSO_ENOTPD;
@@ -352,7 +353,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                 for (int t = 0; t < max_trials; ++t) {
                     CK(ls_build_trial(w.A, w.T, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                     sv.mark_begin(4, eb);
-                    CK(potrf(w.T, n, sc, st));
+                    CK(potrf(w.T, n, w.xd, sc, st));
                     sv.mark_end(4, eb, flop_chol);
                     CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
                     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -830,7 +831,7 @@ glasso_status glasso_potrf(glasso_ctx *ctx, double *A, int64_t n, int *info, dou
     Solver sv{ctx->w, ctx->stream, ctx->last_error, prof};
     cudaEvent_t eb;
     sv.mark_begin(0, eb);
-    CTX_CK(potrf(A, n, ctx->w.sc, ctx->stream));
+    CTX_CK(potrf(A, n, ctx->w.xd, ctx->w.sc, ctx->stream));
     sv.mark_end(0, eb, (double)n * n * n / 3.0);
     s = sync_ctx(ctx);
     if (prof) prof_collect(prof);
@@ -946,14 +947,14 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
     double ldA = 0.0;
     // log det A itself (to express F(A + alpha Delta) relative to F_A)
     CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CTX_CK(potrf(w.T, n, w.sc, st));
+    CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;
     if (w.sc_host->info != 0) return GLASSO_EINVAL;
     ldA = w.sc_host->logdet;
     for (int t = 0; t < max_trials; ++t) {
         CTX_CK(ls_build_trial(A, w.T, n, pi, pj, w.p_a, D, np, a, st));
-        CTX_CK(potrf(w.T, n, w.sc, st));
+        CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
         CTX_CK(ls_dl1(w.p_a, D, pi, pj, np, a, w, w.sc, st));
         s = sync_ctx(ctx);
         if (s != GLASSO_OK) return s;
@@ -984,7 +985,7 @@ glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A
     Work &w = ctx->w;
     cudaStream_t st = ctx->stream;
     CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CTX_CK(potrf(w.T, n, w.sc, st));
+    CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
     // tr(SA) and ||A||_1 come with a scan whose W is S itself (G = 0): only the
     // trace and l1 sums are read from it.
     CTX_CK(scan_full(S, S, A, n, lambda, 0, w, w.pi, w.pj, nullptr, w.sc, st));

@@ -40,36 +40,44 @@ __device__ __forceinline__ double soft(double x, double t) {
     return ax > 0.0 ? copysign(ax, x) : 0.0;
 }
 
+// Stale dots, one CTA per coordinate t of the block: b0_t = G_t + W_{j_t,:} . U_{:,i_t},
+// reduced in a fixed order (deterministic).  CTAs nb .. nb+NKB-1 compute the
+// interaction matrix Kt[s][t] for sources s of their slice and all later t.
 __global__ void __launch_bounds__(CD_B) k_cd_dots(const double *__restrict__ W,
                                                   const double *__restrict__ U, int64_t n,
                                                   const int32_t *__restrict__ pi,
-                                                  const int32_t *__restrict__ pj, int64_t b0,
-                                                  int nb, int64_t KC, int nchunks,
-                                                  double *__restrict__ part,
+                                                  const int32_t *__restrict__ pj,
+                                                  const double *__restrict__ g, int64_t b0, int nb,
+                                                  double *__restrict__ bout,
                                                   double *__restrict__ Kt) {
     __shared__ int si[CD_B], sj[CD_B];
-    const int t = threadIdx.x;
-    if (t < nb) {
-        si[t] = pi[b0 + t];
-        sj[t] = pj[b0 + t];
-    }
-    __syncthreads();
+    __shared__ double red[CD_B];
+    const int tid = threadIdx.x;
     const int c = blockIdx.x;
-    if (c < nchunks) {
-        const int64_t k0 = c * KC, k1 = lmin(n, k0 + KC);
+    if (c < nb) {
+        const int64_t it = pi[b0 + c], jt = pj[b0 + c];
+        const double *wr = W + jt * n;
+        const double *uc = U + it;
         double acc = 0.0;
-        if (t < nb) {
-            const double *wr = W + (int64_t)sj[t] * n;
-            const double *uc = U + si[t];
-            for (int64_t k = k0; k < k1; ++k) acc = fma(wr[k], uc[k * n], acc);
+        for (int64_t k = tid; k < n; k += CD_B) acc = fma(wr[k], uc[k * n], acc);
+        red[tid] = acc;
+        __syncthreads();
+        for (int w = CD_B / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
         }
-        part[c * CD_B + t] = acc;
+        if (tid == 0) bout[c] = g[b0 + c] + red[0];
         return;
     }
-    // interaction matrix: this CTA handles sources s in [s0, s1)
-    const int kb = c - nchunks;
+    if (tid < nb) {
+        si[tid] = pi[b0 + tid];
+        sj[tid] = pj[b0 + tid];
+    }
+    __syncthreads();
+    const int kb = c - nb;
     const int per = CD_B / NKB;
     const int s0 = kb * per, s1 = min(nb, s0 + per);
+    const int t = tid;
     if (t >= nb) return;
     const int64_t it = si[t], jt = sj[t];
     for (int s = s0; s < s1; ++s) {
@@ -83,7 +91,7 @@ __global__ void __launch_bounds__(CD_B) k_cd_dots(const double *__restrict__ W,
 
 __global__ void __launch_bounds__(RT) k_cd_resolve(
     int64_t n, double lam, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj,
-    int64_t b0, int nb, int nchunks, const double *__restrict__ part, const double *__restrict__ Kt,
+    int64_t b0, int nb, const double *__restrict__ bin, const double *__restrict__ Kt,
     const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
     double *__restrict__ D, int32_t *__restrict__ seg, int32_t *__restrict__ esrc,
     double *__restrict__ emu) {
@@ -97,10 +105,9 @@ __global__ void __launch_bounds__(RT) k_cd_resolve(
     __shared__ int wtot[RT / 32];
     const int tid = threadIdx.x;
     (void)n;
+    (void)g;
     if (tid < nb) {
-        double b = g[b0 + tid];
-        for (int c = 0; c < nchunks; ++c) b += part[c * CD_B + tid];
-        bsh[tid] = b;
+        bsh[tid] = bin[tid];
         csh[tid] = aval[b0 + tid] + D[b0 + tid];
         ish[tid] = inva[b0 + tid];
         si[tid] = pi[b0 + tid];
@@ -196,17 +203,25 @@ __global__ void __launch_bounds__(RT) k_cd_resolve(
     }
 }
 
-__global__ void __launch_bounds__(RT) k_cd_rows(const double *__restrict__ W, double *__restrict__ U,
-                                                int64_t n, const int32_t *__restrict__ seg,
-                                                const int32_t *__restrict__ esrc,
-                                                const double *__restrict__ emu) {
+// Row updates: CTA (k, y) applies segment k's updates to columns
+// [y * RCOLS, (y + 1) * RCOLS) of its target row, in sweep order.
+constexpr int RCOLS = 512;
+constexpr int RTH = 128;
+__global__ void __launch_bounds__(RTH) k_cd_rows(const double *__restrict__ W, double *__restrict__ U,
+                                                 int64_t n, const int32_t *__restrict__ seg,
+                                                 const int32_t *__restrict__ esrc,
+                                                 const double *__restrict__ emu) {
     const int k = blockIdx.x;
     const int nseg = seg[0];
     if (k >= nseg) return;
     const int64_t dest = seg[SEG_DEST + k];
     const int e0 = seg[SEG_START + k], e1 = seg[SEG_START + k + 1];
     double *ur = U + dest * n;
-    for (int64_t col = threadIdx.x; col < n; col += RT) {
+    const int64_t c0 = (int64_t)blockIdx.y * RCOLS;
+#pragma unroll
+    for (int q = 0; q < RCOLS / RTH; ++q) {
+        const int64_t col = c0 + threadIdx.x + q * RTH;
+        if (col >= n) break;
         double u = ur[col];
         for (int e = e0; e < e1; ++e) u = fma(emu[e], W[(int64_t)esrc[e] * n + col], u);
         ur[col] = u;
@@ -231,21 +246,17 @@ cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
         g_attr_done = true;
     }
     if (np <= 0) return cudaSuccess;
-    int nchunks = (int)lmin(MAX_CHUNKS, (n + 15) / 16);
-    if (nchunks < 1) nchunks = 1;
-    const int64_t KC = (n + nchunks - 1) / nchunks;
-    double *Kt = w.cd_part + (size_t)MAX_CHUNKS * CD_B;
+    double *bvec = w.cd_part;                     // CD_B stale dots
+    double *Kt = w.cd_part + (size_t)MAX_CHUNKS * CD_B;  // CD_B x CD_B interactions
+    const dim3 rgrid(NE, (unsigned)((n + RCOLS - 1) / RCOLS));
     for (int sw = 0; sw < nsweeps; ++sw) {
         for (int64_t b0 = 0; b0 < np; b0 += CD_B) {
             const int nb = (int)lmin(CD_B, np - b0);
-            k_cd_dots<<<nchunks + NKB, CD_B, 0, st>>>(W, U, n, pi, pj, b0, nb, KC, nchunks,
-                                                      w.cd_part, Kt);
-            counted(1);
-            k_cd_resolve<<<1, RT, kbytes, st>>>(n, lam, pi, pj, b0, nb, nchunks, w.cd_part, Kt,
-                                                inva, g, aval, D, w.cd_seg, w.cd_esrc, w.cd_emu);
-            counted(1);
-            k_cd_rows<<<NE, RT, 0, st>>>(W, U, n, w.cd_seg, w.cd_esrc, w.cd_emu);
-            counted(1);
+            k_cd_dots<<<nb + NKB, CD_B, 0, st>>>(W, U, n, pi, pj, g, b0, nb, bvec, Kt);
+            k_cd_resolve<<<1, RT, kbytes, st>>>(n, lam, pi, pj, b0, nb, bvec, Kt, inva, g, aval, D,
+                                                w.cd_seg, w.cd_esrc, w.cd_emu);
+            k_cd_rows<<<rgrid, RTH, 0, st>>>(W, U, n, w.cd_seg, w.cd_esrc, w.cd_emu);
+            counted(3);
         }
     }
     return cudaGetLastError();

@@ -117,80 +117,122 @@ __global__ void __launch_bounds__(TPB) k_syrk_S(const double *__restrict__ X, in
 }
 
 // ---------------------------------------------------------------- a2: Cholesky
-// Step kb of the blocked right-looking factorisation.  Every CTA factors the
-// (already updated) diagonal block kb in shared memory; CTA 0 stores it and
-// reports a non-positive pivot, CTA r > 0 solves block row kb + r of the
-// panel, L_ik = A_ik L_kk^{-T}.  Fusing the diagonal factorisation into the
-// panel launch costs a redundant 32^3/3 flops per CTA and saves a launch.
-__global__ void __launch_bounds__(TPB) k_potrf_panel(double *__restrict__ A, int64_t n, int kb,
-                                                     DevScalars *sc) {
+// Blocked right-looking factorisation with 32-wide panels.  The serial part
+// of each step, factoring the 32 x 32 diagonal block and inverting its
+// factor, is done by one warp in registers inside the trailing-update launch
+// of the previous step (by the CTA that produces that block, which is
+// scheduled first), so the panel itself is a parallel GEMM with the inverse:
+//   step k:  L_ik = A_ik X_kk^T  (X_kk = L_kk^{-1})       k_potrf_panel
+//            A_IJ -= L_Ik L_Jk^T, and factor block k+1   k_potrf_trail
+// X_kk alternates between two 32 x 32 slots of `xd`.
+
+// 1/sqrt(d) by Newton's iteration r <- r (3 - d r^2) / 2 from a
+// single-precision seed (two steps reach full double precision); plain
+// sqrt/division outside the single-precision range.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double r = (double)rsqrtf((float)d);
+    r = r * fma(-0.5 * d * r, r, 1.5);
+    r = r * fma(-0.5 * d * r, r, 1.5);
+    return r;
+}
+
+// One warp factors the kw x kw lower block B (shared, row-major, padded) in
+// place and writes Xs = L^{-1}.  Returns 0 or the failing pivot + 1 (same in
+// every lane).  Lane i keeps row i of the block in registers.
+__device__ int warp_chol_inv32(double (*B)[NB + 1], double (*Xs)[NB + 1], int kw) {
+    const int lane = threadIdx.x & 31;
+    double a[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[c] = (lane < kw && c <= lane) ? B[lane][c] : 0.0;
+    double rdiag = 0.0;
+    int fail = 0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j < kw && !fail) {
+            const double d = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(d > 0.0)) {
+                fail = j + 1;
+            } else {
+                const double r = rsqrt_newton(d);
+                if (lane == j) { a[j] = d * r; rdiag = r; }
+                if (lane > j) a[j] *= r;
+#pragma unroll
+                for (int k = j + 1; k < NB; ++k) {
+                    const double lkj = __shfl_sync(0xffffffffu, a[j], k);
+                    if (lane >= k) a[k] = fma(-a[j], lkj, a[k]);
+                }
+            }
+        }
+    }
+    if (fail) return fail;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) B[lane][c] = a[c];
+    __syncwarp();
+    // X = L^{-1}: lane c solves L x = e_c (x_i = 0 for i < c)
+    double x[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        double s = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+        for (int t = 0; t < i; ++t) s = fma(-B[i][t], x[t], s);
+        const double ri = __shfl_sync(0xffffffffu, rdiag, i);
+        x[i] = (i < kw && i >= lane) ? s * ri : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) Xs[i][lane] = x[i];
+    __syncwarp();
+    return 0;
+}
+
+// Factor diagonal block kb (used for the first block) and store L_kk, X_kk.
+__global__ void k_potrf_diag(double *__restrict__ A, int64_t n, int kb, double *__restrict__ xd,
+                             DevScalars *sc) {
     if (sc->info != 0) return;
-    __shared__ double Ld[NB][NB + 1];
-    __shared__ double P[NB][NB + 1];
-    __shared__ int fail;
-    const int tid = threadIdx.x;
+    __shared__ double B[NB][NB + 1], Xs[NB][NB + 1];
     const int64_t k0 = (int64_t)kb * NB;
     const int kw = (int)lmin(NB, n - k0);
-    for (int idx = tid; idx < NB * NB; idx += TPB) {
-        int r = idx / NB, c = idx % NB;
-        Ld[r][c] = (r < kw && c <= r) ? A[(k0 + r) * n + k0 + c] : 0.0;
-    }
-    if (tid == 0) fail = 0;
-    __syncthreads();
-    for (int j = 0; j < kw; ++j) {
-        if (tid == 0) {
-            double d = Ld[j][j];
-            if (!(d > 0.0)) fail = j + 1;
-            else Ld[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        if (fail) break;
-        for (int r = j + 1 + tid; r < kw; r += TPB) Ld[r][j] /= Ld[j][j];
-        __syncthreads();
-        int rem = kw - j - 1;
-        for (int idx = tid; idx < rem * rem; idx += TPB) {
-            int r = j + 1 + idx / rem, c = j + 1 + idx % rem;
-            if (c <= r) Ld[r][c] -= Ld[r][j] * Ld[c][j];
-        }
-        __syncthreads();
-    }
-    if (fail) {
-        if (blockIdx.x == 0 && tid == 0) sc->info = (int)(k0 + fail);
+    const int lane = threadIdx.x;
+    for (int r = 0; r < NB; ++r) B[r][lane] = (r < kw && lane <= r) ? A[(k0 + r) * n + k0 + lane] : 0.0;
+    __syncwarp();
+    const int f = warp_chol_inv32(B, Xs, kw);
+    if (f) {
+        if (lane == 0) sc->info = (int)(k0 + f);
         return;
     }
-    if (blockIdx.x == 0) {
-        for (int idx = tid; idx < kw * kw; idx += TPB) {
-            int r = idx / kw, c = idx % kw;
-            if (c <= r) A[(k0 + r) * n + k0 + c] = Ld[r][c];
-        }
-        return;
-    }
-    const int64_t r0 = k0 + (int64_t)blockIdx.x * NB;
-    const int rh = (int)lmin(NB, n - r0);
-    for (int idx = tid; idx < NB * NB; idx += TPB) {
-        int r = idx / NB, c = idx % NB;
-        P[r][c] = (r < rh && c < kw) ? A[(r0 + r) * n + k0 + c] : 0.0;
-    }
-    __syncthreads();
-    for (int c = 0; c < kw; ++c) {
-        if (tid < rh) P[tid][c] /= Ld[c][c];
-        __syncthreads();
-        int rem = kw - c - 1;
-        for (int idx = tid; idx < rh * rem; idx += TPB) {
-            int r = idx / rem, cc = c + 1 + idx % rem;
-            P[r][cc] -= P[r][c] * Ld[cc][c];
-        }
-        __syncthreads();
-    }
-    for (int idx = tid; idx < rh * kw; idx += TPB) {
-        int r = idx / kw, c = idx % kw;
-        A[(r0 + r) * n + k0 + c] = P[r][c];
+    double *X = xd + (kb & 1) * NB * NB;
+    for (int r = 0; r < NB; ++r) {
+        X[r * NB + lane] = Xs[r][lane];
+        if (r < kw && lane <= r) A[(k0 + r) * n + k0 + lane] = B[r][lane];
     }
 }
 
-// Trailing update of step kb: A_IJ -= L_I,kb L_J,kb^T on lower tiles I >= J > kb.
+// Panel of step kb: block row kb + 1 + blockIdx.x, L_ik = A_ik X_kk^T.
+__global__ void __launch_bounds__(TPB) k_potrf_panel(double *__restrict__ A, int64_t n, int kb,
+                                                     const double *__restrict__ xd, DevScalars *sc) {
+    if (sc->info != 0) return;
+    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    const int64_t k0 = (int64_t)kb * NB;
+    const int64_t kw = lmin(NB, n - k0);
+    const int64_t i0 = k0 + (int64_t)(blockIdx.x + 1) * NB;
+    const double *X = xd + (kb & 1) * NB * NB;
+    double acc[2][2] = {{0, 0}, {0, 0}};
+    // opA(i, c) = A[i0 + i, k0 + c]; opB(c, j) = X[j][c]
+    tile_acc<double, false, true>(acc, A + i0 * n + k0, n, X, NB, 0, 0, 0, kw, n - i0, kw, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int64_t i = i0 + ty + 16 * a, j = tx + 16 * b;
+            if (i < n && j < kw) A[i * n + k0 + j] = acc[a][b];
+        }
+}
+
+// Trailing update of step kb on lower tiles I >= J > kb; the CTA of tile
+// (kb+1, kb+1) then factors that block and inverts its factor.
 __global__ void __launch_bounds__(TPB) k_potrf_trail(double *__restrict__ A, int64_t n, int kb,
-                                                     DevScalars *sc) {
+                                                     double *__restrict__ xd, DevScalars *sc) {
     if (sc->info != 0) return;
     __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
     int64_t I, J;
@@ -201,13 +243,34 @@ __global__ void __launch_bounds__(TPB) k_potrf_trail(double *__restrict__ A, int
     double acc[2][2] = {{0, 0}, {0, 0}};
     tile_acc<double, false, true>(acc, A, n, A, n, I * NB, J * NB, k0, k1, n, n, As, Bs);
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const bool diag_next = (I == kb + 1 && J == kb + 1);
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
-            if (i < n && j < n && j <= i) A[i * n + j] -= acc[a][b];
+            const int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
+            if (i < n && j < n && j <= i) {
+                const double v = A[i * n + j] - acc[a][b];
+                A[i * n + j] = v;
+                if (diag_next) As[ty + 16 * a][tx + 16 * b] = v;
+            }
         }
+    if (!diag_next) return;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int64_t d0 = I * NB;
+    const int kw = (int)lmin(NB, n - d0);
+    const int f = warp_chol_inv32(As, Bs, kw);
+    const int lane = threadIdx.x;
+    if (f) {
+        if (lane == 0) sc->info = (int)(d0 + f);
+        return;
+    }
+    double *X = xd + (I & 1) * NB * NB;
+    for (int r = 0; r < NB; ++r) {
+        X[r * NB + lane] = Bs[r][lane];
+        if (r < kw && lane <= r) A[(d0 + r) * n + d0 + lane] = As[r][lane];
+    }
 }
 
 // log det A = 2 sum_i log L_ii, deterministic single-CTA reduction.
@@ -364,18 +427,17 @@ cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, d
     return cudaGetLastError();
 }
 
-cudaError_t potrf(double *A, int64_t n, DevScalars *sc, cudaStream_t st) {
+cudaError_t potrf(double *A, int64_t n, double *xd, DevScalars *sc, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int64_t nb = (n + NB - 1) / NB;
-    for (int64_t kb = 0; kb < nb; ++kb) {
-        k_potrf_panel<<<(unsigned)(nb - kb), TPB, 0, st>>>(A, n, (int)kb, sc);
-        counted(1);
+    k_potrf_diag<<<1, 32, 0, st>>>(A, n, 0, xd, sc);
+    counted(1);
+    for (int64_t kb = 0; kb + 1 < nb; ++kb) {
         const int64_t m = nb - kb - 1;
-        if (m > 0) {
-            k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, sc);
-            counted(1);
-        }
+        k_potrf_panel<<<(unsigned)m, TPB, 0, st>>>(A, n, (int)kb, xd, sc);
+        k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, xd, sc);
+        counted(2);
     }
     k_logdet<<<1, TPB, 0, st>>>(A, n, sc);
     counted(1);

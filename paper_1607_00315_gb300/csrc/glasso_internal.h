@@ -84,6 +84,7 @@ struct Work {
     int32_t *cd_seg = nullptr;             // segment table of the row updates
     double *cd_emu = nullptr;              // 2 CD_B entry coefficients
     int32_t *cd_esrc = nullptr;            // 2 CD_B entry source rows
+    double *xd = nullptr;                  // 2 x 32 x 32: inverses of Cholesky diagonal blocks
     DevScalars *sc = nullptr;              // device scalars
     DevScalars *sc_host = nullptr;         // pinned mirror
 };
@@ -108,7 +109,8 @@ namespace glx {
 cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, double *S,
                    double *mu_scratch, cudaStream_t st);
 // In-place blocked Cholesky of the lower triangle; writes sc->info and sc->logdet.
-cudaError_t potrf(double *A, int64_t n, DevScalars *sc, cudaStream_t st);
+// xd: scratch of 2 * NB * NB doubles (inverses of the diagonal blocks).
+cudaError_t potrf(double *A, int64_t n, double *xd, DevScalars *sc, cudaStream_t st);
 // W = L^{-T} L^{-1}; X (n x n) and Tw (n x n) are scratch.
 cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st);
 
