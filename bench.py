@@ -44,6 +44,11 @@ def fp64_peak_tflops(bf16_tflops):
     return bf16_tflops * 1.25 / 2250.0
 
 
+def fp32_simt_peak_tflops(sm_mhz):
+    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -282,12 +287,16 @@ def main():
     d = classes[dom]
     per_launch_ms = d["ms"] / d["launches"]
     work_per_launch = d["work"] / d["launches"]
-    if dom in ("cholesky", "inverse", "ls_cholesky"):
+    if dom in ("cholesky", "inverse", "ls_cholesky", "ns_refine"):
         achieved = work_per_launch / (per_launch_ms * 1e-3) / 1e12
-        peak = fp64_peak_tflops(bf16)
+        if args.precision == "fp64":
+            peak = fp64_peak_tflops(bf16)
+            psrc = f"FP64 = {src} bf16 burst {bf16} TF/s x nominal 1.25/2250"
+        else:
+            peak = fp32_simt_peak_tflops(2070.0)
+            psrc = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2070 MHz"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "peak_source": f"FP64 = {src} bf16 burst {bf16} TF/s x nominal 1.25/2250"}
+                "frac": achieved / peak, "peak_source": psrc}
     else:
         achieved = work_per_launch / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

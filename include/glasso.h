@@ -138,12 +138,13 @@ glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
 
 /* Kernel classes timed with CUDA events on the context's stream when
  * profiling is on: 0 Cholesky of the iterate, 1 inverse (W = A^{-1}),
- * 2 level-0 free-set scan, 3 CD sweeps, 4 line-search Cholesky trials. */
-#define GLASSO_PROF_CLASSES 5
+ * 2 level-0 free-set scan, 3 CD sweeps, 4 line-search Cholesky trials,
+ * 5 Newton-Schulz refinement GEMMs of W (mixed precision). */
+#define GLASSO_PROF_CLASSES 6
 typedef struct {
     double ms[GLASSO_PROF_CLASSES];        /* summed device time */
     long long launches[GLASSO_PROF_CLASSES];
-    double work[GLASSO_PROF_CLASSES];      /* algorithmic flops (0, 1, 4) or bytes (2, 3) */
+    double work[GLASSO_PROF_CLASSES];      /* algorithmic flops (0, 1, 4, 5) or bytes (2, 3) */
     long long kernels;                     /* kernels launched by the library (all contexts,
                                               counted always) since the last reset */
 } glasso_profile;

@@ -268,7 +268,10 @@ int orc_hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uint8_t
  * reversed; the minimiser of a z^2/2 + b z + lambda |z| is -(b - lambda)/a
  * for b > lambda, which is what the formula above gives.
  * U = Delta W is kept up to date: (W Delta W)_ij = W_i,: . U_:,j and the
- * update adds mu W_j,: to row i of U and mu W_i,: to row j.
+ * update adds mu W_j,: to row i of U and mu W_i,: to row j.  When the
+ * shrinkage returns zero the new value A_ij + Delta_ij is set to exactly zero
+ * (Delta_ij = -A_ij), so that the support test A_ij != 0 of eq. active_set
+ * sees the zero the shrinkage prescribes rather than a rounding residue.
  * D holds Delta on the pair list (in/out); U is n x n (in/out).           */
 void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n, double lam,
                    const int32_t *pi, const int32_t *pj, int64_t np, int nsweeps,
@@ -282,9 +285,16 @@ void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n,
             for (int64_t k = 0; k < n; ++k) wdw += W[i * n + k] * U[k * n + j];
             double b = (S[i * n + j] - wij) + wdw;
             double c = A[i * n + j] + D[p];
-            double mu = -c + soft(c - b / a, lam / a);
+            double z = soft(c - b / a, lam / a);
+            double mu = -c + z;
             if (mu != 0.0) {
-                D[p] += mu;
+                /* a zero from the shrinkage is written exactly: A_ij + Delta_ij = 0 */
+                if (z == 0.0) {
+                    mu = -A[i * n + j] - D[p];
+                    D[p] = -A[i * n + j];
+                } else {
+                    D[p] += mu;
+                }
                 for (int64_t k = 0; k < n; ++k) U[i * n + k] += mu * W[j * n + k];
                 if (i != j)
                     for (int64_t k = 0; k < n; ++k) U[j * n + k] += mu * W[i * n + k];

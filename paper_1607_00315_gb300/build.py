@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libglasso.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["api.cu", "dense.cu", "scan.cu", "hier.cu", "cd.cu"]
+SOURCES = ["api.cu", "dense.cu", "scan.cu", "hier.cu", "cd.cu", "mixed.cu", "tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

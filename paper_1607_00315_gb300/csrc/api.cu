@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -52,6 +53,7 @@ size_t footprint(int64_t n, int64_t m, int xbytes) {
     b += (size_t)n * ((n + 31) / 32) * sizeof(uint32_t);          // masks
     b += (size_t)(n + 1) * sizeof(long long) + (size_t)n * 6 * sizeof(double);
     if (m > 0) b += (size_t)m * n * (sizeof(double) + xbytes) + (size_t)n * sizeof(double);
+    b += nn * (sizeof(int32_t) + sizeof(double));  // CSR of A (mixed precision)
     return b + (4u << 20);
 }
 
@@ -81,7 +83,10 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.mask, st); dfree(w.rowcnt, st); dfree(w.rowred, st); dfree(w.flags, st);
     dfree(w.blkcnt, st); dfree(w.redbuf, st);
     dfree(w.cd_part, st); dfree(w.cd_mu, st); dfree(w.cd_seg, st); dfree(w.cd_emu, st);
-    dfree(w.cd_esrc, st); dfree(w.xd, st); dfree(w.sc, st);
+    dfree(w.cd_esrc, st); dfree(w.xd, st); dfree(w.ldiag, st); dfree(w.sc, st);
+    dfree(w.csr_ptr, st); dfree(w.csr_col, st); dfree(w.csr_val, st); dfree(w.part, st);
+    dfree(w.Wp, st); dfree(w.Qp, st); dfree(w.Xt, st);
+    w.cap_mixed = w.cap_part = w.cap_xt = 0;
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
     w.cap_n = w.cap_pairs = w.cap_x = w.cap_xraw = w.cap_blk = w.cap_red = 0;
@@ -117,8 +122,24 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
     CK(dalloc(w.mask, (size_t)n * ((n + 31) / 32), st));
     CK(dalloc(w.rowcnt, n + 1, st));
     CK(dalloc(w.rowred, (size_t)n * 6, st));
+    CK(dalloc(w.ldiag, n, st));
     w.cap_n = n;
     w.cap_pairs = pairs;
+    return GLASSO_OK;
+}
+
+glasso_status work_ensure_mixed(Work &w, int64_t n, cudaStream_t st, std::string &err) {
+    if (n <= w.cap_mixed) return GLASSO_OK;
+    const int64_t nt = (n + 31) / 32;
+    CK(dalloc(w.csr_ptr, n + 1, st));
+    CK(dalloc(w.csr_col, (size_t)n * n + n, st));
+    CK(dalloc(w.csr_val, (size_t)n * n + n, st));
+    w.cap_part = nt * (nt + 1) / 2 + 1024;
+    CK(dalloc(w.part, w.cap_part, st));
+    const int64_t np2 = tc_pad(n) * tc_pad(n);
+    CK(dalloc(w.Wp, np2, st));
+    CK(dalloc(w.Qp, np2, st));
+    w.cap_mixed = n;
     return GLASSO_OK;
 }
 
@@ -198,7 +219,7 @@ glasso_status check_symmetric(Work &w, const double *M, int64_t n, cudaStream_t 
 struct Prof {
     bool on = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
-    double ms[GLASSO_PROF_CLASSES] = {0};
+    double ms[GLASSO_PROF_CLASSES] = {0};  // indexes as in glasso.h
     long long count[GLASSO_PROF_CLASSES] = {0};
     double work[GLASSO_PROF_CLASSES] = {0};
     std::vector<double> pend_work;
@@ -210,6 +231,7 @@ struct Solver {
     cudaStream_t st;
     std::string &err;
     Prof *prof;
+    int precision = GLASSO_FP64;
     glasso_status sync() {
         CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -273,7 +295,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     if (!have_A0) CK(init_diag(w.S, n, lam, w.A, sc, st));
     CK(cudaMemcpyAsync(w.L, w.A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     sv.mark_begin(0, eb);
-    CK(potrf(w.L, n, w.xd, sc, st));
+    CK(potrf(w.L, n, w.xd, w.ldiag, sc, st));
     sv.mark_end(0, eb, flop_chol);
     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
     if (h->err || h->info != 0) return GLASSO_ENOTPD;
@@ -353,7 +375,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                 for (int t = 0; t < max_trials; ++t) {
                     CK(ls_build_trial(w.A, w.T, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                     sv.mark_begin(4, eb);
-                    CK(potrf(w.T, n, w.xd, sc, st));
+                    CK(potrf(w.T, n, w.xd, w.ldiag, sc, st));
                     sv.mark_end(4, eb, flop_chol);
                     CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
                     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -413,10 +435,299 @@ done:
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision solve (GLASSO_MIXED).  Same ML-cycle and relaxation as
+// solve_core; the differences are confined to how W and the line-search
+// log-det are obtained (mixed.cu):
+//  * W (FP64) comes from the previous W by Newton-Schulz refinement against
+//    the new A (FP32 GEMM corrections, FP64 residual), or after a large step
+//    from an FP32 Cholesky + inverse, then refined the same way;
+//  * the CD sweep runs on FP32 copies of W and U (an inexact Hessian, which
+//    the convergence theory of Section 4.1 allows), with the FP64 gradient;
+//  * the line search uses the log-det series when its remainder bound is below
+//    the objective's FP64 resolution (positive definiteness then holds by
+//    construction, and the increment is exact enough to track log det A), and
+//    otherwise an FP32 Cholesky (FP64 diagonal blocks and log accumulation)
+//    whose log-det error is taken as n 2^-20.
+glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
+                               bool have_A0, glasso_info *info) {
+    Work &w = sv.w;
+    cudaStream_t st = sv.st;
+    std::string &err = sv.err;
+    DevScalars *sc = w.sc;
+    DevScalars *h = w.sc_host;
+    {
+        glasso_status s0 = work_ensure_mixed(w, n, st, err);
+        if (s0 != GLASSO_OK) return s0;
+    }
+    const size_t nn = (size_t)n * (size_t)n;
+    float *T32 = (float *)w.T, *X32 = T32 + nn;
+    float *W32 = (float *)w.L, *R32 = W32 + nn;
+    float *U32 = (float *)w.U, *Tw32 = U32 + nn;
+    double *W64 = w.W;
+    const double sigma = 1e-4;
+    const int max_trials = 30;
+    const double nd = (double)n;
+    const double e_chol = nd * 0x1p-20;  // FP32 Cholesky log-det error allowance
+    const double ns_tol = 1e-11;
+    const int max_ns = 8;
+    int cycles = 0, relax = 0, lstrials = 0;
+    double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
+    long long nnz = 0;
+    glasso_status status = GLASSO_EMAXITER;
+    bool W_valid = false, fresh_scan = false, last_chol = false;
+    int64_t nf = 0;
+    cudaEvent_t eb;
+
+    // W from an FP32 factorisation held in T32 (lower), then refined.
+    auto factor_inverse = [&]() -> glasso_status {
+        sv.mark_begin(1, eb);
+        CK(inverse32(T32, n, W32, X32, Tw32, st));
+        CK(to_f64(W32, W64, (int64_t)nn, st));
+        sv.mark_end(1, eb, 2.0 * nd * nd * nd / 3.0);
+        return GLASSO_OK;
+    };
+    auto fresh_factor = [&]() -> glasso_status {
+        CK(trial32(w.A, T32, n, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
+        CK(potrf32(T32, n, (float *)w.xd, w.ldiag, sc, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        if (h->info != 0) return GLASSO_ENOTPD;
+        return factor_inverse();
+    };
+    auto refine = [&]() -> glasso_status {
+        CK(build_csr(w.A, n, w.csr_ptr, w.csr_col, w.csr_val, st));
+        bool restarted = false;
+        for (int it = 0; it < max_ns; ++it) {
+            CK(residual(w.csr_ptr, w.csr_col, w.csr_val, W64, n, R32, W32, w.rowred, sc, st));
+            if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            if (h->tc_err) {
+                err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
+                return GLASSO_ECUDA;
+            }
+            if (h->ns_max <= ns_tol) break;
+            if (!(sqrt(h->ns_fro2) < 0.9)) {
+                if (restarted) break;
+                restarted = true;
+                glasso_status s2 = fresh_factor();
+                if (s2 != GLASSO_OK) return s2;
+                it = -1;
+                continue;
+            }
+            sv.mark_begin(5, eb);
+            CK(ns_gemm_tc(W64, R32, n, W64, w.Wp, w.Qp, &sc->tc_err, st));
+            sv.mark_end(5, eb, nd * nd * nd);
+        }
+        return GLASSO_OK;
+    };
+    auto update_W = [&]() -> glasso_status {
+        if (last_chol) {
+            glasso_status s2 = factor_inverse();
+            if (s2 != GLASSO_OK) return s2;
+        }
+        return refine();
+    };
+
+    CK(cudaMemsetAsync(sc, 0, sizeof(DevScalars), st));
+    if (!have_A0) {
+        CK(init_diag(w.S, n, lam, w.A, sc, st));
+        CK(diag_inverse(w.A, n, W64, w.ldiag, sc, st));
+        CK(to_f32(W64, W32, (int64_t)nn, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        if (h->err) return GLASSO_ENOTPD;
+        logdet = h->logdet;
+    } else {
+        glasso_status s2 = fresh_factor();
+        if (s2 != GLASSO_OK) return s2;
+        logdet = h->logdet;
+        s2 = refine();
+        if (s2 != GLASSO_OK) return s2;
+    }
+    W_valid = true;
+    CK(scan_full(w.S, W64, w.A, n, lam, 1, w, w.fi, w.fj, w.fabsg, sc, st));
+    if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+    nf = h->count;
+    trSA = h->trSA;
+    l1 = h->l1;
+    F = -logdet + trSA + lam * l1;
+
+    for (int k = 0; k < max_cycles; ++k) {
+        cycles = k + 1;
+        const int nsweeps = std::min(1 + k / 3, 10);
+        CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
+        CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        const int Lv = h->levels;
+        for (int l = Lv; l >= 0; --l) {
+            fresh_scan = false;
+            if (!W_valid) {
+                glasso_status s2 = update_W();
+                if (s2 != GLASSO_OK) return s2;
+                W_valid = true;
+            }
+            int64_t np;
+            if (l == 0) {
+                sv.mark_begin(2, eb);
+                CK(scan_full(w.S, W64, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+                sv.mark_end(2, eb, 3.0 * nd * (nd + 1) / 2 * 8.0);
+                if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                np = h->count;
+                trSA = h->trSA;
+                l1 = h->l1;
+                nnz = h->nnz;
+                F = -logdet + trSA + lam * l1;
+                relkkt = h->kkt_sum / l1;
+                maxkkt = h->kkt_max;
+                fresh_scan = true;
+                CK(cudaMemcpyAsync(w.fi, w.pi, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(w.fj, w.pj, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(w.fabsg, w.pabsg, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                nf = np;
+                if (relkkt <= tol) {
+                    status = GLASSO_OK;
+                    goto done;
+                }
+            } else {
+                CK(scan_cand(w.S, W64, w.A, n, lam, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
+                             nullptr, sc, st));
+                if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                np = h->count;
+            }
+            ++relax;
+            if (np == 0) continue;
+            CK(pair_prep(w.S, W64, w.A, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+            CK(cudaMemsetAsync(U32, 0, nn * sizeof(float), st));
+            CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
+            sv.mark_begin(3, eb);
+            // FP32 resolution chain while the iterate is far from the optimum; FP64
+            // once the relative KKT residual is small, where the Newton step must be
+            // resolved to the gradient's FP64 accuracy
+            CK(cd_sweeps32(W32, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
+                           relkkt <= 1e-6, st));
+            sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 4.0);
+            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
+            CK(series_terms(W64, n, w.pi, w.pj, w.D, np, U32, w.part, w.cap_part, sc, st));
+            if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            if (!h->moved) continue;
+            {
+                const double delta = h->delta, trSD = h->trSD;
+                const double t1 = h->t1, t2 = std::max(h->t2, 0.0);
+                const double epsF = 1e-12 * std::max(fabs(F), nd);
+                double alpha = 1.0;
+                bool ok = false, chol = false;
+                double FT = 0.0, dl1 = 0.0, dld = 0.0;
+                for (int t = 0; t < max_trials; ++t) {
+                    const double rho = alpha * sqrt(t2);
+                    CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
+                    double errb;
+                    bool pd = true;
+                    // the series' remainder bound must be below the objective's
+                    // FP64 resolution, because the increment is also added to the
+                    // tracked log-det
+                    const double rem = rho < 0.5 ? rho * rho * rho / (3.0 * (1.0 - rho)) : INFINITY;
+                    if (rem + 1e-6 * alpha * alpha * t2 <= epsF) {
+                        chol = false;
+                        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                        dld = alpha * t1 - 0.5 * alpha * alpha * t2;
+                        errb = rem + 1e-6 * alpha * alpha * t2;
+                    } else {
+                        chol = true;
+                        CK(trial32(w.A, T32, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                        sv.mark_begin(4, eb);
+                        CK(potrf32(T32, n, (float *)w.xd, w.ldiag, sc, st));
+                        sv.mark_end(4, eb, nd * nd * nd / 3.0);
+                        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                        pd = h->info == 0;
+                        dld = h->logdet - logdet;
+                        errb = 2.0 * e_chol;
+                    }
+                    ++lstrials;
+                    if (pd) {
+                        dl1 = h->dl1;
+                        FT = F - dld + alpha * trSD + lam * dl1;
+                        if (FT <= F + sigma * alpha * delta + errb + epsF) {
+                            ok = true;
+                            break;
+                        }
+                    }
+                    alpha *= 0.5;
+                }
+                if (!ok) {
+                    status = GLASSO_ELINESEARCH;
+                    goto done;
+                }
+                CK(ls_apply(w.A, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                logdet += dld;
+                trSA += alpha * trSD;
+                l1 += dl1;
+                F = FT;
+                W_valid = false;
+                last_chol = chol;
+            }
+        }
+    }
+done:
+    if (!fresh_scan) {
+        if (!W_valid) {
+            glasso_status s2 = update_W();
+            if (s2 != GLASSO_OK) return s2;
+            W_valid = true;
+        }
+        CK(scan_full(w.S, W64, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        trSA = h->trSA;
+        l1 = h->l1;
+        nnz = h->nnz;
+        F = -logdet + trSA + lam * l1;
+        relkkt = h->kkt_sum / l1;
+        maxkkt = h->kkt_max;
+    }
+    if (info) {
+        info->status = status;
+        info->cycles = cycles;
+        info->relaxations = relax;
+        info->ls_trials = lstrials;
+        info->objective = F;
+        info->rel_kkt = relkkt;
+        info->max_kkt = maxkkt;
+        info->logdet = logdet;
+        info->nnz = nnz;
+    }
+    return status;
+}
+
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 // Stage the problem's S (or X -> S) and A0 on the device in w.
-glasso_status stage_problem(Work &w, cudaStream_t st, const glasso_problem *p, std::string &err) {
+glasso_status form_S_ctx(Work &w, cudaStream_t st, int precision, const void *X, int dtype,
+                         int64_t m, int64_t n, int center, double *S, std::string &err) {
+    if (precision == GLASSO_MIXED && dtype == GLASSO_F32) {
+        // TF32 tensor cores with FP32 accumulation (the FP32-sample workload)
+        const int64_t need = n * tc_pad(m);
+        if (need > w.cap_xt) {
+            CK(dalloc(w.Xt, need, st));
+            w.cap_xt = need;
+        }
+        double *mu = nullptr;
+        if (center) {
+            mu = w.Xin + m * n;  // n doubles of the staging buffer
+            CK(form_S(X, dtype, m, n, 2, S, w.Xin, st));  // mode 2: column means only
+        }
+        CK(cudaMemsetAsync(&w.sc->tc_err, 0, sizeof(int), st));
+        CK(syrk_tc(X, dtype, m, n, mu, S, w.Xt, &w.sc->tc_err, st));
+        CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (w.sc_host->tc_err) {
+            err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(w.sc_host->tc_err) + ")";
+            return GLASSO_ECUDA;
+        }
+        return GLASSO_OK;
+    }
+    CK(form_S(X, dtype, m, n, center, S, w.Xin, st));
+    return GLASSO_OK;
+}
+
+glasso_status stage_problem(Work &w, cudaStream_t st, const glasso_problem *p, std::string &err,
+                            int precision) {
     const int64_t n = p->n;
     const cudaMemcpyKind kind = p->location == GLASSO_HOST ? cudaMemcpyHostToDevice
                                                            : cudaMemcpyDeviceToDevice;
@@ -433,7 +744,8 @@ glasso_status stage_problem(Work &w, cudaStream_t st, const glasso_problem *p, s
             CK(cudaMemcpyAsync(w.Xraw, p->data, (size_t)(p->m * n) * xb, kind, st));
             X = w.Xraw;
         }
-        CK(form_S(X, p->dtype, p->m, n, p->center, w.S, w.Xin, st));
+        s = form_S_ctx(w, st, precision, X, p->dtype, p->m, n, p->center, w.S, err);
+        if (s != GLASSO_OK) return s;
     }
     s = check_symmetric(w, w.S, n, st, err);
     if (s != GLASSO_OK) return s;
@@ -457,7 +769,7 @@ glasso_status validate(const glasso_problem *p) {
 
 glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_problem *p,
                        double *A_out, double *W_out, glasso_info *info, std::string &err,
-                       Prof *prof, bool reuse_A, int out_location) {
+                       Prof *prof, bool reuse_A, int out_location, int precision) {
     auto t0 = std::chrono::steady_clock::now();
     glasso_info loc;
     memset(&loc, 0, sizeof(loc));
@@ -470,13 +782,15 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
     if (s == GLASSO_OK) {
         glasso_problem q = *p;
         if (reuse_A) q.A0 = nullptr;
-        s = stage_problem(w, st, &q, err);
+        s = stage_problem(w, st, &q, err, precision);
     }
     if (s == GLASSO_OK) {
-        Solver sv{w, st, err, prof};
+        Solver sv{w, st, err, prof, precision};
         const int mc = p->max_cycles > 0 ? p->max_cycles : 200;
-        s = solve_core(sv, p->n, p->lambda, p->tol, mc, p->A0 != nullptr || reuse_A, W_out != nullptr,
-                       &loc);
+        const bool warm = p->A0 != nullptr || reuse_A;
+        s = precision == GLASSO_MIXED
+                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, &loc)
+                : solve_core(sv, p->n, p->lambda, p->tol, mc, warm, W_out != nullptr, &loc);
         if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
             const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost
                                                                     : cudaMemcpyDeviceToDevice;
@@ -551,7 +865,7 @@ void worker_main(Serve *sv) {
         if (w.cap_n > 0 && (w.cap_n < r->p.n || w.cap_n > 2 * r->p.n)) work_free(w, st);
         glasso_info info;
         glasso_status s = solve_in(w, st, 0, &r->p, r->A_out, nullptr, &info, err, nullptr, false,
-                                   r->out_location);
+                                   r->out_location, sv->ctx->precision);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             r->info = info;
@@ -685,7 +999,7 @@ glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_o
     if (!ctx) return GLASSO_EINVAL;
     cudaSetDevice(ctx->device);
     return solve_in(ctx->w, ctx->stream, ctx->budget, p, A_out, W_out, info, ctx->last_error,
-                    (Prof *)ctx->prof, false, p ? p->location : GLASSO_HOST);
+                    (Prof *)ctx->prof, false, p ? p->location : GLASSO_HOST, ctx->precision);
 }
 
 glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int count,
@@ -722,10 +1036,10 @@ glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int c
         if (chain) {
             // continue from the previous solution kept in the workspace (w.A)
             s = solve_in(ctx->w, ctx->stream, ctx->budget, &p[k], A_out[k], nullptr, &inf,
-                         ctx->last_error, (Prof *)ctx->prof, true, p[k].location);
+                         ctx->last_error, (Prof *)ctx->prof, true, p[k].location, ctx->precision);
         } else {
             s = solve_in(ctx->w, ctx->stream, ctx->budget, &p[k], A_out[k], nullptr, &inf,
-                         ctx->last_error, (Prof *)ctx->prof, false, p[k].location);
+                         ctx->last_error, (Prof *)ctx->prof, false, p[k].location, ctx->precision);
         }
         if (infos) infos[k] = inf;
         if (s != GLASSO_OK && first == GLASSO_OK) first = s;
@@ -817,7 +1131,8 @@ glasso_status glasso_form_S(glasso_ctx *ctx, const void *X, int dtype, int64_t m
     glasso_status s = work_ensure(ctx->w, 1, ctx->stream, ctx->last_error);
     if (s == GLASSO_OK) s = work_ensure_x(ctx->w, m, n, 0, ctx->stream, ctx->last_error);
     if (s != GLASSO_OK) return s;
-    CTX_CK(form_S(X, dtype, m, n, center, S, ctx->w.Xin, ctx->stream));
+    s = form_S_ctx(ctx->w, ctx->stream, ctx->precision, X, dtype, m, n, center, S, ctx->last_error);
+    if (s != GLASSO_OK) return s;
     CTX_CK(cudaStreamSynchronize(ctx->stream));
     return GLASSO_OK;
 }
@@ -825,13 +1140,13 @@ glasso_status glasso_form_S(glasso_ctx *ctx, const void *X, int dtype, int64_t m
 glasso_status glasso_potrf(glasso_ctx *ctx, double *A, int64_t n, int *info, double *logdet) {
     if (!ctx || !A || n < 1) return GLASSO_EINVAL;
     cudaSetDevice(ctx->device);
-    glasso_status s = work_ensure(ctx->w, 1, ctx->stream, ctx->last_error);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
     if (s != GLASSO_OK) return s;
     Prof *prof = (Prof *)ctx->prof;
     Solver sv{ctx->w, ctx->stream, ctx->last_error, prof};
     cudaEvent_t eb;
     sv.mark_begin(0, eb);
-    CTX_CK(potrf(A, n, ctx->w.xd, ctx->w.sc, ctx->stream));
+    CTX_CK(potrf(A, n, ctx->w.xd, ctx->w.ldiag, ctx->w.sc, ctx->stream));
     sv.mark_end(0, eb, (double)n * n * n / 3.0);
     s = sync_ctx(ctx);
     if (prof) prof_collect(prof);
@@ -947,14 +1262,14 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
     double ldA = 0.0;
     // log det A itself (to express F(A + alpha Delta) relative to F_A)
     CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
+    CTX_CK(potrf(w.T, n, w.xd, w.ldiag, w.sc, st));
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;
     if (w.sc_host->info != 0) return GLASSO_EINVAL;
     ldA = w.sc_host->logdet;
     for (int t = 0; t < max_trials; ++t) {
         CTX_CK(ls_build_trial(A, w.T, n, pi, pj, w.p_a, D, np, a, st));
-        CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
+        CTX_CK(potrf(w.T, n, w.xd, w.ldiag, w.sc, st));
         CTX_CK(ls_dl1(w.p_a, D, pi, pj, np, a, w, w.sc, st));
         s = sync_ctx(ctx);
         if (s != GLASSO_OK) return s;
@@ -985,7 +1300,7 @@ glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A
     Work &w = ctx->w;
     cudaStream_t st = ctx->stream;
     CTX_CK(cudaMemcpyAsync(w.T, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CTX_CK(potrf(w.T, n, w.xd, w.sc, st));
+    CTX_CK(potrf(w.T, n, w.xd, w.ldiag, w.sc, st));
     // tr(SA) and ||A||_1 come with a scan whose W is S itself (G = 0): only the
     // trace and l1 sums are read from it.
     CTX_CK(scan_full(S, S, A, n, lambda, 0, w, w.pi, w.pj, nullptr, w.sc, st));

@@ -20,12 +20,12 @@ constexpr int TPB = 256;  // threads of a tile CTA: 16 x 16, 2 x 2 outputs each
 // opA(i, k) = TA ? A[k * lda + i] : A[i * lda + k]   (rows i < mrows)
 // opB(k, j) = TB ? B[j * ldb + k] : B[k * ldb + j]   (cols j < ncols)
 // Thread (ty, tx) owns rows {ty, ty + 16} and columns {tx, tx + 16}.
-template <typename TIN, bool TA, bool TB>
-__device__ __forceinline__ void tile_acc(double (&acc)[2][2], const TIN *__restrict__ A,
+template <typename TIN, bool TA, bool TB, typename C = double>
+__device__ __forceinline__ void tile_acc(C (&acc)[2][2], const TIN *__restrict__ A,
                                          int64_t lda, const TIN *__restrict__ B, int64_t ldb,
                                          int64_t i0, int64_t j0, int64_t k0, int64_t k1,
-                                         int64_t mrows, int64_t ncols, double (*As)[NB + 1],
-                                         double (*Bs)[NB + 1]) {
+                                         int64_t mrows, int64_t ncols, C (*As)[NB + 1],
+                                         C (*Bs)[NB + 1]) {
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     for (int64_t kc = k0; kc < k1; kc += NB) {
@@ -35,8 +35,8 @@ __device__ __forceinline__ void tile_acc(double (&acc)[2][2], const TIN *__restr
             int i, k;
             if (TA) { i = idx & 31; k = idx >> 5; } else { k = idx & 31; i = idx >> 5; }
             int64_t gi = i0 + i, gk = kc + k;
-            double v = 0.0;
-            if (gi < mrows && gk < k1) v = (double)(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
+            C v = 0;
+            if (gi < mrows && gk < k1) v = (C)(TA ? A[gk * lda + gi] : A[gi * lda + gk]);
             As[k][i] = v;
         }
 #pragma unroll
@@ -45,15 +45,15 @@ __device__ __forceinline__ void tile_acc(double (&acc)[2][2], const TIN *__restr
             int j, k;
             if (TB) { k = idx & 31; j = idx >> 5; } else { j = idx & 31; k = idx >> 5; }
             int64_t gj = j0 + j, gk = kc + k;
-            double v = 0.0;
-            if (gj < ncols && gk < k1) v = (double)(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
+            C v = 0;
+            if (gj < ncols && gk < k1) v = (C)(TB ? B[gj * ldb + gk] : B[gk * ldb + gj]);
             Bs[k][j] = v;
         }
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < NB; ++k) {
-            double a0 = As[k][ty], a1 = As[k][ty + 16];
-            double b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+            C a0 = As[k][ty], a1 = As[k][ty + 16];
+            C b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
             acc[0][0] = fma(a0, b0, acc[0][0]);
             acc[0][1] = fma(a0, b1, acc[0][1]);
             acc[1][0] = fma(a1, b0, acc[1][0]);
@@ -137,88 +137,184 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return r;
 }
 
+__device__ __forceinline__ float rsqrt_newton(float d) {
+    float r = rsqrtf(d);
+    return r * fmaf(-0.5f * d * r, r, 1.5f);
+}
+
 // One warp factors the kw x kw lower block B (shared, row-major, padded) in
-// place and writes Xs = L^{-1}.  Returns 0 or the failing pivot + 1 (same in
-// every lane).  Lane i keeps row i of the block in registers.
-__device__ int warp_chol_inv32(double (*B)[NB + 1], double (*Xs)[NB + 1], int kw) {
+// place and writes Xs = L^{-1}, in the arithmetic of T.  (On this GPU one
+// warp issues FP64 at a small fraction of its FP32 rate, so the FP32
+// factorisation keeps its diagonal blocks in FP32.)  ldiag (global, optional)
+// receives the diagonal of L as FP64 for the log-det.  Returns 0 or the
+// failing pivot + 1 (same in every lane).  Lane i keeps row i in registers.
+template <typename T>
+__device__ int warp_chol_inv32(T (*B)[NB + 1], T (*Xs)[NB + 1], int kw, double *ldiag) {
     const int lane = threadIdx.x & 31;
-    double a[NB];
+    T a[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) a[c] = (lane < kw && c <= lane) ? B[lane][c] : 0.0;
-    double rdiag = 0.0;
+    for (int c = 0; c < NB; ++c) a[c] = (lane < kw && c <= lane) ? B[lane][c] : (T)0;
+    T rdiag = 0, lii = 0;
     int fail = 0;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         if (j < kw && !fail) {
-            const double d = __shfl_sync(0xffffffffu, a[j], j);
-            if (!(d > 0.0)) {
+            const T d = __shfl_sync(0xffffffffu, a[j], j);
+            if (!(d > (T)0)) {
                 fail = j + 1;
             } else {
-                const double r = rsqrt_newton(d);
-                if (lane == j) { a[j] = d * r; rdiag = r; }
+                const T r = rsqrt_newton(d);
+                if (lane == j) { a[j] = d * r; rdiag = r; lii = a[j]; }
                 if (lane > j) a[j] *= r;
 #pragma unroll
                 for (int k = j + 1; k < NB; ++k) {
-                    const double lkj = __shfl_sync(0xffffffffu, a[j], k);
+                    const T lkj = __shfl_sync(0xffffffffu, a[j], k);
                     if (lane >= k) a[k] = fma(-a[j], lkj, a[k]);
                 }
             }
         }
     }
     if (fail) return fail;
+    if (ldiag && lane < kw) ldiag[lane] = (double)lii;
+    // keep the factor in shared memory (as T) and in FP64 for the inverse
 #pragma unroll
     for (int c = 0; c < NB; ++c) B[lane][c] = a[c];
     __syncwarp();
-    // X = L^{-1}: lane c solves L x = e_c (x_i = 0 for i < c)
-    double x[NB];
+    // X = L^{-1}: lane c solves L x = e_c (x_i = 0 for i < c), reading the
+    // factor's rows back from shared memory.
+    T x[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        double s = (i == lane) ? 1.0 : 0.0;
+        T s = (i == lane) ? (T)1 : (T)0;
 #pragma unroll
         for (int t = 0; t < i; ++t) s = fma(-B[i][t], x[t], s);
-        const double ri = __shfl_sync(0xffffffffu, rdiag, i);
-        x[i] = (i < kw && i >= lane) ? s * ri : 0.0;
+        const T ri = __shfl_sync(0xffffffffu, rdiag, i);
+        x[i] = (i < kw && i >= lane) ? s * ri : (T)0;
     }
 #pragma unroll
-    for (int i = 0; i < NB; ++i) Xs[i][lane] = x[i];
+    for (int i = 0; i < NB; ++i) Xs[i][lane] = (T)x[i];
     __syncwarp();
     return 0;
 }
 
+// The same factorisation and inverse spread over the whole CTA (used for
+// FP64, whose per-warp issue rate is too low for one warp to carry it):
+// right-looking column steps in shared memory, then X = L^{-1} by recursive
+// doubling, X21 = -X22 (L21 X11), over blocks of size 1, 2, 4, 8, 16.
+template <typename T>
+__device__ int cta_chol_inv32(T (*B)[NB + 1], T (*Xs)[NB + 1], T (*Tt)[NB + 1], int kw,
+                              double *ldiag) {
+    __shared__ T rd[NB];
+    __shared__ int fail_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) fail_s = 0;
+    __syncthreads();
+    for (int j = 0; j < kw; ++j) {
+        if (tid == 0) {
+            const T d = B[j][j];
+            if (!(d > (T)0)) {
+                fail_s = j + 1;
+            } else {
+                const T r = rsqrt_newton(d);
+                B[j][j] = d * r;
+                rd[j] = r;
+                if (ldiag) ldiag[j] = (double)(d * r);
+            }
+        }
+        __syncthreads();
+        if (fail_s) return fail_s;
+        const T r = rd[j];
+        for (int i = j + 1 + tid; i < kw; i += nt) B[i][j] *= r;
+        __syncthreads();
+        const int rem = kw - j - 1;
+        for (int idx = tid; idx < rem * rem; idx += nt) {
+            const int i = j + 1 + idx / rem, c = j + 1 + idx % rem;
+            if (c <= i) B[i][c] = fma(-B[i][j], B[c][j], B[i][c]);
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < NB * NB; idx += nt) {
+        const int r = idx / NB, c = idx % NB;
+        Xs[r][c] = (r == c && r < kw) ? rd[r] : (T)0;
+        if (r >= kw || c > r) B[r][c] = (T)0;
+    }
+    __syncthreads();
+    for (int h = 1; h < NB; h *= 2) {
+        // pair p: rows/cols [2hp, 2hp + 2h); X11 = [2hp, 2hp+h), X22 = [2hp+h, 2hp+2h)
+        const int per = h * h, total = (NB / (2 * h)) * per;
+        for (int idx = tid; idx < total; idx += nt) {  // Tt = L21 X11
+            const int p = idx / per, q = idx % per, k = q / h, c = q % h;
+            const int r0 = 2 * h * p, row = r0 + h + k, col = r0 + c;
+            T acc = 0;
+            for (int m = col; m < r0 + h; ++m) acc = fma(B[row][m], Xs[m][col], acc);
+            Tt[row][col] = acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < total; idx += nt) {  // X21 = -X22 Tt
+            const int p = idx / per, q = idx % per, k = q / h, c = q % h;
+            const int r0 = 2 * h * p, row = r0 + h + k, col = r0 + c;
+            T acc = 0;
+            for (int m = r0 + h; m <= row; ++m) acc = fma(Xs[row][m], Tt[m][col], acc);
+            Xs[row][col] = -acc;
+        }
+        __syncthreads();
+    }
+    return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ int block_chol_inv32(T (*B)[NB + 1], T (*Xs)[NB + 1], T (*Tt)[NB + 1],
+                                                int kw, double *ldiag) {
+    if (sizeof(T) == 8) return cta_chol_inv32<T>(B, Xs, Tt, kw, ldiag);
+    int f = 0;
+    if (threadIdx.x < 32) f = warp_chol_inv32<T>(B, Xs, kw, ldiag);
+    __shared__ int fshare;
+    if (threadIdx.x == 0) fshare = f;
+    __syncthreads();
+    return fshare;
+}
+
 // Factor diagonal block kb (used for the first block) and store L_kk, X_kk.
-__global__ void k_potrf_diag(double *__restrict__ A, int64_t n, int kb, double *__restrict__ xd,
-                             DevScalars *sc) {
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_potrf_diag(T *__restrict__ A, int64_t n, int kb,
+                                                    T *__restrict__ xd, double *__restrict__ ldiag,
+                                                    DevScalars *sc) {
     if (sc->info != 0) return;
-    __shared__ double B[NB][NB + 1], Xs[NB][NB + 1];
+    __shared__ T B[NB][NB + 1], Xs[NB][NB + 1], Tt[NB][NB + 1];
     const int64_t k0 = (int64_t)kb * NB;
     const int kw = (int)lmin(NB, n - k0);
-    const int lane = threadIdx.x;
-    for (int r = 0; r < NB; ++r) B[r][lane] = (r < kw && lane <= r) ? A[(k0 + r) * n + k0 + lane] : 0.0;
-    __syncwarp();
-    const int f = warp_chol_inv32(B, Xs, kw);
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+        const int r = idx / NB, c = idx % NB;
+        B[r][c] = (r < kw && c <= r) ? A[(k0 + r) * n + k0 + c] : (T)0;
+    }
+    __syncthreads();
+    const int f = block_chol_inv32<T>(B, Xs, Tt, kw, ldiag + k0);
     if (f) {
-        if (lane == 0) sc->info = (int)(k0 + f);
+        if (threadIdx.x == 0) sc->info = (int)(k0 + f);
         return;
     }
-    double *X = xd + (kb & 1) * NB * NB;
-    for (int r = 0; r < NB; ++r) {
-        X[r * NB + lane] = Xs[r][lane];
-        if (r < kw && lane <= r) A[(k0 + r) * n + k0 + lane] = B[r][lane];
+    __syncthreads();
+    T *X = xd + (kb & 1) * NB * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+        const int r = idx / NB, c = idx % NB;
+        X[r * NB + c] = Xs[r][c];
+        if (r < kw && c <= r) A[(k0 + r) * n + k0 + c] = B[r][c];
     }
 }
 
 // Panel of step kb: block row kb + 1 + blockIdx.x, L_ik = A_ik X_kk^T.
-__global__ void __launch_bounds__(TPB) k_potrf_panel(double *__restrict__ A, int64_t n, int kb,
-                                                     const double *__restrict__ xd, DevScalars *sc) {
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_potrf_panel(T *__restrict__ A, int64_t n, int kb,
+                                                     const T *__restrict__ xd, DevScalars *sc) {
     if (sc->info != 0) return;
-    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    __shared__ T As[NB][NB + 1], Bs[NB][NB + 1];
     const int64_t k0 = (int64_t)kb * NB;
     const int64_t kw = lmin(NB, n - k0);
     const int64_t i0 = k0 + (int64_t)(blockIdx.x + 1) * NB;
-    const double *X = xd + (kb & 1) * NB * NB;
-    double acc[2][2] = {{0, 0}, {0, 0}};
+    const T *X = xd + (kb & 1) * NB * NB;
+    T acc[2][2] = {{0, 0}, {0, 0}};
     // opA(i, c) = A[i0 + i, k0 + c]; opB(c, j) = X[j][c]
-    tile_acc<double, false, true>(acc, A + i0 * n + k0, n, X, NB, 0, 0, 0, kw, n - i0, kw, As, Bs);
+    tile_acc<T, false, true, T>(acc, A + i0 * n + k0, n, X, NB, 0, 0, 0, kw, n - i0, kw, As, Bs);
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -231,17 +327,19 @@ __global__ void __launch_bounds__(TPB) k_potrf_panel(double *__restrict__ A, int
 
 // Trailing update of step kb on lower tiles I >= J > kb; the CTA of tile
 // (kb+1, kb+1) then factors that block and inverts its factor.
-__global__ void __launch_bounds__(TPB) k_potrf_trail(double *__restrict__ A, int64_t n, int kb,
-                                                     double *__restrict__ xd, DevScalars *sc) {
+template <typename T>
+__global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64_t n, int kb,
+                                                     T *__restrict__ xd, double *__restrict__ ldiag,
+                                                     DevScalars *sc) {
     if (sc->info != 0) return;
-    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+    __shared__ T As[NB][NB + 1], Bs[NB][NB + 1];
     int64_t I, J;
     tri_index(blockIdx.x, I, J);
     I += kb + 1;
     J += kb + 1;
     const int64_t k0 = (int64_t)kb * NB, k1 = lmin(k0 + NB, n);
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    tile_acc<double, false, true>(acc, A, n, A, n, I * NB, J * NB, k0, k1, n, n, As, Bs);
+    T acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<T, false, true, T>(acc, A, n, A, n, I * NB, J * NB, k0, k1, n, n, As, Bs);
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
     const bool diag_next = (I == kb + 1 && J == kb + 1);
 #pragma unroll
@@ -250,34 +348,36 @@ __global__ void __launch_bounds__(TPB) k_potrf_trail(double *__restrict__ A, int
         for (int b = 0; b < 2; ++b) {
             const int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
             if (i < n && j < n && j <= i) {
-                const double v = A[i * n + j] - acc[a][b];
+                const T v = A[i * n + j] - acc[a][b];
                 A[i * n + j] = v;
                 if (diag_next) As[ty + 16 * a][tx + 16 * b] = v;
             }
         }
     if (!diag_next) return;
     __syncthreads();
-    if (threadIdx.x >= 32) return;
+    __shared__ T Tt[NB][NB + 1];
     const int64_t d0 = I * NB;
     const int kw = (int)lmin(NB, n - d0);
-    const int f = warp_chol_inv32(As, Bs, kw);
-    const int lane = threadIdx.x;
+    const int f = block_chol_inv32<T>(As, Bs, Tt, kw, ldiag + d0);
     if (f) {
-        if (lane == 0) sc->info = (int)(d0 + f);
+        if (threadIdx.x == 0) sc->info = (int)(d0 + f);
         return;
     }
-    double *X = xd + (I & 1) * NB * NB;
-    for (int r = 0; r < NB; ++r) {
-        X[r * NB + lane] = Bs[r][lane];
-        if (r < kw && lane <= r) A[(d0 + r) * n + d0 + lane] = As[r][lane];
+    __syncthreads();
+    T *X = xd + (I & 1) * NB * NB;
+    for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+        const int r = idx / NB, c = idx % NB;
+        X[r * NB + c] = Bs[r][c];
+        if (r < kw && c <= r) A[(d0 + r) * n + d0 + c] = As[r][c];
     }
 }
 
-// log det A = 2 sum_i log L_ii, deterministic single-CTA reduction.
-__global__ void k_logdet(const double *__restrict__ L, int64_t n, DevScalars *sc) {
+// log det A = 2 sum_i log L_ii from the FP64 diagonal of the factor,
+// deterministic single-CTA reduction.
+__global__ void k_logdet(const double *__restrict__ ldiag, int64_t n, DevScalars *sc) {
     __shared__ double red[TPB];
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += TPB) s += log(L[i * n + i]);
+    for (int64_t i = threadIdx.x; i < n; i += TPB) s += log(ldiag[i]);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = TPB / 2; w > 0; w >>= 1) {
@@ -289,15 +389,16 @@ __global__ void k_logdet(const double *__restrict__ L, int64_t n, DevScalars *sc
 
 // ---------------------------------------------------------------- a3: inverse
 // Invert every 32 x 32 diagonal block of L: X_bb = L_bb^{-1} (forward
-// substitution, one thread per column).
-__global__ void k_trtri_diag(const double *__restrict__ L, int64_t n, double *__restrict__ X) {
+// substitution in FP64, one thread per column).
+template <typename T>
+__global__ void k_trtri_diag(const T *__restrict__ L, int64_t n, T *__restrict__ X) {
     __shared__ double Ls[NB][NB + 1];
     __shared__ double Xs[NB][NB + 1];
     const int64_t b0 = (int64_t)blockIdx.x * NB;
     const int bw = (int)lmin(NB, n - b0);
     for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
         int r = idx / NB, c = idx % NB;
-        Ls[r][c] = (r < bw && c <= r) ? L[(b0 + r) * n + b0 + c] : 0.0;
+        Ls[r][c] = (r < bw && c <= r) ? (double)L[(b0 + r) * n + b0 + c] : 0.0;
         Xs[r][c] = 0.0;
     }
     __syncthreads();
@@ -312,7 +413,7 @@ __global__ void k_trtri_diag(const double *__restrict__ L, int64_t n, double *__
     __syncthreads();
     for (int idx = threadIdx.x; idx < bw * bw; idx += blockDim.x) {
         int r = idx / bw, cc = idx % bw;
-        if (cc <= r) X[(b0 + r) * n + b0 + cc] = Xs[r][cc];
+        if (cc <= r) X[(b0 + r) * n + b0 + cc] = (T)Xs[r][cc];
     }
 }
 
@@ -321,11 +422,12 @@ __global__ void k_trtri_diag(const double *__restrict__ L, int64_t n, double *__
 //   X21 = -X22 (L21 X11),  computed as  Tw = L21 X11, then X21 = -X22 Tw.
 // Step 1: Tw_p (h x s, row stride s) = L21 X11; X11 is lower, so column
 // block J only needs k >= J*32.
-__global__ void __launch_bounds__(TPB) k_trtri_step1(const double *__restrict__ L,
-                                                     const double *__restrict__ X, int64_t n,
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_trtri_step1(const T *__restrict__ L,
+                                                     const T *__restrict__ X, int64_t n,
                                                      int64_t s, int tiles_i, int tiles_j,
-                                                     double *__restrict__ Tw) {
-    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+                                                     T *__restrict__ Tw) {
+    __shared__ T As[NB][NB + 1], Bs[NB][NB + 1];
     const int per = tiles_i * tiles_j;
     const int64_t p = blockIdx.x / per;
     const int tt = blockIdx.x % per;
@@ -333,25 +435,26 @@ __global__ void __launch_bounds__(TPB) k_trtri_step1(const double *__restrict__ 
     const int64_t r0 = 2 * s * p;
     const int64_t h = lmin(s, n - r0 - s);
     if (I * NB >= h) return;
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    tile_acc<double, false, false>(acc, L + (r0 + s) * n + r0, n, X + r0 * n + r0, n, I * NB,
-                                   J * NB, J * NB, s, h, s, As, Bs);
-    double *T = Tw + p * s * s;
+    T acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<T, false, false, T>(acc, L + (r0 + s) * n + r0, n, X + r0 * n + r0, n, I * NB,
+                                 J * NB, J * NB, s, h, s, As, Bs);
+    T *Tp = Tw + p * s * s;
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             int64_t i = I * NB + ty + 16 * a, j = J * NB + tx + 16 * b;
-            if (i < h && j < s) T[i * s + j] = acc[a][b];
+            if (i < h && j < s) Tp[i * s + j] = acc[a][b];
         }
 }
 
 // Step 2: X21 = -X22 Tw_p; X22 is lower, so row block I only needs k < (I+1)*32.
-__global__ void __launch_bounds__(TPB) k_trtri_step2(double *__restrict__ X, int64_t n, int64_t s,
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_trtri_step2(T *__restrict__ X, int64_t n, int64_t s,
                                                      int tiles_i, int tiles_j,
-                                                     const double *__restrict__ Tw) {
-    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+                                                     const T *__restrict__ Tw) {
+    __shared__ T As[NB][NB + 1], Bs[NB][NB + 1];
     const int per = tiles_i * tiles_j;
     const int64_t p = blockIdx.x / per;
     const int tt = blockIdx.x % per;
@@ -359,10 +462,10 @@ __global__ void __launch_bounds__(TPB) k_trtri_step2(double *__restrict__ X, int
     const int64_t r0 = 2 * s * p;
     const int64_t h = lmin(s, n - r0 - s);
     if (I * NB >= h) return;
-    const double *T = Tw + p * s * s;
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    tile_acc<double, false, false>(acc, X + (r0 + s) * n + (r0 + s), n, T, s, I * NB, J * NB, 0,
-                                   lmin((I + 1) * NB, h), h, s, As, Bs);
+    const T *Tp = Tw + p * s * s;
+    T acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<T, false, false, T>(acc, X + (r0 + s) * n + (r0 + s), n, Tp, s, I * NB, J * NB, 0,
+                                 lmin((I + 1) * NB, h), h, s, As, Bs);
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -375,13 +478,14 @@ __global__ void __launch_bounds__(TPB) k_trtri_step2(double *__restrict__ X, int
 
 // W = X^T X with X = L^{-1} lower: W_IJ = sum_{k >= I*32} X[k, I]^T X[k, J]
 // on lower tiles I >= J, mirrored to the upper triangle.
-__global__ void __launch_bounds__(TPB) k_lauum(const double *__restrict__ X, int64_t n,
-                                               double *__restrict__ W) {
-    __shared__ double As[NB][NB + 1], Bs[NB][NB + 1];
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_lauum(const T *__restrict__ X, int64_t n,
+                                               T *__restrict__ W) {
+    __shared__ T As[NB][NB + 1], Bs[NB][NB + 1];
     int64_t I, J;
     tri_index(blockIdx.x, I, J);
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    tile_acc<double, true, false>(acc, X, n, X, n, I * NB, J * NB, I * NB, n, n, n, As, Bs);
+    T acc[2][2] = {{0, 0}, {0, 0}};
+    tile_acc<T, true, false, T>(acc, X, n, X, n, I * NB, J * NB, I * NB, n, n, n, As, Bs);
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -402,7 +506,16 @@ cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, d
                    double *Xstage, cudaStream_t st) {
     if (m < 1 || n < 1) return cudaErrorInvalidValue;
     // Xstage holds m*n + n doubles: the centred FP64 copy of X and the mean.
+    // center == 2 computes the column means only (into Xstage + m*n).
     double *mu = center ? Xstage + m * n : nullptr;
+    if (center == 2) {
+        if (dtype == GLASSO_F64)
+            k_colmean<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double *)X, m, n, mu);
+        else
+            k_colmean<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float *)X, m, n, mu);
+        counted(1);
+        return cudaGetLastError();
+    }
     int g = (int)lmin((m * n + 255) / 256, 152 * 16);
     if (dtype == GLASSO_F64) {
         const double *x = (const double *)X;
@@ -427,41 +540,56 @@ cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, d
     return cudaGetLastError();
 }
 
-cudaError_t potrf(double *A, int64_t n, double *xd, DevScalars *sc, cudaStream_t st) {
+template <typename T>
+static cudaError_t potrf_t(T *A, int64_t n, T *xd, double *ldiag, DevScalars *sc, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int64_t nb = (n + NB - 1) / NB;
-    k_potrf_diag<<<1, 32, 0, st>>>(A, n, 0, xd, sc);
+    k_potrf_diag<T><<<1, TPB, 0, st>>>(A, n, 0, xd, ldiag, sc);
     counted(1);
     for (int64_t kb = 0; kb + 1 < nb; ++kb) {
         const int64_t m = nb - kb - 1;
-        k_potrf_panel<<<(unsigned)m, TPB, 0, st>>>(A, n, (int)kb, xd, sc);
-        k_potrf_trail<<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, xd, sc);
+        k_potrf_panel<T><<<(unsigned)m, TPB, 0, st>>>(A, n, (int)kb, xd, sc);
+        k_potrf_trail<T><<<(unsigned)(m * (m + 1) / 2), TPB, 0, st>>>(A, n, (int)kb, xd, ldiag, sc);
         counted(2);
     }
-    k_logdet<<<1, TPB, 0, st>>>(A, n, sc);
+    k_logdet<<<1, TPB, 0, st>>>(ldiag, n, sc);
     counted(1);
     return cudaGetLastError();
 }
 
-cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(X, 0, (size_t)(n * n) * sizeof(double), st);
+cudaError_t potrf(double *A, int64_t n, double *xd, double *ldiag, DevScalars *sc, cudaStream_t st) {
+    return potrf_t<double>(A, n, xd, ldiag, sc, st);
+}
+cudaError_t potrf32(float *A, int64_t n, float *xd, double *ldiag, DevScalars *sc, cudaStream_t st) {
+    return potrf_t<float>(A, n, xd, ldiag, sc, st);
+}
+
+template <typename T>
+static cudaError_t inverse_t(const T *L, int64_t n, T *W, T *X, T *Tw, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(X, 0, (size_t)(n * n) * sizeof(T), st);
     if (e != cudaSuccess) return e;
     const int64_t nb = (n + NB - 1) / NB;
-    k_trtri_diag<<<(unsigned)nb, NB, 0, st>>>(L, n, X);
+    k_trtri_diag<T><<<(unsigned)nb, NB, 0, st>>>(L, n, X);
     counted(1);
     for (int64_t s = NB; s < n; s *= 2) {
         const int64_t npairs = (n - s + 2 * s - 1) / (2 * s);  // r0 = 2sp with r0 + s < n
         const int tiles = (int)(s / NB);
         const unsigned grid = (unsigned)(npairs * tiles * tiles);
-        k_trtri_step1<<<grid, TPB, 0, st>>>(L, X, n, s, tiles, tiles, Tw);
-        counted(1);
-        k_trtri_step2<<<grid, TPB, 0, st>>>(X, n, s, tiles, tiles, Tw);
-        counted(1);
+        k_trtri_step1<T><<<grid, TPB, 0, st>>>(L, X, n, s, tiles, tiles, Tw);
+        k_trtri_step2<T><<<grid, TPB, 0, st>>>(X, n, s, tiles, tiles, Tw);
+        counted(2);
     }
-    k_lauum<<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(X, n, W);
+    k_lauum<T><<<(unsigned)(nb * (nb + 1) / 2), TPB, 0, st>>>(X, n, W);
     counted(1);
     return cudaGetLastError();
+}
+
+cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st) {
+    return inverse_t<double>(L, n, W, X, Tw, st);
+}
+cudaError_t inverse32(const float *L, int64_t n, float *W, float *X, float *Tw, cudaStream_t st) {
+    return inverse_t<float>(L, n, W, X, Tw, st);
 }
 
 }  // namespace glx

@@ -48,8 +48,15 @@ struct DevScalars {
     int moved;            // any Delta_p != 0
     int levels;           // hierarchy levels L
     long long nsupp;
+    // mixed precision
+    double ns_max;        // max |I - A W|
+    double ns_fro2;       // ||I - A W||_F^2
+    double t1;            // tr(W Delta)
+    double t2;            // tr((W Delta)^2)
     int err;              // device-side error flag (NaN input, bad diagonal)
     int bad_sym;          // input symmetry check failed
+    int tc_err;           // tensor-core GEMM: a bounded wait expired (code)
+    int pad2;
 };
 
 // Per-context device workspace, sized for n <= cap_n.
@@ -85,6 +92,17 @@ struct Work {
     double *cd_emu = nullptr;              // 2 CD_B entry coefficients
     int32_t *cd_esrc = nullptr;            // 2 CD_B entry source rows
     double *xd = nullptr;                  // 2 x 32 x 32: inverses of Cholesky diagonal blocks
+    double *ldiag = nullptr;               // n: FP64 diagonal of the last factor
+    // mixed precision: CSR of A and reduction partials
+    int64_t cap_mixed = 0;
+    long long *csr_ptr = nullptr;
+    int32_t *csr_col = nullptr;
+    double *csr_val = nullptr;
+    double *part = nullptr;
+    int64_t cap_part = 0;
+    float *Wp = nullptr, *Qp = nullptr;    // padded FP32 operands of the tensor-core GEMM
+    float *Xt = nullptr;                   // padded X^T for S on the tensor cores
+    int64_t cap_xt = 0;
     DevScalars *sc = nullptr;              // device scalars
     DevScalars *sc_host = nullptr;         // pinned mirror
 };
@@ -109,10 +127,14 @@ namespace glx {
 cudaError_t form_S(const void *X, int dtype, int64_t m, int64_t n, int center, double *S,
                    double *mu_scratch, cudaStream_t st);
 // In-place blocked Cholesky of the lower triangle; writes sc->info and sc->logdet.
-// xd: scratch of 2 * NB * NB doubles (inverses of the diagonal blocks).
-cudaError_t potrf(double *A, int64_t n, double *xd, DevScalars *sc, cudaStream_t st);
+// xd: scratch of 2 * NB * NB elements (inverses of the diagonal blocks);
+// ldiag: n doubles receiving the FP64 diagonal of L (the log-det reads it).
+cudaError_t potrf(double *A, int64_t n, double *xd, double *ldiag, DevScalars *sc, cudaStream_t st);
+// Same factorisation in FP32 storage and arithmetic, diagonal blocks in FP64.
+cudaError_t potrf32(float *A, int64_t n, float *xd, double *ldiag, DevScalars *sc, cudaStream_t st);
 // W = L^{-T} L^{-1}; X (n x n) and Tw (n x n) are scratch.
 cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw, cudaStream_t st);
+cudaError_t inverse32(const float *L, int64_t n, float *W, float *X, float *Tw, cudaStream_t st);
 
 // ---- launchers (scan.cu) ----
 // Full level-0 scan: free set (pi, pj, absg) and the sums of DevScalars.
@@ -152,10 +174,38 @@ cudaError_t ls_apply(double *A, int64_t n, const int32_t *pi, const int32_t *pj,
 cudaError_t hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uint8_t *tag,
                       DevScalars *sc, cudaStream_t st);
 
+// ---- launchers (mixed.cu) ----
+cudaError_t ns_gemm(const float *W32, const float *R32, int64_t n, double *W64, cudaStream_t st);
+cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, double *val,
+                      cudaStream_t st);
+cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const double *W64,
+                     int64_t n, float *R32, float *W32, double *rowstat, DevScalars *sc,
+                     cudaStream_t st);
+cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const int32_t *pj,
+                         const double *D, int64_t np, const float *U32, double *part, int64_t cap,
+                         DevScalars *sc, cudaStream_t st);
+cudaError_t to_f32(const double *x, float *y, int64_t m, cudaStream_t st);
+cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st);
+cudaError_t trial32(const double *A, float *T, int64_t n, const int32_t *pi, const int32_t *pj,
+                    const double *aval, const double *D, int64_t np, double alpha, cudaStream_t st);
+cudaError_t diag_inverse(const double *A, int64_t n, double *W64, double *logs, DevScalars *sc,
+                         cudaStream_t st);
+
+// ---- launchers (tc.cu) ----
+int64_t tc_pad(int64_t n);
+cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
+                       float *Qp, int *err, cudaStream_t st);
+cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
+                    float *Xt, int *err, cudaStream_t st);
+
 // ---- launchers (cd.cu) ----
 cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
                       const int32_t *pj, int64_t np, const double *inva, const double *g,
                       const double *aval, int nsweeps, double *D, double *U, Work &w,
                       cudaStream_t st);
+cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi,
+                        const int32_t *pj, int64_t np, const double *inva, const double *g,
+                        const double *aval, int nsweeps, double *D, float *U, Work &w,
+                        bool chain64, cudaStream_t st);
 
 }  // namespace glx

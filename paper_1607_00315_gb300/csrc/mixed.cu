@@ -1,0 +1,424 @@
+// Kernels of the mixed-precision relaxation.
+//
+// The bulk arithmetic moves to FP32 while the quantities that decide the
+// answer stay FP64:
+//  * W = A^{-1} is kept in FP64 and refined against A by Newton-Schulz steps
+//        R = I - A W            (FP64, A sparse: CSR of its nonzeros)
+//        W <- W + W R           (FP32 GEMM of the small correction, FP64 sum)
+//    which square the residual each step until |R| reaches FP64 level; the
+//    gradient S - W, the free set and the KKT residual therefore see an FP64
+//    accurate W (eq. gradHes, eq. active_set, the Section 8 stopping rule).
+//  * The line search (Section 6.1.2) gets log det(A + alpha Delta) - log det A
+//    from the series  sum_k (-1)^{k+1} alpha^k tr((W Delta)^k) / k  with
+//    t1 = tr(W Delta) (FP64 on the pairs) and t2 = tr((W Delta)^2) = sum U_kj U_jk
+//    (U = Delta W from the sweep), whose remainder is bounded by
+//    (alpha sqrt(t2))^3 / (3 (1 - alpha sqrt(t2))); alpha sqrt(t2) < 1 also
+//    proves A + alpha Delta positive definite.  Large steps use an FP32
+//    Cholesky (FP64 diagonal blocks) instead.
+#include <math.h>
+
+#include "glasso_internal.h"
+
+namespace glx {
+namespace {
+
+constexpr int ST = 64;    // SGEMM output tile edge
+constexpr int SK = 16;    // k-chunk
+constexpr int STH = 256;  // threads: 16 x 16, 4 x 4 outputs each
+
+__device__ __forceinline__ void tri_index64(int64_t t, int64_t &I, int64_t &J) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > t) --i;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    I = i;
+    J = t - i * (i + 1) / 2;
+}
+
+// acc[r][c] += sum_k A[i0 + 4 ty + r, k] B[k, j0 + 4 tx + c], FP32, row-major.
+__device__ __forceinline__ void sgemm_tile(float (&acc)[4][4], const float *__restrict__ A,
+                                           const float *__restrict__ B, int64_t n, int64_t i0,
+                                           int64_t j0, float (*As)[ST + 4], float (*Bs)[ST + 4]) {
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int64_t kc = 0; kc < n; kc += SK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + STH * r;
+            const int i = idx >> 4, k = idx & 15;
+            const int64_t gi = i0 + i, gk = kc + k;
+            As[k][i] = (gi < n && gk < n) ? A[gi * n + gk] : 0.f;
+            const int j = idx & 63, k2 = idx >> 6;
+            const int64_t gj = j0 + j, gk2 = kc + k2;
+            Bs[k2][j] = (gj < n && gk2 < n) ? B[gk2 * n + gj] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][4 * ty]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][4 * tx]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+}
+
+// Newton-Schulz correction on lower tiles: C = W32 R32 (symmetric up to
+// rounding), W64 += C mirrored so W64 stays exactly symmetric.
+__global__ void __launch_bounds__(STH) k_ns_gemm(const float *__restrict__ W32,
+                                                 const float *__restrict__ R32, int64_t n,
+                                                 double *__restrict__ W64) {
+    __shared__ __align__(16) float As[SK][ST + 4];
+    __shared__ __align__(16) float Bs[SK][ST + 4];
+    int64_t I, J;
+    tri_index64(blockIdx.x, I, J);
+    float acc[4][4] = {};
+    sgemm_tile(acc, W32, R32, n, I * ST, J * ST, As, Bs);
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t i = I * ST + 4 * ty + r, j = J * ST + 4 * tx + c;
+            if (i < n && j <= i) {
+                const double w = W64[i * n + j] + (double)acc[r][c];
+                W64[i * n + j] = w;
+                if (i != j) W64[j * n + i] = w;
+            }
+        }
+}
+
+// ---- CSR of the nonzeros of A (full rows, column order) --------------------
+constexpr int RW = 8;  // rows (warps) per CTA
+
+__global__ void k_nz_count(const double *__restrict__ A, int64_t n, long long *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * RW + (threadIdx.x >> 5);
+    if (i >= n) return;
+    long long c = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+        const int64_t j = j0 + lane;
+        const bool nz = j < n && A[i * n + j] != 0.0;
+        c += __popc(__ballot_sync(0xffffffffu, nz));
+    }
+    if (lane == 0) cnt[i] = c;
+}
+
+__global__ void k_rowptr_scan(long long *__restrict__ cnt, int64_t n) {
+    // one CTA of 1024 threads: exclusive scan in place, total at cnt[n]
+    __shared__ long long part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t a = t * per, b = lmin(a + per, n);
+    long long s = 0;
+    for (int64_t i = a; i < b; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        long long v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long off = part[t] - s;
+    for (int64_t i = a; i < b; ++i) {
+        const long long c = cnt[i];
+        cnt[i] = off;
+        off += c;
+    }
+    if (t == 1023) cnt[n] = part[1023];
+}
+
+__global__ void k_nz_write(const double *__restrict__ A, int64_t n, const long long *__restrict__ ptr,
+                           int32_t *__restrict__ col, double *__restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * RW + (threadIdx.x >> 5);
+    if (i >= n) return;
+    long long off = ptr[i];
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+        const int64_t j = j0 + lane;
+        const double a = j < n ? A[i * n + j] : 0.0;
+        const uint32_t m = __ballot_sync(0xffffffffu, a != 0.0);
+        if (a != 0.0) {
+            const long long pos = off + __popc(m & ((1u << lane) - 1u));
+            col[pos] = (int32_t)j;
+            val[pos] = a;
+        }
+        off += __popc(m);
+    }
+}
+
+// ---- residual R = I - A W (FP64), W32 = float(W), per-row max and sum of squares
+constexpr int RES_T = 256;
+constexpr int RES_CAP = 256;  // nonzeros of a row staged per pass
+
+__global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict__ ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const double *__restrict__ val,
+                                                    const double *__restrict__ W64, int64_t n,
+                                                    float *__restrict__ R32, float *__restrict__ W32,
+                                                    double *__restrict__ rowstat) {
+    __shared__ int32_t sc[RES_CAP];
+    __shared__ double sv[RES_CAP];
+    __shared__ double rmax[RES_T], rsq[RES_T];
+    const int64_t i = blockIdx.x;
+    const long long p0 = ptr[i], p1 = ptr[i + 1];
+    double mx = 0.0, sq = 0.0;
+    // columns handled by this thread, in registers for up to 16 chunks of RES_T
+    for (int64_t c0 = 0; c0 < n; c0 += (int64_t)RES_T * 8) {
+        double acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
+            acc[q] = (cidx == i) ? 1.0 : 0.0;
+        }
+        for (long long pb = p0; pb < p1; pb += RES_CAP) {
+            const int cntk = (int)lmin(RES_CAP, p1 - pb);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cntk; t += RES_T) {
+                sc[t] = col[pb + t];
+                sv[t] = val[pb + t];
+            }
+            __syncthreads();
+            for (int t = 0; t < cntk; ++t) {
+                const double a = sv[t];
+                const double *wr = W64 + (int64_t)sc[t] * n;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
+                    if (cidx < n) acc[q] = fma(-a, wr[cidx], acc[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
+            if (cidx < n) {
+                R32[i * n + cidx] = (float)acc[q];
+                W32[i * n + cidx] = (float)W64[i * n + cidx];
+                mx = fmax(mx, fabs(acc[q]));
+                sq = fma(acc[q], acc[q], sq);
+            }
+        }
+    }
+    rmax[threadIdx.x] = mx;
+    rsq[threadIdx.x] = sq;
+    __syncthreads();
+    for (int w = RES_T / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + w]);
+            rsq[threadIdx.x] += rsq[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rowstat[2 * i] = rmax[0];
+        rowstat[2 * i + 1] = rsq[0];
+    }
+}
+
+// Fixed-order reduction of per-row (max, sum) pairs into sc->ns_max, sc->ns_fro2.
+__global__ void k_rowstat_final(const double *__restrict__ rowstat, int64_t n, DevScalars *sc) {
+    __shared__ double m[1024], s[1024];
+    const int t = threadIdx.x;
+    double mx = 0.0, sq = 0.0;
+    for (int64_t i = t; i < n; i += 1024) {
+        mx = fmax(mx, rowstat[2 * i]);
+        sq += rowstat[2 * i + 1];
+    }
+    m[t] = mx;
+    s[t] = sq;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (t < w) {
+            m[t] = fmax(m[t], m[t + w]);
+            s[t] += s[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        sc->ns_max = m[0];
+        sc->ns_fro2 = s[0];
+    }
+}
+
+// ---- t2 = tr((Delta W)^2) = sum_kj U_kj U_jk over 32 x 32 tile pairs -------
+__global__ void k_t2_tiles(const float *__restrict__ U, int64_t n, double *__restrict__ part) {
+    __shared__ float Ut[32][33];
+    __shared__ double red[256];
+    int64_t I, J;
+    tri_index64(blockIdx.x, I, J);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
+    // stage U[J-block rows, I-block cols] transposed
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t gr = J * 32 + r, gc = I * 32 + tx;
+        Ut[tx][r] = (gr < n && gc < n) ? U[gr * n + gc] : 0.f;
+    }
+    __syncthreads();
+    double s = 0.0;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t gr = I * 32 + r, gc = J * 32 + tx;
+        if (gr < n && gc < n) s += (double)U[gr * n + gc] * (double)Ut[r][tx];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = (I == J ? 1.0 : 2.0) * red[0];
+}
+
+__global__ void k_sum_final(const double *__restrict__ part, int64_t m, double *out) {
+    __shared__ double s[1024];
+    const int t = threadIdx.x;
+    double a = 0.0;
+    for (int64_t i = t; i < m; i += 1024) a += part[i];
+    s[t] = a;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (t < w) s[t] += s[t + w];
+        __syncthreads();
+    }
+    if (t == 0) *out = s[0];
+}
+
+// t1 = tr(W Delta) = sum over pairs of mult W_ij Delta_ij (FP64); per-block partials
+__global__ void k_t1_part(const double *__restrict__ W64, int64_t n, const int32_t *__restrict__ pi,
+                          const int32_t *__restrict__ pj, const double *__restrict__ D, int64_t np,
+                          double *__restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t p = blockIdx.x * 256ll + threadIdx.x; p < np; p += (int64_t)gridDim.x * 256) {
+        const int64_t i = pi[p], j = pj[p];
+        s += (i == j ? 1.0 : 2.0) * W64[i * n + j] * D[p];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// ---- conversions and trial matrices -----------------------------------------
+__global__ void k_to_f32(const double *__restrict__ x, float *__restrict__ y, int64_t m) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = (float)x[t];
+}
+
+__global__ void k_to_f64(const float *__restrict__ x, double *__restrict__ y, int64_t m) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = (double)x[t];
+}
+
+__global__ void k_scatter_f32(float *__restrict__ T, int64_t n, const int32_t *__restrict__ pi,
+                              const int32_t *__restrict__ pj, const double *__restrict__ aval,
+                              const double *__restrict__ D, int64_t np, double alpha) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = pi[p], j = pj[p];
+        const float v = (float)(aval[p] + alpha * D[p]);
+        T[i * n + j] = v;
+        T[j * n + i] = v;
+    }
+}
+
+// W64 = diag(1 / A_ii) for a diagonal A (the initial iterate), per-row log A_ii
+__global__ void k_diag_inverse(const double *__restrict__ A, int64_t n, double *__restrict__ W64,
+                               double *__restrict__ logs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = A[i * n + i];
+        W64[i * n + i] = 1.0 / a;
+        logs[i] = log(a);
+    }
+}
+
+inline unsigned gridn(int64_t work, int per = 256) {
+    int64_t g = (work + per - 1) / per;
+    return (unsigned)lmax(1, lmin(g, 152 * 16));
+}
+
+}  // namespace
+
+cudaError_t ns_gemm(const float *W32, const float *R32, int64_t n, double *W64, cudaStream_t st) {
+    const int64_t nt = (n + ST - 1) / ST;
+    k_ns_gemm<<<(unsigned)(nt * (nt + 1) / 2), STH, 0, st>>>(W32, R32, n, W64);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, double *val,
+                      cudaStream_t st) {
+    const unsigned g = (unsigned)((n + RW - 1) / RW);
+    k_nz_count<<<g, 32 * RW, 0, st>>>(A, n, ptr);
+    k_rowptr_scan<<<1, 1024, 0, st>>>(ptr, n);
+    k_nz_write<<<g, 32 * RW, 0, st>>>(A, n, ptr, col, val);
+    counted(3);
+    return cudaGetLastError();
+}
+
+cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const double *W64,
+                     int64_t n, float *R32, float *W32, double *rowstat, DevScalars *sc,
+                     cudaStream_t st) {
+    k_residual<<<(unsigned)n, RES_T, 0, st>>>(ptr, col, val, W64, n, R32, W32, rowstat);
+    k_rowstat_final<<<1, 1024, 0, st>>>(rowstat, n, sc);
+    counted(2);
+    return cudaGetLastError();
+}
+
+cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const int32_t *pj,
+                         const double *D, int64_t np, const float *U32, double *part, int64_t cap,
+                         DevScalars *sc, cudaStream_t st) {
+    const int64_t nt = (n + 31) / 32;
+    const int64_t ntiles = nt * (nt + 1) / 2;
+    const int nb1 = (int)lmin(1024, lmax(1, (np + 255) / 256));
+    if (ntiles + nb1 > cap) return cudaErrorInvalidValue;
+    k_t2_tiles<<<(unsigned)ntiles, 256, 0, st>>>(U32, n, part);
+    k_sum_final<<<1, 1024, 0, st>>>(part, ntiles, &sc->t2);
+    k_t1_part<<<nb1, 256, 0, st>>>(W64, n, pi, pj, D, np, part + ntiles);
+    k_sum_final<<<1, 1024, 0, st>>>(part + ntiles, nb1, &sc->t1);
+    counted(4);
+    return cudaGetLastError();
+}
+
+cudaError_t to_f32(const double *x, float *y, int64_t m, cudaStream_t st) {
+    k_to_f32<<<gridn(m), 256, 0, st>>>(x, y, m);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st) {
+    k_to_f64<<<gridn(m), 256, 0, st>>>(x, y, m);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t trial32(const double *A, float *T, int64_t n, const int32_t *pi, const int32_t *pj,
+                    const double *aval, const double *D, int64_t np, double alpha, cudaStream_t st) {
+    k_to_f32<<<gridn(n * n), 256, 0, st>>>(A, T, n * n);
+    counted(1);
+    if (np > 0) {
+        k_scatter_f32<<<gridn(np), 256, 0, st>>>(T, n, pi, pj, aval, D, np, alpha);
+        counted(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t diag_inverse(const double *A, int64_t n, double *W64, double *logs, DevScalars *sc,
+                         cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(W64, 0, (size_t)(n * n) * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    k_diag_inverse<<<gridn(n), 256, 0, st>>>(A, n, W64, logs);
+    k_sum_final<<<1, 1024, 0, st>>>(logs, n, &sc->logdet);
+    counted(2);
+    return cudaGetLastError();
+}
+
+}  // namespace glx

@@ -1,0 +1,388 @@
+// TF32 tensor-core GEMM on the 5th-generation tensor cores (tcgen05):
+//   C[i][j] = sum_k P[i][k] Q[j][k]      (both operands K-major, FP32 in HBM)
+// on 128 x 128 output tiles, fed by TMA into 128-byte-swizzled shared-memory
+// tiles through a 4-stage mbarrier pipeline, accumulated in TMEM by
+// tcgen05.mma.kind::tf32 (M = 128, N = 128, K = 8 per instruction) and read
+// back with tcgen05.ld for a fused epilogue.  One CTA of 4 warps per tile:
+// warp 0 lane 0 issues the TMA loads, warp 1 lane 0 issues the MMAs, all four
+// warps drain the accumulator (warp w owns TMEM lanes 32w .. 32w + 31).
+//
+// Uses:
+//  * Newton-Schulz refinement of W (mixed precision): C = W R, computed as
+//    W Q^T with Q = R^T, lower tiles only (C is symmetric), W64 += C mirrored;
+//  * S = X^T X / m from FP32 samples: C = Xt Xt^T with Xt = X^T (m contiguous),
+//    lower tiles only, S = C / m mirrored.
+//
+// Every wait on an mbarrier is bounded (globaltimer); on expiry the kernel
+// records an error code, drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "glasso_internal.h"
+
+namespace glx {
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 32, TST = 4;
+constexpr uint32_t TILE_BYTES = TBM * TBK * 4;  // 16 KB, one operand tile
+constexpr int TTHREADS = 128;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr unsigned long long WAIT_NS = 200000000ull;  // 200 ms per wait
+
+struct __align__(1024) TcSmem {
+    float a[TST][TBM * TBK];
+    float b[TST][TBN * TBK];
+    unsigned long long full[TST];
+    unsigned long long empty[TST];
+    unsigned long long done;
+    uint32_t tmem;
+};
+constexpr size_t TC_SMEM = sizeof(TcSmem) + 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity) {
+    const uint32_t a = smem_u32(b);
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (gtimer() - t0 > WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                       unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);
+    d |= 1ull << 16;                      // leading byte offset (unused for swizzled K-major)
+    d |= (unsigned long long)(1024 >> 4) << 32;  // stride byte offset
+    d |= 1ull << 46;                      // version
+    d |= 2ull << 61;                      // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t tf32_idesc() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+           ((uint32_t)(TBM >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, unsigned long long adesc,
+                                          unsigned long long bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tri_tile(int64_t t, int64_t &I, int64_t &J) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (i * (i + 1) / 2 > t) --i;
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    I = i;
+    J = t - i * (i + 1) / 2;
+}
+
+enum { EPI_NS = 0, EPI_SYRK = 1 };
+
+// Lower tiles (I >= J) of C = P Q^T, P and Q each n_rows x K (K-major).
+// EPI_NS:   out[i][j] += C_ij, mirrored (out: FP64, row stride ldo)
+// EPI_SYRK: out[i][j]  = scale C_ij, mirrored
+template <int EPI>
+__global__ void __launch_bounds__(TTHREADS, 1)
+    k_tc_lower(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
+               int64_t nrows, int64_t K, double *__restrict__ out, int64_t ldo, double scale,
+               int *err) {
+    extern __shared__ unsigned char raw[];
+    TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t ti, tj;
+    tri_tile(blockIdx.x, ti, tj);
+    const int nk = (int)((K + TBK - 1) / TBK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TST; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], 1);
+        }
+        mbar_init(&sm.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+
+    int issued = 0;  // TMA stage loads issued (producer)
+    if (warp == 0 && lane == 0) {
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TST;
+            if (kt >= TST && !mbar_wait(&sm.empty[s], ((kt / TST) & 1) ^ 1)) {
+                atomicExch(err, 1);
+                break;
+            }
+            mbar_expect_tx(&sm.full[s], 2 * TILE_BYTES);
+            tma_2d(&sm.a[s][0], &tp, kt * TBK, (int)(ti * TBM), &sm.full[s]);
+            tma_2d(&sm.b[s][0], &tq, kt * TBK, (int)(tj * TBN), &sm.full[s]);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = tf32_idesc();
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % TST;
+            if (!mbar_wait(&sm.full[s], (kt / TST) & 1)) {
+                atomicExch(err, 2);
+                break;
+            }
+            tc_fence_after();
+            const unsigned long long ad = sw128_desc(smem_u32(&sm.a[s][0]));
+            const unsigned long long bd = sw128_desc(smem_u32(&sm.b[s][0]));
+#pragma unroll
+            for (int kk = 0; kk < TBK / 8; ++kk)
+                umma_tf32(tmem, ad + 2ull * kk, bd + 2ull * kk, idesc, (kt | kk) != 0);
+            umma_commit(&sm.empty[s]);
+        }
+        umma_commit(&sm.done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&sm.done, 0);
+    tc_fence_after();
+    if (ok) {
+        const int64_t i = ti * TBM + warp * 32 + lane;
+#pragma unroll 1
+        for (int cb = 0; cb < TBN / 32; ++cb) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
+            if (i < nrows) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int64_t j = tj * TBN + cb * 32 + c;
+                    if (j < nrows && j <= i) {
+                        double w;
+                        if (EPI == EPI_NS) w = out[i * ldo + j] + (double)v[c];
+                        else w = scale * (double)v[c];
+                        out[i * ldo + j] = w;
+                        if (i != j) out[j * ldo + i] = w;
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 3);
+    }
+    // error path: wait (bounded) for the producer's copies still in flight;
+    // only the last TST issued stages can be outstanding
+    if (warp == 0 && lane == 0 && !ok) {
+        for (int kt = issued > TST ? issued - TST : 0; kt < issued; ++kt)
+            mbar_wait(&sm.full[kt % TST], (kt / TST) & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ---- operand packing -----------------------------------------------------
+// Qp[j][k] = R[k][j] for j, k < n, zero in the padding (ld = ldp).
+__global__ void k_transpose_pad(const float *__restrict__ R, int64_t n, float *__restrict__ Qp,
+                                int64_t ldp) {
+    __shared__ float t[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t k = by + r, j = bx + threadIdx.x;
+        t[r][threadIdx.x] = (k < n && j < n) ? R[k * n + j] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t j = bx + r, k = by + threadIdx.x;
+        if (j < ldp && k < ldp) Qp[j * ldp + k] = t[threadIdx.x][r];
+    }
+}
+
+// Wp[i][k] = W[i][k] (FP32 copy of FP64), zero padding.
+__global__ void k_pack_w(const double *__restrict__ W, int64_t n, float *__restrict__ Wp, int64_t ldp) {
+    const int64_t total = ldp * ldp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / ldp, k = t % ldp;
+        Wp[t] = (i < n && k < n) ? (float)W[i * n + k] : 0.f;
+    }
+}
+
+// Xt[i][k] = X[k][i] - mu_i as FP32 (i < n, k < m), zero padding (ld = ldp).
+template <typename TIN>
+__global__ void k_xt_pad(const TIN *__restrict__ X, int64_t m, int64_t n, const double *__restrict__ mu,
+                         float *__restrict__ Xt, int64_t ldp) {
+    __shared__ float t[32][33];
+    const int64_t bk = (int64_t)blockIdx.x * 32, bi = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t k = bk + r, i = bi + threadIdx.x;
+        float v = 0.f;
+        if (k < m && i < n) v = (float)((double)X[k * n + i] - (mu ? mu[i] : 0.0));
+        t[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t i = bi + r, k = bk + threadIdx.x;
+        if (i < n && k < ldp) Xt[i * ldp + k] = t[threadIdx.x][r];
+    }
+}
+
+// ---- host: tensor maps -----------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+cudaError_t get_encode() {
+    std::lock_guard<std::mutex> lk(g_encode_mu);
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return cudaSuccess;
+}
+
+// 2-D FP32 map over `rows` x `cols` (cols contiguous, row stride ld floats),
+// box 32 x 128 with 128-byte swizzle.
+cudaError_t make_map(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld) {
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    if (((uintptr_t)base & 15) || ((ld * 4) & 15)) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {TBK, TBM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+bool g_tc_attr[2] = {false, false};
+
+template <int EPI>
+cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t K, int64_t ld,
+                         double *out, int64_t ldo, double scale, int *err, cudaStream_t st) {
+    if (!g_tc_attr[EPI]) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        if (e != cudaSuccess) return e;
+        g_tc_attr[EPI] = true;
+    }
+    CUtensorMap mp, mq;
+    cudaError_t e = make_map(&mp, P, nrows, K, ld);
+    if (e != cudaSuccess) return e;
+    e = make_map(&mq, Q, nrows, K, ld);
+    if (e != cudaSuccess) return e;
+    const int64_t nt = (nrows + TBM - 1) / TBM;
+    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, out,
+                                                                            ldo, scale, err);
+    counted(1);
+    return cudaGetLastError();
+}
+
+inline unsigned gridn(int64_t work, int per = 256) {
+    int64_t g = (work + per - 1) / per;
+    return (unsigned)lmax(1, lmin(g, 152 * 16));
+}
+
+}  // namespace
+
+int64_t tc_pad(int64_t n) { return (n + 31) / 32 * 32; }
+
+// W64 += W R (lower tiles, mirrored) with R32 row-major (ld n); Wp and Qp are
+// scratch of tc_pad(n)^2 floats each.
+cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
+                       float *Qp, int *err, cudaStream_t st) {
+    const int64_t ldp = tc_pad(n);
+    k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(W64, n, Wp, ldp);
+    const dim3 tg((unsigned)(ldp / 32), (unsigned)(ldp / 32)), tb(32, 8);
+    k_transpose_pad<<<tg, tb, 0, st>>>(R32, n, Qp, ldp);
+    counted(2);
+    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, W64out, n, 1.0, err, st);
+}
+
+// S = (X - mu)^T (X - mu) / m from X (m x n, FP32 or FP64 values used as TF32)
+// on the tensor cores; Xt is scratch of n x tc_pad(m) floats.
+cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
+                    float *Xt, int *err, cudaStream_t st) {
+    const int64_t ldp = tc_pad(m);
+    const dim3 tg((unsigned)(ldp / 32), (unsigned)((n + 31) / 32)), tb(32, 8);
+    if (dtype == GLASSO_F32)
+        k_xt_pad<float><<<tg, tb, 0, st>>>((const float *)X, m, n, mu, Xt, ldp);
+    else
+        k_xt_pad<double><<<tg, tb, 0, st>>>((const double *)X, m, n, mu, Xt, ldp);
+    counted(1);
+    return launch_lower<EPI_SYRK>(Xt, Xt, n, ldp, ldp, S, n, 1.0 / (double)m, err, st);
+}
+
+}  // namespace glx

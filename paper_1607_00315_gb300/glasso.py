@@ -20,8 +20,8 @@ FP64, MIXED = 0, 1
 INPUT_S, INPUT_X = 0, 1
 F64, F32 = 0, 1
 HOST, DEVICE = 0, 1
-PROF_CLASSES = 5
-PROF_NAMES = ("cholesky", "inverse", "scan", "cd_sweeps", "ls_cholesky")
+PROF_CLASSES = 6
+PROF_NAMES = ("cholesky", "inverse", "scan", "cd_sweeps", "ls_cholesky", "ns_refine")
 
 _lib = None
 
