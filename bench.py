@@ -103,6 +103,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_value(local_ms, steps, world, device):
+    """Whole-job throughput of `steps` solves on each of `world` ranks: the
+    timed region is the slowest rank's (max over ranks), value = solves of all
+    ranks / that time.  Returns (max_ms, solves_per_s)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return max_ms, world * steps / (max_ms * 1e-3)
+
+
 def oracle_relaxation_sample(p, S, n_relax=1):
     """Time the FP64 oracle on a bounded sample of the same workload: forming S
     and `n_relax` level-0 relaxations (Cholesky, inverse, free set + KKT, one
@@ -197,7 +211,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="path whose solves/s is `value` (the other one is timed beside it)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -254,12 +271,34 @@ def main():
         dist.barrier()
     prof = ctx.get_profile(reset=True)
     ctx.set_profiling(False)
-    total_ms = float(sum(lat))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps / (total_ms * 1e-3)
+    total_ms, value = job_value(sum(lat), args.steps, world, dev)
+
+    # the other precision path on the same input, same timing protocol
+    compare = None
+    if not args.no_compare:
+        other = glasso.MIXED if prec == glasso.FP64 else glasso.FP64
+        octx = glasso.Context(local, precision=other)
+        octx.set_stream(stream.cuda_stream)
+        oinfo = None
+        for _ in range(2):
+            _, _, oinfo = octx.solve(X, p.lam, tol=p.tol, samples=True, A_out=A_out)
+        olat = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, oinfo = octx.solve(X, p.lam, tol=p.tol, samples=True, A_out=A_out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            olat.append(e0.elapsed_time(e1))
+        octx.close()
+        oname = "fp64" if other == glasso.FP64 else "mixed"
+        this = "mixed" if prec == glasso.MIXED else "fp64"
+        ms = {this: total_ms / args.steps, oname: float(np.mean(olat))}
+        compare = {"ms_per_solve": ms, "mixed_speedup_over_fp64": ms["fp64"] / ms["mixed"],
+                   f"{oname}_solve": {"relaxations": oinfo["relaxations"], "rel_kkt": oinfo["rel_kkt"],
+                                      "objective": oinfo["objective"]}}
 
     # end to end through the public API with host buffers
     Xh = np.ascontiguousarray(p.X)
@@ -269,10 +308,7 @@ def main():
         t0 = time.perf_counter()
         ctx.solve(Xh, p.lam, tol=p.tol, samples=True, A_out=Ah)
         e2e.append(time.perf_counter() - t0)
-    e2e_v = torch.tensor([sum(e2e)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_v, op=dist.ReduceOp.MAX)
-    e2e_value = world * len(e2e) / float(e2e_v.item())
+    _, e2e_value = job_value(sum(e2e) * 1e3, len(e2e), world, dev)
 
     if rank != 0:
         ctx.close()
@@ -323,6 +359,7 @@ def main():
                   "ls_trials": infos[-1]["ls_trials"], "rel_kkt": infos[-1]["rel_kkt"],
                   "objective": infos[-1]["objective"], "nnz": infos[-1]["nnz"]},
         "time_share": share,
+        "compare": compare,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Xh.nbytes),
                 "d2h_bytes_per_step": int(Ah.nbytes)},
         "gpu_launches": int(prof["kernels"]),

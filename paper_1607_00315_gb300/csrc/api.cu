@@ -12,6 +12,8 @@
 //   line search: T = A + alpha Delta, Cholesky  [sync per trial]
 //   accept: A += alpha Delta, the trial's factor becomes the new factor.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -43,6 +45,17 @@ namespace {
 glasso_status fail_cuda(std::string &err, cudaError_t e, const char *what) {
     err = std::string(what) + ": " + cudaGetErrorString(e);
     return GLASSO_ECUDA;
+}
+
+// GLASSO_TRACE=1 prints one line per relaxation to stderr (level, free pairs,
+// objective, line-search regime and step, refinement steps).
+bool trace_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = getenv("GLASSO_TRACE");
+        on = (e && *e && *e != '0') ? 1 : 0;
+    }
+    return on == 1;
 }
 
 size_t footprint(int64_t n, int64_t m, int xbytes) {
@@ -82,10 +95,9 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.p_inva, st); dfree(w.p_g, st); dfree(w.p_a, st); dfree(w.p_s, st);
     dfree(w.mask, st); dfree(w.rowcnt, st); dfree(w.rowred, st); dfree(w.flags, st);
     dfree(w.blkcnt, st); dfree(w.redbuf, st);
-    dfree(w.cd_part, st); dfree(w.cd_mu, st); dfree(w.cd_seg, st); dfree(w.cd_emu, st);
-    dfree(w.cd_esrc, st); dfree(w.xd, st); dfree(w.ldiag, st); dfree(w.sc, st);
+    dfree(w.cd_part, st); dfree(w.xd, st); dfree(w.ldiag, st); dfree(w.sc, st);
     dfree(w.csr_ptr, st); dfree(w.csr_col, st); dfree(w.csr_val, st); dfree(w.part, st);
-    dfree(w.Wp, st); dfree(w.Qp, st); dfree(w.Xt, st);
+    dfree(w.Wp, st); dfree(w.Qp, st); dfree(w.U2p, st); dfree(w.U3p, st); dfree(w.Xt, st);
     w.cap_mixed = w.cap_part = w.cap_xt = 0;
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
@@ -99,10 +111,6 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
         CK(dalloc(w.redbuf, 3 * 1024, st));
         w.cap_red = 3 * 1024;
         CK(dalloc(w.cd_part, (size_t)CD_MAX_CHUNKS * CD_B + (size_t)CD_B * CD_B, st));
-        CK(dalloc(w.cd_mu, CD_B, st));
-        CK(dalloc(w.cd_seg, 4 * CD_B + 8, st));
-        CK(dalloc(w.cd_emu, 2 * CD_B, st));
-        CK(dalloc(w.cd_esrc, 2 * CD_B, st));
         CK(dalloc(w.xd, 2 * NB * NB, st));
     }
     if (n <= w.cap_n) return GLASSO_OK;
@@ -131,14 +139,16 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
 glasso_status work_ensure_mixed(Work &w, int64_t n, cudaStream_t st, std::string &err) {
     if (n <= w.cap_mixed) return GLASSO_OK;
     const int64_t nt = (n + 31) / 32;
+    const int64_t np2 = tc_pad(n) * tc_pad(n);
     CK(dalloc(w.csr_ptr, n + 1, st));
     CK(dalloc(w.csr_col, (size_t)n * n + n, st));
     CK(dalloc(w.csr_val, (size_t)n * n + n, st));
-    w.cap_part = nt * (nt + 1) / 2 + 1024;
+    w.cap_part = nt * nt + 1024;
     CK(dalloc(w.part, w.cap_part, st));
-    const int64_t np2 = tc_pad(n) * tc_pad(n);
     CK(dalloc(w.Wp, np2, st));
     CK(dalloc(w.Qp, np2, st));
+    CK(dalloc(w.U2p, np2, st));
+    CK(dalloc(w.U3p, np2, st));
     w.cap_mixed = n;
     return GLASSO_OK;
 }
@@ -365,6 +375,10 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 8.0);
             CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            if (h->bar_err) {
+                err = "CD sweep: a bounded grid-barrier wait expired";
+                return GLASSO_ECUDA;
+            }
             if (!h->moved) continue;
             {
                 const double delta = h->delta, trSD = h->trSD;
@@ -494,10 +508,12 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         if (h->info != 0) return GLASSO_ENOTPD;
         return factor_inverse();
     };
+    int ns_steps = 0;
     auto refine = [&]() -> glasso_status {
         CK(build_csr(w.A, n, w.csr_ptr, w.csr_col, w.csr_val, st));
         bool restarted = false;
-        for (int it = 0; it < max_ns; ++it) {
+        ns_steps = 0;
+        for (int it = 0; it < max_ns; ++it, ++ns_steps) {
             CK(residual(w.csr_ptr, w.csr_col, w.csr_val, W64, n, R32, W32, w.rowred, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->tc_err) {
@@ -607,28 +623,64 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
             CK(series_terms(W64, n, w.pi, w.pj, w.D, np, U32, w.part, w.cap_part, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            if (h->bar_err) {
+                err = "CD sweep: a bounded grid-barrier wait expired";
+                return GLASSO_ECUDA;
+            }
             if (!h->moved) continue;
             {
                 const double delta = h->delta, trSD = h->trSD;
                 const double t1 = h->t1, t2 = std::max(h->t2, 0.0);
                 const double epsF = 1e-12 * std::max(fabs(F), nd);
+                // per-step budget of the tracked log-det (the stated objective accuracy)
+                const double track = 1e-10 * std::max(fabs(F), nd);
+                double t3 = 0.0, t4 = 0.0, t5 = 0.0, t6 = 0.0;
+                bool high = false;
                 double alpha = 1.0;
                 bool ok = false, chol = false;
                 double FT = 0.0, dl1 = 0.0, dld = 0.0;
+                int nterms = 0;
                 for (int t = 0; t < max_trials; ++t) {
                     const double rho = alpha * sqrt(t2);
                     CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
-                    double errb;
+                    double errb = INFINITY;
                     bool pd = true;
-                    // the series' remainder bound must be below the objective's
-                    // FP64 resolution, because the increment is also added to the
-                    // tracked log-det
-                    const double rem = rho < 0.5 ? rho * rho * rho / (3.0 * (1.0 - rho)) : INFINITY;
-                    if (rem + 1e-6 * alpha * alpha * t2 <= epsF) {
+                    // log det(A + alpha Delta) - log det A = sum_k (-1)^{k+1} alpha^k t_k / k,
+                    // remainder after K terms <= rho^{K+1} / ((K+1)(1 - rho)); rho < 1
+                    // also proves A + alpha Delta positive definite
+                    nterms = 0;
+                    if (rho < 0.5) {
+                        const double r2 = rho * rho * rho / (3.0 * (1.0 - rho)) + 1e-6 * alpha * alpha * t2;
+                        if (r2 <= track) {
+                            nterms = 2;
+                            errb = r2;
+                        } else {
+                            if (!high) {
+                                CK(series_high(U32, n, w.Wp, w.Qp, w.U2p, w.U3p, w.part, w.cap_part, sc, st));
+                                if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                                if (h->tc_err) {
+                                    err = "tensor-core GEMM: a bounded wait expired";
+                                    return GLASSO_ECUDA;
+                                }
+                                t3 = h->t3; t4 = h->t4; t5 = h->t5; t6 = h->t6;
+                                high = true;
+                            }
+                            const double r7 = pow(rho, 7.0) / (7.0 * (1.0 - rho));
+                            const double tf32 = 0x1p-9 * (pow(rho, 3.0) / 3 + pow(rho, 4.0) / 4 +
+                                                         pow(rho, 5.0) / 5 + pow(rho, 6.0) / 6);
+                            if (r7 + tf32 + 1e-6 * alpha * alpha * t2 <= track) {
+                                nterms = 6;
+                                errb = r7 + tf32 + 1e-6 * alpha * alpha * t2;
+                            }
+                        }
+                    }
+                    if (nterms > 0) {
                         chol = false;
                         if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
-                        dld = alpha * t1 - 0.5 * alpha * alpha * t2;
-                        errb = rem + 1e-6 * alpha * alpha * t2;
+                        const double a2 = alpha * alpha, a3 = a2 * alpha;
+                        dld = alpha * t1 - 0.5 * a2 * t2;
+                        if (nterms == 6)
+                            dld += a3 * t3 / 3.0 - a2 * a2 * t4 / 4.0 + a3 * a2 * t5 / 5.0 - a3 * a3 * t6 / 6.0;
                     } else {
                         chol = true;
                         CK(trial32(w.A, T32, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
@@ -656,6 +708,12 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                     goto done;
                 }
                 CK(ls_apply(w.A, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                if (trace_on())
+                    fprintf(stderr,
+                            "glasso[mixed] cycle %d level %d pairs %lld F %.12g dF %.3e rho %.3e "
+                            "alpha %g regime %s terms %d ns_prev %d relkkt %.3e\n",
+                            k, l, (long long)np, FT, FT - F, alpha * sqrt(t2), alpha,
+                            chol ? "chol32" : "series", nterms, ns_steps, relkkt);
                 logdet += dld;
                 trSA += alpha * trSD;
                 l1 += dl1;
@@ -1232,8 +1290,13 @@ glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W
     sv.mark_begin(3, eb);
     CTX_CK(cd_sweeps(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, D, U, w, ctx->stream));
     sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * (double)n * 8.0);
-    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    s = sync_ctx(ctx);
     if (prof) prof_collect(prof);
+    if (s != GLASSO_OK) return s;
+    if (w.sc_host->bar_err) {
+        ctx->last_error = "CD sweep: a bounded grid-barrier wait expired";
+        return GLASSO_ECUDA;
+    }
     return GLASSO_OK;
 }
 

@@ -25,7 +25,7 @@ inline void counted(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 constexpr int NB = 32;
 // Coordinates resolved together by one blocked CD step (see cd.cu).
 constexpr int CD_B = 128;
-// Maximum number of k-chunks of the CD dot products.
+// Maximum number of 256-column chunks of the CD dot products (n <= 65536).
 constexpr int CD_MAX_CHUNKS = 256;
 
 // Device-side scalar results of the reduction kernels (one struct per context).
@@ -53,10 +53,16 @@ struct DevScalars {
     double ns_fro2;       // ||I - A W||_F^2
     double t1;            // tr(W Delta)
     double t2;            // tr((W Delta)^2)
+    double t3, t4, t5, t6;  // tr((W Delta)^k), k = 3..6
     int err;              // device-side error flag (NaN input, bad diagonal)
     int bad_sym;          // input symmetry check failed
     int tc_err;           // tensor-core GEMM: a bounded wait expired (code)
     int pad2;
+    // grid barrier of the persistent CD sweep: count, generation, error, pad
+    unsigned bar_count;
+    unsigned bar_gen;
+    int bar_err;
+    int pad3;
 };
 
 // Per-context device workspace, sized for n <= cap_n.
@@ -86,11 +92,7 @@ struct Work {
     double *redbuf = nullptr;              // generic reduction partials
     int64_t cap_red = 0;
     // CD scratch
-    double *cd_part = nullptr;             // CD_MAX_CHUNKS x CD_B partial dots
-    double *cd_mu = nullptr;               // CD_B
-    int32_t *cd_seg = nullptr;             // segment table of the row updates
-    double *cd_emu = nullptr;              // 2 CD_B entry coefficients
-    int32_t *cd_esrc = nullptr;            // 2 CD_B entry source rows
+    double *cd_part = nullptr;             // CD_MAX_CHUNKS x CD_B partial dots, then CD_B^2 K
     double *xd = nullptr;                  // 2 x 32 x 32: inverses of Cholesky diagonal blocks
     double *ldiag = nullptr;               // n: FP64 diagonal of the last factor
     // mixed precision: CSR of A and reduction partials
@@ -101,6 +103,7 @@ struct Work {
     double *part = nullptr;
     int64_t cap_part = 0;
     float *Wp = nullptr, *Qp = nullptr;    // padded FP32 operands of the tensor-core GEMM
+    float *U2p = nullptr, *U3p = nullptr;  // padded U^2, U^3 of the log-det series
     float *Xt = nullptr;                   // padded X^T for S on the tensor cores
     int64_t cap_xt = 0;
     DevScalars *sc = nullptr;              // device scalars
@@ -175,7 +178,6 @@ cudaError_t hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uin
                       DevScalars *sc, cudaStream_t st);
 
 // ---- launchers (mixed.cu) ----
-cudaError_t ns_gemm(const float *W32, const float *R32, int64_t n, double *W64, cudaStream_t st);
 cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, double *val,
                       cudaStream_t st);
 cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const double *W64,
@@ -184,6 +186,8 @@ cudaError_t residual(const long long *ptr, const int32_t *col, const double *val
 cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const int32_t *pj,
                          const double *D, int64_t np, const float *U32, double *part, int64_t cap,
                          DevScalars *sc, cudaStream_t st);
+cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float *U2, float *U3,
+                        double *part, int64_t cap, DevScalars *sc, cudaStream_t st);
 cudaError_t to_f32(const double *x, float *y, int64_t m, cudaStream_t st);
 cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st);
 cudaError_t trial32(const double *A, float *T, int64_t n, const int32_t *pi, const int32_t *pj,
@@ -197,6 +201,9 @@ cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W
                        float *Qp, int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
                     float *Xt, int *err, cudaStream_t st);
+cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, cudaStream_t st);
+cudaError_t gemm_tn_tc(const float *P, const float *Q, int64_t n, float *C, int *err,
+                       cudaStream_t st);
 
 // ---- launchers (cd.cu) ----
 cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,

@@ -1,20 +1,21 @@
 // Kernels of the mixed-precision relaxation.
 //
-// The bulk arithmetic moves to FP32 while the quantities that decide the
-// answer stay FP64:
+// The bulk arithmetic moves to FP32 / TF32 while the quantities that decide
+// the answer stay FP64:
 //  * W = A^{-1} is kept in FP64 and refined against A by Newton-Schulz steps
 //        R = I - A W            (FP64, A sparse: CSR of its nonzeros)
-//        W <- W + W R           (FP32 GEMM of the small correction, FP64 sum)
-//    which square the residual each step until |R| reaches FP64 level; the
-//    gradient S - W, the free set and the KKT residual therefore see an FP64
-//    accurate W (eq. gradHes, eq. active_set, the Section 8 stopping rule).
+//        W <- W + W R           (TF32 tensor-core GEMM of the small correction,
+//                                FP64 sum, tc.cu)
+//    until |R| reaches 1e-11; the gradient S - W, the free set and the KKT
+//    residual therefore see an FP64-accurate W (eq. gradHes, eq. active_set,
+//    the Section 8 stopping rule).
 //  * The line search (Section 6.1.2) gets log det(A + alpha Delta) - log det A
-//    from the series  sum_k (-1)^{k+1} alpha^k tr((W Delta)^k) / k  with
-//    t1 = tr(W Delta) (FP64 on the pairs) and t2 = tr((W Delta)^2) = sum U_kj U_jk
-//    (U = Delta W from the sweep), whose remainder is bounded by
-//    (alpha sqrt(t2))^3 / (3 (1 - alpha sqrt(t2))); alpha sqrt(t2) < 1 also
-//    proves A + alpha Delta positive definite.  Large steps use an FP32
-//    Cholesky (FP64 diagonal blocks) instead.
+//    from the series  sum_k (-1)^{k+1} alpha^k t_k / k,  t_k = tr((W Delta)^k):
+//    t1 on the pairs (FP64), t2 = sum U_kj U_jk with U = Delta W from the
+//    sweep, t3 .. t6 from U^2 and U^3 on the tensor cores; the remainder after
+//    K terms is at most rho^{K+1} / ((K+1)(1 - rho)), rho = alpha sqrt(t2), and
+//    rho < 1 also proves A + alpha Delta positive definite.  Large steps use an
+//    FP32 Cholesky (FP64 log accumulation) instead.
 #include <math.h>
 
 #include "glasso_internal.h"
@@ -22,72 +23,12 @@
 namespace glx {
 namespace {
 
-constexpr int ST = 64;    // SGEMM output tile edge
-constexpr int SK = 16;    // k-chunk
-constexpr int STH = 256;  // threads: 16 x 16, 4 x 4 outputs each
-
 __device__ __forceinline__ void tri_index64(int64_t t, int64_t &I, int64_t &J) {
     int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while (i * (i + 1) / 2 > t) --i;
     while ((i + 1) * (i + 2) / 2 <= t) ++i;
     I = i;
     J = t - i * (i + 1) / 2;
-}
-
-// acc[r][c] += sum_k A[i0 + 4 ty + r, k] B[k, j0 + 4 tx + c], FP32, row-major.
-__device__ __forceinline__ void sgemm_tile(float (&acc)[4][4], const float *__restrict__ A,
-                                           const float *__restrict__ B, int64_t n, int64_t i0,
-                                           int64_t j0, float (*As)[ST + 4], float (*Bs)[ST + 4]) {
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int64_t kc = 0; kc < n; kc += SK) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int idx = tid + STH * r;
-            const int i = idx >> 4, k = idx & 15;
-            const int64_t gi = i0 + i, gk = kc + k;
-            As[k][i] = (gi < n && gk < n) ? A[gi * n + gk] : 0.f;
-            const int j = idx & 63, k2 = idx >> 6;
-            const int64_t gj = j0 + j, gk2 = kc + k2;
-            Bs[k2][j] = (gj < n && gk2 < n) ? B[gk2 * n + gj] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < SK; ++k) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[k][4 * ty]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][4 * tx]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-}
-
-// Newton-Schulz correction on lower tiles: C = W32 R32 (symmetric up to
-// rounding), W64 += C mirrored so W64 stays exactly symmetric.
-__global__ void __launch_bounds__(STH) k_ns_gemm(const float *__restrict__ W32,
-                                                 const float *__restrict__ R32, int64_t n,
-                                                 double *__restrict__ W64) {
-    __shared__ __align__(16) float As[SK][ST + 4];
-    __shared__ __align__(16) float Bs[SK][ST + 4];
-    int64_t I, J;
-    tri_index64(blockIdx.x, I, J);
-    float acc[4][4] = {};
-    sgemm_tile(acc, W32, R32, n, I * ST, J * ST, As, Bs);
-    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int64_t i = I * ST + 4 * ty + r, j = J * ST + 4 * tx + c;
-            if (i < n && j <= i) {
-                const double w = W64[i * n + j] + (double)acc[r][c];
-                W64[i * n + j] = w;
-                if (i != j) W64[j * n + i] = w;
-            }
-        }
 }
 
 // ---- CSR of the nonzeros of A (full rows, column order) --------------------
@@ -285,6 +226,32 @@ __global__ void k_sum_final(const double *__restrict__ part, int64_t m, double *
     if (t == 0) *out = s[0];
 }
 
+// sum_{i,j < n} P_ij Q_ji over all 32 x 32 tile pairs (FP64 partial per tile)
+__global__ void k_tdot_tiles(const float *__restrict__ P, int64_t ldp_, const float *__restrict__ Q,
+                             int64_t ldq, int64_t n, double *__restrict__ part) {
+    __shared__ float Qt[32][33];
+    __shared__ double red[256];
+    const int64_t I = blockIdx.y, J = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {  // Qt[c][r] = Q[J*32 + r][I*32 + c]
+        const int64_t gr = J * 32 + r, gc = I * 32 + tx;
+        Qt[tx][r] = (gr < n && gc < n) ? Q[gr * ldq + gc] : 0.f;
+    }
+    __syncthreads();
+    double s = 0.0;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t gr = I * 32 + r, gc = J * 32 + tx;
+        if (gr < n && gc < n) s += (double)P[gr * ldp_ + gc] * (double)Qt[r][tx];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
 // t1 = tr(W Delta) = sum over pairs of mult W_ij Delta_ij (FP64); per-block partials
 __global__ void k_t1_part(const double *__restrict__ W64, int64_t n, const int32_t *__restrict__ pi,
                           const int32_t *__restrict__ pj, const double *__restrict__ D, int64_t np,
@@ -347,13 +314,6 @@ inline unsigned gridn(int64_t work, int per = 256) {
 
 }  // namespace
 
-cudaError_t ns_gemm(const float *W32, const float *R32, int64_t n, double *W64, cudaStream_t st) {
-    const int64_t nt = (n + ST - 1) / ST;
-    k_ns_gemm<<<(unsigned)(nt * (nt + 1) / 2), STH, 0, st>>>(W32, R32, n, W64);
-    counted(1);
-    return cudaGetLastError();
-}
-
 cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, double *val,
                       cudaStream_t st) {
     const unsigned g = (unsigned)((n + RW - 1) / RW);
@@ -385,6 +345,33 @@ cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const 
     k_t1_part<<<nb1, 256, 0, st>>>(W64, n, pi, pj, D, np, part + ntiles);
     k_sum_final<<<1, 1024, 0, st>>>(part + ntiles, nb1, &sc->t1);
     counted(4);
+    return cudaGetLastError();
+}
+
+// t3 .. t6 of the log-det series from U = Delta W (FP32, ld n):
+//   t3 = sum (U^2)_ij U_ji, t4 = sum (U^2)_ij (U^2)_ji, t5 = sum (U^2)_ij (U^3)_ji,
+//   t6 = sum (U^3)_ij (U^3)_ji, with U^2 and U^3 from TF32 tensor-core GEMMs.
+// Up, Ut, U2, U3: scratch of tc_pad(n)^2 floats each.
+cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float *U2, float *U3,
+                        double *part, int64_t cap, DevScalars *sc, cudaStream_t st) {
+    const int64_t p = tc_pad(n);
+    const int64_t nt = (n + 31) / 32;
+    if (nt * nt > cap) return cudaErrorInvalidValue;
+    cudaError_t e = pad_and_transpose(U32, n, Up, Ut, st);
+    if (e != cudaSuccess) return e;
+    e = gemm_tn_tc(Up, Ut, n, U2, &sc->tc_err, st);  // U^2
+    if (e != cudaSuccess) return e;
+    e = gemm_tn_tc(U2, Ut, n, U3, &sc->tc_err, st);  // U^3
+    if (e != cudaSuccess) return e;
+    const dim3 g((unsigned)nt, (unsigned)nt);
+    const float *Ps[4] = {U2, U2, U2, U3};
+    const float *Qs[4] = {Up, U2, U3, U3};
+    double *outs[4] = {&sc->t3, &sc->t4, &sc->t5, &sc->t6};
+    for (int k = 0; k < 4; ++k) {
+        k_tdot_tiles<<<g, 256, 0, st>>>(Ps[k], p, Qs[k], p, n, part);
+        k_sum_final<<<1, 1024, 0, st>>>(part, nt * nt, outs[k]);
+        counted(2);
+    }
     return cudaGetLastError();
 }
 
