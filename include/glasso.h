@@ -178,6 +178,18 @@ glasso_status glasso_potrf(glasso_ctx *ctx, double *A, int64_t n, int *info, dou
  * read), eq. gradHes.  W is written in full.  FP64. */
 glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double *W);
 
+/* a2 + a3 in the arithmetic of the mixed-precision solve: A (lower triangle
+ * read, FP64) is rounded to FP32 and factored, A = L L^T, with the inverse
+ * factor X = L^{-1} formed alongside (recursive blocking; every O(n^3)
+ * contraction on the tensor cores as a split-TF32 product, about 2^-21
+ * relative error per product, FP32 accumulation); then W = X^T X = A^{-1}
+ * (eq. gradHes; not refined) is written in full as FP64.  *info and *logdet
+ * as glasso_potrf (log det accumulated in FP64 from the FP32 pivots); W is
+ * left unwritten when *info != 0.  A is not modified.  Needs a
+ * GLASSO_MIXED context (else GLASSO_EINVAL). */
+glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, double *W, int *info,
+                                   double *logdet);
+
 /* a4. Free set of eq. active_set, {(i,j): A_ij != 0 or |(S - W)_ij| > lambda},
  * restricted to a candidate set C_l (eq. MLE_l1_prior_C).  When cand_i is
  * NULL all upper-triangle pairs are candidates and the scan also returns the

@@ -67,6 +67,8 @@ size_t footprint(int64_t n, int64_t m, int xbytes) {
     b += (size_t)(n + 1) * sizeof(long long) + (size_t)n * 6 * sizeof(double);
     if (m > 0) b += (size_t)m * n * (sizeof(double) + xbytes) + (size_t)n * sizeof(double);
     b += nn * (sizeof(int32_t) + sizeof(double));  // CSR of A (mixed precision)
+    b += nn * sizeof(double);                      // CD interaction matrices (at most)
+    b += (size_t)4 * n * ((n + 31) / 32 * 32) * sizeof(float);  // tensor-core factorisation planes
     return b + (4u << 20);
 }
 
@@ -96,6 +98,9 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.mask, st); dfree(w.rowcnt, st); dfree(w.rowred, st); dfree(w.flags, st);
     dfree(w.blkcnt, st); dfree(w.redbuf, st);
     dfree(w.cd_part, st); dfree(w.xd, st); dfree(w.ldiag, st); dfree(w.sc, st);
+    dfree(w.cd_k, st);
+    dfree(w.fa, st);
+    w.cap_cd_k = 0;
     dfree(w.csr_ptr, st); dfree(w.csr_col, st); dfree(w.csr_val, st); dfree(w.part, st);
     dfree(w.Wp, st); dfree(w.Qp, st); dfree(w.U2p, st); dfree(w.U3p, st); dfree(w.Xt, st);
     w.cap_mixed = w.cap_part = w.cap_xt = 0;
@@ -149,6 +154,7 @@ glasso_status work_ensure_mixed(Work &w, int64_t n, cudaStream_t st, std::string
     CK(dalloc(w.Qp, np2, st));
     CK(dalloc(w.U2p, np2, st));
     CK(dalloc(w.U3p, np2, st));
+    CK(dalloc(w.fa, (size_t)4 * n * tc_pad(n), st));
     w.cap_mixed = n;
     return GLASSO_OK;
 }
@@ -475,9 +481,10 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         if (s0 != GLASSO_OK) return s0;
     }
     const size_t nn = (size_t)n * (size_t)n;
-    float *T32 = (float *)w.T, *X32 = T32 + nn;
+    const int64_t ldf = tc_pad(n);
+    float *FA = w.fa, *FX = FA + n * ldf, *FXt = FX + n * ldf, *FZ = FXt + n * ldf;
     float *W32 = (float *)w.L, *R32 = W32 + nn;
-    float *U32 = (float *)w.U, *Tw32 = U32 + nn;
+    float *U32 = (float *)w.U;
     double *W64 = w.W;
     const double sigma = 1e-4;
     const int max_trials = 30;
@@ -493,18 +500,28 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     int64_t nf = 0;
     cudaEvent_t eb;
 
-    // W from an FP32 factorisation held in T32 (lower), then refined.
+    // W = X^T X from the inverse factor X = L^{-1} of the last tensor-core
+    // factorisation (FXt = X^T), then refined.
     auto factor_inverse = [&]() -> glasso_status {
         sv.mark_begin(1, eb);
-        CK(inverse32(T32, n, W32, X32, Tw32, st));
+        CK(lauum_tc(FXt, n, ldf, W32, n, sc, st));
         CK(to_f64(W32, W64, (int64_t)nn, st));
-        sv.mark_end(1, eb, 2.0 * nd * nd * nd / 3.0);
+        sv.mark_end(1, eb, nd * nd * nd / 3.0);
+        return GLASSO_OK;
+    };
+    auto factor_wait = [&]() -> glasso_status {
+        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        if (h->tc_err) {
+            err = "tensor-core factorisation: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
+            return GLASSO_ECUDA;
+        }
         return GLASSO_OK;
     };
     auto fresh_factor = [&]() -> glasso_status {
-        CK(trial32(w.A, T32, n, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
-        CK(potrf32(T32, n, (float *)w.xd, w.ldiag, sc, st));
-        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+        CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st));
+        glasso_status s2 = factor_wait();
+        if (s2 != GLASSO_OK) return s2;
         if (h->info != 0) return GLASSO_ENOTPD;
         return factor_inverse();
     };
@@ -683,11 +700,12 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                             dld += a3 * t3 / 3.0 - a2 * a2 * t4 / 4.0 + a3 * a2 * t5 / 5.0 - a3 * a3 * t6 / 6.0;
                     } else {
                         chol = true;
-                        CK(trial32(w.A, T32, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                        CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                         sv.mark_begin(4, eb);
-                        CK(potrf32(T32, n, (float *)w.xd, w.ldiag, sc, st));
-                        sv.mark_end(4, eb, nd * nd * nd / 3.0);
-                        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+                        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st));
+                        sv.mark_end(4, eb, 2.0 * nd * nd * nd / 3.0);
+                        glasso_status s2 = factor_wait();
+                        if (s2 != GLASSO_OK) return s2;
                         pd = h->info == 0;
                         dld = h->logdet - logdet;
                         errb = 2.0 * e_chol;
@@ -1226,6 +1244,51 @@ glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double
     CTX_CK(inverse(L, n, W, ctx->w.T, ctx->w.U, ctx->stream));
     sv.mark_end(1, eb, 2.0 * (double)n * n * n / 3.0);
     CTX_CK(cudaStreamSynchronize(ctx->stream));
+    if (prof) prof_collect(prof);
+    return GLASSO_OK;
+}
+
+glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, double *W, int *info,
+                                   double *logdet) {
+    if (!ctx || !A || !W || n < 1) return GLASSO_EINVAL;
+    if (ctx->precision != GLASSO_MIXED) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    s = work_ensure_mixed(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    Work &w = ctx->w;
+    const int64_t ldf = tc_pad(n);
+    float *FA = w.fa, *FX = FA + n * ldf, *FXt = FX + n * ldf, *FZ = FXt + n * ldf;
+    float *W32 = (float *)w.L;
+    Prof *prof = (Prof *)ctx->prof;
+    Solver sv{w, ctx->stream, ctx->last_error, prof};
+    cudaEvent_t eb;
+    CTX_CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), ctx->stream));
+    CTX_CK(trial32(A, FA, n, ldf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, ctx->stream));
+    sv.mark_begin(4, eb);
+    CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream));
+    sv.mark_end(4, eb, 2.0 * (double)n * n * n / 3.0);
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    if (w.sc_host->tc_err) {
+        ctx->last_error = "tensor-core factorisation: a bounded wait expired";
+        return GLASSO_ECUDA;
+    }
+    if (info) *info = w.sc_host->info;
+    if (logdet) *logdet = w.sc_host->logdet;
+    if (w.sc_host->info == 0) {
+        sv.mark_begin(1, eb);
+        CTX_CK(lauum_tc(FXt, n, ldf, W32, n, w.sc, ctx->stream));
+        CTX_CK(to_f64(W32, W, n * n, ctx->stream));
+        sv.mark_end(1, eb, (double)n * n * n / 3.0);
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (w.sc_host->tc_err) {
+            ctx->last_error = "tensor-core GEMM: a bounded wait expired";
+            return GLASSO_ECUDA;
+        }
+    }
     if (prof) prof_collect(prof);
     return GLASSO_OK;
 }

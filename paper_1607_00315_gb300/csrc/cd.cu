@@ -20,6 +20,8 @@
 //  3. row updates: each target row of U gets its updates in sweep order.
 #include <math.h>
 
+#include <algorithm>
+
 #include "glasso_internal.h"
 
 namespace glx {
@@ -47,11 +49,13 @@ __device__ __forceinline__ CT soft(CT x, CT t) {
 //      arithmetic is identical in every CTA, so all hold the same mu_t and the
 //      same update list without a broadcast (CTA 0 alone writes Delta, after
 //      the next barrier, when no CTA still reads it).
-// The barrier is a counter plus generation word in global memory; every wait
-// is bounded (2 s, globaltimer) and sets an error word read by the host.
+// The barrier is a monotonic arrival counter in global memory: the k-th
+// barrier of the launch completes when the counter reaches k G (no reset, so
+// the last CTA to arrive has nothing more to do).  Every wait is bounded (2 s,
+// globaltimer) and sets an error word read by the host.
 struct GridBar {
     unsigned count;
-    unsigned gen;
+    unsigned unused;
     int err;
     int pad;
 };
@@ -62,34 +66,130 @@ __device__ __forceinline__ unsigned long long cd_gtimer() {
     return t;
 }
 
-__device__ bool grid_sync(GridBar *gb, unsigned nblocks) {
+__device__ __forceinline__ void red_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// `epoch` counts the barriers this CTA has passed in the launch.  Arrival is a
+// release reduction (no round trip); the wait polls with acquire loads.
+__device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch) {
     __shared__ int ok_s;
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &gb->gen;
         volatile int *verr = &gb->err;
-        const unsigned g0 = *vgen;
-        __threadfence();
+        const unsigned target = epoch * nblocks;
+        red_release_gpu(&gb->count, 1u);
         int ok = 1;
-        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            const unsigned long long t0 = cd_gtimer();
-            while (*vgen == g0) {
-                if (*verr || cd_gtimer() - t0 > 2000000000ull) {
-                    ok = 0;
-                    atomicExch(&gb->err, 1);
-                    break;
-                }
+        const unsigned long long t0 = cd_gtimer();
+        while ((int)(ld_acquire_gpu(&gb->count) - target) < 0) {
+            if (*verr || cd_gtimer() - t0 > 2000000000ull) {
+                ok = 0;
+                atomicExch(&gb->err, 1);
+                break;
             }
         }
-        __threadfence();
         ok_s = ok && !*verr;
     }
     __syncthreads();
     return ok_s != 0;
+}
+
+// Bulk asynchronous copy of the interaction matrix into shared memory,
+// completed on an mbarrier (bounded waits).
+__device__ __forceinline__ uint32_t cd_smem(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void kcopy_issue(void *dst, const void *src, uint32_t bytes,
+                                            unsigned long long *bar) {
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cd_smem(bar)),
+                 "r"(bytes)
+                 : "memory");
+    constexpr uint32_t CH = 16384;
+    for (uint32_t o = 0; o < bytes; o += CH)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                cd_smem(dst) + o),
+            "l"((const unsigned char *)src + o), "r"(bytes - o < CH ? bytes - o : CH), "r"(cd_smem(bar))
+            : "memory");
+}
+__device__ __forceinline__ bool kcopy_wait(unsigned long long *bar, uint32_t parity) {
+    const uint32_t a = cd_smem(bar);
+    const unsigned long long t0 = cd_gtimer();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (cd_gtimer() - t0 > 200000000ull) return false;
+    }
+}
+
+// FP32 resolution of one block by one warp, in sub-blocks of SB coordinates.
+// Lane l keeps b of coordinates l, l + 32, l + 64, l + 96.  For a sub-block,
+// every lane takes a copy of its SB values (shuffles), so each step's
+// dependent path is the closed form plus one FMA with no broadcast; then each
+// lane adds the sub-block's SB terms to its own coordinates.  Every b_t
+// receives its terms K[s][t] mu_s in ascending s, as in the lane-owner form
+// (lanes also update coordinates already resolved; those values are unused).
+__device__ __forceinline__ void resolve_f32(const float *__restrict__ Ks, const float *bsh,
+                                            const float *csh, const float *ish, float lam,
+                                            int nb, float *mush, int *zsh) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NQ = CD_B / 32, SB = 8;
+    float bl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) bl[q] = bsh[lane + 32 * q];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+        for (int h = 0; h < 32 / SB; ++h) {
+            const int t0 = 32 * q + SB * h;
+            if (t0 >= nb) break;
+            float bc[SB], mu[SB];
+#pragma unroll
+            for (int k = 0; k < SB; ++k) bc[k] = __shfl_sync(0xffffffffu, bl[q], SB * h + k);
+#pragma unroll
+            for (int k = 0; k < SB; ++k) {
+                // coordinates t >= nb hold zeros and take mu = 0
+                const int t = t0 + k;
+                const float c = csh[t], ia = ish[t];
+                const float x = c - bc[k] * ia;
+                const float th = lam * ia;
+                const float z = x - fminf(fmaxf(x, -th), th);  // S_th(x), exact zero inside
+                const float m = (t < nb) ? z - c : 0.0f;
+                if (lane == (t & 31)) {
+                    mush[t] = m;
+                    zsh[t] = (z == 0.0f);
+                }
+#pragma unroll
+                for (int g = (k + 1) / 4; g < SB / 4; ++g) {
+                    const float4 kv = *reinterpret_cast<const float4 *>(Ks + t * CD_B + t0 + 4 * g);
+                    if (4 * g > k) bc[4 * g] = fmaf(kv.x, m, bc[4 * g]);
+                    if (4 * g + 1 > k) bc[4 * g + 1] = fmaf(kv.y, m, bc[4 * g + 1]);
+                    if (4 * g + 2 > k) bc[4 * g + 2] = fmaf(kv.z, m, bc[4 * g + 2]);
+                    if (4 * g + 3 > k) bc[4 * g + 3] = fmaf(kv.w, m, bc[4 * g + 3]);
+                }
+                mu[k] = m;
+            }
+#pragma unroll
+            for (int qq = q; qq < NQ; ++qq) {
+                const float *Kr = Ks + t0 * CD_B + 32 * qq + lane;
+#pragma unroll
+                for (int k = 0; k < SB; ++k) bl[qq] = fmaf(Kr[k * CD_B], mu[k], bl[qq]);
+            }
+        }
+    }
 }
 
 template <typename T, typename CT>
@@ -98,7 +198,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
     const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
     const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
     double *__restrict__ D, int nsweeps, double *__restrict__ bvec, double *__restrict__ Kt,
-    GridBar *gb) {
+    CT *__restrict__ Kall, GridBar *gb) {
     extern __shared__ __align__(16) unsigned char ks_raw[];
     CT *Ks = reinterpret_cast<CT *>(ks_raw);  // Ks[s * CD_B + t]
     __shared__ CT bsh[CD_B], csh[CD_B], ish[CD_B], mush[CD_B];
@@ -110,6 +210,10 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
     __shared__ double smu[NE];
     __shared__ int seg_start[NE + 1], seg_dest[NE];
     __shared__ int nseg_s, wtot[RT / 32];
+    __shared__ __align__(8) unsigned long long kbar;
+    __shared__ int kok;
+    unsigned epoch = 0, kuse = 0;
+    constexpr uint32_t KBYTES = CD_B * CD_B * sizeof(CT);
     const unsigned G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t gthread = (int64_t)blockIdx.x * RT + tid, nthreads = (int64_t)G * RT;
@@ -118,7 +222,28 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
     const int64_t total = nbatch * nsweeps;
     int64_t prev_b0 = -1;
     int prev_nb = 0;
-    if (tid == 0) nseg_s = 0;
+    if (tid == 0) {
+        nseg_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // 0. with Kall: the interaction matrices of all blocks (they depend on W
+    //    and the pair list only, so every sweep reuses them); zero outside s < t < nb
+    if (Kall) {
+        const int64_t ktot = nbatch * (int64_t)CD_B * CD_B;
+        for (int64_t q = gthread; q < ktot; q += nthreads) {
+            const int64_t bb = q / (CD_B * CD_B);
+            const int r = (int)(q - bb * CD_B * CD_B), s = r / CD_B, t = r - s * CD_B;
+            const int64_t kb0 = bb * CD_B;
+            double v = 0.0;
+            if (s < t && kb0 + t < np) {
+                const int64_t is = pi[kb0 + s], js = pj[kb0 + s], it2 = pi[kb0 + t], jt = pj[kb0 + t];
+                v = (double)W[it2 * n + is] * (double)W[js * n + jt];
+                if (is != js) v = fma((double)W[it2 * n + js], (double)W[is * n + jt], v);
+            }
+            Kall[q] = (CT)v;
+        }
+    }
     __syncthreads();
     for (int64_t it = 0; it <= total; ++it) {
         // 1. row updates of the previous block
@@ -153,11 +278,12 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             }
         }
         if (it == total) break;
-        if (!grid_sync(gb, G)) return;
+        if (!grid_sync(gb, G, epoch)) return;
         if (blockIdx.x == 0 && prev_b0 >= 0)
             for (int t = tid; t < prev_nb; t += RT) D[prev_b0 + t] = dnew[t];
         const int64_t b0 = (it % nbatch) * CD_B;
         const int nb = (int)lmin(CD_B, np - b0);
+        if (Kall && tid == 0) kcopy_issue(Ks, Kall + (it % nbatch) * CD_B * CD_B, KBYTES, &kbar);
         // 2. stale dots as (coordinate, chunk of DCH columns) warp tasks, partial
         //    sums per chunk (summed in a fixed order in step 3); interactions
         const int nch = (int)((n + DCH - 1) / DCH);
@@ -176,7 +302,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             if (lane == 0) bvec[(int64_t)c * CD_B + t] = a;
         }
         CT *Ktc = reinterpret_cast<CT *>(Kt);
-        for (int q = (int)gthread; q < nb * nb; q += (int)nthreads) {
+        for (int q = (int)gthread; !Kall && q < nb * nb; q += (int)nthreads) {
             const int s = q / nb, t = q - s * nb;
             if (s < t) {
                 const int64_t is = pi[b0 + s], js = pj[b0 + s], it2 = pi[b0 + t], jt = pj[b0 + t];
@@ -185,7 +311,11 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 Ktc[s * CD_B + t] = (CT)v;
             }
         }
-        if (!grid_sync(gb, G)) return;
+        if (!grid_sync(gb, G, epoch)) {
+            if (Kall && tid == 0) kcopy_wait(&kbar, kuse & 1u);  // the prefetch in flight
+            return;
+        }
+        if (!Kall && tid == 0) kcopy_issue(Ks, Ktc, KBYTES, &kbar);
         // 3. resolution, identical in every CTA
         if (tid < nb) {
             // independent loads of the chunk partials, summed in chunk order
@@ -204,52 +334,60 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             ish[tid] = (CT)inva[b0 + tid];
             si[tid] = pi[b0 + tid];
             sj[tid] = pj[b0 + tid];
+        } else if (tid < CD_B) {
+            bsh[tid] = csh[tid] = ish[tid] = (CT)0;
+            si[tid] = sj[tid] = 0;
         }
-        {
-            // the interaction matrix as 16-byte vectors, eight independent loads
-            // in flight per thread (entries with s >= t or t >= nb are ignored by
-            // the chain, whatever they hold)
-            constexpr int VEC = 16 / sizeof(CT);
-            const uint4 *src = reinterpret_cast<const uint4 *>(Kt);
-            uint4 *dst = reinterpret_cast<uint4 *>(Ks);
-            constexpr int NV = CD_B * CD_B / VEC;
-#pragma unroll 8
-            for (int q = tid; q < NV; q += RT) dst[q] = src[q];
-        }
-        __syncthreads();
-        if (tid < 32) {
-            // lane l holds b, c, 1/a of coordinates l, l+32, l+64, l+96 in registers;
-            // the owner of coordinate t computes mu_t and broadcasts it by shuffle
-            CT br[CD_B / 32], cr[CD_B / 32], ir[CD_B / 32];
-#pragma unroll
-            for (int q = 0; q < CD_B / 32; ++q) {
-                br[q] = bsh[lane + 32 * q];
-                cr[q] = csh[lane + 32 * q];
-                ir[q] = ish[lane + 32 * q];
+        if (tid == 0) {
+            const bool got = kcopy_wait(&kbar, kuse & 1u);
+            if (!got) {
+                atomicExch(&gb->err, 1);
+                kcopy_wait(&kbar, kuse & 1u);  // let the copy land before leaving
             }
-            const CT lamc = (CT)lam;
+            kok = got;
+        }
+        ++kuse;
+        __syncthreads();
+        if (!kok) return;
+        if (tid < 32) {
+            if constexpr (sizeof(CT) == 4) {
+                resolve_f32(reinterpret_cast<const float *>(Ks), reinterpret_cast<const float *>(bsh),
+                            reinterpret_cast<const float *>(csh), reinterpret_cast<const float *>(ish),
+                            (float)lam, nb, reinterpret_cast<float *>(mush), zsh);
+            } else {
+                // lane l holds b, c, 1/a of coordinates l, l+32, l+64, l+96 in registers;
+                // the owner of coordinate t computes mu_t and broadcasts it by shuffle
+                CT br[CD_B / 32], cr[CD_B / 32], ir[CD_B / 32];
 #pragma unroll
-            for (int q = 0; q < CD_B / 32; ++q) {
+                for (int q = 0; q < CD_B / 32; ++q) {
+                    br[q] = bsh[lane + 32 * q];
+                    cr[q] = csh[lane + 32 * q];
+                    ir[q] = ish[lane + 32 * q];
+                }
+                const CT lamc = (CT)lam;
+#pragma unroll
+                for (int q = 0; q < CD_B / 32; ++q) {
 #pragma unroll 4
-                for (int tt = 0; tt < 32; ++tt) {
-                    const int t = 32 * q + tt;
-                    if (t >= nb) break;
-                    CT mu = 0;
-                    int zf = 0;
-                    if (lane == tt) {
-                        const CT z = soft(cr[q] - br[q] * ir[q], lamc * ir[q]);
-                        mu = z - cr[q];
-                        zf = (z == (CT)0);
-                        mush[t] = mu;
-                        zsh[t] = zf;
-                    }
-                    mu = __shfl_sync(0xffffffffu, mu, tt);
-                    if (mu != (CT)0) {
-                        const CT *kr = Ks + t * CD_B;
+                    for (int tt = 0; tt < 32; ++tt) {
+                        const int t = 32 * q + tt;
+                        if (t >= nb) break;
+                        CT mu = 0;
+                        int zf = 0;
+                        if (lane == tt) {
+                            const CT z = soft(cr[q] - br[q] * ir[q], lamc * ir[q]);
+                            mu = z - cr[q];
+                            zf = (z == (CT)0);
+                            mush[t] = mu;
+                            zsh[t] = zf;
+                        }
+                        mu = __shfl_sync(0xffffffffu, mu, tt);
+                        if (mu != (CT)0) {
+                            const CT *kr = Ks + t * CD_B;
 #pragma unroll
-                        for (int qq = q; qq < CD_B / 32; ++qq) {
-                            const int s2 = lane + 32 * qq;
-                            if (s2 > t) br[qq] = fma(kr[s2], mu, br[qq]);
+                            for (int qq = q; qq < CD_B / 32; ++qq) {
+                                const int s2 = lane + 32 * qq;
+                                if (s2 > t) br[qq] = fma(kr[s2], mu, br[qq]);
+                            }
                         }
                     }
                 }
@@ -275,33 +413,34 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
         // row updates: entry e = 2t + k (k = 0: row i_t gets mu W_{j_t}; k = 1: row
         // j_t gets mu W_{i_t}); sort the packed keys (target row, e) so that the
         // updates of a row are contiguous and in sweep order
-        for (int e = tid; e < NE; e += RT) {
-            const int t = e >> 1, k = e & 1;
-            unsigned key = 0xFFFFFFFFu;
+        unsigned key = 0xFFFFFFFFu;
+        {
+            const int e = tid, t = e >> 1, k = e & 1;  // RT == NE
             if (t < nb && meff[t] != 0.0) {
                 if (k == 0) key = ((unsigned)si[t] << 9) | (unsigned)e;
                 else if (si[t] != sj[t]) key = ((unsigned)sj[t] << 9) | (unsigned)e;
             }
-            skey[e] = key;
         }
-        __syncthreads();
+        // bitonic sort, one key per thread: partners inside a warp by shuffle,
+        // across warps through shared memory
         for (int size = 2; size <= NE; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                const int e = tid, pr = e ^ stride;
-                if (pr > e) {
-                    const bool up = (e & size) == 0;
-                    const unsigned a = skey[e], b = skey[pr];
-                    if ((a > b) == up) {
-                        skey[e] = b;
-                        skey[pr] = a;
-                    }
+                unsigned other;
+                if (stride >= 32) {
+                    skey[tid] = key;
+                    __syncthreads();
+                    other = skey[tid ^ stride];
+                    __syncthreads();
+                } else {
+                    other = __shfl_xor_sync(0xffffffffu, key, stride);
                 }
-                __syncthreads();
+                const bool up = (tid & size) == 0, lower = (tid & stride) == 0;
+                key = (lower == up) ? min(key, other) : max(key, other);
             }
         }
         int V = 0;
         {
-            const unsigned kk = skey[tid];
+            const unsigned kk = key;
             const int valid = kk != 0xFFFFFFFFu;
             if (valid) {
                 const int e = (int)(kk & 511u), t = e >> 1;
@@ -386,9 +525,29 @@ static cudaError_t cd_sweeps_t(const T *W, int64_t n, double lam, const int32_t 
     GridBar *gb = reinterpret_cast<GridBar *>(&w.sc->bar_count);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
+    // interaction matrices of all blocks, computed once per launch, while they
+    // fit in n^2 doubles (else each block computes its own)
+    const size_t kneed = (size_t)((np + CD_B - 1) / CD_B) * kbytes;
+    CT *Kall = nullptr;
+    if (kneed <= (size_t)n * (size_t)n * sizeof(double)) {
+        if (w.cap_cd_k < kneed) {
+            const size_t want = std::min((size_t)n * (size_t)n * sizeof(double),
+                                         std::max(kneed, 2 * w.cap_cd_k));
+            if (w.cd_k) {
+                e = cudaFreeAsync(w.cd_k, st);
+                w.cd_k = nullptr;
+                w.cap_cd_k = 0;
+                if (e != cudaSuccess) return e;
+            }
+            e = cudaMallocAsync((void **)&w.cd_k, want, st);
+            if (e != cudaSuccess) return e;
+            w.cap_cd_k = want;
+        }
+        Kall = reinterpret_cast<CT *>(w.cd_k);
+    }
     void *args[] = {(void *)&W, (void *)&U, (void *)&n, (void *)&lam, (void *)&pi, (void *)&pj,
                     (void *)&np, (void *)&inva, (void *)&g, (void *)&aval, (void *)&D,
-                    (void *)&nsweeps, (void *)&bvec, (void *)&Kt, (void *)&gb};
+                    (void *)&nsweeps, (void *)&bvec, (void *)&Kt, (void *)&Kall, (void *)&gb};
     e = cudaLaunchCooperativeKernel((const void *)k_cd_persist<T, CT>, dim3(G), dim3(RT), args,
                                     kbytes, st);
     counted(1);

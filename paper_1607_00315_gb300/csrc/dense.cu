@@ -372,6 +372,119 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
     }
 }
 
+// Leaf of the tensor-core factorisation (FP32): one CTA factors and inverts
+// the diagonal block [o, o + s), s <= 128, of A (row stride ld) in shared
+// memory.  L in 32-wide steps: each diagonal 32 x 32 block and its inverse by
+// one warp in registers, the panel L_ib = A_ib X_kk^T and the trailing update
+// by the whole CTA; then X = L^{-1} by block substitution,
+//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (32-blocks, i > j),
+// with the inner sums parked in the free upper blocks.  Rows beyond s are
+// identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
+// (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the first
+// failing pivot + 1 (global index) into sc->info.
+constexpr int LB = 128, LP = LB + 1;
+constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
+
+__global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
+                                                    int s, float *__restrict__ Xo,
+                                                    float *__restrict__ Xto, double *__restrict__ ldiag,
+                                                    DevScalars *sc) {
+    if (sc->info != 0) return;
+    extern __shared__ float lsm[];
+    float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
+    float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
+    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1];
+    __shared__ int fshare;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < LB * LB; idx += TPB) {
+        const int r = idx / LB, c = idx % LB;
+        float v = 0.f;
+        if (r < s && c <= r) v = A[(o + r) * ld + o + c];
+        else if (r == c) v = 1.f;
+        L[r][c] = v;
+        X[r][c] = 0.f;
+    }
+    __syncthreads();
+    for (int kb = 0; kb < LB / NB; ++kb) {
+        const int d0 = kb * NB;
+        for (int idx = tid; idx < NB * NB; idx += TPB) B[idx / NB][idx % NB] = L[d0 + idx / NB][d0 + idx % NB];
+        __syncthreads();
+        if (tid < 32) {
+            const int f = warp_chol_inv32<float>(B, Xd, NB, nullptr);
+            if (tid == 0) fshare = f;
+        }
+        __syncthreads();
+        if (fshare) {
+            if (tid == 0) atomicCAS(&sc->info, 0, (int)(o + d0 + fshare));
+            return;
+        }
+        for (int idx = tid; idx < NB * NB; idx += TPB) {
+            const int r = idx / NB, c = idx % NB;
+            L[d0 + r][d0 + c] = B[r][c];
+            X[d0 + r][d0 + c] = Xd[r][c];
+        }
+        __syncthreads();
+        const int nrem = LB / NB - kb - 1;
+        if (nrem == 0) break;
+        // panel rows below: L[row][d0 + c] = sum_{t <= c} L[row][d0 + t] Xd[c][t]
+        float pv[(LB - NB) * NB / TPB];
+#pragma unroll
+        for (int q = 0; q < (LB - NB) * NB / TPB; ++q) {
+            const int idx = tid + TPB * q;
+            pv[q] = 0.f;
+            if (idx < nrem * NB * NB) {
+                const int row = d0 + NB + idx / NB, c = idx % NB;
+                float acc = 0.f;
+                for (int t = 0; t <= c; ++t) acc = fmaf(L[row][d0 + t], Xd[c][t], acc);
+                pv[q] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < (LB - NB) * NB / TPB; ++q) {
+            const int idx = tid + TPB * q;
+            if (idx < nrem * NB * NB) L[d0 + NB + idx / NB][d0 + idx % NB] = pv[q];
+        }
+        __syncthreads();
+        // trailing update of the lower part
+        const int m = LB - d0 - NB;
+        for (int idx = tid; idx < m * m; idx += TPB) {
+            const int i = d0 + NB + idx / m, j = d0 + NB + idx % m;
+            if (j <= i) {
+                float acc = 0.f;
+#pragma unroll 8
+                for (int t = 0; t < NB; ++t) acc = fmaf(L[i][d0 + t], L[j][d0 + t], acc);
+                L[i][j] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < s; r += TPB) ldiag[o + r] = (double)L[r][r];
+    // X below the diagonal blocks, by distance of block row and column
+    for (int diff = 1; diff < LB / NB; ++diff) {
+        const int nblk = LB / NB - diff;
+        for (int idx = tid; idx < nblk * NB * NB; idx += TPB) {
+            const int jb = idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB, ib = jb + diff;
+            float acc = 0.f;
+            for (int k = jb * NB; k < ib * NB; ++k) acc = fmaf(L[ib * NB + r][k], X[k][jb * NB + c], acc);
+            X[jb * NB + r][ib * NB + c] = acc;  // T_ij, parked in the upper block (jb, ib)
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nblk * NB * NB; idx += TPB) {
+            const int jb = idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB, ib = jb + diff;
+            float acc = 0.f;
+            for (int t = 0; t <= r; ++t) acc = fmaf(X[ib * NB + r][ib * NB + t], X[jb * NB + t][ib * NB + c], acc);
+            X[ib * NB + r][jb * NB + c] = -acc;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < s * s; idx += TPB) {
+        const int r = idx / s, c = idx % s;
+        Xo[(o + r) * ld + o + c] = (c <= r) ? X[r][c] : 0.f;
+        Xto[(o + r) * ld + o + c] = (c >= r) ? X[c][r] : 0.f;
+    }
+}
+
 // log det A = 2 sum_i log L_ii from the FP64 diagonal of the factor,
 // deterministic single-CTA reduction.
 __global__ void k_logdet(const double *__restrict__ ldiag, int64_t n, DevScalars *sc) {
@@ -590,6 +703,27 @@ cudaError_t inverse(const double *L, int64_t n, double *W, double *X, double *Tw
 }
 cudaError_t inverse32(const float *L, int64_t n, float *W, float *X, float *Tw, cudaStream_t st) {
     return inverse_t<float>(L, n, W, X, Tw, st);
+}
+
+cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, float *Xt, double *ldiag,
+                        DevScalars *sc, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)LEAF_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (s < 1 || s > LB) return cudaErrorInvalidValue;
+    k_leaf32<<<1, TPB, LEAF_SMEM, st>>>(A, ld, o, s, X, Xt, ldiag, sc);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t logdet_from_diag(const double *ldiag, int64_t n, DevScalars *sc, cudaStream_t st) {
+    k_logdet<<<1, TPB, 0, st>>>(ldiag, n, sc);
+    counted(1);
+    return cudaGetLastError();
 }
 
 }  // namespace glx

@@ -93,6 +93,9 @@ struct Work {
     int64_t cap_red = 0;
     // CD scratch
     double *cd_part = nullptr;             // CD_MAX_CHUNKS x CD_B partial dots, then CD_B^2 K
+    float *fa = nullptr;                   // 4 x n x tc_pad(n) FP32: matrix, X, Xt, scratch of cholinv_tc
+    unsigned char *cd_k = nullptr;         // interaction matrices of all CD blocks (grown on demand)
+    size_t cap_cd_k = 0;
     double *xd = nullptr;                  // 2 x 32 x 32: inverses of Cholesky diagonal blocks
     double *ldiag = nullptr;               // n: FP64 diagonal of the last factor
     // mixed precision: CSR of A and reduction partials
@@ -190,13 +193,22 @@ cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float
                         double *part, int64_t cap, DevScalars *sc, cudaStream_t st);
 cudaError_t to_f32(const double *x, float *y, int64_t m, cudaStream_t st);
 cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st);
-cudaError_t trial32(const double *A, float *T, int64_t n, const int32_t *pi, const int32_t *pj,
-                    const double *aval, const double *D, int64_t np, double alpha, cudaStream_t st);
+cudaError_t trial32(const double *A, float *T, int64_t n, int64_t ldT, const int32_t *pi,
+                    const int32_t *pj, const double *aval, const double *D, int64_t np, double alpha,
+                    cudaStream_t st);
 cudaError_t diag_inverse(const double *A, int64_t n, double *W64, double *logs, DevScalars *sc,
                          cudaStream_t st);
 
 // ---- launchers (tc.cu) ----
 int64_t tc_pad(int64_t n);
+// FP32 factorisation and inverse on the tensor cores (split TF32): see cholinv_tc.cu
+cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, float *Xt, double *ldiag,
+                        DevScalars *sc, cudaStream_t st);
+cudaError_t logdet_from_diag(const double *ldiag, int64_t n, DevScalars *sc, cudaStream_t st);
+cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z, double *ldiag,
+                       DevScalars *sc, cudaStream_t st);
+cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t ldw, DevScalars *sc,
+                     cudaStream_t st);
 cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
                        float *Qp, int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,

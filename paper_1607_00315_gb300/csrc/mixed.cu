@@ -284,15 +284,24 @@ __global__ void k_to_f64(const float *__restrict__ x, double *__restrict__ y, in
         y[t] = (double)x[t];
 }
 
-__global__ void k_scatter_f32(float *__restrict__ T, int64_t n, const int32_t *__restrict__ pi,
+__global__ void k_scatter_f32(float *__restrict__ T, int64_t ldT, const int32_t *__restrict__ pi,
                               const int32_t *__restrict__ pj, const double *__restrict__ aval,
                               const double *__restrict__ D, int64_t np, double alpha) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = pi[p], j = pj[p];
         const float v = (float)(aval[p] + alpha * D[p]);
-        T[i * n + j] = v;
-        T[j * n + i] = v;
+        T[i * ldT + j] = v;
+        T[j * ldT + i] = v;
+    }
+}
+
+// T[i][j] = (float)A[i][j] with row stride ldT.
+__global__ void k_to_f32_ld(const double *__restrict__ A, int64_t n, float *__restrict__ T, int64_t ldT) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / n, j = t - i * n;
+        T[i * ldT + j] = (float)A[t];
     }
 }
 
@@ -387,12 +396,13 @@ cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t trial32(const double *A, float *T, int64_t n, const int32_t *pi, const int32_t *pj,
-                    const double *aval, const double *D, int64_t np, double alpha, cudaStream_t st) {
-    k_to_f32<<<gridn(n * n), 256, 0, st>>>(A, T, n * n);
+cudaError_t trial32(const double *A, float *T, int64_t n, int64_t ldT, const int32_t *pi,
+                    const int32_t *pj, const double *aval, const double *D, int64_t np, double alpha,
+                    cudaStream_t st) {
+    k_to_f32_ld<<<gridn(n * n), 256, 0, st>>>(A, n, T, ldT);
     counted(1);
     if (np > 0) {
-        k_scatter_f32<<<gridn(np), 256, 0, st>>>(T, n, pi, pj, aval, D, np, alpha);
+        k_scatter_f32<<<gridn(np), 256, 0, st>>>(T, ldT, pi, pj, aval, D, np, alpha);
         counted(1);
     }
     return cudaGetLastError();

@@ -22,15 +22,16 @@
 #include <mutex>
 
 #include "glasso_internal.h"
+#include "tc_ptx.h"
 
 namespace glx {
 namespace {
+using namespace ptx;
 
 constexpr int TBM = 128, TBN = 128, TBK = 32, TST = 4;
 constexpr uint32_t TILE_BYTES = TBM * TBK * 4;  // 16 KB, one operand tile
 constexpr int TTHREADS = 128;
 constexpr uint32_t TMEM_COLS = 128;
-constexpr unsigned long long WAIT_NS = 200000000ull;  // 200 ms per wait
 
 struct __align__(1024) TcSmem {
     float a[TST][TBM * TBK];
@@ -41,97 +42,6 @@ struct __align__(1024) TcSmem {
     uint32_t tmem;
 };
 constexpr size_t TC_SMEM = sizeof(TcSmem) + 1024;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-                 : "memory");
-}
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity) {
-    const uint32_t a = smem_u32(b);
-    const unsigned long long t0 = gtimer();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (gtimer() - t0 > WAIT_NS) return false;
-    }
-}
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                       unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride byte offset), descriptor version 1.
-__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((saddr & 0x3FFFF) >> 4);
-    d |= 1ull << 16;                      // leading byte offset (unused for swizzled K-major)
-    d |= (unsigned long long)(1024 >> 4) << 32;  // stride byte offset
-    d |= 1ull << 46;                      // version
-    d |= 2ull << 61;                      // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
-__host__ __device__ constexpr uint32_t tf32_idesc() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TBN >> 3) << 17) |
-           ((uint32_t)(TBM >> 4) << 24);
-}
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, unsigned long long adesc,
-                                          unsigned long long bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-        "%30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __device__ __forceinline__ void tri_tile(int64_t t, int64_t &I, int64_t &J) {
     int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -389,6 +299,10 @@ inline unsigned gridn(int64_t work, int per = 256) {
 }  // namespace
 
 int64_t tc_pad(int64_t n) { return (n + 31) / 32 * 32; }
+
+cudaError_t make_tmap(CUtensorMap *map, const float *base, int64_t rows, int64_t cols, int64_t ld) {
+    return make_map(map, base, rows, cols, ld);
+}
 
 // W64 += W R (lower tiles, mirrored) with R32 row-major (ld n); Wp and Qp are
 // scratch of tc_pad(n)^2 floats each.

@@ -86,6 +86,7 @@ def load():
     L.glasso_form_S.argtypes = [vp, vp, i32, i64, i64, i32, vp]
     L.glasso_potrf.argtypes = [vp, vp, i64, C.POINTER(i32), C.POINTER(d)]
     L.glasso_inverse.argtypes = [vp, vp, i64, vp]
+    L.glasso_cholinv_mixed.argtypes = [vp, vp, i64, vp, C.POINTER(i32), C.POINTER(d)]
     L.glasso_free_set.argtypes = [vp, vp, vp, vp, i64, d, vp, vp, i64, vp, vp, vp,
                                   C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
     L.glasso_hierarchy.argtypes = [vp, vp, vp, i64, vp, C.POINTER(i32)]
@@ -246,6 +247,14 @@ class Context:
     def inverse(self, L, W):
         self._check(self.L.glasso_inverse(self.h, _ptr(L), L.shape[0], _ptr(W)), "inverse")
 
+    def cholinv_mixed(self, A, W):
+        """FP32 tensor-core factorisation of A and W = A^-1 (unrefined) as FP64;
+        returns (info, logdet)."""
+        info, ld = C.c_int(0), C.c_double(0.0)
+        self._check(self.L.glasso_cholinv_mixed(self.h, _ptr(A), A.shape[0], _ptr(W), C.byref(info),
+                                                C.byref(ld)), "cholinv_mixed")
+        return info.value, ld.value
+
     def free_set(self, S, W, A, lam, oi, oj, absg=None, cand=None):
         cnt = C.c_int64(0)
         rk, mk = C.c_double(0.0), C.c_double(0.0)
@@ -299,6 +308,6 @@ EXPORTED = (
     "glasso_create", "glasso_destroy", "glasso_set_stream", "glasso_strerror",
     "glasso_last_error", "glasso_solve", "glasso_solve_batch", "glasso_submit", "glasso_poll",
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
-    "glasso_inverse", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
+    "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc",
 )

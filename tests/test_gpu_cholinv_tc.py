@@ -1,0 +1,110 @@
+"""The mixed-precision factorisation (rows a2 + a3 in the arithmetic of the
+mixed solve) through the C ABI: A rounded to FP32, A = L L^T with the inverse
+factor formed alongside on the tensor cores (split TF32, FP32 accumulation),
+W = X^T X, against the FP64 oracle's Cholesky, log det and inverse.
+
+Error statement.  Rounding A to FP32 perturbs each entry by at most 2^-24
+relative; the factorisation is backward stable with unit roundoff about
+2^-21 (split-TF32 products) plus FP32 accumulation.  The line search allows
+n 2^-20 for the log det of one FP32 factorisation, so that is the bar here;
+W = A^{-1} is held to kappa(A) 2^-14 relative (max norm), which keeps
+||I - A W|| far below the 0.9 at which the Newton-Schulz refinement of the
+solve would restart.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00315_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mctx():
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso
+
+    build.build()
+    torch.cuda.init()
+    c = glasso.Context(0, precision=glasso.MIXED)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _spd(n, seed, cond=50.0):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (q * np.exp(rng.uniform(0, np.log(cond), n))) @ q.T
+
+
+def _run(mctx, A):
+    import torch
+
+    n = A.shape[0]
+    W = torch.full((n, n), np.nan, dtype=torch.float64, device="cuda")
+    info, ld = mctx.cholinv_mixed(_dev(A), W)
+    return info, ld, W.cpu().numpy()
+
+
+# 1: one leaf; 100/128: one ragged / one full leaf; 129, 200, 300: two to
+# three leaves with a ragged tail; 513, 1000: several recursion levels
+@pytest.mark.parametrize("n", [1, 5, 100, 128, 129, 200, 300, 513, 1000])
+def test_cholinv_matches_oracle(mctx, n):
+    A = _spd(n, 1000 + n)
+    info_ref, L = oracle.cholesky(A)
+    assert info_ref == 0
+    ld_ref = oracle.logdet_from_chol(L)
+    W_ref = oracle.inverse_from_chol(L)
+    info, ld, W = _run(mctx, A)
+    assert info == 0
+    assert abs(ld - ld_ref) <= n * 2.0 ** -20, (ld, ld_ref)
+    kappa = np.linalg.cond(A)
+    err = np.abs(W - W_ref).max() / np.abs(W_ref).max()
+    assert err <= kappa * 2.0 ** -14, (err, kappa)
+    assert np.array_equal(W, W.T)
+    # split TF32, not plain TF32: the error is far below 2^-11
+    assert err < 2.0 ** -16 * kappa
+
+
+def test_cholinv_precision_matrix_of_the_workload(mctx):
+    """A sparse-Theta precision matrix of the n = 2000 workload's generator
+    (the kind of iterate the solve factors), n = 600."""
+    Theta = synth.sparse_theta(600, np.random.default_rng(77))
+    info_ref, L = oracle.cholesky(Theta)
+    assert info_ref == 0
+    info, ld, W = _run(mctx, Theta)
+    assert info == 0
+    assert abs(ld - oracle.logdet_from_chol(L)) <= 600 * 2.0 ** -20
+    R = np.eye(600) - Theta @ W
+    assert np.abs(R).max() < 1e-4
+
+
+@pytest.mark.parametrize("n,k", [(50, 0), (50, 37), (300, 129), (300, 299), (700, 400)])
+def test_cholinv_reports_the_failing_pivot(mctx, n, k):
+    """A negative diagonal entry at k in an otherwise well-conditioned SPD
+    matrix: the leading minors are positive up to k - 1 and the k-th is not
+    (Sylvester's criterion, as the oracle reports), so info = k + 1."""
+    A = _spd(n, 7 + n, cond=4.0)
+    A[k, k] = -5.0
+    info_ref, _ = oracle.cholesky(A)
+    info, _, W = _run(mctx, A)
+    assert info_ref == k + 1
+    assert info == info_ref
+    assert np.isnan(W).all()  # W untouched when A is not positive definite
+
+
+def test_cholinv_consecutive_calls_and_sizes(mctx):
+    """Different sizes in a row on one context (buffers grow, state resets)."""
+    for n, seed in [(400, 1), (130, 2), (400, 3), (1, 4)]:
+        A = _spd(n, seed)
+        info_ref, L = oracle.cholesky(A)
+        info, ld, W = _run(mctx, A)
+        assert info == 0 and abs(ld - oracle.logdet_from_chol(L)) <= n * 2.0 ** -20
