@@ -683,11 +683,14 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                                 high = true;
                             }
                             const double r7 = pow(rho, 7.0) / (7.0 * (1.0 - rho));
-                            const double tf32 = 0x1p-9 * (pow(rho, 3.0) / 3 + pow(rho, 4.0) / 4 +
+                            // t3 .. t6 from split-TF32 products: relative error
+                            // about (n / 8 + 2) 2^-24 of each term
+                            const double eps_t = (nd / 8.0 + 2.0) * 0x1p-24;
+                            const double terr = eps_t * (pow(rho, 3.0) / 3 + pow(rho, 4.0) / 4 +
                                                          pow(rho, 5.0) / 5 + pow(rho, 6.0) / 6);
-                            if (r7 + tf32 + 1e-6 * alpha * alpha * t2 <= track) {
+                            if (r7 + terr + 1e-6 * alpha * alpha * t2 <= track) {
                                 nterms = 6;
-                                errb = r7 + tf32 + 1e-6 * alpha * alpha * t2;
+                                errb = r7 + terr + 1e-6 * alpha * alpha * t2;
                             }
                         }
                     }

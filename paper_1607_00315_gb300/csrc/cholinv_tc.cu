@@ -166,17 +166,21 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                 const int nsteps = nk * (XK / 8);
                 for (int step = 0; step < nsteps; ++step) {
                     const int b = step % XNB;
-                    if (!mbar_wait(&sm.mfull[b], (step / XNB) & 1)) {
-                        atomicExch(a.err, 16);
+                    // warp-uniform outcome: the TMEM loads below need the whole warp
+                    const bool got = __all_sync(0xffffffffu, mbar_wait(&sm.mfull[b], (step / XNB) & 1));
+                    if (!got) {
+                        if (lane == 0) atomicExch(a.err, 16);
                         break;
                     }
                     tc_fence_after();
+                    uint32_t v0[32], v1[32];
+                    tmem_ld32_issue(tmem + lane_off + 128u * (uint32_t)(b + 1) + col0, v0);
+                    tmem_ld32_issue(tmem + lane_off + 128u * (uint32_t)(b + 1) + col0 + 32u, v1);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int cb = 0; cb < HC / 32; ++cb) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_off + 128u * (uint32_t)(b + 1) + col0 + (uint32_t)(cb * 32), v);
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) acc[cb * 32 + c] += v[c];
+                    for (int c = 0; c < 32; ++c) {
+                        acc[c] += __uint_as_float(v0[c]);
+                        acc[32 + c] += __uint_as_float(v1[c]);
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -184,12 +188,16 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                 }
             }
             __syncwarp();
-            ok = mbar_wait(&sm.done, 0);
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.done, 0));
             tc_fence_after();
-            if (!ok && lane == 0 && warp == 6) atomicExch(a.err, 14);
+            if (!ok && lane == 0) atomicExch(a.err, 14);
         }
+        // stage C in the (now idle) stage buffers, padded rows, then write it out
+        // with coalesced rows (and, for outT / the mirror, columns); every drain
+        // warp reaches the named barrier, whatever its wait returned
+        float(*Ct)[XM + 1] = reinterpret_cast<float(*)[XM + 1]>(&sm.a[0][0]);
         if (ok) {
-            const int64_t i = ti * XM + lw * 32 + lane;
+            const int rl = lw * 32 + lane;
 #pragma unroll
             for (int cb = 0; cb < HC / 32; ++cb) {
                 float v[32];
@@ -199,22 +207,43 @@ __global__ void __launch_bounds__(XTHREADS, 1)
 #pragma unroll
                     for (int c = 0; c < 32; ++c) v[c] = 0.f;
                 }
-                if (i >= a.M) continue;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int64_t j = tj * XN + col0 + cb * 32 + c;
-                    const float r = acc[cb * 32 + c] + v[c];
-                    if (j < a.N) {
-                        if (a.epi == XE_ASSIGN) {
-                            const float w = a.alpha * r;
-                            a.out[i * a.ldo + j] = w;
-                            if (a.outT) a.outT[j * a.ldt + i] = w;
-                        } else if (a.epi == XE_SUB) {
-                            if (j <= i) a.out[i * a.ldo + j] -= r;
-                        } else if (j <= i) {
-                            a.out[i * a.ldo + j] = r;
-                            a.out[j * a.ldo + i] = r;
-                        }
+                for (int c = 0; c < 32; ++c) Ct[rl][col0 + cb * 32 + c] = acc[cb * 32 + c] + v[c];
+            }
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (ok) {
+            const int et = threadIdx.x - 192, wr = et >> 5;  // 8 warps x 32 lanes
+#pragma unroll 1
+            for (int r = wr; r < XM; r += 8) {
+                const int64_t i = ti * XM + r;
+                if (i >= a.M) break;
+#pragma unroll
+                for (int p = 0; p < XN / 32; ++p) {
+                    const int cc = lane + 32 * p;
+                    const int64_t j = tj * XN + cc;
+                    if (j >= a.N) continue;
+                    const float v = Ct[r][cc];
+                    if (a.epi == XE_ASSIGN) a.out[i * a.ldo + j] = a.alpha * v;
+                    else if (j <= i) {
+                        if (a.epi == XE_SUB) a.out[i * a.ldo + j] -= v;
+                        else a.out[i * a.ldo + j] = v;
+                    }
+                }
+            }
+            if (a.outT || a.epi == XE_SYM) {
+#pragma unroll 1
+                for (int cc = wr; cc < XN; cc += 8) {
+                    const int64_t j = tj * XN + cc;
+                    if (j >= a.N) break;
+#pragma unroll
+                    for (int p = 0; p < XM / 32; ++p) {
+                        const int r = lane + 32 * p;
+                        const int64_t i = ti * XM + r;
+                        if (i >= a.M) continue;
+                        const float v = Ct[r][cc];
+                        if (a.epi == XE_ASSIGN) a.outT[j * a.ldt + i] = a.alpha * v;
+                        else if (j < i) a.out[j * a.ldo + i] = v;
                     }
                 }
             }
@@ -418,6 +447,16 @@ cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, flo
     e = node(r, 0, n);
     if (e != cudaSuccess) return e;
     return logdet_from_diag(ldiag, n, sc, st);
+}
+
+// C = P Q^T for n x n FP32 operands (row stride ld, a multiple of 32), split
+// TF32 with the main products summed outside the tensor core: relative error
+// about 2^-21 per product plus FP32 round-to-nearest summation of n / 8
+// partial sums.  C (row stride ld) is written for rows and columns < n.
+cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,
+                          cudaStream_t st) {
+    return tcx(P, Q, n, n, n, ld, false, 0, 0, 0, true, XE_ASSIGN, 1.f, C, ld, nullptr, 0, nullptr,
+               err, st);
 }
 
 // W = Xt Xt^T (= X^T X = A^{-1}), lower tiles mirrored, W row stride ldw.

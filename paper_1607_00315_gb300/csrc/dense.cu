@@ -375,15 +375,51 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 // Leaf of the tensor-core factorisation (FP32): one CTA factors and inverts
 // the diagonal block [o, o + s), s <= 128, of A (row stride ld) in shared
 // memory.  L in 32-wide steps: each diagonal 32 x 32 block and its inverse by
-// one warp in registers, the panel L_ib = A_ib X_kk^T and the trailing update
-// by the whole CTA; then X = L^{-1} by block substitution,
+// the whole CTA (cta_chol_inv32: a one-warp form is latency bound, about 18 us
+// per block on this GPU), then the panel L_ib = A_ib X_kk^T and the trailing
+// update; then X = L^{-1} by block substitution,
 //   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (32-blocks, i > j),
 // with the inner sums parked in the free upper blocks.  Rows beyond s are
 // identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
 // (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the first
-// failing pivot + 1 (global index) into sc->info.
+// failing pivot + 1 (global index) into sc->info.  The CTA-wide products keep
+// several independent accumulators per thread (register tiles): this kernel
+// runs once per leaf on one SM, so its latency is what counts.
 constexpr int LB = 128, LP = LB + 1;
 constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
+
+// Trailing update of the m x m block below and right of step d0 (m = 96, 64,
+// 32): L[i][j] -= sum_t L[i][d0+t] L[j][d0+t], lower part; thread (warp w,
+// lane c) owns rows w + 8 q and columns c + 32 p.
+template <int M>
+__device__ __forceinline__ void leaf_trail(float (*L)[LP], int d0) {
+    constexpr int NQ = M / 8, NPC = M / 32;
+    const int w = threadIdx.x >> 5, c = threadIdx.x & 31, b0 = d0 + NB;
+    float acc[NQ][NPC];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int p = 0; p < NPC; ++p) acc[q][p] = 0.f;
+#pragma unroll 4
+    for (int t = 0; t < NB; ++t) {
+        float lj[NPC], li[NQ];
+#pragma unroll
+        for (int p = 0; p < NPC; ++p) lj[p] = L[b0 + c + 32 * p][d0 + t];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) li[q] = L[b0 + w + 8 * q][d0 + t];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int p = 0; p < NPC; ++p) acc[q][p] = fmaf(li[q], lj[p], acc[q][p]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int p = 0; p < NPC; ++p) {
+            const int i = b0 + w + 8 * q, j = b0 + c + 32 * p;
+            if (j <= i) L[i][j] -= acc[q][p];
+        }
+}
 
 __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
                                                     int s, float *__restrict__ Xo,
@@ -393,24 +429,24 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     extern __shared__ float lsm[];
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
-    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1];
+    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1], Tt[NB][NB + 1];
     __shared__ int fshare;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, w = tid >> 5, c = tid & 31;
     for (int idx = tid; idx < LB * LB; idx += TPB) {
-        const int r = idx / LB, c = idx % LB;
+        const int r = idx / LB, cc = idx % LB;
         float v = 0.f;
-        if (r < s && c <= r) v = A[(o + r) * ld + o + c];
-        else if (r == c) v = 1.f;
-        L[r][c] = v;
-        X[r][c] = 0.f;
+        if (r < s && cc <= r) v = A[(o + r) * ld + o + cc];
+        else if (r == cc) v = 1.f;
+        L[r][cc] = v;
+        X[r][cc] = 0.f;
     }
     __syncthreads();
     for (int kb = 0; kb < LB / NB; ++kb) {
         const int d0 = kb * NB;
         for (int idx = tid; idx < NB * NB; idx += TPB) B[idx / NB][idx % NB] = L[d0 + idx / NB][d0 + idx % NB];
         __syncthreads();
-        if (tid < 32) {
-            const int f = warp_chol_inv32<float>(B, Xd, NB, nullptr);
+        {
+            const int f = cta_chol_inv32<float>(B, Xd, Tt, NB, nullptr);
             if (tid == 0) fshare = f;
         }
         __syncthreads();
@@ -419,69 +455,73 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
             return;
         }
         for (int idx = tid; idx < NB * NB; idx += TPB) {
-            const int r = idx / NB, c = idx % NB;
-            L[d0 + r][d0 + c] = B[r][c];
-            X[d0 + r][d0 + c] = Xd[r][c];
+            const int r = idx / NB, cc = idx % NB;
+            L[d0 + r][d0 + cc] = B[r][cc];
+            X[d0 + r][d0 + cc] = Xd[r][cc];
         }
-        __syncthreads();
         const int nrem = LB / NB - kb - 1;
         if (nrem == 0) break;
-        // panel rows below: L[row][d0 + c] = sum_{t <= c} L[row][d0 + t] Xd[c][t]
-        float pv[(LB - NB) * NB / TPB];
+        // panel: L[row][d0 + c] = sum_{t <= c} L[row][d0 + t] Xd[c][t]; thread
+        // (warp w, lane c) owns rows d0 + 32 + w + 8 q
+        {
+            float acc[12];
 #pragma unroll
-        for (int q = 0; q < (LB - NB) * NB / TPB; ++q) {
-            const int idx = tid + TPB * q;
-            pv[q] = 0.f;
-            if (idx < nrem * NB * NB) {
-                const int row = d0 + NB + idx / NB, c = idx % NB;
-                float acc = 0.f;
-                for (int t = 0; t <= c; ++t) acc = fmaf(L[row][d0 + t], Xd[c][t], acc);
-                pv[q] = acc;
+            for (int q = 0; q < 12; ++q) acc[q] = 0.f;
+            const int rows = nrem * NB;
+            for (int t = 0; t <= c; ++t) {
+                const float xc = Xd[c][t];
+#pragma unroll
+                for (int q = 0; q < 12; ++q)
+                    if (w + 8 * q < rows) acc[q] = fmaf(L[d0 + NB + w + 8 * q][d0 + t], xc, acc[q]);
             }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 12; ++q)
+                if (w + 8 * q < rows) L[d0 + NB + w + 8 * q][d0 + c] = acc[q];
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < (LB - NB) * NB / TPB; ++q) {
-            const int idx = tid + TPB * q;
-            if (idx < nrem * NB * NB) L[d0 + NB + idx / NB][d0 + idx % NB] = pv[q];
-        }
-        __syncthreads();
-        // trailing update of the lower part
-        const int m = LB - d0 - NB;
-        for (int idx = tid; idx < m * m; idx += TPB) {
-            const int i = d0 + NB + idx / m, j = d0 + NB + idx % m;
-            if (j <= i) {
-                float acc = 0.f;
-#pragma unroll 8
-                for (int t = 0; t < NB; ++t) acc = fmaf(L[i][d0 + t], L[j][d0 + t], acc);
-                L[i][j] -= acc;
-            }
-        }
+        if (kb == 0) leaf_trail<96>(L, d0);
+        else if (kb == 1) leaf_trail<64>(L, d0);
+        else leaf_trail<32>(L, d0);
         __syncthreads();
     }
     for (int r = tid; r < s; r += TPB) ldiag[o + r] = (double)L[r][r];
-    // X below the diagonal blocks, by distance of block row and column
+    // X below the diagonal blocks, by distance of block row and column; thread
+    // (warp w, lane c) owns rows w + 8 q (q < 4) of each block in the step
     for (int diff = 1; diff < LB / NB; ++diff) {
         const int nblk = LB / NB - diff;
-        for (int idx = tid; idx < nblk * NB * NB; idx += TPB) {
-            const int jb = idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB, ib = jb + diff;
-            float acc = 0.f;
-            for (int k = jb * NB; k < ib * NB; ++k) acc = fmaf(L[ib * NB + r][k], X[k][jb * NB + c], acc);
-            X[jb * NB + r][ib * NB + c] = acc;  // T_ij, parked in the upper block (jb, ib)
+        for (int jb = 0; jb < nblk; ++jb) {
+            const int ib = jb + diff;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = jb * NB; k < ib * NB; ++k) {
+                const float xk = X[k][jb * NB + c];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(L[ib * NB + w + 8 * q][k], xk, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) X[jb * NB + w + 8 * q][ib * NB + c] = acc[q];  // T_ij, parked
         }
         __syncthreads();
-        for (int idx = tid; idx < nblk * NB * NB; idx += TPB) {
-            const int jb = idx / (NB * NB), r = (idx / NB) % NB, c = idx % NB, ib = jb + diff;
-            float acc = 0.f;
-            for (int t = 0; t <= r; ++t) acc = fmaf(X[ib * NB + r][ib * NB + t], X[jb * NB + t][ib * NB + c], acc);
-            X[ib * NB + r][jb * NB + c] = -acc;
+        for (int jb = 0; jb < nblk; ++jb) {
+            const int ib = jb + diff;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int t = 0; t < NB; ++t) {
+                const float tv = X[jb * NB + t][ib * NB + c];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = w + 8 * q;
+                    if (t <= r) acc[q] = fmaf(X[ib * NB + r][ib * NB + t], tv, acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) X[ib * NB + w + 8 * q][jb * NB + c] = -acc[q];
         }
         __syncthreads();
     }
     for (int idx = tid; idx < s * s; idx += TPB) {
-        const int r = idx / s, c = idx % s;
-        Xo[(o + r) * ld + o + c] = (c <= r) ? X[r][c] : 0.f;
-        Xto[(o + r) * ld + o + c] = (c >= r) ? X[c][r] : 0.f;
+        const int r = idx / s, cc = idx % s;
+        Xo[(o + r) * ld + o + cc] = (cc <= r) ? X[r][cc] : 0.f;
+        Xto[(o + r) * ld + o + cc] = (cc >= r) ? X[cc][r] : 0.f;
     }
 }
 

@@ -209,13 +209,13 @@ cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, flo
                        DevScalars *sc, cudaStream_t st);
 cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t ldw, DevScalars *sc,
                      cudaStream_t st);
+cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,
+                          cudaStream_t st);
 cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
                        float *Qp, int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
                     float *Xt, int *err, cudaStream_t st);
 cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, cudaStream_t st);
-cudaError_t gemm_tn_tc(const float *P, const float *Q, int64_t n, float *C, int *err,
-                       cudaStream_t st);
 
 // ---- launchers (cd.cu) ----
 cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,

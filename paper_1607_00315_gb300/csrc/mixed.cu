@@ -368,9 +368,12 @@ cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float
     if (nt * nt > cap) return cudaErrorInvalidValue;
     cudaError_t e = pad_and_transpose(U32, n, Up, Ut, st);
     if (e != cudaSuccess) return e;
-    e = gemm_tn_tc(Up, Ut, n, U2, &sc->tc_err, st);  // U^2
+    // split-TF32 products with unbiased summation: the terms carry about
+    // (n / 8 + 2) 2^-24 relative error, so the series is usable up to a
+    // larger step than with single-TF32 products
+    e = gemm_nt_split(Up, Ut, n, p, U2, &sc->tc_err, st);  // U^2
     if (e != cudaSuccess) return e;
-    e = gemm_tn_tc(U2, Ut, n, U3, &sc->tc_err, st);  // U^3
+    e = gemm_nt_split(U2, Ut, n, p, U3, &sc->tc_err, st);  // U^3
     if (e != cudaSuccess) return e;
     const dim3 g((unsigned)nt, (unsigned)nt);
     const float *Ps[4] = {U2, U2, U2, U3};

@@ -13,7 +13,7 @@
 //  * S = X^T X / m from FP32 samples: C = Xt Xt^T with Xt = X^T (m contiguous),
 //    lower tiles only, S = C / m mirrored.
 //
-// Every wait on an mbarrier is bounded (globaltimer); on expiry the kernel
+// Every wait on an mbarrier is bounded (SM cycles); on expiry the kernel
 // records an error code, drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -51,28 +51,21 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t &I, int64_t &J) {
     J = t - i * (i + 1) / 2;
 }
 
-enum { EPI_NS = 0, EPI_SYRK = 1, EPI_STORE = 2 };
+enum { EPI_NS = 0, EPI_SYRK = 1 };
 
 // Tiles of C = P Q^T, P and Q each n_rows x K (K-major).
 // EPI_NS:    lower tiles, out[i][j] += C_ij, mirrored (out: FP64, row stride ldo)
 // EPI_SYRK:  lower tiles, out[i][j]  = scale C_ij, mirrored
-// EPI_STORE: all tiles, out32[i][j] = C_ij (FP32, row stride ldo), zero padding
-//            written for rows/columns in [n_rows, ldo)
 template <int EPI>
 __global__ void __launch_bounds__(TTHREADS, 1)
     k_tc_lower(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
                int64_t nrows, int64_t K, double *__restrict__ out, int64_t ldo, double scale,
-               int *err, float *__restrict__ out32) {
+               int *err) {
     extern __shared__ unsigned char raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t ti, tj;
-    if (EPI == EPI_STORE) {
-        ti = blockIdx.y;
-        tj = blockIdx.x;
-    } else {
-        tri_tile(blockIdx.x, ti, tj);
-    }
+    tri_tile(blockIdx.x, ti, tj);
     const int nk = (int)((K + TBK - 1) / TBK);
 
     if (threadIdx.x == 0) {
@@ -127,7 +120,8 @@ __global__ void __launch_bounds__(TTHREADS, 1)
         umma_commit(&sm.done);
     }
     __syncwarp();
-    const bool ok = mbar_wait(&sm.done, 0);
+    // warp-uniform outcome: the TMEM loads of the epilogue need the whole warp
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.done, 0));
     tc_fence_after();
     if (ok) {
         const int64_t i = ti * TBM + warp * 32 + lane;
@@ -135,15 +129,7 @@ __global__ void __launch_bounds__(TTHREADS, 1)
         for (int cb = 0; cb < TBN / 32; ++cb) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
-            if (EPI == EPI_STORE) {
-                if (i < ldo) {
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const int64_t j = tj * TBN + cb * 32 + c;
-                        if (j < ldo) out32[i * ldo + j] = (i < nrows && j < nrows) ? v[c] : 0.f;
-                    }
-                }
-            } else if (i < nrows) {
+            if (i < nrows) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     const int64_t j = tj * TBN + cb * 32 + c;
@@ -261,12 +247,11 @@ cudaError_t make_map(CUtensorMap *map, const float *base, int64_t rows, int64_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-bool g_tc_attr[3] = {false, false, false};
+bool g_tc_attr[2] = {false, false};
 
 template <int EPI>
 cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t K, int64_t ld,
-                         double *out, int64_t ldo, double scale, int *err, cudaStream_t st,
-                         float *out32 = nullptr) {
+                         double *out, int64_t ldo, double scale, int *err, cudaStream_t st) {
     if (!g_tc_attr[EPI]) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -279,14 +264,8 @@ cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t 
     e = make_map(&mq, Q, nrows, K, ld);
     if (e != cudaSuccess) return e;
     const int64_t nt = (nrows + TBM - 1) / TBM;
-    if (EPI == EPI_STORE) {
-        const int64_t ntp = (ldo + TBM - 1) / TBM;  // cover the padding too
-        k_tc_lower<EPI><<<dim3((unsigned)ntp, (unsigned)ntp), TTHREADS, TC_SMEM, st>>>(
-            mp, mq, nrows, K, out, ldo, scale, err, out32);
-    } else {
-        k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, out,
-                                                                                ldo, scale, err, out32);
-    }
+    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, out,
+                                                                            ldo, scale, err);
     counted(1);
     return cudaGetLastError();
 }
@@ -324,13 +303,6 @@ cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, c
     k_copy_pad<<<tg, tb, 0, st>>>(U, n, Up, ldp);
     counted(2);
     return cudaGetLastError();
-}
-
-// C = P Q^T for padded n x n FP32 operands (ld = tc_pad(n)), C padded FP32.
-cudaError_t gemm_tn_tc(const float *P, const float *Q, int64_t n, float *C, int *err,
-                       cudaStream_t st) {
-    const int64_t ldp = tc_pad(n);
-    return launch_lower<EPI_STORE>(P, Q, n, ldp, ldp, nullptr, ldp, 1.0, err, st, C);
 }
 
 // S = (X - mu)^T (X - mu) / m from X (m x n, FP32 or FP64 values used as TF32)

@@ -13,11 +13,9 @@ namespace ptx {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+// SM cycle counter: cheap to read, so wait loops can bound themselves by it
+// (reading the global nanosecond timer costs far more than one poll).
+__device__ __forceinline__ long long cycles() { return clock64(); }
 __device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
 }
@@ -28,7 +26,7 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t b
 // Bounded wait for the completion of the phase with the given parity.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity) {
     const uint32_t a = smem_u32(b);
-    const unsigned long long t0 = gtimer();
+    const long long t0 = cycles();
     while (true) {
         uint32_t ok;
         asm volatile(
@@ -38,7 +36,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (gtimer() - t0 > 200000000ull) return false;  // 200 ms
+        if (cycles() - t0 > 400000000ll) return false;  // about 0.2 s
     }
 }
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y,
@@ -84,6 +82,21 @@ __device__ __forceinline__ void umma_commit(unsigned long long *bar) {
                      smem_u32(bar))
                  : "memory");
 }
+// Issue a 32-lane x 32-column TMEM load without waiting (pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
