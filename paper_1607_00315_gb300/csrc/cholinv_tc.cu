@@ -51,7 +51,7 @@ struct __align__(1024) XSmem {
 };
 constexpr size_t XSMEM = sizeof(XSmem) + 1024;
 
-enum { XE_ASSIGN = 0, XE_SUB = 1, XE_SYM = 2 };
+enum { XE_ASSIGN = 0, XE_SUB = 1, XE_SYM = 2, XE_SYM64 = 3 };
 
 struct XArgs {
     int64_t M, N, K;        // output rows (rows of P), output columns (rows of Q), depth
@@ -62,7 +62,10 @@ struct XArgs {
     int epi;                // XE_ASSIGN: out = alpha C (+ outT = its transpose)
                             // XE_SUB:    out -= C on j <= i
                             // XE_SYM:    out[i][j] = out[j][i] = C on j <= i
+                            // XE_SYM64:  out64[i][j] = out64[j][i] = scale C on j <= i (FP64)
     float alpha;
+    double scale;
+    double *out64;
     float *out;
     int64_t ldo;
     float *outT;
@@ -227,11 +230,12 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                     if (a.epi == XE_ASSIGN) a.out[i * a.ldo + j] = a.alpha * v;
                     else if (j <= i) {
                         if (a.epi == XE_SUB) a.out[i * a.ldo + j] -= v;
-                        else a.out[i * a.ldo + j] = v;
+                        else if (a.epi == XE_SYM) a.out[i * a.ldo + j] = v;
+                        else a.out64[i * a.ldo + j] = a.scale * (double)v;
                     }
                 }
             }
-            if (a.outT || a.epi == XE_SYM) {
+            if (a.outT || a.epi == XE_SYM || a.epi == XE_SYM64) {
 #pragma unroll 1
                 for (int cc = wr; cc < XN; cc += 8) {
                     const int64_t j = tj * XN + cc;
@@ -243,7 +247,10 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                         if (i >= a.M) continue;
                         const float v = Ct[r][cc];
                         if (a.epi == XE_ASSIGN) a.outT[j * a.ldt + i] = a.alpha * v;
-                        else if (j < i) a.out[j * a.ldo + i] = v;
+                        else if (j < i) {
+                            if (a.epi == XE_SYM) a.out[j * a.ldo + i] = v;
+                            else a.out64[j * a.ldo + i] = a.scale * (double)v;
+                        }
                     }
                 }
             }
@@ -354,7 +361,7 @@ bool g_tcx_attr = false;
 cudaError_t tcx(const float *P, const float *Q, int64_t M, int64_t N, int64_t K, int64_t ld,
                 bool lower, int kbeg_i, int kend_i, int kend_j, bool drain, int epi, float alpha,
                 float *out, int64_t ldo, float *outT, int64_t ldt, const int *info, int *err,
-                cudaStream_t st) {
+                cudaStream_t st, double scale64 = 1.0) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (!g_tcx_attr) {
         cudaError_t e = cudaFuncSetAttribute(k_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XSMEM);
@@ -379,12 +386,19 @@ cudaError_t tcx(const float *P, const float *Q, int64_t M, int64_t N, int64_t K,
     a.drain = drain ? 1 : 0;
     a.epi = epi;
     a.alpha = alpha;
+    a.scale = 0.0;
+    a.out64 = nullptr;
     a.out = out;
     a.ldo = ldo;
     a.outT = outT;
     a.ldt = ldt;
     a.info = info;
     a.err = err;
+    if (epi == XE_SYM64) {
+        a.out64 = reinterpret_cast<double *>(out);
+        a.scale = scale64;
+        a.out = nullptr;
+    }
     const int64_t grid = lower ? tm * (tm + 1) / 2 : tm * tn;
     k_tcx<<<(unsigned)grid, XTHREADS, XSMEM, st>>>(mp, mq, a);
     counted(1);
@@ -457,6 +471,15 @@ cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld,
                           cudaStream_t st) {
     return tcx(P, Q, n, n, n, ld, false, 0, 0, 0, true, XE_ASSIGN, 1.f, C, ld, nullptr, 0, nullptr,
                err, st);
+}
+
+// S = scale Xt Xt^T (FP64, row stride n, mirrored) from Xt (n x m FP32, row
+// stride ldx), split TF32 with unbiased summation (eq. cov_estimate: Xt holds
+// the centred samples transposed, scale = 1 / m).
+cudaError_t syrk_split(const float *Xt, int64_t n, int64_t m, int64_t ldx, double scale, double *S,
+                       int *err, cudaStream_t st) {
+    return tcx(Xt, Xt, n, n, m, ldx, true, 0, 0, 0, true, XE_SYM64, 1.f,
+               reinterpret_cast<float *>(S), n, nullptr, 0, nullptr, err, st, scale);
 }
 
 // W = Xt Xt^T (= X^T X = A^{-1}), lower tiles mirrored, W row stride ldw.

@@ -211,6 +211,8 @@ cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t l
                      cudaStream_t st);
 cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,
                           cudaStream_t st);
+cudaError_t syrk_split(const float *Xt, int64_t n, int64_t m, int64_t ldx, double scale, double *S,
+                       int *err, cudaStream_t st);
 cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
                        float *Qp, int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,

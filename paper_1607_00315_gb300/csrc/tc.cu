@@ -7,11 +7,12 @@
 // warp 0 lane 0 issues the TMA loads, warp 1 lane 0 issues the MMAs, all four
 // warps drain the accumulator (warp w owns TMEM lanes 32w .. 32w + 31).
 //
-// Uses:
-//  * Newton-Schulz refinement of W (mixed precision): C = W R, computed as
-//    W Q^T with Q = R^T, lower tiles only (C is symmetric), W64 += C mirrored;
-//  * S = X^T X / m from FP32 samples: C = Xt Xt^T with Xt = X^T (m contiguous),
-//    lower tiles only, S = C / m mirrored.
+// Use: the Newton-Schulz refinement of W (mixed precision): C = W R, computed
+// as W Q^T with Q = R^T, lower tiles only (C is symmetric), W64 += C
+// mirrored.  (The correction is small next to W, so single TF32 products
+// suffice here; the factorisation and S use the split-TF32 kernel of
+// cholinv_tc.cu.)  This file also packs the operands and encodes the tensor
+// maps used by both kernels.
 //
 // Every wait on an mbarrier is bounded (SM cycles); on expiry the kernel
 // records an error code, drains what it issued, frees its TMEM and returns.
@@ -51,15 +52,14 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t &I, int64_t &J) {
     J = t - i * (i + 1) / 2;
 }
 
-enum { EPI_NS = 0, EPI_SYRK = 1 };
+enum { EPI_NS = 0 };
 
 // Tiles of C = P Q^T, P and Q each n_rows x K (K-major).
 // EPI_NS:    lower tiles, out[i][j] += C_ij, mirrored (out: FP64, row stride ldo)
-// EPI_SYRK:  lower tiles, out[i][j]  = scale C_ij, mirrored
 template <int EPI>
 __global__ void __launch_bounds__(TTHREADS, 1)
     k_tc_lower(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
-               int64_t nrows, int64_t K, double *__restrict__ out, int64_t ldo, double scale,
+               int64_t nrows, int64_t K, double *__restrict__ out, int64_t ldo,
                int *err) {
     extern __shared__ unsigned char raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
@@ -134,9 +134,7 @@ __global__ void __launch_bounds__(TTHREADS, 1)
                 for (int c = 0; c < 32; ++c) {
                     const int64_t j = tj * TBN + cb * 32 + c;
                     if (j < nrows && j <= i) {
-                        double w;
-                        if (EPI == EPI_NS) w = out[i * ldo + j] + (double)v[c];
-                        else w = scale * (double)v[c];
+                        const double w = out[i * ldo + j] + (double)v[c];
                         out[i * ldo + j] = w;
                         if (i != j) out[j * ldo + i] = w;
                     }
@@ -247,11 +245,11 @@ cudaError_t make_map(CUtensorMap *map, const float *base, int64_t rows, int64_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-bool g_tc_attr[2] = {false, false};
+bool g_tc_attr[1] = {false};
 
 template <int EPI>
 cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t K, int64_t ld,
-                         double *out, int64_t ldo, double scale, int *err, cudaStream_t st) {
+                         double *out, int64_t ldo, int *err, cudaStream_t st) {
     if (!g_tc_attr[EPI]) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -265,7 +263,7 @@ cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t 
     if (e != cudaSuccess) return e;
     const int64_t nt = (nrows + TBM - 1) / TBM;
     k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, out,
-                                                                            ldo, scale, err);
+                                                                            ldo, err);
     counted(1);
     return cudaGetLastError();
 }
@@ -292,7 +290,7 @@ cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W
     const dim3 tg((unsigned)(ldp / 32), (unsigned)(ldp / 32)), tb(32, 8);
     k_transpose_pad<<<tg, tb, 0, st>>>(R32, n, Qp, ldp);
     counted(2);
-    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, W64out, n, 1.0, err, st);
+    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, W64out, n, err, st);
 }
 
 // Up = U padded (ld = tc_pad(n)), Ut = U^T padded.
@@ -305,8 +303,9 @@ cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, c
     return cudaGetLastError();
 }
 
-// S = (X - mu)^T (X - mu) / m from X (m x n, FP32 or FP64 values used as TF32)
-// on the tensor cores; Xt is scratch of n x tc_pad(m) floats.
+// S = (X - mu)^T (X - mu) / m from X (m x n, FP32 or FP64 values rounded to
+// FP32) on the tensor cores, split TF32 with unbiased summation; Xt is
+// scratch of n x tc_pad(m) floats.
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
                     float *Xt, int *err, cudaStream_t st) {
     const int64_t ldp = tc_pad(m);
@@ -316,7 +315,7 @@ cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double
     else
         k_xt_pad<double><<<tg, tb, 0, st>>>((const double *)X, m, n, mu, Xt, ldp);
     counted(1);
-    return launch_lower<EPI_SYRK>(Xt, Xt, n, ldp, ldp, S, n, 1.0 / (double)m, err, st);
+    return syrk_split(Xt, n, m, ldp, 1.0 / (double)m, S, err, st);
 }
 
 }  // namespace glx
