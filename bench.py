@@ -1,14 +1,15 @@
 """Benchmark: time to relative KKT 1e-5 per solve on the n = 2000 sparse-Theta
-workload (m = 1000 Gaussian samples, lambda = 0.1), one step = one complete
-solve from the samples X (forming S = X^T X / m, then ML-cycles of the
-proximal-Newton relaxation until rel. KKT <= 1e-5).
+workload (m = 1000 Gaussian samples, lambda = 0.1, FP64 S), one step = one
+complete solve from the FP64 covariance S (ML-cycles of the proximal-Newton
+relaxation until rel. KKT <= 1e-5).  S is formed once on the GPU from the
+samples before timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
     python bench.py --impl reference ...    (the FP64 CPU oracle, same metric)
 
-Prints one JSON line (rank 0).  `value` is whole-job solves/s with X already
-resident in HBM; `e2e` is the same metric through the public API with host
-buffers (X copied in, A copied out, inside the timed region).
+Prints one JSON line (rank 0).  `value` is whole-job solves/s with S already
+resident in HBM; `e2e` is the same metric through the public API with pinned
+host buffers (S copied in, A copied out, inside the timed region).
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to rel. KKT 1e-5 per solve (mixed vs FP64 GPU); solves/sec, p50/p99 latency"
 CONFIG_ID = 2
+WORKLOAD = "sparse-Theta n=2000 m=1000 lambda=0.1, fp64 S given, to rel. KKT 1e-5"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -125,14 +127,11 @@ def job_value(local_ms, steps, world, device):
 
 
 def oracle_relaxation_sample(p, S, n_relax=1):
-    """Time the FP64 oracle on a bounded sample of the same workload: forming S
-    and `n_relax` level-0 relaxations (Cholesky, inverse, free set + KKT, one
-    CD sweep, line search).  Returns (t_form_S, t_per_relaxation)."""
+    """Time the FP64 oracle on a bounded sample of the same workload (S given):
+    `n_relax` level-0 relaxations (Cholesky, inverse, free set + KKT, one CD
+    sweep, line search).  Returns the mean time per relaxation."""
     import oracle
 
-    t0 = time.perf_counter()
-    oracle.form_S(p.X)
-    t_S = time.perf_counter() - t0
     A = np.diag(1.0 / (np.diag(S) + p.lam))
     _, F = oracle.objective(S, A, p.lam)
     t_rel = []
@@ -145,7 +144,7 @@ def oracle_relaxation_sample(p, S, n_relax=1):
         D, _ = oracle.cd_sweeps(S, W, A, p.lam, fi, fj, 1)
         rc, A, F, _, _ = oracle.line_search(S, W, A, p.lam, fi, fj, D, F)
         t_rel.append(time.perf_counter() - t0)
-    return t_S, float(np.mean(t_rel))
+    return float(np.mean(t_rel))
 
 
 def oracle_relaxations_per_solve():
@@ -188,24 +187,23 @@ def run_reference(args):
     R, R_src = oracle_relaxations_per_solve()
     times = []
     for k in range(args.warmup + args.steps):
-        t_S, t_rel = oracle_relaxation_sample(p, S, 1)
+        t_rel = oracle_relaxation_sample(p, S, 1)
         if k >= args.warmup:
-            times.append((t_S, t_rel))
-    t_S = float(np.mean([t[0] for t in times]))
-    t_rel = float(np.mean([t[1] for t in times]))
-    per_solve = t_S + (R or 0) * t_rel
+            times.append(t_rel)
+    t_rel = float(np.mean(times))
+    per_solve = (R or 0) * t_rel
     value = (1.0 / per_solve) if R else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_solve * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"sparse-Theta n=2000 m=1000 lambda=0.1 to rel. KKT 1e-5",
-                   "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol},
+        "config": {"workload": WORKLOAD, "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol,
+                   "input": "S (fp64) given"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: S = X^T X/m plus one level-0 relaxation of the "
-                                   f"oracle ({t_rel:.2f} s); solve time = t_S + R x t_relax with "
-                                   f"R = {R} relaxations from the {R_src}"},
+                         "sample": f"per step: one level-0 relaxation of the oracle from the same "
+                                   f"S ({t_rel:.2f} s); solve time = R x t_relax with R = {R} "
+                                   f"relaxations from the {R_src}"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -224,6 +222,9 @@ def main():
                     help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="open the CUDA profiler range around the timed solves only "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -243,16 +244,20 @@ def main():
     dev = torch.device("cuda", local)
     # independent instances per rank (weak scaling, no data-path collective)
     p = synth.config_problem(CONFIG_ID, instance=rank)
-    X = torch.from_numpy(p.X).to(dev)
     prec = glasso.FP64 if args.precision == "fp64" else glasso.MIXED
     ctx = glasso.Context(local, precision=prec)
     stream = torch.cuda.current_stream(dev)
     ctx.set_stream(stream.cuda_stream)
+    # the workload's input is the FP64 covariance S (eq. cov_estimate), formed
+    # once on the GPU from the samples, outside the timed region
+    S = torch.empty((p.n, p.n), dtype=torch.float64, device=dev)
+    glasso.Context(local).form_S(torch.from_numpy(p.X).to(dev), S)
+    torch.cuda.synchronize()
     A_out = torch.empty((p.n, p.n), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        _, _, info = ctx.solve(X, p.lam, tol=p.tol, samples=True, A_out=A_out)
+        _, _, info = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out)
         return info
 
     for _ in range(max(args.warmup, 3)):
@@ -263,6 +268,8 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.start()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1.0)  # evict the L2 between timed steps
@@ -274,6 +281,8 @@ def main():
             torch.cuda.synchronize()
             lat.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     prof = ctx.get_profile(reset=True)
@@ -288,14 +297,14 @@ def main():
         octx.set_stream(stream.cuda_stream)
         oinfo = None
         for _ in range(2):
-            _, _, oinfo = octx.solve(X, p.lam, tol=p.tol, samples=True, A_out=A_out)
+            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out)
         olat = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, _, oinfo = octx.solve(X, p.lam, tol=p.tol, samples=True, A_out=A_out)
+            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out)
             e1.record(stream)
             torch.cuda.synchronize()
             olat.append(e0.elapsed_time(e1))
@@ -307,13 +316,13 @@ def main():
                    f"{oname}_solve": {"relaxations": oinfo["relaxations"], "rel_kkt": oinfo["rel_kkt"],
                                       "objective": oinfo["objective"]}}
 
-    # end to end through the public API with host buffers
-    Xh = np.ascontiguousarray(p.X)
-    Ah = np.empty((p.n, p.n))
+    # end to end through the public API with host buffers (pinned): S in, A out
+    Sh = S.cpu().pin_memory().numpy()
+    Ah = torch.empty((p.n, p.n), dtype=torch.float64).pin_memory().numpy()
     e2e = []
     for _ in range(max(1, args.e2e_steps)):
         t0 = time.perf_counter()
-        ctx.solve(Xh, p.lam, tol=p.tol, samples=True, A_out=Ah)
+        ctx.solve(Sh, p.lam, tol=p.tol, A_out=Ah)
         e2e.append(time.perf_counter() - t0)
     _, e2e_value = job_value(sum(e2e) * 1e3, len(e2e), world, dev)
 
@@ -362,8 +371,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "mixed(f32/tf32+f64)",
         "data": "synthetic",
-        "config": {"workload": "sparse-Theta n=2000 m=1000 lambda=0.1 to rel. KKT 1e-5",
-                   "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol, "input": "samples X (fp64)",
+        "config": {"workload": WORKLOAD,
+                   "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol, "input": "S (fp64) given",
                    "precision": args.precision, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -373,7 +382,7 @@ def main():
                   "objective": infos[-1]["objective"], "nnz": infos[-1]["nnz"]},
         "time_share": share,
         "compare": compare,
-        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Xh.nbytes),
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Sh.nbytes),
                 "d2h_bytes_per_step": int(Ah.nbytes)},
         "gpu_launches": int(prof["kernels"]),
         "roofline": roof,
@@ -383,15 +392,14 @@ def main():
         import oracle
 
         oracle.build()
-        S = oracle.form_S(p.X)
-        t_S, t_rel = oracle_relaxation_sample(p, S, 2)
+        S_h = S.cpu().numpy()
+        t_rel = oracle_relaxation_sample(p, S_h, 2)
         R = infos[-1]["relaxations"]
-        per = t_S + R * t_rel
+        per = R * t_rel
         line["cpu_baseline"] = {
             "value": 1.0 / per, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"S = X^T X/m ({t_S:.2f} s) and 2 level-0 relaxations ({t_rel:.2f} s each) "
-                      f"of the FP64 oracle on this workload; solve = t_S + {R} x t_relax, "
-                      f"{R} = relaxations of this solve"}
+            "sample": f"2 level-0 relaxations ({t_rel:.2f} s each) of the FP64 oracle from the "
+                      f"same S; solve = {R} x t_relax, {R} = relaxations of this solve"}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -375,9 +375,10 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 // Leaf of the tensor-core factorisation (FP32): one CTA factors and inverts
 // the diagonal block [o, o + s), s <= 128, of A (row stride ld) in shared
 // memory.  L in 32-wide steps: each diagonal 32 x 32 block and its inverse by
-// the whole CTA (cta_chol_inv32: a one-warp form is latency bound, about 18 us
-// per block on this GPU), then the panel L_ib = A_ib X_kk^T and the trailing
-// update; then X = L^{-1} by block substitution,
+// one warp in 8-wide sub-steps (warp_chol_inv32_blk; column-at-a-time forms,
+// one warp or the whole CTA, took about 18 us per block on this GPU), then the
+// panel L_ib = A_ib X_kk^T and the trailing update by the CTA; then X = L^{-1}
+// by block substitution,
 //   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (32-blocks, i > j),
 // with the inner sums parked in the free upper blocks.  Rows beyond s are
 // identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
@@ -387,6 +388,167 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 // runs once per leaf on one SM, so its latency is what counts.
 constexpr int LB = 128, LP = LB + 1;
 constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
+
+// One thread: Cholesky of the 8 x 8 lower block a (registers) in place and
+// x = L^{-1}; rd[i] = 1 / L_ii.  Returns 0 or the failing pivot + 1.
+__device__ __forceinline__ int thread_chol_inv8(float (&a)[8][8], float (&x)[8][8], float (&rd)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float d = a[j][j];
+        if (!(d > 0.f)) return j + 1;
+        const float r = rsqrt_newton(d);
+        rd[j] = r;
+        a[j][j] = d * r;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i) a[i][j] *= r;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+            for (int k = j + 1; k <= i; ++k) a[i][k] = fmaf(-a[i][j], a[k][j], a[i][k]);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < c) {
+                x[i][c] = 0.f;
+            } else {
+                float s = (i == c) ? 1.f : 0.f;
+#pragma unroll
+                for (int t = c; t < i; ++t) s = fmaf(-a[i][t], x[t][c], s);
+                x[i][c] = s * rd[i];
+            }
+        }
+    return 0;
+}
+
+// One warp: Cholesky of the 32 x 32 block B (lower, row stride NB + 1) in
+// place and Xs = L^{-1}, both with zero upper triangles, in 8-wide steps: one
+// lane factors and inverts each 8 x 8 diagonal block in registers, the warp
+// forms the sub-panel (L_ik = A_ik X_kk^T) and the trailing update; then the
+// off-diagonal 8-blocks of the inverse by substitution,
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj.  The serial path is four 8 x 8
+// factorisations, not 32 dependent column steps.  Returns 0 or pivot + 1.
+__device__ int warp_chol_inv32_blk(float (*B)[NB + 1], float (*Xs)[NB + 1], int *fflag) {
+    const int lane = threadIdx.x & 31;
+    for (int kb = 0; kb < 4; ++kb) {
+        const int o = 8 * kb;
+        if (lane == 0) {
+            float a[8][8], x[8][8], rd[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? B[o + i][o + j] : 0.f;
+            const int f = thread_chol_inv8(a, x, rd);
+            *fflag = f ? o + f : 0;
+            if (!f) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        B[o + i][o + j] = (j <= i) ? a[i][j] : 0.f;
+                        Xs[o + i][o + j] = x[i][j];
+                    }
+            }
+        }
+        __syncwarp();
+        const int f = *fflag;
+        if (f) return f;
+        const int rows = NB - o - 8;  // rows below the diagonal block
+        if (rows == 0) break;
+        // sub-panel: L[r][o + c] = sum_{t <= c} B[r][o + t] Xs[o + c][o + t]
+        float pv[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            pv[q] = 0.f;
+            if (idx < rows * 8) {
+                const int r = o + 8 + idx / 8, c = idx % 8;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (t <= c) acc = fmaf(B[r][o + t], Xs[o + c][o + t], acc);
+                pv[q] = acc;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            if (idx < rows * 8) B[o + 8 + idx / 8][o + idx % 8] = pv[q];
+        }
+        __syncwarp();
+        // trailing update: lane owns column j = o + 8 + lane, rows i >= j
+        if (lane < rows) {
+            const int j = o + 8 + lane;
+            float lj[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) lj[t] = B[j][o + t];
+            for (int i = j; i < NB; ++i) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc = fmaf(B[i][o + t], lj[t], acc);
+                B[i][j] -= acc;
+            }
+        }
+        __syncwarp();
+    }
+    // off-diagonal 8-blocks of the inverse, by block distance
+    for (int diff = 1; diff < 4; ++diff) {
+        const int nblk = 4 - diff;
+        // T_ij = sum_{k = 8 jb}^{8 ib - 1} L[8 ib + r][k] X[k][8 jb + c], parked in the upper block
+        float tv[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            tv[q] = 0.f;
+            if (idx < nblk * 64) {
+                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
+                float acc = 0.f;
+                for (int k = 8 * jb; k < 8 * ib; ++k) acc = fmaf(B[8 * ib + r][k], Xs[k][8 * jb + c], acc);
+                tv[q] = acc;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            if (idx < nblk * 64) {
+                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
+                Xs[8 * jb + r][8 * ib + c] = tv[q];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            if (idx < nblk * 64) {
+                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (t <= r) acc = fmaf(Xs[8 * ib + r][8 * ib + t], Xs[8 * jb + t][8 * ib + c], acc);
+                tv[q] = -acc;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int idx = lane + 32 * q;
+            if (idx < nblk * 64) {
+                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
+                Xs[8 * ib + r][8 * jb + c] = tv[q];
+            }
+        }
+        __syncwarp();
+    }
+    // zero the upper triangle of the inverse (it held the parked sums)
+    for (int idx = lane; idx < NB * NB; idx += 32) {
+        const int r = idx / NB, c = idx % NB;
+        if (c > r) Xs[r][c] = 0.f;
+    }
+    __syncwarp();
+    return 0;
+}
 
 // Trailing update of the m x m block below and right of step d0 (m = 96, 64,
 // 32): L[i][j] -= sum_t L[i][d0+t] L[j][d0+t], lower part; thread (warp w,
@@ -429,8 +591,8 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     extern __shared__ float lsm[];
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
-    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1], Tt[NB][NB + 1];
-    __shared__ int fshare;
+    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1];
+    __shared__ int fshare, fflag;
     const int tid = threadIdx.x, w = tid >> 5, c = tid & 31;
     for (int idx = tid; idx < LB * LB; idx += TPB) {
         const int r = idx / LB, cc = idx % LB;
@@ -445,9 +607,9 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
         const int d0 = kb * NB;
         for (int idx = tid; idx < NB * NB; idx += TPB) B[idx / NB][idx % NB] = L[d0 + idx / NB][d0 + idx % NB];
         __syncthreads();
-        {
-            const int f = cta_chol_inv32<float>(B, Xd, Tt, NB, nullptr);
-            if (tid == 0) fshare = f;
+        if (w == 0) {
+            const int f = warp_chol_inv32_blk(B, Xd, &fflag);
+            if (c == 0) fshare = f;
         }
         __syncthreads();
         if (fshare) {
