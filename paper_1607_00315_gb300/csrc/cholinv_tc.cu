@@ -101,10 +101,12 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
 // FP32 ulp of the accumulator per step, toward zero), which over a long k
 // range becomes a systematic relative error of (k / 8) 2^-24 -- harmless for
 // the inverse (refined afterwards) but not for a log-determinant summed over
-// n pivots.  With `drain`, the main product hi hi of every 8-wide step goes
-// to a fresh TMEM buffer (three in rotation) that the drain warps add into
-// FP32 registers with round-to-nearest; the small hi lo + lo hi terms keep
-// one TMEM accumulator.  Without it, all products accumulate in TMEM.
+// n pivots.  With `drain`, the main product hi hi of every pair of 8-wide
+// steps goes to a fresh TMEM buffer (three in rotation) that the drain warps
+// add into FP32 registers with round-to-nearest (measured bias: about one
+// ulp of each 16-wide partial, independent of k); the small hi lo + lo hi
+// terms keep one TMEM accumulator.  Without it, all products accumulate in
+// TMEM.
 __global__ void __launch_bounds__(XTHREADS, 1)
     k_tcx(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
           const XArgs a) {
@@ -165,12 +167,12 @@ __global__ void __launch_bounds__(XTHREADS, 1)
         for (int c = 0; c < HC; ++c) acc[c] = 0.f;
         if (nk > 0) {
             if (drain) {
-                // add the main product of every 8-wide step (round to nearest)
-                const int nsteps = nk * (XK / 8);
-                for (int step = 0; step < nsteps; ++step) {
-                    const int b = step % XNB;
+                // add the main product of every pair of 8-wide steps (round to nearest)
+                const int npairs = nk * (XK / 16);
+                for (int pr = 0; pr < npairs; ++pr) {
+                    const int b = pr % XNB;
                     // warp-uniform outcome: the TMEM loads below need the whole warp
-                    const bool got = __all_sync(0xffffffffu, mbar_wait(&sm.mfull[b], (step / XNB) & 1));
+                    const bool got = __all_sync(0xffffffffu, mbar_wait(&sm.mfull[b], (pr / XNB) & 1));
                     if (!got) {
                         if (lane == 0) atomicExch(a.err, 16);
                         break;
@@ -287,15 +289,18 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                 for (int kk = 0; kk < XK / 8; ++kk) {
                     const uint32_t first = (kt | kk) != 0;
                     if (drain) {
-                        const int step = kt * (XK / 8) + kk, b = step % XNB;
-                        if (step >= XNB && !mbar_wait(&sm.mfree[b], ((step / XNB) & 1) ^ 1)) {
+                        // pair p of 8-wide steps into buffer p % XNB
+                        const int step = kt * (XK / 8) + kk, pr = step >> 1, b = pr % XNB;
+                        if ((step & 1) == 0 && pr >= XNB &&
+                            !mbar_wait(&sm.mfree[b], ((pr / XNB) & 1) ^ 1)) {
                             atomicExch(a.err, 15);
                             mok = false;
                             break;
                         }
                         tc_fence_after();
-                        umma_tf32(tmem + 128u * (uint32_t)(b + 1), ah + 2ull * kk, bh + 2ull * kk, idesc, 0u);
-                        umma_commit(&sm.mfull[b]);
+                        umma_tf32(tmem + 128u * (uint32_t)(b + 1), ah + 2ull * kk, bh + 2ull * kk, idesc,
+                                  (uint32_t)(step & 1));
+                        if (step & 1) umma_commit(&sm.mfull[b]);
                         umma_tf32(tmem, ah + 2ull * kk, bl + 2ull * kk, idesc, first);
                     } else {
                         umma_tf32(tmem, ah + 2ull * kk, bh + 2ull * kk, idesc, first);

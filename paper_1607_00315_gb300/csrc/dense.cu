@@ -374,19 +374,18 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 
 // Leaf of the tensor-core factorisation (FP32): one CTA factors and inverts
 // the diagonal block [o, o + s), s <= 128, of A (row stride ld) in shared
-// memory.  L in 32-wide steps: each diagonal 32 x 32 block and its inverse by
-// one warp in 8-wide sub-steps (warp_chol_inv32_blk; column-at-a-time forms,
-// one warp or the whole CTA, took about 18 us per block on this GPU), then the
-// panel L_ib = A_ib X_kk^T and the trailing update by the CTA; then X = L^{-1}
-// by block substitution,
-//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (32-blocks, i > j),
+// memory, in 8-wide steps: one thread factors and inverts each 8 x 8 diagonal
+// block in registers (the serial path: 16 such blocks), then the CTA forms
+// the panel L_ib = A_ib X_kk^T and the trailing update.  X = L^{-1} then
+// follows by 8-block substitution,
+//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (i > j),
 // with the inner sums parked in the free upper blocks.  Rows beyond s are
 // identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
-// (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the first
-// failing pivot + 1 (global index) into sc->info.  The CTA-wide products keep
-// several independent accumulators per thread (register tiles): this kernel
-// runs once per leaf on one SM, so its latency is what counts.
-constexpr int LB = 128, LP = LB + 1;
+// (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the
+// first failing pivot + 1 (global index) into sc->info.  (Column-at-a-time
+// forms of 32-wide diagonal blocks -- one warp or the whole CTA -- took about
+// 18 us per block on this GPU: long dependent chains through shared memory.)
+constexpr int LB = 128, LP = LB + 4;  // rows padded to 16-byte multiples
 constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
 
 // One thread: Cholesky of the 8 x 8 lower block a (registers) in place and
@@ -422,167 +421,6 @@ __device__ __forceinline__ int thread_chol_inv8(float (&a)[8][8], float (&x)[8][
     return 0;
 }
 
-// One warp: Cholesky of the 32 x 32 block B (lower, row stride NB + 1) in
-// place and Xs = L^{-1}, both with zero upper triangles, in 8-wide steps: one
-// lane factors and inverts each 8 x 8 diagonal block in registers, the warp
-// forms the sub-panel (L_ik = A_ik X_kk^T) and the trailing update; then the
-// off-diagonal 8-blocks of the inverse by substitution,
-// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj.  The serial path is four 8 x 8
-// factorisations, not 32 dependent column steps.  Returns 0 or pivot + 1.
-__device__ int warp_chol_inv32_blk(float (*B)[NB + 1], float (*Xs)[NB + 1], int *fflag) {
-    const int lane = threadIdx.x & 31;
-    for (int kb = 0; kb < 4; ++kb) {
-        const int o = 8 * kb;
-        if (lane == 0) {
-            float a[8][8], x[8][8], rd[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? B[o + i][o + j] : 0.f;
-            const int f = thread_chol_inv8(a, x, rd);
-            *fflag = f ? o + f : 0;
-            if (!f) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        B[o + i][o + j] = (j <= i) ? a[i][j] : 0.f;
-                        Xs[o + i][o + j] = x[i][j];
-                    }
-            }
-        }
-        __syncwarp();
-        const int f = *fflag;
-        if (f) return f;
-        const int rows = NB - o - 8;  // rows below the diagonal block
-        if (rows == 0) break;
-        // sub-panel: L[r][o + c] = sum_{t <= c} B[r][o + t] Xs[o + c][o + t]
-        float pv[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            pv[q] = 0.f;
-            if (idx < rows * 8) {
-                const int r = o + 8 + idx / 8, c = idx % 8;
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (t <= c) acc = fmaf(B[r][o + t], Xs[o + c][o + t], acc);
-                pv[q] = acc;
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            if (idx < rows * 8) B[o + 8 + idx / 8][o + idx % 8] = pv[q];
-        }
-        __syncwarp();
-        // trailing update: lane owns column j = o + 8 + lane, rows i >= j
-        if (lane < rows) {
-            const int j = o + 8 + lane;
-            float lj[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) lj[t] = B[j][o + t];
-            for (int i = j; i < NB; ++i) {
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc = fmaf(B[i][o + t], lj[t], acc);
-                B[i][j] -= acc;
-            }
-        }
-        __syncwarp();
-    }
-    // off-diagonal 8-blocks of the inverse, by block distance
-    for (int diff = 1; diff < 4; ++diff) {
-        const int nblk = 4 - diff;
-        // T_ij = sum_{k = 8 jb}^{8 ib - 1} L[8 ib + r][k] X[k][8 jb + c], parked in the upper block
-        float tv[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            tv[q] = 0.f;
-            if (idx < nblk * 64) {
-                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
-                float acc = 0.f;
-                for (int k = 8 * jb; k < 8 * ib; ++k) acc = fmaf(B[8 * ib + r][k], Xs[k][8 * jb + c], acc);
-                tv[q] = acc;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            if (idx < nblk * 64) {
-                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
-                Xs[8 * jb + r][8 * ib + c] = tv[q];
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            if (idx < nblk * 64) {
-                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (t <= r) acc = fmaf(Xs[8 * ib + r][8 * ib + t], Xs[8 * jb + t][8 * ib + c], acc);
-                tv[q] = -acc;
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int idx = lane + 32 * q;
-            if (idx < nblk * 64) {
-                const int jb = idx / 64, r = (idx / 8) % 8, c = idx % 8, ib = jb + diff;
-                Xs[8 * ib + r][8 * jb + c] = tv[q];
-            }
-        }
-        __syncwarp();
-    }
-    // zero the upper triangle of the inverse (it held the parked sums)
-    for (int idx = lane; idx < NB * NB; idx += 32) {
-        const int r = idx / NB, c = idx % NB;
-        if (c > r) Xs[r][c] = 0.f;
-    }
-    __syncwarp();
-    return 0;
-}
-
-// Trailing update of the m x m block below and right of step d0 (m = 96, 64,
-// 32): L[i][j] -= sum_t L[i][d0+t] L[j][d0+t], lower part; thread (warp w,
-// lane c) owns rows w + 8 q and columns c + 32 p.
-template <int M>
-__device__ __forceinline__ void leaf_trail(float (*L)[LP], int d0) {
-    constexpr int NQ = M / 8, NPC = M / 32;
-    const int w = threadIdx.x >> 5, c = threadIdx.x & 31, b0 = d0 + NB;
-    float acc[NQ][NPC];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int p = 0; p < NPC; ++p) acc[q][p] = 0.f;
-#pragma unroll 4
-    for (int t = 0; t < NB; ++t) {
-        float lj[NPC], li[NQ];
-#pragma unroll
-        for (int p = 0; p < NPC; ++p) lj[p] = L[b0 + c + 32 * p][d0 + t];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) li[q] = L[b0 + w + 8 * q][d0 + t];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-            for (int p = 0; p < NPC; ++p) acc[q][p] = fmaf(li[q], lj[p], acc[q][p]);
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int p = 0; p < NPC; ++p) {
-            const int i = b0 + w + 8 * q, j = b0 + c + 32 * p;
-            if (j <= i) L[i][j] -= acc[q][p];
-        }
-}
-
 __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
                                                     int s, float *__restrict__ Xo,
                                                     float *__restrict__ Xto, double *__restrict__ ldiag,
@@ -591,101 +429,212 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     extern __shared__ float lsm[];
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
-    __shared__ float B[NB][NB + 1], Xd[NB][NB + 1];
-    __shared__ int fshare, fflag;
-    const int tid = threadIdx.x, w = tid >> 5, c = tid & 31;
-    for (int idx = tid; idx < LB * LB; idx += TPB) {
-        const int r = idx / LB, cc = idx % LB;
-        float v = 0.f;
-        if (r < s && cc <= r) v = A[(o + r) * ld + o + cc];
-        else if (r == cc) v = 1.f;
-        L[r][cc] = v;
-        X[r][cc] = 0.f;
-    }
-    __syncthreads();
-    for (int kb = 0; kb < LB / NB; ++kb) {
-        const int d0 = kb * NB;
-        for (int idx = tid; idx < NB * NB; idx += TPB) B[idx / NB][idx % NB] = L[d0 + idx / NB][d0 + idx % NB];
-        __syncthreads();
-        if (w == 0) {
-            const int f = warp_chol_inv32_blk(B, Xd, &fflag);
-            if (c == 0) fshare = f;
+    __shared__ int fshare;
+    const int tid = threadIdx.x;
+    // 16-byte loads of the rows (the block starts at a multiple of 128 in a
+    // matrix whose row stride is a multiple of 32 floats), all issued at once
+#pragma unroll
+    for (int q = 0; q < LB * LB / 4 / TPB; ++q) {
+        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < s && c4 <= r) {
+            if (c4 + 3 < s) {
+                v = *reinterpret_cast<const float4 *>(A + (o + r) * ld + o + c4);
+            } else {
+                v.x = A[(o + r) * ld + o + c4];
+                if (c4 + 1 < s) v.y = A[(o + r) * ld + o + c4 + 1];
+                if (c4 + 2 < s) v.z = A[(o + r) * ld + o + c4 + 2];
+            }
         }
-        __syncthreads();
+        float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cc = c4 + k;
+            L[r][cc] = (cc <= r && r < s) ? e[k] : (r == cc ? 1.f : 0.f);
+        }
+        *reinterpret_cast<float4 *>(&X[r][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid == 0) fshare = 0;
+    __syncthreads();
+    // one thread: factor and invert the 8 x 8 diagonal block at d (registers)
+    auto diag8 = [&](int d) {
+        float a[8][8], x[8][8], rd[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
+        const int f = thread_chol_inv8(a, x, rd);
+        if (f) {
+            fshare = d + f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j <= i) L[d + i][d + j] = a[i][j];
+                    X[d + i][d + j] = x[i][j];
+                }
+        }
+    };
+    if (tid == 0) diag8(0);
+    __syncthreads();
+    for (int d0 = 0; d0 < LB; d0 += 8) {
+        // diagonal block d0 is factored (look-ahead from the previous step)
         if (fshare) {
-            if (tid == 0) atomicCAS(&sc->info, 0, (int)(o + d0 + fshare));
+            if (tid == 0) atomicCAS(&sc->info, 0, (int)(o + fshare));
             return;
         }
-        for (int idx = tid; idx < NB * NB; idx += TPB) {
-            const int r = idx / NB, cc = idx % NB;
-            L[d0 + r][d0 + cc] = B[r][cc];
-            X[d0 + r][d0 + cc] = Xd[r][cc];
-        }
-        const int nrem = LB / NB - kb - 1;
-        if (nrem == 0) break;
-        // panel: L[row][d0 + c] = sum_{t <= c} L[row][d0 + t] Xd[c][t]; thread
-        // (warp w, lane c) owns rows d0 + 32 + w + 8 q
-        {
-            float acc[12];
+        const int R = LB - d0 - 8;  // rows below the diagonal block
+        if (R == 0) break;
+        // panel: L[r][d0 + c] = sum_{t <= c} L[r][d0 + t] X[d0 + c][d0 + t]
+        float pv[4];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) acc[q] = 0.f;
-            const int rows = nrem * NB;
-            for (int t = 0; t <= c; ++t) {
-                const float xc = Xd[c][t];
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + TPB * q;
+            pv[q] = 0.f;
+            if (idx < R * 8) {
+                const int r = d0 + 8 + idx / 8, c = idx % 8;
+                float acc = 0.f;
 #pragma unroll
-                for (int q = 0; q < 12; ++q)
-                    if (w + 8 * q < rows) acc[q] = fmaf(L[d0 + NB + w + 8 * q][d0 + t], xc, acc[q]);
+                for (int t = 0; t < 8; ++t)
+                    if (t <= c) acc = fmaf(L[r][d0 + t], X[d0 + c][d0 + t], acc);
+                pv[q] = acc;
             }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < 12; ++q)
-                if (w + 8 * q < rows) L[d0 + NB + w + 8 * q][d0 + c] = acc[q];
         }
         __syncthreads();
-        if (kb == 0) leaf_trail<96>(L, d0);
-        else if (kb == 1) leaf_trail<64>(L, d0);
-        else leaf_trail<32>(L, d0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + TPB * q;
+            if (idx < R * 8) L[d0 + 8 + idx / 8][d0 + idx % 8] = pv[q];
+        }
+        __syncthreads();
+        const int b0 = d0 + 8, g = tid >> 5, c = tid & 31;
+        if (g == 0) {
+            // look-ahead: warp 0 updates the next diagonal block (36 entries)
+            // and one lane factors it while warps 1..7 update the rest
+            for (int e = c; e < 36; e += 32) {
+                int i = 0;
+                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                const int j = e - i * (i + 1) / 2;
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc = fmaf(L[b0 + i][d0 + t], L[b0 + j][d0 + t], acc);
+                L[b0 + i][b0 + j] -= acc;
+            }
+            __syncwarp();
+            if (c == 0) diag8(b0);
+        } else {
+            // trailing update of the lower part outside the next diagonal
+            // block: warp g takes rows b0 + (g - 1) + 7 k, lane c columns
+            // b0 + c + 32 p (only j <= i)
+            for (int pc = 0; pc * 32 < R; ++pc) {
+                const int j = b0 + c + 32 * pc;
+                if (j >= LB) continue;
+                const float4 j0 = *reinterpret_cast<const float4 *>(&L[j][d0]);
+                const float4 j1 = *reinterpret_cast<const float4 *>(&L[j][d0 + 4]);
+                int i = b0 + (g - 1);
+                if (i < j) i += ((j - i + 6) / 7) * 7;
+                if (j < b0 + 8) {
+                    while (i < b0 + 8) i += 7;  // rows of the next diagonal block are warp 0's
+                }
+                for (; i < LB; i += 7) {
+                    const float4 i0 = *reinterpret_cast<const float4 *>(&L[i][d0]);
+                    const float4 i1 = *reinterpret_cast<const float4 *>(&L[i][d0 + 4]);
+                    float a0 = i0.x * j0.x, a1 = i0.y * j0.y;
+                    a0 = fmaf(i0.z, j0.z, a0);
+                    a1 = fmaf(i0.w, j0.w, a1);
+                    a0 = fmaf(i1.x, j1.x, a0);
+                    a1 = fmaf(i1.y, j1.y, a1);
+                    a0 = fmaf(i1.z, j1.z, a0);
+                    a1 = fmaf(i1.w, j1.w, a1);
+                    L[i][j] -= a0 + a1;
+                }
+            }
+        }
         __syncthreads();
     }
     for (int r = tid; r < s; r += TPB) ldiag[o + r] = (double)L[r][r];
-    // X below the diagonal blocks, by distance of block row and column; thread
-    // (warp w, lane c) owns rows w + 8 q (q < 4) of each block in the step
-    for (int diff = 1; diff < LB / NB; ++diff) {
-        const int nblk = LB / NB - diff;
-        for (int jb = 0; jb < nblk; ++jb) {
-            const int ib = jb + diff;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int k = jb * NB; k < ib * NB; ++k) {
-                const float xk = X[k][jb * NB + c];
+    // off-diagonal 8-blocks of the inverse by block distance:
+    // T_ij = sum_{k=8jb}^{8ib-1} L[8ib+r][k] X[k][8jb+c] (parked in the upper
+    // block), then X_ij = -X_ii T_ij.  A thread owns a 4 x 2 tile of a block
+    // (8 tiles per block), so each loaded value feeds two or four FMAs.
+    for (int diff = 1; diff < LB / 8; ++diff) {
+        const int nblk = LB / 8 - diff;
+        const int item = tid;  // nblk * 8 tiles <= 120 < TPB
+        float t8[4][2];
+        const bool act = item < nblk * 8;
+        const int jb = item / 8, tt = item % 8, ib = jb + diff;
+        const int r0 = 4 * (tt / 4), c0 = 2 * (tt % 4);
+        if (act) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(L[ib * NB + w + 8 * q][k], xk, acc[q]);
-            }
+            for (int a = 0; a < 4; ++a) t8[a][0] = t8[a][1] = 0.f;
+            for (int k = 8 * jb; k < 8 * ib; ++k) {
+                const float x0 = X[k][8 * jb + c0], x1 = X[k][8 * jb + c0 + 1];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) X[jb * NB + w + 8 * q][ib * NB + c] = acc[q];  // T_ij, parked
-        }
-        __syncthreads();
-        for (int jb = 0; jb < nblk; ++jb) {
-            const int ib = jb + diff;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int t = 0; t < NB; ++t) {
-                const float tv = X[jb * NB + t][ib * NB + c];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r = w + 8 * q;
-                    if (t <= r) acc[q] = fmaf(X[ib * NB + r][ib * NB + t], tv, acc[q]);
+                for (int a = 0; a < 4; ++a) {
+                    const float l = L[8 * ib + r0 + a][k];
+                    t8[a][0] = fmaf(l, x0, t8[a][0]);
+                    t8[a][1] = fmaf(l, x1, t8[a][1]);
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) X[ib * NB + w + 8 * q][jb * NB + c] = -acc[q];
+            for (int a = 0; a < 4; ++a) {
+                X[8 * jb + r0 + a][8 * ib + c0] = t8[a][0];
+                X[8 * jb + r0 + a][8 * ib + c0 + 1] = t8[a][1];
+            }
+        }
+        __syncthreads();
+        // X_ij rows r0..r0+3 = -X_ii[r][0..r] T[0..r][c0..c0+1]
+        float u[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) u[a][0] = u[a][1] = 0.f;
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float y0 = X[8 * jb + t][8 * ib + c0], y1 = X[8 * jb + t][8 * ib + c0 + 1];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (t <= r0 + a) {
+                        const float xi = X[8 * ib + r0 + a][8 * ib + t];
+                        u[a][0] = fmaf(xi, y0, u[a][0]);
+                        u[a][1] = fmaf(xi, y1, u[a][1]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                X[8 * ib + r0 + a][8 * jb + c0] = -u[a][0];
+                X[8 * ib + r0 + a][8 * jb + c0 + 1] = -u[a][1];
+            }
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < s * s; idx += TPB) {
-        const int r = idx / s, cc = idx % s;
-        Xo[(o + r) * ld + o + cc] = (cc <= r) ? X[r][cc] : 0.f;
-        Xto[(o + r) * ld + o + cc] = (cc >= r) ? X[cc][r] : 0.f;
+    // X rows with 16-byte stores (zeros above the diagonal), X^T by columns of X
+#pragma unroll 4
+    for (int q = 0; q < LB * LB / 4 / TPB; ++q) {
+        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
+        if (r >= s || c4 >= s) continue;
+        float4 v = *reinterpret_cast<const float4 *>(&X[r][c4]);
+        float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (c4 + k > r) e[k] = 0.f;
+        if (c4 + 3 < s) {
+            *reinterpret_cast<float4 *>(Xo + (o + r) * ld + o + c4) = make_float4(e[0], e[1], e[2], e[3]);
+        } else {
+            for (int k = 0; k < 4 && c4 + k < s; ++k) Xo[(o + r) * ld + o + c4 + k] = e[k];
+        }
+    }
+#pragma unroll 4
+    for (int q = 0; q < LB * LB / TPB; ++q) {
+        const int idx = tid + TPB * q, r = idx / LB, cc = idx % LB;
+        if (r < s && cc < s) Xto[(o + r) * ld + o + cc] = (cc >= r) ? X[cc][r] : 0.f;
     }
 }
+
 
 // log det A = 2 sum_i log L_ii from the FP64 diagonal of the factor,
 // deterministic single-CTA reduction.
