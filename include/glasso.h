@@ -113,12 +113,16 @@ const char *glasso_last_error(glasso_ctx *ctx);
 glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
                            double *W_out, glasso_info *info);
 
-/* Solve `count` independent problems (e.g. several subjects, or a lambda
- * path) on the device.  A_out[k] receives the solution of p[k]; infos[k] (if
- * infos is not NULL) its statistics.  When p[k].A0 is NULL and k > 0 and
- * warm_from_prev is set, problem k starts from the solution of problem k-1
- * (continuation along decreasing lambda, Section 2; both must have the same
- * n and data).  Returns the first non-OK status, or GLASSO_OK. */
+/* Solve `count` problems (e.g. several subjects, or lambda paths) on the
+ * device.  A_out[k] receives the solution of p[k]; infos[k] (if infos is not
+ * NULL) its statistics.  When p[k].A0 is NULL and k > 0 and warm_from_prev is
+ * set, problem k starts from the solution of problem k-1 if both have the
+ * same n, input kind and data pointer (continuation along decreasing lambda,
+ * Section 2).  Problems that do not continue one another (and, with
+ * warm_from_prev, each maximal run of continuing problems) are solved
+ * concurrently through the context's serving slots; a run is solved in order
+ * on one slot.  Inputs are copied to host memory before solving, so they may
+ * be in either location.  Returns the first non-OK status, or GLASSO_OK. */
 glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int count,
                                  int warm_from_prev, double **A_out, glasso_info *infos);
 

@@ -899,6 +899,11 @@ struct Request {
     glasso_status status = GLASSO_EAGAIN;
     size_t fp = 0;
     bool done = false;
+    // a lambda path on the same data: solved after p, in order, each warm
+    // started from the previous solution in the worker's workspace
+    std::vector<glasso_problem> more;
+    std::vector<double *> more_out;
+    std::vector<glasso_info> more_info;
 };
 
 struct Serve {
@@ -945,6 +950,19 @@ void worker_main(Serve *sv) {
         glasso_info info;
         glasso_status s = solve_in(w, st, 0, &r->p, r->A_out, nullptr, &info, err, nullptr, false,
                                    r->out_location, sv->ctx->precision);
+        for (size_t i = 0; i < r->more.size(); ++i) {
+            glasso_info inf2;
+            memset(&inf2, 0, sizeof(inf2));
+            glasso_status s2 = GLASSO_ECUDA;
+            if (s == GLASSO_OK || s == GLASSO_EMAXITER || s == GLASSO_ELINESEARCH) {
+                s2 = solve_in(w, st, 0, &r->more[i], r->more_out[i], nullptr, &inf2, err, nullptr,
+                              true, r->out_location, sv->ctx->precision);
+            } else {
+                inf2.status = s;
+            }
+            r->more_info[i] = inf2;
+            if (s == GLASSO_OK) s = s2;
+        }
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             r->info = info;
@@ -987,6 +1005,84 @@ void serve_shutdown(glasso_ctx *ctx) {
     ctx->serve = nullptr;
 }
 
+
+// Queue `count` problems on the same data (count > 1: a warm-started lambda
+// path) as one request; the input is copied to the host before returning.
+glasso_status submit_chain(glasso_ctx *ctx, const glasso_problem *p, int count, double **A_out,
+                           uint64_t *ticket) {
+    if (!ctx || !ticket || !A_out || count < 1) return GLASSO_EINVAL;
+    for (int k = 0; k < count; ++k) {
+        glasso_status s = validate(&p[k]);
+        if (s != GLASSO_OK) return s;
+        if (!A_out[k]) return GLASSO_EINVAL;
+    }
+    const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
+    const int xb = p->dtype == GLASSO_F32 ? 4 : 8;
+    const size_t fp = footprint(p->n, m, xb);
+    if (ctx->budget && fp > ctx->budget) return GLASSO_ENOMEM;
+    Request *r = new Request();
+    r->p = *p;
+    const size_t bytes = p->input == GLASSO_INPUT_S ? (size_t)(p->n * p->n) * 8 : (size_t)(m * p->n) * xb;
+    r->data.resize(bytes);
+    const cudaMemcpyKind kind = p->location == GLASSO_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    cudaSetDevice(ctx->device);
+    if (cudaMemcpy(r->data.data(), p->data, bytes, kind) != cudaSuccess) {
+        delete r;
+        return GLASSO_ECUDA;
+    }
+    if (p->A0) {
+        r->a0.resize((size_t)(p->n * p->n));
+        if (cudaMemcpy(r->a0.data(), p->A0, r->a0.size() * 8, kind) != cudaSuccess) {
+            delete r;
+            return GLASSO_ECUDA;
+        }
+        r->p.A0 = r->a0.data();
+    }
+    // the staged copies live on the host; outputs go where the caller said
+    r->p.data = r->data.data();
+    r->A_out = A_out[0];
+    r->out_location = p->location;
+    r->fp = fp;
+    r->p.location = GLASSO_HOST;  // inputs now live in the request's host copy
+    for (int k = 1; k < count; ++k) {
+        glasso_problem q = p[k];
+        q.data = r->data.data();
+        q.location = GLASSO_HOST;
+        q.A0 = nullptr;
+        r->more.push_back(q);
+        r->more_out.push_back(A_out[k]);
+    }
+    r->more_info.resize(r->more.size());
+    Serve *sv = serve_get(ctx);
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        r->ticket = sv->next++;
+        sv->all[r->ticket] = r;
+        sv->queue.push_back(r);
+    }
+    sv->cv_work.notify_one();
+    *ticket = r->ticket;
+    return GLASSO_OK;
+}
+
+// Wait for a request; infos[0 .. 1 + more) receive its problems' infos.
+glasso_status wait_chain(glasso_ctx *ctx, uint64_t ticket, glasso_info *infos) {
+    Serve *sv = (Serve *)ctx->serve;
+    if (!sv) return GLASSO_EINVAL;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return GLASSO_EINVAL;
+    Request *r = it->second;
+    sv->cv_done.wait(lk, [&] { return r->done; });
+    if (infos) {
+        infos[0] = r->info;
+        for (size_t i = 0; i < r->more_info.size(); ++i) infos[1 + i] = r->more_info[i];
+    }
+    glasso_status s = r->status;
+    sv->all.erase(it);
+    delete r;
+    return s;
+}
 }  // namespace
 
 // =================================================================== C ABI
@@ -1107,9 +1203,41 @@ glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int c
         }
         return first;
     }
+    // lambda paths: maximal runs of problems on the same data; several runs go
+    // through the serving slots concurrently (each run in order on one slot)
+    auto continues = [&](int k) {
+        return k > 0 && p[k].A0 == nullptr && p[k].n == p[k - 1].n && p[k].data == p[k - 1].data &&
+               p[k].input == p[k - 1].input;
+    };
+    std::vector<int> starts;
+    for (int k = 0; k < count; ++k)
+        if (!continues(k)) starts.push_back(k);
+    if (starts.size() > 1) {
+        std::vector<uint64_t> tickets(starts.size(), 0);
+        for (size_t c = 0; c < starts.size(); ++c) {
+            const int k0 = starts[c];
+            const int k1 = c + 1 < starts.size() ? starts[c + 1] : count;
+            glasso_status s = submit_chain(ctx, &p[k0], k1 - k0, &A_out[k0], &tickets[c]);
+            if (s != GLASSO_OK) {
+                for (int k = k0; k < k1; ++k)
+                    if (infos) { memset(&infos[k], 0, sizeof(glasso_info)); infos[k].status = s; }
+                if (first == GLASSO_OK) first = s;
+            }
+        }
+        for (size_t c = 0; c < starts.size(); ++c) {
+            if (!tickets[c]) continue;
+            const int k0 = starts[c];
+            const int k1 = c + 1 < starts.size() ? starts[c + 1] : count;
+            std::vector<glasso_info> inf(k1 - k0);
+            glasso_status s = wait_chain(ctx, tickets[c], inf.data());
+            if (infos)
+                for (int k = k0; k < k1; ++k) infos[k] = inf[k - k0];
+            if (s != GLASSO_OK && first == GLASSO_OK) first = s;
+        }
+        return first;
+    }
     for (int k = 0; k < count; ++k) {
-        const bool chain = k > 0 && p[k].A0 == nullptr && p[k].n == p[k - 1].n &&
-                           p[k].data == p[k - 1].data && p[k].input == p[k - 1].input;
+        const bool chain = continues(k);
         glasso_info inf;
         glasso_status s;
         if (chain) {
@@ -1128,47 +1256,7 @@ glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int c
 
 glasso_status glasso_submit(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
                             uint64_t *ticket) {
-    if (!ctx || !ticket || !A_out) return GLASSO_EINVAL;
-    glasso_status s = validate(p);
-    if (s != GLASSO_OK) return s;
-    const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
-    const int xb = p->dtype == GLASSO_F32 ? 4 : 8;
-    const size_t fp = footprint(p->n, m, xb);
-    if (ctx->budget && fp > ctx->budget) return GLASSO_ENOMEM;
-    Request *r = new Request();
-    r->p = *p;
-    const size_t bytes = p->input == GLASSO_INPUT_S ? (size_t)(p->n * p->n) * 8 : (size_t)(m * p->n) * xb;
-    r->data.resize(bytes);
-    const cudaMemcpyKind kind = p->location == GLASSO_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
-    cudaSetDevice(ctx->device);
-    if (cudaMemcpy(r->data.data(), p->data, bytes, kind) != cudaSuccess) {
-        delete r;
-        return GLASSO_ECUDA;
-    }
-    if (p->A0) {
-        r->a0.resize((size_t)(p->n * p->n));
-        if (cudaMemcpy(r->a0.data(), p->A0, r->a0.size() * 8, kind) != cudaSuccess) {
-            delete r;
-            return GLASSO_ECUDA;
-        }
-        r->p.A0 = r->a0.data();
-    }
-    // the staged copies live on the host; outputs go where the caller said
-    r->p.data = r->data.data();
-    r->A_out = A_out;
-    r->out_location = p->location;
-    r->fp = fp;
-    r->p.location = GLASSO_HOST;  // inputs now live in the request's host copy
-    Serve *sv = serve_get(ctx);
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        r->ticket = sv->next++;
-        sv->all[r->ticket] = r;
-        sv->queue.push_back(r);
-    }
-    sv->cv_work.notify_one();
-    *ticket = r->ticket;
-    return GLASSO_OK;
+    return submit_chain(ctx, p, 1, &A_out, ticket);
 }
 
 glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us, glasso_info *info) {

@@ -187,6 +187,28 @@ def test_warm_start_and_batch_path(ctx):
         assert np.abs(A - B).max() <= 1e-7
 
 
+def test_concurrent_lambda_paths(ctx):
+    """Several instances, each a warm-started lambda path, in one batch call:
+    the paths run concurrently on the serving slots, each in order on one
+    slot; every result meets the oracle bar."""
+    from paper_1607_00315_gb300 import glasso
+
+    insts = [synth.random_problem(n, 2 * n, 0.1, 31 + k, gen=g)
+             for k, (n, g) in enumerate([(60, "sparse"), (90, "tridiag"), (45, "sparse")])]
+    probs, outs, meta = [], [], []
+    for p in insts:
+        S = oracle.form_S(p.X)
+        for lam in synth.LAMBDA_PATH:
+            probs.append(glasso.Context.problem(S, lam, 1e-10))
+            outs.append(np.empty((p.n, p.n)))
+            meta.append((S, lam))
+    s, infos = ctx.solve_batch(probs, outs, warm_from_prev=True)
+    assert s == 0
+    for (S, lam), A, inf in zip(meta, outs, infos):
+        A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-10)
+        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"])
+
+
 def test_serving_results_same_alone_and_in_the_mix(ctx):
     from paper_1607_00315_gb300 import glasso
 
