@@ -90,15 +90,22 @@ __global__ void k_scan_rows(const double *__restrict__ S, const double *__restri
         bool fr = false;
         if (valid) {
             const double s = Si[j], w = Wi[j], a = Ai[j];
-            const double g = s - w;
-            fr = (a != 0.0) || (mode == 0 ? fabs(g) > lam : fabs(s) > lam);
-            const double wt = (j == i) ? 1.0 : 2.0;
-            const double r = (a != 0.0) ? g + lam * sgnd(a) : soft(g, lam);
-            kkt += wt * fabs(r);
-            kmax = fmax(kmax, fabs(r));
-            tr += wt * s * a;
-            l1 += wt * fabs(a);
-            nnz += (a != 0.0) ? wt : 0.0;
+            const double g = s - w, ag = fabs(g);
+            const bool nz = a != 0.0;
+            fr = nz || (mode == 0 ? ag > lam : fabs(s) > lam);
+            // most entries have A_ij = 0 and |G_ij| <= lambda and add nothing:
+            // keep the FP64 work (slow on this GPU) to the rest
+            if (nz || ag > lam) {
+                const double wt = (j == i) ? 1.0 : 2.0;
+                const double r = nz ? g + lam * sgnd(a) : soft(g, lam);
+                kkt += wt * fabs(r);
+                kmax = fmax(kmax, fabs(r));
+                if (nz) {
+                    tr += wt * s * a;
+                    l1 += wt * fabs(a);
+                    nnz += wt;
+                }
+            }
         }
         const uint32_t m = __ballot_sync(0xffffffffu, fr);
         if (lane == 0) mask[i * nw + jb / 32] = m;
