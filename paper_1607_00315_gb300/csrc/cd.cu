@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
     __shared__ int si[CD_B], sj[CD_B];
     __shared__ unsigned skey[NE];
     __shared__ int sdest[NE], ssrc[NE];
-    __shared__ double smu[NE];
+    __shared__ T smu[NE];  // row-update multipliers in the arithmetic of W and U
     __shared__ int seg_start[NE + 1], seg_dest[NE];
     __shared__ int nseg_s, wtot[RT / 32];
     __shared__ __align__(8) unsigned long long kbar;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                     u[r] = col < n ? ur[col] : (T)0;
                 }
                 for (int e = seg_start[k]; e < seg_start[k + 1]; ++e) {
-                    const T m = (T)smu[e];
+                    const T m = smu[e];
                     const T *wr = W + (int64_t)ssrc[e] * n;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -290,10 +290,12 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             T acc = 0;
 #pragma unroll 8
             for (int64_t k = k0 + lane; k < k1; k += 32) acc = fma(wr[k], uc[k * n], acc);
-            double a = (double)acc;
+            // warp sum in the arithmetic of W and U (FP64 operations and
+            // conversions run at a small fraction of the FP32 rate on this
+            // GPU); the chunk partials are summed in FP64
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) bvec[(int64_t)c * CD_B + t] = a;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) bvec[(int64_t)c * CD_B + t] = (double)acc;
         }
         CT *Ktc = reinterpret_cast<CT *>(Kt);
         for (int q = (int)gthread; !Kall && q < nb * nb; q += (int)nthreads) {
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 const int e = (int)(kk & 511u), t = e >> 1;
                 sdest[tid] = (int)(kk >> 9);
                 ssrc[tid] = (e & 1) ? si[t] : sj[t];
-                smu[tid] = meff[t];
+                smu[tid] = (T)meff[t];
             }
             int v = valid;
 #pragma unroll
