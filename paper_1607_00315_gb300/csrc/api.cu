@@ -115,7 +115,7 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
         CK(cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)));
         CK(dalloc(w.redbuf, 3 * 1024, st));
         w.cap_red = 3 * 1024;
-        CK(dalloc(w.cd_part, (size_t)CD_MAX_CHUNKS * CD_B + (size_t)CD_B * CD_B, st));
+        CK(dalloc(w.cd_part, (size_t)2 * CD_MAX_CHUNKS * CD_B + (size_t)CD_B * CD_B, st));
         CK(dalloc(w.xd, 2 * NB * NB, st));
     }
     if (n <= w.cap_n) return GLASSO_OK;
@@ -634,8 +634,9 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             // FP32 resolution chain while the iterate is far from the optimum; FP64
             // once the relative KKT residual is small, where the Newton step must be
             // resolved to the gradient's FP64 accuracy
+            // (the FP64 buffer T is free in this path: it holds the second copy of U)
             CK(cd_sweeps32(W32, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
-                           relkkt <= 1e-6, st));
+                           relkkt <= 1e-6, st, (float *)w.T));
             sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 4.0);
             CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
             CK(series_terms(W64, n, w.pi, w.pj, w.D, np, U32, w.part, w.cap_part, sc, st));

@@ -16,7 +16,8 @@
 //     K[s][t] = (W E_s W)_{i_t j_t} = W_{i_t i_s} W_{j_s j_t} + W_{i_t j_s} W_{i_s j_t}
 //     (one term when s is diagonal);
 //  2. resolution: for t = 0..B-1, b_t = b0_t + sum_{s<t} mu_s K[s][t] and mu_t
-//     from the closed form; every CTA runs this chain itself;
+//     from the closed form (the FP32 chain carries x_t = c_t - b_t / a_t
+//     instead of b_t); every CTA runs this chain itself;
 //  3. row updates: each target row of U gets its updates in sweep order.
 #include <math.h>
 
@@ -81,8 +82,11 @@ __device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch) {
         red_release_gpu(&gb->count, 1u);
         int ok = 1;
         const long long t0 = clock64();
+        unsigned spins = 0;
+        // one acquire load per poll; the error word (a CTA that gave up) is
+        // read every 32 polls
         while ((int)(ld_acquire_gpu(&gb->count) - target) < 0) {
-            if (*verr || clock64() - t0 > 4000000000ll) {  // about 2 s
+            if ((++spins & 31u) == 0 && (*verr || clock64() - t0 > 4000000000ll)) {  // about 2 s
                 ok = 0;
                 atomicExch(&gb->err, 1);
                 break;
@@ -129,50 +133,67 @@ __device__ __forceinline__ bool kcopy_wait(unsigned long long *bar, uint32_t par
     }
 }
 
-// FP32 resolution of one block by one warp, in sub-blocks of SB coordinates.
-// Lane l keeps b of coordinates l, l + 32, l + 64, l + 96.  For a sub-block,
+// FP32 resolution of one block by one warp, in sub-blocks of SB coordinates,
+// in the argument x_t = c_t - b_t / a_t of the closed form of eq. 1d_l1,
+// mu_t = S_{lambda/a_t}(x_t) - c_t.  An update mu_s of an earlier coordinate
+// changes x_t by -(K[s][t] / a_t) mu_s, so Ks holds K[s][t] / a_t (s < t, zero
+// elsewhere) and no scaling sits on the dependent path.
+// xsh[t] = c_t - b_t / a_t, csh[t] = c_t, thsh[t] = lam / a_t (zero for t >= nb).
+// Lane l keeps x of coordinates l, l + 32, l + 64, l + 96.  For a sub-block,
 // every lane takes a copy of its SB values (shuffles), so each step's
-// dependent path is the closed form plus one FMA with no broadcast; then each
-// lane adds the sub-block's SB terms to its own coordinates.  Every b_t
-// receives its terms K[s][t] mu_s in ascending s, as in the lane-owner form
-// (lanes also update coordinates already resolved; those values are unused).
-__device__ __forceinline__ void resolve_f32(const float *__restrict__ Ks, const float *bsh,
-                                            const float *csh, const float *ish, float lam,
-                                            int nb, float *mush, int *zsh) {
+// dependent path is the clamp, two subtractions and one FMA with no
+// broadcast; then each lane adds the sub-block's SB terms to its own
+// coordinates.  Every x_t receives its terms in ascending s, as in the
+// lane-owner form (lanes also update coordinates already resolved; those
+// values are unused).  The owner lane of t keeps mu_t and the zero flag in
+// registers and stores them once at the end.
+__device__ __forceinline__ void resolve_f32(const float *__restrict__ Ks, const float *__restrict__ xsh,
+                                            const float *__restrict__ csh,
+                                            const float *__restrict__ thsh, int nb,
+                                            float *__restrict__ mush, int *__restrict__ zsh) {
     const int lane = threadIdx.x & 31;
     constexpr int NQ = CD_B / 32, SB = 8;
-    float bl[NQ];
+    float xl[NQ], mown[NQ];
+    int zown[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) bl[q] = bsh[lane + 32 * q];
+    for (int q = 0; q < NQ; ++q) {
+        xl[q] = xsh[lane + 32 * q];
+        mown[q] = 0.f;
+        zown[q] = 0;
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
 #pragma unroll
         for (int h = 0; h < 32 / SB; ++h) {
             const int t0 = 32 * q + SB * h;
             if (t0 >= nb) break;
-            float bc[SB], mu[SB];
+            float xc[SB], cc[SB], th[SB], mu[SB];
 #pragma unroll
-            for (int k = 0; k < SB; ++k) bc[k] = __shfl_sync(0xffffffffu, bl[q], SB * h + k);
+            for (int k = 0; k < SB; ++k) xc[k] = __shfl_sync(0xffffffffu, xl[q], SB * h + k);
+#pragma unroll
+            for (int k = 0; k < SB; k += 4) {
+                const float4 cv = *reinterpret_cast<const float4 *>(csh + t0 + k);
+                const float4 tv = *reinterpret_cast<const float4 *>(thsh + t0 + k);
+                cc[k] = cv.x, cc[k + 1] = cv.y, cc[k + 2] = cv.z, cc[k + 3] = cv.w;
+                th[k] = tv.x, th[k + 1] = tv.y, th[k + 2] = tv.z, th[k + 3] = tv.w;
+            }
 #pragma unroll
             for (int k = 0; k < SB; ++k) {
                 // coordinates t >= nb hold zeros and take mu = 0
                 const int t = t0 + k;
-                const float c = csh[t], ia = ish[t];
-                const float x = c - bc[k] * ia;
-                const float th = lam * ia;
-                const float z = x - fminf(fmaxf(x, -th), th);  // S_th(x), exact zero inside
-                const float m = (t < nb) ? z - c : 0.0f;
-                if (lane == (t & 31)) {
-                    mush[t] = m;
-                    zsh[t] = (z == 0.0f);
+                const float z = xc[k] - fminf(fmaxf(xc[k], -th[k]), th[k]);  // exact zero inside
+                const float m = (t < nb) ? z - cc[k] : 0.0f;
+                if (lane == SB * h + k) {
+                    mown[q] = m;
+                    zown[q] = (z == 0.0f);
                 }
 #pragma unroll
                 for (int g = (k + 1) / 4; g < SB / 4; ++g) {
                     const float4 kv = *reinterpret_cast<const float4 *>(Ks + t * CD_B + t0 + 4 * g);
-                    if (4 * g > k) bc[4 * g] = fmaf(kv.x, m, bc[4 * g]);
-                    if (4 * g + 1 > k) bc[4 * g + 1] = fmaf(kv.y, m, bc[4 * g + 1]);
-                    if (4 * g + 2 > k) bc[4 * g + 2] = fmaf(kv.z, m, bc[4 * g + 2]);
-                    if (4 * g + 3 > k) bc[4 * g + 3] = fmaf(kv.w, m, bc[4 * g + 3]);
+                    if (4 * g > k) xc[4 * g] = fmaf(-kv.x, m, xc[4 * g]);
+                    if (4 * g + 1 > k) xc[4 * g + 1] = fmaf(-kv.y, m, xc[4 * g + 1]);
+                    if (4 * g + 2 > k) xc[4 * g + 2] = fmaf(-kv.z, m, xc[4 * g + 2]);
+                    if (4 * g + 3 > k) xc[4 * g + 3] = fmaf(-kv.w, m, xc[4 * g + 3]);
                 }
                 mu[k] = m;
             }
@@ -180,9 +201,14 @@ __device__ __forceinline__ void resolve_f32(const float *__restrict__ Ks, const 
             for (int qq = q; qq < NQ; ++qq) {
                 const float *Kr = Ks + t0 * CD_B + 32 * qq + lane;
 #pragma unroll
-                for (int k = 0; k < SB; ++k) bl[qq] = fmaf(Kr[k * CD_B], mu[k], bl[qq]);
+                for (int k = 0; k < SB; ++k) xl[qq] = fmaf(-Kr[k * CD_B], mu[k], xl[qq]);
             }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        mush[lane + 32 * q] = mown[q];
+        zsh[lane + 32 * q] = zown[q];
     }
 }
 
@@ -234,6 +260,9 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 const int64_t is = pi[kb0 + s], js = pj[kb0 + s], it2 = pi[kb0 + t], jt = pj[kb0 + t];
                 v = (double)W[it2 * n + is] * (double)W[js * n + jt];
                 if (is != js) v = fma((double)W[it2 * n + js], (double)W[is * n + jt], v);
+            }
+            if constexpr (sizeof(CT) == 4) {  // the FP32 chain works in x (K[s][t] / a_t)
+                if (s < t && kb0 + t < np) v *= inva[kb0 + t];
             }
             Kall[q] = (CT)v;
         }
@@ -304,6 +333,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 const int64_t is = pi[b0 + s], js = pj[b0 + s], it2 = pi[b0 + t], jt = pj[b0 + t];
                 double v = (double)W[it2 * n + is] * (double)W[js * n + jt];
                 if (is != js) v = fma((double)W[it2 * n + js], (double)W[is * n + jt], v);
+                if constexpr (sizeof(CT) == 4) v *= inva[b0 + t];
                 Ktc[s * CD_B + t] = (CT)v;
             }
         }
@@ -325,9 +355,16 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 for (int r = 0; r < 8; ++r) b += v[r];
             }
             for (; c < nch; ++c) b += bvec[(int64_t)c * CD_B + tid];
-            bsh[tid] = (CT)b;
-            csh[tid] = (CT)(aval[b0 + tid] + D[b0 + tid]);
-            ish[tid] = (CT)inva[b0 + tid];
+            const double cv = aval[b0 + tid] + D[b0 + tid], ia = inva[b0 + tid];
+            if constexpr (sizeof(CT) == 4) {  // x, c and the threshold of the FP32 chain
+                bsh[tid] = (CT)(cv - b * ia);
+                csh[tid] = (CT)cv;
+                ish[tid] = (CT)(lam * ia);
+            } else {
+                bsh[tid] = (CT)b;
+                csh[tid] = (CT)cv;
+                ish[tid] = (CT)ia;
+            }
             si[tid] = pi[b0 + tid];
             sj[tid] = pj[b0 + tid];
         } else if (tid < CD_B) {
@@ -349,7 +386,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             if constexpr (sizeof(CT) == 4) {
                 resolve_f32(reinterpret_cast<const float *>(Ks), reinterpret_cast<const float *>(bsh),
                             reinterpret_cast<const float *>(csh), reinterpret_cast<const float *>(ish),
-                            (float)lam, nb, reinterpret_cast<float *>(mush), zsh);
+                            nb, reinterpret_cast<float *>(mush), zsh);
             } else {
                 // lane l holds b, c, 1/a of coordinates l, l+32, l+64, l+96 in registers;
                 // the owner of coordinate t computes mu_t and broadcasts it by shuffle
@@ -484,6 +521,508 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
         for (int t = tid; t < prev_nb; t += RT) D[prev_b0 + t] = dnew[t];
 }
 
+// ---------------------------------------------------------------------------
+// FP32 sweep with the serial chain on one CTA and the row updates off its
+// path.  CTA 0 (the chain CTA) holds the interaction matrices and resolves
+// the chain; CTAs 1..G-1 (work CTAs) take the stale dots and apply the row
+// updates.  Two copies of U alternate: in pass p, copy p mod 2 holds U after
+// blocks < p - 1 and is only read, copy (p + 1) mod 2 holds U after blocks
+// < p - 2 and is only written.  Pass p:
+//   chain CTA: x of block p from its stale dots (taken in pass p - 1 against
+//     U after blocks < p - 2) minus the exact terms of blocks p - 2 and p - 1,
+//     (K2_{p-2})^T mu_{p-2} + (K1_{p-1})^T mu_{p-1}, where
+//     Kd_q[s][t] = K(s in block q -> t in block q + d) / a_t (all s and t;
+//     the block sequence wraps around the sweep); warp 0 resolves the chain
+//     of block p while warps 1-8 take the term of block p - 1 on block p + 1;
+//     FP64 increments with exact zeros; block p's row-update entries are
+//     staged in global memory; the term of block p on block p + 1;
+//   work CTAs: stale dots of block p + 1 against copy p mod 2; sort block
+//     p - 1's staged entries, merge them after block p - 2's and apply both
+//     to copy (p + 1) mod 2, which then holds U after blocks <= p - 1;
+//   grid barrier.
+// A last pass without a chain applies the final two blocks.  The intra and
+// cross matrices of all blocks are computed once per launch; the chain CTA
+// fetches them with cp.async.bulk one pass ahead.
+constexpr int LW = 8;              // worker warps (warps 1..LW)
+constexpr int LT = 32 * (LW + 1);  // warp 0 of the chain CTA runs the chain
+constexpr int NWK = 32 * LW;       // worker threads
+constexpr int NE2 = 2 * NE;        // merged row updates of two blocks
+static_assert(NWK == NE && NWK == 2 * CD_B, "one entry per worker thread; cross-term halves");
+
+__device__ __forceinline__ void wsync() { asm volatile("bar.sync 1, %0;" ::"n"(NWK) : "memory"); }
+
+__global__ void __launch_bounds__(LT, 1) k_cd_lag2(
+    const float *__restrict__ W, float *__restrict__ Ubuf0, float *__restrict__ Ubuf1, int64_t n,
+    double lam, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
+    const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
+    double *__restrict__ D, int nsweeps, double *__restrict__ bvec, float *__restrict__ Kall,
+    int *__restrict__ stage, GridBar *gb) {
+    extern __shared__ __align__(16) unsigned char ks_raw[];
+    float *KI = reinterpret_cast<float *>(ks_raw);  // intra: K[s][t] / a_t, s < t
+    float *K1 = KI + CD_B * CD_B;                   // block p -> p + 1
+    float *K2 = K1 + CD_B * CD_B;                   // block p - 1 -> p + 1
+    // chain CTA
+    __shared__ __align__(16) float xsh[CD_B], csh[CD_B], thsh[CD_B];
+    __shared__ float mush[CD_B], mprev[CD_B], xn[CD_B], xc2[2][CD_B], x1[2][CD_B];
+    __shared__ int zsh[CD_B], si[CD_B], sj[CD_B];
+    __shared__ double meff[CD_B], dold[CD_B], aold[CD_B];
+    // work CTAs: staged entries, sort scratch, sorted lists of the last two
+    // blocks (by block parity), merged list and its segments
+    __shared__ unsigned sx[NE];
+    __shared__ int stsrc[NE];
+    __shared__ float stmu[NE];
+    __shared__ int ldest[2][NE], lsrc[2][NE], lcount[2];
+    __shared__ float lmu[2][NE];
+    __shared__ int mdest[NE2], msrc[NE2];
+    __shared__ float mmu[NE2];
+    __shared__ int seg_start[NE2 + 1], seg_dest[NE2];
+    __shared__ int nseg_s, wtot[LW], wv[LW];
+    __shared__ __align__(8) unsigned long long kbarI, kbar1, kbar2;
+    constexpr uint32_t KB = CD_B * CD_B * sizeof(float);
+    unsigned *gkey = reinterpret_cast<unsigned *>(stage);  // [2][NE], by block parity
+    int *gsrc = stage + 2 * NE;                            // [2][NE]
+    float *gmu = reinterpret_cast<float *>(stage + 4 * NE);  // [2][NE]
+    const unsigned G = gridDim.x;
+    const bool cc = blockIdx.x == 0;
+    const int GW = (int)G - 1, wb = (int)blockIdx.x - 1;  // work CTAs
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, wtid = tid - 32;
+    const int64_t nbatch = (np + CD_B - 1) / CD_B;
+    const int64_t total = nbatch * nsweeps;
+    const int nch = (int)((n + DCH - 1) / DCH);
+    const int64_t KS = (int64_t)CD_B * CD_B;
+    const float *KallI = Kall, *Kall1 = Kall + nbatch * KS, *Kall2 = Kall + 2 * nbatch * KS;
+    unsigned epoch = 0, phI = 0, ph1 = 0, ph2 = 0;
+    bool pendI = false, pend1 = false, pend2 = false;  // issued, not yet waited for (issuer)
+    if (tid == 0) {
+        lcount[0] = lcount[1] = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI)), "r"(1u));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar1)), "r"(1u));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar2)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int t = tid; t < CD_B; t += LT) {
+        mprev[t] = 0.f;
+        xn[t] = 0.f;
+    }
+    auto drain = [&]() {  // let issued copies land before the CTA leaves
+        if (pendI) kcopy_wait(&kbarI, phI & 1u);
+        if (pend1) kcopy_wait(&kbar1, ph1 & 1u);
+        if (pend2) kcopy_wait(&kbar2, ph2 & 1u);
+    };
+    auto kwait = [&](unsigned long long *bar, unsigned &ph, bool &pend) {
+        if (!kcopy_wait(bar, ph & 1u)) {
+            atomicExch(&gb->err, 1);
+            kcopy_wait(bar, ph & 1u);
+        }
+        ++ph;
+        pend = false;
+    };
+    // 0. interaction matrices of all blocks: intra, +1 and +2 (scaled by 1/a of
+    //    the target), four entries per thread in flight
+    {
+        const int64_t per = nbatch * KS, tot = 3 * per;
+        const int64_t gthread = (int64_t)blockIdx.x * LT + tid, nthreads = (int64_t)G * LT;
+        for (int64_t q0 = gthread; q0 < tot; q0 += 4 * nthreads) {
+            int64_t is[4], js[4], it2[4], jt[4], kt[4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t q = q0 + u * nthreads;
+                ok[u] = false;
+                if (q < tot) {
+                    const int kind = (int)(q / per);
+                    const int64_t qq = q - kind * per;
+                    const int64_t bb = qq / KS;
+                    const int r = (int)(qq - bb * KS), s = r / CD_B, t = r - s * CD_B;
+                    const int64_t ks0 = bb * CD_B, kt0 = ((bb + kind) % nbatch) * CD_B;
+                    ok[u] = (kind > 0 || s < t) && ks0 + s < np && kt0 + t < np;
+                    kt[u] = kt0 + t;
+                    if (ok[u]) {
+                        is[u] = pi[ks0 + s];
+                        js[u] = pj[ks0 + s];
+                        it2[u] = pi[kt0 + t];
+                        jt[u] = pj[kt0 + t];
+                    }
+                }
+            }
+            float w1[4], w2[4], w3[4], w4[4];
+            double ia[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (ok[u]) {
+                    w1[u] = W[it2[u] * n + is[u]];
+                    w2[u] = W[js[u] * n + jt[u]];
+                    w3[u] = W[it2[u] * n + js[u]];
+                    w4[u] = W[is[u] * n + jt[u]];
+                    ia[u] = inva[kt[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t q = q0 + u * nthreads;
+                if (q < tot) {
+                    double v = 0.0;
+                    if (ok[u]) {
+                        v = (double)w1[u] * (double)w2[u];
+                        if (is[u] != js[u]) v = fma((double)w3[u], (double)w4[u], v);
+                        v *= ia[u];
+                    }
+                    Kall[q] = (float)v;
+                }
+            }
+        }
+    }
+    // stale dots of the block at coordinate b1 (count nb1) against U copy R,
+    // (coordinate, chunk) tasks over the given warps, FP32 warp sums
+    auto dots = [&](const float *R, int64_t b1, int nb1, double *out, int64_t wfirst, int64_t wcount) {
+        for (int64_t task = wfirst; task < (int64_t)nb1 * nch; task += wcount) {
+            const int t = (int)(task / nch), c = (int)(task - (int64_t)t * nch);
+            const int64_t it_ = pi[b1 + t], jt = pj[b1 + t];
+            const float *wr = W + jt * n;
+            const float *uc = R + it_;
+            const int64_t k0 = (int64_t)c * DCH, k1 = lmin(n, k0 + DCH);
+            float acc = 0.f;
+#pragma unroll 8
+            for (int64_t k = k0 + lane; k < k1; k += 32) acc = fmaf(wr[k], uc[k * n], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) out[(int64_t)c * CD_B + t] = (double)acc;
+        }
+    };
+    // prologue: dots of block 0 against copy 0 (both copies hold the initial U)
+    dots(Ubuf0, 0, (int)lmin(CD_B, np), bvec, (int64_t)blockIdx.x * (LT / 32) + warp,
+         (int64_t)G * (LT / 32));
+    if (!grid_sync(gb, G, epoch)) return;
+    if (cc && tid == 0) {  // the matrices are complete after the barrier
+        kcopy_issue(KI, KallI, KB, &kbarI);
+        pendI = true;
+        if (total > 1) {
+            kcopy_issue(K1, Kall1, KB, &kbar1);
+            pend1 = true;
+        }
+    }
+    for (int64_t it = 0; it <= total; ++it) {
+        const bool chain = it < total;
+        if (cc) {
+            if (!chain) break;
+            const int64_t b0 = (it % nbatch) * CD_B;
+            const int nb = (int)lmin(CD_B, np - b0);
+            const bool need2 = it >= 1 && it + 1 < total;  // term of block it-1 on block it+1
+            // A. x, c and the threshold of block it (Delta is current in D: only
+            //    this CTA writes it)
+            {
+                const double *bcur = bvec + (it & 1) * (int64_t)CD_MAX_CHUNKS * CD_B;
+                for (int t = tid; t < CD_B; t += LT) {
+                    if (t < nb) {
+                        const double gv = g[b0 + t], av = aval[b0 + t], ia = inva[b0 + t];
+                        const double d = D[b0 + t];
+                        const int i_ = pi[b0 + t], j_ = pj[b0 + t];
+                        double b = gv;
+                        if (nch <= 8) {
+                            double v[8];
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) v[r] = r < nch ? bcur[(int64_t)r * CD_B + t] : 0.0;
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) b += v[r];
+                        } else {
+                            int c = 0;
+                            for (; c + 8 <= nch; c += 8) {
+                                double v[8];
+#pragma unroll
+                                for (int r = 0; r < 8; ++r) v[r] = bcur[(int64_t)(c + r) * CD_B + t];
+#pragma unroll
+                                for (int r = 0; r < 8; ++r) b += v[r];
+                            }
+                            for (; c < nch; ++c) b += bcur[(int64_t)c * CD_B + t];
+                        }
+                        const double cv = av + d;
+                        xsh[t] = (float)(cv - b * ia) - xn[t];
+                        csh[t] = (float)cv;
+                        thsh[t] = (float)(lam * ia);
+                        dold[t] = d;
+                        aold[t] = av;
+                        si[t] = i_;
+                        sj[t] = j_;
+                    } else {
+                        xsh[t] = csh[t] = thsh[t] = 0.f;
+                        si[t] = sj[t] = 0;
+                    }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // B. the chain; the intra matrix of the next block is fetched right after
+                if (lane == 0) kwait(&kbarI, phI, pendI);
+                __syncwarp();
+                resolve_f32(KI, xsh, csh, thsh, nb, mush, zsh);
+                __syncwarp();
+                if (lane == 0 && it + 1 < total) {
+                    kcopy_issue(KI, KallI + ((it + 1) % nbatch) * KS, KB, &kbarI);
+                    pendI = true;
+                }
+            } else {
+                // term of block it-1 (increments in mprev) on block it+1
+                if (need2) {
+                    if (wtid == 0) kwait(&kbar2, ph2, pend2);
+                    wsync();
+                    const int t = wtid & (CD_B - 1), h = wtid >> 7;
+                    float a0 = 0.f, a1 = 0.f;
+                    for (int s2 = h * (CD_B / 2); s2 < (h + 1) * (CD_B / 2); s2 += 2) {
+                        a0 = fmaf(K2[s2 * CD_B + t], mprev[s2], a0);
+                        a1 = fmaf(K2[(s2 + 1) * CD_B + t], mprev[s2 + 1], a1);
+                    }
+                    xc2[h][t] = a0 + a1;
+                    wsync();
+                }
+                if (wtid == 0 && it + 2 < total) {  // the +2 matrix of block it, used in pass it+1
+                    kcopy_issue(K2, Kall2 + (it % nbatch) * KS, KB, &kbar2);
+                    pend2 = true;
+                }
+            }
+            __syncthreads();
+            // C. FP64 increments (exact zeros), written through to D
+            if (tid < nb) {
+                const double d0 = dold[tid];
+                double m = 0.0, dn = d0;
+                if (mush[tid] != 0.f) {
+                    if (zsh[tid]) {
+                        dn = -aold[tid];
+                        m = dn - d0;
+                    } else {
+                        m = (double)mush[tid];
+                        dn = d0 + m;
+                    }
+                }
+                meff[tid] = m;
+                D[b0 + tid] = dn;
+            }
+            __syncthreads();
+            // row-update entries of block it (entry e = 2t + k) for the work CTAs
+            if (tid < NE) {
+                const int e = tid, t = e >> 1, k = e & 1;
+                unsigned key = 0xFFFFFFFFu;
+                float mu = 0.f;
+                if (t < nb && meff[t] != 0.0) {
+                    mu = (float)meff[t];
+                    if (k == 0) key = ((unsigned)si[t] << 9) | (unsigned)e;
+                    else if (si[t] != sj[t]) key = ((unsigned)sj[t] << 9) | (unsigned)e;
+                }
+                const int64_t o = (it & 1) * NE + e;
+                gkey[o] = key;
+                gsrc[o] = k ? si[t] : sj[t];
+                gmu[o] = mu;
+                if (k == 0) mprev[t] = mu;
+            }
+            __syncthreads();
+            // term of block it on block it+1; x of block it+1 loses both terms
+            if (it + 1 < total) {
+                if (tid == 0) kwait(&kbar1, ph1, pend1);
+                __syncthreads();
+                if (tid < 2 * CD_B) {
+                    const int t = tid & (CD_B - 1), h = tid >> 7;
+                    float a0 = 0.f, a1 = 0.f;
+                    for (int s2 = h * (CD_B / 2); s2 < (h + 1) * (CD_B / 2); s2 += 2) {
+                        a0 = fmaf(K1[s2 * CD_B + t], mprev[s2], a0);
+                        a1 = fmaf(K1[(s2 + 1) * CD_B + t], mprev[s2 + 1], a1);
+                    }
+                    x1[h][t] = a0 + a1;
+                }
+                __syncthreads();
+                if (tid < CD_B)
+                    xn[tid] = (need2 ? xc2[0][tid] + xc2[1][tid] : 0.f) + (x1[0][tid] + x1[1][tid]);
+                if (tid == 0 && it + 2 < total) {
+                    kcopy_issue(K1, Kall1 + ((it + 1) % nbatch) * KS, KB, &kbar1);
+                    pend1 = true;
+                }
+            }
+        } else {
+            // work CTA. Stale dots of block it+1 against copy it mod 2 (all warps)
+            if (it + 1 < total) {
+                const int64_t nb0 = ((it + 1) % nbatch) * CD_B;
+                dots((it & 1) ? Ubuf1 : Ubuf0, nb0, (int)lmin(CD_B, np - nb0),
+                     bvec + ((it + 1) & 1) * (int64_t)CD_MAX_CHUNKS * CD_B,
+                     (int64_t)wb * (LT / 32) + warp, (int64_t)GW * (LT / 32));
+            }
+            if (warp > 0) {
+                // sort block it-1's staged entries
+                const int sc = (int)((it + 1) & 1), sp = (int)(it & 1);  // parity of blocks it-1, it-2
+                {
+                    unsigned key = 0xFFFFFFFFu;
+                    if (it >= 1) {
+                        const int64_t o = (int64_t)sc * NE + wtid;
+                        key = gkey[o];
+                        stsrc[wtid] = gsrc[o];
+                        stmu[wtid] = gmu[o];
+                    }
+                    for (int size = 2; size <= NE; size <<= 1) {
+                        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                            unsigned other;
+                            if (stride >= 32) {
+                                sx[wtid] = key;
+                                wsync();
+                                other = sx[wtid ^ stride];
+                                wsync();
+                            } else {
+                                other = __shfl_xor_sync(0xffffffffu, key, stride);
+                            }
+                            const bool up = (wtid & size) == 0, lower = (wtid & stride) == 0;
+                            key = (lower == up) ? min(key, other) : max(key, other);
+                        }
+                    }
+                    const bool valid = key != 0xFFFFFFFFu;
+                    const int v = __popc(__ballot_sync(0xffffffffu, valid));
+                    if (lane == 0) wv[warp - 1] = v;
+                    if (valid) {
+                        const int e = (int)(key & 511u);
+                        ldest[sc][wtid] = (int)(key >> 9);
+                        lsrc[sc][wtid] = stsrc[e];
+                        lmu[sc][wtid] = stmu[e];
+                    }
+                    wsync();
+                    if (wtid == 0) {
+                        int V = 0;
+                        for (int w2 = 0; w2 < LW; ++w2) V += wv[w2];
+                        lcount[sc] = V;
+                    }
+                    wsync();
+                }
+                // merge: block it-2's entries before block it-1's within a row
+                {
+                    const int VP = lcount[sp], VC = lcount[sc];
+                    if (wtid < VP) {
+                        const int d = ldest[sp][wtid];
+                        int lo = 0, hi = VC;  // entries of block it-1 with dest < d
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ldest[sc][mid] < d) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        const int pos = wtid + lo;
+                        mdest[pos] = d;
+                        msrc[pos] = lsrc[sp][wtid];
+                        mmu[pos] = lmu[sp][wtid];
+                    }
+                    if (wtid < VC) {
+                        const int d = ldest[sc][wtid];
+                        int lo = 0, hi = VP;  // entries of block it-2 with dest <= d
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ldest[sp][mid] <= d) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        const int pos = wtid + lo;
+                        mdest[pos] = d;
+                        msrc[pos] = lsrc[sc][wtid];
+                        mmu[pos] = lmu[sc][wtid];
+                    }
+                    wsync();
+                    const int V = VP + VC;
+                    int flag[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = 2 * wtid + h;
+                        flag[h] = r < V && (r == 0 || mdest[r] != mdest[r - 1]);
+                    }
+                    const int x = flag[0] + flag[1];
+                    int xi = x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, xi, o);
+                        if (lane >= o) xi += y;
+                    }
+                    if (lane == 31) wtot[warp - 1] = xi;
+                    wsync();
+                    int before = 0, nsg = 0;
+                    for (int w2 = 0; w2 < LW; ++w2) {
+                        if (w2 < warp - 1) before += wtot[w2];
+                        nsg += wtot[w2];
+                    }
+                    int idx = before + xi - x;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = 2 * wtid + h;
+                        if (flag[h]) {
+                            seg_start[idx] = r;
+                            seg_dest[idx] = mdest[r];
+                            ++idx;
+                        }
+                    }
+                    if (wtid == 0) {
+                        nseg_s = nsg;
+                        seg_start[nsg] = V;
+                    }
+                    wsync();
+                }
+                // apply to copy (it + 1) mod 2: items (segment, group of 4 columns
+                // spaced by ncg) over the work CTAs, two per step with the loads first
+                {
+                    float *Y = (it & 1) ? Ubuf0 : Ubuf1;
+                    const int nseg = nseg_s;
+                    const int ncg = (int)((n + 3) / 4);
+                    const int items = nseg * ncg;
+                    const int nw = GW * NWK;
+                    for (int q = wb * NWK + wtid; q < items; q += 2 * nw) {
+                        const int qb = q + nw;
+                        const bool hb = qb < items;
+                        const int ka = q / ncg, ca = q - ka * ncg;
+                        const int kb = hb ? qb / ncg : ka, cb = hb ? qb - kb * ncg : ca;
+                        float *ura = Y + (int64_t)seg_dest[ka] * n, *urb = Y + (int64_t)seg_dest[kb] * n;
+                        const int ea = seg_start[ka], eb = seg_start[kb];
+                        const float ma = mmu[ea], mb = mmu[eb];
+                        const float *wa = W + (int64_t)msrc[ea] * n, *wbr = W + (int64_t)msrc[eb] * n;
+                        float ua[4], ub[4], va[4], vb[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
+                            ua[r] = col < n ? ura[col] : 0.f;
+                            va[r] = col < n ? wa[col] : 0.f;
+                            ub[r] = (hb && colb < n) ? urb[colb] : 0.f;
+                            vb[r] = (hb && colb < n) ? wbr[colb] : 0.f;
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            ua[r] = fmaf(ma, va[r], ua[r]);
+                            ub[r] = fmaf(mb, vb[r], ub[r]);
+                        }
+                        for (int e = ea + 1; e < seg_start[ka + 1]; ++e) {
+                            const float m = mmu[e];
+                            const float *wr = W + (int64_t)msrc[e] * n;
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const int64_t col = ca + (int64_t)r * ncg;
+                                if (col < n) ua[r] = fmaf(m, wr[col], ua[r]);
+                            }
+                        }
+                        if (hb)
+                            for (int e = eb + 1; e < seg_start[kb + 1]; ++e) {
+                                const float m = mmu[e];
+                                const float *wr = W + (int64_t)msrc[e] * n;
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) {
+                                    const int64_t col = cb + (int64_t)r * ncg;
+                                    if (col < n) ub[r] = fmaf(m, wr[col], ub[r]);
+                                }
+                            }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
+                            if (col < n) ura[col] = ua[r];
+                            if (hb && colb < n) urb[colb] = ub[r];
+                        }
+                    }
+                }
+            }
+            if (!chain) break;
+        }
+        if (!grid_sync(gb, G, epoch)) {
+            drain();
+            return;
+        }
+    }
+}
+
+bool g_lag_attr = false;
+
 bool g_attr_done[4] = {false, false, false, false};
 
 }  // namespace
@@ -558,12 +1097,78 @@ cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
     return cd_sweeps_t<double, double>(W, n, lam, pi, pj, np, inva, g, aval, nsweeps, D, U, w, st);
 }
 
+// FP32 sweep with the row updates off the serial path (k_cd_lag2); U2 is
+// n x n FP32 scratch for the second copy of U.  Returns cudaErrorNotSupported
+// when the interaction matrices of all blocks do not fit in n^2 doubles (the
+// caller falls back to the one-copy sweep).
+static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const int32_t *pi,
+                                 const int32_t *pj, int64_t np, const double *inva, const double *g,
+                                 const double *aval, int nsweeps, double *D, float *U, float *U2,
+                                 Work &w, cudaStream_t st) {
+    if (n > (1 << 22) || (n + DCH - 1) / DCH > CD_MAX_CHUNKS) return cudaErrorNotSupported;
+    const int64_t nbatch = (np + CD_B - 1) / CD_B;
+    const size_t kb = (size_t)CD_B * CD_B * sizeof(float);
+    const size_t kneed = (size_t)(3 * nbatch) * kb;
+    if (kneed > (size_t)n * (size_t)n * sizeof(double)) return cudaErrorNotSupported;
+    static int nsm = 0, occ = 0;
+    const size_t dyn = 3 * kb;
+    if (!g_lag_attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_cd_lag2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cd_lag2, LT, dyn);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        g_lag_attr = true;
+    }
+    GridBar *gb = reinterpret_cast<GridBar *>(&w.sc->bar_count);
+    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
+    if (e != cudaSuccess) return e;
+    // both copies start as the current U
+    e = cudaMemcpyAsync(U2, U, (size_t)n * (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (w.cap_cd_k < kneed) {
+        const size_t want = std::min((size_t)n * (size_t)n * sizeof(double), std::max(kneed, 2 * w.cap_cd_k));
+        if (w.cd_k) {
+            e = cudaFreeAsync(w.cd_k, st);
+            w.cd_k = nullptr;
+            w.cap_cd_k = 0;
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaMallocAsync((void **)&w.cd_k, want, st);
+        if (e != cudaSuccess) return e;
+        w.cap_cd_k = want;
+    }
+    float *Kall = reinterpret_cast<float *>(w.cd_k);
+    double *bvec = w.cd_part;
+    static_assert(6 * NE * sizeof(int) <= CD_B * CD_B * sizeof(double), "staging area");
+    // staged row-update entries: 6 x NE words after the two generations of partial dots
+    int *stage = reinterpret_cast<int *>(w.cd_part + (size_t)2 * CD_MAX_CHUNKS * CD_B);
+    // the last pass (index total, no chain) writes copy (total + 1) mod 2: make that U
+    const int64_t total = nbatch * (int64_t)nsweeps;
+    float *b0 = ((total + 1) & 1) ? U2 : U, *b1 = ((total + 1) & 1) ? U : U2;
+    const int G = (int)lmax(4, lmin((int64_t)nsm * occ, (n + 7) / 8));
+    void *args[] = {(void *)&W, (void *)&b0, (void *)&b1, (void *)&n, (void *)&lam, (void *)&pi,
+                    (void *)&pj, (void *)&np, (void *)&inva, (void *)&g, (void *)&aval, (void *)&D,
+                    (void *)&nsweeps, (void *)&bvec, (void *)&Kall, (void *)&stage, (void *)&gb};
+    e = cudaLaunchCooperativeKernel((const void *)k_cd_lag2, dim3(G), dim3(LT), args, dyn, st);
+    counted(1);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi,
                         const int32_t *pj, int64_t np, const double *inva, const double *g,
                         const double *aval, int nsweeps, double *D, float *U, Work &w,
-                        bool chain64, cudaStream_t st) {
+                        bool chain64, cudaStream_t st, float *U2) {
     if (chain64)
         return cd_sweeps_t<float, double>(W, n, lam, pi, pj, np, inva, g, aval, nsweeps, D, U, w, st);
+    if (U2 && np > 0 && nsweeps > 0) {
+        cudaError_t e = cd_sweeps_lag(W, n, lam, pi, pj, np, inva, g, aval, nsweeps, D, U, U2, w, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     return cd_sweeps_t<float, float>(W, n, lam, pi, pj, np, inva, g, aval, nsweeps, D, U, w, st);
 }
 

@@ -92,7 +92,7 @@ struct Work {
     double *redbuf = nullptr;              // generic reduction partials
     int64_t cap_red = 0;
     // CD scratch
-    double *cd_part = nullptr;             // CD_MAX_CHUNKS x CD_B partial dots, then CD_B^2 K
+    double *cd_part = nullptr;             // 2 x CD_MAX_CHUNKS x CD_B partial dots, then CD_B^2 K
     float *fa = nullptr;                   // 4 x n x tc_pad(n) FP32: matrix, X, Xt, scratch of cholinv_tc
     unsigned char *cd_k = nullptr;         // interaction matrices of all CD blocks (grown on demand)
     size_t cap_cd_k = 0;
@@ -227,6 +227,6 @@ cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
 cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi,
                         const int32_t *pj, int64_t np, const double *inva, const double *g,
                         const double *aval, int nsweeps, double *D, float *U, Work &w,
-                        bool chain64, cudaStream_t st);
+                        bool chain64, cudaStream_t st, float *U2 = nullptr);
 
 }  // namespace glx
