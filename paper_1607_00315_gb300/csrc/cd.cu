@@ -558,9 +558,11 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     double *__restrict__ D, int nsweeps, double *__restrict__ bvec, float *__restrict__ Kall,
     int *__restrict__ stage, GridBar *gb) {
     extern __shared__ __align__(16) unsigned char ks_raw[];
-    float *KI = reinterpret_cast<float *>(ks_raw);  // intra: K[s][t] / a_t, s < t
-    float *K1 = KI + CD_B * CD_B;                   // block p -> p + 1
-    float *K2 = K1 + CD_B * CD_B;                   // block p - 1 -> p + 1
+    // intra matrices K[s][t] / a_t (s < t) of this pass and the next (by pass
+    // parity), and the block p -> p + 1 matrix; the p - 1 -> p + 1 term is
+    // read from global memory by the otherwise idle worker warps
+    float *KIb = reinterpret_cast<float *>(ks_raw);
+    float *K1 = KIb + 2 * CD_B * CD_B;
     // chain CTA
     __shared__ __align__(16) float xsh[CD_B], csh[CD_B], thsh[CD_B];
     __shared__ float mush[CD_B], mprev[CD_B], xn[CD_B], xc2[2][CD_B], x1[2][CD_B];
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     __shared__ float mmu[NE2];
     __shared__ int seg_start[NE2 + 1], seg_dest[NE2];
     __shared__ int nseg_s, wtot[LW], wv[LW];
-    __shared__ __align__(8) unsigned long long kbarI, kbar1, kbar2;
+    __shared__ __align__(8) unsigned long long kbarI[2], kbar1;
     constexpr uint32_t KB = CD_B * CD_B * sizeof(float);
     unsigned *gkey = reinterpret_cast<unsigned *>(stage);  // [2][NE], by block parity
     int *gsrc = stage + 2 * NE;                            // [2][NE]
@@ -591,13 +593,15 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     const int nch = (int)((n + DCH - 1) / DCH);
     const int64_t KS = (int64_t)CD_B * CD_B;
     const float *KallI = Kall, *Kall1 = Kall + nbatch * KS, *Kall2 = Kall + 2 * nbatch * KS;
-    unsigned epoch = 0, phI = 0, ph1 = 0, ph2 = 0;
-    bool pendI = false, pend1 = false, pend2 = false;  // issued, not yet waited for (issuer)
+    // mbarrier phases, advanced by every thread of the chain CTA in step (the
+    // waiting and the issuing threads differ); outstanding copies per issuer
+    unsigned epoch = 0, phI0 = 0, phI1 = 0, ph1 = 0;
+    int pendI0 = 0, pendI1 = 0, pend1 = 0;
     if (tid == 0) {
         lcount[0] = lcount[1] = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI)), "r"(1u));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI[0])), "r"(1u));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI[1])), "r"(1u));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar1)), "r"(1u));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar2)), "r"(1u));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int t = tid; t < CD_B; t += LT) {
@@ -605,17 +609,15 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
         xn[t] = 0.f;
     }
     auto drain = [&]() {  // let issued copies land before the CTA leaves
-        if (pendI) kcopy_wait(&kbarI, phI & 1u);
+        if (pendI0) kcopy_wait(&kbarI[0], phI0 & 1u);
+        if (pendI1) kcopy_wait(&kbarI[1], phI1 & 1u);
         if (pend1) kcopy_wait(&kbar1, ph1 & 1u);
-        if (pend2) kcopy_wait(&kbar2, ph2 & 1u);
     };
-    auto kwait = [&](unsigned long long *bar, unsigned &ph, bool &pend) {
+    auto kwait = [&](unsigned long long *bar, unsigned ph) {
         if (!kcopy_wait(bar, ph & 1u)) {
             atomicExch(&gb->err, 1);
             kcopy_wait(bar, ph & 1u);
         }
-        ++ph;
-        pend = false;
     };
     // 0. interaction matrices of all blocks: intra, +1 and +2 (scaled by 1/a of
     //    the target), four entries per thread in flight
@@ -673,10 +675,12 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
         }
     }
     // stale dots of the block at coordinate b1 (count nb1) against U copy R,
-    // (coordinate, chunk) tasks over the given warps, FP32 warp sums
+    // (chunk, coordinate) tasks over the given warps (neighbouring warps take
+    // neighbouring coordinates of one chunk, which mostly share the U column
+    // i_t: pairs are in row order), FP32 warp sums
     auto dots = [&](const float *R, int64_t b1, int nb1, double *out, int64_t wfirst, int64_t wcount) {
         for (int64_t task = wfirst; task < (int64_t)nb1 * nch; task += wcount) {
-            const int t = (int)(task / nch), c = (int)(task - (int64_t)t * nch);
+            const int c = (int)(task / nb1), t = (int)(task - (int64_t)c * nb1);
             const int64_t it_ = pi[b1 + t], jt = pj[b1 + t];
             const float *wr = W + jt * n;
             const float *uc = R + it_;
@@ -693,13 +697,9 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     dots(Ubuf0, 0, (int)lmin(CD_B, np), bvec, (int64_t)blockIdx.x * (LT / 32) + warp,
          (int64_t)G * (LT / 32));
     if (!grid_sync(gb, G, epoch)) return;
-    if (cc && tid == 0) {  // the matrices are complete after the barrier
-        kcopy_issue(KI, KallI, KB, &kbarI);
-        pendI = true;
-        if (total > 1) {
-            kcopy_issue(K1, Kall1, KB, &kbar1);
-            pend1 = true;
-        }
+    if (cc && tid == 32) {  // the matrices are complete after the barrier
+        kcopy_issue(KIb, KallI, KB, &kbarI[0]);
+        pendI0 = 1;
     }
     for (int64_t it = 0; it <= total; ++it) {
         const bool chain = it < total;
@@ -708,6 +708,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             const int64_t b0 = (it % nbatch) * CD_B;
             const int nb = (int)lmin(CD_B, np - b0);
             const bool need2 = it >= 1 && it + 1 < total;  // term of block it-1 on block it+1
+            float *KI = KIb + (it & 1) * KS;
             // A. x, c and the threshold of block it (Delta is current in D: only
             //    this CTA writes it)
             {
@@ -751,33 +752,43 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             }
             __syncthreads();
             if (warp == 0) {
-                // B. the chain; the intra matrix of the next block is fetched right after
-                if (lane == 0) kwait(&kbarI, phI, pendI);
+                // B. the chain
+                if (lane == 0) kwait(&kbarI[it & 1], (it & 1) ? phI1 : phI0);
                 __syncwarp();
                 resolve_f32(KI, xsh, csh, thsh, nb, mush, zsh);
-                __syncwarp();
-                if (lane == 0 && it + 1 < total) {
-                    kcopy_issue(KI, KallI + ((it + 1) % nbatch) * KS, KB, &kbarI);
-                    pendI = true;
-                }
             } else {
-                // term of block it-1 (increments in mprev) on block it+1
-                if (need2) {
-                    if (wtid == 0) kwait(&kbar2, ph2, pend2);
-                    wsync();
-                    const int t = wtid & (CD_B - 1), h = wtid >> 7;
-                    float a0 = 0.f, a1 = 0.f;
-                    for (int s2 = h * (CD_B / 2); s2 < (h + 1) * (CD_B / 2); s2 += 2) {
-                        a0 = fmaf(K2[s2 * CD_B + t], mprev[s2], a0);
-                        a1 = fmaf(K2[(s2 + 1) * CD_B + t], mprev[s2 + 1], a1);
+                // copies for later: the next block's intra matrix (the other
+                // buffer: its last reader was the previous chain) and this
+                // block's +1 matrix (read in C)
+                if (wtid == 0) {
+                    if (it + 1 < total) {
+                        kcopy_issue(KIb + ((it + 1) & 1) * KS, KallI + ((it + 1) % nbatch) * KS, KB,
+                                    &kbarI[(it + 1) & 1]);
+                        if ((it + 1) & 1) pendI1 = 1;
+                        else pendI0 = 1;
+                        kcopy_issue(K1, Kall1 + (it % nbatch) * KS, KB, &kbar1);
+                        pend1 = 1;
                     }
-                    xc2[h][t] = a0 + a1;
-                    wsync();
                 }
-                if (wtid == 0 && it + 2 < total) {  // the +2 matrix of block it, used in pass it+1
-                    kcopy_issue(K2, Kall2 + (it % nbatch) * KS, KB, &kbar2);
-                    pend2 = true;
+                // term of block it-1 (increments in mprev) on block it+1, from
+                // the +2 matrix of block it-1 in global memory (coalesced rows)
+                if (need2) {
+                    const float *K2g = Kall2 + ((it - 1) % nbatch) * KS;
+                    const int t = wtid & (CD_B - 1), h = wtid >> 7;
+                    float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                    for (int s2 = h * (CD_B / 2); s2 < (h + 1) * (CD_B / 2); s2 += 4) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) a[u] = fmaf(K2g[(s2 + u) * CD_B + t], mprev[s2 + u], a[u]);
+                    }
+                    xc2[h][t] = (a[0] + a[1]) + (a[2] + a[3]);
                 }
+            }
+            if (it & 1) ++phI1;
+            else ++phI0;
+            if (wtid == 0) {
+                if (it & 1) pendI1 = 0;
+                else pendI0 = 0;
             }
             __syncthreads();
             // C. FP64 increments (exact zeros), written through to D
@@ -816,7 +827,9 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             __syncthreads();
             // term of block it on block it+1; x of block it+1 loses both terms
             if (it + 1 < total) {
-                if (tid == 0) kwait(&kbar1, ph1, pend1);
+                if (tid == 0) kwait(&kbar1, ph1);
+                ++ph1;
+                if (wtid == 0) pend1 = 0;
                 __syncthreads();
                 if (tid < 2 * CD_B) {
                     const int t = tid & (CD_B - 1), h = tid >> 7;
@@ -830,13 +843,20 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
                 __syncthreads();
                 if (tid < CD_B)
                     xn[tid] = (need2 ? xc2[0][tid] + xc2[1][tid] : 0.f) + (x1[0][tid] + x1[1][tid]);
-                if (tid == 0 && it + 2 < total) {
-                    kcopy_issue(K1, Kall1 + ((it + 1) % nbatch) * KS, KB, &kbar1);
-                    pend1 = true;
-                }
             }
         } else {
-            // work CTA. Stale dots of block it+1 against copy it mod 2 (all warps)
+            // work CTA. Block it-1's staged entries are loaded first (they land
+            // during the dots); stale dots of block it+1 against copy it mod 2
+            const int sc = (int)((it + 1) & 1), sp = (int)(it & 1);  // parity of blocks it-1, it-2
+            unsigned key = 0xFFFFFFFFu;
+            int ksrc = 0;
+            float kmu = 0.f;
+            if (warp > 0 && it >= 1) {
+                const int64_t o = (int64_t)sc * NE + wtid;
+                key = gkey[o];
+                ksrc = gsrc[o];
+                kmu = gmu[o];
+            }
             if (it + 1 < total) {
                 const int64_t nb0 = ((it + 1) % nbatch) * CD_B;
                 dots((it & 1) ? Ubuf1 : Ubuf0, nb0, (int)lmin(CD_B, np - nb0),
@@ -845,15 +865,9 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             }
             if (warp > 0) {
                 // sort block it-1's staged entries
-                const int sc = (int)((it + 1) & 1), sp = (int)(it & 1);  // parity of blocks it-1, it-2
                 {
-                    unsigned key = 0xFFFFFFFFu;
-                    if (it >= 1) {
-                        const int64_t o = (int64_t)sc * NE + wtid;
-                        key = gkey[o];
-                        stsrc[wtid] = gsrc[o];
-                        stmu[wtid] = gmu[o];
-                    }
+                    stsrc[wtid] = ksrc;
+                    stmu[wtid] = kmu;
                     for (int size = 2; size <= NE; size <<= 1) {
                         for (int stride = size >> 1; stride > 0; stride >>= 1) {
                             unsigned other;
