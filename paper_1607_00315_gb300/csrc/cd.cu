@@ -92,7 +92,9 @@ __device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch) {
                 break;
             }
         }
-        ok_s = ok && !*verr;
+        // (an error word set by a CTA that still arrived is left to the host,
+        // which reads it after the launch: no extra round trip here)
+        ok_s = ok;
     }
     __syncthreads();
     return ok_s != 0;
@@ -534,20 +536,27 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
 //     Kd_q[s][t] = K(s in block q -> t in block q + d) / a_t (all s and t;
 //     the block sequence wraps around the sweep); warp 0 resolves the chain
 //     of block p while warps 1-8 take the term of block p - 1 on block p + 1;
-//     FP64 increments with exact zeros; block p's row-update entries are
-//     staged in global memory; the term of block p on block p + 1;
-//   work CTAs: stale dots of block p + 1 against copy p mod 2; sort block
-//     p - 1's staged entries, merge them after block p - 2's and apply both
-//     to copy (p + 1) mod 2, which then holds U after blocks <= p - 1;
+//     FP64 increments with exact zeros; block p's row-update multipliers go
+//     to global memory; the term of block p on block p + 1;
+//   work CTAs: stale dots of block p + 1 against copy p mod 2; the row
+//     updates of blocks p - 2 and p - 1 applied to copy (p + 1) mod 2, which
+//     then holds U after blocks <= p - 1;
 //   grid barrier.
-// A last pass without a chain applies the final two blocks.  The intra and
-// cross matrices of all blocks are computed once per launch; the chain CTA
-// fetches them with cp.async.bulk one pass ahead.
+// A last pass without a chain applies the final two blocks.  Which rows an
+// update touches depends only on the pair list, so the per-launch setup
+// computes, besides the intra and cross matrices, for every pair of
+// consecutive blocks the list of their row updates sorted by target row
+// (the earlier block first within a row) and its segments; a pass only
+// looks up the multipliers (an update with multiplier 0 leaves U as it is).
 constexpr int LW = 8;              // worker warps (warps 1..LW)
 constexpr int LT = 32 * (LW + 1);  // warp 0 of the chain CTA runs the chain
 constexpr int NWK = 32 * LW;       // worker threads
-constexpr int NE2 = 2 * NE;        // merged row updates of two blocks
+constexpr int NE2 = 2 * NE;        // row updates of two blocks
 static_assert(NWK == NE && NWK == 2 * CD_B, "one entry per worker thread; cross-term halves");
+// merged list of two blocks in global memory: V, nseg, src[NE2], ref[NE2],
+// seg_start[NE2 + 1], seg_dest[NE2] (ref = slot * NE + entry; slot 0 = the
+// earlier block); padded to a multiple of 4 words
+constexpr int LST = (2 + 4 * NE2 + 1 + 3) / 4 * 4;
 
 __device__ __forceinline__ void wsync() { asm volatile("bar.sync 1, %0;" ::"n"(NWK) : "memory"); }
 
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     double lam, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
     const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
     double *__restrict__ D, int nsweeps, double *__restrict__ bvec, float *__restrict__ Kall,
-    int *__restrict__ stage, GridBar *gb) {
+    int *__restrict__ lists, float *__restrict__ gmu, GridBar *gb) {
     extern __shared__ __align__(16) unsigned char ks_raw[];
     // intra matrices K[s][t] / a_t (s < t) of this pass and the next (by pass
     // parity), and the block p -> p + 1 matrix; the p - 1 -> p + 1 term is
@@ -566,24 +575,17 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     // chain CTA
     __shared__ __align__(16) float xsh[CD_B], csh[CD_B], thsh[CD_B];
     __shared__ float mush[CD_B], mprev[CD_B], xn[CD_B], xc2[2][CD_B], x1[2][CD_B];
-    __shared__ int zsh[CD_B], si[CD_B], sj[CD_B];
+    __shared__ int zsh[CD_B];
     __shared__ double meff[CD_B], dold[CD_B], aold[CD_B];
-    // work CTAs: staged entries, sort scratch, sorted lists of the last two
-    // blocks (by block parity), merged list and its segments
+    // list setup and work CTAs
     __shared__ unsigned sx[NE];
-    __shared__ int stsrc[NE];
-    __shared__ float stmu[NE];
-    __shared__ int ldest[2][NE], lsrc[2][NE], lcount[2];
-    __shared__ float lmu[2][NE];
-    __shared__ int mdest[NE2], msrc[NE2];
-    __shared__ float mmu[NE2];
+    __shared__ int ldest[2][NE], lsrc[2][NE], lref[2][NE], lcount[2];
+    __shared__ int mdest[NE2], msrc[NE2], mref[NE2];
+    __shared__ float mutab[NE2];
     __shared__ int seg_start[NE2 + 1], seg_dest[NE2];
-    __shared__ int nseg_s, wtot[LW], wv[LW];
+    __shared__ int nseg_s, nv_s, wtot[LW], wv[LW];
     __shared__ __align__(8) unsigned long long kbarI[2], kbar1;
     constexpr uint32_t KB = CD_B * CD_B * sizeof(float);
-    unsigned *gkey = reinterpret_cast<unsigned *>(stage);  // [2][NE], by block parity
-    int *gsrc = stage + 2 * NE;                            // [2][NE]
-    float *gmu = reinterpret_cast<float *>(stage + 4 * NE);  // [2][NE]
     const unsigned G = gridDim.x;
     const bool cc = blockIdx.x == 0;
     const int GW = (int)G - 1, wb = (int)blockIdx.x - 1;  // work CTAs
@@ -598,7 +600,6 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     unsigned epoch = 0, phI0 = 0, phI1 = 0, ph1 = 0;
     int pendI0 = 0, pendI1 = 0, pend1 = 0;
     if (tid == 0) {
-        lcount[0] = lcount[1] = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI[0])), "r"(1u));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbarI[1])), "r"(1u));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(cd_smem(&kbar1)), "r"(1u));
@@ -619,8 +620,8 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             kcopy_wait(bar, ph & 1u);
         }
     };
-    // 0. interaction matrices of all blocks: intra, +1 and +2 (scaled by 1/a of
-    //    the target), four entries per thread in flight
+    // 0a. interaction matrices of all blocks: intra, +1 and +2 (scaled by 1/a
+    //     of the target), four entries per thread in flight
     {
         const int64_t per = nbatch * KS, tot = 3 * per;
         const int64_t gthread = (int64_t)blockIdx.x * LT + tid, nthreads = (int64_t)G * LT;
@@ -674,6 +675,139 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             }
         }
     }
+    // 0b. merged row-update lists: list L < nbatch holds blocks (L - 1) mod
+    //     nbatch (slot 0) and L (slot 1); list nbatch holds block 0 alone
+    //     (slot 1).  Entry e = 2t + k of a block updates row i_t from row j_t
+    //     (k = 0) or row j_t from row i_t (k = 1, off-diagonal pairs only).
+    if (warp > 0) {
+        for (int64_t L = blockIdx.x; L <= nbatch; L += G) {
+#pragma unroll 1
+            for (int slot = 0; slot < 2; ++slot) {
+                const bool has = slot == 1 || L < nbatch;
+                const int64_t q = slot == 1 ? (L < nbatch ? L : 0) : (L + nbatch - 1) % nbatch;
+                const int64_t q0 = q * CD_B;
+                const int nbq = (int)lmin(CD_B, np - q0);
+                const int e = wtid, t = e >> 1, k = e & 1;
+                unsigned key = 0xFFFFFFFFu;
+                int src = 0;
+                if (has && t < nbq) {
+                    const int i_ = pi[q0 + t], j_ = pj[q0 + t];
+                    src = k ? i_ : j_;
+                    if (k == 0) key = ((unsigned)i_ << 9) | (unsigned)e;
+                    else if (i_ != j_) key = ((unsigned)j_ << 9) | (unsigned)e;
+                }
+                lsrc[slot][e] = src;  // by entry, gathered after the sort
+                for (int size = 2; size <= NE; size <<= 1) {
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        unsigned other;
+                        if (stride >= 32) {
+                            sx[wtid] = key;
+                            wsync();
+                            other = sx[wtid ^ stride];
+                            wsync();
+                        } else {
+                            other = __shfl_xor_sync(0xffffffffu, key, stride);
+                        }
+                        const bool up = (wtid & size) == 0, lower = (wtid & stride) == 0;
+                        key = (lower == up) ? min(key, other) : max(key, other);
+                    }
+                }
+                const bool valid = key != 0xFFFFFFFFu;
+                const int v = __popc(__ballot_sync(0xffffffffu, valid));
+                if (lane == 0) wv[warp - 1] = v;
+                int ssrc = 0, sref = 0;
+                if (valid) {
+                    const int ee = (int)(key & 511u);
+                    ssrc = lsrc[slot][ee];
+                    sref = slot * NE + ee;
+                }
+                wsync();
+                if (valid) {
+                    ldest[slot][wtid] = (int)(key >> 9);
+                    lsrc[slot][wtid] = ssrc;
+                    lref[slot][wtid] = sref;
+                }
+                if (wtid == 0) {
+                    int V = 0;
+                    for (int w2 = 0; w2 < LW; ++w2) V += wv[w2];
+                    lcount[slot] = V;
+                }
+                wsync();
+            }
+            // merge: slot 0 before slot 1 within a row (binary search placement)
+            const int VP = lcount[0], VC = lcount[1];
+            if (wtid < VP) {
+                const int d = ldest[0][wtid];
+                int lo = 0, hi = VC;  // slot-1 entries with dest < d
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ldest[1][mid] < d) lo = mid + 1;
+                    else hi = mid;
+                }
+                const int pos = wtid + lo;
+                mdest[pos] = d;
+                msrc[pos] = lsrc[0][wtid];
+                mref[pos] = lref[0][wtid];
+            }
+            if (wtid < VC) {
+                const int d = ldest[1][wtid];
+                int lo = 0, hi = VP;  // slot-0 entries with dest <= d
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ldest[0][mid] <= d) lo = mid + 1;
+                    else hi = mid;
+                }
+                const int pos = wtid + lo;
+                mdest[pos] = d;
+                msrc[pos] = lsrc[1][wtid];
+                mref[pos] = lref[1][wtid];
+            }
+            wsync();
+            const int V = VP + VC;
+            int flag[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * wtid + h;
+                flag[h] = r < V && (r == 0 || mdest[r] != mdest[r - 1]);
+            }
+            const int x = flag[0] + flag[1];
+            int xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            if (lane == 31) wtot[warp - 1] = xi;
+            wsync();
+            int before = 0, nsg = 0;
+            for (int w2 = 0; w2 < LW; ++w2) {
+                if (w2 < warp - 1) before += wtot[w2];
+                nsg += wtot[w2];
+            }
+            int *lst = lists + L * LST;
+            int *lsrcg = lst + 2, *lrefg = lsrcg + NE2, *lstart = lrefg + NE2, *ldestg = lstart + NE2 + 1;
+            int idx = before + xi - x;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = 2 * wtid + h;
+                if (r < V) {
+                    lsrcg[r] = msrc[r];
+                    lrefg[r] = mref[r];
+                }
+                if (flag[h]) {
+                    lstart[idx] = r;
+                    ldestg[idx] = mdest[r];
+                    ++idx;
+                }
+            }
+            if (wtid == 0) {
+                lst[0] = V;
+                lst[1] = nsg;
+                lstart[nsg] = V;
+            }
+            wsync();  // the shared lists are reused by the next L
+        }
+    }
     // stale dots of the block at coordinate b1 (count nb1) against U copy R,
     // (chunk, coordinate) tasks over the given warps (neighbouring warps take
     // neighbouring coordinates of one chunk, which mostly share the U column
@@ -717,7 +851,6 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
                     if (t < nb) {
                         const double gv = g[b0 + t], av = aval[b0 + t], ia = inva[b0 + t];
                         const double d = D[b0 + t];
-                        const int i_ = pi[b0 + t], j_ = pj[b0 + t];
                         double b = gv;
                         if (nch <= 8) {
                             double v[8];
@@ -742,11 +875,8 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
                         thsh[t] = (float)(lam * ia);
                         dold[t] = d;
                         aold[t] = av;
-                        si[t] = i_;
-                        sj[t] = j_;
                     } else {
                         xsh[t] = csh[t] = thsh[t] = 0.f;
-                        si[t] = sj[t] = 0;
                     }
                 }
             }
@@ -808,21 +938,13 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
                 D[b0 + tid] = dn;
             }
             __syncthreads();
-            // row-update entries of block it (entry e = 2t + k) for the work CTAs
+            // the row-update multipliers of block it (entry e = 2t + k) for the
+            // work CTAs, three generations by block index mod 3
             if (tid < NE) {
-                const int e = tid, t = e >> 1, k = e & 1;
-                unsigned key = 0xFFFFFFFFu;
-                float mu = 0.f;
-                if (t < nb && meff[t] != 0.0) {
-                    mu = (float)meff[t];
-                    if (k == 0) key = ((unsigned)si[t] << 9) | (unsigned)e;
-                    else if (si[t] != sj[t]) key = ((unsigned)sj[t] << 9) | (unsigned)e;
-                }
-                const int64_t o = (it & 1) * NE + e;
-                gkey[o] = key;
-                gsrc[o] = k ? si[t] : sj[t];
-                gmu[o] = mu;
-                if (k == 0) mprev[t] = mu;
+                const int e = tid, t = e >> 1;
+                const float mu = t < nb ? (float)meff[t] : 0.f;
+                gmu[(it % 3) * NE + e] = mu;
+                if ((e & 1) == 0) mprev[t] = mu;
             }
             __syncthreads();
             // term of block it on block it+1; x of block it+1 loses both terms
@@ -845,184 +967,114 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
                     xn[tid] = (need2 ? xc2[0][tid] + xc2[1][tid] : 0.f) + (x1[0][tid] + x1[1][tid]);
             }
         } else {
-            // work CTA. Block it-1's staged entries are loaded first (they land
-            // during the dots); stale dots of block it+1 against copy it mod 2
-            const int sc = (int)((it + 1) & 1), sp = (int)(it & 1);  // parity of blocks it-1, it-2
-            unsigned key = 0xFFFFFFFFu;
-            int ksrc = 0;
-            float kmu = 0.f;
-            if (warp > 0 && it >= 1) {
-                const int64_t o = (int64_t)sc * NE + wtid;
-                key = gkey[o];
-                ksrc = gsrc[o];
-                kmu = gmu[o];
+            // work CTA.  The merged list of blocks it-2 and it-1 and their
+            // multipliers are loaded first (they land during the dots)
+            const int64_t L = it == 0 ? -1 : (it == 1 ? nbatch : (it - 1) % nbatch);
+            constexpr int PER = (NE2 + LT - 1) / LT;  // list words per thread and array
+            int rs[PER], rr[PER], rst[PER], rd[PER], hdr0 = 0, hdr1 = 0;
+            float rmu[PER];
+            if (L >= 0) {
+                const int *lst = lists + L * LST;
+                const int *lsrcg = lst + 2, *lrefg = lsrcg + NE2, *lstart = lrefg + NE2, *ldestg = lstart + NE2 + 1;
+                if (tid == 0) {
+                    hdr0 = lst[0];
+                    hdr1 = lst[1];
+                }
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    const int r = tid + u * LT;
+                    if (r < NE2) {
+                        rs[u] = lsrcg[r];
+                        rr[u] = lrefg[r];
+                        rst[u] = lstart[r];
+                        rd[u] = ldestg[r];
+                        // multipliers: slot 0 = block it-2, slot 1 = block it-1
+                        const int slot = r / NE, e = r - slot * NE;
+                        const int64_t blk = it - 2 + slot;
+                        rmu[u] = blk >= 0 ? gmu[(blk % 3) * NE + e] : 0.f;
+                    }
+                }
             }
+            // stale dots of block it+1 against copy it mod 2 (all warps)
             if (it + 1 < total) {
                 const int64_t nb0 = ((it + 1) % nbatch) * CD_B;
                 dots((it & 1) ? Ubuf1 : Ubuf0, nb0, (int)lmin(CD_B, np - nb0),
                      bvec + ((it + 1) & 1) * (int64_t)CD_MAX_CHUNKS * CD_B,
                      (int64_t)wb * (LT / 32) + warp, (int64_t)GW * (LT / 32));
             }
-            if (warp > 0) {
-                // sort block it-1's staged entries
-                {
-                    stsrc[wtid] = ksrc;
-                    stmu[wtid] = kmu;
-                    for (int size = 2; size <= NE; size <<= 1) {
-                        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                            unsigned other;
-                            if (stride >= 32) {
-                                sx[wtid] = key;
-                                wsync();
-                                other = sx[wtid ^ stride];
-                                wsync();
-                            } else {
-                                other = __shfl_xor_sync(0xffffffffu, key, stride);
-                            }
-                            const bool up = (wtid & size) == 0, lower = (wtid & stride) == 0;
-                            key = (lower == up) ? min(key, other) : max(key, other);
-                        }
+            if (L >= 0) {
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    const int r = tid + u * LT;
+                    if (r < NE2) {
+                        msrc[r] = rs[u];
+                        mref[r] = rr[u];
+                        seg_start[r] = rst[u];
+                        seg_dest[r] = rd[u];
+                        mutab[r] = rmu[u];
                     }
-                    const bool valid = key != 0xFFFFFFFFu;
-                    const int v = __popc(__ballot_sync(0xffffffffu, valid));
-                    if (lane == 0) wv[warp - 1] = v;
-                    if (valid) {
-                        const int e = (int)(key & 511u);
-                        ldest[sc][wtid] = (int)(key >> 9);
-                        lsrc[sc][wtid] = stsrc[e];
-                        lmu[sc][wtid] = stmu[e];
-                    }
-                    wsync();
-                    if (wtid == 0) {
-                        int V = 0;
-                        for (int w2 = 0; w2 < LW; ++w2) V += wv[w2];
-                        lcount[sc] = V;
-                    }
-                    wsync();
                 }
-                // merge: block it-2's entries before block it-1's within a row
-                {
-                    const int VP = lcount[sp], VC = lcount[sc];
-                    if (wtid < VP) {
-                        const int d = ldest[sp][wtid];
-                        int lo = 0, hi = VC;  // entries of block it-1 with dest < d
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (ldest[sc][mid] < d) lo = mid + 1;
-                            else hi = mid;
-                        }
-                        const int pos = wtid + lo;
-                        mdest[pos] = d;
-                        msrc[pos] = lsrc[sp][wtid];
-                        mmu[pos] = lmu[sp][wtid];
-                    }
-                    if (wtid < VC) {
-                        const int d = ldest[sc][wtid];
-                        int lo = 0, hi = VP;  // entries of block it-2 with dest <= d
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (ldest[sp][mid] <= d) lo = mid + 1;
-                            else hi = mid;
-                        }
-                        const int pos = wtid + lo;
-                        mdest[pos] = d;
-                        msrc[pos] = lsrc[sc][wtid];
-                        mmu[pos] = lmu[sc][wtid];
-                    }
-                    wsync();
-                    const int V = VP + VC;
-                    int flag[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int r = 2 * wtid + h;
-                        flag[h] = r < V && (r == 0 || mdest[r] != mdest[r - 1]);
-                    }
-                    const int x = flag[0] + flag[1];
-                    int xi = x;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, xi, o);
-                        if (lane >= o) xi += y;
-                    }
-                    if (lane == 31) wtot[warp - 1] = xi;
-                    wsync();
-                    int before = 0, nsg = 0;
-                    for (int w2 = 0; w2 < LW; ++w2) {
-                        if (w2 < warp - 1) before += wtot[w2];
-                        nsg += wtot[w2];
-                    }
-                    int idx = before + xi - x;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int r = 2 * wtid + h;
-                        if (flag[h]) {
-                            seg_start[idx] = r;
-                            seg_dest[idx] = mdest[r];
-                            ++idx;
-                        }
-                    }
-                    if (wtid == 0) {
-                        nseg_s = nsg;
-                        seg_start[nsg] = V;
-                    }
-                    wsync();
+                if (tid == 0) {
+                    nv_s = hdr0;
+                    nseg_s = hdr1;
                 }
+                __syncthreads();
+                if (tid == 0) seg_start[nseg_s] = nv_s;
+                __syncthreads();
                 // apply to copy (it + 1) mod 2: items (segment, group of 4 columns
                 // spaced by ncg) over the work CTAs, two per step with the loads first
-                {
-                    float *Y = (it & 1) ? Ubuf0 : Ubuf1;
-                    const int nseg = nseg_s;
-                    const int ncg = (int)((n + 3) / 4);
-                    const int items = nseg * ncg;
-                    const int nw = GW * NWK;
-                    for (int q = wb * NWK + wtid; q < items; q += 2 * nw) {
-                        const int qb = q + nw;
-                        const bool hb = qb < items;
-                        const int ka = q / ncg, ca = q - ka * ncg;
-                        const int kb = hb ? qb / ncg : ka, cb = hb ? qb - kb * ncg : ca;
-                        float *ura = Y + (int64_t)seg_dest[ka] * n, *urb = Y + (int64_t)seg_dest[kb] * n;
-                        const int ea = seg_start[ka], eb = seg_start[kb];
-                        const float ma = mmu[ea], mb = mmu[eb];
-                        const float *wa = W + (int64_t)msrc[ea] * n, *wbr = W + (int64_t)msrc[eb] * n;
-                        float ua[4], ub[4], va[4], vb[4];
+                float *Y = (it & 1) ? Ubuf0 : Ubuf1;
+                const int nseg = nseg_s;
+                const int ncg = (int)((n + 3) / 4);
+                const int items = nseg * ncg;
+                const int nw = GW * LT;
+                for (int q = wb * LT + tid; q < items; q += 2 * nw) {
+                    const int qb = q + nw;
+                    const bool hb = qb < items;
+                    const int ka = q / ncg, ca = q - ka * ncg;
+                    const int kb = hb ? qb / ncg : ka, cb = hb ? qb - kb * ncg : ca;
+                    float *ura = Y + (int64_t)seg_dest[ka] * n, *urb = Y + (int64_t)seg_dest[kb] * n;
+                    const int ea = seg_start[ka], eb = seg_start[kb];
+                    const float ma = mutab[mref[ea]], mb = mutab[mref[eb]];
+                    const float *wa = W + (int64_t)msrc[ea] * n, *wbr = W + (int64_t)msrc[eb] * n;
+                    float ua[4], ub[4], va[4], vb[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
+                        ua[r] = col < n ? ura[col] : 0.f;
+                        va[r] = col < n ? wa[col] : 0.f;
+                        ub[r] = (hb && colb < n) ? urb[colb] : 0.f;
+                        vb[r] = (hb && colb < n) ? wbr[colb] : 0.f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        ua[r] = fmaf(ma, va[r], ua[r]);
+                        ub[r] = fmaf(mb, vb[r], ub[r]);
+                    }
+                    for (int e = ea + 1; e < seg_start[ka + 1]; ++e) {
+                        const float m = mutab[mref[e]];
+                        const float *wr = W + (int64_t)msrc[e] * n;
 #pragma unroll
                         for (int r = 0; r < 4; ++r) {
-                            const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
-                            ua[r] = col < n ? ura[col] : 0.f;
-                            va[r] = col < n ? wa[col] : 0.f;
-                            ub[r] = (hb && colb < n) ? urb[colb] : 0.f;
-                            vb[r] = (hb && colb < n) ? wbr[colb] : 0.f;
+                            const int64_t col = ca + (int64_t)r * ncg;
+                            if (col < n) ua[r] = fmaf(m, wr[col], ua[r]);
                         }
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            ua[r] = fmaf(ma, va[r], ua[r]);
-                            ub[r] = fmaf(mb, vb[r], ub[r]);
-                        }
-                        for (int e = ea + 1; e < seg_start[ka + 1]; ++e) {
-                            const float m = mmu[e];
+                    }
+                    if (hb)
+                        for (int e = eb + 1; e < seg_start[kb + 1]; ++e) {
+                            const float m = mutab[mref[e]];
                             const float *wr = W + (int64_t)msrc[e] * n;
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
-                                const int64_t col = ca + (int64_t)r * ncg;
-                                if (col < n) ua[r] = fmaf(m, wr[col], ua[r]);
+                                const int64_t col = cb + (int64_t)r * ncg;
+                                if (col < n) ub[r] = fmaf(m, wr[col], ub[r]);
                             }
                         }
-                        if (hb)
-                            for (int e = eb + 1; e < seg_start[kb + 1]; ++e) {
-                                const float m = mmu[e];
-                                const float *wr = W + (int64_t)msrc[e] * n;
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) {
-                                    const int64_t col = cb + (int64_t)r * ncg;
-                                    if (col < n) ub[r] = fmaf(m, wr[col], ub[r]);
-                                }
-                            }
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
-                            if (col < n) ura[col] = ua[r];
-                            if (hb && colb < n) urb[colb] = ub[r];
-                        }
+                    for (int r = 0; r < 4; ++r) {
+                        const int64_t col = ca + (int64_t)r * ncg, colb = cb + (int64_t)r * ncg;
+                        if (col < n) ura[col] = ua[r];
+                        if (hb && colb < n) urb[colb] = ub[r];
                     }
                 }
             }
@@ -1122,10 +1174,11 @@ static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const in
     if (n > (1 << 22) || (n + DCH - 1) / DCH > CD_MAX_CHUNKS) return cudaErrorNotSupported;
     const int64_t nbatch = (np + CD_B - 1) / CD_B;
     const size_t kb = (size_t)CD_B * CD_B * sizeof(float);
-    const size_t kneed = (size_t)(3 * nbatch) * kb;
+    const size_t kbytes = (size_t)(3 * nbatch) * kb;  // intra, +1, +2 matrices
+    const size_t kneed = kbytes + (size_t)(nbatch + 1) * LST * sizeof(int);  // + merged lists
     if (kneed > (size_t)n * (size_t)n * sizeof(double)) return cudaErrorNotSupported;
     static int nsm = 0, occ = 0;
-    const size_t dyn = 3 * kb;
+    const size_t dyn = 3 * kb;  // two intra buffers and the +1 matrix
     if (!g_lag_attr) {
         cudaError_t e = cudaFuncSetAttribute(k_cd_lag2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -1157,16 +1210,18 @@ static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const in
     }
     float *Kall = reinterpret_cast<float *>(w.cd_k);
     double *bvec = w.cd_part;
-    static_assert(6 * NE * sizeof(int) <= CD_B * CD_B * sizeof(double), "staging area");
-    // staged row-update entries: 6 x NE words after the two generations of partial dots
-    int *stage = reinterpret_cast<int *>(w.cd_part + (size_t)2 * CD_MAX_CHUNKS * CD_B);
+    int *lists = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(w.cd_k) + kbytes);
+    static_assert(3 * NE * sizeof(float) <= CD_B * CD_B * sizeof(double), "multiplier area");
+    // row-update multipliers of the last three blocks, after the two
+    // generations of partial dots
+    float *gmu = reinterpret_cast<float *>(w.cd_part + (size_t)2 * CD_MAX_CHUNKS * CD_B);
     // the last pass (index total, no chain) writes copy (total + 1) mod 2: make that U
     const int64_t total = nbatch * (int64_t)nsweeps;
     float *b0 = ((total + 1) & 1) ? U2 : U, *b1 = ((total + 1) & 1) ? U : U2;
     const int G = (int)lmax(4, lmin((int64_t)nsm * occ, (n + 7) / 8));
     void *args[] = {(void *)&W, (void *)&b0, (void *)&b1, (void *)&n, (void *)&lam, (void *)&pi,
                     (void *)&pj, (void *)&np, (void *)&inva, (void *)&g, (void *)&aval, (void *)&D,
-                    (void *)&nsweeps, (void *)&bvec, (void *)&Kall, (void *)&stage, (void *)&gb};
+                    (void *)&nsweeps, (void *)&bvec, (void *)&Kall, (void *)&lists, (void *)&gmu, (void *)&gb};
     e = cudaLaunchCooperativeKernel((const void *)k_cd_lag2, dim3(G), dim3(LT), args, dyn, st);
     counted(1);
     if (e != cudaSuccess) return e;
