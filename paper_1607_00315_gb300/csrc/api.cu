@@ -89,6 +89,20 @@ void dfree(T *&p, cudaStream_t st) {
     p = nullptr;
 }
 
+// The factorisation's side stream (lowest priority, so the serial path keeps
+// the SMs it needs) and its two events, created on first use.
+cudaError_t ensure_side(Work &w) {
+    if (w.side) return cudaSuccess;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamCreateWithPriority(&w.side, cudaStreamNonBlocking, lo);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&w.ev_a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_b, cudaEventDisableTiming);
+    return e;
+}
+
 void work_free(Work &w, cudaStream_t st) {
     dfree(w.S, st); dfree(w.A, st); dfree(w.L, st); dfree(w.T, st); dfree(w.W, st); dfree(w.U, st);
     dfree(w.Xin, st); dfree(w.Xraw, st);
@@ -106,6 +120,11 @@ void work_free(Work &w, cudaStream_t st) {
     w.cap_mixed = w.cap_part = w.cap_xt = 0;
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
+    if (w.ev_a) cudaEventDestroy(w.ev_a);
+    if (w.ev_b) cudaEventDestroy(w.ev_b);
+    if (w.side) cudaStreamDestroy(w.side);
+    w.ev_a = w.ev_b = nullptr;
+    w.side = nullptr;
     w.cap_n = w.cap_pairs = w.cap_x = w.cap_xraw = w.cap_blk = w.cap_red = 0;
 }
 
@@ -519,7 +538,8 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     };
     auto fresh_factor = [&]() -> glasso_status {
         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
-        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st));
+        CK(ensure_side(w));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b));
         glasso_status s2 = factor_wait();
         if (s2 != GLASSO_OK) return s2;
         if (h->info != 0) return GLASSO_ENOTPD;
@@ -706,7 +726,8 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                         chol = true;
                         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                         sv.mark_begin(4, eb);
-                        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st));
+                        CK(ensure_side(w));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b));
                         sv.mark_end(4, eb, 2.0 * nd * nd * nd / 3.0);
                         glasso_status s2 = factor_wait();
                         if (s2 != GLASSO_OK) return s2;
@@ -1359,7 +1380,8 @@ glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, 
     CTX_CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), ctx->stream));
     CTX_CK(trial32(A, FA, n, ldf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, ctx->stream));
     sv.mark_begin(4, eb);
-    CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream));
+    CTX_CK(ensure_side(w));
+    CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream, w.side, w.ev_a, w.ev_b));
     sv.mark_end(4, eb, 2.0 * (double)n * n * n / 3.0);
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;

@@ -416,6 +416,8 @@ struct Rec {
     double *ldiag;
     DevScalars *sc;
     cudaStream_t st;
+    cudaStream_t side;  // optional: Yt runs here, beside SYRK and the right subtree
+    cudaEvent_t ev_a, ev_b;
 };
 
 cudaError_t node(const Rec &r, int64_t o, int64_t s) {
@@ -435,16 +437,35 @@ cudaError_t node(const Rec &r, int64_t o, int64_t s) {
     e = tcx(A21, X11, s2, s1, s1, ld, false, 0, 0, 1, true, XE_ASSIGN, 1.f, Z21, ld, nullptr, 0, info,
             err, r.st);
     if (e != cudaSuccess) return e;
+    // Yt = Xt11 L21^T (Xt11 upper: k >= ti 128).  It needs only the left
+    // subtree and the panel, so with a side stream it runs beside SYRK and the
+    // right subtree (it writes rows [o, o + s1) of Z; the right subtree's
+    // scratch lies in rows >= o + s1)
+    cudaStream_t ys = r.st;
+    if (r.side) {
+        e = cudaEventRecord(r.ev_a, r.st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(r.side, r.ev_a, 0);
+        if (e != cudaSuccess) return e;
+        ys = r.side;
+    }
+    e = tcx(Xt11, Z21, s1, s2, s1, ld, false, 1, 0, 0, false, XE_ASSIGN, 1.f, Z12, ld, nullptr, 0, info,
+            err, ys);
+    if (e != cudaSuccess) return e;
+    if (r.side) {
+        e = cudaEventRecord(r.ev_b, r.side);
+        if (e != cudaSuccess) return e;
+    }
     // A22 -= L21 L21^T
     e = tcx(Z21, Z21, s2, s2, s1, ld, true, 0, 0, 0, true, XE_SUB, 1.f, A22, ld, nullptr, 0, info, err,
             r.st);
     if (e != cudaSuccess) return e;
     e = node(r, o + s1, s2);
     if (e != cudaSuccess) return e;
-    // Yt = Xt11 L21^T (Xt11 upper: k >= ti 128)
-    e = tcx(Xt11, Z21, s1, s2, s1, ld, false, 1, 0, 0, false, XE_ASSIGN, 1.f, Z12, ld, nullptr, 0, info,
-            err, r.st);
-    if (e != cudaSuccess) return e;
+    // (the last record of ev_b follows this node's Yt on the side stream)
+    if (r.side) {
+        e = cudaStreamWaitEvent(r.st, r.ev_b, 0);
+        if (e != cudaSuccess) return e;
+    }
     // X21 = -X22 Yt^T (X22 lower: k < (ti + 1) 128), Xt12 = X21^T
     return tcx(X22, Z12, s2, s1, s2, ld, false, 0, 1, 0, false, XE_ASSIGN, -1.f, X21, ld, Xt12, ld,
                info, err, r.st);
@@ -458,11 +479,13 @@ cudaError_t node(const Rec &r, int64_t o, int64_t s) {
 // sc->info = first failing pivot + 1 (0 if positive definite), sc->logdet =
 // log det A (when info == 0), sc->tc_err = nonzero if a bounded wait expired.
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z,
-                       double *ldiag, DevScalars *sc, cudaStream_t st) {
+                       double *ldiag, DevScalars *sc, cudaStream_t st, cudaStream_t side,
+                       cudaEvent_t ev_a, cudaEvent_t ev_b) {
     if (ld % 32 != 0 || ld < n) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    Rec r{A, X, Xt, Z, ld, ldiag, sc, st};
+    if (side && (!ev_a || !ev_b)) return cudaErrorInvalidValue;
+    Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b};
     e = node(r, 0, n);
     if (e != cudaSuccess) return e;
     return logdet_from_diag(ldiag, n, sc, st);

@@ -111,6 +111,10 @@ struct Work {
     int64_t cap_xt = 0;
     DevScalars *sc = nullptr;              // device scalars
     DevScalars *sc_host = nullptr;         // pinned mirror
+    // a lower-priority stream and two events for the factorisation's off-path
+    // GEMMs (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 };
 
 }  // namespace glx
@@ -206,7 +210,8 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
                         DevScalars *sc, cudaStream_t st);
 cudaError_t logdet_from_diag(const double *ldiag, int64_t n, DevScalars *sc, cudaStream_t st);
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z, double *ldiag,
-                       DevScalars *sc, cudaStream_t st);
+                       DevScalars *sc, cudaStream_t st, cudaStream_t side = nullptr,
+                       cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr);
 cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t ldw, DevScalars *sc,
                      cudaStream_t st);
 cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,
