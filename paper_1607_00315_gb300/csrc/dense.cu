@@ -377,9 +377,9 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 // memory, in 8-wide steps: one thread factors and inverts each 8 x 8 diagonal
 // block in registers (the serial path: 16 such blocks), then the CTA forms
 // the panel L_ib = A_ib X_kk^T and the trailing update.  X = L^{-1} then
-// follows by 8-block substitution,
-//   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   (i > j),
-// with the inner sums parked in the free upper blocks.  Rows beyond s are
+// follows from the 8 x 8 inverses by doubling the block size,
+//   [X11 0; X21 X22] with X21 = -X22 (L21 X11),
+// with L21 X11 parked in the free upper quarter.  Rows beyond s are
 // identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
 // (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the
 // first failing pivot + 1 (global index) into sc->info.  (Column-at-a-time
@@ -431,28 +431,40 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
     __shared__ int fshare;
     const int tid = threadIdx.x;
+    constexpr int NQ = LB * LB / 4 / TPB;  // 16-byte groups per thread
     // 16-byte loads of the rows (the block starts at a multiple of 128 in a
-    // matrix whose row stride is a multiple of 32 floats), all issued at once
+    // matrix whose row stride is a multiple of 32 floats), all issued before
+    // the first shared-memory store
+    {
+        float4 v[NQ];
 #pragma unroll
-    for (int q = 0; q < LB * LB / 4 / TPB; ++q) {
-        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < s && c4 <= r) {
-            if (c4 + 3 < s) {
-                v = *reinterpret_cast<const float4 *>(A + (o + r) * ld + o + c4);
-            } else {
-                v.x = A[(o + r) * ld + o + c4];
-                if (c4 + 1 < s) v.y = A[(o + r) * ld + o + c4 + 1];
-                if (c4 + 2 < s) v.z = A[(o + r) * ld + o + c4 + 2];
+        for (int q = 0; q < NQ; ++q) {
+            const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
+            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < s && c4 <= r) {
+                const float *src = A + (o + r) * ld + o + c4;
+                if (c4 + 3 < s) {
+                    v[q] = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    v[q].x = src[0];
+                    if (c4 + 1 < s) v[q].y = src[1];
+                    if (c4 + 2 < s) v[q].z = src[2];
+                }
             }
         }
-        float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int cc = c4 + k;
-            L[r][cc] = (cc <= r && r < s) ? e[k] : (r == cc ? 1.f : 0.f);
+        for (int q = 0; q < NQ; ++q) {
+            const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
+            const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+            float f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int cc = c4 + k;
+                f[k] = (cc <= r && r < s) ? e[k] : (r == cc ? 1.f : 0.f);
+            }
+            *reinterpret_cast<float4 *>(&L[r][c4]) = make_float4(f[0], f[1], f[2], f[3]);
+            *reinterpret_cast<float4 *>(&X[r][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        *reinterpret_cast<float4 *>(&X[r][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (tid == 0) fshare = 0;
     __syncthreads();
@@ -472,9 +484,19 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j <= i) L[d + i][d + j] = a[i][j];
-                    X[d + i][d + j] = x[i][j];
+                    X[d + i][d + j] = x[i][j];  // zeros above the diagonal
                 }
         }
+    };
+    auto dot8 = [](float4 p0, float4 p1, float4 q0, float4 q1) {
+        float a0 = p0.x * q0.x, a1 = p0.y * q0.y;
+        a0 = fmaf(p0.z, q0.z, a0);
+        a1 = fmaf(p0.w, q0.w, a1);
+        a0 = fmaf(p1.x, q1.x, a0);
+        a1 = fmaf(p1.y, q1.y, a1);
+        a0 = fmaf(p1.z, q1.z, a0);
+        a1 = fmaf(p1.w, q1.w, a1);
+        return a0 + a1;
     };
     if (tid == 0) diag8(0);
     __syncthreads();
@@ -486,7 +508,8 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
         }
         const int R = LB - d0 - 8;  // rows below the diagonal block
         if (R == 0) break;
-        // panel: L[r][d0 + c] = sum_{t <= c} L[r][d0 + t] X[d0 + c][d0 + t]
+        // panel: L[r][d0 + c] = L[r][d0 .. d0 + 7] . X[d0 + c][d0 .. d0 + 7]
+        // (X's diagonal block is zero above its diagonal)
         float pv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -494,11 +517,10 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
             pv[q] = 0.f;
             if (idx < R * 8) {
                 const int r = d0 + 8 + idx / 8, c = idx % 8;
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (t <= c) acc = fmaf(L[r][d0 + t], X[d0 + c][d0 + t], acc);
-                pv[q] = acc;
+                pv[q] = dot8(*reinterpret_cast<const float4 *>(&L[r][d0]),
+                             *reinterpret_cast<const float4 *>(&L[r][d0 + 4]),
+                             *reinterpret_cast<const float4 *>(&X[d0 + c][d0]),
+                             *reinterpret_cast<const float4 *>(&X[d0 + c][d0 + 4]));
             }
         }
         __syncthreads();
@@ -513,20 +535,21 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
             // look-ahead: warp 0 updates the next diagonal block (36 entries)
             // and one lane factors it while warps 1..7 update the rest
             for (int e = c; e < 36; e += 32) {
-                int i = 0;
-                while ((i + 1) * (i + 2) / 2 <= e) ++i;
+                int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);  // row of entry e (j <= i)
+                if ((i + 1) * (i + 2) / 2 <= e) ++i;
+                if (i * (i + 1) / 2 > e) --i;
                 const int j = e - i * (i + 1) / 2;
-                float acc = 0.f;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) acc = fmaf(L[b0 + i][d0 + t], L[b0 + j][d0 + t], acc);
-                L[b0 + i][b0 + j] -= acc;
+                L[b0 + i][b0 + j] -= dot8(*reinterpret_cast<const float4 *>(&L[b0 + i][d0]),
+                                          *reinterpret_cast<const float4 *>(&L[b0 + i][d0 + 4]),
+                                          *reinterpret_cast<const float4 *>(&L[b0 + j][d0]),
+                                          *reinterpret_cast<const float4 *>(&L[b0 + j][d0 + 4]));
             }
             __syncwarp();
             if (c == 0) diag8(b0);
         } else {
             // trailing update of the lower part outside the next diagonal
             // block: warp g takes rows b0 + (g - 1) + 7 k, lane c columns
-            // b0 + c + 32 p (only j <= i)
+            // b0 + c + 32 p (only j <= i); four rows in flight
             for (int pc = 0; pc * 32 < R; ++pc) {
                 const int j = b0 + c + 32 * pc;
                 if (j >= LB) continue;
@@ -537,101 +560,122 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
                 if (j < b0 + 8) {
                     while (i < b0 + 8) i += 7;  // rows of the next diagonal block are warp 0's
                 }
+                for (; i + 21 < LB; i += 28) {
+                    float4 p0[4], p1[4];
+                    float cur[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        p0[u] = *reinterpret_cast<const float4 *>(&L[i + 7 * u][d0]);
+                        p1[u] = *reinterpret_cast<const float4 *>(&L[i + 7 * u][d0 + 4]);
+                        cur[u] = L[i + 7 * u][j];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) L[i + 7 * u][j] = cur[u] - dot8(p0[u], p1[u], j0, j1);
+                }
                 for (; i < LB; i += 7) {
                     const float4 i0 = *reinterpret_cast<const float4 *>(&L[i][d0]);
                     const float4 i1 = *reinterpret_cast<const float4 *>(&L[i][d0 + 4]);
-                    float a0 = i0.x * j0.x, a1 = i0.y * j0.y;
-                    a0 = fmaf(i0.z, j0.z, a0);
-                    a1 = fmaf(i0.w, j0.w, a1);
-                    a0 = fmaf(i1.x, j1.x, a0);
-                    a1 = fmaf(i1.y, j1.y, a1);
-                    a0 = fmaf(i1.z, j1.z, a0);
-                    a1 = fmaf(i1.w, j1.w, a1);
-                    L[i][j] -= a0 + a1;
+                    L[i][j] -= dot8(i0, i1, j0, j1);
                 }
             }
         }
         __syncthreads();
     }
     for (int r = tid; r < s; r += TPB) ldiag[o + r] = (double)L[r][r];
-    // off-diagonal 8-blocks of the inverse by block distance:
-    // T_ij = sum_{k=8jb}^{8ib-1} L[8ib+r][k] X[k][8jb+c] (parked in the upper
-    // block), then X_ij = -X_ii T_ij.  A thread owns a 4 x 2 tile of a block
-    // (8 tiles per block), so each loaded value feeds two or four FMAs.
-    for (int diff = 1; diff < LB / 8; ++diff) {
-        const int nblk = LB / 8 - diff;
-        const int item = tid;  // nblk * 8 tiles <= 120 < TPB
-        float t8[4][2];
-        const bool act = item < nblk * 8;
-        const int jb = item / 8, tt = item % 8, ib = jb + diff;
-        const int r0 = 4 * (tt / 4), c0 = 2 * (tt % 4);
-        if (act) {
+    // X = L^{-1} from the 8 x 8 diagonal inverses by doubling: for blocks of
+    // size bs = 16, 32, 64, 128 with halves h, X21 = -X22 (L21 X11).  The
+    // product T = L21 X11 is parked in the block's upper-right quarter (above
+    // the diagonal, masked out of X below).  Each thread forms a 4 x 4 tile.
+#pragma unroll 1
+    for (int bs = 16; bs <= LB; bs *= 2) {
+        const int h = bs / 2, th = h / 4, tpp = th * th, ntile = (LB / bs) * tpp;
+        for (int it = tid; it < ntile; it += TPB) {
+            const int p = (it / tpp) * bs, tt = it % tpp, r0 = 4 * (tt / th), c0 = 4 * (tt % th);
+            float acc[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) t8[a][0] = t8[a][1] = 0.f;
-            for (int k = 8 * jb; k < 8 * ib; ++k) {
-                const float x0 = X[k][8 * jb + c0], x1 = X[k][8 * jb + c0 + 1];
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            for (int k = c0; k < h; ++k) {  // X11[k][c] = 0 for k < c
+                const float4 xq = *reinterpret_cast<const float4 *>(&X[p + k][p + c0]);
+                const float xv[4] = {k >= c0 ? xq.x : 0.f, k >= c0 + 1 ? xq.y : 0.f,
+                                     k >= c0 + 2 ? xq.z : 0.f, k >= c0 + 3 ? xq.w : 0.f};
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float l = L[8 * ib + r0 + a][k];
-                    t8[a][0] = fmaf(l, x0, t8[a][0]);
-                    t8[a][1] = fmaf(l, x1, t8[a][1]);
+                    const float lv = L[p + h + r0 + a][p + k];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(lv, xv[b], acc[a][b]);
                 }
             }
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                X[8 * jb + r0 + a][8 * ib + c0] = t8[a][0];
-                X[8 * jb + r0 + a][8 * ib + c0 + 1] = t8[a][1];
-            }
+            for (int a = 0; a < 4; ++a)
+                *reinterpret_cast<float4 *>(&X[p + r0 + a][p + h + c0]) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
         }
         __syncthreads();
-        // X_ij rows r0..r0+3 = -X_ii[r][0..r] T[0..r][c0..c0+1]
-        float u[4][2];
+        for (int it = tid; it < ntile; it += TPB) {
+            const int p = (it / tpp) * bs, tt = it % tpp, r0 = 4 * (tt / th), c0 = 4 * (tt % th);
+            float acc[4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) u[a][0] = u[a][1] = 0.f;
-        if (act) {
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const float y0 = X[8 * jb + t][8 * ib + c0], y1 = X[8 * jb + t][8 * ib + c0 + 1];
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            const int kend = r0 + 4 < h ? r0 + 4 : h;
+            for (int k = 0; k < kend; ++k) {  // X22[r][k] = 0 for k > r
+                const float4 tq = *reinterpret_cast<const float4 *>(&X[p + k][p + h + c0]);
+                const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    if (t <= r0 + a) {
-                        const float xi = X[8 * ib + r0 + a][8 * ib + t];
-                        u[a][0] = fmaf(xi, y0, u[a][0]);
-                        u[a][1] = fmaf(xi, y1, u[a][1]);
-                    }
+                    const float xv = k <= r0 + a ? X[p + h + r0 + a][p + h + k] : 0.f;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv, tv[b], acc[a][b]);
                 }
             }
-        }
-        __syncthreads();
-        if (act) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                X[8 * ib + r0 + a][8 * jb + c0] = -u[a][0];
-                X[8 * ib + r0 + a][8 * jb + c0 + 1] = -u[a][1];
-            }
+            for (int a = 0; a < 4; ++a)
+                *reinterpret_cast<float4 *>(&X[p + h + r0 + a][p + c0]) =
+                    make_float4(-acc[a][0], -acc[a][1], -acc[a][2], -acc[a][3]);
         }
         __syncthreads();
     }
-    // X rows with 16-byte stores (zeros above the diagonal), X^T by columns of X
+    // X rows with 16-byte stores (zeros above the diagonal); X^T staged in
+    // L's space with stride LB + 1 (conflict-free transposition), then rows
+    // of X^T with 16-byte stores
+    float *Lt = lsm;
+    constexpr int LTS = LB + 1;
 #pragma unroll 4
-    for (int q = 0; q < LB * LB / 4 / TPB; ++q) {
+    for (int q = 0; q < NQ; ++q) {
         const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-        if (r >= s || c4 >= s) continue;
-        float4 v = *reinterpret_cast<const float4 *>(&X[r][c4]);
+        const float4 v = *reinterpret_cast<const float4 *>(&X[r][c4]);
         float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (c4 + k > r) e[k] = 0.f;
-        if (c4 + 3 < s) {
-            *reinterpret_cast<float4 *>(Xo + (o + r) * ld + o + c4) = make_float4(e[0], e[1], e[2], e[3]);
-        } else {
-            for (int k = 0; k < 4 && c4 + k < s; ++k) Xo[(o + r) * ld + o + c4 + k] = e[k];
+        if (r < s && c4 < s) {
+            if (c4 + 3 < s) {
+                *reinterpret_cast<float4 *>(Xo + (o + r) * ld + o + c4) = make_float4(e[0], e[1], e[2], e[3]);
+            } else {
+                for (int k = 0; k < 4 && c4 + k < s; ++k) Xo[(o + r) * ld + o + c4 + k] = e[k];
+            }
         }
     }
+    __syncthreads();  // L is free (ldiag was read before the inverse)
 #pragma unroll 4
     for (int q = 0; q < LB * LB / TPB; ++q) {
         const int idx = tid + TPB * q, r = idx / LB, cc = idx % LB;
-        if (r < s && cc < s) Xto[(o + r) * ld + o + cc] = (cc >= r) ? X[cc][r] : 0.f;
+        Lt[cc * LTS + r] = (cc <= r) ? X[r][cc] : 0.f;  // Lt[c][r] = X[r][c] (lower X)
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < NQ; ++q) {
+        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
+        if (r >= s || c4 >= s) continue;
+        const float *row = Lt + r * LTS + c4;
+        if (c4 + 3 < s) {
+            *reinterpret_cast<float4 *>(Xto + (o + r) * ld + o + c4) = make_float4(row[0], row[1], row[2], row[3]);
+        } else {
+            for (int k = 0; k < 4 && c4 + k < s; ++k) Xto[(o + r) * ld + o + c4 + k] = row[k];
+        }
     }
 }
 
