@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
 constexpr int LB = 128, LP = LB + 4;  // rows padded to 16-byte multiples
 constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
 
-// One thread: Cholesky of the 8 x 8 lower block a (registers) in place and
-// x = L^{-1}; rd[i] = 1 / L_ii.  Returns 0 or the failing pivot + 1.
-__device__ __forceinline__ int thread_chol_inv8(float (&a)[8][8], float (&x)[8][8], float (&rd)[8]) {
+// One thread: Cholesky of the 8 x 8 lower block a (registers) in place;
+// rd[i] = 1 / L_ii.  Returns 0 or the failing pivot + 1.
+__device__ __forceinline__ int thread_chol8(float (&a)[8][8], float (&rd)[8]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const float d = a[j][j];
@@ -405,19 +405,6 @@ __device__ __forceinline__ int thread_chol_inv8(float (&a)[8][8], float (&x)[8][
 #pragma unroll
             for (int k = j + 1; k <= i; ++k) a[i][k] = fmaf(-a[i][j], a[k][j], a[i][k]);
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (i < c) {
-                x[i][c] = 0.f;
-            } else {
-                float s = (i == c) ? 1.f : 0.f;
-#pragma unroll
-                for (int t = c; t < i; ++t) s = fmaf(-a[i][t], x[t][c], s);
-                x[i][c] = s * rd[i];
-            }
-        }
     return 0;
 }
 
@@ -430,6 +417,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
     __shared__ int fshare;
+    __shared__ float rdg[8];
     const int tid = threadIdx.x;
     constexpr int NQ = LB * LB / 4 / TPB;  // 16-byte groups per thread
     // 16-byte loads of the rows (the block starts at a multiple of 128 in a
@@ -468,24 +456,55 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     }
     if (tid == 0) fshare = 0;
     __syncthreads();
-    // one thread: factor and invert the 8 x 8 diagonal block at d (registers)
-    auto diag8 = [&](int d) {
-        float a[8][8], x[8][8], rd[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
-        const int f = thread_chol_inv8(a, x, rd);
-        if (f) {
-            fshare = d + f;
-        } else {
+    // warp 0: factor the 8 x 8 diagonal block at d (lane 0, registers), then
+    // lanes 0..7 form one column each of its inverse by forward substitution,
+    //   x_cc = 1 / L_cc,  x_ic = -(sum_{t<i} L_it x_tc) / L_ii  (x_tc = 0, t < c)
+    auto diag8 = [&](int d, int lane) {
+        if (lane == 0) {
+            float a[8][8], rd[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j <= i) L[d + i][d + j] = a[i][j];
-                    X[d + i][d + j] = x[i][j];  // zeros above the diagonal
+                for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
+            const int f = thread_chol8(a, rd);
+            if (f) {
+                fshare = d + f;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) L[d + i][d + j] = a[i][j];
+                    rdg[i] = rd[i];
                 }
+            }
+        }
+        __syncwarp();
+        if (lane < 8 && !fshare) {
+            const int cc = lane;
+            float lr[8][8];
+#pragma unroll
+            for (int i = 1; i < 8; ++i) {
+                const float4 v0 = *reinterpret_cast<const float4 *>(&L[d + i][d]);
+                const float4 v1 = *reinterpret_cast<const float4 *>(&L[d + i][d + 4]);
+                lr[i][0] = v0.x, lr[i][1] = v0.y, lr[i][2] = v0.z, lr[i][3] = v0.w;
+                lr[i][4] = v1.x, lr[i][5] = v1.y, lr[i][6] = v1.z, lr[i][7] = v1.w;
+            }
+            float rdv[8], x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) rdv[i] = rdg[i];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i == 0) {
+                    x[0] = cc == 0 ? rdv[0] : 0.f;
+                } else {
+                    float sum = 0.f;
+#pragma unroll
+                    for (int t = 0; t < i; ++t) sum = fmaf(lr[i][t], x[t], sum);
+                    x[i] = i < cc ? 0.f : (i == cc ? rdv[i] : -sum * rdv[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) X[d + i][d + cc] = x[i];  // zeros above the diagonal
         }
     };
     auto dot8 = [](float4 p0, float4 p1, float4 q0, float4 q1) {
@@ -498,7 +517,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
         a1 = fmaf(p1.w, q1.w, a1);
         return a0 + a1;
     };
-    if (tid == 0) diag8(0);
+    if (tid < 32) diag8(0, tid);
     __syncthreads();
     for (int d0 = 0; d0 < LB; d0 += 8) {
         // diagonal block d0 is factored (look-ahead from the previous step)
@@ -534,48 +553,58 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
         if (g == 0) {
             // look-ahead: warp 0 updates the next diagonal block (36 entries)
             // and one lane factors it while warps 1..7 update the rest
-            for (int e = c; e < 36; e += 32) {
-                int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);  // row of entry e (j <= i)
-                if ((i + 1) * (i + 2) / 2 <= e) ++i;
-                if (i * (i + 1) / 2 > e) --i;
-                const int j = e - i * (i + 1) / 2;
-                L[b0 + i][b0 + j] -= dot8(*reinterpret_cast<const float4 *>(&L[b0 + i][d0]),
-                                          *reinterpret_cast<const float4 *>(&L[b0 + i][d0 + 4]),
-                                          *reinterpret_cast<const float4 *>(&L[b0 + j][d0]),
-                                          *reinterpret_cast<const float4 *>(&L[b0 + j][d0 + 4]));
+            {
+                // entries e = c and c + 32 (< 36) of the block's lower triangle
+                int ii[2], jj[2];
+                float4 a0[2], a1[2], q0[2], q1[2];
+                float cur[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = c + 32 * u < 36 ? c + 32 * u : 0;
+                    int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);  // row of entry e (j <= i)
+                    if ((i + 1) * (i + 2) / 2 <= e) ++i;
+                    if (i * (i + 1) / 2 > e) --i;
+                    ii[u] = i;
+                    jj[u] = e - i * (i + 1) / 2;
+                    a0[u] = *reinterpret_cast<const float4 *>(&L[b0 + i][d0]);
+                    a1[u] = *reinterpret_cast<const float4 *>(&L[b0 + i][d0 + 4]);
+                    q0[u] = *reinterpret_cast<const float4 *>(&L[b0 + jj[u]][d0]);
+                    q1[u] = *reinterpret_cast<const float4 *>(&L[b0 + jj[u]][d0 + 4]);
+                    cur[u] = L[b0 + i][b0 + jj[u]];
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (c + 32 * u < 36) L[b0 + ii[u]][b0 + jj[u]] = cur[u] - dot8(a0[u], a1[u], q0[u], q1[u]);
             }
             __syncwarp();
-            if (c == 0) diag8(b0);
+            diag8(b0, c);
         } else {
             // trailing update of the lower part outside the next diagonal
-            // block: warp g takes rows b0 + (g - 1) + 7 k, lane c columns
-            // b0 + c + 32 p (only j <= i); four rows in flight
-            for (int pc = 0; pc * 32 < R; ++pc) {
-                const int j = b0 + c + 32 * pc;
-                if (j >= LB) continue;
-                const float4 j0 = *reinterpret_cast<const float4 *>(&L[j][d0]);
-                const float4 j1 = *reinterpret_cast<const float4 *>(&L[j][d0 + 4]);
-                int i = b0 + (g - 1);
-                if (i < j) i += ((j - i + 6) / 7) * 7;
-                if (j < b0 + 8) {
-                    while (i < b0 + 8) i += 7;  // rows of the next diagonal block are warp 0's
-                }
-                for (; i + 21 < LB; i += 28) {
-                    float4 p0[4], p1[4];
-                    float cur[4];
+            // block, 4 x 4 register tiles (I, J), J <= I, in units of 4 from
+            // b0; tiles 0..2 (the next diagonal block) are warp 0's
+            const int TI = R / 4, ntl = TI * (TI + 1) / 2;
+            for (int qq = 3 + (tid - 32); qq < ntl; qq += TPB - 32) {
+                int I = (int)((sqrtf(8.f * qq + 1.f) - 1.f) * 0.5f);
+                if ((I + 1) * (I + 2) / 2 <= qq) ++I;
+                if (I * (I + 1) / 2 > qq) --I;
+                const int J = qq - I * (I + 1) / 2;
+                const int i0 = b0 + 4 * I, j0 = b0 + 4 * J;
+                float4 p0[4], p1[4], r0[4], r1[4], cv[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        p0[u] = *reinterpret_cast<const float4 *>(&L[i + 7 * u][d0]);
-                        p1[u] = *reinterpret_cast<const float4 *>(&L[i + 7 * u][d0 + 4]);
-                        cur[u] = L[i + 7 * u][j];
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) L[i + 7 * u][j] = cur[u] - dot8(p0[u], p1[u], j0, j1);
+                for (int u = 0; u < 4; ++u) {
+                    p0[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][d0]);
+                    p1[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][d0 + 4]);
+                    r0[u] = *reinterpret_cast<const float4 *>(&L[j0 + u][d0]);
+                    r1[u] = *reinterpret_cast<const float4 *>(&L[j0 + u][d0 + 4]);
+                    cv[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][j0]);
                 }
-                for (; i < LB; i += 7) {
-                    const float4 i0 = *reinterpret_cast<const float4 *>(&L[i][d0]);
-                    const float4 i1 = *reinterpret_cast<const float4 *>(&L[i][d0 + 4]);
-                    L[i][j] -= dot8(i0, i1, j0, j1);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float o4[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (I != J || v <= u) o4[v] -= dot8(p0[u], p1[u], r0[v], r1[v]);
+                    *reinterpret_cast<float4 *>(&L[i0 + u][j0]) = make_float4(o4[0], o4[1], o4[2], o4[3]);
                 }
             }
         }
@@ -596,6 +625,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
             for (int k = c0; k < h; ++k) {  // X11[k][c] = 0 for k < c
                 const float4 xq = *reinterpret_cast<const float4 *>(&X[p + k][p + c0]);
                 const float xv[4] = {k >= c0 ? xq.x : 0.f, k >= c0 + 1 ? xq.y : 0.f,
@@ -621,6 +651,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
             const int kend = r0 + 4 < h ? r0 + 4 : h;
+#pragma unroll 4
             for (int k = 0; k < kend; ++k) {  // X22[r][k] = 0 for k > r
                 const float4 tq = *reinterpret_cast<const float4 *>(&X[p + k][p + h + c0]);
                 const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
