@@ -391,10 +391,12 @@ constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
 // One thread: Cholesky of the 8 x 8 lower block a (registers) in place;
 // rd[i] = 1 / L_ii.  Returns 0 or the failing pivot + 1.
 __device__ __forceinline__ int thread_chol8(float (&a)[8][8], float (&rd)[8]) {
+    int fail = 0;  // recorded, not branched on: the pivot chain stays straight-line
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float d = a[j][j];
-        if (!(d > 0.f)) return j + 1;
+        float d = a[j][j];
+        if (fail == 0 && !(d > 0.f)) fail = j + 1;
+        d = d > 0.f ? d : 1.f;
         const float r = rsqrt_newton(d);
         rd[j] = r;
         a[j][j] = d * r;
@@ -405,7 +407,7 @@ __device__ __forceinline__ int thread_chol8(float (&a)[8][8], float (&rd)[8]) {
 #pragma unroll
             for (int k = j + 1; k <= i; ++k) a[i][k] = fmaf(-a[i][j], a[k][j], a[i][k]);
     }
-    return 0;
+    return fail;
 }
 
 __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
@@ -417,7 +419,6 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
     float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
     __shared__ int fshare;
-    __shared__ float rdg[8];
     const int tid = threadIdx.x;
     constexpr int NQ = LB * LB / 4 / TPB;  // 16-byte groups per thread
     // 16-byte loads of the rows (the block starts at a multiple of 128 in a
@@ -456,56 +457,40 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
     }
     if (tid == 0) fshare = 0;
     __syncthreads();
-    // warp 0: factor the 8 x 8 diagonal block at d (lane 0, registers), then
-    // lanes 0..7 form one column each of its inverse by forward substitution,
-    //   x_cc = 1 / L_cc,  x_ic = -(sum_{t<i} L_it x_tc) / L_ii  (x_tc = 0, t < c)
-    auto diag8 = [&](int d, int lane) {
-        if (lane == 0) {
-            float a[8][8], rd[8];
+    // one thread: factor and invert the 8 x 8 diagonal block at d (registers;
+    // the eight columns of the inverse are independent chains, so one thread
+    // keeps them all in flight)
+    auto diag8 = [&](int d) {
+        float a[8][8], x[8][8], rd[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
-            const int f = thread_chol8(a, rd);
-            if (f) {
-                fshare = d + f;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-#pragma unroll
-                    for (int j = 0; j <= i; ++j) L[d + i][d + j] = a[i][j];
-                    rdg[i] = rd[i];
-                }
-            }
+            for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
+        const int f = thread_chol8(a, rd);
+        if (f) {
+            fshare = d + f;
+            return;
         }
-        __syncwarp();
-        if (lane < 8 && !fshare) {
-            const int cc = lane;
-            float lr[8][8];
 #pragma unroll
-            for (int i = 1; i < 8; ++i) {
-                const float4 v0 = *reinterpret_cast<const float4 *>(&L[d + i][d]);
-                const float4 v1 = *reinterpret_cast<const float4 *>(&L[d + i][d + 4]);
-                lr[i][0] = v0.x, lr[i][1] = v0.y, lr[i][2] = v0.z, lr[i][3] = v0.w;
-                lr[i][4] = v1.x, lr[i][5] = v1.y, lr[i][6] = v1.z, lr[i][7] = v1.w;
-            }
-            float rdv[8], x[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) rdv[i] = rdg[i];
+        for (int cc = 0; cc < 8; ++cc)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                if (i == 0) {
-                    x[0] = cc == 0 ? rdv[0] : 0.f;
+                if (i < cc) {
+                    x[i][cc] = 0.f;
                 } else {
-                    float sum = 0.f;
+                    float sum = (i == cc) ? 1.f : 0.f;
 #pragma unroll
-                    for (int t = 0; t < i; ++t) sum = fmaf(lr[i][t], x[t], sum);
-                    x[i] = i < cc ? 0.f : (i == cc ? rdv[i] : -sum * rdv[i]);
+                    for (int t = cc; t < i; ++t) sum = fmaf(-a[i][t], x[t][cc], sum);
+                    x[i][cc] = sum * rd[i];
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) X[d + i][d + cc] = x[i];  // zeros above the diagonal
-        }
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j <= i) L[d + i][d + j] = a[i][j];
+                X[d + i][d + j] = x[i][j];  // zeros above the diagonal
+            }
     };
     auto dot8 = [](float4 p0, float4 p1, float4 q0, float4 q1) {
         float a0 = p0.x * q0.x, a1 = p0.y * q0.y;
@@ -517,7 +502,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
         a1 = fmaf(p1.w, q1.w, a1);
         return a0 + a1;
     };
-    if (tid < 32) diag8(0, tid);
+    if (tid == 0) diag8(0);
     __syncthreads();
     for (int d0 = 0; d0 < LB; d0 += 8) {
         // diagonal block d0 is factored (look-ahead from the previous step)
@@ -577,7 +562,7 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
                     if (c + 32 * u < 36) L[b0 + ii[u]][b0 + jj[u]] = cur[u] - dot8(a0[u], a1[u], q0[u], q1[u]);
             }
             __syncwarp();
-            diag8(b0, c);
+            if (c == 0) diag8(b0);
         } else {
             // trailing update of the lower part outside the next diagonal
             // block, 4 x 4 register tiles (I, J), J <= I, in units of 4 from
