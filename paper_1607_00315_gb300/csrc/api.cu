@@ -479,8 +479,9 @@ done:
 // solve_core; the differences are confined to how W and the line-search
 // log-det are obtained (mixed.cu):
 //  * W (FP64) comes from the previous W by Newton-Schulz refinement against
-//    the new A (FP32 GEMM corrections, FP64 residual), or after a large step
-//    from an FP32 Cholesky + inverse, then refined the same way;
+//    the new A (TF32 GEMM corrections, residual and sum in double-float FP32
+//    arithmetic), or after a large step from an FP32 Cholesky + inverse, then
+//    refined the same way;
 //  * the CD sweep runs on FP32 copies of W and U (an inexact Hessian, which
 //    the convergence theory of Section 4.1 allows), with the FP64 gradient;
 //  * the line search uses the log-det series when its remainder bound is below
@@ -502,8 +503,10 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     const size_t nn = (size_t)n * (size_t)n;
     const int64_t ldf = tc_pad(n);
     float *FA = w.fa, *FX = FA + n * ldf, *FXt = FX + n * ldf, *FZ = FXt + n * ldf;
+    // W during refinement: W32 + Wlo (double-float); W32 is also the FP32 copy
+    // the sweep and the series read, W64 the FP64 W after refinement
     float *W32 = (float *)w.L, *R32 = W32 + nn;
-    float *U32 = (float *)w.U;
+    float *U32 = (float *)w.U, *Wlo = U32 + nn;
     double *W64 = w.W;
     const double sigma = 1e-4;
     const int max_trials = 30;
@@ -525,6 +528,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         sv.mark_begin(1, eb);
         CK(lauum_tc(FXt, n, ldf, W32, n, sc, st));
         CK(to_f64(W32, W64, (int64_t)nn, st));
+        CK(cudaMemsetAsync(Wlo, 0, nn * sizeof(float), st));
         sv.mark_end(1, eb, nd * nd * nd / 3.0);
         return GLASSO_OK;
     };
@@ -551,7 +555,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         bool restarted = false;
         ns_steps = 0;
         for (int it = 0; it < max_ns; ++it, ++ns_steps) {
-            CK(residual(w.csr_ptr, w.csr_col, w.csr_val, W64, n, R32, W32, w.rowred, sc, st));
+            CK(residual(w.csr_ptr, w.csr_col, w.csr_val, W32, Wlo, n, R32, w.rowred, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->tc_err) {
                 err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
@@ -567,9 +571,10 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                 continue;
             }
             sv.mark_begin(5, eb);
-            CK(ns_gemm_tc(W64, R32, n, W64, w.Wp, w.Qp, &sc->tc_err, st));
+            CK(ns_gemm_tc(W32, Wlo, R32, n, w.Wp, w.Qp, &sc->tc_err, st));
             sv.mark_end(5, eb, nd * nd * nd);
         }
+        CK(join64(W32, Wlo, W64, (int64_t)nn, st));  // the FP64 W of the gradient and the pairs
         return GLASSO_OK;
     };
     auto update_W = [&]() -> glasso_status {
@@ -584,7 +589,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     if (!have_A0) {
         CK(init_diag(w.S, n, lam, w.A, sc, st));
         CK(diag_inverse(w.A, n, W64, w.ldiag, sc, st));
-        CK(to_f32(W64, W32, (int64_t)nn, st));
+        CK(split64(W64, W32, Wlo, (int64_t)nn, st));
         if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
         if (h->err) return GLASSO_ENOTPD;
         logdet = h->logdet;

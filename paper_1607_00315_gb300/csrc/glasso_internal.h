@@ -187,8 +187,8 @@ cudaError_t hierarchy(const double *absg, const uint8_t *insupp, int64_t nf, uin
 // ---- launchers (mixed.cu) ----
 cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, double *val,
                       cudaStream_t st);
-cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const double *W64,
-                     int64_t n, float *R32, float *W32, double *rowstat, DevScalars *sc,
+cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const float *Whi,
+                     const float *Wlo, int64_t n, float *R32, double *rowstat, DevScalars *sc,
                      cudaStream_t st);
 cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const int32_t *pj,
                          const double *D, int64_t np, const float *U32, double *part, int64_t cap,
@@ -196,6 +196,8 @@ cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const 
 cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float *U2, float *U3,
                         double *part, int64_t cap, DevScalars *sc, cudaStream_t st);
 cudaError_t to_f32(const double *x, float *y, int64_t m, cudaStream_t st);
+cudaError_t split64(const double *W, float *hi, float *lo, int64_t m, cudaStream_t st);
+cudaError_t join64(const float *hi, const float *lo, double *W, int64_t m, cudaStream_t st);
 cudaError_t to_f64(const float *x, double *y, int64_t m, cudaStream_t st);
 cudaError_t trial32(const double *A, float *T, int64_t n, int64_t ldT, const int32_t *pi,
                     const int32_t *pj, const double *aval, const double *D, int64_t np, double alpha,
@@ -218,8 +220,8 @@ cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld,
                           cudaStream_t st);
 cudaError_t syrk_split(const float *Xt, int64_t n, int64_t m, int64_t ldx, double scale, double *S,
                        int *err, cudaStream_t st);
-cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
-                       float *Qp, int *err, cudaStream_t st);
+cudaError_t ns_gemm_tc(float *Whi, float *Wlo, const float *R32, int64_t n, float *Wp, float *Qp,
+                       int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
                     float *Xt, int *err, cudaStream_t st);
 cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, cudaStream_t st);

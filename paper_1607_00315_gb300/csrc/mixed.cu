@@ -2,13 +2,20 @@
 //
 // The bulk arithmetic moves to FP32 / TF32 while the quantities that decide
 // the answer stay FP64:
-//  * W = A^{-1} is kept in FP64 and refined against A by Newton-Schulz steps
-//        R = I - A W            (FP64, A sparse: CSR of its nonzeros)
+//  * W = A^{-1} is refined against A by Newton-Schulz steps
+//        R = I - A W            (A sparse: CSR of its nonzeros)
 //        W <- W + W R           (TF32 tensor-core GEMM of the small correction,
-//                                FP64 sum, tc.cu)
-//    until |R| reaches 1e-11; the gradient S - W, the free set and the KKT
-//    residual therefore see an FP64-accurate W (eq. gradHes, eq. active_set,
-//    the Section 8 stopping rule).
+//                                tc.cu)
+//    until |R| reaches 1e-11, and then rounded to FP64; the gradient S - W,
+//    the free set and the KKT residual therefore see an FP64-accurate W (eq.
+//    gradHes, eq. active_set, the Section 8 stopping rule).  During the
+//    refinement W is a pair of FP32 arrays, W = hi + lo (|lo| <= ulp(hi) / 2,
+//    about 48 significant bits), and R and the update are formed with
+//    error-free products and sums in FP32 (FP64 arithmetic runs at a small
+//    fraction of the FP32 rate on this GPU): per term, a_hi w_hi = p + e
+//    exactly (p rounded, e = fma(a_hi, w_hi, -p)), the cross terms a_hi w_lo +
+//    a_lo w_hi in FP32 (relative 2^-48 of the product), and the running sum
+//    kept as hi + lo with Knuth's two-sum.
 //  * The line search (Section 6.1.2) gets log det(A + alpha Delta) - log det A
 //    from the series  sum_k (-1)^{k+1} alpha^k t_k / k,  t_k = tr((W Delta)^k):
 //    t1 on the pairs (FP64), t2 = sum U_kj U_jk with U = Delta W from the
@@ -91,45 +98,64 @@ __global__ void k_nz_write(const double *__restrict__ A, int64_t n, const long l
     }
 }
 
-// ---- residual R = I - A W (FP64), W32 = float(W), per-row max and sum of squares
+// ---- residual R = I - A W with W = hi + lo (double-float), per-row max and
+// sum of squares of R (FP32; they decide convergence against 1e-11 and the
+// restart at |R|_F >= 0.9).  The CSR values of A are split into FP32 pairs
+// as they are staged.
 constexpr int RES_T = 256;
 constexpr int RES_CAP = 256;  // nonzeros of a row staged per pass
 
 __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict__ ptr,
                                                     const int32_t *__restrict__ col,
                                                     const double *__restrict__ val,
-                                                    const double *__restrict__ W64, int64_t n,
-                                                    float *__restrict__ R32, float *__restrict__ W32,
+                                                    const float *__restrict__ Whi,
+                                                    const float *__restrict__ Wlo, int64_t n,
+                                                    float *__restrict__ R32,
                                                     double *__restrict__ rowstat) {
     __shared__ int32_t sc[RES_CAP];
-    __shared__ double sv[RES_CAP];
-    __shared__ double rmax[RES_T], rsq[RES_T];
+    __shared__ float sh[RES_CAP], sl[RES_CAP];
+    __shared__ float rmax[RES_T], rsq[RES_T];
     const int64_t i = blockIdx.x;
     const long long p0 = ptr[i], p1 = ptr[i + 1];
-    double mx = 0.0, sq = 0.0;
-    // columns handled by this thread, in registers for up to 16 chunks of RES_T
+    float mx = 0.f, sq = 0.f;
+    // columns handled by this thread, in registers for up to 8 chunks of RES_T
     for (int64_t c0 = 0; c0 < n; c0 += (int64_t)RES_T * 8) {
-        double acc[8];
+        float ah[8], al[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
-            acc[q] = (cidx == i) ? 1.0 : 0.0;
+            ah[q] = (cidx == i) ? 1.f : 0.f;
+            al[q] = 0.f;
         }
         for (long long pb = p0; pb < p1; pb += RES_CAP) {
             const int cntk = (int)lmin(RES_CAP, p1 - pb);
             __syncthreads();
             for (int t = threadIdx.x; t < cntk; t += RES_T) {
+                const double a = val[pb + t];
+                const float h = (float)a;
                 sc[t] = col[pb + t];
-                sv[t] = val[pb + t];
+                sh[t] = h;
+                sl[t] = (float)(a - (double)h);
             }
             __syncthreads();
             for (int t = 0; t < cntk; ++t) {
-                const double a = sv[t];
-                const double *wr = W64 + (int64_t)sc[t] * n;
+                const float a1 = sh[t], a2 = sl[t];
+                const float *wh = Whi + (int64_t)sc[t] * n, *wl = Wlo + (int64_t)sc[t] * n;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
-                    if (cidx < n) acc[q] = fma(-a, wr[cidx], acc[q]);
+                    if (cidx < n) {
+                        const float x1 = wh[cidx], x2 = wl[cidx];
+                        const float pr = __fmul_rn(a1, x1);
+                        const float pe = fmaf(a1, x1, -pr);                 // a1 x1 = pr + pe
+                        const float px = fmaf(a1, x2, __fmul_rn(a2, x1));  // cross terms
+                        // (ah, al) -= pr + (pe + px): two-sum of ah and -pr
+                        const float sm = __fsub_rn(ah[q], pr);
+                        const float bb = __fsub_rn(sm, ah[q]);
+                        const float er = __fadd_rn(__fsub_rn(ah[q], __fsub_rn(sm, bb)), __fsub_rn(-pr, bb));
+                        al[q] = __fadd_rn(al[q], __fsub_rn(er, __fadd_rn(pe, px)));
+                        ah[q] = sm;
+                    }
                 }
             }
         }
@@ -137,10 +163,10 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
         for (int q = 0; q < 8; ++q) {
             const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
             if (cidx < n) {
-                R32[i * n + cidx] = (float)acc[q];
-                W32[i * n + cidx] = (float)W64[i * n + cidx];
-                mx = fmax(mx, fabs(acc[q]));
-                sq = fma(acc[q], acc[q], sq);
+                const float r = __fadd_rn(ah[q], al[q]);
+                R32[i * n + cidx] = r;
+                mx = fmaxf(mx, fabsf(r));
+                sq = fmaf(r, r, sq);
             }
         }
     }
@@ -149,15 +175,34 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
     __syncthreads();
     for (int w = RES_T / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
-            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + w]);
+            rmax[threadIdx.x] = fmaxf(rmax[threadIdx.x], rmax[threadIdx.x + w]);
             rsq[threadIdx.x] += rsq[threadIdx.x + w];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        rowstat[2 * i] = rmax[0];
-        rowstat[2 * i + 1] = rsq[0];
+        rowstat[2 * i] = (double)rmax[0];
+        rowstat[2 * i + 1] = (double)rsq[0];
     }
+}
+
+// W (FP64) -> hi = fl32(W), lo = fl32(W - hi); and back, W = hi + lo.
+__global__ void k_split64(const double *__restrict__ W, float *__restrict__ hi, float *__restrict__ lo,
+                          int64_t m) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double w = W[t];
+        const float h = (float)w;
+        hi[t] = h;
+        lo[t] = (float)(w - (double)h);
+    }
+}
+
+__global__ void k_join64(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ W,
+                         int64_t m) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+         t += (int64_t)gridDim.x * blockDim.x)
+        W[t] = (double)hi[t] + (double)lo[t];
 }
 
 // Fixed-order reduction of per-row (max, sum) pairs into sc->ns_max, sc->ns_fro2.
@@ -333,10 +378,10 @@ cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, 
     return cudaGetLastError();
 }
 
-cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const double *W64,
-                     int64_t n, float *R32, float *W32, double *rowstat, DevScalars *sc,
+cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const float *Whi,
+                     const float *Wlo, int64_t n, float *R32, double *rowstat, DevScalars *sc,
                      cudaStream_t st) {
-    k_residual<<<(unsigned)n, RES_T, 0, st>>>(ptr, col, val, W64, n, R32, W32, rowstat);
+    k_residual<<<(unsigned)n, RES_T, 0, st>>>(ptr, col, val, Whi, Wlo, n, R32, rowstat);
     k_rowstat_final<<<1, 1024, 0, st>>>(rowstat, n, sc);
     counted(2);
     return cudaGetLastError();
@@ -384,6 +429,18 @@ cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float
         k_sum_final<<<1, 1024, 0, st>>>(part, nt * nt, outs[k]);
         counted(2);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t split64(const double *W, float *hi, float *lo, int64_t m, cudaStream_t st) {
+    k_split64<<<gridn(m), 256, 0, st>>>(W, hi, lo, m);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t join64(const float *hi, const float *lo, double *W, int64_t m, cudaStream_t st) {
+    k_join64<<<gridn(m), 256, 0, st>>>(hi, lo, W, m);
+    counted(1);
     return cudaGetLastError();
 }
 

@@ -55,12 +55,14 @@ __device__ __forceinline__ void tri_tile(int64_t t, int64_t &I, int64_t &J) {
 enum { EPI_NS = 0 };
 
 // Tiles of C = P Q^T, P and Q each n_rows x K (K-major).
-// EPI_NS:    lower tiles, out[i][j] += C_ij, mirrored (out: FP64, row stride ldo)
+// EPI_NS:    lower tiles, W[i][j] += C_ij, mirrored, with W = hi + lo a
+//            symmetric double-float pair (two FP32 arrays, row stride ldo):
+//            two-sum of hi and C, the error into lo, renormalised
 template <int EPI>
 __global__ void __launch_bounds__(TTHREADS, 1)
     k_tc_lower(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
-               int64_t nrows, int64_t K, double *__restrict__ out, int64_t ldo,
-               int *err) {
+               int64_t nrows, int64_t K, float *__restrict__ outh, float *__restrict__ outl,
+               int64_t ldo, int *err) {
     extern __shared__ unsigned char raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -123,26 +125,81 @@ __global__ void __launch_bounds__(TTHREADS, 1)
     // warp-uniform outcome: the TMEM loads of the epilogue need the whole warp
     const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.done, 0));
     tc_fence_after();
+    // the tile goes through the idle stage buffers (128 x 129 floats) so that
+    // both the lower entries and their mirror images are updated by rows
+    float(*T)[TBN + 1] = reinterpret_cast<float(*)[TBN + 1]>(&sm.a[0][0]);
+    static_assert(sizeof(float) * TBM * (TBN + 1) <= sizeof(float) * 2 * TST * TBM * TBK, "staging tile");
     if (ok) {
-        const int64_t i = ti * TBM + warp * 32 + lane;
 #pragma unroll 1
         for (int cb = 0; cb < TBN / 32; ++cb) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
-            if (i < nrows) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int64_t j = tj * TBN + cb * 32 + c;
-                    if (j < nrows && j <= i) {
-                        const double w = out[i * ldo + j] + (double)v[c];
-                        out[i * ldo + j] = w;
-                        if (i != j) out[j * ldo + i] = w;
+            for (int c = 0; c < 32; ++c) T[warp * 32 + lane][cb * 32 + c] = v[c];
+        }
+    } else if (lane == 0) {
+        atomicExch(err, 3);
+    }
+    const int allok = __syncthreads_and(ok);
+    // (h, l) + x for the double-float W = hi + lo: two-sum of h and x, the
+    // error into l, renormalised.  Four rows of a warp's share at a time, all
+    // loads issued before the stores (one round trip per group).
+    float *__restrict__ oh = outh;
+    float *__restrict__ ol = outl;
+    auto dfadd = [](float h, float l, float x, float &h2, float &l3) {
+        const float sm = __fadd_rn(h, x), bb = __fsub_rn(sm, h);
+        const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(sm, bb)), __fsub_rn(x, bb));
+        const float l2 = __fadd_rn(l, er);
+        h2 = __fadd_rn(sm, l2);
+        l3 = __fsub_rn(l2, __fsub_rn(h2, sm));
+    };
+    constexpr int RG = 4, NW = TTHREADS / 32;
+    if (allok) {
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            // pass 0: entries (i, j), j <= i, by rows i (lanes along j);
+            // pass 1: their mirror images (j, i), j < i, by rows j (lanes
+            // along i) -- W is kept symmetric, so (j, i) holds the same pair
+            // as (i, j) and gets the same sum
+#pragma unroll 1
+            for (int r0 = warp * RG; r0 < TBM; r0 += NW * RG) {
+                int64_t at[RG][4];
+                bool act[RG][4];
+                float h[RG][4], l[RG][4], x[RG][4];
+#pragma unroll
+                for (int u = 0; u < RG; ++u)
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb) {
+                        const int a = r0 + u, b = cb * 32 + lane;  // a: the row's tile index
+                        int64_t i, j;
+                        if (pass == 0) {
+                            i = ti * TBM + a;
+                            j = tj * TBN + b;
+                            act[u][cb] = i < nrows && j < nrows && j <= i;
+                            at[u][cb] = i * ldo + j;
+                            x[u][cb] = T[a][b];
+                        } else {
+                            j = tj * TBN + a;
+                            i = ti * TBM + b;
+                            act[u][cb] = i < nrows && j < nrows && j < i;
+                            at[u][cb] = j * ldo + i;
+                            x[u][cb] = T[b][a];
+                        }
+                        h[u][cb] = act[u][cb] ? oh[at[u][cb]] : 0.f;
+                        l[u][cb] = act[u][cb] ? ol[at[u][cb]] : 0.f;
                     }
-                }
+#pragma unroll
+                for (int u = 0; u < RG; ++u)
+#pragma unroll
+                    for (int cb = 0; cb < 4; ++cb)
+                        if (act[u][cb]) {
+                            float h2, l3;
+                            dfadd(h[u][cb], l[u][cb], x[u][cb], h2, l3);
+                            oh[at[u][cb]] = h2;
+                            ol[at[u][cb]] = l3;
+                        }
             }
         }
-    } else if (threadIdx.x == 0) {
-        atomicExch(err, 3);
     }
     // error path: wait (bounded) for the producer's copies still in flight;
     // only the last TST issued stages can be outstanding
@@ -183,13 +240,13 @@ __global__ void k_copy_pad(const float *__restrict__ U, int64_t n, float *__rest
     }
 }
 
-// Wp[i][k] = W[i][k] (FP32 copy of FP64), zero padding.
-__global__ void k_pack_w(const double *__restrict__ W, int64_t n, float *__restrict__ Wp, int64_t ldp) {
+// Wp[i][k] = W[i][k] (FP32), zero padding.
+__global__ void k_pack_w(const float *__restrict__ W, int64_t n, float *__restrict__ Wp, int64_t ldp) {
     const int64_t total = ldp * ldp;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / ldp, k = t % ldp;
-        Wp[t] = (i < n && k < n) ? (float)W[i * n + k] : 0.f;
+        Wp[t] = (i < n && k < n) ? W[i * n + k] : 0.f;
     }
 }
 
@@ -249,7 +306,7 @@ bool g_tc_attr[1] = {false};
 
 template <int EPI>
 cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t K, int64_t ld,
-                         double *out, int64_t ldo, int *err, cudaStream_t st) {
+                         float *outh, float *outl, int64_t ldo, int *err, cudaStream_t st) {
     if (!g_tc_attr[EPI]) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -262,8 +319,8 @@ cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t 
     e = make_map(&mq, Q, nrows, K, ld);
     if (e != cudaSuccess) return e;
     const int64_t nt = (nrows + TBM - 1) / TBM;
-    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, out,
-                                                                            ldo, err);
+    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, outh,
+                                                                            outl, ldo, err);
     counted(1);
     return cudaGetLastError();
 }
@@ -281,16 +338,17 @@ cudaError_t make_tmap(CUtensorMap *map, const float *base, int64_t rows, int64_t
     return make_map(map, base, rows, cols, ld);
 }
 
-// W64 += W R (lower tiles, mirrored) with R32 row-major (ld n); Wp and Qp are
-// scratch of tc_pad(n)^2 floats each.
-cudaError_t ns_gemm_tc(const double *W64, const float *R32, int64_t n, double *W64out, float *Wp,
-                       float *Qp, int *err, cudaStream_t st) {
+// W += W R (lower tiles, mirrored) for the double-float W = Whi + Wlo
+// (symmetric, row stride n); the product takes Whi and R32 (row-major, ld n)
+// as TF32 operands.  Wp and Qp are scratch of tc_pad(n)^2 floats each.
+cudaError_t ns_gemm_tc(float *Whi, float *Wlo, const float *R32, int64_t n, float *Wp, float *Qp,
+                       int *err, cudaStream_t st) {
     const int64_t ldp = tc_pad(n);
-    k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(W64, n, Wp, ldp);
+    k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(Whi, n, Wp, ldp);
     const dim3 tg((unsigned)(ldp / 32), (unsigned)(ldp / 32)), tb(32, 8);
     k_transpose_pad<<<tg, tb, 0, st>>>(R32, n, Qp, ldp);
     counted(2);
-    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, W64out, n, err, st);
+    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, Whi, Wlo, n, err, st);
 }
 
 // Up = U padded (ld = tc_pad(n)), Ut = U^T padded.
