@@ -57,7 +57,7 @@ struct DevScalars {
     int err;              // device-side error flag (NaN input, bad diagonal)
     int bad_sym;          // input symmetry check failed
     int tc_err;           // tensor-core GEMM: a bounded wait expired (code)
-    int pad2;
+    unsigned res_done;    // residual: CTAs finished (the last one reduces, then resets it)
     // grid barrier of the persistent CD sweep: count, generation, error, pad
     unsigned bar_count;
     unsigned bar_gen;

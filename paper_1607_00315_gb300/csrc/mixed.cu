@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
                                                     const float *__restrict__ Whi,
                                                     const float *__restrict__ Wlo, int64_t n,
                                                     float *__restrict__ R32,
-                                                    double *__restrict__ rowstat) {
+                                                    double *__restrict__ rowstat, DevScalars *dsc) {
     __shared__ int32_t sc[RES_CAP];
+    __shared__ int last_s;
     __shared__ float sh[RES_CAP], sl[RES_CAP];
     __shared__ float rmax[RES_T], rsq[RES_T];
     const int64_t i = blockIdx.x;
@@ -183,6 +184,33 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
     if (threadIdx.x == 0) {
         rowstat[2 * i] = (double)rmax[0];
         rowstat[2 * i + 1] = (double)rsq[0];
+        __threadfence();
+        last_s = atomicAdd(&dsc->res_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    // the last CTA: fixed-order reduction of the per-row (max, sum) pairs
+    // into ns_max, ns_fro2 (L2 loads: the pairs were written by other SMs)
+    __shared__ double m2[RES_T], s2[RES_T];
+    double mxd = 0.0, sqd = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += RES_T) {
+        mxd = fmax(mxd, __ldcg(rowstat + 2 * r));
+        sqd += __ldcg(rowstat + 2 * r + 1);
+    }
+    m2[threadIdx.x] = mxd;
+    s2[threadIdx.x] = sqd;
+    __syncthreads();
+    for (int w = RES_T / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            m2[threadIdx.x] = fmax(m2[threadIdx.x], m2[threadIdx.x + w]);
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        dsc->ns_max = m2[0];
+        dsc->ns_fro2 = s2[0];
+        dsc->res_done = 0u;  // ready for the next launch
     }
 }
 
@@ -203,31 +231,6 @@ __global__ void k_join64(const float *__restrict__ hi, const float *__restrict__
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
          t += (int64_t)gridDim.x * blockDim.x)
         W[t] = (double)hi[t] + (double)lo[t];
-}
-
-// Fixed-order reduction of per-row (max, sum) pairs into sc->ns_max, sc->ns_fro2.
-__global__ void k_rowstat_final(const double *__restrict__ rowstat, int64_t n, DevScalars *sc) {
-    __shared__ double m[1024], s[1024];
-    const int t = threadIdx.x;
-    double mx = 0.0, sq = 0.0;
-    for (int64_t i = t; i < n; i += 1024) {
-        mx = fmax(mx, rowstat[2 * i]);
-        sq += rowstat[2 * i + 1];
-    }
-    m[t] = mx;
-    s[t] = sq;
-    __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if (t < w) {
-            m[t] = fmax(m[t], m[t + w]);
-            s[t] += s[t + w];
-        }
-        __syncthreads();
-    }
-    if (t == 0) {
-        sc->ns_max = m[0];
-        sc->ns_fro2 = s[0];
-    }
 }
 
 // ---- t2 = tr((Delta W)^2) = sum_kj U_kj U_jk over 32 x 32 tile pairs -------
@@ -381,9 +384,8 @@ cudaError_t build_csr(const double *A, int64_t n, long long *ptr, int32_t *col, 
 cudaError_t residual(const long long *ptr, const int32_t *col, const double *val, const float *Whi,
                      const float *Wlo, int64_t n, float *R32, double *rowstat, DevScalars *sc,
                      cudaStream_t st) {
-    k_residual<<<(unsigned)n, RES_T, 0, st>>>(ptr, col, val, Whi, Wlo, n, R32, rowstat);
-    k_rowstat_final<<<1, 1024, 0, st>>>(rowstat, n, sc);
-    counted(2);
+    k_residual<<<(unsigned)n, RES_T, 0, st>>>(ptr, col, val, Whi, Wlo, n, R32, rowstat, sc);
+    counted(1);
     return cudaGetLastError();
 }
 

@@ -304,9 +304,12 @@ cudaError_t make_map(CUtensorMap *map, const float *base, int64_t rows, int64_t 
 
 bool g_tc_attr[1] = {false};
 
+// P: nrows x kp (row stride ldp_), Q: nrows x K (row stride ld); the k-loop
+// runs to K, and TMA fills P's columns beyond kp with zeros.
 template <int EPI>
-cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t K, int64_t ld,
-                         float *outh, float *outl, int64_t ldo, int *err, cudaStream_t st) {
+cudaError_t launch_lower(const float *P, int64_t kp, int64_t ldp_, const float *Q, int64_t nrows,
+                         int64_t K, int64_t ld, float *outh, float *outl, int64_t ldo, int *err,
+                         cudaStream_t st) {
     if (!g_tc_attr[EPI]) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -314,7 +317,7 @@ cudaError_t launch_lower(const float *P, const float *Q, int64_t nrows, int64_t 
         g_tc_attr[EPI] = true;
     }
     CUtensorMap mp, mq;
-    cudaError_t e = make_map(&mp, P, nrows, K, ld);
+    cudaError_t e = make_map(&mp, P, nrows, kp, ldp_);
     if (e != cudaSuccess) return e;
     e = make_map(&mq, Q, nrows, K, ld);
     if (e != cudaSuccess) return e;
@@ -344,11 +347,13 @@ cudaError_t make_tmap(CUtensorMap *map, const float *base, int64_t rows, int64_t
 cudaError_t ns_gemm_tc(float *Whi, float *Wlo, const float *R32, int64_t n, float *Wp, float *Qp,
                        int *err, cudaStream_t st) {
     const int64_t ldp = tc_pad(n);
-    k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(Whi, n, Wp, ldp);
     const dim3 tg((unsigned)(ldp / 32), (unsigned)(ldp / 32)), tb(32, 8);
     k_transpose_pad<<<tg, tb, 0, st>>>(R32, n, Qp, ldp);
+    // the operand is a snapshot of W: the epilogue updates W while other
+    // tiles are still reading their rows
+    k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(Whi, n, Wp, ldp);
     counted(2);
-    return launch_lower<EPI_NS>(Wp, Qp, n, ldp, ldp, Whi, Wlo, n, err, st);
+    return launch_lower<EPI_NS>(Wp, ldp, ldp, Qp, n, ldp, ldp, Whi, Wlo, n, err, st);
 }
 
 // Up = U padded (ld = tc_pad(n)), Ut = U^T padded.
