@@ -219,21 +219,47 @@ __global__ void __launch_bounds__(XTHREADS, 1)
         asm volatile("bar.sync 1, 256;" ::: "memory");
         if (ok) {
             const int et = threadIdx.x - 192, wr = et >> 5;  // 8 warps x 32 lanes
+            if (a.epi == XE_SUB) {
+                // read-modify-write: the loads of four rows are issued before
+                // their stores (one round trip per group, not per element)
+                float *__restrict__ o = a.out;
 #pragma unroll 1
-            for (int r = wr; r < XM; r += 8) {
-                const int64_t i = ti * XM + r;
-                if (i >= a.M) break;
+                for (int r0 = wr * 4; r0 < XM; r0 += 32) {
+                    float cur[4][XN / 32];
+                    bool act[4][XN / 32];
 #pragma unroll
-                for (int p = 0; p < XN / 32; ++p) {
-                    const int cc = lane + 32 * p;
-                    const int64_t j = tj * XN + cc;
-                    if (j >= a.N) continue;
-                    const float v = Ct[r][cc];
-                    if (a.epi == XE_ASSIGN) a.out[i * a.ldo + j] = a.alpha * v;
-                    else if (j <= i) {
-                        if (a.epi == XE_SUB) a.out[i * a.ldo + j] -= v;
-                        else if (a.epi == XE_SYM) a.out[i * a.ldo + j] = v;
-                        else a.out64[i * a.ldo + j] = a.scale * (double)v;
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int p = 0; p < XN / 32; ++p) {
+                            const int64_t i = ti * XM + r0 + u, j = tj * XN + lane + 32 * p;
+                            act[u][p] = i < a.M && j < a.N && j <= i;
+                            cur[u][p] = act[u][p] ? o[i * a.ldo + j] : 0.f;
+                        }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int p = 0; p < XN / 32; ++p)
+                            if (act[u][p]) {
+                                const int64_t i = ti * XM + r0 + u, j = tj * XN + lane + 32 * p;
+                                o[i * a.ldo + j] = cur[u][p] - Ct[r0 + u][lane + 32 * p];
+                            }
+                }
+            } else {
+#pragma unroll 1
+                for (int r = wr; r < XM; r += 8) {
+                    const int64_t i = ti * XM + r;
+                    if (i >= a.M) break;
+#pragma unroll
+                    for (int p = 0; p < XN / 32; ++p) {
+                        const int cc = lane + 32 * p;
+                        const int64_t j = tj * XN + cc;
+                        if (j >= a.N) continue;
+                        const float v = Ct[r][cc];
+                        if (a.epi == XE_ASSIGN) a.out[i * a.ldo + j] = a.alpha * v;
+                        else if (j <= i) {
+                            if (a.epi == XE_SYM) a.out[i * a.ldo + j] = v;
+                            else a.out64[i * a.ldo + j] = a.scale * (double)v;
+                        }
                     }
                 }
             }
