@@ -110,7 +110,6 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
 __global__ void __launch_bounds__(XTHREADS, 1)
     k_tcx(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
           const XArgs a) {
-    if (a.info && *a.info != 0) return;
     extern __shared__ unsigned char raw[];
     XSmem &sm = *reinterpret_cast<XSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -153,6 +152,17 @@ __global__ void __launch_bounds__(XTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem;  // column 0: the accumulator (drain: the hi lo + lo hi terms)
+    // inputs come from the preceding kernel from here on
+    pdl_wait();
+    pdl_trigger();
+    if (a.info && *a.info != 0) {  // an earlier pivot failed: nothing to do (same in every thread)
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                         : "memory");
+        return;
+    }
     const int lw = warp & 3;
     const uint32_t lane_off = (uint32_t)(lw * 32) << 16;
 
@@ -431,8 +441,21 @@ cudaError_t tcx(const float *P, const float *Q, int64_t M, int64_t N, int64_t K,
         a.out = nullptr;
     }
     const int64_t grid = lower ? tm * (tm + 1) / 2 : tm * tn;
-    k_tcx<<<(unsigned)grid, XTHREADS, XSMEM, st>>>(mp, mq, a);
+    // programmatic serialisation: the prologue (barriers, TMEM) overlaps the
+    // predecessor's tail; the kernel waits for it before reading inputs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(XTHREADS);
+    cfg.dynamicSmemBytes = XSMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_tcx, mp, mq, a);
     counted(1);
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 

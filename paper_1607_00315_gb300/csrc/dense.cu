@@ -414,6 +414,8 @@ __global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, 
                                                     int s, float *__restrict__ Xo,
                                                     float *__restrict__ Xto, double *__restrict__ ldiag,
                                                     DevScalars *sc) {
+    pdl_wait();  // the block comes from the preceding kernel
+    pdl_trigger();
     if (sc->info != 0) return;
     extern __shared__ float lsm[];
     float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
@@ -926,8 +928,19 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
         attr = true;
     }
     if (s < 1 || s > LB) return cudaErrorInvalidValue;
-    k_leaf32<<<1, TPB, LEAF_SMEM, st>>>(A, ld, o, s, X, Xt, ldiag, sc);
+    cudaLaunchConfig_t cfg = {};  // programmatic serialisation, as for the GEMMs
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(TPB);
+    cfg.dynamicSmemBytes = LEAF_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    la[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_leaf32, A, ld, o, s, X, Xt, ldiag, sc);
     counted(1);
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 

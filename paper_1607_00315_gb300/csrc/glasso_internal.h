@@ -13,6 +13,17 @@
 
 namespace glx {
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation runs its prologue while its predecessor finishes; it must
+// pass pdl_wait() (the predecessor complete, its writes visible) before it
+// reads anything the predecessor wrote.  pdl_trigger() lets the successor
+// start its own prologue.  Both are no-ops for a normal launch.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
+
 __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
 
