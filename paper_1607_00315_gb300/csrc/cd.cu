@@ -809,11 +809,14 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
         }
     }
     // stale dots of the block at coordinate b1 (count nb1) against U copy R,
-    // (chunk, coordinate) tasks over the given warps (neighbouring warps take
-    // neighbouring coordinates of one chunk, which mostly share the U column
-    // i_t: pairs are in row order), FP32 warp sums
-    auto dots = [&](const float *R, int64_t b1, int nb1, double *out, int64_t wfirst, int64_t wcount) {
-        for (int64_t task = wfirst; task < (int64_t)nb1 * nch; task += wcount) {
+    // (chunk, coordinate) tasks: CTA `part` of `nparts` takes a contiguous
+    // share (so every CTA gets some, and neighbouring warps take neighbouring
+    // coordinates of one chunk, which mostly share the U column i_t: pairs
+    // are in row order), one task per warp in turn, FP32 warp sums
+    auto dots = [&](const float *R, int64_t b1, int nb1, double *out, int part, int nparts) {
+        const int64_t ntask = (int64_t)nb1 * nch;
+        const int64_t lo = ntask * part / nparts, hi = ntask * (part + 1) / nparts;
+        for (int64_t task = lo + warp; task < hi; task += LT / 32) {
             const int c = (int)(task / nb1), t = (int)(task - (int64_t)c * nb1);
             const int64_t it_ = pi[b1 + t], jt = pj[b1 + t];
             const float *wr = W + jt * n;
@@ -828,8 +831,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
         }
     };
     // prologue: dots of block 0 against copy 0 (both copies hold the initial U)
-    dots(Ubuf0, 0, (int)lmin(CD_B, np), bvec, (int64_t)blockIdx.x * (LT / 32) + warp,
-         (int64_t)G * (LT / 32));
+    dots(Ubuf0, 0, (int)lmin(CD_B, np), bvec, (int)blockIdx.x, (int)G);
     if (!grid_sync(gb, G, epoch)) return;
     if (cc && tid == 32) {  // the matrices are complete after the barrier
         kcopy_issue(KIb, KallI, KB, &kbarI[0]);
@@ -999,8 +1001,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             if (it + 1 < total) {
                 const int64_t nb0 = ((it + 1) % nbatch) * CD_B;
                 dots((it & 1) ? Ubuf1 : Ubuf0, nb0, (int)lmin(CD_B, np - nb0),
-                     bvec + ((it + 1) & 1) * (int64_t)CD_MAX_CHUNKS * CD_B,
-                     (int64_t)wb * (LT / 32) + warp, (int64_t)GW * (LT / 32));
+                     bvec + ((it + 1) & 1) * (int64_t)CD_MAX_CHUNKS * CD_B, wb, GW);
             }
             if (L >= 0) {
 #pragma unroll
