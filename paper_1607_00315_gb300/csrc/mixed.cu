@@ -103,6 +103,7 @@ __global__ void k_nz_write(const double *__restrict__ A, int64_t n, const long l
 // restart at |R|_F >= 0.9).  The CSR values of A are split into FP32 pairs
 // as they are staged.
 constexpr int RES_T = 256;
+constexpr int64_t SERIES_CTAS = 152 * 4;  // persistent CTAs of the series reductions
 constexpr int RES_CAP = 256;  // nonzeros of a row staged per pass
 
 __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict__ ptr,
@@ -234,30 +235,55 @@ __global__ void k_join64(const float *__restrict__ hi, const float *__restrict__
 }
 
 // ---- t2 = tr((Delta W)^2) = sum_kj U_kj U_jk over 32 x 32 tile pairs -------
+// Persistent CTAs walk the upper tile pairs (I <= J; the off-diagonal pairs
+// count twice).  Each product is split exactly (p + e, e = fma(a, b, -p)) and
+// summed in double-float FP32 (two-sum), so no FP64 arithmetic runs per
+// element; each CTA's sum goes to part[] in FP64.
+__device__ __forceinline__ void df_acc(float &h, float &l, float a, float b, float w) {
+    const float p = __fmul_rn(a, b) * w, pe = fmaf(a, b, -__fmul_rn(a, b)) * w;  // w = 1 or 2 (exact)
+    const float sm = __fadd_rn(h, p), bb = __fsub_rn(sm, h);
+    const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(sm, bb)), __fsub_rn(p, bb));
+    l = __fadd_rn(l, __fadd_rn(er, pe));
+    h = sm;
+}
+
+// block sum of (h + l) in FP64 (one value per thread), written by thread 0
+__device__ __forceinline__ void df_block_sum(float h, float l, double *out) {
+    __shared__ double wsum[8];
+    double v = (double)h + (double)l;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        *out = t;
+    }
+}
+
 __global__ void k_t2_tiles(const float *__restrict__ U, int64_t n, double *__restrict__ part) {
     __shared__ float Ut[32][33];
-    __shared__ double red[256];
-    int64_t I, J;
-    tri_index64(blockIdx.x, I, J);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 x 32
-    // stage U[J-block rows, I-block cols] transposed
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t gr = J * 32 + r, gc = I * 32 + tx;
-        Ut[tx][r] = (gr < n && gc < n) ? U[gr * n + gc] : 0.f;
-    }
-    __syncthreads();
-    double s = 0.0;
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t gr = I * 32 + r, gc = J * 32 + tx;
-        if (gr < n && gc < n) s += (double)U[gr * n + gc] * (double)Ut[r][tx];
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    const int64_t nt = (n + 31) / 32, ntiles = nt * (nt + 1) / 2;
+    float h = 0.f, l = 0.f;
+    for (int64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
+        int64_t I, J;
+        tri_index64(q, I, J);
+        // stage U[J-block rows, I-block cols] transposed
         __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t gr = J * 32 + r, gc = I * 32 + tx;
+            Ut[tx][r] = (gr < n && gc < n) ? U[gr * n + gc] : 0.f;
+        }
+        __syncthreads();
+        const float w = I == J ? 1.f : 2.f;
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t gr = I * 32 + r, gc = J * 32 + tx;
+            if (gr < n && gc < n) df_acc(h, l, U[gr * n + gc], Ut[r][tx], w);
+        }
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = (I == J ? 1.0 : 2.0) * red[0];
+    df_block_sum(h, l, part + blockIdx.x);
 }
 
 __global__ void k_sum_final(const double *__restrict__ part, int64_t m, double *out) {
@@ -274,30 +300,28 @@ __global__ void k_sum_final(const double *__restrict__ part, int64_t m, double *
     if (t == 0) *out = s[0];
 }
 
-// sum_{i,j < n} P_ij Q_ji over all 32 x 32 tile pairs (FP64 partial per tile)
+// sum_{i,j < n} P_ij Q_ji over all 32 x 32 tile pairs, persistent CTAs,
+// products and sums as in k_t2_tiles; one FP64 partial per CTA
 __global__ void k_tdot_tiles(const float *__restrict__ P, int64_t ldp_, const float *__restrict__ Q,
                              int64_t ldq, int64_t n, double *__restrict__ part) {
     __shared__ float Qt[32][33];
-    __shared__ double red[256];
-    const int64_t I = blockIdx.y, J = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int r = ty; r < 32; r += 8) {  // Qt[c][r] = Q[J*32 + r][I*32 + c]
-        const int64_t gr = J * 32 + r, gc = I * 32 + tx;
-        Qt[tx][r] = (gr < n && gc < n) ? Q[gr * ldq + gc] : 0.f;
-    }
-    __syncthreads();
-    double s = 0.0;
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t gr = I * 32 + r, gc = J * 32 + tx;
-        if (gr < n && gc < n) s += (double)P[gr * ldp_ + gc] * (double)Qt[r][tx];
-    }
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    const int64_t nt = (n + 31) / 32;
+    float h = 0.f, l = 0.f;
+    for (int64_t q = blockIdx.x; q < nt * nt; q += gridDim.x) {
+        const int64_t I = q / nt, J = q - (q / nt) * nt;
         __syncthreads();
+        for (int r = ty; r < 32; r += 8) {  // Qt[c][r] = Q[J*32 + r][I*32 + c]
+            const int64_t gr = J * 32 + r, gc = I * 32 + tx;
+            Qt[tx][r] = (gr < n && gc < n) ? Q[gr * ldq + gc] : 0.f;
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t gr = I * 32 + r, gc = J * 32 + tx;
+            if (gr < n && gc < n) df_acc(h, l, P[gr * ldp_ + gc], Qt[r][tx], 1.f);
+        }
     }
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    df_block_sum(h, l, part + blockIdx.x);
 }
 
 // t1 = tr(W Delta) = sum over pairs of mult W_ij Delta_ij (FP64); per-block partials
@@ -393,7 +417,7 @@ cudaError_t series_terms(const double *W64, int64_t n, const int32_t *pi, const 
                          const double *D, int64_t np, const float *U32, double *part, int64_t cap,
                          DevScalars *sc, cudaStream_t st) {
     const int64_t nt = (n + 31) / 32;
-    const int64_t ntiles = nt * (nt + 1) / 2;
+    const int64_t ntiles = lmin(nt * (nt + 1) / 2, SERIES_CTAS);  // persistent CTAs
     const int nb1 = (int)lmin(1024, lmax(1, (np + 255) / 256));
     if (ntiles + nb1 > cap) return cudaErrorInvalidValue;
     k_t2_tiles<<<(unsigned)ntiles, 256, 0, st>>>(U32, n, part);
@@ -412,7 +436,8 @@ cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float
                         double *part, int64_t cap, DevScalars *sc, cudaStream_t st) {
     const int64_t p = tc_pad(n);
     const int64_t nt = (n + 31) / 32;
-    if (nt * nt > cap) return cudaErrorInvalidValue;
+    const int64_t nct = lmin(nt * nt, SERIES_CTAS);  // persistent CTAs
+    if (nct > cap) return cudaErrorInvalidValue;
     cudaError_t e = pad_and_transpose(U32, n, Up, Ut, st);
     if (e != cudaSuccess) return e;
     // split-TF32 products with unbiased summation: the terms carry about
@@ -422,13 +447,12 @@ cudaError_t series_high(const float *U32, int64_t n, float *Up, float *Ut, float
     if (e != cudaSuccess) return e;
     e = gemm_nt_split(U2, Ut, n, p, U3, &sc->tc_err, st);  // U^3
     if (e != cudaSuccess) return e;
-    const dim3 g((unsigned)nt, (unsigned)nt);
     const float *Ps[4] = {U2, U2, U2, U3};
     const float *Qs[4] = {Up, U2, U3, U3};
     double *outs[4] = {&sc->t3, &sc->t4, &sc->t5, &sc->t6};
     for (int k = 0; k < 4; ++k) {
-        k_tdot_tiles<<<g, 256, 0, st>>>(Ps[k], p, Qs[k], p, n, part);
-        k_sum_final<<<1, 1024, 0, st>>>(part, nt * nt, outs[k]);
+        k_tdot_tiles<<<(unsigned)nct, 256, 0, st>>>(Ps[k], p, Qs[k], p, n, part);
+        k_sum_final<<<1, 1024, 0, st>>>(part, nct, outs[k]);
         counted(2);
     }
     return cudaGetLastError();
