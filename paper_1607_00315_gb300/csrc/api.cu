@@ -554,8 +554,11 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         CK(build_csr(w.A, n, w.csr_ptr, w.csr_col, w.csr_val, st));
         bool restarted = false;
         ns_steps = 0;
+        // hi alternates between W32 and a second buffer (the GEMM reads the
+        // current one while its epilogue writes the next)
+        float *hcur = W32, *hnext = reinterpret_cast<float *>(w.T) + nn;
         for (int it = 0; it < max_ns; ++it, ++ns_steps) {
-            CK(residual(w.csr_ptr, w.csr_col, w.csr_val, W32, Wlo, n, R32, w.rowred, sc, st));
+            CK(residual(w.csr_ptr, w.csr_col, w.csr_val, hcur, Wlo, n, R32, w.rowred, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->tc_err) {
                 err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
@@ -567,13 +570,18 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                 restarted = true;
                 glasso_status s2 = fresh_factor();
                 if (s2 != GLASSO_OK) return s2;
+                hcur = W32;  // the fresh factor's W
+                hnext = reinterpret_cast<float *>(w.T) + nn;
                 it = -1;
                 continue;
             }
             sv.mark_begin(5, eb);
-            CK(ns_gemm_tc(W32, Wlo, R32, n, w.Wp, w.Qp, &sc->tc_err, st));
+            CK(ns_gemm_tc(hcur, hnext, Wlo, R32, n, w.Wp, w.Qp, &sc->tc_err, st));
             sv.mark_end(5, eb, nd * nd * nd);
+            std::swap(hcur, hnext);
         }
+        if (hcur != W32)
+            CK(cudaMemcpyAsync(W32, hcur, nn * sizeof(float), cudaMemcpyDeviceToDevice, st));
         CK(join64(W32, Wlo, W64, (int64_t)nn, st));  // the FP64 W of the gradient and the pairs
         return GLASSO_OK;
     };

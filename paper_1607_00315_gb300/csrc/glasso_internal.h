@@ -231,8 +231,8 @@ cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld,
                           cudaStream_t st);
 cudaError_t syrk_split(const float *Xt, int64_t n, int64_t m, int64_t ldx, double scale, double *S,
                        int *err, cudaStream_t st);
-cudaError_t ns_gemm_tc(float *Whi, float *Wlo, const float *R32, int64_t n, float *Wp, float *Qp,
-                       int *err, cudaStream_t st);
+cudaError_t ns_gemm_tc(const float *Whi, float *Whi_next, float *Wlo, const float *R32, int64_t n,
+                       float *Wp, float *Qp, int *err, cudaStream_t st);
 cudaError_t syrk_tc(const void *X, int dtype, int64_t m, int64_t n, const double *mu, double *S,
                     float *Xt, int *err, cudaStream_t st);
 cudaError_t pad_and_transpose(const float *U, int64_t n, float *Up, float *Ut, cudaStream_t st);

@@ -140,17 +140,29 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
                 sl[t] = (float)(a - (double)h);
             }
             __syncthreads();
-            for (int t = 0; t < cntk; ++t) {
-                const float a1 = sh[t], a2 = sl[t];
-                const float *wh = Whi + (int64_t)sc[t] * n, *wl = Wlo + (int64_t)sc[t] * n;
+            // two nonzeros per step, all their W loads issued before the sums
+            for (int t0 = 0; t0 < cntk; t0 += 2) {
+                float x1[2][8], x2[2][8], a1[2], a2[2];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
-                    if (cidx < n) {
-                        const float x1 = wh[cidx], x2 = wl[cidx];
-                        const float pr = __fmul_rn(a1, x1);
-                        const float pe = fmaf(a1, x1, -pr);                 // a1 x1 = pr + pe
-                        const float px = fmaf(a1, x2, __fmul_rn(a2, x1));  // cross terms
+                for (int u = 0; u < 2; ++u) {
+                    const int t = t0 + u < cntk ? t0 + u : t0;  // (a repeated term gets a = 0)
+                    a1[u] = t0 + u < cntk ? sh[t] : 0.f;
+                    a2[u] = t0 + u < cntk ? sl[t] : 0.f;
+                    const float *wh = Whi + (int64_t)sc[t] * n, *wl = Wlo + (int64_t)sc[t] * n;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int64_t cidx = c0 + threadIdx.x + (int64_t)q * RES_T;
+                        x1[u][q] = cidx < n ? wh[cidx] : 0.f;
+                        x2[u][q] = cidx < n ? wl[cidx] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float pr = __fmul_rn(a1[u], x1[u][q]);
+                        const float pe = fmaf(a1[u], x1[u][q], -pr);                     // a1 x1 = pr + pe
+                        const float px = fmaf(a1[u], x2[u][q], __fmul_rn(a2[u], x1[u][q]));  // cross terms
                         // (ah, al) -= pr + (pe + px): two-sum of ah and -pr
                         const float sm = __fsub_rn(ah[q], pr);
                         const float bb = __fsub_rn(sm, ah[q]);
@@ -158,7 +170,6 @@ __global__ void __launch_bounds__(RES_T) k_residual(const long long *__restrict_
                         al[q] = __fadd_rn(al[q], __fsub_rn(er, __fadd_rn(pe, px)));
                         ah[q] = sm;
                     }
-                }
             }
         }
 #pragma unroll

@@ -56,13 +56,15 @@ enum { EPI_NS = 0 };
 
 // Tiles of C = P Q^T, P and Q each n_rows x K (K-major).
 // EPI_NS:    lower tiles, W[i][j] += C_ij, mirrored, with W = hi + lo a
-//            symmetric double-float pair (two FP32 arrays, row stride ldo):
+//            symmetric double-float pair (FP32 arrays, row stride ldo): hi is
+//            read from inh and written to outh (another buffer: P may be inh
+//            itself, read by other tiles meanwhile), lo is updated in place;
 //            two-sum of hi and C, the error into lo, renormalised
 template <int EPI>
 __global__ void __launch_bounds__(TTHREADS, 1)
     k_tc_lower(const __grid_constant__ CUtensorMap tp, const __grid_constant__ CUtensorMap tq,
-               int64_t nrows, int64_t K, float *__restrict__ outh, float *__restrict__ outl,
-               int64_t ldo, int *err) {
+               int64_t nrows, int64_t K, const float *__restrict__ inh, float *__restrict__ outh,
+               float *__restrict__ outl, int64_t ldo, int *err) {
     extern __shared__ unsigned char raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(TTHREADS, 1)
                             at[u][cb] = j * ldo + i;
                             x[u][cb] = T[b][a];
                         }
-                        h[u][cb] = act[u][cb] ? oh[at[u][cb]] : 0.f;
+                        h[u][cb] = act[u][cb] ? inh[at[u][cb]] : 0.f;
                         l[u][cb] = act[u][cb] ? ol[at[u][cb]] : 0.f;
                     }
 #pragma unroll
@@ -308,8 +310,8 @@ bool g_tc_attr[1] = {false};
 // runs to K, and TMA fills P's columns beyond kp with zeros.
 template <int EPI>
 cudaError_t launch_lower(const float *P, int64_t kp, int64_t ldp_, const float *Q, int64_t nrows,
-                         int64_t K, int64_t ld, float *outh, float *outl, int64_t ldo, int *err,
-                         cudaStream_t st) {
+                         int64_t K, int64_t ld, const float *inh, float *outh, float *outl, int64_t ldo,
+                         int *err, cudaStream_t st) {
     if (!g_tc_attr[EPI]) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
@@ -322,8 +324,8 @@ cudaError_t launch_lower(const float *P, int64_t kp, int64_t ldp_, const float *
     e = make_map(&mq, Q, nrows, K, ld);
     if (e != cudaSuccess) return e;
     const int64_t nt = (nrows + TBM - 1) / TBM;
-    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, outh,
-                                                                            outl, ldo, err);
+    k_tc_lower<EPI><<<(unsigned)(nt * (nt + 1) / 2), TTHREADS, TC_SMEM, st>>>(mp, mq, nrows, K, inh,
+                                                                            outh, outl, ldo, err);
     counted(1);
     return cudaGetLastError();
 }
@@ -341,19 +343,23 @@ cudaError_t make_tmap(CUtensorMap *map, const float *base, int64_t rows, int64_t
     return make_map(map, base, rows, cols, ld);
 }
 
-// W += W R (lower tiles, mirrored) for the double-float W = Whi + Wlo
-// (symmetric, row stride n); the product takes Whi and R32 (row-major, ld n)
-// as TF32 operands.  Wp and Qp are scratch of tc_pad(n)^2 floats each.
-cudaError_t ns_gemm_tc(float *Whi, float *Wlo, const float *R32, int64_t n, float *Wp, float *Qp,
-                       int *err, cudaStream_t st) {
+// W += W R (lower tiles, mirrored) for the double-float W = hi + lo
+// (symmetric, row stride n): hi is read from Whi and the new hi written to
+// Whi_next (a different buffer), lo is updated in place.  The product takes
+// hi and R32 (row-major, ld n) as TF32 operands; hi is read in place when its
+// rows are 16-byte multiples (n % 4 == 0), else through the padded copy Wp.
+// Qp (and Wp) are scratch of tc_pad(n)^2 floats.
+cudaError_t ns_gemm_tc(const float *Whi, float *Whi_next, float *Wlo, const float *R32, int64_t n,
+                       float *Wp, float *Qp, int *err, cudaStream_t st) {
     const int64_t ldp = tc_pad(n);
     const dim3 tg((unsigned)(ldp / 32), (unsigned)(ldp / 32)), tb(32, 8);
     k_transpose_pad<<<tg, tb, 0, st>>>(R32, n, Qp, ldp);
-    // the operand is a snapshot of W: the epilogue updates W while other
-    // tiles are still reading their rows
+    counted(1);
+    if (n % 4 == 0)
+        return launch_lower<EPI_NS>(Whi, n, n, Qp, n, ldp, ldp, Whi, Whi_next, Wlo, n, err, st);
     k_pack_w<<<gridn(ldp * ldp), 256, 0, st>>>(Whi, n, Wp, ldp);
-    counted(2);
-    return launch_lower<EPI_NS>(Wp, ldp, ldp, Qp, n, ldp, ldp, Whi, Wlo, n, err, st);
+    counted(1);
+    return launch_lower<EPI_NS>(Wp, ldp, ldp, Qp, n, ldp, ldp, Whi, Whi_next, Wlo, n, err, st);
 }
 
 // Up = U padded (ld = tc_pad(n)), Ut = U^T padded.
