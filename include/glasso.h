@@ -227,7 +227,10 @@ glasso_status glasso_hierarchy(glasso_ctx *ctx, const double *absg, const uint8_
  * a = W_ij^2 + W_ii W_jj (W_ii^2 on the diagonal), b = (S - W)_ij + (W Delta W)_ij,
  * c = A_ij + Delta_ij.  D (np, device) holds Delta on the pairs and U (n x n,
  * device) = Delta W; both are read and updated.  The result equals the
- * sequential sweep up to floating-point reassociation. */
+ * sequential sweep up to floating-point reassociation.  In a GLASSO_MIXED
+ * context the sweep is the mixed solve's: W and U rounded to FP32, the
+ * resolution chain in FP32, the increments of Delta in FP64 (exact zeros of
+ * the shrinkage kept); U is returned converted to FP64. */
 glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W,
                                const double *A, int64_t n, double lambda, const int32_t *pi,
                                const int32_t *pj, int64_t np, int nsweeps, double *D, double *U);

@@ -1478,7 +1478,20 @@ glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W
     CTX_CK(pair_prep(S, W, A, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, ctx->stream));
     cudaEvent_t eb;
     sv.mark_begin(3, eb);
-    CTX_CK(cd_sweeps(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, D, U, w, ctx->stream));
+    if (ctx->precision == GLASSO_MIXED) {
+        // the mixed solve's sweep: W and U in FP32 (FP32 resolution chain,
+        // FP64 increments), U converted back; scratch in the FP64 buffers
+        const int64_t nn = n * n;
+        float *W32 = reinterpret_cast<float *>(w.L), *U32 = reinterpret_cast<float *>(w.W);
+        float *U2 = reinterpret_cast<float *>(w.T);
+        CTX_CK(to_f32(W, W32, nn, ctx->stream));
+        CTX_CK(to_f32(U, U32, nn, ctx->stream));
+        CTX_CK(cd_sweeps32(W32, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, D, U32, w, false,
+                           ctx->stream, U2));
+        CTX_CK(to_f64(U32, U, nn, ctx->stream));
+    } else {
+        CTX_CK(cd_sweeps(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, D, U, w, ctx->stream));
+    }
     sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * (double)n * 8.0);
     s = sync_ctx(ctx);
     if (prof) prof_collect(prof);

@@ -177,6 +177,68 @@ def test_cd_sweeps(ctx, n, lam, sweeps):
     assert np.array_equal(D == 0, D_ref == 0) or np.abs(D - D_ref).max() <= 1e-12
 
 
+@pytest.fixture(scope="module")
+def mctx():
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso
+
+    build.build()
+    torch.cuda.init()
+    c = glasso.Context(0, precision=glasso.MIXED)
+    yield c
+    c.close()
+
+
+# pair lists of one block (<= 128 coordinates), two blocks, and several with
+# a ragged last block; one to three sweeps (the pipelined FP32 sweep keeps
+# two copies of U and the matrices of the next two blocks, so these are the
+# cases whose bookkeeping differs)
+# (95 pairs: one block; 155 and 250: two blocks; 406, 811, 1123: four to nine)
+@pytest.mark.parametrize("n,lam,sweeps", [(30, 0.15, 1), (30, 0.15, 3), (45, 0.15, 2), (40, 0.1, 1),
+                                          (70, 0.1, 2), (129, 0.08, 1), (260, 0.1, 3)])
+def test_cd_sweeps_mixed(mctx, n, lam, sweeps):
+    """The mixed solve's FP32 sweep against the FP64 sequential sweep of the
+    oracle.  W and U are rounded to FP32 and the chain and the length-n dots
+    run in FP32: each b_t = G_t + (W Delta W)_t carries an error of at most
+    about n 2^-24 max|b| (FP32 dot of n terms), and the coordinate's
+    increment that error divided by a_t; the Gauss-Seidel sweep (a
+    contraction) does not amplify it beyond a small factor per sweep, so
+    |Delta - Delta_ref| <= 8 sweeps n 2^-24 max|b| / min a.  U is checked
+    against Delta W formed in FP64 from the GPU's own Delta, which pins the
+    row-update bookkeeping independently of the chain's rounding: each entry
+    is a sum of at most d_max sweeps updates rounded to FP32, d_max the
+    largest number of pairs touching a row.  A wrong cross term or a skipped
+    block gives errors of the order of Delta itself."""
+    S, A, W = _state(n, 2 * n + 1, lam)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    D_ref, U_ref = oracle.cd_sweeps(S, W, A, lam, fi, fj, sweeps)
+    import torch
+
+    D = torch.zeros(len(fi), dtype=torch.float64, device="cuda")
+    U = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    mctx.cd_sweeps(_dev(S), _dev(W), _dev(A), lam, _dev(fi), _dev(fj), sweeps, D, U)
+    D = D.cpu().numpy()
+    U = U.cpu().numpy()
+    eps = 2.0 ** -24
+    a = np.where(fi == fj, W[fi, fi] ** 2, W[fi, fj] ** 2 + W[fi, fi] * W[fj, fj])
+    bmax = np.abs((S - W)[fi, fj]).max() + np.abs((W @ U_ref)[fi, fj]).max()
+    tol_d = 8 * sweeps * n * eps * bmax / a.min()
+    err_d = np.abs(D - D_ref).max()
+    assert err_d <= tol_d, (len(fi), err_d, tol_d)
+    # U against Delta W in FP64 from the returned Delta
+    Dm = np.zeros((n, n))
+    Dm[fi, fj] = D
+    Dm[fj, fi] = D
+    E = np.abs(Dm) @ np.abs(W)
+    dmax = np.bincount(np.concatenate([fi, fj[fi != fj]]), minlength=n).max()
+    assert np.all(np.abs(U - Dm @ W) <= (4 + 2 * dmax * sweeps) * eps * E + 1e-300)
+    # exact zeros: the patterns agree except where the oracle's increment is
+    # itself within the FP32 error of zero
+    differ = (D == 0) != (D_ref == 0)
+    assert np.all(np.abs(D_ref[differ]) <= tol_d)
+
+
 def test_line_search(ctx):
     n, lam = 120, 0.1
     S, A, W = _state(n, 11, lam)
