@@ -194,8 +194,12 @@ def mctx():
 # a ragged last block; one to three sweeps (the pipelined FP32 sweep keeps
 # two copies of U and the matrices of the next two blocks, so these are the
 # cases whose bookkeeping differs)
-# (95 pairs: one block; 155 and 250: two blocks; 406, 811, 1123: four to nine)
-@pytest.mark.parametrize("n,lam,sweeps", [(30, 0.15, 1), (30, 0.15, 3), (45, 0.15, 2), (40, 0.1, 1),
+# The pipelined kernel runs when its interaction matrices (three 64 KB per
+# block) fit in n^2 doubles, else the one-copy sweep does.  Pipelined: 241
+# pairs (two blocks), 640, 1431 (five, twelve); one-copy: 95 (one block),
+# 155 and 250 (two), 406, 811, 1123.
+@pytest.mark.parametrize("n,lam,sweeps", [(240, 0.35, 1), (240, 0.35, 3), (500, 0.15, 2), (700, 0.1, 3),
+                                          (30, 0.15, 1), (30, 0.15, 3), (45, 0.15, 2), (40, 0.1, 1),
                                           (70, 0.1, 2), (129, 0.08, 1), (260, 0.1, 3)])
 def test_cd_sweeps_mixed(mctx, n, lam, sweeps):
     """The mixed solve's FP32 sweep against the FP64 sequential sweep of the
@@ -226,13 +230,29 @@ def test_cd_sweeps_mixed(mctx, n, lam, sweeps):
     tol_d = 8 * sweeps * n * eps * bmax / a.min()
     err_d = np.abs(D - D_ref).max()
     assert err_d <= tol_d, (len(fi), err_d, tol_d)
-    # U against Delta W in FP64 from the returned Delta
+    # U against Delta W in FP64 from the returned Delta.  Each pair is updated
+    # once per sweep, so sum_k |mu_k| = sum_s |Delta_s - Delta_{s-1}| (the
+    # oracle's sweep-by-sweep Delta); the FP32 sum of those terms (W and mu
+    # rounded) errs by at most about (2 + d_max sweeps) 2^-24 of |mu| |W|,
+    # plus FP32 underflow
     Dm = np.zeros((n, n))
     Dm[fi, fj] = D
     Dm[fj, fi] = D
-    E = np.abs(Dm) @ np.abs(W)
+    prev, msum = np.zeros(len(fi)), np.zeros(len(fi))
+    for s_ in range(1, sweeps + 1):
+        Ds = D_ref if s_ == sweeps else oracle.cd_sweeps(S, W, A, lam, fi, fj, s_)[0]
+        msum += np.abs(Ds - prev)
+        prev = Ds
+    msum = np.maximum(msum, np.abs(D))  # pairs the two sides zero differently
+    Mm = np.zeros((n, n))
+    Mm[fi, fj] = msum
+    Mm[fj, fi] = msum
+    E = np.abs(Mm) @ np.abs(W)
     dmax = np.bincount(np.concatenate([fi, fj[fi != fj]]), minlength=n).max()
-    assert np.all(np.abs(U - Dm @ W) <= (4 + 2 * dmax * sweeps) * eps * E + 1e-300)
+    # (+ entries of W below FP32's smallest normal, 2^-126, flush to zero)
+    bound = 2 * (2 + dmax * sweeps) * eps * E + (dmax * sweeps + 1) * 2.0 ** -126 * msum.max() + 1e-300
+    ratio = (np.abs(U - Dm @ W) / bound).max()
+    assert ratio <= 1.0, (ratio, dmax)
     # exact zeros: the patterns agree except where the oracle's increment is
     # itself within the FP32 error of zero
     differ = (D == 0) != (D_ref == 0)
