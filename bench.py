@@ -463,6 +463,28 @@ def main():
         compare = {"ms_per_solve": ms, "mixed_speedup_over_fp64": ms["fp64"] / ms["mixed"],
                    f"{oname}_solve": {"relaxations": oinfo["relaxations"], "rel_kkt": oinfo["rel_kkt"],
                                       "objective": oinfo["objective"]}}
+        # the paper's comparison (Section 8): the ML-cycle against the
+        # one-level method (the full free set every cycle) on the same kernels
+        # and input: time, relaxations and the largest support seen (max-supp)
+        lv = {}
+        for name, one in (("ml_cycle", False), ("one_level", True)):
+            linfo = None
+            for _ in range(2):
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one)
+            llat = []
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                llat.append(e0.elapsed_time(e1))
+            lv[name] = {"ms_per_solve": float(np.mean(llat)), "relaxations": linfo["relaxations"],
+                        "cycles": linfo["cycles"], "max_supp": linfo["max_nnz"], "nnz": linfo["nnz"],
+                        "objective": linfo["objective"]}
+        compare["levels"] = lv
 
     # end to end through the public API with host buffers (pinned): S in, A out
     Sh = S.cpu().pin_memory().numpy()

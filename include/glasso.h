@@ -69,6 +69,8 @@ typedef struct {
     double tol;       /* stop when the relative KKT residual is <= tol */
     int max_cycles;   /* ML-cycles (Algorithm 1) before GLASSO_EMAXITER; <= 0 means 200 */
     const double *A0; /* optional warm start (n x n, positive definite); NULL: diag(1/(S_ii + lambda)) */
+    int one_level;    /* 0: the ML-cycle of Algorithm 1; nonzero: the one-level method of the paper's
+                         comparison (Section 8) -- every cycle a single relaxation on the full free set */
 } glasso_problem;
 
 typedef struct {
@@ -82,6 +84,8 @@ typedef struct {
     double logdet;       /* log det A at return */
     double seconds;      /* wall time of the solve */
     int64_t nnz;         /* nonzeros of A (both triangles) */
+    int64_t max_nnz;     /* largest nnz(A) at the fine-level free-set scans and at return (the
+                            paper's max-supp, sampled where the full free set is formed) */
 } glasso_info;
 
 /* ---- context -------------------------------------------------------- */

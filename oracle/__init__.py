@@ -40,7 +40,7 @@ class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relaxations", C.c_int),
                 ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
                 ("max_kkt", C.c_double), ("logdet", C.c_double), ("nnz", C.c_int64),
-                ("ntrace", C.c_int64)]
+                ("ntrace", C.c_int64), ("max_nnz", C.c_int64)]
 
 
 _d = C.POINTER(C.c_double)
@@ -75,7 +75,7 @@ def lib():
                                       C.POINTER(C.c_int)]
         L.orc_line_search.restype = C.c_int
         L.orc_solve.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d, _d,
-                                C.POINTER(Info), _d, C.c_int64]
+                                C.POINTER(Info), _d, C.c_int64, C.c_int]
         L.orc_solve.restype = C.c_int
         _lib = L
     return _lib
@@ -199,8 +199,11 @@ def line_search(S, W, A, lam, pi, pj, D, F0, sigma=1e-4, beta=0.5, max_trials=30
     return rc, A, F.value, alpha.value, trials.value
 
 
-def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0):
-    """a8: the full ML-cycle solve.  Returns (A, W, info dict, trace array)."""
+def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=False):
+    """a8: the full ML-cycle solve (one_level: the paper's one-level
+    comparison, the full free set every cycle).  Returns (A, W, info dict,
+    trace array); info["max_nnz"] is the largest nnz(A) at the fine-level
+    scans and at return."""
     S = _f64(S)
     n = S.shape[0]
     A = np.empty((n, n))
@@ -209,6 +212,6 @@ def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0):
     tr = np.zeros((max(trace_cap, 1), 2))
     a0 = None if A0 is None else _f64(A0)
     lib().orc_solve(_p(S), n, lam, tol, max_cycles, None if a0 is None else _p(a0),
-                    _p(A), _p(W), C.byref(info), _p(tr), trace_cap)
+                    _p(A), _p(W), C.byref(info), _p(tr), trace_cap, 1 if one_level else 0)
     d = {k: getattr(info, k) for k, _ in Info._fields_}
     return A, W, d, tr[: info.ntrace].copy()

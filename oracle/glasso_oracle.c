@@ -369,6 +369,13 @@ int orc_line_search(const double *S, const double *W, double *A, int64_t n, doub
  * |G| = |S - A0^{-1}|.
  * READING: nsweeps = min(1 + floor(k/3), 10) for cycle k.
  *
+ * one_level != 0: the one-level method the paper compares the multilevel
+ * cycle against (Section 8: the same relaxation without the coarse levels):
+ * every cycle is the single relaxation on the full free set (l = 0 only).
+ * max_nnz: the largest nnz(A) (both triangles) seen at the start of a level-0
+ * relaxation and at return (the paper's max-supp, sampled where the fine
+ * free set is formed).
+ *
  * trace (optional, capacity trace_cap): after every relaxation, the objective
  * and the level, as (F, level) pairs.                                         */
 typedef struct {
@@ -382,11 +389,18 @@ typedef struct {
     double logdet;
     int64_t nnz;
     int64_t ntrace;
+    int64_t max_nnz;
 } orc_info;
+
+static int64_t count_nnz(const double *A, size_t nn) {
+    int64_t c = 0;
+    for (size_t t = 0; t < nn; ++t) c += A[t] != 0.0;
+    return c;
+}
 
 int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles,
               const double *A0, double *A, double *W_out, orc_info *info,
-              double *trace, int64_t trace_cap) {
+              double *trace, int64_t trace_cap, int one_level) {
     if (n < 1 || !(lam > 0.0)) return ORC_EINVAL;
     size_t nn = (size_t)(n * n);
     double *L = (double *)malloc(nn * sizeof(double));
@@ -405,7 +419,7 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
     double *D = (double *)malloc((size_t)maxp * sizeof(double));
     int status = ORC_EMAXITER;
     int relax = 0, lstrials = 0, cycles = 0;
-    int64_t ntrace = 0;
+    int64_t ntrace = 0, max_nnz = 0;
     double F = 0.0, relkkt = INFINITY, maxkkt = INFINITY, logdet = 0.0;
 
     if (A0) {
@@ -437,6 +451,7 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
         for (int64_t p = 0; p < nf; ++p) insupp[p] = A[fi[p] * n + fj[p]] != 0.0;
         int L_levels = 1;
         orc_hierarchy(absg, insupp, nf, tag, &L_levels);
+        if (one_level) L_levels = 0;
         for (int l = L_levels; l >= 0; --l) {
             /* 1. factor, invert, objective */
             if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
@@ -448,6 +463,8 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
             /* 2. free set restricted to C_l */
             int64_t np;
             if (l == 0) {
+                const int64_t z = count_nnz(A, nn);
+                if (z > max_nnz) max_nnz = z;
                 np = orc_free_set(S, W, A, n, lam, NULL, NULL, 0, pi, pj);
                 relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
                 /* 3. keep F_{k+1} and |G| for the next hierarchy */
@@ -500,8 +517,7 @@ done:
         }
     }
     if (info) {
-        int64_t nnz = 0;
-        for (size_t t = 0; t < nn; ++t) nnz += A[t] != 0.0;
+        const int64_t nnz = count_nnz(A, nn);
         info->status = status;
         info->cycles = cycles;
         info->relaxations = relax;
@@ -512,6 +528,7 @@ done:
         info->logdet = logdet;
         info->nnz = nnz;
         info->ntrace = ntrace;
+        info->max_nnz = nnz > max_nnz ? nnz : max_nnz;
     }
     free(L); free(W); free(U); free(fi); free(fj); free(ci); free(cj); free(pi); free(pj);
     free(absg); free(insupp); free(tag); free(D);

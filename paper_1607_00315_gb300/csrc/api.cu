@@ -308,7 +308,7 @@ void prof_collect(Prof *prof) {
 // Runs the ML-cycle solve on w.S (and w.A if have_A0).  Leaves the iterate in
 // w.A and its inverse in w.W when W is requested (want_W).
 glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
-                         bool have_A0, bool want_W, glasso_info *info) {
+                         bool have_A0, bool want_W, bool one_level, glasso_info *info) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -320,7 +320,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     const double flop_chol = nd * nd * nd / 3.0, flop_inv = 2.0 * nd * nd * nd / 3.0;
     int cycles = 0, relax = 0, lstrials = 0;
     double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
-    long long nnz = 0;
+    long long nnz = 0, max_nnz = 0;
     glasso_status status = GLASSO_EMAXITER;
     bool W_valid = false, fresh_scan = false;
     int64_t nf = 0;
@@ -350,10 +350,15 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     for (int k = 0; k < max_cycles; ++k) {
         cycles = k + 1;
         const int nsweeps = std::min(1 + k / 3, 10);
-        CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
-        CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
-        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
-        const int Lv = h->levels;
+        // the one-level method (Section 8's comparison): the full free set
+        // every cycle, no hierarchy
+        int Lv = 0;
+        if (!one_level) {
+            CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
+            CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
+            if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            Lv = h->levels;
+        }
         for (int l = Lv; l >= 0; --l) {
             fresh_scan = false;
             if (!W_valid) {
@@ -372,6 +377,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                 trSA = h->trSA;
                 l1 = h->l1;
                 nnz = h->nnz;
+                max_nnz = std::max(max_nnz, nnz);
                 F = -logdet + trSA + lam * l1;
                 relkkt = h->kkt_sum / l1;
                 maxkkt = h->kkt_max;
@@ -459,6 +465,7 @@ done:
         relkkt = h->kkt_sum / l1;
         maxkkt = h->kkt_max;
     }
+    max_nnz = std::max(max_nnz, nnz);
     (void)want_W;
     if (info) {
         info->status = status;
@@ -470,6 +477,7 @@ done:
         info->max_kkt = maxkkt;
         info->logdet = logdet;
         info->nnz = nnz;
+        info->max_nnz = max_nnz;
     }
     return status;
 }
@@ -490,7 +498,7 @@ done:
 //    otherwise an FP32 Cholesky (FP64 diagonal blocks and log accumulation)
 //    whose log-det error is taken as n 2^-20.
 glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
-                               bool have_A0, glasso_info *info) {
+                               bool have_A0, bool one_level, glasso_info *info) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -516,7 +524,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     const int max_ns = 8;
     int cycles = 0, relax = 0, lstrials = 0;
     double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
-    long long nnz = 0;
+    long long nnz = 0, max_nnz = 0;
     glasso_status status = GLASSO_EMAXITER;
     bool W_valid = false, fresh_scan = false, last_chol = false;
     int64_t nf = 0;
@@ -619,10 +627,15 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     for (int k = 0; k < max_cycles; ++k) {
         cycles = k + 1;
         const int nsweeps = std::min(1 + k / 3, 10);
-        CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
-        CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
-        if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
-        const int Lv = h->levels;
+        // the one-level method (Section 8's comparison): the full free set
+        // every cycle, no hierarchy
+        int Lv = 0;
+        if (!one_level) {
+            CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
+            CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
+            if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+            Lv = h->levels;
+        }
         for (int l = Lv; l >= 0; --l) {
             fresh_scan = false;
             if (!W_valid) {
@@ -640,6 +653,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                 trSA = h->trSA;
                 l1 = h->l1;
                 nnz = h->nnz;
+                max_nnz = std::max(max_nnz, nnz);
                 F = -logdet + trSA + lam * l1;
                 relkkt = h->kkt_sum / l1;
                 maxkkt = h->kkt_max;
@@ -795,6 +809,7 @@ done:
         relkkt = h->kkt_sum / l1;
         maxkkt = h->kkt_max;
     }
+    max_nnz = std::max(max_nnz, nnz);
     if (info) {
         info->status = status;
         info->cycles = cycles;
@@ -805,6 +820,7 @@ done:
         info->max_kkt = maxkkt;
         info->logdet = logdet;
         info->nnz = nnz;
+        info->max_nnz = max_nnz;
     }
     return status;
 }
@@ -903,8 +919,9 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
         const int mc = p->max_cycles > 0 ? p->max_cycles : 200;
         const bool warm = p->A0 != nullptr || reuse_A;
         s = precision == GLASSO_MIXED
-                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, &loc)
-                : solve_core(sv, p->n, p->lambda, p->tol, mc, warm, W_out != nullptr, &loc);
+                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, p->one_level != 0, &loc)
+                : solve_core(sv, p->n, p->lambda, p->tol, mc, warm, W_out != nullptr, p->one_level != 0,
+                             &loc);
         if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
             const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost
                                                                     : cudaMemcpyDeviceToDevice;

@@ -40,14 +40,14 @@ class Problem(C.Structure):
     _fields_ = [("input", C.c_int), ("dtype", C.c_int), ("location", C.c_int),
                 ("data", C.c_void_p), ("n", C.c_int64), ("m", C.c_int64), ("center", C.c_int),
                 ("lambda_", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("A0", C.c_void_p)]
+                ("A0", C.c_void_p), ("one_level", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relaxations", C.c_int),
                 ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
                 ("max_kkt", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
-                ("nnz", C.c_int64)]
+                ("nnz", C.c_int64), ("max_nnz", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -172,7 +172,7 @@ class Context:
     # ---------------------------------------------------------------- solver
     @staticmethod
     def problem(data, lam, tol=1e-8, *, samples=False, m=None, n=None, center=False,
-                max_cycles=0, A0=None):
+                max_cycles=0, A0=None, one_level=False):
         """Build a glasso_problem from a numpy array (host) or a torch CUDA tensor."""
         dev = hasattr(data, "data_ptr") and getattr(data, "is_cuda", False)
         if not dev and isinstance(data, np.ndarray) and not data.flags.c_contiguous:
@@ -186,14 +186,15 @@ class Context:
             dt = F64
         p = Problem(INPUT_X if samples else INPUT_S, dt, DEVICE if dev else HOST, _ptr(data),
                     nn if n is None else n, mm if m is None else m, int(center), float(lam),
-                    float(tol), int(max_cycles), _ptr(A0))
+                    float(tol), int(max_cycles), _ptr(A0), int(bool(one_level)))
         return p
 
     def solve(self, data, lam, tol=1e-8, *, samples=False, center=False, max_cycles=0, A0=None,
-              A_out=None, W_out=None, want_W=False, check=True):
-        """glasso_solve.  Returns (A, W or None, info dict)."""
+              A_out=None, W_out=None, want_W=False, check=True, one_level=False):
+        """glasso_solve (one_level: the paper's one-level comparison method).
+        Returns (A, W or None, info dict)."""
         p = self.problem(data, lam, tol, samples=samples, center=center, max_cycles=max_cycles,
-                         A0=A0)
+                         A0=A0, one_level=one_level)
         n = p.n
         if A_out is None:
             if p.location == DEVICE:

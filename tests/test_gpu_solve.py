@@ -96,6 +96,28 @@ def test_mixed_solve_matches_oracle(mctx, gen, n, m, lam, seed):
     assert abs(F_exact - info_ref["objective"]) <= 1e-9 * abs(info_ref["objective"])
 
 
+@pytest.mark.parametrize("gen,n,m,lam,seed", CASES[:3])
+def test_one_level_matches_oracle(ctx, mctx, gen, n, m, lam, seed):
+    """The one-level comparison method (Section 8) against the oracle's
+    one-level run: the FP64 path makes the same relaxations and sees the same
+    largest support (up to pairs on the lambda border); both paths reach the
+    ML-cycle's minimiser."""
+    p = synth.random_problem(n, m, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-11, one_level=True)
+    assert info_ref["status"] == 0
+    A, _, info = ctx.solve(S, lam, tol=1e-11, one_level=True)
+    assert info["status"] == 0, info
+    _compare(A, A_ref, S, lam, info["objective"], info_ref["objective"])
+    assert info["relaxations"] == info_ref["relaxations"]
+    W = np.linalg.inv(A_ref)
+    border = int(np.count_nonzero(np.abs(np.abs(S - W) - lam) <= 1e-7))
+    assert abs(info["max_nnz"] - info_ref["max_nnz"]) <= border
+    Am, _, infom = mctx.solve(S, lam, tol=1e-11, one_level=True)
+    assert infom["status"] == 0, infom
+    _compare(Am, A_ref, S, lam, infom["objective"], info_ref["objective"], MIXED_OBJ_RTOL)
+
+
 def test_config1_from_samples_on_device(ctx):
     import torch
 

@@ -481,3 +481,24 @@ def test_warm_start_at_optimum_stops_immediately():
     A2, _, info, _ = oracle.solve(S, p.lam, tol=1e-9, A0=A)
     assert info["status"] == 0 and info["cycles"] == 1
     assert np.allclose(A2, A, atol=1e-12)
+
+
+@pytest.mark.parametrize("gen,n,lam,seed", [("sparse", 60, 0.1, 41), ("tridiag", 90, 0.15, 42)])
+def test_one_level_reaches_the_same_minimiser(gen, n, lam, seed):
+    """The one-level method (the paper's Section 8 comparison: every cycle a
+    single relaxation on the full free set) and the ML-cycle minimise the
+    same strictly convex objective, whose minimiser is unique: the two
+    oracle runs must agree, the one-level run must make exactly one
+    relaxation per cycle, and max-supp bounds the final support."""
+    p = synth.random_problem(n, 2 * n, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    A_ml, _, i_ml, _ = oracle.solve(S, lam, tol=1e-11)
+    A_1, _, i_1, tr = oracle.solve(S, lam, tol=1e-11, one_level=True, trace_cap=200)
+    assert i_ml["status"] == 0 and i_1["status"] == 0
+    assert np.abs(A_1 - A_ml).max() <= 1e-7
+    assert abs(i_1["objective"] - i_ml["objective"]) <= 1e-10 * abs(i_ml["objective"])
+    assert i_1["relaxations"] in (i_1["cycles"], i_1["cycles"] - 1)
+    assert np.all(tr[:, 1] == 0)  # every relaxation on the finest level
+    for info in (i_ml, i_1):
+        assert info["max_nnz"] >= info["nnz"] == np.count_nonzero(A_ml)
+
