@@ -50,12 +50,11 @@ glasso_status fail_cuda(std::string &err, cudaError_t e, const char *what) {
 // GLASSO_TRACE=1 prints one line per relaxation to stderr (level, free pairs,
 // objective, line-search regime and step, refinement steps).
 bool trace_on() {
-    static int on = -1;
-    if (on < 0) {
+    static const bool on = [] {
         const char *e = getenv("GLASSO_TRACE");
-        on = (e && *e && *e != '0') ? 1 : 0;
-    }
-    return on == 1;
+        return e && *e && *e != '0';
+    }();
+    return on;
 }
 
 size_t footprint(int64_t n, int64_t m, int xbytes) {

@@ -1088,9 +1088,11 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     }
 }
 
-bool g_lag_attr = false;
+OncePerDevice g_lag_once;
+int g_lag_nsm[kMaxDevices], g_lag_occ[kMaxDevices];
 
-bool g_attr_done[4] = {false, false, false, false};
+OncePerDevice g_persist_once[4];
+int g_persist_nsm[4][kMaxDevices], g_persist_occ[4][kMaxDevices];
 
 }  // namespace
 
@@ -1103,22 +1105,23 @@ static cudaError_t cd_sweeps_t(const T *W, int64_t n, double lam, const int32_t 
     if (n > (1 << 22)) return cudaErrorInvalidValue;  // packed sort keys hold the row in 23 bits
     const size_t kbytes = (size_t)CD_B * CD_B * sizeof(CT);
     const int which = (sizeof(T) == 8 ? 2 : 0) + (sizeof(CT) == 8 ? 1 : 0);
-    static int nsm = 0, occ[4] = {0, 0, 0, 0};
-    if (!g_attr_done[which]) {
+    int dev = 0;
+    cudaError_t ie = g_persist_once[which].run(dev, [&](int d) {
         cudaError_t e = cudaFuncSetAttribute(k_cd_persist<T, CT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kbytes);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[which], k_cd_persist<T, CT>, RT, kbytes);
+        e = cudaDeviceGetAttribute(&g_persist_nsm[which][d], cudaDevAttrMultiProcessorCount, d);
         if (e != cudaSuccess) return e;
-        if (occ[which] < 1) return cudaErrorInvalidConfiguration;
-        g_attr_done[which] = true;
-    }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_persist_occ[which][d], k_cd_persist<T, CT>, RT,
+                                                          kbytes);
+        if (e != cudaSuccess) return e;
+        return g_persist_occ[which][d] < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
+    });
+    if (ie != cudaSuccess) return ie;
+    const int nsm = g_persist_nsm[which][dev], occ = g_persist_occ[which][dev];
     if (np <= 0 || nsweeps <= 0) return cudaSuccess;
     // enough CTAs for the row-update and dot phases, no more than co-resident
-    int G = (int)lmax(4, lmin((int64_t)nsm * occ[which], (n + 7) / 8));
+    int G = (int)lmax(4, lmin((int64_t)nsm * occ, (n + 7) / 8));
     // partial dots: ceil(n / DCH) x CD_B doubles, then the interaction matrix
     if ((n + DCH - 1) / DCH > CD_MAX_CHUNKS) return cudaErrorInvalidValue;
     double *bvec = w.cd_part;
@@ -1178,19 +1181,19 @@ static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const in
     const size_t kbytes = (size_t)(3 * nbatch) * kb;  // intra, +1, +2 matrices
     const size_t kneed = kbytes + (size_t)(nbatch + 1) * LST * sizeof(int);  // + merged lists
     if (kneed > (size_t)n * (size_t)n * sizeof(double)) return cudaErrorNotSupported;
-    static int nsm = 0, occ = 0;
     const size_t dyn = 3 * kb;  // two intra buffers and the +1 matrix
-    if (!g_lag_attr) {
+    int dev = 0;
+    cudaError_t ie = g_lag_once.run(dev, [&](int d) {
         cudaError_t e = cudaFuncSetAttribute(k_cd_lag2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cd_lag2, LT, dyn);
+        e = cudaDeviceGetAttribute(&g_lag_nsm[d], cudaDevAttrMultiProcessorCount, d);
         if (e != cudaSuccess) return e;
-        if (occ < 1) return cudaErrorInvalidConfiguration;
-        g_lag_attr = true;
-    }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_lag_occ[d], k_cd_lag2, LT, dyn);
+        if (e != cudaSuccess) return e;
+        return g_lag_occ[d] < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
+    });
+    if (ie != cudaSuccess) return ie;
+    const int nsm = g_lag_nsm[dev], occ = g_lag_occ[dev];
     GridBar *gb = reinterpret_cast<GridBar *>(&w.sc->bar_count);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;

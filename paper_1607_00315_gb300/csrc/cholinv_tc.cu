@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(XTHREADS, 1)
                      : "memory");
 }
 
-bool g_tcx_attr = false;
+OncePerDevice g_tcx_once;
 
 // C (M x N) from P (M x K) and Q (N x K), both sub-matrices of FP32 buffers
 // with row stride ld (a multiple of 32 floats, 16-byte aligned bases).
@@ -404,11 +404,11 @@ cudaError_t tcx(const float *P, const float *Q, int64_t M, int64_t N, int64_t K,
                 float *out, int64_t ldo, float *outT, int64_t ldt, const int *info, int *err,
                 cudaStream_t st, double scale64 = 1.0) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    if (!g_tcx_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XSMEM);
-        if (e != cudaSuccess) return e;
-        g_tcx_attr = true;
-    }
+    int dev = 0;
+    cudaError_t ie = g_tcx_once.run(dev, [](int) {
+        return cudaFuncSetAttribute(k_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XSMEM);
+    });
+    if (ie != cudaSuccess) return ie;
     CUtensorMap mp, mq;
     cudaError_t e = make_tmap(&mp, P, M, lmax(K, 1), ld);
     if (e != cudaSuccess) return e;

@@ -920,13 +920,12 @@ cudaError_t inverse32(const float *L, int64_t n, float *W, float *X, float *Tw, 
 
 cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, float *Xt, double *ldiag,
                         DevScalars *sc, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)LEAF_SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static OncePerDevice once;
+    int dev = 0;
+    cudaError_t ie = once.run(dev, [](int) {
+        return cudaFuncSetAttribute(k_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
+    });
+    if (ie != cudaSuccess) return ie;
     if (s < 1 || s > LB) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};  // programmatic serialisation, as for the GEMMs
     cfg.gridDim = dim3(1);

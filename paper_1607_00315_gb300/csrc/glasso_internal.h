@@ -7,11 +7,30 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "glasso.h"
 
 namespace glx {
+
+// One-time set-up per device (kernel attributes, occupancy), thread-safe:
+// host threads of the serving slots may enter a launcher together, and a
+// process may drive several devices.  init(dev) runs once per device; its
+// status is returned to every caller.
+constexpr int kMaxDevices = 64;
+struct OncePerDevice {
+    std::once_flag flag[kMaxDevices];
+    cudaError_t status[kMaxDevices] = {};
+    template <typename F>
+    cudaError_t run(int &dev, F init) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+        std::call_once(flag[dev], [&] { status[dev] = init(dev); });
+        return status[dev];
+    }
+};
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialisation runs its prologue while its predecessor finishes; it must

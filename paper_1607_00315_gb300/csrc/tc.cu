@@ -304,7 +304,7 @@ cudaError_t make_map(CUtensorMap *map, const float *base, int64_t rows, int64_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-bool g_tc_attr[1] = {false};
+OncePerDevice g_tc_once[1];
 
 // P: nrows x kp (row stride ldp_), Q: nrows x K (row stride ld); the k-loop
 // runs to K, and TMA fills P's columns beyond kp with zeros.
@@ -312,12 +312,11 @@ template <int EPI>
 cudaError_t launch_lower(const float *P, int64_t kp, int64_t ldp_, const float *Q, int64_t nrows,
                          int64_t K, int64_t ld, const float *inh, float *outh, float *outl, int64_t ldo,
                          int *err, cudaStream_t st) {
-    if (!g_tc_attr[EPI]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_lower<EPI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        if (e != cudaSuccess) return e;
-        g_tc_attr[EPI] = true;
-    }
+    int dev = 0;
+    cudaError_t ie = g_tc_once[EPI].run(dev, [](int) {
+        return cudaFuncSetAttribute(k_tc_lower<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    });
+    if (ie != cudaSuccess) return ie;
     CUtensorMap mp, mq;
     cudaError_t e = make_map(&mp, P, nrows, kp, ldp_);
     if (e != cudaSuccess) return e;
