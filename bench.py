@@ -464,20 +464,24 @@ def main():
                    f"{oname}_solve": {"relaxations": oinfo["relaxations"], "rel_kkt": oinfo["rel_kkt"],
                                       "objective": oinfo["objective"]}}
         # the paper's comparison (Section 8): the ML-cycle against the
-        # one-level method (the full free set every cycle) on the same kernels
-        # and input: time, relaxations and the largest support seen (max-supp)
+        # one-level method (the full free set every cycle) and the one-level
+        # method after continuation stages, on the same kernels and input:
+        # time, relaxations and the largest support seen (max-supp)
         lv = {}
-        for name, one in (("ml_cycle", False), ("one_level", True)):
+        for name, one, cont in (("ml_cycle", False, False), ("one_level", True, False),
+                                ("continuation", True, True)):
             linfo = None
             for _ in range(2):
-                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one)
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one,
+                                        continuation=cont)
             llat = []
             for _ in range(args.steps):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one)
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one,
+                                        continuation=cont)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 llat.append(e0.elapsed_time(e1))

@@ -71,6 +71,12 @@ typedef struct {
     const double *A0; /* optional warm start (n x n, positive definite); NULL: diag(1/(S_ii + lambda)) */
     int one_level;    /* 0: the ML-cycle of Algorithm 1; nonzero: the one-level method of the paper's
                          comparison (Section 8) -- every cycle a single relaxation on the full free set */
+    int continuation; /* nonzero: the continuation strategy (end of Section 2, schedule of Section 8):
+                         before the cycles, one full-free-set relaxation at each of lambda_4 > lambda_3 >
+                         lambda_2, lambda_s = lambda + (s-1)(lambda_4 - lambda)/3, lambda_4 =
+                         (max_{i!=j} |S_ij| + lambda)/2 (no stages when that maximum is <= lambda).
+                         These relaxations count in `relaxations` and `max_nnz`, not in `cycles`;
+                         max_cycles bounds the cycles at lambda.  Combines with either method. */
 } glasso_problem;
 
 typedef struct {

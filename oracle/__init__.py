@@ -75,8 +75,10 @@ def lib():
                                       C.POINTER(C.c_int)]
         L.orc_line_search.restype = C.c_int
         L.orc_solve.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d, _d,
-                                C.POINTER(Info), _d, C.c_int64, C.c_int]
+                                C.POINTER(Info), _d, C.c_int64, C.c_int, C.c_int]
         L.orc_solve.restype = C.c_int
+        L.orc_continuation_lambdas.argtypes = [_d, C.c_int64, C.c_double, _d]
+        L.orc_continuation_lambdas.restype = C.c_int
         _lib = L
     return _lib
 
@@ -199,9 +201,21 @@ def line_search(S, W, A, lam, pi, pj, D, F0, sigma=1e-4, beta=0.5, max_trials=30
     return rc, A, F.value, alpha.value, trials.value
 
 
-def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=False):
+def continuation_lambdas(S, lam):
+    """The continuation's stage values lambda_4 > lambda_3 > lambda_2
+    (Section 8; lambda_4 = (max_{i != j} |S_ij| + lambda) / 2), empty when the
+    solution at lambda is diagonal."""
+    S = _f64(S)
+    out = np.zeros(3)
+    k = lib().orc_continuation_lambdas(_p(S), S.shape[0], lam, _p(out))
+    return out[:k].copy()
+
+
+def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=False,
+          continuation=False):
     """a8: the full ML-cycle solve (one_level: the paper's one-level
-    comparison, the full free set every cycle).  Returns (A, W, info dict,
+    comparison, the full free set every cycle; continuation: one relaxation
+    at each continuation_lambdas value first).  Returns (A, W, info dict,
     trace array); info["max_nnz"] is the largest nnz(A) at the fine-level
     scans and at return."""
     S = _f64(S)
@@ -212,6 +226,7 @@ def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=Fals
     tr = np.zeros((max(trace_cap, 1), 2))
     a0 = None if A0 is None else _f64(A0)
     lib().orc_solve(_p(S), n, lam, tol, max_cycles, None if a0 is None else _p(a0),
-                    _p(A), _p(W), C.byref(info), _p(tr), trace_cap, 1 if one_level else 0)
+                    _p(A), _p(W), C.byref(info), _p(tr), trace_cap, 1 if one_level else 0,
+                    1 if continuation else 0)
     d = {k: getattr(info, k) for k, _ in Info._fields_}
     return A, W, d, tr[: info.ntrace].copy()

@@ -376,8 +376,16 @@ int orc_line_search(const double *S, const double *W, double *A, int64_t n, doub
  * relaxation and at return (the paper's max-supp, sampled where the fine
  * free set is formed).
  *
+ * continuation != 0: the continuation strategy (end of Section 2; the
+ * schedule of Section 8): before the cycles at lambda, one level-0
+ * relaxation at each of lambda_4 > lambda_3 > lambda_2 in that order, each
+ * from the previous one's iterate (see orc_continuation_lambdas).  The free
+ * set of the last one seeds the first cycle's hierarchy.  These relaxations
+ * count in `relaxations` and in max_nnz, not in `cycles`; max_cycles bounds
+ * the cycles at lambda only.
+ *
  * trace (optional, capacity trace_cap): after every relaxation, the objective
- * and the level, as (F, level) pairs.                                         */
+ * (at the lambda that relaxation used) and the level, as (F, level) pairs.    */
 typedef struct {
     int status;
     int cycles;
@@ -398,9 +406,33 @@ static int64_t count_nnz(const double *A, size_t nn) {
     return c;
 }
 
+/* The continuation's intermediate regularisation values (Section 8):
+ * lambda_4 = (lambda_max + lambda) / 2 and lambda_3, lambda_2 linearly spaced
+ * between lambda_4 and lambda_1 = lambda, i.e. lambda_s = lambda +
+ * (s - 1)(lambda_4 - lambda) / 3.
+ * READING: the paper takes lambda_4 = (1 + lambda) / 2 because its data are
+ * normalised (diag S = 1), so every off-diagonal |S_ij| <= 1 and any lambda
+ * >= 1 gives a diagonal minimiser.  For unnormalised S the same role is
+ * played by lambda_max = max_{i != j} |S_ij|, the smallest lambda whose
+ * minimiser is diagonal; lambda_max <= 1 on normalised data.  When
+ * lambda_max <= lambda the solution at lambda is already diagonal and there
+ * are no stages.
+ * Writes lambda_4, lambda_3, lambda_2 to out[0..2]; returns the stage count
+ * (3 or 0).                                                                  */
+int orc_continuation_lambdas(const double *S, int64_t n, double lam, double *out) {
+    double lmax = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            if (fabs(S[i * n + j]) > lmax) lmax = fabs(S[i * n + j]);
+    if (!(lmax > lam)) return 0;
+    const double l4 = 0.5 * (lmax + lam);
+    for (int s = 4; s >= 2; --s) out[4 - s] = lam + (double)(s - 1) * (l4 - lam) / 3.0;
+    return 3;
+}
+
 int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles,
               const double *A0, double *A, double *W_out, orc_info *info,
-              double *trace, int64_t trace_cap, int one_level) {
+              double *trace, int64_t trace_cap, int one_level, int continuation) {
     if (n < 1 || !(lam > 0.0)) return ORC_EINVAL;
     size_t nn = (size_t)(n * n);
     double *L = (double *)malloc(nn * sizeof(double));
@@ -444,14 +476,18 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
                 ++nf;
             }
 
-    for (int k = 0; k < max_cycles; ++k) {
-        cycles = k + 1;
-        int nsweeps = 1 + k / 3;
+    double stage_lam[3];
+    const int nstage = continuation ? orc_continuation_lambdas(S, n, lam, stage_lam) : 0;
+    /* k < 0: the continuation stages, one level-0 relaxation each at lambda_s */
+    for (int k = -nstage; k < max_cycles; ++k) {
+        const double lk = k < 0 ? stage_lam[k + nstage] : lam;
+        if (k >= 0) cycles = k + 1;
+        int nsweeps = k < 0 ? 1 : 1 + k / 3;
         if (nsweeps > 10) nsweeps = 10;
         for (int64_t p = 0; p < nf; ++p) insupp[p] = A[fi[p] * n + fj[p]] != 0.0;
         int L_levels = 1;
         orc_hierarchy(absg, insupp, nf, tag, &L_levels);
-        if (one_level) L_levels = 0;
+        if (one_level || k < 0) L_levels = 0;
         for (int l = L_levels; l >= 0; --l) {
             /* 1. factor, invert, objective */
             if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
@@ -459,14 +495,14 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
             orc_inverse_from_chol(L, n, W);
             double tr, l1;
             trace_and_l1(S, A, n, &tr, &l1);
-            F = -logdet + tr + lam * l1;
+            F = -logdet + tr + lk * l1;
             /* 2. free set restricted to C_l */
             int64_t np;
             if (l == 0) {
                 const int64_t z = count_nnz(A, nn);
                 if (z > max_nnz) max_nnz = z;
-                np = orc_free_set(S, W, A, n, lam, NULL, NULL, 0, pi, pj);
-                relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
+                np = orc_free_set(S, W, A, n, lk, NULL, NULL, 0, pi, pj);
+                relkkt = orc_rel_kkt(S, W, A, n, lk, &maxkkt);
                 /* 3. keep F_{k+1} and |G| for the next hierarchy */
                 for (int64_t p = 0; p < np; ++p) {
                     fi[p] = pi[p];
@@ -474,24 +510,24 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
                     absg[p] = fabs(S[pi[p] * n + pj[p]] - W[pi[p] * n + pj[p]]);
                 }
                 nf = np;
-                if (relkkt <= tol) { status = ORC_OK; goto done; }
+                if (k >= 0 && relkkt <= tol) { status = ORC_OK; goto done; }
             } else {
                 int64_t nc = 0;
                 for (int64_t p = 0; p < nf; ++p)
                     if (tag[p] >= l) { ci[nc] = fi[p]; cj[nc] = fj[p]; ++nc; }
-                np = orc_free_set(S, W, A, n, lam, ci, cj, nc, pi, pj);
+                np = orc_free_set(S, W, A, n, lk, ci, cj, nc, pi, pj);
             }
             /* 4. Newton direction */
             memset(U, 0, nn * sizeof(double));
             memset(D, 0, (size_t)np * sizeof(double));
-            orc_cd_sweeps(S, W, A, n, lam, pi, pj, np, nsweeps, D, U);
+            orc_cd_sweeps(S, W, A, n, lk, pi, pj, np, nsweeps, D, U);
             int moved = 0;
             for (int64_t p = 0; p < np; ++p) moved |= (D[p] != 0.0);
             /* 5. line search */
             if (moved) {
                 double alpha;
                 int tr_used;
-                int rc = orc_line_search(S, W, A, n, lam, pi, pj, np, D, 1e-4, 0.5, 30, &F,
+                int rc = orc_line_search(S, W, A, n, lk, pi, pj, np, D, 1e-4, 0.5, 30, &F,
                                          &alpha, &tr_used);
                 lstrials += tr_used;
                 if (rc != ORC_OK) { status = rc; goto done; }

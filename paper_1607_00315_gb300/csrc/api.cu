@@ -304,10 +304,26 @@ void prof_collect(Prof *prof) {
     prof->pend_work.clear();
 }
 
+// The continuation's stage values (end of Section 2; the schedule of
+// Section 8): lambda_4 halfway between lambda and lambda_max = max_{i != j}
+// |S_ij| (the smallest lambda whose minimiser is diagonal; at most 1 on the
+// paper's normalised data, where it takes lambda_4 = (1 + lambda) / 2), then
+// lambda_3, lambda_2 evenly spaced down to lambda.  Returns the stage count:
+// 3, or 0 when lambda_max <= lambda.
+int continuation_lambdas(unsigned long long smax_bits, double lam, double out[3]) {
+    double lmax;
+    memcpy(&lmax, &smax_bits, sizeof(lmax));
+    if (!(lmax > lam)) return 0;
+    const double l4 = 0.5 * (lmax + lam);
+    for (int s = 4; s >= 2; --s) out[4 - s] = lam + (double)(s - 1) * (l4 - lam) / 3.0;
+    return 3;
+}
+
 // Runs the ML-cycle solve on w.S (and w.A if have_A0).  Leaves the iterate in
 // w.A and its inverse in w.W when W is requested (want_W).
 glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
-                         bool have_A0, bool want_W, bool one_level, glasso_info *info) {
+                         bool have_A0, bool want_W, bool one_level, bool continuation,
+                         glasso_info *info) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -338,6 +354,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     CK(inverse(w.L, n, w.W, w.T, w.U, st));
     sv.mark_end(1, eb, flop_inv);
     W_valid = true;
+    if (continuation) CK(offdiag_absmax(w.S, n, sc, st));
     // initial free set (Section 7 footnote): {|S_ij| > lambda} united with supp(A0)
     CK(scan_full(w.S, w.W, w.A, n, lam, 1, w, w.fi, w.fj, w.fabsg, sc, st));
     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -346,13 +363,22 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     l1 = h->l1;
     F = -logdet + trSA + lam * l1;
 
-    for (int k = 0; k < max_cycles; ++k) {
-        cycles = k + 1;
-        const int nsweeps = std::min(1 + k / 3, 10);
-        // the one-level method (Section 8's comparison): the full free set
-        // every cycle, no hierarchy
+    double stage_lam[3];
+    const int nstage = continuation ? continuation_lambdas(h->smax_bits, lam, stage_lam) : 0;
+    double lam_F = lam;  // the lambda that F currently includes
+    // k < 0: the continuation stages, one level-0 relaxation each at lambda_s
+    for (int k = -nstage; k < max_cycles; ++k) {
+        const double lk = k < 0 ? stage_lam[k + nstage] : lam;
+        if (k >= 0) cycles = k + 1;
+        const int nsweeps = k < 0 ? 1 : std::min(1 + k / 3, 10);
+        if (lk != lam_F) {
+            F = -logdet + trSA + lk * l1;
+            lam_F = lk;
+        }
+        // the one-level method (Section 8's comparison) and the continuation
+        // stages: the full free set, no hierarchy
         int Lv = 0;
-        if (!one_level) {
+        if (!one_level && k >= 0) {
             CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
             CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -369,7 +395,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             int64_t np;
             if (l == 0) {
                 sv.mark_begin(2, eb);
-                CK(scan_full(w.S, w.W, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+                CK(scan_full(w.S, w.W, w.A, n, lk, 0, w, w.pi, w.pj, w.pabsg, sc, st));
                 sv.mark_end(2, eb, 3.0 * nd * (nd + 1) / 2 * 8.0);
                 if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                 np = h->count;
@@ -377,33 +403,33 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                 l1 = h->l1;
                 nnz = h->nnz;
                 max_nnz = std::max(max_nnz, nnz);
-                F = -logdet + trSA + lam * l1;
+                F = -logdet + trSA + lk * l1;
                 relkkt = h->kkt_sum / l1;
                 maxkkt = h->kkt_max;
-                fresh_scan = true;
+                fresh_scan = k >= 0;  // a stage scan is at lambda_s, not lambda
                 CK(cudaMemcpyAsync(w.fi, w.pi, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(w.fj, w.pj, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(w.fabsg, w.pabsg, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
                 nf = np;
-                if (relkkt <= tol) {
+                if (k >= 0 && relkkt <= tol) {
                     status = GLASSO_OK;
                     goto done;
                 }
             } else {
-                CK(scan_cand(w.S, w.W, w.A, n, lam, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
+                CK(scan_cand(w.S, w.W, w.A, n, lk, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
                              nullptr, sc, st));
                 if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                 np = h->count;
             }
             ++relax;
             if (np == 0) continue;
-            CK(pair_prep(w.S, w.W, w.A, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+            CK(pair_prep(w.S, w.W, w.A, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
             CK(cudaMemsetAsync(w.U, 0, (size_t)(n * n) * sizeof(double), st));
             CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
             sv.mark_begin(3, eb);
-            CK(cd_sweeps(w.W, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
+            CK(cd_sweeps(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
             sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 8.0);
-            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
+            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lk, w, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->bar_err) {
                 err = "CD sweep: a bounded grid-barrier wait expired";
@@ -427,7 +453,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                     if (h->info == 0) {
                         ldT = h->logdet;
                         dl1 = h->dl1;
-                        FT = -ldT + trSA + alpha * trSD + lam * (l1 + dl1);
+                        FT = -ldT + trSA + alpha * trSD + lk * (l1 + dl1);
                         if (FT <= F + sigma * alpha * delta + epsF) {
                             ok = true;
                             break;
@@ -497,7 +523,7 @@ done:
 //    otherwise an FP32 Cholesky (FP64 diagonal blocks and log accumulation)
 //    whose log-det error is taken as n 2^-20.
 glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
-                               bool have_A0, bool one_level, glasso_info *info) {
+                               bool have_A0, bool one_level, bool continuation, glasso_info *info) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -616,6 +642,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         if (s2 != GLASSO_OK) return s2;
     }
     W_valid = true;
+    if (continuation) CK(offdiag_absmax(w.S, n, sc, st));
     CK(scan_full(w.S, W64, w.A, n, lam, 1, w, w.fi, w.fj, w.fabsg, sc, st));
     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
     nf = h->count;
@@ -623,13 +650,22 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     l1 = h->l1;
     F = -logdet + trSA + lam * l1;
 
-    for (int k = 0; k < max_cycles; ++k) {
-        cycles = k + 1;
-        const int nsweeps = std::min(1 + k / 3, 10);
-        // the one-level method (Section 8's comparison): the full free set
-        // every cycle, no hierarchy
+    double stage_lam[3];
+    const int nstage = continuation ? continuation_lambdas(h->smax_bits, lam, stage_lam) : 0;
+    double lam_F = lam;  // the lambda that F currently includes
+    // k < 0: the continuation stages, one level-0 relaxation each at lambda_s
+    for (int k = -nstage; k < max_cycles; ++k) {
+        const double lk = k < 0 ? stage_lam[k + nstage] : lam;
+        if (k >= 0) cycles = k + 1;
+        const int nsweeps = k < 0 ? 1 : std::min(1 + k / 3, 10);
+        if (lk != lam_F) {
+            F = -logdet + trSA + lk * l1;
+            lam_F = lk;
+        }
+        // the one-level method (Section 8's comparison) and the continuation
+        // stages: the full free set, no hierarchy
         int Lv = 0;
-        if (!one_level) {
+        if (!one_level && k >= 0) {
             CK(support_flags(w.A, n, w.fi, w.fj, nf, w.fsupp, st));
             CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -645,7 +681,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             int64_t np;
             if (l == 0) {
                 sv.mark_begin(2, eb);
-                CK(scan_full(w.S, W64, w.A, n, lam, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+                CK(scan_full(w.S, W64, w.A, n, lk, 0, w, w.pi, w.pj, w.pabsg, sc, st));
                 sv.mark_end(2, eb, 3.0 * nd * (nd + 1) / 2 * 8.0);
                 if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                 np = h->count;
@@ -653,27 +689,27 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                 l1 = h->l1;
                 nnz = h->nnz;
                 max_nnz = std::max(max_nnz, nnz);
-                F = -logdet + trSA + lam * l1;
+                F = -logdet + trSA + lk * l1;
                 relkkt = h->kkt_sum / l1;
                 maxkkt = h->kkt_max;
-                fresh_scan = true;
+                fresh_scan = k >= 0;  // a stage scan is at lambda_s, not lambda
                 CK(cudaMemcpyAsync(w.fi, w.pi, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(w.fj, w.pj, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
                 CK(cudaMemcpyAsync(w.fabsg, w.pabsg, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
                 nf = np;
-                if (relkkt <= tol) {
+                if (k >= 0 && relkkt <= tol) {
                     status = GLASSO_OK;
                     goto done;
                 }
             } else {
-                CK(scan_cand(w.S, W64, w.A, n, lam, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
+                CK(scan_cand(w.S, W64, w.A, n, lk, w.fi, w.fj, w.ftag, l, nf, w, w.pi, w.pj,
                              nullptr, sc, st));
                 if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                 np = h->count;
             }
             ++relax;
             if (np == 0) continue;
-            CK(pair_prep(w.S, W64, w.A, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+            CK(pair_prep(w.S, W64, w.A, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
             CK(cudaMemsetAsync(U32, 0, nn * sizeof(float), st));
             CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
             sv.mark_begin(3, eb);
@@ -681,10 +717,10 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             // once the relative KKT residual is small, where the Newton step must be
             // resolved to the gradient's FP64 accuracy
             // (the FP64 buffer T is free in this path: it holds the second copy of U)
-            CK(cd_sweeps32(W32, n, lam, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
+            CK(cd_sweeps32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
                            relkkt <= 1e-6, st, (float *)w.T));
             sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 4.0);
-            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lam, w, sc, st));
+            CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lk, w, sc, st));
             CK(series_terms(W64, n, w.pi, w.pj, w.D, np, U32, w.part, w.cap_part, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->bar_err) {
@@ -764,7 +800,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                     ++lstrials;
                     if (pd) {
                         dl1 = h->dl1;
-                        FT = F - dld + alpha * trSD + lam * dl1;
+                        FT = F - dld + alpha * trSD + lk * dl1;
                         if (FT <= F + sigma * alpha * delta + errb + epsF) {
                             ok = true;
                             break;
@@ -918,8 +954,10 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
         const int mc = p->max_cycles > 0 ? p->max_cycles : 200;
         const bool warm = p->A0 != nullptr || reuse_A;
         s = precision == GLASSO_MIXED
-                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, p->one_level != 0, &loc)
+                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, p->one_level != 0,
+                                   p->continuation != 0, &loc)
                 : solve_core(sv, p->n, p->lambda, p->tol, mc, warm, W_out != nullptr, p->one_level != 0,
+                             p->continuation != 0,
                              &loc);
         if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
             const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost

@@ -93,6 +93,7 @@ struct DevScalars {
     unsigned bar_gen;
     int bar_err;
     int pad3;
+    unsigned long long smax_bits;  // max_{i != j} |S_ij| as the bits of a non-negative double
 };
 
 // Per-context device workspace, sized for n <= cap_n.
@@ -193,6 +194,8 @@ cudaError_t support_flags(const double *A, int64_t n, const int32_t *fi, const i
                           int64_t nf, uint8_t *flag, cudaStream_t st);
 cudaError_t init_diag(const double *S, int64_t n, double lam, double *A, DevScalars *sc,
                       cudaStream_t st);
+// sc->smax_bits = the bits of max_{i < j} |S_ij| (0 for n = 1)
+cudaError_t offdiag_absmax(const double *S, int64_t n, DevScalars *sc, cudaStream_t st);
 // per-pair data for the CD sweep
 cudaError_t pair_prep(const double *S, const double *W, const double *A, int64_t n, double lam,
                       const int32_t *pi, const int32_t *pj, int64_t np, double *inva, double *g,

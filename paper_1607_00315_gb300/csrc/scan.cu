@@ -6,6 +6,7 @@
 // partials in a fixed order, then one CTA combines them in a fixed order.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "glasso_internal.h"
@@ -295,6 +296,27 @@ __global__ void k_init_diag(const double *__restrict__ S, int64_t n, double lam,
     }
 }
 
+// max_{i < j} |S_ij| (the smallest lambda whose minimiser is diagonal), for
+// the continuation schedule.  One row per block step, coalesced along the
+// row; block maximum by warp shuffles; one atomicMax per block on the bits of
+// the (non-negative) double, whose unsigned order is the numeric order.
+// sc->smax_bits must be zero on entry.
+__global__ void k_offdiag_absmax(const double *__restrict__ S, int64_t n, DevScalars *sc) {
+    __shared__ double red[8];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const double *row = S + i * n;
+        for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) m = fmax(m, fabs(row[j]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+        atomicMax(&sc->smax_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 __global__ void k_pair_prep(const double *__restrict__ S, const double *__restrict__ W,
                             const double *__restrict__ A, int64_t n, const int32_t *__restrict__ pi,
                             const int32_t *__restrict__ pj, int64_t np, double *__restrict__ inva,
@@ -425,6 +447,15 @@ cudaError_t scan_cand(const double *S, const double *W, const double *A, int64_t
 cudaError_t support_flags(const double *A, int64_t n, const int32_t *fi, const int32_t *fj,
                           int64_t nf, uint8_t *flag, cudaStream_t st) {
     k_support<<<grid_for(nf), 256, 0, st>>>(A, n, fi, fj, nf, flag);
+    counted(1);
+    return cudaGetLastError();
+}
+
+cudaError_t offdiag_absmax(const double *S, int64_t n, DevScalars *sc, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&sc->smax_bits, 0, sizeof(sc->smax_bits), st);
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)std::min<int64_t>(std::max<int64_t>(n, 1), 152 * 8);
+    k_offdiag_absmax<<<g, 256, 0, st>>>(S, n, sc);
     counted(1);
     return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ class Problem(C.Structure):
     _fields_ = [("input", C.c_int), ("dtype", C.c_int), ("location", C.c_int),
                 ("data", C.c_void_p), ("n", C.c_int64), ("m", C.c_int64), ("center", C.c_int),
                 ("lambda_", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("A0", C.c_void_p), ("one_level", C.c_int)]
+                ("A0", C.c_void_p), ("one_level", C.c_int), ("continuation", C.c_int)]
 
 
 class Info(C.Structure):
@@ -172,7 +172,7 @@ class Context:
     # ---------------------------------------------------------------- solver
     @staticmethod
     def problem(data, lam, tol=1e-8, *, samples=False, m=None, n=None, center=False,
-                max_cycles=0, A0=None, one_level=False):
+                max_cycles=0, A0=None, one_level=False, continuation=False):
         """Build a glasso_problem from a numpy array (host) or a torch CUDA tensor."""
         dev = hasattr(data, "data_ptr") and getattr(data, "is_cuda", False)
         if not dev and isinstance(data, np.ndarray) and not data.flags.c_contiguous:
@@ -186,15 +186,18 @@ class Context:
             dt = F64
         p = Problem(INPUT_X if samples else INPUT_S, dt, DEVICE if dev else HOST, _ptr(data),
                     nn if n is None else n, mm if m is None else m, int(center), float(lam),
-                    float(tol), int(max_cycles), _ptr(A0), int(bool(one_level)))
+                    float(tol), int(max_cycles), _ptr(A0), int(bool(one_level)),
+                    int(bool(continuation)))
         return p
 
     def solve(self, data, lam, tol=1e-8, *, samples=False, center=False, max_cycles=0, A0=None,
-              A_out=None, W_out=None, want_W=False, check=True, one_level=False):
-        """glasso_solve (one_level: the paper's one-level comparison method).
+              A_out=None, W_out=None, want_W=False, check=True, one_level=False,
+              continuation=False):
+        """glasso_solve (one_level: the paper's one-level comparison method;
+        continuation: the paper's continuation stages before the cycles).
         Returns (A, W or None, info dict)."""
         p = self.problem(data, lam, tol, samples=samples, center=center, max_cycles=max_cycles,
-                         A0=A0, one_level=one_level)
+                         A0=A0, one_level=one_level, continuation=continuation)
         n = p.n
         if A_out is None:
             if p.location == DEVICE:

@@ -118,6 +118,34 @@ def test_one_level_matches_oracle(ctx, mctx, gen, n, m, lam, seed):
     _compare(Am, A_ref, S, lam, infom["objective"], info_ref["objective"], MIXED_OBJ_RTOL)
 
 
+@pytest.mark.parametrize("one_level", [True, False])
+@pytest.mark.parametrize("gen,n,m,lam,seed", [CASES[0], CASES[2]])
+def test_continuation_matches_oracle(ctx, mctx, gen, n, m, lam, seed, one_level):
+    """The continuation strategy (Sections 2 and 8: one relaxation at each of
+    lambda_4 > lambda_3 > lambda_2 before the cycles at lambda) against the
+    oracle's run of the same schedule: the FP64 path makes the same
+    relaxations and sees the same largest support (up to pairs on the lambda
+    borders), and both paths reach the oracle's minimiser."""
+    p = synth.random_problem(n, m, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    lams = oracle.continuation_lambdas(S, lam)
+    assert lams.size == 3
+    A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-11, one_level=one_level, continuation=True)
+    assert info_ref["status"] == 0
+    A, _, info = ctx.solve(S, lam, tol=1e-11, one_level=one_level, continuation=True)
+    assert info["status"] == 0, info
+    _compare(A, A_ref, S, lam, info["objective"], info_ref["objective"])
+    assert info["relaxations"] == info_ref["relaxations"]
+    assert info["cycles"] == info_ref["cycles"]
+    W = np.linalg.inv(A_ref)
+    G = np.abs(S - W)
+    border = sum(int(np.count_nonzero(np.abs(G - l) <= 1e-7)) for l in [lam, *lams])
+    assert abs(info["max_nnz"] - info_ref["max_nnz"]) <= border
+    Am, _, infom = mctx.solve(S, lam, tol=1e-11, one_level=one_level, continuation=True)
+    assert infom["status"] == 0, infom
+    _compare(Am, A_ref, S, lam, infom["objective"], info_ref["objective"], MIXED_OBJ_RTOL)
+
+
 def test_config1_from_samples_on_device(ctx):
     import torch
 

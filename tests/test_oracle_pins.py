@@ -502,3 +502,69 @@ def test_one_level_reaches_the_same_minimiser(gen, n, lam, seed):
     for info in (i_ml, i_1):
         assert info["max_nnz"] >= info["nnz"] == np.count_nonzero(A_ml)
 
+
+
+def test_continuation_lambdas_hand_derived():
+    """Section 8's continuation values: lambda_4 halfway between lambda and the
+    largest off-diagonal |S_ij| (the smallest lambda with a diagonal minimiser;
+    1 on normalised data, where the paper's lambda_4 = (1 + lambda) / 2), then
+    lambda_3, lambda_2 evenly spaced down to lambda.  Hand values: the largest
+    off-diagonal entry is -0.7 (the diagonal, larger still, does not count),
+    so lambda = 0.1 gives 0.4, 0.3, 0.2."""
+    S = np.array([[3.0, 0.2, -0.7], [0.2, 2.0, 0.5], [-0.7, 0.5, 4.0]])
+    np.testing.assert_allclose(oracle.continuation_lambdas(S, 0.1), [0.4, 0.3, 0.2], rtol=1e-15)
+    # no stages once the solution at lambda is diagonal
+    assert oracle.continuation_lambdas(S, 0.7).size == 0
+    assert oracle.continuation_lambdas(np.diag([1.0, 2.0]), 0.05).size == 0
+    # normalised data: never above the paper's (1 + lambda) / 2
+    X = np.random.default_rng(3).standard_normal((40, 12))
+    Sn = np.corrcoef(X, rowvar=False)
+    lam = 0.05
+    l4 = oracle.continuation_lambdas(Sn, lam)[0]
+    assert lam < l4 <= 0.5 * (1.0 + lam)
+
+
+def test_continuation_is_one_relaxation_per_stage():
+    """The continuation stages are one level-0 relaxation at each lambda_s in
+    decreasing order, each from the previous iterate: with no cycles at the
+    target lambda the solve must return exactly what three single-relaxation
+    one-level solves at lambda_4, lambda_3, lambda_2 chained from A0 return,
+    and each stage's recorded objective is F(A_s) at its own lambda_s
+    (library slogdet)."""
+    p = synth.random_problem(50, 100, 0.1, 51, gen="sparse")
+    S = oracle.form_S(p.X)
+    lams = oracle.continuation_lambdas(S, p.lam)
+    assert lams.size == 3 and np.all(np.diff(lams) < 0) and lams[-1] > p.lam
+    A0 = np.diag(1.0 / (np.diag(S) + p.lam))
+    A_c, _, info, tr = oracle.solve(S, p.lam, tol=0.0, max_cycles=0, A0=A0, continuation=True,
+                                    trace_cap=10)
+    assert info["cycles"] == 0 and info["relaxations"] == 3 and tr.shape[0] == 3
+    A = A0
+    for s, ls in enumerate(lams):
+        A, _, inf1, _ = oracle.solve(S, ls, tol=0.0, max_cycles=1, A0=A, one_level=True)
+        assert inf1["relaxations"] == 1
+        sign, ld = np.linalg.slogdet(A)
+        assert sign > 0
+        F = -ld + np.sum(S * A) + ls * np.abs(A).sum()
+        assert abs(tr[s, 0] - F) <= 1e-11 * abs(F) and tr[s, 1] == 0
+    assert np.array_equal(A_c, A)
+
+
+@pytest.mark.parametrize("one_level", [False, True])
+def test_continuation_reaches_the_same_minimiser(one_level):
+    """Continuation changes the path, not the minimiser (the objective at the
+    target lambda is strictly convex): with the ML-cycle or the one-level
+    method after the stages, the result is the ML-cycle's; the three stage
+    relaxations come first, on the finest level."""
+    p = synth.random_problem(60, 120, 0.1, 41, gen="sparse")
+    S = oracle.form_S(p.X)
+    A_ml, _, i_ml, _ = oracle.solve(S, p.lam, tol=1e-11)
+    A_c, _, i_c, tr = oracle.solve(S, p.lam, tol=1e-11, one_level=one_level, continuation=True,
+                                   trace_cap=200)
+    assert i_c["status"] == 0
+    assert np.abs(A_c - A_ml).max() <= 1e-7
+    assert abs(i_c["objective"] - i_ml["objective"]) <= 1e-10 * abs(i_ml["objective"])
+    assert np.all(tr[:3, 1] == 0)
+    if one_level:
+        assert i_c["relaxations"] in (3 + i_c["cycles"], 3 + i_c["cycles"] - 1)
+    assert i_c["max_nnz"] >= i_c["nnz"] == np.count_nonzero(A_ml)
