@@ -78,6 +78,8 @@ def lib():
                                 C.POINTER(Info), _d, C.c_int64, C.c_int, C.c_int]
         L.orc_solve.restype = C.c_int
         L.orc_continuation_lambdas.argtypes = [_d, C.c_int64, C.c_double, _d]
+        L.orc_components.argtypes = [_d, C.c_int64, C.c_double, C.POINTER(C.c_int32)]
+        L.orc_components.restype = C.c_int64
         L.orc_continuation_lambdas.restype = C.c_int
         _lib = L
     return _lib
@@ -209,6 +211,15 @@ def continuation_lambdas(S, lam):
     out = np.zeros(3)
     k = lib().orc_continuation_lambdas(_p(S), S.shape[0], lam, _p(out))
     return out[:k].copy()
+
+
+def components(S, lam):
+    """Screening: labels of the connected components of {|S_ij| > lam, i != j}
+    (each vertex's component's smallest vertex) and their number."""
+    S = _f64(S)
+    comp = np.empty(S.shape[0], dtype=np.int32)
+    k = lib().orc_components(_p(S), S.shape[0], lam, comp.ctypes.data_as(C.POINTER(C.c_int32)))
+    return comp, int(k)
 
 
 def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=False,

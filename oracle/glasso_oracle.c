@@ -571,5 +571,40 @@ done:
     return status;
 }
 
+/* Screening: connected components of the graph with an edge (i, j), i != j,
+ * wherever |S_ij| > lambda.  The minimiser is block diagonal over them and
+ * each block is the minimiser of the problem on its sub-matrix of S (if A is
+ * assembled from the blocks' minimisers, W = A^{-1} is block diagonal, and a
+ * pair across blocks has A_ij = 0 and |G_ij| = |S_ij| <= lambda: the
+ * zero-entry condition of eq. subgradient1; the minimiser is unique).
+ * comp[i] = the smallest vertex of i's component, found by breadth-first
+ * search from each unlabelled vertex in ascending order.  Returns the number
+ * of components.                                                             */
+int64_t orc_components(const double *S, int64_t n, double lam, int32_t *comp) {
+    int32_t *queue = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int64_t ncomp = 0;
+    for (int64_t i = 0; i < n; ++i) comp[i] = -1;
+    for (int64_t r = 0; r < n; ++r) {
+        if (comp[r] >= 0) continue;
+        ++ncomp;
+        int64_t head = 0, tail = 0;
+        comp[r] = (int32_t)r;
+        queue[tail++] = (int32_t)r;
+        while (head < tail) {
+            const int64_t v = queue[head++];
+            for (int64_t u = 0; u < n; ++u) {
+                if (u == v || comp[u] >= 0) continue;
+                const double s = v < u ? S[v * n + u] : S[u * n + v];  /* upper triangle */
+                if (fabs(s) > lam) {
+                    comp[u] = (int32_t)r;
+                    queue[tail++] = (int32_t)u;
+                }
+            }
+        }
+    }
+    free(queue);
+    return ncomp;
+}
+
 /* Relaxation count of trace entries written (for callers sizing buffers). */
 int64_t orc_max_pairs(int64_t n) { return n * (n + 1) / 2; }

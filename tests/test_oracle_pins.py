@@ -568,3 +568,78 @@ def test_continuation_reaches_the_same_minimiser(one_level):
     if one_level:
         assert i_c["relaxations"] in (3 + i_c["cycles"], 3 + i_c["cycles"] - 1)
     assert i_c["max_nnz"] >= i_c["nnz"] == np.count_nonzero(A_ml)
+
+
+def _library_components(S, lam):
+    """Component labels by scipy's graph routine, renamed to each component's
+    smallest vertex."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    G = np.abs(np.triu(S, 1)) > lam
+    k, lab = connected_components(csr_matrix(G | G.T), directed=False)
+    first = {}
+    for i, c in enumerate(lab):
+        first.setdefault(c, i)
+    return np.array([first[c] for c in lab], dtype=np.int32), k
+
+
+def _screen_cases():
+    rng = np.random.default_rng(61)
+    out = []
+    for gen, n, lam in (("sparse", 120, 0.2), ("sparse", 120, 0.1), ("sparse", 200, 0.3),
+                        ("tridiag", 80, 0.2), ("tridiag", 80, 0.6)):
+        p = synth.random_problem(n, 2 * n, lam, 71, gen=gen)
+        out.append((oracle.form_S(p.X), lam))
+    # hand-built blocks {0, 3, 5}, {1, 4}, {2}, {6} under a permutation-free layout
+    S = np.eye(7) * 2.0
+    for i, j, v in ((0, 3, 0.5), (3, 5, -0.4), (1, 4, 0.3), (2, 6, 0.05), (0, 6, -0.1)):
+        S[i, j] = S[j, i] = v
+    out.append((S, 0.2))
+    out.append((np.array([[1.5]]), 0.1))
+    X = rng.standard_normal((30, 25))
+    out.append((X.T @ X / 30, 1e-6))  # every pair an edge: one component
+    return out
+
+
+def test_components_match_library():
+    """Component labels (smallest vertex of each component) equal scipy's
+    connected components of the thresholded graph; the hand-built case has
+    components {0, 3, 5}, {1, 4}, {2}, {6} (0.05 and -0.1 are below lambda)."""
+    for S, lam in _screen_cases():
+        comp, k = oracle.components(S, lam)
+        ref, kr = _library_components(S, lam)
+        assert k == kr and np.array_equal(comp, ref)
+    S, lam = _screen_cases()[5]
+    comp, k = oracle.components(S, lam)
+    assert k == 4 and comp.tolist() == [0, 1, 2, 0, 1, 0, 6]
+
+
+def test_screening_theorem_blocks_solve_separately():
+    """The minimiser is block diagonal over the components, each block the
+    minimiser on its own sub-matrix, an isolated vertex 1/(S_ii + lambda); and
+    solving all non-isolated vertices as one sub-problem (the GPU's screened
+    solve) gives the same matrix."""
+    p = synth.random_problem(90, 180, 0.2, 72, gen="sparse")
+    S = oracle.form_S(p.X)
+    lam = p.lam
+    comp, k = oracle.components(S, lam)
+    sizes = np.bincount(comp, minlength=S.shape[0])
+    assert 3 <= k < S.shape[0] and (sizes >= 2).sum() >= 2  # several non-trivial blocks
+    A_full, _, info, _ = oracle.solve(S, lam, tol=1e-12)
+    assert info["status"] == 0
+    A_blk = np.zeros_like(S)
+    for r in np.unique(comp):
+        idx = np.flatnonzero(comp == r)
+        if idx.size == 1:
+            A_blk[idx[0], idx[0]] = 1.0 / (S[idx[0], idx[0]] + lam)
+        else:
+            Ab, *_ = oracle.solve(S[np.ix_(idx, idx)], lam, tol=1e-12)
+            A_blk[np.ix_(idx, idx)] = Ab
+    assert np.abs(A_blk - A_full).max() <= 1e-8
+    iso = sizes[comp] == 1
+    idx = np.flatnonzero(~iso)
+    A_uni = np.diag(np.where(iso, 1.0 / (np.diag(S) + lam), 0.0))
+    Au, *_ = oracle.solve(S[np.ix_(idx, idx)], lam, tol=1e-12)
+    A_uni[np.ix_(idx, idx)] = Au
+    assert np.abs(A_uni - A_full).max() <= 1e-8
