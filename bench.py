@@ -235,7 +235,8 @@ def run_batched(args):
         plist, outs = [], []
         for p in ps:
             for lam in synth.LAMBDA_PATH:
-                plist.append(glasso.Context.problem(p.X, lam, 1e-5, samples=True))
+                plist.append(glasso.Context.problem(p.X, lam, 1e-5, samples=True,
+                                                    screen=args.screen))
                 outs.append(np.empty((p.n, p.n)))
         return plist, outs
 
@@ -254,7 +255,7 @@ def run_batched(args):
         "config": {"workload": f"{args.instances} instances, n ~ U[32, 512], m = 2n, "
                                f"tridiagonal/sparse alternating, lambda path {list(synth.LAMBDA_PATH)} "
                                f"warm started, tol 1e-5, samples X (fp64) on the host",
-                   "solves": len(plist), "wall_s": dt},
+                   "screen": bool(args.screen), "solves": len(plist), "wall_s": dt},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                        "mean": float(per.mean())},
         "failed": int(sum(1 for i in infos if i["status"] != 0)),
@@ -363,6 +364,8 @@ def main():
                     help="solve: the n=2000 single-solve metric (default); batched: lambda paths "
                          "of many small instances; serving: a Poisson request stream")
     ap.add_argument("--instances", type=int, default=512, help="batched: instances")
+    ap.add_argument("--screen", action="store_true",
+                    help="batched: exact screening (isolated vertices in closed form)")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests of the trace")
     ap.add_argument("--rate", type=float, default=60.0,
                     help="serving: arrivals per second (60: the device loaded, not saturated)")
@@ -489,6 +492,24 @@ def main():
                         "cycles": linfo["cycles"], "max_supp": linfo["max_nnz"], "nnz": linfo["nnz"],
                         "objective": linfo["objective"]}
         compare["levels"] = lv
+        # exact screening on the same input: isolated vertices of {|S_ij| > lambda}
+        # in closed form, the other vertices as one sub-problem (same minimiser)
+        sinfo = None
+        for _ in range(2):
+            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, screen=True)
+        slat = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, screen=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            slat.append(e0.elapsed_time(e1))
+        compare["screened"] = {"ms_per_solve": float(np.mean(slat)), "components": sinfo["components"],
+                               "max_block": sinfo["max_block"], "relaxations": sinfo["relaxations"],
+                               "nnz": sinfo["nnz"], "objective": sinfo["objective"]}
 
     # end to end through the public API with host buffers (pinned): S in, A out
     Sh = S.cpu().pin_memory().numpy()

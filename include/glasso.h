@@ -77,6 +77,12 @@ typedef struct {
                          (max_{i!=j} |S_ij| + lambda)/2 (no stages when that maximum is <= lambda).
                          These relaxations count in `relaxations` and `max_nnz`, not in `cycles`;
                          max_cycles bounds the cycles at lambda.  Combines with either method. */
+    int screen;       /* nonzero: exact screening.  The minimiser is block diagonal over the connected
+                         components of {(i,j): i != j, |S_ij| > lambda}; isolated vertices get the closed
+                         form A_ii = 1/(S_ii + lambda), and the remaining vertices are solved as one
+                         sub-problem (the method never couples two components: their pairs never enter
+                         the free set).  Same minimiser; the statistics are the sub-problem's plus the
+                         isolated vertices' (objective, log det, nnz). */
 } glasso_problem;
 
 typedef struct {
@@ -92,6 +98,8 @@ typedef struct {
     int64_t nnz;         /* nonzeros of A (both triangles) */
     int64_t max_nnz;     /* largest nnz(A) at the fine-level free-set scans and at return (the
                             paper's max-supp, sampled where the full free set is formed) */
+    int64_t components;  /* screen: connected components of {|S_ij| > lambda}; 0 without screening */
+    int64_t max_block;   /* screen: vertices in the largest component; 0 without screening */
 } glasso_info;
 
 /* ---- context -------------------------------------------------------- */
@@ -257,6 +265,16 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
                                  int64_t n, double lambda, const int32_t *pi, const int32_t *pj,
                                  int64_t np, const double *D, double F_A, double sigma,
                                  int max_trials, double *F_new, double *alpha, int *trials);
+
+/* Screening: connected components of the graph {(i, j): i != j, |S_ij| > lambda}
+ * on S (n x n, device, symmetric; only the upper triangle is read).
+ * comp (device, n int32) receives for each vertex the smallest vertex of its
+ * component (so labels are independent of the order of discovery); *ncomp
+ * (host, may be NULL) the number of components.  Lock-free union-find; a
+ * retry bound that the algorithm cannot reach is checked and reported as
+ * GLASSO_ECUDA. */
+glasso_status glasso_components(glasso_ctx *ctx, const double *S, int64_t n, double lambda,
+                                int32_t *comp, int64_t *ncomp);
 
 /* F(A) = -log det A + tr(S A) + lambda ||A||_1 (eq. MLE_l1_prior); *info as
  * glasso_potrf (F undefined when *info != 0). */

@@ -57,7 +57,7 @@ bool trace_on() {
     return on;
 }
 
-size_t footprint(int64_t n, int64_t m, int xbytes) {
+size_t footprint(int64_t n, int64_t m, int xbytes, bool screen = false) {
     const size_t nn = (size_t)n * (size_t)n;
     const size_t pairs = (size_t)n * (size_t)(n + 1) / 2;
     size_t b = 6 * nn * sizeof(double);                           // S A L T W U
@@ -68,6 +68,7 @@ size_t footprint(int64_t n, int64_t m, int xbytes) {
     b += nn * (sizeof(int32_t) + sizeof(double));  // CSR of A (mixed precision)
     b += nn * sizeof(double);                      // CD interaction matrices (at most)
     b += (size_t)4 * n * ((n + 31) / 32 * 32) * sizeof(float);  // tensor-core factorisation planes
+    if (screen) b += 4 * nn * sizeof(double) + (size_t)n * (4 * sizeof(int32_t) + sizeof(double));
     return b + (4u << 20);
 }
 
@@ -117,6 +118,10 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.csr_ptr, st); dfree(w.csr_col, st); dfree(w.csr_val, st); dfree(w.part, st);
     dfree(w.Wp, st); dfree(w.Qp, st); dfree(w.U2p, st); dfree(w.U3p, st); dfree(w.Xt, st);
     w.cap_mixed = w.cap_part = w.cap_xt = 0;
+    dfree(w.scr_S, st); dfree(w.scr_A, st); dfree(w.scr_W, st); dfree(w.scr_A0, st);
+    dfree(w.scr_diag, st); dfree(w.cc_parent, st); dfree(w.cc_size, st); dfree(w.cc_comp, st);
+    dfree(w.scr_idx, st);
+    w.cap_scr = w.cap_cc = 0;
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
     if (w.ev_a) cudaEventDestroy(w.ev_a);
@@ -156,6 +161,27 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
     CK(dalloc(w.ldiag, n, st));
     w.cap_n = n;
     w.cap_pairs = pairs;
+    return GLASSO_OK;
+}
+
+// Screening buffers: full-size copies of S, A, W and A0 (the sub-problem
+// occupies S .. U), the component labels and the sub-problem's vertex list.
+glasso_status work_ensure_labels(Work &w, int64_t n, cudaStream_t st, std::string &err) {
+    if (n <= w.cap_cc) return GLASSO_OK;
+    CK(dalloc(w.scr_diag, n, st));
+    CK(dalloc(w.cc_parent, n, st)); CK(dalloc(w.cc_size, n, st));
+    CK(dalloc(w.cc_comp, n, st)); CK(dalloc(w.scr_idx, n, st));
+    w.cap_cc = n;
+    return GLASSO_OK;
+}
+
+glasso_status work_ensure_screen(Work &w, int64_t n, cudaStream_t st, std::string &err) {
+    glasso_status s = work_ensure_labels(w, n, st, err);
+    if (s != GLASSO_OK || n <= w.cap_scr) return s;
+    const size_t nn = (size_t)n * (size_t)n;
+    CK(dalloc(w.scr_S, nn, st)); CK(dalloc(w.scr_A, nn, st));
+    CK(dalloc(w.scr_W, nn, st)); CK(dalloc(w.scr_A0, nn, st));
+    w.cap_scr = n;
     return GLASSO_OK;
 }
 
@@ -304,6 +330,11 @@ void prof_collect(Prof *prof) {
     prof->pend_work.clear();
 }
 
+// Sums a caller combining several solves needs beyond glasso_info.
+struct CoreSums {
+    double l1 = 0.0;  // ||A||_1 at return
+};
+
 // The continuation's stage values (end of Section 2; the schedule of
 // Section 8): lambda_4 halfway between lambda and lambda_max = max_{i != j}
 // |S_ij| (the smallest lambda whose minimiser is diagonal; at most 1 on the
@@ -323,7 +354,7 @@ int continuation_lambdas(unsigned long long smax_bits, double lam, double out[3]
 // w.A and its inverse in w.W when W is requested (want_W).
 glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
                          bool have_A0, bool want_W, bool one_level, bool continuation,
-                         glasso_info *info) {
+                         glasso_info *info, CoreSums *sums = nullptr) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -492,6 +523,7 @@ done:
     }
     max_nnz = std::max(max_nnz, nnz);
     (void)want_W;
+    if (sums) sums->l1 = l1;
     if (info) {
         info->status = status;
         info->cycles = cycles;
@@ -523,7 +555,8 @@ done:
 //    otherwise an FP32 Cholesky (FP64 diagonal blocks and log accumulation)
 //    whose log-det error is taken as n 2^-20.
 glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, int max_cycles,
-                               bool have_A0, bool one_level, bool continuation, glasso_info *info) {
+                               bool have_A0, bool one_level, bool continuation, glasso_info *info,
+                               CoreSums *sums = nullptr) {
     Work &w = sv.w;
     cudaStream_t st = sv.st;
     std::string &err = sv.err;
@@ -845,6 +878,7 @@ done:
         maxkkt = h->kkt_max;
     }
     max_nnz = std::max(max_nnz, nnz);
+    if (sums) sums->l1 = l1;
     if (info) {
         info->status = status;
         info->cycles = cycles;
@@ -932,6 +966,119 @@ glasso_status validate(const glasso_problem *p) {
     return GLASSO_OK;
 }
 
+glasso_status solve_one(Solver &sv, int64_t n, const glasso_problem *p, int mc, bool warm,
+                        bool want_W, glasso_info *info, CoreSums *sums) {
+    return sv.precision == GLASSO_MIXED
+               ? solve_core_mixed(sv, n, p->lambda, p->tol, mc, warm, p->one_level != 0,
+                                  p->continuation != 0, info, sums)
+               : solve_core(sv, n, p->lambda, p->tol, mc, warm, want_W, p->one_level != 0,
+                            p->continuation != 0, info, sums);
+}
+
+// Exact screening (screen.cu): the isolated vertices of {|S_ij| > lambda} in
+// closed form, every other vertex in one sub-problem on the principal
+// sub-matrix of S (and of A0), solved like any problem and scattered back.
+// The non-isolated components stay together: the relaxation never couples
+// two components (A starts and stays block diagonal, so W does too, and a
+// pair across components has A_ij = 0 and |G_ij| = |S_ij| <= lambda, so it
+// never enters the free set).  Solving them together therefore reaches the
+// same minimiser and pays the fixed cost of one solve, not one per component.
+glasso_status solve_screened(Solver &sv, const glasso_problem *p, int mc, bool warm, bool want_W,
+                             glasso_info *info) {
+    Work &w = sv.w;
+    cudaStream_t st = sv.st;
+    std::string &err = sv.err;
+    const int64_t n = p->n;
+    const double lam = p->lambda;
+    const size_t bytes = (size_t)n * (size_t)n * sizeof(double);
+    glasso_status s = work_ensure_screen(w, n, st, err);
+    if (s != GLASSO_OK) return s;
+    CK(cudaMemcpyAsync(w.scr_S, w.S, bytes, cudaMemcpyDeviceToDevice, st));
+    if (warm) CK(cudaMemcpyAsync(w.scr_A0, w.A, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w.scr_A, 0, bytes, st));
+    if (want_W) CK(cudaMemsetAsync(w.scr_W, 0, bytes, st));
+    CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), st));
+    CK(components(w.scr_S, n, lam, w.cc_parent, w.cc_comp, w.cc_size, &w.sc->cc_err, st));
+    CK(screen_diag(w.scr_S, n, lam, w.cc_comp, w.cc_size, w.scr_A, want_W ? w.scr_W : nullptr,
+                   w.scr_diag, &w.sc->err, st));
+    std::vector<int32_t> comp((size_t)n);
+    std::vector<double> diag((size_t)n);
+    CK(cudaMemcpyAsync(comp.data(), w.cc_comp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(diag.data(), w.scr_diag, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
+    if (w.sc_host->cc_err) {
+        err = "component labelling: a retry bound was exceeded";
+        return GLASSO_ECUDA;
+    }
+    if (w.sc_host->err) return GLASSO_ENOTPD;
+    // component sizes (a label is its component's smallest vertex)
+    std::vector<int64_t> size((size_t)n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t r = comp[i];
+        if (r < 0 || r > i) {
+            err = "component labelling: invalid label";
+            return GLASSO_ECUDA;
+        }
+        ++size[r];
+    }
+    int64_t ncomp = 0, max_block = 0;
+    for (int64_t r = 0; r < n; ++r)
+        if (size[r]) {
+            ++ncomp;
+            max_block = std::max(max_block, size[r]);
+        }
+    // isolated vertices: F, log det and ||A||_1 of A_ii = 1/(S_ii + lambda), in
+    // index order; the other vertices, ascending, form the sub-problem
+    std::vector<int32_t> idx;
+    idx.reserve((size_t)n);
+    double F = 0.0, logdet = 0.0, l1 = 0.0;
+    int64_t n_iso = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (size[comp[i]] == 1) {
+            const double d = diag[i] + lam;
+            F += log(d) + 1.0;  // -log(1/d) + (S_ii + lambda)/d
+            logdet -= log(d);
+            l1 += 1.0 / d;
+            ++n_iso;
+        } else {
+            idx.push_back((int32_t)i);
+        }
+    }
+    const int64_t nb = (int64_t)idx.size();
+    glasso_info sub;
+    memset(&sub, 0, sizeof(sub));
+    sub.status = GLASSO_OK;
+    double kkt_sum = 0.0;
+    if (nb > 0) {
+        CoreSums cs;
+        CK(cudaMemcpyAsync(w.scr_idx, idx.data(), (size_t)nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        CK(gather_block(w.scr_S, n, w.scr_idx, nb, w.S, st));
+        if (warm) CK(gather_block(w.scr_A0, n, w.scr_idx, nb, w.A, st));
+        s = solve_one(sv, nb, p, mc, warm, want_W, &sub, &cs);
+        if (s == GLASSO_ECUDA || s == GLASSO_ENOTPD) return s;
+        CK(scatter_block(w.A, nb, w.scr_idx, n, w.scr_A, st));
+        if (want_W) CK(scatter_block(w.W, nb, w.scr_idx, n, w.scr_W, st));
+        F += sub.objective;
+        logdet += sub.logdet;
+        kkt_sum = sub.rel_kkt * cs.l1;  // the isolated vertices are exact: no residual
+        l1 += cs.l1;
+    }
+    CK(cudaMemcpyAsync(w.A, w.scr_A, bytes, cudaMemcpyDeviceToDevice, st));
+    if (want_W) CK(cudaMemcpyAsync(w.W, w.scr_W, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w.S, w.scr_S, bytes, cudaMemcpyDeviceToDevice, st));
+    if (info) {
+        *info = sub;
+        info->objective = F;
+        info->logdet = logdet;
+        info->rel_kkt = l1 > 0.0 ? kkt_sum / l1 : 0.0;
+        info->nnz = sub.nnz + n_iso;
+        info->max_nnz = sub.max_nnz + n_iso;
+        info->components = ncomp;
+        info->max_block = max_block;
+    }
+    return (glasso_status)sub.status;
+}
+
 glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_problem *p,
                        double *A_out, double *W_out, glasso_info *info, std::string &err,
                        Prof *prof, bool reuse_A, int out_location, int precision) {
@@ -942,7 +1089,7 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
     if (s == GLASSO_OK && !A_out) s = GLASSO_EINVAL;
     if (s == GLASSO_OK && budget) {
         const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
-        if (footprint(p->n, m, p->dtype == GLASSO_F32 ? 4 : 8) > budget) s = GLASSO_ENOMEM;
+        if (footprint(p->n, m, p->dtype == GLASSO_F32 ? 4 : 8, p->screen != 0) > budget) s = GLASSO_ENOMEM;
     }
     if (s == GLASSO_OK) {
         glasso_problem q = *p;
@@ -953,12 +1100,8 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
         Solver sv{w, st, err, prof, precision};
         const int mc = p->max_cycles > 0 ? p->max_cycles : 200;
         const bool warm = p->A0 != nullptr || reuse_A;
-        s = precision == GLASSO_MIXED
-                ? solve_core_mixed(sv, p->n, p->lambda, p->tol, mc, warm, p->one_level != 0,
-                                   p->continuation != 0, &loc)
-                : solve_core(sv, p->n, p->lambda, p->tol, mc, warm, W_out != nullptr, p->one_level != 0,
-                             p->continuation != 0,
-                             &loc);
+        s = p->screen ? solve_screened(sv, p, mc, warm, W_out != nullptr, &loc)
+                      : solve_one(sv, p->n, p, mc, warm, W_out != nullptr, &loc, nullptr);
         if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
             const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost
                                                                     : cudaMemcpyDeviceToDevice;
@@ -1107,7 +1250,9 @@ glasso_status submit_chain(glasso_ctx *ctx, const glasso_problem *p, int count, 
     }
     const int64_t m = p->input == GLASSO_INPUT_X ? p->m : 0;
     const int xb = p->dtype == GLASSO_F32 ? 4 : 8;
-    const size_t fp = footprint(p->n, m, xb);
+    bool screen = false;
+    for (int k = 0; k < count; ++k) screen = screen || p[k].screen != 0;
+    const size_t fp = footprint(p->n, m, xb, screen);
     if (ctx->budget && fp > ctx->budget) return GLASSO_ENOMEM;
     Request *r = new Request();
     r->p = *p;
@@ -1609,6 +1754,32 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
     if (trials) *trials = max_trials;
     if (alpha) *alpha = 0.0;
     return GLASSO_ELINESEARCH;
+}
+
+glasso_status glasso_components(glasso_ctx *ctx, const double *S, int64_t n, double lambda,
+                                int32_t *comp, int64_t *ncomp) {
+    if (!ctx || !S || !comp || n < 1 || n > 46340 || !finite_pos(lambda)) return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    glasso_status s = work_ensure(w, 1, st, ctx->last_error);  // the device scalars
+    if (s == GLASSO_OK) s = work_ensure_labels(w, n, st, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    CTX_CK(cudaMemsetAsync(&w.sc->cc_err, 0, sizeof(int), st));
+    CTX_CK(components(S, n, lambda, w.cc_parent, comp, w.cc_size, &w.sc->cc_err, st));
+    std::vector<int> size;
+    if (ncomp) {
+        size.resize((size_t)n);
+        CTX_CK(cudaMemcpyAsync(size.data(), w.cc_size, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    if (w.sc_host->cc_err) {
+        ctx->last_error = "component labelling: a retry bound was exceeded";
+        return GLASSO_ECUDA;
+    }
+    if (ncomp) *ncomp = (int64_t)std::count_if(size.begin(), size.end(), [](int c) { return c > 0; });
+    return GLASSO_OK;
 }
 
 glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A, int64_t n,

@@ -92,7 +92,7 @@ struct DevScalars {
     unsigned bar_count;
     unsigned bar_gen;
     int bar_err;
-    int pad3;
+    int cc_err;           // component labelling: a retry bound was exceeded
     unsigned long long smax_bits;  // max_{i != j} |S_ij| as the bits of a non-negative double
 };
 
@@ -146,6 +146,13 @@ struct Work {
     // GEMMs (created on first use)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    // screening: the full S, A, W and A0 while a sub-problem occupies S .. U,
+    // the component labels and the sub-problem's vertex list
+    int64_t cap_scr = 0, cap_cc = 0;
+    double *scr_S = nullptr, *scr_A = nullptr, *scr_W = nullptr, *scr_A0 = nullptr;
+    double *scr_diag = nullptr;
+    int *cc_parent = nullptr, *cc_size = nullptr;
+    int32_t *cc_comp = nullptr, *scr_idx = nullptr;
 };
 
 }  // namespace glx
@@ -196,6 +203,22 @@ cudaError_t init_diag(const double *S, int64_t n, double lam, double *A, DevScal
                       cudaStream_t st);
 // sc->smax_bits = the bits of max_{i < j} |S_ij| (0 for n = 1)
 cudaError_t offdiag_absmax(const double *S, int64_t n, DevScalars *sc, cudaStream_t st);
+
+// ---- screening (screen.cu) ----
+// Connected components of {(i, j): i != j, |S_ij| > lambda}: comp[i] = the
+// smallest vertex of i's component, csize[r] = the size of the component
+// whose smallest vertex is r (0 elsewhere).  parent, csize: n ints of scratch.
+cudaError_t components(const double *S, int64_t n, double lam, int *parent, int32_t *comp,
+                       int *csize, int *err, cudaStream_t st);
+// For each isolated vertex i: A_ii = 1/(S_ii + lambda) and W_ii = S_ii + lambda
+// (W may be NULL); diag[i] = S_ii for every i; *err = 1 if some S_ii + lambda <= 0.
+cudaError_t screen_diag(const double *S, int64_t n, double lam, const int32_t *comp, const int *csize,
+                        double *A, double *W, double *diag, int *err, cudaStream_t st);
+// dst (nb x nb) = src[idx, idx] and back; idx holds nb distinct indices < n.
+cudaError_t gather_block(const double *src, int64_t n, const int32_t *idx, int64_t nb, double *dst,
+                         cudaStream_t st);
+cudaError_t scatter_block(const double *src, int64_t nb, const int32_t *idx, int64_t n, double *dst,
+                          cudaStream_t st);
 // per-pair data for the CD sweep
 cudaError_t pair_prep(const double *S, const double *W, const double *A, int64_t n, double lam,
                       const int32_t *pi, const int32_t *pj, int64_t np, double *inva, double *g,

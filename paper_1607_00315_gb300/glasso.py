@@ -40,14 +40,16 @@ class Problem(C.Structure):
     _fields_ = [("input", C.c_int), ("dtype", C.c_int), ("location", C.c_int),
                 ("data", C.c_void_p), ("n", C.c_int64), ("m", C.c_int64), ("center", C.c_int),
                 ("lambda_", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
-                ("A0", C.c_void_p), ("one_level", C.c_int), ("continuation", C.c_int)]
+                ("A0", C.c_void_p), ("one_level", C.c_int), ("continuation", C.c_int),
+                ("screen", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("relaxations", C.c_int),
                 ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
                 ("max_kkt", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
-                ("nnz", C.c_int64), ("max_nnz", C.c_int64)]
+                ("nnz", C.c_int64), ("max_nnz", C.c_int64), ("components", C.c_int64),
+                ("max_block", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,13 +96,15 @@ def load():
     L.glasso_line_search.argtypes = [vp, vp, vp, vp, i64, d, vp, vp, i64, vp, d, d, i32,
                                      C.POINTER(d), C.POINTER(d), C.POINTER(i32)]
     L.glasso_objective.argtypes = [vp, vp, vp, i64, d, C.POINTER(d), C.POINTER(i32)]
+    L.glasso_components.argtypes = [vp, vp, i64, d, vp, C.POINTER(i64)]
     L.glasso_free_set_noalloc.argtypes = [vp, vp, vp, i64, d, vp, vp, vp, C.POINTER(i64),
                                           C.POINTER(d), C.POINTER(d), vp]
     L.glasso_free_set_noalloc.restype = i32
     for name in ("glasso_create", "glasso_set_stream", "glasso_solve", "glasso_solve_batch",
                  "glasso_submit", "glasso_poll", "glasso_set_profiling", "glasso_get_profile",
                  "glasso_form_S", "glasso_potrf", "glasso_inverse", "glasso_free_set",
-                 "glasso_hierarchy", "glasso_cd_sweeps", "glasso_line_search", "glasso_objective"):
+                 "glasso_hierarchy", "glasso_cd_sweeps", "glasso_line_search", "glasso_objective",
+                 "glasso_components"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -172,7 +176,7 @@ class Context:
     # ---------------------------------------------------------------- solver
     @staticmethod
     def problem(data, lam, tol=1e-8, *, samples=False, m=None, n=None, center=False,
-                max_cycles=0, A0=None, one_level=False, continuation=False):
+                max_cycles=0, A0=None, one_level=False, continuation=False, screen=False):
         """Build a glasso_problem from a numpy array (host) or a torch CUDA tensor."""
         dev = hasattr(data, "data_ptr") and getattr(data, "is_cuda", False)
         if not dev and isinstance(data, np.ndarray) and not data.flags.c_contiguous:
@@ -187,17 +191,18 @@ class Context:
         p = Problem(INPUT_X if samples else INPUT_S, dt, DEVICE if dev else HOST, _ptr(data),
                     nn if n is None else n, mm if m is None else m, int(center), float(lam),
                     float(tol), int(max_cycles), _ptr(A0), int(bool(one_level)),
-                    int(bool(continuation)))
+                    int(bool(continuation)), int(bool(screen)))
         return p
 
     def solve(self, data, lam, tol=1e-8, *, samples=False, center=False, max_cycles=0, A0=None,
               A_out=None, W_out=None, want_W=False, check=True, one_level=False,
-              continuation=False):
+              continuation=False, screen=False):
         """glasso_solve (one_level: the paper's one-level comparison method;
-        continuation: the paper's continuation stages before the cycles).
+        continuation: the paper's continuation stages before the cycles;
+        screen: isolated vertices in closed form, the rest as one sub-problem).
         Returns (A, W or None, info dict)."""
         p = self.problem(data, lam, tol, samples=samples, center=center, max_cycles=max_cycles,
-                         A0=A0, one_level=one_level, continuation=continuation)
+                         A0=A0, one_level=one_level, continuation=continuation, screen=screen)
         n = p.n
         if A_out is None:
             if p.location == DEVICE:
@@ -286,6 +291,15 @@ class Context:
                                       C.byref(Fn), C.byref(al), C.byref(tr))
         return s, Fn.value, al.value, tr.value
 
+    def components(self, S, lam, comp):
+        """glasso_components: comp (device int32, n) receives the smallest
+        vertex of each vertex's component of {|S_ij| > lam}; returns the
+        number of components."""
+        k = C.c_int64(0)
+        self._check(self.L.glasso_components(self.h, _ptr(S), S.shape[0], lam, _ptr(comp), C.byref(k)),
+                    "components")
+        return k.value
+
     def objective(self, S, A, lam):
         F, info = C.c_double(0.0), C.c_int(0)
         self._check(self.L.glasso_objective(self.h, _ptr(S), _ptr(A), A.shape[0], lam, C.byref(F),
@@ -313,5 +327,5 @@ EXPORTED = (
     "glasso_last_error", "glasso_solve", "glasso_solve_batch", "glasso_submit", "glasso_poll",
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
-    "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc",
+    "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
 )
