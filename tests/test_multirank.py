@@ -123,3 +123,26 @@ def test_batched_job_value_two_gloo_ranks():
     for rank, max_s, total, value in res:
         assert max_s == 2.5 and total == 512
         assert value == pytest.approx(512 / 2.5)
+
+
+def test_route_stream_properties():
+    """Online routing of a serving stream: deterministic, covers every
+    request, sends each request to a rank whose assigned work before it was
+    the least, and keeps the final loads within one request's cost of each
+    other."""
+    import numpy as np
+
+    from paper_1607_00315_gb300 import shard, synth
+
+    trace = synth.serving_trace(300)
+    costs = [shard.unit_cost(r[1]) for r in trace]
+    for world in (1, 2, 4, 8):
+        own = shard.route_stream(costs, world)
+        assert own == shard.route_stream(costs, world)
+        assert len(own) == len(costs) and set(own) <= set(range(world))
+        load = np.zeros(world)
+        for c, r in zip(costs, own):
+            assert load[r] == load.min()
+            load[r] += c
+        assert load.max() - load.min() <= max(costs) + 1e-9
+    assert shard.route_stream([], 2) == []
