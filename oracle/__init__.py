@@ -79,6 +79,12 @@ def lib():
         L.orc_solve.restype = C.c_int
         L.orc_continuation_lambdas.argtypes = [_d, C.c_int64, C.c_double, _d]
         L.orc_components.argtypes = [_d, C.c_int64, C.c_double, C.POINTER(C.c_int32)]
+        L.orc_pcd_direction.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64,
+                                        _d, _d, _d, _d]
+        L.orc_pcd_direction.restype = None
+        L.orc_pcd.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64, C.c_int,
+                              C.c_int, _d, _d]
+        L.orc_pcd.restype = C.c_int
         L.orc_components.restype = C.c_int64
         L.orc_continuation_lambdas.restype = C.c_int
         _lib = L
@@ -185,6 +191,36 @@ def cd_sweeps(S, W, A, lam, pi, pj, nsweeps, D=None, U=None):
     lib().orc_cd_sweeps(_p(S), _p(W), _p(A), n, lam, _p(pi, _i32), _p(pj, _i32), len(pi),
                         nsweeps, _p(D), _p(U))
     return D, U
+
+
+def pcd_direction(S, W, A, lam, pi, pj, D=None, U=None):
+    """The PCD direction d (every coordinate's 1-D minimiser at once) and
+    b = G + W Delta W on the pairs, at Delta = D (U = Delta W)."""
+    S, W, A = _f64(S), _f64(W), _f64(A)
+    n = A.shape[0]
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    D = np.zeros(len(pi)) if D is None else _f64(D)
+    U = np.zeros((n, n)) if U is None else _f64(U)
+    d = np.zeros(len(pi))
+    b = np.zeros(len(pi))
+    lib().orc_pcd_direction(_p(S), _p(W), _p(A), n, lam, _p(pi, _i32), _p(pj, _i32), len(pi),
+                            _p(D), _p(U), _p(d), _p(b))
+    return d, b
+
+
+def pcd(S, W, A, lam, pi, pj, iters, cg=True, D=None, U=None):
+    """PCD (cg=False) or PCD-CG iterations with exact steps on the Newton
+    LASSO; returns (Delta on pairs, U = Delta W, iterations taken)."""
+    S, W, A = _f64(S), _f64(W), _f64(A)
+    n = A.shape[0]
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    D = np.zeros(len(pi)) if D is None else _f64(D).copy()
+    U = np.zeros((n, n)) if U is None else _f64(U).copy()
+    k = lib().orc_pcd(_p(S), _p(W), _p(A), n, lam, _p(pi, _i32), _p(pj, _i32), len(pi), iters,
+                      1 if cg else 0, _p(D), _p(U))
+    return D, U, k
 
 
 def line_search(S, W, A, lam, pi, pj, D, F0, sigma=1e-4, beta=0.5, max_trials=30):

@@ -304,6 +304,206 @@ void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n,
 }
 
 /* ---------------------------------------------------------------------- */
+/* PCD and PCD-CG for the same Newton LASSO (the Jacobi-parallel alternative
+ * to the CD sweep; the paper's inner solver of Section 6.3).
+ *
+ * Direction (Section 2, eq. IST_direction with D = diag of the Hessian, the
+ * generalised parallel coordinate descent): every coordinate's own 1-D
+ * minimiser at the current Delta, all taken at once,
+ *     d_p = S_{lambda/a_p}(c_p - b_p/a_p) - c_p
+ * with a, b, c as in the CD sweep above.
+ * Step (eq. Line-search): the exact minimiser t >= 0 of the model along the
+ * search direction.  Along Delta + t P the model changes by
+ *     phi(t) = t g1 + t^2 g2 / 2 + lambda sum_p w_p (|c_p + t P_p| - |c_p|),
+ *     g1 = sum_p w_p b_p P_p,  g2 = sum_p w_p P_p (W P W)_p,
+ * w_p = 2 off the diagonal and 1 on it (a pair stands for two entries); phi
+ * is a convex quadratic plus a piecewise-linear term, so its minimiser is
+ * found by walking the kinks t = -c_p / P_p > 0 in increasing order.  When
+ * the minimiser is a kink, the coordinates of that kink get exact zeros
+ * (Delta_p = -A_p), as the CD sweep does for a zero of the shrinkage.
+ * READING (zero snap): a coordinate whose own minimiser is zero (the
+ * shrinkage returned 0, so d_p = -c_p) approaches zero only geometrically
+ * when the step is shorter than its kink, and once its value lies below the
+ * resolution of the update (Delta_p + t P_p rounds to Delta_p) it freezes at
+ * a nonzero residue whose sign keeps pulling the other coordinates; plain PCD
+ * then stalls.  Such a coordinate is set to its limit, the exact zero.
+ * Acceleration by non-linear conjugate gradients (PCD-CG, Section 6.3).
+ * READING (the paper defers the details to its references): the search
+ * direction is P_k = d_k + beta_k P_{k-1} with the Polak-Ribiere-plus
+ * coefficient beta_k = max(0, <d_k, d_k - d_{k-1}> / <d_{k-1}, d_{k-1}>) in
+ * the w-weighted pair inner product; P_k = d_k when the directional
+ * derivative phi'(0+) along P_k is not negative.  cg = 0: plain PCD.
+ * Stops after `iters` iterations or when d = 0 (the LASSO minimiser).
+ * D holds Delta on the pair list (in/out); U = Delta W (n x n, in/out) is
+ * updated with the exact increments.  Returns the iterations taken.         */
+
+/* (W X W)_p on the pairs for the symmetric X given on the pairs: V = X W
+ * (row updates), then the dot of row i of W with column j of V.  V: n x n. */
+static void pair_wxw(const double *W, int64_t n, const int32_t *pi, const int32_t *pj,
+                     int64_t np, const double *x, double *V, double *out) {
+    memset(V, 0, (size_t)(n * n) * sizeof(double));
+    for (int64_t p = 0; p < np; ++p) {
+        const int64_t i = pi[p], j = pj[p];
+        if (x[p] == 0.0) continue;
+        for (int64_t k = 0; k < n; ++k) V[i * n + k] += x[p] * W[j * n + k];
+        if (i != j)
+            for (int64_t k = 0; k < n; ++k) V[j * n + k] += x[p] * W[i * n + k];
+    }
+    for (int64_t p = 0; p < np; ++p) {
+        const int64_t i = pi[p], j = pj[p];
+        double s = 0.0;
+        for (int64_t k = 0; k < n; ++k) s += W[i * n + k] * V[k * n + j];
+        out[p] = s;
+    }
+}
+
+/* The PCD direction at the current Delta (D, U = Delta W): d_p as above and
+ * b_p = G_p + (W Delta W)_p. */
+void orc_pcd_direction(const double *S, const double *W, const double *A, int64_t n, double lam,
+                       const int32_t *pi, const int32_t *pj, int64_t np, const double *D,
+                       const double *U, double *d, double *b) {
+    for (int64_t p = 0; p < np; ++p) {
+        const int64_t i = pi[p], j = pj[p];
+        const double wij = W[i * n + j];
+        const double a = (i == j) ? wij * wij : wij * wij + W[i * n + i] * W[j * n + j];
+        double wdw = 0.0;
+        for (int64_t k = 0; k < n; ++k) wdw += W[i * n + k] * U[k * n + j];
+        b[p] = (S[i * n + j] - wij) + wdw;
+        const double c = A[i * n + j] + D[p];
+        d[p] = soft(c - b[p] / a, lam / a) - c;
+    }
+}
+
+typedef struct {
+    double t;
+    int64_t p;
+} kink;
+
+static int cmp_kink(const void *x, const void *y) {
+    const kink *a = (const kink *)x, *b = (const kink *)y;
+    if (a->t < b->t) return -1;
+    if (a->t > b->t) return 1;
+    return (a->p > b->p) - (a->p < b->p);
+}
+
+/* Exact minimiser t >= 0 of phi (above); *at_kink = the kink value when the
+ * minimiser is one (else -1). */
+static double exact_step(const double *c, const double *P, const double *w, int64_t np, double lam,
+                         double g1, double g2, kink *ks, double *at_kink) {
+    *at_kink = -1.0;
+    double h = 0.0; /* lambda sum w P s, s = the sign just right of t */
+    int64_t nk = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        if (P[p] == 0.0) continue;
+        const double s = c[p] != 0.0 ? sgn(c[p]) : sgn(P[p]);
+        h += lam * w[p] * P[p] * s;
+        if (c[p] != 0.0 && sgn(c[p]) != sgn(P[p])) {
+            ks[nk].t = -c[p] / P[p];
+            ks[nk].p = p;
+            ++nk;
+        }
+    }
+    if (!(g2 > 0.0) || g1 + h >= 0.0) return 0.0;
+    qsort(ks, (size_t)nk, sizeof(kink), cmp_kink);
+    int64_t k = 0;
+    while (k < nk) {
+        const double tk = ks[k].t;
+        const double tstar = -(g1 + h) / g2;
+        if (tstar <= tk) return tstar;
+        /* crossing the kink(s) at tk: each sign flips from -sign(P) to sign(P) */
+        double jump = 0.0;
+        int64_t k2 = k;
+        while (k2 < nk && ks[k2].t == tk) {
+            jump += 2.0 * lam * w[ks[k2].p] * fabs(P[ks[k2].p]);
+            ++k2;
+        }
+        if (g1 + g2 * tk + h + jump >= 0.0) {
+            *at_kink = tk;
+            return tk;
+        }
+        h += jump;
+        k = k2;
+    }
+    return -(g1 + h) / g2;
+}
+
+int orc_pcd(const double *S, const double *W, const double *A, int64_t n, double lam,
+            const int32_t *pi, const int32_t *pj, int64_t np, int iters, int cg, double *D,
+            double *U) {
+    const size_t m = (size_t)(np > 0 ? np : 1);
+    double *d = (double *)malloc(m * sizeof(double));
+    double *dprev = (double *)malloc(m * sizeof(double));
+    double *P = (double *)calloc(m, sizeof(double)); /* the previous direction: none yet */
+    double *b = (double *)malloc(m * sizeof(double));
+    double *c = (double *)malloc(m * sizeof(double));
+    double *w = (double *)malloc(m * sizeof(double));
+    double *wpw = (double *)malloc(m * sizeof(double));
+    unsigned char *zt = (unsigned char *)malloc(m);
+    kink *ks = (kink *)malloc(m * sizeof(kink));
+    double *V = (double *)malloc((size_t)(n * n) * sizeof(double));
+    int it = 0;
+    for (int64_t p = 0; p < np; ++p) w[p] = pi[p] == pj[p] ? 1.0 : 2.0;
+    for (; it < iters; ++it) {
+        orc_pcd_direction(S, W, A, n, lam, pi, pj, np, D, U, d, b);
+        int any = 0;
+        for (int64_t p = 0; p < np; ++p) any |= d[p] != 0.0;
+        if (!any) break;
+        double beta = 0.0;
+        if (cg && it > 0) {
+            double num = 0.0, den = 0.0;
+            for (int64_t p = 0; p < np; ++p) {
+                num += w[p] * d[p] * (d[p] - dprev[p]);
+                den += w[p] * dprev[p] * dprev[p];
+            }
+            beta = den > 0.0 ? fmax(0.0, num / den) : 0.0;
+        }
+        for (int64_t p = 0; p < np; ++p) {
+            P[p] = d[p] + beta * P[p];
+            c[p] = A[pi[p] * n + pj[p]] + D[p];
+            zt[p] = c[p] + d[p] == 0.0; /* the coordinate's own minimiser is zero */
+        }
+        double g1 = 0.0;
+        for (int64_t p = 0; p < np; ++p) g1 += w[p] * b[p] * P[p];
+        if (beta != 0.0) {
+            /* a descent direction or back to the PCD direction */
+            double h = 0.0;
+            for (int64_t p = 0; p < np; ++p)
+                if (P[p] != 0.0) h += lam * w[p] * P[p] * (c[p] != 0.0 ? sgn(c[p]) : sgn(P[p]));
+            if (g1 + h >= 0.0) {
+                for (int64_t p = 0; p < np; ++p) P[p] = d[p];
+                g1 = 0.0;
+                for (int64_t p = 0; p < np; ++p) g1 += w[p] * b[p] * P[p];
+            }
+        }
+        pair_wxw(W, n, pi, pj, np, P, V, wpw);
+        double g2 = 0.0;
+        for (int64_t p = 0; p < np; ++p) g2 += w[p] * P[p] * wpw[p];
+        double kinkt;
+        const double t = exact_step(c, P, w, np, lam, g1, g2, ks, &kinkt);
+        for (int64_t p = 0; p < np; ++p) dprev[p] = d[p];
+        if (t == 0.0) break;
+        for (int64_t p = 0; p < np; ++p) {
+            if (P[p] == 0.0) continue;
+            const int64_t i = pi[p], j = pj[p];
+            double nd;
+            if (kinkt >= 0.0 && c[p] != 0.0 && -c[p] / P[p] == kinkt && sgn(c[p]) != sgn(P[p]))
+                nd = -A[i * n + j]; /* lands on the kink: an exact zero */
+            else
+                nd = D[p] + t * P[p];
+            if (zt[p] && c[p] != 0.0 && nd == D[p]) nd = -A[i * n + j]; /* zero snap */
+            const double inc = nd - D[p];
+            D[p] = nd;
+            if (inc == 0.0) continue;
+            for (int64_t k = 0; k < n; ++k) U[i * n + k] += inc * W[j * n + k];
+            if (i != j)
+                for (int64_t k = 0; k < n; ++k) U[j * n + k] += inc * W[i * n + k];
+        }
+    }
+    free(d); free(dprev); free(P); free(b); free(c); free(w); free(wpw); free(zt); free(ks); free(V);
+    return it;
+}
+
+/* ---------------------------------------------------------------------- */
 /* a7. Armijo backtracking line search (Section 2 eq. Line-search; Section
  * 6.1.2 uses alpha_0 = 1, beta = 1/2 and positive definiteness).
  * READING: accept the first alpha = beta^t (t = 0..max_trials-1) for which

@@ -643,3 +643,115 @@ def test_screening_theorem_blocks_solve_separately():
     Au, *_ = oracle.solve(S[np.ix_(idx, idx)], lam, tol=1e-12)
     A_uni[np.ix_(idx, idx)] = Au
     assert np.abs(A_uni - A_full).max() <= 1e-8
+
+
+def _coupled_lasso(n=14, lam=0.06, seed=11):
+    """A Newton LASSO whose Hessian couples the coordinates: the iterate after
+    one ML-cycle (off-diagonal support), its inverse and its free set."""
+    S = _S(n, 30, seed)
+    A, *_ = oracle.solve(S, lam, tol=1e-2, max_cycles=1)
+    assert np.count_nonzero(A - np.diag(np.diag(A))) > 0
+    W = np.linalg.inv(A)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    return S, A, W, fi, fj, lam
+
+
+def test_pcd_direction_is_each_coordinates_1d_minimiser():
+    """Section 2's PCD direction (eq. IST_direction with the Hessian's
+    diagonal): each component is that coordinate's own exact minimiser of the
+    dense Newton LASSO model (library matmul) with every other coordinate
+    held, at a Delta that is not zero."""
+    from scipy.optimize import minimize_scalar
+
+    S, A, W, fi, fj, lam = _coupled_lasso()
+    n = A.shape[0]
+    D0, U0 = oracle.cd_sweeps(S, W, A, lam, fi, fj, 1)
+    d, _ = oracle.pcd_direction(S, W, A, lam, fi, fj, D0, U0)
+    G = S - W
+    base = _dense(n, fi, fj, D0)
+    for p in range(len(fi)):
+        E = _dense(n, [fi[p]], [fj[p]], [1.0])
+        f = lambda mu: _model(G, W, A, base + mu * E, lam)  # noqa: E731
+        r = minimize_scalar(f, bounds=(d[p] - 1.0, d[p] + 1.0), method="bounded",
+                            options={"xatol": 1e-12})
+        assert f(d[p]) <= f(r.x) + 1e-13
+        assert abs(r.x - d[p]) <= 1e-6
+
+
+def test_pcd_step_is_the_exact_minimiser_along_the_direction():
+    """One PCD iteration moves Delta by t d with t the exact minimiser of the
+    dense model along d (library matmul, bounded scalar search and a grid)."""
+    from scipy.optimize import minimize_scalar
+
+    S, A, W, fi, fj, lam = _coupled_lasso()
+    n = A.shape[0]
+    D0, U0 = oracle.cd_sweeps(S, W, A, lam, fi, fj, 1)
+    d, _ = oracle.pcd_direction(S, W, A, lam, fi, fj, D0, U0)
+    D1, U1, k = oracle.pcd(S, W, A, lam, fi, fj, 1, cg=False, D=D0, U=U0)
+    assert k == 1
+    G = S - W
+    step = D1 - D0
+    t = step[np.argmax(np.abs(d))] / d[np.argmax(np.abs(d))]
+    assert t > 0
+    # every coordinate moved by the same multiple of d (or landed on an exact zero)
+    T1 = A[fi, fj] + D1
+    ok = np.isclose(step, t * d, rtol=1e-9, atol=1e-15) | (T1 == 0.0)
+    assert ok.all()
+    f = lambda s: _model(G, W, A, _dense(n, fi, fj, D0 + s * d), lam)  # noqa: E731
+    r = minimize_scalar(f, bounds=(0.0, 4.0 * t), method="bounded", options={"xatol": 1e-13})
+    assert f(t) <= f(r.x) + 1e-13
+    assert all(f(t) <= f(s) + 1e-13 for s in np.linspace(0.0, 3.0 * t, 301))
+    assert np.allclose(U1, _dense(n, fi, fj, D1) @ W, atol=1e-13)
+
+
+@pytest.mark.parametrize("cg", [False, True])
+def test_pcd_decreases_the_model_and_solves_the_lasso(cg):
+    """PCD and PCD-CG decrease the model at every iteration and reach the
+    restricted Newton LASSO's KKT point, the same minimiser the CD sweeps
+    reach; U stays Delta W (library matmul)."""
+    S, A, W, fi, fj, lam = _coupled_lasso()
+    n = A.shape[0]
+    G = S - W
+    prev = _model(G, W, A, np.zeros((n, n)), lam)
+    for k in range(1, 16):
+        Dk, _, _ = oracle.pcd(S, W, A, lam, fi, fj, k, cg=cg)
+        cur = _model(G, W, A, _dense(n, fi, fj, Dk), lam)
+        assert cur <= prev + 1e-13
+        prev = cur
+    D, U, _ = oracle.pcd(S, W, A, lam, fi, fj, 2000, cg=cg)
+    Dm = _dense(n, fi, fj, D)
+    assert np.allclose(U, Dm @ W, atol=1e-12)
+    R = G + W @ Dm @ W
+    T = A + Dm
+    for i, j in zip(fi, fj):
+        if T[i, j] != 0:
+            assert abs(R[i, j] + lam * np.sign(T[i, j])) < 1e-9
+        else:
+            assert abs(R[i, j]) <= lam + 1e-9
+    Dc, _ = oracle.cd_sweeps(S, W, A, lam, fi, fj, 2000)
+    assert np.abs(D - Dc).max() <= 1e-10
+    # the minimiser's zeros are exact (kinks and the zero snap), as CD's are
+    assert np.array_equal(A[fi, fj] + D == 0, A[fi, fj] + Dc == 0)
+
+
+def test_pcd_cg_needs_fewer_iterations_than_pcd():
+    """The conjugate-gradient acceleration (Section 6.3's PCD-CG) brings the
+    PCD direction below 1e-10 in fewer iterations than plain PCD on a coupled
+    problem."""
+    S, A, W, fi, fj, lam = _coupled_lasso()
+
+    def below(D, U, tol):
+        d, _ = oracle.pcd_direction(S, W, A, lam, fi, fj, D, U)
+        return np.abs(d).max() <= tol
+
+    # plain PCD keeps no state between iterations: continue one at a time
+    D, U, k_pcd = None, None, 0
+    while k_pcd < 3000:
+        D, U, _ = oracle.pcd(S, W, A, lam, fi, fj, 1, cg=False, D=D, U=U)
+        k_pcd += 1
+        if below(D, U, 1e-10):
+            break
+    # PCD-CG carries its previous direction: rerun from the start
+    k_cg = next(k for k in range(1, 3001)
+                if below(*oracle.pcd(S, W, A, lam, fi, fj, k, cg=True)[:2], 1e-10))
+    assert k_cg < k_pcd < 3000
