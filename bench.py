@@ -68,7 +68,9 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to BENCH_CLOCKS_DIR (default: bench_clocks/ beside this file)
+        out = os.environ.get("BENCH_CLOCKS_DIR", os.path.join(ROOT, "bench_clocks"))
+        self.path = os.path.join(out, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
