@@ -75,7 +75,7 @@ def lib():
                                       C.POINTER(C.c_int)]
         L.orc_line_search.restype = C.c_int
         L.orc_solve.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d, _d,
-                                C.POINTER(Info), _d, C.c_int64, C.c_int, C.c_int]
+                                C.POINTER(Info), _d, C.c_int64, C.c_int, C.c_int, C.c_int]
         L.orc_solve.restype = C.c_int
         L.orc_continuation_lambdas.argtypes = [_d, C.c_int64, C.c_double, _d]
         L.orc_components.argtypes = [_d, C.c_int64, C.c_double, C.POINTER(C.c_int32)]
@@ -83,7 +83,7 @@ def lib():
                                         _d, _d, _d, _d]
         L.orc_pcd_direction.restype = None
         L.orc_pcd.argtypes = [_d, _d, _d, C.c_int64, C.c_double, _i32, _i32, C.c_int64, C.c_int,
-                              C.c_int, _d, _d]
+                              C.c_int, C.c_double, _d, _d]
         L.orc_pcd.restype = C.c_int
         L.orc_components.restype = C.c_int64
         L.orc_continuation_lambdas.restype = C.c_int
@@ -209,9 +209,10 @@ def pcd_direction(S, W, A, lam, pi, pj, D=None, U=None):
     return d, b
 
 
-def pcd(S, W, A, lam, pi, pj, iters, cg=True, D=None, U=None):
+def pcd(S, W, A, lam, pi, pj, iters, cg=True, D=None, U=None, rtol=0.0):
     """PCD (cg=False) or PCD-CG iterations with exact steps on the Newton
-    LASSO; returns (Delta on pairs, U = Delta W, iterations taken)."""
+    LASSO (rtol > 0: stop once the direction fell by that factor); returns
+    (Delta on pairs, U = Delta W, iterations taken)."""
     S, W, A = _f64(S), _f64(W), _f64(A)
     n = A.shape[0]
     pi = np.ascontiguousarray(pi, dtype=np.int32)
@@ -219,7 +220,7 @@ def pcd(S, W, A, lam, pi, pj, iters, cg=True, D=None, U=None):
     D = np.zeros(len(pi)) if D is None else _f64(D).copy()
     U = np.zeros((n, n)) if U is None else _f64(U).copy()
     k = lib().orc_pcd(_p(S), _p(W), _p(A), n, lam, _p(pi, _i32), _p(pj, _i32), len(pi), iters,
-                      1 if cg else 0, _p(D), _p(U))
+                      1 if cg else 0, rtol, _p(D), _p(U))
     return D, U, k
 
 
@@ -259,12 +260,15 @@ def components(S, lam):
 
 
 def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=False,
-          continuation=False):
+          continuation=False, inner="cd"):
     """a8: the full ML-cycle solve (one_level: the paper's one-level
     comparison, the full free set every cycle; continuation: one relaxation
     at each continuation_lambdas value first).  Returns (A, W, info dict,
     trace array); info["max_nnz"] is the largest nnz(A) at the fine-level
-    scans and at return."""
+    scans and at return.  inner: "cd" (CD sweeps) or "pcd_cg" (PCD-CG to the
+    relative precision 1e-4) for the Newton direction."""
+    if inner not in ("cd", "pcd_cg"):
+        raise ValueError("inner must be 'cd' or 'pcd_cg'")
     S = _f64(S)
     n = S.shape[0]
     A = np.empty((n, n))
@@ -274,6 +278,6 @@ def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=Fals
     a0 = None if A0 is None else _f64(A0)
     lib().orc_solve(_p(S), n, lam, tol, max_cycles, None if a0 is None else _p(a0),
                     _p(A), _p(W), C.byref(info), _p(tr), trace_cap, 1 if one_level else 0,
-                    1 if continuation else 0)
+                    1 if continuation else 0, 1 if inner == "pcd_cg" else 0)
     d = {k: getattr(info, k) for k, _ in Info._fields_}
     return A, W, d, tr[: info.ntrace].copy()

@@ -333,7 +333,10 @@ void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n,
  * coefficient beta_k = max(0, <d_k, d_k - d_{k-1}> / <d_{k-1}, d_{k-1}>) in
  * the w-weighted pair inner product; P_k = d_k when the directional
  * derivative phi'(0+) along P_k is not negative.  cg = 0: plain PCD.
- * Stops after `iters` iterations or when d = 0 (the LASSO minimiser).
+ * Stops after `iters` iterations, when d = 0 (the LASSO minimiser), or, for
+ * rtol > 0, once max|d| <= rtol * max|d| of the first iteration (Section 8
+ * runs PCD-CG "up to a relative precision of 1e-4"; READING: precision
+ * measured by the PCD direction, which vanishes exactly at the minimiser).
  * D holds Delta on the pair list (in/out); U = Delta W (n x n, in/out) is
  * updated with the exact increments.  Returns the iterations taken.         */
 
@@ -428,8 +431,8 @@ static double exact_step(const double *c, const double *P, const double *w, int6
 }
 
 int orc_pcd(const double *S, const double *W, const double *A, int64_t n, double lam,
-            const int32_t *pi, const int32_t *pj, int64_t np, int iters, int cg, double *D,
-            double *U) {
+            const int32_t *pi, const int32_t *pj, int64_t np, int iters, int cg, double rtol,
+            double *D, double *U) {
     const size_t m = (size_t)(np > 0 ? np : 1);
     double *d = (double *)malloc(m * sizeof(double));
     double *dprev = (double *)malloc(m * sizeof(double));
@@ -442,12 +445,15 @@ int orc_pcd(const double *S, const double *W, const double *A, int64_t n, double
     kink *ks = (kink *)malloc(m * sizeof(kink));
     double *V = (double *)malloc((size_t)(n * n) * sizeof(double));
     int it = 0;
+    double d0max = 0.0;
     for (int64_t p = 0; p < np; ++p) w[p] = pi[p] == pj[p] ? 1.0 : 2.0;
     for (; it < iters; ++it) {
         orc_pcd_direction(S, W, A, n, lam, pi, pj, np, D, U, d, b);
-        int any = 0;
-        for (int64_t p = 0; p < np; ++p) any |= d[p] != 0.0;
-        if (!any) break;
+        double dmax = 0.0;
+        for (int64_t p = 0; p < np; ++p) dmax = fmax(dmax, fabs(d[p]));
+        if (dmax == 0.0) break;
+        if (it == 0) d0max = dmax;
+        else if (rtol > 0.0 && dmax <= rtol * d0max) break;
         double beta = 0.0;
         if (cg && it > 0) {
             double num = 0.0, den = 0.0;
@@ -584,6 +590,10 @@ int orc_line_search(const double *S, const double *W, double *A, int64_t n, doub
  * count in `relaxations` and in max_nnz, not in `cycles`; max_cycles bounds
  * the cycles at lambda only.
  *
+ * inner = 0: the Newton direction by nsweeps CD sweeps (above); inner = 1: by
+ * PCD-CG (orc_pcd) to the relative precision 1e-4 of Section 8, at most
+ * 500 iterations.
+ *
  * trace (optional, capacity trace_cap): after every relaxation, the objective
  * (at the lambda that relaxation used) and the level, as (F, level) pairs.    */
 typedef struct {
@@ -632,7 +642,7 @@ int orc_continuation_lambdas(const double *S, int64_t n, double lam, double *out
 
 int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles,
               const double *A0, double *A, double *W_out, orc_info *info,
-              double *trace, int64_t trace_cap, int one_level, int continuation) {
+              double *trace, int64_t trace_cap, int one_level, int continuation, int inner) {
     if (n < 1 || !(lam > 0.0)) return ORC_EINVAL;
     size_t nn = (size_t)(n * n);
     double *L = (double *)malloc(nn * sizeof(double));
@@ -720,7 +730,10 @@ int orc_solve(const double *S, int64_t n, double lam, double tol, int max_cycles
             /* 4. Newton direction */
             memset(U, 0, nn * sizeof(double));
             memset(D, 0, (size_t)np * sizeof(double));
-            orc_cd_sweeps(S, W, A, n, lk, pi, pj, np, nsweeps, D, U);
+            if (inner == 1)
+                orc_pcd(S, W, A, n, lk, pi, pj, np, 500, 1, 1e-4, D, U);
+            else
+                orc_cd_sweeps(S, W, A, n, lk, pi, pj, np, nsweeps, D, U);
             int moved = 0;
             for (int64_t p = 0; p < np; ++p) moved |= (D[p] != 0.0);
             /* 5. line search */

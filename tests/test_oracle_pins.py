@@ -755,3 +755,26 @@ def test_pcd_cg_needs_fewer_iterations_than_pcd():
     k_cg = next(k for k in range(1, 3001)
                 if below(*oracle.pcd(S, W, A, lam, fi, fj, k, cg=True)[:2], 1e-10))
     assert k_cg < k_pcd < 3000
+
+
+@pytest.mark.parametrize("gen,n,lam,seed", [("sparse", 60, 0.1, 41), ("tridiag", 90, 0.15, 42)])
+def test_pcd_cg_inner_solver_reaches_the_same_minimiser(gen, n, lam, seed):
+    """The ML-cycle with PCD-CG (to Section 8's relative precision 1e-4) as
+    the Newton-direction solver minimises the same strictly convex objective:
+    it must reach the CD-based solve's minimiser, and the relative-precision
+    stop must end the inner iteration well before its cap."""
+    p = synth.random_problem(n, 2 * n, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    A_cd, _, i_cd, _ = oracle.solve(S, lam, tol=1e-11)
+    A_pc, _, i_pc, _ = oracle.solve(S, lam, tol=1e-11, inner="pcd_cg")
+    assert i_cd["status"] == 0 and i_pc["status"] == 0
+    assert np.abs(A_pc - A_cd).max() <= 1e-9
+    assert abs(i_pc["objective"] - i_cd["objective"]) <= 1e-12 * abs(i_cd["objective"])
+    # the relative stop: from a fresh Newton LASSO, far fewer than 500 iterations
+    A0 = np.diag(1.0 / (np.diag(S) + lam))
+    W0 = np.linalg.inv(A0)
+    fi, fj = oracle.free_set(S, W0, A0, lam)
+    _, _, k = oracle.pcd(S, W0, A0, lam, fi, fj, 500, cg=True, rtol=1e-4)
+    assert 1 <= k < 500
+    with pytest.raises(ValueError):
+        oracle.solve(S, lam, inner="newton")
