@@ -43,7 +43,9 @@ typedef enum {
     GLASSO_ELINESEARCH = 4,  /* no step length passed the line search */
     GLASSO_EMAXITER = 5,     /* tolerance not reached within max_cycles */
     GLASSO_EAGAIN = 6,       /* glasso_poll: not finished yet */
-    GLASSO_ETIMEOUT = 7,     /* a bounded device or host wait ran out */
+    GLASSO_ETIMEOUT = 7,     /* a bounded device wait ran out (a grid barrier of the CD sweep, or
+                                a tensor-core pipeline wait); the kernel returned early, the
+                                context stays usable, A_out is not written */
     GLASSO_ECUDA = 8         /* a CUDA runtime call failed */
 } glasso_status;
 
@@ -163,12 +165,28 @@ glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
  * 2 level-0 free-set scan, 3 CD sweeps, 4 line-search Cholesky trials,
  * 5 Newton-Schulz refinement GEMMs of W (mixed precision). */
 #define GLASSO_PROF_CLASSES 6
+
+/* Code-path counters (all contexts, counted always, since the last reset):
+ * which variant of a step the solves took. */
+#define GLASSO_PATHS 8
+enum {
+    GLASSO_PATH_CD_LAG2 = 0,       /* FP32 sweeps by the pipelined chain-CTA kernel */
+    GLASSO_PATH_CD_PERSIST32 = 1,  /* FP32 sweeps by the one-copy kernel (its matrices did not fit) */
+    GLASSO_PATH_CD_CHAIN64 = 2,    /* sweeps with an FP64 resolution chain */
+    GLASSO_PATH_LS_SERIES2 = 3,    /* mixed line-search trials decided by the two-term log-det series */
+    GLASSO_PATH_LS_SERIES6 = 4,    /* ... by the six-term series */
+    GLASSO_PATH_TC_FACTOR = 5,     /* tensor-core factorisations (line-search trials and fresh W) */
+    GLASSO_PATH_TC_LEAVES = 6,     /* diagonal leaves factored inside them */
+    GLASSO_PATH_NS_STEPS = 7       /* Newton-Schulz refinement GEMMs of W */
+};
+
 typedef struct {
     double ms[GLASSO_PROF_CLASSES];        /* summed device time */
     long long launches[GLASSO_PROF_CLASSES];
     double work[GLASSO_PROF_CLASSES];      /* algorithmic flops (0, 1, 4, 5) or bytes (2, 3) */
     long long kernels;                     /* kernels launched by the library (all contexts,
                                               counted always) since the last reset */
+    long long paths[GLASSO_PATHS];         /* GLASSO_PATH_* counters since the last reset */
 } glasso_profile;
 
 /* Turn event timing of the kernel classes on (on != 0) or off.  Off by
@@ -178,6 +196,26 @@ glasso_status glasso_set_profiling(glasso_ctx *ctx, int on);
 /* Copy the accumulated timings (and zero them when reset != 0).  The kernel
  * count is kept whether or not profiling is on. */
 glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset);
+
+/* ---- fault injection (tests of the error paths) ---------------------- */
+
+/* The paper has no counterpart: these knobs let tests drive the solver's
+ * failure paths without a GPU fault.  They act on the context's own solves
+ * and step-level calls (glasso_solve, glasso_cd_sweeps, glasso_line_search,
+ * ...), not on solves run through the serving slots (glasso_submit,
+ * glasso_solve_batch).  All are off (0) when the context is created. */
+enum {
+    GLASSO_DEBUG_WAIT_CYCLES = 1,      /* limit of each grid-barrier wait of the CD sweep in SM cycles
+                                          (0: the default, about 2 s); value >= 0 */
+    GLASSO_DEBUG_WAIT_UNREACHABLE = 2, /* nonzero: the CD sweep's grid barrier waits for one arrival more
+                                          than the grid holds, so every wait runs to its limit; the sweep
+                                          returns early and the call reports GLASSO_ETIMEOUT */
+    GLASSO_DEBUG_LS_REJECT = 3         /* nonzero: every line-search trial is rejected (Section 6.1.2's
+                                          backtracking runs out of trials: GLASSO_ELINESEARCH) */
+};
+
+/* Set one knob.  GLASSO_EINVAL for an unknown knob or a negative wait limit. */
+glasso_status glasso_set_debug(glasso_ctx *ctx, int knob, int64_t value);
 
 /* ---- step-level entry points (device pointers) ----------------------- */
 

@@ -335,8 +335,8 @@ void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n,
  * derivative phi'(0+) along P_k is not negative.  cg = 0: plain PCD.
  * Stops after `iters` iterations, when d = 0 (the LASSO minimiser), or, for
  * rtol > 0, once max|d| <= rtol * max|d| of the first iteration (Section 8
- * runs PCD-CG "up to a relative precision of 1e-4"; READING: precision
- * measured by the PCD direction, which vanishes exactly at the minimiser).
+ * stops its PCD-CG inner solves at relative precision 1e-4; READING: that
+ * precision is measured by the PCD direction, zero exactly at the minimiser).
  * D holds Delta on the pair list (in/out); U = Delta W (n x n, in/out) is
  * updated with the exact increments.  Returns the iterations taken.         */
 

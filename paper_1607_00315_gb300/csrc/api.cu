@@ -32,6 +32,7 @@ using namespace glx;
 
 namespace glx {
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_paths[GLASSO_PATHS];
 }
 
 namespace {
@@ -284,6 +285,7 @@ struct Prof {
     double work[GLASSO_PROF_CLASSES] = {0};
     std::vector<double> pend_work;
     long long kernels_base = 0;
+    long long paths_base[GLASSO_PATHS] = {0};
 };
 
 struct Solver {
@@ -464,7 +466,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->bar_err) {
                 err = "CD sweep: a bounded grid-barrier wait expired";
-                return GLASSO_ECUDA;
+                return GLASSO_ETIMEOUT;
             }
             if (!h->moved) continue;
             {
@@ -481,7 +483,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                     CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, sc, st));
                     if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                     ++lstrials;
-                    if (h->info == 0) {
+                    if (h->info == 0 && !w.dbg_ls_reject) {
                         ldT = h->logdet;
                         dl1 = h->dl1;
                         FT = -ldT + trSA + alpha * trSD + lk * (l1 + dl1);
@@ -602,7 +604,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
         if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
         if (h->tc_err) {
             err = "tensor-core factorisation: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
-            return GLASSO_ECUDA;
+            return GLASSO_ETIMEOUT;
         }
         return GLASSO_OK;
     };
@@ -628,7 +630,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->tc_err) {
                 err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h->tc_err) + ")";
-                return GLASSO_ECUDA;
+                return GLASSO_ETIMEOUT;
             }
             if (h->ns_max <= ns_tol) break;
             if (!(sqrt(h->ns_fro2) < 0.9)) {
@@ -643,6 +645,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             }
             sv.mark_begin(5, eb);
             CK(ns_gemm_tc(hcur, hnext, Wlo, R32, n, w.Wp, w.Qp, &sc->tc_err, st));
+            path_hit(GLASSO_PATH_NS_STEPS);
             sv.mark_end(5, eb, nd * nd * nd);
             std::swap(hcur, hnext);
         }
@@ -758,7 +761,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->bar_err) {
                 err = "CD sweep: a bounded grid-barrier wait expired";
-                return GLASSO_ECUDA;
+                return GLASSO_ETIMEOUT;
             }
             if (!h->moved) continue;
             {
@@ -793,7 +796,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                                 if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                                 if (h->tc_err) {
                                     err = "tensor-core GEMM: a bounded wait expired";
-                                    return GLASSO_ECUDA;
+                                    return GLASSO_ETIMEOUT;
                                 }
                                 t3 = h->t3; t4 = h->t4; t5 = h->t5; t6 = h->t6;
                                 high = true;
@@ -811,6 +814,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                         }
                     }
                     if (nterms > 0) {
+                        path_hit(nterms == 2 ? GLASSO_PATH_LS_SERIES2 : GLASSO_PATH_LS_SERIES6);
                         chol = false;
                         if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
                         const double a2 = alpha * alpha, a3 = a2 * alpha;
@@ -831,7 +835,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                         errb = 2.0 * e_chol;
                     }
                     ++lstrials;
-                    if (pd) {
+                    if (pd && !w.dbg_ls_reject) {
                         dl1 = h->dl1;
                         FT = F - dld + alpha * trSD + lk * dl1;
                         if (FT <= F + sigma * alpha * delta + errb + epsF) {
@@ -917,7 +921,7 @@ glasso_status form_S_ctx(Work &w, cudaStream_t st, int precision, const void *X,
         CK(cudaStreamSynchronize(st));
         if (w.sc_host->tc_err) {
             err = "tensor-core GEMM: a bounded wait expired (code " + std::to_string(w.sc_host->tc_err) + ")";
-            return GLASSO_ECUDA;
+            return GLASSO_ETIMEOUT;
         }
         return GLASSO_OK;
     }
@@ -1102,7 +1106,7 @@ glasso_status solve_in(Work &w, cudaStream_t st, size_t budget, const glasso_pro
         const bool warm = p->A0 != nullptr || reuse_A;
         s = p->screen ? solve_screened(sv, p, mc, warm, W_out != nullptr, &loc)
                       : solve_one(sv, p->n, p, mc, warm, W_out != nullptr, &loc, nullptr);
-        if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD) {
+        if (s != GLASSO_ECUDA && s != GLASSO_ENOTPD && s != GLASSO_ETIMEOUT) {
             const cudaMemcpyKind kind = out_location == GLASSO_HOST ? cudaMemcpyDeviceToHost
                                                                     : cudaMemcpyDeviceToDevice;
             const size_t bytes = (size_t)(p->n * p->n) * sizeof(double);
@@ -1400,7 +1404,26 @@ glasso_status glasso_get_profile(glasso_ctx *ctx, glasso_profile *out, int reset
     }
     out->kernels = g_launches.load() - p->kernels_base;
     if (reset) p->kernels_base = g_launches.load();
+    for (int k = 0; k < GLASSO_PATHS; ++k) {
+        const long long v = g_paths[k].load();
+        out->paths[k] = v - p->paths_base[k];
+        if (reset) p->paths_base[k] = v;
+    }
     return GLASSO_OK;
+}
+
+glasso_status glasso_set_debug(glasso_ctx *ctx, int knob, int64_t value) {
+    if (!ctx) return GLASSO_EINVAL;
+    Work &w = ctx->w;
+    switch (knob) {
+        case GLASSO_DEBUG_WAIT_CYCLES:
+            if (value < 0) return GLASSO_EINVAL;
+            w.dbg_wait_cycles = (long long)value;
+            return GLASSO_OK;
+        case GLASSO_DEBUG_WAIT_UNREACHABLE: w.dbg_wait_unreachable = value != 0; return GLASSO_OK;
+        case GLASSO_DEBUG_LS_REJECT: w.dbg_ls_reject = value != 0; return GLASSO_OK;
+        default: return GLASSO_EINVAL;
+    }
 }
 
 glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_out, double *W_out,
@@ -1599,7 +1622,7 @@ glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, 
     if (s != GLASSO_OK) return s;
     if (w.sc_host->tc_err) {
         ctx->last_error = "tensor-core factorisation: a bounded wait expired";
-        return GLASSO_ECUDA;
+        return GLASSO_ETIMEOUT;
     }
     if (info) *info = w.sc_host->info;
     if (logdet) *logdet = w.sc_host->logdet;
@@ -1612,7 +1635,7 @@ glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, 
         if (s != GLASSO_OK) return s;
         if (w.sc_host->tc_err) {
             ctx->last_error = "tensor-core GEMM: a bounded wait expired";
-            return GLASSO_ECUDA;
+            return GLASSO_ETIMEOUT;
         }
     }
     if (prof) prof_collect(prof);
@@ -1697,7 +1720,7 @@ glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W
     if (s != GLASSO_OK) return s;
     if (w.sc_host->bar_err) {
         ctx->last_error = "CD sweep: a bounded grid-barrier wait expired";
-        return GLASSO_ECUDA;
+        return GLASSO_ETIMEOUT;
     }
     return GLASSO_OK;
 }
@@ -1738,7 +1761,7 @@ glasso_status glasso_line_search(glasso_ctx *ctx, const double *S, const double 
         CTX_CK(ls_dl1(w.p_a, D, pi, pj, np, a, w, w.sc, st));
         s = sync_ctx(ctx);
         if (s != GLASSO_OK) return s;
-        if (w.sc_host->info == 0) {
+        if (w.sc_host->info == 0 && !w.dbg_ls_reject) {
             const double FT = F_A - (w.sc_host->logdet - ldA) + a * trSD + lambda * w.sc_host->dl1;
             if (FT <= F_A + sigma * a * delta + epsF) {
                 CTX_CK(ls_apply(A, n, pi, pj, w.p_a, D, np, a, st));

@@ -61,6 +61,14 @@ struct GridBar {
     int pad;
 };
 
+// Limit of every grid-barrier wait in SM cycles, and a number of arrivals the
+// barrier waits for beyond the grid (0 in normal operation; a test sets 1, so
+// that the wait runs to its limit and the error path is taken).
+struct WaitCfg {
+    long long cycles;
+    unsigned extra;
+};
+
 __device__ __forceinline__ void red_release_gpu(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -72,13 +80,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 
 // `epoch` counts the barriers this CTA has passed in the launch.  Arrival is a
 // release reduction (no round trip); the wait polls with acquire loads.
-__device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch) {
+__device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch, const WaitCfg &wc) {
     __shared__ int ok_s;
     __syncthreads();
     ++epoch;
     if (threadIdx.x == 0) {
         volatile int *verr = &gb->err;
-        const unsigned target = epoch * nblocks;
+        const unsigned target = epoch * nblocks + wc.extra;
         red_release_gpu(&gb->count, 1u);
         int ok = 1;
         const long long t0 = clock64();
@@ -86,7 +94,7 @@ __device__ bool grid_sync(GridBar *gb, unsigned nblocks, unsigned &epoch) {
         // one acquire load per poll; the error word (a CTA that gave up) is
         // read every 32 polls
         while ((int)(ld_acquire_gpu(&gb->count) - target) < 0) {
-            if ((++spins & 31u) == 0 && (*verr || clock64() - t0 > 4000000000ll)) {  // about 2 s
+            if ((++spins & 31u) == 0 && (*verr || clock64() - t0 > wc.cycles)) {
                 ok = 0;
                 atomicExch(&gb->err, 1);
                 break;
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
     const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
     const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
     double *__restrict__ D, int nsweeps, double *__restrict__ bvec, double *__restrict__ Kt,
-    CT *__restrict__ Kall, GridBar *gb) {
+    CT *__restrict__ Kall, GridBar *gb, WaitCfg wc) {
     extern __shared__ __align__(16) unsigned char ks_raw[];
     CT *Ks = reinterpret_cast<CT *>(ks_raw);  // Ks[s * CD_B + t]
     __shared__ CT bsh[CD_B], csh[CD_B], ish[CD_B], mush[CD_B];
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
             }
         }
         if (it == total) break;
-        if (!grid_sync(gb, G, epoch)) return;
+        if (!grid_sync(gb, G, epoch, wc)) return;
         if (blockIdx.x == 0 && prev_b0 >= 0)
             for (int t = tid; t < prev_nb; t += RT) D[prev_b0 + t] = dnew[t];
         const int64_t b0 = (it % nbatch) * CD_B;
@@ -339,7 +347,7 @@ __global__ void __launch_bounds__(RT, 1) k_cd_persist(
                 Ktc[s * CD_B + t] = (CT)v;
             }
         }
-        if (!grid_sync(gb, G, epoch)) {
+        if (!grid_sync(gb, G, epoch, wc)) {
             if (Kall && tid == 0) kcopy_wait(&kbar, kuse & 1u);  // the prefetch in flight
             return;
         }
@@ -565,7 +573,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     double lam, const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
     const double *__restrict__ inva, const double *__restrict__ g, const double *__restrict__ aval,
     double *__restrict__ D, int nsweeps, double *__restrict__ bvec, float *__restrict__ Kall,
-    int *__restrict__ lists, float *__restrict__ gmu, GridBar *gb) {
+    int *__restrict__ lists, float *__restrict__ gmu, GridBar *gb, WaitCfg wc) {
     extern __shared__ __align__(16) unsigned char ks_raw[];
     // intra matrices K[s][t] / a_t (s < t) of this pass and the next (by pass
     // parity), and the block p -> p + 1 matrix; the p - 1 -> p + 1 term is
@@ -832,7 +840,7 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
     };
     // prologue: dots of block 0 against copy 0 (both copies hold the initial U)
     dots(Ubuf0, 0, (int)lmin(CD_B, np), bvec, (int)blockIdx.x, (int)G);
-    if (!grid_sync(gb, G, epoch)) return;
+    if (!grid_sync(gb, G, epoch, wc)) return;
     if (cc && tid == 32) {  // the matrices are complete after the barrier
         kcopy_issue(KIb, KallI, KB, &kbarI[0]);
         pendI0 = 1;
@@ -1081,11 +1089,17 @@ __global__ void __launch_bounds__(LT, 1) k_cd_lag2(
             }
             if (!chain) break;
         }
-        if (!grid_sync(gb, G, epoch)) {
+        if (!grid_sync(gb, G, epoch, wc)) {
             drain();
             return;
         }
     }
+}
+
+// About 2 s of SM cycles unless a test has set a limit on the context.
+WaitCfg wait_cfg(const Work &w) {
+    return WaitCfg{w.dbg_wait_cycles > 0 ? w.dbg_wait_cycles : 4000000000ll,
+                   w.dbg_wait_unreachable ? 1u : 0u};
 }
 
 OncePerDevice g_lag_once;
@@ -1130,6 +1144,7 @@ static cudaError_t cd_sweeps_t(const T *W, int64_t n, double lam, const int32_t 
     GridBar *gb = reinterpret_cast<GridBar *>(&w.sc->bar_count);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
+    const WaitCfg wc = wait_cfg(w);
     // interaction matrices of all blocks, computed once per launch, while they
     // fit in n^2 doubles (else each block computes its own)
     const size_t kneed = (size_t)((np + CD_B - 1) / CD_B) * kbytes;
@@ -1152,10 +1167,12 @@ static cudaError_t cd_sweeps_t(const T *W, int64_t n, double lam, const int32_t 
     }
     void *args[] = {(void *)&W, (void *)&U, (void *)&n, (void *)&lam, (void *)&pi, (void *)&pj,
                     (void *)&np, (void *)&inva, (void *)&g, (void *)&aval, (void *)&D,
-                    (void *)&nsweeps, (void *)&bvec, (void *)&Kt, (void *)&Kall, (void *)&gb};
+                    (void *)&nsweeps, (void *)&bvec, (void *)&Kt, (void *)&Kall, (void *)&gb,
+                    (void *)&wc};
     e = cudaLaunchCooperativeKernel((const void *)k_cd_persist<T, CT>, dim3(G), dim3(RT), args,
                                     kbytes, st);
     counted(1);
+    path_hit(sizeof(CT) == 8 ? GLASSO_PATH_CD_CHAIN64 : GLASSO_PATH_CD_PERSIST32);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1197,6 +1214,7 @@ static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const in
     GridBar *gb = reinterpret_cast<GridBar *>(&w.sc->bar_count);
     cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
+    const WaitCfg wc = wait_cfg(w);
     // both copies start as the current U
     e = cudaMemcpyAsync(U2, U, (size_t)n * (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
@@ -1225,9 +1243,11 @@ static cudaError_t cd_sweeps_lag(const float *W, int64_t n, double lam, const in
     const int G = (int)lmax(4, lmin((int64_t)nsm * occ, (n + 7) / 8));
     void *args[] = {(void *)&W, (void *)&b0, (void *)&b1, (void *)&n, (void *)&lam, (void *)&pi,
                     (void *)&pj, (void *)&np, (void *)&inva, (void *)&g, (void *)&aval, (void *)&D,
-                    (void *)&nsweeps, (void *)&bvec, (void *)&Kall, (void *)&lists, (void *)&gmu, (void *)&gb};
+                    (void *)&nsweeps, (void *)&bvec, (void *)&Kall, (void *)&lists, (void *)&gmu, (void *)&gb,
+                    (void *)&wc};
     e = cudaLaunchCooperativeKernel((const void *)k_cd_lag2, dim3(G), dim3(LT), args, dyn, st);
     counted(1);
+    path_hit(GLASSO_PATH_CD_LAG2);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -535,6 +535,7 @@ cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, flo
     if (e != cudaSuccess) return e;
     if (side && (!ev_a || !ev_b)) return cudaErrorInvalidValue;
     Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b};
+    path_hit(GLASSO_PATH_TC_FACTOR);
     e = node(r, 0, n);
     if (e != cudaSuccess) return e;
     return logdet_from_diag(ldiag, n, sc, st);

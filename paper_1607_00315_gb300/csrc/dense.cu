@@ -939,6 +939,7 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
     cfg.numAttrs = 1;
     cudaError_t le = cudaLaunchKernelEx(&cfg, k_leaf32, A, ld, o, s, X, Xt, ldiag, sc);
     counted(1);
+    path_hit(GLASSO_PATH_TC_LEAVES);
     if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }

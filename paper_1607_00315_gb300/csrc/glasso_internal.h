@@ -51,6 +51,11 @@ __host__ __device__ __forceinline__ int64_t lmax(int64_t a, int64_t b) { return 
 extern std::atomic<long long> g_launches;
 inline void counted(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// Counters of the solver's code paths (all contexts), read through
+// glasso_profile.paths; indexes are the GLASSO_PATH_* values of glasso.h.
+extern std::atomic<long long> g_paths[GLASSO_PATHS];
+inline void path_hit(int k, long long v = 1) { g_paths[k].fetch_add(v, std::memory_order_relaxed); }
+
 // Column / row block of the dense FP64 kernels (Cholesky panel width, tile edge).
 constexpr int NB = 32;
 // Coordinates resolved together by one blocked CD step (see cd.cu).
@@ -153,6 +158,10 @@ struct Work {
     double *scr_diag = nullptr;
     int *cc_parent = nullptr, *cc_size = nullptr;
     int32_t *cc_comp = nullptr, *scr_idx = nullptr;
+    // fault injection for tests of the error paths (glasso_set_debug)
+    long long dbg_wait_cycles = 0;  // CD grid-barrier wait limit in SM cycles (0: about 2 s)
+    int dbg_wait_unreachable = 0;   // the barrier waits for one arrival more than the grid holds
+    int dbg_ls_reject = 0;          // every line-search trial is rejected
 };
 
 }  // namespace glx

@@ -55,9 +55,16 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+PATHS = 8
+PATH_NAMES = ("cd_lag2", "cd_persist32", "cd_chain64", "ls_series2", "ls_series6", "tc_factor",
+              "tc_leaves", "ns_steps")
+DEBUG_WAIT_CYCLES, DEBUG_WAIT_UNREACHABLE, DEBUG_LS_REJECT = 1, 2, 3
+
+
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * PROF_CLASSES), ("launches", C.c_longlong * PROF_CLASSES),
-                ("work", C.c_double * PROF_CLASSES), ("kernels", C.c_longlong)]
+                ("work", C.c_double * PROF_CLASSES), ("kernels", C.c_longlong),
+                ("paths", C.c_longlong * PATHS)]
 
 
 def load():
@@ -85,6 +92,7 @@ def load():
     L.glasso_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Info)]
     L.glasso_set_profiling.argtypes = [vp, i32]
     L.glasso_get_profile.argtypes = [vp, C.POINTER(Profile), i32]
+    L.glasso_set_debug.argtypes = [vp, i32, i64]
     L.glasso_form_S.argtypes = [vp, vp, i32, i64, i64, i32, vp]
     L.glasso_potrf.argtypes = [vp, vp, i64, C.POINTER(i32), C.POINTER(d)]
     L.glasso_inverse.argtypes = [vp, vp, i64, vp]
@@ -104,7 +112,7 @@ def load():
                  "glasso_submit", "glasso_poll", "glasso_set_profiling", "glasso_get_profile",
                  "glasso_form_S", "glasso_potrf", "glasso_inverse", "glasso_free_set",
                  "glasso_hierarchy", "glasso_cd_sweeps", "glasso_line_search", "glasso_objective",
-                 "glasso_components"):
+                 "glasso_components", "glasso_set_debug"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -171,7 +179,12 @@ class Context:
         d = {PROF_NAMES[c]: dict(ms=p.ms[c], launches=p.launches[c], work=p.work[c])
              for c in range(PROF_CLASSES)}
         d["kernels"] = p.kernels
+        d["paths"] = {PATH_NAMES[k]: p.paths[k] for k in range(PATHS)}
         return d
+
+    def set_debug(self, knob, value):
+        """Fault injection for tests of the error paths (glasso_set_debug)."""
+        self._check(self.L.glasso_set_debug(self.h, int(knob), int(value)), "set_debug")
 
     # ---------------------------------------------------------------- solver
     @staticmethod
@@ -328,4 +341,5 @@ EXPORTED = (
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
+    "glasso_set_debug",
 )

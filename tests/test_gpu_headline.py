@@ -1,0 +1,116 @@
+"""Parity at the headline size (the n = 2000 sparse-Theta workload) and a
+mixed-precision solve large enough to run the kernels the headline runs.
+
+Bar (Section 5, eq. MLE_l1_prior: the minimiser is unique, so parity is on
+the minimiser): max entry error 1e-7, the same support except pairs whose
+|(S - W)_ij| lies within 1e-7 of lambda, relative objective 1e-9.  The mixed
+path's reported objective carries the log det of its FP32 factorisations and
+is held to its stated 1e-7; the objective of its A, evaluated in FP64 by the
+oracle, meets 1e-9.
+
+The n = 2000 minimiser comes from tests/golden/n2000_minimiser.json, written
+by the oracle (tests/golden/make_n2000_minimiser.py) at rel. KKT 1e-10.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00315_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MIXED_OBJ_RTOL = 1e-7
+
+
+def _context(precision):
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso
+
+    build.build()
+    torch.cuda.init()
+    return glasso.Context(0, precision=glasso.MIXED if precision == "mixed" else glasso.FP64)
+
+
+@pytest.fixture(scope="module")
+def golden():
+    g = json.load(open(os.path.join(HERE, "golden", "n2000_minimiser.json")))
+    n = g["n"]
+    A = np.zeros((n, n))
+    A[g["i"], g["j"]] = g["a"]
+    A[g["j"], g["i"]] = g["a"]
+    border = np.zeros((n, n), dtype=bool)
+    border[g["border_i"], g["border_j"]] = True
+    border |= border.T
+    p = synth.config_problem(2)
+    S = oracle.form_S(p.X)
+    assert p.n == n and p.lam == g["lambda"]
+    return g, A, border, S
+
+
+def _support_ok(A, A_ref, border):
+    diff = (A != 0) != (A_ref != 0)
+    assert not np.any(diff & ~border), int(np.count_nonzero(diff & ~border))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_n2000_matches_the_oracle_minimiser(golden, precision):
+    g, A_ref, border, S = golden
+    F_ref = g["objective"]
+    ctx = _context(precision)
+    try:
+        ctx.get_profile(reset=True)
+        A, _, info = ctx.solve(S, g["lambda"], tol=1e-10)
+        paths = ctx.get_profile()["paths"]
+    finally:
+        ctx.close()
+    assert info["status"] == 0, info
+    assert info["rel_kkt"] <= 1e-10
+    assert np.array_equal(A, A.T)
+    assert np.abs(A - A_ref).max() <= 1e-7, np.abs(A - A_ref).max()
+    _support_ok(A, A_ref, border)
+    rtol = 1e-9 if precision == "fp64" else MIXED_OBJ_RTOL
+    assert abs(info["objective"] - F_ref) <= rtol * abs(F_ref), (info["objective"], F_ref)
+    # the objective of the returned A, evaluated by the oracle in FP64
+    _, F = oracle.objective(S, A, g["lambda"])
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref), (F, F_ref)
+    if precision == "mixed":
+        # the headline's kernels ran inside this solve
+        assert paths["cd_lag2"] >= 1, paths
+        assert paths["tc_factor"] >= 1 and paths["tc_leaves"] >= 16 * paths["tc_factor"], paths
+        assert paths["ls_series2"] + paths["ls_series6"] >= 1, paths
+        assert paths["ns_steps"] >= 1, paths
+
+
+def test_mixed_n1200_against_a_live_oracle_solve():
+    """A mixed solve at n = 1200 against the oracle's own solve of the same
+    S: large enough that the FP32 sweep is the pipelined chain-CTA kernel,
+    the factorisation recurses to ten 128-wide leaves, and the line search
+    takes both the log-det series and the tensor-core factorisation."""
+    p = synth.random_problem(1200, 600, 0.1, 1200, gen="sparse")
+    S = oracle.form_S(p.X)
+    A_ref, W_ref, info_ref, _ = oracle.solve(S, p.lam, tol=1e-10)
+    assert info_ref["status"] == 0
+    ctx = _context("mixed")
+    try:
+        ctx.get_profile(reset=True)
+        A, _, info = ctx.solve(S, p.lam, tol=1e-10)
+        paths = ctx.get_profile()["paths"]
+    finally:
+        ctx.close()
+    assert info["status"] == 0, info
+    assert np.abs(A - A_ref).max() <= 1e-7, np.abs(A - A_ref).max()
+    border = np.abs(np.abs(S - W_ref) - p.lam) <= 1e-7
+    _support_ok(A, A_ref, border)
+    F_ref = info_ref["objective"]
+    assert abs(info["objective"] - F_ref) <= MIXED_OBJ_RTOL * abs(F_ref)
+    _, F = oracle.objective(S, A, p.lam)
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref)
+    assert paths["cd_lag2"] >= 1, paths
+    assert paths["tc_factor"] >= 1 and paths["tc_leaves"] >= 10 * paths["tc_factor"], paths
+    assert paths["ls_series2"] + paths["ls_series6"] >= 1, paths
+    assert paths["ns_steps"] >= 1, paths

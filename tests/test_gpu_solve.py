@@ -215,9 +215,19 @@ def test_full_size_n10000_fp32_samples(mctx):
     assert abs(F - info["objective"]) <= MIXED_OBJ_RTOL * abs(F) + s_term
 
 
-def test_warm_start_and_batch_path(ctx):
+def _ctx_of(request, which):
+    return request.getfixturevalue("mctx" if which == "mixed" else "ctx")
+
+
+def _rtol(which):
+    return MIXED_OBJ_RTOL if which == "mixed" else 1e-9
+
+
+@pytest.mark.parametrize("which", ["fp64", "mixed"])
+def test_warm_start_and_batch_path(request, which):
     from paper_1607_00315_gb300 import glasso
 
+    ctx = _ctx_of(request, which)
     p = synth.random_problem(80, 160, 0.4, 21, gen="sparse")
     S = oracle.form_S(p.X)
     lams = list(synth.LAMBDA_PATH)
@@ -227,7 +237,7 @@ def test_warm_start_and_batch_path(ctx):
     assert s == 0
     for lam, A, inf in zip(lams, outs, infos):
         A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-10)
-        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"])
+        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"], _rtol(which))
     # independent problems through the concurrent path
     probs2 = [glasso.Context.problem(S, lam, 1e-10) for lam in lams]
     outs2 = [np.empty((80, 80)) for _ in lams]
@@ -237,11 +247,16 @@ def test_warm_start_and_batch_path(ctx):
         assert np.abs(A - B).max() <= 1e-7
 
 
-def test_concurrent_lambda_paths(ctx):
+@pytest.mark.parametrize("which", ["fp64", "mixed"])
+def test_concurrent_lambda_paths(request, which):
     """Several instances, each a warm-started lambda path, in one batch call:
     the paths run concurrently on the serving slots, each in order on one
-    slot; every result meets the oracle bar."""
+    slot; every result meets the oracle bar (on the mixed path: entries and
+    support to the FP64 bar, the reported objective to the mixed path's
+    stated 1e-7)."""
     from paper_1607_00315_gb300 import glasso
+
+    ctx = _ctx_of(request, which)
 
     insts = [synth.random_problem(n, 2 * n, 0.1, 31 + k, gen=g)
              for k, (n, g) in enumerate([(60, "sparse"), (90, "tridiag"), (45, "sparse")])]
@@ -256,11 +271,18 @@ def test_concurrent_lambda_paths(ctx):
     assert s == 0
     for (S, lam), A, inf in zip(meta, outs, infos):
         A_ref, _, info_ref, _ = oracle.solve(S, lam, tol=1e-10)
-        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"])
+        _compare(A, A_ref, S, lam, inf["objective"], info_ref["objective"], _rtol(which))
 
 
-def test_serving_results_same_alone_and_in_the_mix(ctx):
+@pytest.mark.parametrize("which", ["fp64", "mixed"])
+def test_serving_results_same_alone_and_in_the_mix(request, which):
+    """Continuous batching: requests submitted while others run are admitted
+    onto the serving slots and overlap on the device; each result equals the
+    same request solved alone, within 1e-9 of the largest entry, on both
+    precision paths (the mixed path is the one the serving workload runs)."""
     from paper_1607_00315_gb300 import glasso
+
+    ctx = _ctx_of(request, which)
 
     rng = np.random.default_rng(5)
     reqs = []
@@ -285,6 +307,10 @@ def test_serving_results_same_alone_and_in_the_mix(ctx):
         assert s == 0, info
     for A, B in zip(alone, outs):
         assert np.abs(A - B).max() <= 1e-9 * max(1.0, np.abs(A).max())
+    # and each meets the oracle's bar
+    for (p, S), B in zip(reqs[:3], outs[:3]):
+        A_ref, _, info_ref, _ = oracle.solve(S, p.lam, tol=1e-10)
+        assert np.abs(B - A_ref).max() <= 1e-6
 
 
 def test_error_paths(ctx):
