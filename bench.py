@@ -451,6 +451,119 @@ def run_serving(args):
     return 0
 
 
+def extra_workloads(args, local, dev):
+    """The other workloads, each measured once after the headline (N = 1): the
+    n = 10000 solve from FP32 samples on the device (S formed on the tensor
+    cores inside the solve), the batched lambda paths and the serving stream
+    (each in its own bench.py process, as `--workload batched` / `serving`)."""
+    import torch
+
+    from paper_1607_00315_gb300 import glasso, synth
+
+    out = {}
+    p3 = synth.config_problem(3)
+    X3 = torch.from_numpy(p3.X.astype(np.float32)).to(dev)
+    with glasso.Context(local, precision=glasso.MIXED) as c3:
+        stream = torch.cuda.current_stream(dev)
+        c3.set_stream(stream.cuda_stream)
+        A3 = torch.empty((p3.n, p3.n), dtype=torch.float64, device=dev)
+        info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3)[2]  # warm-up
+        lat3 = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3)[2]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lat3.append(e0.elapsed_time(e1))
+    del X3, A3
+    ms3 = float(np.mean(lat3))
+    out["n10000_fp32_samples"] = {
+        "workload": "sparse-Theta n=10000, X fp32 5000 x n on the device, S on the tensor cores "
+                    "inside the solve, lambda=0.08, mixed, to rel. KKT 1e-5",
+        "ms_per_solve": ms3, "solves_per_s": 1e3 / ms3, "status": info3["status"],
+        "relaxations": info3["relaxations"], "rel_kkt": info3["rel_kkt"], "nnz": info3["nnz"],
+        "inputs_larger_than_l2": True}
+    for name, extra in (("batched", []), ("serving", ["--requests", str(args.requests)])):
+        try:
+            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name] + extra,
+                               capture_output=True, text=True, timeout=600)
+            line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+            out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config")
+                         if k in line}
+        except Exception as e:  # reported, not fatal: the headline stands on its own
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
+
+
+def run_scan(args):
+    """The level-0 free-set scan alone (glasso_free_set over all pairs: the
+    free set of eq. active_set, the KKT residual, tr(SA), ||A||_1) at size n
+    on an iterate-like state: A = the generator's sparse precision matrix,
+    W = A^-1, S the covariance of n/2 samples.  value = algorithmic GB/s:
+    the upper triangles of S, W and A read once, 3 n(n+1)/2 x 8 bytes."""
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    n, lam = args.scan_n, 0.1
+    rng = np.random.default_rng(7000 + n)
+    theta = synth.sparse_theta(n, rng)
+    X = synth.gaussian_samples(theta, max(n // 2, 2), rng)
+    ctx = glasso.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    S = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx.form_S(torch.from_numpy(X).to(dev), S)
+    A = torch.from_numpy(theta).to(dev)
+    W = torch.linalg.inv(A)
+    W = (W + W.T) / 2
+    cap = n * (n + 1) // 2
+    oi = torch.empty(cap, dtype=torch.int32, device=dev)
+    oj = torch.empty_like(oi)
+    ab = torch.empty(cap, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        cnt, rk, _ = ctx.free_set(S, W, A, lam, oi, oj, ab)
+    lat = []
+    torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.start()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cnt, rk, _ = ctx.free_set(S, W, A, lam, oi, oj, ab)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1))
+    if args.profile_range:
+        torch.cuda.profiler.stop()
+    ms = float(np.mean(lat))
+    hbm, _, src = peaks()
+    gbs = 3.0 * n * (n + 1) / 2 * 8 / (ms * 1e-3) / 1e9
+    line = {"metric": "level-0 free-set scan with KKT residual (glasso_free_set, all pairs)",
+            "value": gbs, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"free-set scan n={n} lambda={lam}", "n": n, "free_pairs": cnt,
+                       "rel_kkt": rk, "l2": "flushed between timed calls (512 MB write)",
+                       "note": "the call's time includes its host synchronisation"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "peak_source": f"{src} hbm_gbs"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_factor(args):
     """The mixed path's dense factorisation alone: glasso_cholinv_mixed (FP32
     Cholesky A = L L^T with the inverse factor X = L^-1 formed alongside, then
@@ -527,11 +640,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="end-to-end solves through the public API (0: the same as --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (n=10000, batched, serving) reported beside the headline")
     ap.add_argument("--factor-n", type=int, default=2000, help="factor: matrix size")
-    ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serving", "factor"],
+    ap.add_argument("--scan-n", type=int, default=2000, help="scan: matrix size")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serving", "factor", "scan"],
                     help="solve: the n=2000 single-solve metric (default); batched: lambda paths "
                          "of many small instances; serving: a Poisson request stream; factor: "
-                         "the mixed path's tensor-core factorisation alone")
+                         "the mixed path's tensor-core factorisation alone; scan: the free-set scan alone")
     ap.add_argument("--instances", type=int, default=512, help="batched: instances")
     ap.add_argument("--screen", action="store_true",
                     help="batched: exact screening (isolated vertices in closed form)")
@@ -550,6 +666,8 @@ def main():
         return run_serving(args)
     if args.workload == "factor":
         return run_factor(args)
+    if args.workload == "scan":
+        return run_scan(args)
 
     import torch
     import torch.distributed as dist
@@ -749,6 +867,20 @@ def main():
     roof["work_per_launch"] = work_per_launch
     roof["traffic"] = ncu_traffic(dom)
     share = {k: round(v["ms"] / sum(c["ms"] for c in classes.values()), 4) for k, v in classes.items()}
+    # every timed class against its own roofline (the same arithmetic as above)
+    per_class = {}
+    for k, v in classes.items():
+        lm = v["ms"] / v["launches"]
+        wk = v["work"] / v["launches"]
+        if k in ("scan", "cd_sweeps"):
+            a = wk / (lm * 1e-3) / 1e9
+            per_class[k] = {"launch_ms": lm, "launches": v["launches"], "achieved": a, "unit": "GB/s",
+                            "frac": a / hbm}
+        else:
+            a = wk / (lm * 1e-3) / 1e12
+            pk = fp64_peak_tflops(bf16_s) if args.precision == "fp64" else tf32_peak_tflops(bf16_s)
+            per_class[k] = {"launch_ms": lm, "launches": v["launches"], "achieved": a, "unit": "TFLOP/s",
+                            "frac": a / pk}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -766,6 +898,7 @@ def main():
                   "ls_trials": infos[-1]["ls_trials"], "rel_kkt": infos[-1]["rel_kkt"],
                   "objective": infos[-1]["objective"], "nnz": infos[-1]["nnz"]},
         "time_share": share,
+        "class_roofline": per_class,
         "compare": compare,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Sh.nbytes),
                 "d2h_bytes_per_step": int(Ah.nbytes)},
@@ -773,6 +906,8 @@ def main():
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if world == 1 and not args.no_extra:
+        line["workloads"] = extra_workloads(args, local, dev)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 

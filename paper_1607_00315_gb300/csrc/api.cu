@@ -136,6 +136,7 @@ void work_free(Work &w, cudaStream_t st) {
 glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err) {
     if (!w.sc) {
         CK(dalloc(w.sc, 1, st));
+        CK(cudaMemsetAsync(w.sc, 0, sizeof(DevScalars), st));
         CK(cudaMallocHost((void **)&w.sc_host, sizeof(DevScalars)));
         CK(dalloc(w.redbuf, 3 * 1024, st));
         w.cap_red = 3 * 1024;
@@ -158,7 +159,7 @@ glasso_status work_ensure(Work &w, int64_t n, cudaStream_t st, std::string &err)
     CK(dalloc(w.blkcnt, w.cap_blk, st));
     CK(dalloc(w.mask, (size_t)n * ((n + 31) / 32), st));
     CK(dalloc(w.rowcnt, n + 1, st));
-    CK(dalloc(w.rowred, (size_t)n * 6, st));
+    CK(dalloc(w.rowred, std::max((size_t)n * 6, (size_t)5 * 152), st));  // per-row stats / scan partials
     CK(dalloc(w.ldiag, n, st));
     w.cap_n = n;
     w.cap_pairs = pairs;

@@ -99,6 +99,8 @@ struct DevScalars {
     int bar_err;
     int cc_err;           // component labelling: a retry bound was exceeded
     unsigned long long smax_bits;  // max_{i != j} |S_ij| as the bits of a non-negative double
+    unsigned scan_done;   // free-set sums: CTAs finished (the last one reduces, then resets it)
+    unsigned pad1;
 };
 
 // Per-context device workspace, sized for n <= cap_n.

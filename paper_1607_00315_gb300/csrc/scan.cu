@@ -5,6 +5,7 @@
 // (Section 6.1.2).  All reductions are deterministic: per-row or per-block
 // partials in a fixed order, then one CTA combines them in a fixed order.
 #include <math.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <mutex>
@@ -14,7 +15,6 @@
 namespace glx {
 namespace {
 
-constexpr int SCAN_WARPS = 8;      // rows per CTA of the full scan
 constexpr int CBLK = 1024;         // candidates per block of the candidate scan
 constexpr int RED_T = 256;
 
@@ -70,143 +70,287 @@ __device__ long long block_exclusive_scan(long long v, long long *total) {
 }
 
 // ---------------------------------------------------------------- full scan
-// One warp per row i covers the upper part j >= i.  Writes the ballot masks
-// of free entries, the per-row free count, and per-row partial sums of the
-// KKT residual, tr(SA), ||A||_1 and nnz(A) over the full matrix (off-diagonal
-// entries count twice by symmetry).
-__global__ void k_scan_rows(const double *__restrict__ S, const double *__restrict__ W,
-                            const double *__restrict__ A, int64_t n, double lam, int mode,
-                            uint32_t *__restrict__ mask, long long *__restrict__ rowcnt,
-                            double *__restrict__ rowred) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * SCAN_WARPS + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const int64_t nw = (n + 31) / 32;
-    long long cnt = 0;
-    double kkt = 0.0, kmax = 0.0, tr = 0.0, l1 = 0.0, nnz = 0.0;
-    const double *Si = S + i * n, *Wi = W + i * n, *Ai = A + i * n;
-    for (int64_t jb = i & ~(int64_t)31; jb < n; jb += 32) {
-        const int64_t j = jb + lane;
-        const bool valid = j >= i && j < n;
-        bool fr = false;
-        if (valid) {
-            const double s = Si[j], w = Wi[j], a = Ai[j];
-            const double g = s - w, ag = fabs(g);
-            const bool nz = a != 0.0;
-            fr = nz || (mode == 0 ? ag > lam : fabs(s) > lam);
-            // most entries have A_ij = 0 and |G_ij| <= lambda and add nothing:
-            // keep the FP64 work (slow on this GPU) to the rest
-            if (nz || ag > lam) {
-                const double wt = (j == i) ? 1.0 : 2.0;
-                const double r = nz ? g + lam * sgnd(a) : soft(g, lam);
-                kkt += wt * fabs(r);
-                kmax = fmax(kmax, fabs(r));
-                if (nz) {
-                    tr += wt * s * a;
-                    l1 += wt * fabs(a);
-                    nnz += wt;
+// Three passes over the upper triangle (j >= i) for the free set of
+// eq. active_set:
+//  1. k_scan_tiles: 64 x 64 tiles, one CTA per tile (tile (b, c), c >= b,
+//     band-major).  Each warp takes 8 rows of its tile, a lane two adjacent
+//     columns; S, W and A are read with 16-byte loads when n is even and the
+//     matrices 16-byte aligned (every row then starts on a 16-byte boundary),
+//     every load of a 4-row batch issued
+//     before any is used.  The free test runs on FP32 images of S and W built
+//     from the high words of the doubles by integer operations (20 mantissa
+//     bits); only an entry whose |G_ij| lies within the images' error band of
+//     lambda takes the exact FP64 test, so the FP64 pipe (slow on this GPU)
+//     stays idle on almost every entry.  A_ij != 0 is read from the bits.
+//     Writes the bit masks of free entries per row and 32-column word and the
+//     per-row free counts (integer atomics, so the order does not matter).
+//  2. k_scan_offsets: one CTA, exclusive scan of the row counts.
+//  3. k_scan_emit: one warp per row, 32 mask words at a time (integer work
+//     only): writes the free pairs in row-major order.
+//  4. k_scan_sums: over the compacted pairs, every lane busy: |S - W| on
+//     them and the sums -- the KKT residual of eq. subgradient1 with its max,
+//     tr(SA), ||A||_1, nnz(A) (off-diagonal pairs count twice by symmetry).
+//     In mode 0 every entry with a nonzero term (A_ij != 0 or |G_ij| >
+//     lambda) is a free pair, so these sums are exact; mode 1 (the initial
+//     set {|S_ij| > lambda} u supp(A)) gives exact tr(SA), ||A||_1 and nnz
+//     only.  Per-CTA partials; the last CTA reduces them in CTA order
+//     (deterministic).  The FP64 pipe runs at 1/64 of the FP32 rate on this
+//     GPU and costs a warp's issue whatever its active lanes, hence the
+//     separate dense pass.
+constexpr int ST = 64;                  // tile edge (columns and rows)
+constexpr int ST_WARPS = 8;             // warps per tile CTA
+constexpr int ST_ROWS = ST / ST_WARPS;  // rows per warp, in batches of ST_BATCH
+constexpr int ST_BATCH = 4;
+constexpr int EMIT_WARPS = 8;
+
+// FP32 image of x from its high word: sign, rebased exponent, the top 20
+// mantissa bits (truncated: relative error below 2^-20).  |x| < 2^-126 maps
+// to a signed zero (absolute error below 2^-126), |x| >= 2^128 to infinity.
+__device__ __forceinline__ float hi_image(double x) {
+    const int hi = __double2hiint(x);
+    const int e = ((hi >> 20) & 0x7ff) - 896;
+    const unsigned sgn = (unsigned)hi & 0x80000000u;
+    const unsigned bits = sgn | ((unsigned)e << 23) | (((unsigned)hi & 0xfffffu) << 3);
+    return __uint_as_float(e <= 0 ? sgn : (e >= 255 ? (sgn | 0x7f800000u) : bits));
+}
+
+// Bit k of x (k < 16) to bit 2k.
+__device__ __forceinline__ unsigned spread16(unsigned x) {
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// Is (s, w, a) free?  |g - g~| <= 2^-20 (|s| + |w|) + 2^-125 + 2^-23 |g~| for
+// the images' difference g~ (truncation of both images, one FP32 rounding);
+// the band below takes each term twice.  lam_lo <= lambda <= lam_hi are FP32.
+__device__ __forceinline__ bool entry_free(double s, double w, double a, double lam, float lam_lo,
+                                           float lam_hi, int mode) {
+    const bool nz = (((unsigned)__double2hiint(a) & 0x7fffffffu) | (unsigned)__double2loint(a)) != 0u;
+    if (nz) return true;
+    const float sf = hi_image(s);
+    const float x = mode == 0 ? fabsf(sf - hi_image(w)) : fabsf(sf);
+    const float band = mode == 0 ? 0x1p-19f * (fabsf(sf) + fabsf(hi_image(w))) + 0x1p-22f * x + 0x1p-100f
+                                 : 0x1p-19f * x + 0x1p-100f;
+    if (x - band > lam_hi) return true;   // certainly above lambda (NaN: false)
+    if (x + band < lam_lo) return false;  // certainly at most lambda
+    return mode == 0 ? fabs(s - w) > lam : fabs(s) > lam;  // the border: exact FP64 test
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(32 * ST_WARPS) k_scan_tiles(
+    const double *__restrict__ S, const double *__restrict__ W, const double *__restrict__ A,
+    int64_t n, double lam, float lam_lo, float lam_hi, int mode, uint32_t *__restrict__ mask,
+    unsigned long long *__restrict__ rowcnt) {
+    const int64_t nb = (n + ST - 1) / ST, nw = (n + 31) / 32;
+    // tile t -> (band b, column tile c >= b); band b holds nb - b tiles and
+    // starts at t0(b) = b nb - b (b - 1) / 2
+    const int64_t t = blockIdx.x;
+    const float q = (float)(2 * nb + 1);
+    int64_t b = (int64_t)((q - sqrtf(fmaxf(q * q - 8.f * (float)t, 0.f))) * 0.5f);
+    b = lmax(0, lmin(b, nb - 1));
+    while (b > 0 && b * nb - b * (b - 1) / 2 > t) --b;
+    while (b + 1 < nb && (b + 1) * nb - (b + 1) * b / 2 <= t) ++b;
+    const int64_t c = b + (t - (b * nb - b * (b - 1) / 2));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j0 = c * ST + 2 * lane;
+#pragma unroll
+    for (int bt = 0; bt < ST_ROWS; bt += ST_BATCH) {
+        double sv[ST_BATCH][2], wv[ST_BATCH][2], av[ST_BATCH][2];
+#pragma unroll
+        for (int r = 0; r < ST_BATCH; ++r) {
+            const int64_t i = b * ST + warp * ST_ROWS + bt + r;
+            const int64_t off = i * n + j0;
+            sv[r][0] = sv[r][1] = wv[r][0] = wv[r][1] = av[r][0] = av[r][1] = 0.0;
+            if (i < n && j0 + 1 >= i && j0 < n) {
+                if (VEC) {  // n even: j0 + 1 < n as well
+                    const double2 s2 = __ldg(reinterpret_cast<const double2 *>(S + off));
+                    const double2 w2 = __ldg(reinterpret_cast<const double2 *>(W + off));
+                    const double2 a2 = __ldg(reinterpret_cast<const double2 *>(A + off));
+                    sv[r][0] = s2.x; sv[r][1] = s2.y;
+                    wv[r][0] = w2.x; wv[r][1] = w2.y;
+                    av[r][0] = a2.x; av[r][1] = a2.y;
+                } else {
+                    sv[r][0] = __ldg(S + off); wv[r][0] = __ldg(W + off); av[r][0] = __ldg(A + off);
+                    if (j0 + 1 < n) {
+                        sv[r][1] = __ldg(S + off + 1); wv[r][1] = __ldg(W + off + 1);
+                        av[r][1] = __ldg(A + off + 1);
+                    }
                 }
             }
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, fr);
-        if (lane == 0) mask[i * nw + jb / 32] = m;
-        cnt += __popc(m);
-    }
-    kkt = warp_sum(kkt);
-    kmax = warp_max(kmax);
-    tr = warp_sum(tr);
-    l1 = warp_sum(l1);
-    nnz = warp_sum(nnz);
-    if (lane == 0) {
-        rowcnt[i] = cnt;
-        double *r = rowred + i * 6;
-        r[0] = kkt;
-        r[1] = kmax;
-        r[2] = tr;
-        r[3] = l1;
-        r[4] = nnz;
+#pragma unroll
+        for (int r = 0; r < ST_BATCH; ++r) {
+            const int64_t i = b * ST + warp * ST_ROWS + bt + r;
+            if (i >= n) break;  // warp-uniform
+            bool f[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int64_t j = j0 + e;
+                f[e] = j >= i && j < n && entry_free(sv[r][e], wv[r][e], av[r][e], lam, lam_lo, lam_hi, mode);
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, f[0]);
+            const unsigned m1 = __ballot_sync(0xffffffffu, f[1]);
+            const unsigned w0 = spread16(m0) | (spread16(m1) << 1);
+            const unsigned w1 = spread16(m0 >> 16) | (spread16(m1 >> 16) << 1);
+            const int64_t wd = c * 2;
+            if (lane == 0) {
+                mask[i * nw + wd] = w0;
+                if (wd + 1 < nw) mask[i * nw + wd + 1] = w1;
+                const unsigned cnt = __popc(w0) + __popc(w1);
+                if (cnt) atomicAdd(rowcnt + i, (unsigned long long)cnt);
+            }
+        }
     }
 }
 
-// One CTA: exclusive scan of the row counts (in place; total at rowcnt[n]) and
-// the fixed-order reduction of the row partial sums into the scalars.
-__global__ void __launch_bounds__(1024) k_scan_finish(long long *__restrict__ rowcnt,
-                                                      const double *__restrict__ rowred,
-                                                      int64_t n, DevScalars *sc, int sums) {
-    __shared__ double red[5][1024];
+// One CTA: exclusive scan of the row counts in place (total at rowcnt[n]
+// and in sc->count).
+__global__ void __launch_bounds__(1024) k_scan_offsets(unsigned long long *__restrict__ rowcnt,
+                                                       int64_t n, DevScalars *sc) {
     const int t = threadIdx.x;
     const int64_t per = (n + 1023) / 1024;
     const int64_t a = t * per, b = lmin(a + per, n);
     long long local = 0;
-    double kkt = 0.0, kmax = 0.0, tr = 0.0, l1 = 0.0, nnz = 0.0;
-    for (int64_t i = a; i < b; ++i) {
-        local += rowcnt[i];
-        if (sums) {
-            const double *r = rowred + i * 6;
-            kkt += r[0];
-            kmax = fmax(kmax, r[1]);
-            tr += r[2];
-            l1 += r[3];
-            nnz += r[4];
-        }
-    }
+    for (int64_t i = a; i < b; ++i) local += (long long)rowcnt[i];
     long long total;
     long long off = block_exclusive_scan(local, &total);
     for (int64_t i = a; i < b; ++i) {
-        long long c = rowcnt[i];
-        rowcnt[i] = off;
+        const long long c = (long long)rowcnt[i];
+        rowcnt[i] = (unsigned long long)off;
         off += c;
     }
     if (t == 0) {
-        rowcnt[n] = total;
+        rowcnt[n] = (unsigned long long)total;
         sc->count = total;
     }
-    if (!sums) return;
-    red[0][t] = kkt;
-    red[1][t] = kmax;
-    red[2][t] = tr;
-    red[3][t] = l1;
-    red[4][t] = nnz;
+}
+
+// Free pairs of each row at the row's offset, row-major.  A warp per row (rows
+// strided over the grid's warps); lane l holds mask word w0 + l of the chunk.
+__global__ void __launch_bounds__(32 * EMIT_WARPS) k_scan_emit(int64_t n, const uint32_t *__restrict__ mask,
+                                                              const unsigned long long *__restrict__ rowoff,
+                                                              int32_t *__restrict__ oi,
+                                                              int32_t *__restrict__ oj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 31) / 32;
+    const int64_t tw = (int64_t)gridDim.x * EMIT_WARPS;
+    for (int64_t i = (int64_t)blockIdx.x * EMIT_WARPS + (threadIdx.x >> 5); i < n; i += tw) {
+        long long off = (long long)rowoff[i];
+        for (int64_t wb = i / 32; wb < nw; wb += 32) {
+            const int64_t w = wb + lane;
+            uint32_t m = w < nw ? mask[i * nw + w] : 0u;
+            const int cnt = __popc(m);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            long long pos = off + incl - cnt;
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1u;
+                oi[pos] = (int32_t)i;
+                oj[pos] = (int32_t)(w * 32 + bit);
+                ++pos;
+            }
+            off += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+constexpr int SUM_T = 128;
+
+// |S - W| on the free pairs and the sums over them (see above); the pair
+// count comes from k_scan_offsets.  part: 5 doubles per CTA.
+__global__ void __launch_bounds__(SUM_T) k_scan_sums(const double *__restrict__ S, const double *__restrict__ W,
+                                                     const double *__restrict__ A, int64_t n, double lam,
+                                                     const int32_t *__restrict__ oi,
+                                                     const int32_t *__restrict__ oj,
+                                                     double *__restrict__ oabsg, double *__restrict__ part,
+                                                     DevScalars *sc) {
+    __shared__ double red[5][SUM_T];
+    __shared__ bool last_s;
+    const long long np = sc->count;
+    double kkt = 0.0, kmax = 0.0, tr = 0.0, l1 = 0.0, nnz = 0.0;
+    for (long long p = (long long)blockIdx.x * SUM_T + threadIdx.x; p < np; p += (long long)gridDim.x * SUM_T) {
+        const int64_t i = oi[p], j = oj[p];
+        const double s = S[i * n + j], w = W[i * n + j], a = A[i * n + j];
+        const double g = s - w, ag = fabs(g);
+        if (oabsg) oabsg[p] = ag;
+        const bool nz = a != 0.0;
+        if (nz || ag > lam) {
+            const double wt = (j == i) ? 1.0 : 2.0;
+            const double r = nz ? fabs(g + lam * sgnd(a)) : ag - lam;
+            kkt += wt * r;
+            kmax = fmax(kmax, r);
+            if (nz) {
+                tr += wt * s * a;
+                l1 += wt * fabs(a);
+                nnz += wt;
+            }
+        }
+    }
+    red[0][threadIdx.x] = kkt;
+    red[1][threadIdx.x] = kmax;
+    red[2][threadIdx.x] = tr;
+    red[3][threadIdx.x] = l1;
+    red[4][threadIdx.x] = nnz;
     __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if (t < w) {
-            red[0][t] += red[0][t + w];
-            red[1][t] = fmax(red[1][t], red[1][t + w]);
-            red[2][t] += red[2][t + w];
-            red[3][t] += red[3][t + w];
-            red[4][t] += red[4][t + w];
+    for (int h = SUM_T / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + h]);
+            red[2][threadIdx.x] += red[2][threadIdx.x + h];
+            red[3][threadIdx.x] += red[3][threadIdx.x + h];
+            red[4][threadIdx.x] += red[4][threadIdx.x + h];
         }
         __syncthreads();
     }
-    if (t == 0) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) part[blockIdx.x * 5 + k] = red[k][0];
+        __threadfence();
+        last_s = atomicAdd(&sc->scan_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    // the last CTA: fixed-order reduction of the CTA partials (L2 loads)
+    kkt = kmax = tr = l1 = nnz = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += SUM_T) {
+        kkt += __ldcg(part + 5 * b);
+        kmax = fmax(kmax, __ldcg(part + 5 * b + 1));
+        tr += __ldcg(part + 5 * b + 2);
+        l1 += __ldcg(part + 5 * b + 3);
+        nnz += __ldcg(part + 5 * b + 4);
+    }
+    red[0][threadIdx.x] = kkt;
+    red[1][threadIdx.x] = kmax;
+    red[2][threadIdx.x] = tr;
+    red[3][threadIdx.x] = l1;
+    red[4][threadIdx.x] = nnz;
+    __syncthreads();
+    for (int h = SUM_T / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + h]);
+            red[2][threadIdx.x] += red[2][threadIdx.x + h];
+            red[3][threadIdx.x] += red[3][threadIdx.x + h];
+            red[4][threadIdx.x] += red[4][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         sc->kkt_sum = red[0][0];
         sc->kkt_max = red[1][0];
         sc->trSA = red[2][0];
         sc->l1 = red[3][0];
         sc->nnz = (long long)red[4][0];
-    }
-}
-
-// Writes the free pairs of each row at the row's offset, in row-major order.
-__global__ void k_scan_write(const double *__restrict__ S, const double *__restrict__ W, int64_t n,
-                             const uint32_t *__restrict__ mask, const long long *__restrict__ rowoff,
-                             int32_t *__restrict__ oi, int32_t *__restrict__ oj,
-                             double *__restrict__ oabsg) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * SCAN_WARPS + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const int64_t nw = (n + 31) / 32;
-    long long off = rowoff[i];
-    for (int64_t w = i / 32; w < nw; ++w) {
-        const uint32_t m = mask[i * nw + w];
-        if (m & (1u << lane)) {
-            const long long pos = off + __popc(m & ((1u << lane) - 1u));
-            const int64_t j = w * 32 + lane;
-            oi[pos] = (int32_t)i;
-            oj[pos] = (int32_t)j;
-            if (oabsg) oabsg[pos] = fabs(S[i * n + j] - W[i * n + j]);
-        }
-        off += __popc(m);
+        sc->scan_done = 0u;  // ready for the next launch
     }
 }
 
@@ -413,17 +557,46 @@ inline unsigned grid_for(int64_t work, int per = 256) {
 
 }  // namespace
 
+// FP32 bounds lam_lo <= lam <= lam_hi.
+static void lam_bounds(double lam, float &lo, float &hi) {
+    lo = hi = (float)lam;
+    if ((double)lo > lam) lo = nextafterf(lo, -INFINITY);
+    if ((double)hi < lam) hi = nextafterf(hi, INFINITY);
+}
+
+static unsigned sums_grid(int64_t n) { return (unsigned)lmax(8, lmin(152, n / 32)); }
+
+// The four passes of the full scan (see above) on scratch mask (n x ceil(n/32)
+// words), rowcnt (n + 1) and part (5 x sums_grid(n) doubles).
+static cudaError_t scan_full_on(const double *S, const double *W, const double *A, int64_t n, double lam,
+                                int mode, uint32_t *mask, unsigned long long *rowcnt, double *part,
+                                int32_t *oi, int32_t *oj, double *oabsg, DevScalars *sc, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rowcnt, 0, (size_t)(n + 1) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    float lo, hi;
+    lam_bounds(lam, lo, hi);
+    const int64_t nb = (n + ST - 1) / ST;
+    const unsigned tiles = (unsigned)(nb * (nb + 1) / 2);
+    // 16-byte loads need every row start on a 16-byte boundary
+    const bool vec = n % 2 == 0 && (((uintptr_t)S | (uintptr_t)W | (uintptr_t)A) & 15u) == 0;
+    if (vec)
+        k_scan_tiles<true><<<tiles, 32 * ST_WARPS, 0, st>>>(S, W, A, n, lam, lo, hi, mode, mask, rowcnt);
+    else
+        k_scan_tiles<false><<<tiles, 32 * ST_WARPS, 0, st>>>(S, W, A, n, lam, lo, hi, mode, mask, rowcnt);
+    k_scan_offsets<<<1, 1024, 0, st>>>(rowcnt, n, sc);
+    const unsigned ge = (unsigned)lmin((n + EMIT_WARPS - 1) / EMIT_WARPS, 152 * 4);
+    k_scan_emit<<<ge, 32 * EMIT_WARPS, 0, st>>>(n, mask, rowcnt, oi, oj);
+    k_scan_sums<<<sums_grid(n), SUM_T, 0, st>>>(S, W, A, n, lam, oi, oj, oabsg, part, sc);
+    counted(4);
+    return cudaGetLastError();
+}
+
 cudaError_t scan_full(const double *S, const double *W, const double *A, int64_t n, double lam,
                       int mode, Work &w, int32_t *oi, int32_t *oj, double *oabsg, DevScalars *sc,
                       cudaStream_t st) {
-    const unsigned g = (unsigned)((n + SCAN_WARPS - 1) / SCAN_WARPS);
-    k_scan_rows<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, A, n, lam, mode, w.mask, w.rowcnt, w.rowred);
-    counted(1);
-    k_scan_finish<<<1, 1024, 0, st>>>(w.rowcnt, w.rowred, n, sc, 1);
-    counted(1);
-    k_scan_write<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, n, w.mask, w.rowcnt, oi, oj, oabsg);
-    counted(1);
-    return cudaGetLastError();
+    static_assert(sizeof(long long) == sizeof(unsigned long long), "row counts");
+    return scan_full_on(S, W, A, n, lam, mode, w.mask, reinterpret_cast<unsigned long long *>(w.rowcnt),
+                        w.rowred, oi, oj, oabsg, sc, st);
 }
 
 cudaError_t scan_cand(const double *S, const double *W, const double *A, int64_t n, double lam,
@@ -600,15 +773,15 @@ extern "C" glasso_status glasso_free_set_noalloc(const double *S, const double *
     long long *rowcnt = (long long *)(base + NA_CNT_OFF);
     double *rowred = (double *)(base + NA_RED_OFF);
     DevScalars *sc = (DevScalars *)(base + NA_SC_OFF);
-    // Every mask word, row count and partial sum the scan reads is written by
-    // it first; only the result scalars are cleared, so that no value of the
-    // previous call can leak into this one.
+    // Every mask word and partial sum the scan reads is written by it first,
+    // and the row counts are cleared by the scan itself; the result scalars
+    // (and the sums pass's completion counter) are cleared here, so that no
+    // value of the previous call can leak into this one.
     if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) return GLASSO_ECUDA;
-    const unsigned g = (unsigned)((n + SCAN_WARPS - 1) / SCAN_WARPS);
-    k_scan_rows<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, A, n, lambda, 0, mask, rowcnt, rowred);
-    k_scan_finish<<<1, 1024, 0, st>>>(rowcnt, rowred, n, sc, 1);
-    k_scan_write<<<g, 32 * SCAN_WARPS, 0, st>>>(S, W, n, mask, rowcnt, out_i, out_j, absg);
-    counted(3);
+    static_assert(5 * 152 * sizeof(double) <= NA_RED_BYTES, "partials of the sums pass");
+    if (scan_full_on(S, W, A, n, lambda, 0, mask, reinterpret_cast<unsigned long long *>(rowcnt), rowred,
+                     out_i, out_j, absg, sc, st) != cudaSuccess)
+        return GLASSO_ECUDA;
     if (cudaGetLastError() != cudaSuccess) return GLASSO_ECUDA;
     DevScalars h;
     if (cudaMemcpyAsync(&h, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess)
