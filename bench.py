@@ -521,8 +521,8 @@ def run_scan(args):
     S = torch.empty((n, n), dtype=torch.float64, device=dev)
     ctx.form_S(torch.from_numpy(X).to(dev), S)
     A = torch.from_numpy(theta).to(dev)
-    W = torch.linalg.inv(A)
-    W = (W + W.T) / 2
+    Wh = np.linalg.inv(theta)
+    W = torch.from_numpy((Wh + Wh.T) / 2).to(dev)
     cap = n * (n + 1) // 2
     oi = torch.empty(cap, dtype=torch.int32, device=dev)
     oj = torch.empty_like(oi)
@@ -817,6 +817,27 @@ def main():
         compare["screened"] = {"ms_per_solve": float(np.mean(slat)), "components": sinfo["components"],
                                "max_block": sinfo["max_block"], "relaxations": sinfo["relaxations"],
                                "nnz": sinfo["nnz"], "objective": sinfo["objective"]}
+        # the Newton-direction solver: CD sweeps (the headline) against PCD-CG
+        # to Section 8's relative precision 1e-4, same input and protocol
+        pinfo = None
+        for _ in range(2):
+            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner="pcd_cg")
+        plat = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner="pcd_cg")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            plat.append(e0.elapsed_time(e1))
+        compare["inner"] = {
+            "cd": {"ms_per_solve": total_ms / args.steps, "relaxations": infos[-1]["relaxations"],
+                   "inner_iters": infos[-1]["inner_iters"], "objective": infos[-1]["objective"]},
+            "pcd_cg": {"ms_per_solve": float(np.mean(plat)), "relaxations": pinfo["relaxations"],
+                       "inner_iters": pinfo["inner_iters"], "rel_kkt": pinfo["rel_kkt"],
+                       "objective": pinfo["objective"], "status": pinfo["status"]}}
 
     # end to end through the public API with host buffers (pinned): S in, A out
     Sh = S.cpu().pin_memory().numpy()

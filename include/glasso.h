@@ -85,7 +85,12 @@ typedef struct {
                          sub-problem (the method never couples two components: their pairs never enter
                          the free set).  Same minimiser; the statistics are the sub-problem's plus the
                          isolated vertices' (objective, log det, nnz). */
+    int inner;        /* Newton-direction solver of each relaxation: GLASSO_INNER_CD (0, the default):
+                         CD sweeps, min(1 + floor(k/3), 10) in cycle k; GLASSO_INNER_PCD_CG (1): PCD-CG
+                         (glasso_pcd) to relative precision 1e-4 (Section 8), at most 500 iterations */
 } glasso_problem;
+
+enum { GLASSO_INNER_CD = 0, GLASSO_INNER_PCD_CG = 1 };
 
 typedef struct {
     int status;          /* glasso_status of this solve */
@@ -102,6 +107,7 @@ typedef struct {
                             paper's max-supp, sampled where the full free set is formed) */
     int64_t components;  /* screen: connected components of {|S_ij| > lambda}; 0 without screening */
     int64_t max_block;   /* screen: vertices in the largest component; 0 without screening */
+    int64_t inner_iters; /* CD sweeps or PCD-CG iterations, summed over the relaxations */
 } glasso_info;
 
 /* ---- context -------------------------------------------------------- */
@@ -290,6 +296,29 @@ glasso_status glasso_hierarchy(glasso_ctx *ctx, const double *absg, const uint8_
 glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W,
                                const double *A, int64_t n, double lambda, const int32_t *pi,
                                const int32_t *pj, int64_t np, int nsweeps, double *D, double *U);
+
+/* a6 (alternative inner solver).  PCD-CG on the same Newton LASSO as
+ * glasso_cd_sweeps: the generalised parallel coordinate descent direction
+ * (Section 2, eq. IST_direction with D = the diagonal of the Hessian) -- every
+ * coordinate's own 1-D minimiser d_p = S_{lambda/a}(c - b/a) - c at once --
+ * with the exact minimising step along the search direction (the model is a
+ * convex quadratic plus a piecewise-linear term: its kinks are walked in
+ * increasing order, and a coordinate that lands on its kink becomes an
+ * exact zero), accelerated by non-linear conjugate gradients (Section 6.3;
+ * Polak-Ribiere-plus coefficient in the pair inner product with weight 2 off
+ * the diagonal, reset to the PCD direction when not a descent direction).
+ * A coordinate whose own minimiser is zero and that the step no longer moves
+ * is set to its exact zero.  cg == 0 gives plain PCD.  Stops after `iters`
+ * iterations, when the direction is zero, when the step is zero, or for
+ * rtol > 0 once max|d| <= rtol * max|d| of the first iteration.  D (np,
+ * device) holds Delta on the pairs (in/out; b starts from (W Delta W) of the
+ * given Delta); U (n x n, device) receives Delta W (its input is not read).
+ * *iters_done (host, may be NULL) receives the iterations taken.  In a
+ * GLASSO_MIXED context the products with W run in FP32 (the mixed solve's
+ * arithmetic) and U is returned converted to FP64. */
+glasso_status glasso_pcd(glasso_ctx *ctx, const double *S, const double *W, const double *A, int64_t n,
+                         double lambda, const int32_t *pi, const int32_t *pj, int64_t np, int iters,
+                         int cg, double rtol, double *D, double *U, int *iters_done);
 
 /* a7. Armijo backtracking line search (eq. Line-search; Section 6.1.2 with
  * alpha_0 = 1, beta = 1/2): the first alpha = 2^-t, t < max_trials, for which

@@ -123,6 +123,11 @@ void work_free(Work &w, cudaStream_t st) {
     dfree(w.scr_diag, st); dfree(w.cc_parent, st); dfree(w.cc_size, st); dfree(w.cc_comp, st);
     dfree(w.scr_idx, st);
     w.cap_scr = w.cap_cc = 0;
+    if (w.pcd_vec) cudaFreeAsync(w.pcd_vec, st);
+    if (w.pcd_rows) cudaFreeAsync(w.pcd_rows, st);
+    w.pcd_vec = nullptr;
+    w.pcd_rows = nullptr;
+    w.pcd_cap_np = w.pcd_cap_n = 0;
     if (w.sc_host) cudaFreeHost(w.sc_host);
     w.sc_host = nullptr;
     if (w.ev_a) cudaEventDestroy(w.ev_a);
@@ -295,6 +300,7 @@ struct Solver {
     std::string &err;
     Prof *prof;
     int precision = GLASSO_FP64;
+    int inner = GLASSO_INNER_CD;  // Newton-direction solver of the relaxations
     glasso_status sync() {
         CK(cudaMemcpyAsync(w.sc_host, w.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -333,6 +339,15 @@ void prof_collect(Prof *prof) {
     prof->pend_work.clear();
 }
 
+// PCD-CG as the inner solver: Section 8's relative precision, and an
+// iteration cap that the precision normally reaches long before.
+constexpr int kPcdIters = 500;
+constexpr double kPcdRtol = 1e-4;
+// Algorithmic bytes of one PCD-CG iteration with word size ws: the SpMM reads
+// the 2 np rows of W its pairs name and writes V^T (n^2), the SDDMM reads two
+// rows per pair.
+double pcd_bytes(int64_t np, double nd, double ws) { return (4.0 * (double)np * nd + nd * nd) * ws; }
+
 // Sums a caller combining several solves needs beyond glasso_info.
 struct CoreSums {
     double l1 = 0.0;  // ||A||_1 at return
@@ -368,6 +383,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
     const double nd = (double)n;
     const double flop_chol = nd * nd * nd / 3.0, flop_inv = 2.0 * nd * nd * nd / 3.0;
     int cycles = 0, relax = 0, lstrials = 0;
+    long long inner_iters = 0;
     double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
     long long nnz = 0, max_nnz = 0;
     glasso_status status = GLASSO_EMAXITER;
@@ -461,8 +477,18 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             CK(cudaMemsetAsync(w.U, 0, (size_t)(n * n) * sizeof(double), st));
             CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
             sv.mark_begin(3, eb);
-            CK(cd_sweeps(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
-            sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 8.0);
+            if (sv.inner == GLASSO_INNER_PCD_CG) {
+                // PCD-CG to relative precision 1e-4 (Section 8); T is free until the line search
+                int its = 0;
+                CK(pcd(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1, kPcdRtol, w.D, w.U,
+                       w.T, false, w, st, &its));
+                inner_iters += its;
+                sv.mark_end(3, eb, (double)its * pcd_bytes(np, nd, 8.0));
+            } else {
+                CK(cd_sweeps(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
+                inner_iters += nsweeps;
+                sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 8.0);
+            }
             CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lk, w, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
             if (h->bar_err) {
@@ -538,6 +564,7 @@ done:
         info->logdet = logdet;
         info->nnz = nnz;
         info->max_nnz = max_nnz;
+        info->inner_iters = inner_iters;
     }
     return status;
 }
@@ -584,6 +611,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     const double ns_tol = 1e-11;
     const int max_ns = 8;
     int cycles = 0, relax = 0, lstrials = 0;
+    long long inner_iters = 0;
     double F = 0.0, logdet = 0.0, trSA = 0.0, l1 = 0.0, relkkt = INFINITY, maxkkt = INFINITY;
     long long nnz = 0, max_nnz = 0;
     glasso_status status = GLASSO_EMAXITER;
@@ -754,9 +782,19 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             // once the relative KKT residual is small, where the Newton step must be
             // resolved to the gradient's FP64 accuracy
             // (the FP64 buffer T is free in this path: it holds the second copy of U)
-            CK(cd_sweeps32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
-                           relkkt <= 1e-6, st, (float *)w.T));
-            sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 4.0);
+            if (sv.inner == GLASSO_INNER_PCD_CG) {
+                // PCD-CG with FP32 products (T's FP32 halves are free until the next refinement)
+                int its = 0;
+                CK(pcd32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1, kPcdRtol, w.D,
+                         U32, (float *)w.T, false, w, st, &its));
+                inner_iters += its;
+                sv.mark_end(3, eb, (double)its * pcd_bytes(np, nd, 4.0));
+            } else {
+                CK(cd_sweeps32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, U32, w,
+                               relkkt <= 1e-6, st, (float *)w.T));
+                inner_iters += nsweeps;
+                sv.mark_end(3, eb, (double)nsweeps * (double)np * 6.0 * nd * 4.0);
+            }
             CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lk, w, sc, st));
             CK(series_terms(W64, n, w.pi, w.pj, w.D, np, U32, w.part, w.cap_part, sc, st));
             if (sv.sync() != GLASSO_OK) return GLASSO_ECUDA;
@@ -895,6 +933,7 @@ done:
         info->logdet = logdet;
         info->nnz = nnz;
         info->max_nnz = max_nnz;
+        info->inner_iters = inner_iters;
     }
     return status;
 }
@@ -968,11 +1007,13 @@ glasso_status validate(const glasso_problem *p) {
     if (p->input == GLASSO_INPUT_X && (p->m < 1 || (p->dtype != GLASSO_F64 && p->dtype != GLASSO_F32)))
         return GLASSO_EINVAL;
     if (p->n > 46340) return GLASSO_EINVAL;  // n^2 int32-indexed pair bound
+    if (p->inner != GLASSO_INNER_CD && p->inner != GLASSO_INNER_PCD_CG) return GLASSO_EINVAL;
     return GLASSO_OK;
 }
 
 glasso_status solve_one(Solver &sv, int64_t n, const glasso_problem *p, int mc, bool warm,
                         bool want_W, glasso_info *info, CoreSums *sums) {
+    sv.inner = p->inner;
     return sv.precision == GLASSO_MIXED
                ? solve_core_mixed(sv, n, p->lambda, p->tol, mc, warm, p->one_level != 0,
                                   p->continuation != 0, info, sums)
@@ -1723,6 +1764,39 @@ glasso_status glasso_cd_sweeps(glasso_ctx *ctx, const double *S, const double *W
         ctx->last_error = "CD sweep: a bounded grid-barrier wait expired";
         return GLASSO_ETIMEOUT;
     }
+    return GLASSO_OK;
+}
+
+glasso_status glasso_pcd(glasso_ctx *ctx, const double *S, const double *W, const double *A, int64_t n,
+                         double lambda, const int32_t *pi, const int32_t *pj, int64_t np, int iters,
+                         int cg, double rtol, double *D, double *U, int *iters_done) {
+    if (!ctx || !S || !W || !A || !U || n < 1 || !finite_pos(lambda) || np < 0 || iters < 0 ||
+        !(rtol >= 0.0) || (np > 0 && (!pi || !pj || !D)))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    if (np > ctx->w.cap_pairs) return GLASSO_EINVAL;
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int its = 0;
+    CTX_CK(pair_prep(S, W, A, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+    if (ctx->precision == GLASSO_MIXED) {
+        // the mixed solve's arithmetic: the products with W in FP32
+        const int64_t nn = n * n;
+        float *W32 = reinterpret_cast<float *>(w.L), *U32 = reinterpret_cast<float *>(w.W);
+        float *Vt = reinterpret_cast<float *>(w.T);
+        CTX_CK(to_f32(W, W32, nn, st));
+        CTX_CK(pcd32(W32, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D, U32, Vt, true, w,
+                     st, &its));
+        CTX_CK(to_f64(U32, U, nn, st));
+    } else {
+        CTX_CK(pcd(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D, U, w.T, true, w, st,
+                   &its));
+    }
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    if (iters_done) *iters_done = its;
     return GLASSO_OK;
 }
 

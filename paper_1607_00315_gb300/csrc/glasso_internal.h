@@ -160,6 +160,11 @@ struct Work {
     double *scr_diag = nullptr;
     int *cc_parent = nullptr, *cc_size = nullptr;
     int32_t *cc_comp = nullptr, *scr_idx = nullptr;
+    // PCD-CG scratch (pcd.cu): pair vectors and CSR of the pairs, grown on demand
+    unsigned char *pcd_vec = nullptr;
+    int64_t pcd_cap_np = 0;
+    int *pcd_rows = nullptr;
+    int64_t pcd_cap_n = 0;
     // fault injection for tests of the error paths (glasso_set_debug)
     long long dbg_wait_cycles = 0;  // CD grid-barrier wait limit in SM cycles (0: about 2 s)
     int dbg_wait_unreachable = 0;   // the barrier waits for one arrival more than the grid holds
@@ -298,6 +303,15 @@ cudaError_t cd_sweeps(const double *W, int64_t n, double lam, const int32_t *pi,
                       const int32_t *pj, int64_t np, const double *inva, const double *g,
                       const double *aval, int nsweeps, double *D, double *U, Work &w,
                       cudaStream_t st);
+// PCD-CG Newton-direction solver on the pair list (pcd.cu): W, U, Vt n x n
+// (Vt scratch); D on the pairs in/out (d_nonzero: D may be nonzero on entry);
+// U = Delta W on return; *iters_done (host, optional; synchronises).
+cudaError_t pcd(const double *W, int64_t n, double lam, const int32_t *pi, const int32_t *pj, int64_t np,
+                const double *inva, const double *g, const double *aval, int iters, int cg, double rtol,
+                double *D, double *U, double *Vt, bool d_nonzero, Work &w, cudaStream_t st, int *iters_done);
+cudaError_t pcd32(const float *W, int64_t n, double lam, const int32_t *pi, const int32_t *pj, int64_t np,
+                  const double *inva, const double *g, const double *aval, int iters, int cg, double rtol,
+                  double *D, float *U, float *Vt, bool d_nonzero, Work &w, cudaStream_t st, int *iters_done);
 cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi,
                         const int32_t *pj, int64_t np, const double *inva, const double *g,
                         const double *aval, int nsweeps, double *D, float *U, Work &w,

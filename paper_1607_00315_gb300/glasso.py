@@ -24,6 +24,13 @@ PROF_CLASSES = 6
 PROF_NAMES = ("cholesky", "inverse", "scan", "cd_sweeps", "ls_cholesky", "ns_refine")
 
 _lib = None
+INNER = {"cd": 0, "pcd_cg": 1}
+
+
+def _inner_code(inner):
+    if inner not in INNER:
+        raise ValueError(f"inner must be one of {sorted(INNER)}")
+    return INNER[inner]
 
 
 class GlassoError(RuntimeError):
@@ -41,7 +48,7 @@ class Problem(C.Structure):
                 ("data", C.c_void_p), ("n", C.c_int64), ("m", C.c_int64), ("center", C.c_int),
                 ("lambda_", C.c_double), ("tol", C.c_double), ("max_cycles", C.c_int),
                 ("A0", C.c_void_p), ("one_level", C.c_int), ("continuation", C.c_int),
-                ("screen", C.c_int)]
+                ("screen", C.c_int), ("inner", C.c_int)]
 
 
 class Info(C.Structure):
@@ -49,7 +56,7 @@ class Info(C.Structure):
                 ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
                 ("max_kkt", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
                 ("nnz", C.c_int64), ("max_nnz", C.c_int64), ("components", C.c_int64),
-                ("max_block", C.c_int64)]
+                ("max_block", C.c_int64), ("inner_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +100,7 @@ def load():
     L.glasso_set_profiling.argtypes = [vp, i32]
     L.glasso_get_profile.argtypes = [vp, C.POINTER(Profile), i32]
     L.glasso_set_debug.argtypes = [vp, i32, i64]
+    L.glasso_pcd.argtypes = [vp, vp, vp, vp, i64, d, vp, vp, i64, i32, i32, d, vp, vp, C.POINTER(i32)]
     L.glasso_form_S.argtypes = [vp, vp, i32, i64, i64, i32, vp]
     L.glasso_potrf.argtypes = [vp, vp, i64, C.POINTER(i32), C.POINTER(d)]
     L.glasso_inverse.argtypes = [vp, vp, i64, vp]
@@ -112,7 +120,7 @@ def load():
                  "glasso_submit", "glasso_poll", "glasso_set_profiling", "glasso_get_profile",
                  "glasso_form_S", "glasso_potrf", "glasso_inverse", "glasso_free_set",
                  "glasso_hierarchy", "glasso_cd_sweeps", "glasso_line_search", "glasso_objective",
-                 "glasso_components", "glasso_set_debug"):
+                 "glasso_components", "glasso_set_debug", "glasso_pcd"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -189,7 +197,8 @@ class Context:
     # ---------------------------------------------------------------- solver
     @staticmethod
     def problem(data, lam, tol=1e-8, *, samples=False, m=None, n=None, center=False,
-                max_cycles=0, A0=None, one_level=False, continuation=False, screen=False):
+                max_cycles=0, A0=None, one_level=False, continuation=False, screen=False,
+                inner="cd"):
         """Build a glasso_problem from a numpy array (host) or a torch CUDA tensor."""
         dev = hasattr(data, "data_ptr") and getattr(data, "is_cuda", False)
         if not dev and isinstance(data, np.ndarray) and not data.flags.c_contiguous:
@@ -204,18 +213,19 @@ class Context:
         p = Problem(INPUT_X if samples else INPUT_S, dt, DEVICE if dev else HOST, _ptr(data),
                     nn if n is None else n, mm if m is None else m, int(center), float(lam),
                     float(tol), int(max_cycles), _ptr(A0), int(bool(one_level)),
-                    int(bool(continuation)), int(bool(screen)))
+                    int(bool(continuation)), int(bool(screen)), _inner_code(inner))
         return p
 
     def solve(self, data, lam, tol=1e-8, *, samples=False, center=False, max_cycles=0, A0=None,
               A_out=None, W_out=None, want_W=False, check=True, one_level=False,
-              continuation=False, screen=False):
+              continuation=False, screen=False, inner="cd"):
         """glasso_solve (one_level: the paper's one-level comparison method;
         continuation: the paper's continuation stages before the cycles;
         screen: isolated vertices in closed form, the rest as one sub-problem).
         Returns (A, W or None, info dict)."""
         p = self.problem(data, lam, tol, samples=samples, center=center, max_cycles=max_cycles,
-                         A0=A0, one_level=one_level, continuation=continuation, screen=screen)
+                         A0=A0, one_level=one_level, continuation=continuation, screen=screen,
+                         inner=inner)
         n = p.n
         if A_out is None:
             if p.location == DEVICE:
@@ -297,6 +307,15 @@ class Context:
                                             _ptr(pi), _ptr(pj), len(pi), nsweeps, _ptr(D), _ptr(U)),
                     "cd_sweeps")
 
+    def pcd(self, S, W, A, lam, pi, pj, iters, D, U, cg=True, rtol=0.0):
+        """glasso_pcd: PCD(-CG) iterations on the pair list; D in/out, U = Delta W
+        out.  Returns the iterations taken."""
+        it = C.c_int(0)
+        self._check(self.L.glasso_pcd(self.h, _ptr(S), _ptr(W), _ptr(A), A.shape[0], lam, _ptr(pi),
+                                      _ptr(pj), len(pi), int(iters), int(bool(cg)), float(rtol), _ptr(D),
+                                      _ptr(U), C.byref(it)), "pcd")
+        return it.value
+
     def line_search(self, S, W, A, lam, pi, pj, D, F_A, sigma=1e-4, max_trials=30):
         Fn, al, tr = C.c_double(0.0), C.c_double(0.0), C.c_int(0)
         s = self.L.glasso_line_search(self.h, _ptr(S), _ptr(W), _ptr(A), A.shape[0], lam, _ptr(pi),
@@ -341,5 +360,5 @@ EXPORTED = (
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
-    "glasso_set_debug",
+    "glasso_set_debug", "glasso_pcd",
 )

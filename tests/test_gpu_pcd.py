@@ -1,0 +1,187 @@
+"""GPU parity of the PCD-CG Newton-direction solver (glasso_pcd) and of whole
+solves with it as the inner solver, against the oracle (orc_pcd,
+orc_solve(..., inner = PCD-CG)).
+
+The GPU carries b = G + (W Delta W) across iterations (adding t (W P W) and the
+exact zeros' corrections) where the oracle recomputes it from U = Delta W, so
+the two agree to rounding: on the FP64 path Delta and U to 1e-9 of their
+largest entry and the iteration counts exactly.  On the mixed path the
+products with W are FP32 sums of n terms (relative error up to about
+n 2^-24 each), held to 1e-4 of the largest entry after a few iterations.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_00315_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _context(precision):
+    import torch
+
+    from paper_1607_00315_gb300 import build, glasso
+
+    build.build()
+    torch.cuda.init()
+    return glasso.Context(0, precision=glasso.MIXED if precision == "mixed" else glasso.FP64)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = _context("fp64")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def mctx():
+    c = _context("mixed")
+    yield c
+    c.close()
+
+
+def _state(n, m, lam, seed, gen="sparse", cycles=1):
+    """An iterate after `cycles` oracle ML-cycles (or A0 for cycles = 0), its
+    inverse and its level-0 free set."""
+    p = synth.random_problem(n, m, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    if cycles > 0:
+        A, _, _, _ = oracle.solve(S, lam, tol=1e-14, max_cycles=cycles)
+    else:
+        A = np.diag(1.0 / (np.diag(S) + lam))
+    _, L = oracle.cholesky(A)
+    W = oracle.inverse_from_chol(L)
+    fi, fj = oracle.free_set(S, W, A, lam)
+    return S, W, A, fi, fj
+
+
+def _dev(*xs):
+    import torch
+
+    return [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in xs]
+
+
+CASES = [
+    (60, 120, 0.1, 11, "sparse", 0),
+    (150, 300, 0.1, 12, "sparse", 1),
+    (257, 200, 0.08, 13, "sparse", 2),   # m < n, a ragged tail of the 32 x 128 SpMM blocks
+    (100, 200, 0.2, 14, "tridiag", 1),
+]
+
+
+@pytest.mark.parametrize("iters", [1, 3, 12])
+@pytest.mark.parametrize("n,m,lam,seed,gen,cycles", CASES)
+def test_pcd_cg_matches_oracle(ctx, n, m, lam, seed, gen, cycles, iters):
+    import torch
+
+    S, W, A, fi, fj = _state(n, m, lam, seed, gen, cycles)
+    D_ref, U_ref, k_ref = oracle.pcd(S, W, A, lam, fi, fj, iters, cg=True)
+    Sd, Wd, Ad, pi, pj = _dev(S, W, A, fi, fj)
+    D = torch.zeros(len(fi), dtype=torch.float64, device="cuda")
+    U = torch.full((n, n), np.nan, dtype=torch.float64, device="cuda")  # not read
+    k = ctx.pcd(Sd, Wd, Ad, lam, pi, pj, iters, D, U, cg=True)
+    assert k == k_ref
+    D, U = D.cpu().numpy(), U.cpu().numpy()
+    scale = max(np.abs(D_ref).max(), 1e-300)
+    assert np.abs(D - D_ref).max() <= 1e-9 * scale
+    assert np.abs(U - U_ref).max() <= 1e-9 * max(np.abs(U_ref).max(), 1e-300)
+    # exact zeros (A + Delta = 0) agree where the oracle has them
+    z_ref = (A[fi, fj] + D_ref) == 0.0
+    z = (A[fi, fj] + D) == 0.0
+    assert np.array_equal(z, z_ref)
+
+
+@pytest.mark.parametrize("n,m,lam,seed,gen,cycles", CASES[:2])
+def test_plain_pcd_and_precision_stop_match_oracle(ctx, n, m, lam, seed, gen, cycles):
+    import torch
+
+    S, W, A, fi, fj = _state(n, m, lam, seed, gen, cycles)
+    Sd, Wd, Ad, pi, pj = _dev(S, W, A, fi, fj)
+    for cg, iters, rtol in ((False, 6, 0.0), (True, 500, 1e-4)):
+        D_ref, U_ref, k_ref = oracle.pcd(S, W, A, lam, fi, fj, iters, cg=cg, rtol=rtol)
+        D = torch.zeros(len(fi), dtype=torch.float64, device="cuda")
+        U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        k = ctx.pcd(Sd, Wd, Ad, lam, pi, pj, iters, D, U, cg=cg, rtol=rtol)
+        assert k == k_ref, (cg, k, k_ref)
+        assert np.abs(D.cpu().numpy() - D_ref).max() <= 1e-9 * np.abs(D_ref).max()
+
+
+def test_pcd_continues_from_a_nonzero_delta(ctx):
+    """b starts from (W Delta W) of the given Delta: one CD sweep, then PCD-CG."""
+    import torch
+
+    n, lam = 150, 0.1
+    S, W, A, fi, fj = _state(n, 300, lam, 12, "sparse", 1)
+    D0, U0 = oracle.cd_sweeps(S, W, A, lam, fi, fj, 1)
+    D_ref, U_ref, k_ref = oracle.pcd(S, W, A, lam, fi, fj, 5, cg=True, D=D0, U=U0)
+    Sd, Wd, Ad, pi, pj, D = _dev(S, W, A, fi, fj, D0)
+    U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    k = ctx.pcd(Sd, Wd, Ad, lam, pi, pj, 5, D, U, cg=True)
+    assert k == k_ref
+    assert np.abs(D.cpu().numpy() - D_ref).max() <= 1e-9 * np.abs(D_ref).max()
+    assert np.abs(U.cpu().numpy() - U_ref).max() <= 1e-9 * np.abs(U_ref).max()
+
+
+def test_pcd_empty_pair_list(ctx):
+    import torch
+
+    n = 40
+    S = np.eye(n)
+    Sd, Wd, Ad = _dev(S, S, S)
+    pi = torch.empty(0, dtype=torch.int32, device="cuda")
+    D = torch.empty(0, dtype=torch.float64, device="cuda")
+    U = torch.full((n, n), 3.0, dtype=torch.float64, device="cuda")
+    assert ctx.pcd(Sd, Wd, Ad, 0.1, pi, pi, 10, D, U) == 0
+    assert float(U.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,m,lam,seed,gen,cycles", CASES[1:3])
+def test_mixed_pcd_matches_oracle(mctx, n, m, lam, seed, gen, cycles):
+    import torch
+
+    S, W, A, fi, fj = _state(n, m, lam, seed, gen, cycles)
+    D_ref, U_ref, k_ref = oracle.pcd(S, W, A, lam, fi, fj, 3, cg=True)
+    Sd, Wd, Ad, pi, pj = _dev(S, W, A, fi, fj)
+    D = torch.zeros(len(fi), dtype=torch.float64, device="cuda")
+    U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    k = mctx.pcd(Sd, Wd, Ad, lam, pi, pj, 3, D, U, cg=True)
+    assert k == k_ref
+    assert np.abs(D.cpu().numpy() - D_ref).max() <= 1e-4 * np.abs(D_ref).max()
+    assert np.abs(U.cpu().numpy() - U_ref).max() <= 1e-4 * np.abs(U_ref).max()
+
+
+SOLVES = [
+    ("sparse", 120, 240, 0.1, 21),
+    ("tridiag", 90, 180, 0.2, 22),
+    ("sparse", 300, 150, 0.08, 23),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("gen,n,m,lam,seed", SOLVES)
+def test_solve_with_pcd_cg_inner_matches_oracle(request, precision, gen, n, m, lam, seed):
+    """Whole ML-cycle solves with PCD-CG as the Newton-direction solver (to
+    Section 8's relative precision 1e-4) against the oracle's run of the same
+    method: the FP64 path makes the same relaxations; both reach the unique
+    minimiser (entries 1e-7, support up to the lambda border, objective 1e-9;
+    the mixed path's reported objective 1e-7, its A's objective 1e-9)."""
+    c = request.getfixturevalue("mctx" if precision == "mixed" else "ctx")
+    p = synth.random_problem(n, m, lam, seed, gen=gen)
+    S = oracle.form_S(p.X)
+    A_ref, W_ref, info_ref, _ = oracle.solve(S, lam, tol=1e-10, inner="pcd_cg")
+    assert info_ref["status"] == 0
+    A, _, info = c.solve(S, lam, tol=1e-10, inner="pcd_cg")
+    assert info["status"] == 0, info
+    assert info["inner_iters"] > 0
+    if precision == "fp64":
+        assert info["relaxations"] == info_ref["relaxations"]
+    assert np.abs(A - A_ref).max() <= 1e-7
+    border = np.abs(np.abs(S - W_ref) - lam) <= 1e-7
+    assert not np.any(((A != 0) != (A_ref != 0)) & ~border)
+    F_ref = info_ref["objective"]
+    rtol = 1e-9 if precision == "fp64" else 1e-7
+    assert abs(info["objective"] - F_ref) <= rtol * abs(F_ref)
+    _, F = oracle.objective(S, A, lam)
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref)
