@@ -334,7 +334,9 @@ void orc_cd_sweeps(const double *S, const double *W, const double *A, int64_t n,
  * the w-weighted pair inner product; P_k = d_k when the directional
  * derivative phi'(0+) along P_k is not negative.  cg = 0: plain PCD.
  * Stops after `iters` iterations, when d = 0 (the LASSO minimiser), or, for
- * rtol > 0, once max|d| <= rtol * max|d| of the first iteration (Section 8
+ * rtol > 0, once max|d| <= rtol * max|d| of the first iteration; on that
+ * last stop, coordinates whose own minimiser is zero take their exact zero
+ * (READING: the final shrinkage, below) (Section 8
  * stops its PCD-CG inner solves at relative precision 1e-4; READING: that
  * precision is measured by the PCD direction, zero exactly at the minimiser).
  * D holds Delta on the pair list (in/out); U = Delta W (n x n, in/out) is
@@ -453,7 +455,23 @@ int orc_pcd(const double *S, const double *W, const double *A, int64_t n, double
         for (int64_t p = 0; p < np; ++p) dmax = fmax(dmax, fabs(d[p]));
         if (dmax == 0.0) break;
         if (it == 0) d0max = dmax;
-        else if (rtol > 0.0 && dmax <= rtol * d0max) break;
+        else if (rtol > 0.0 && dmax <= rtol * d0max) {
+            /* READING (final shrinkage): a coordinate whose own minimiser is
+             * zero is left by the steps at a residue below the stopping
+             * precision, on either side of zero; it takes its exact zero here,
+             * as a coordinate-descent step on it would give */
+            for (int64_t p = 0; p < np; ++p) {
+                const int64_t i = pi[p], j = pj[p];
+                const double cp = A[i * n + j] + D[p];
+                if (cp == 0.0 || cp + d[p] != 0.0) continue;
+                const double inc = -A[i * n + j] - D[p];
+                D[p] = -A[i * n + j];
+                for (int64_t k = 0; k < n; ++k) U[i * n + k] += inc * W[j * n + k];
+                if (i != j)
+                    for (int64_t k = 0; k < n; ++k) U[j * n + k] += inc * W[i * n + k];
+            }
+            break;
+        }
         double beta = 0.0;
         if (cg && it > 0) {
             double num = 0.0, den = 0.0;

@@ -526,6 +526,10 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
                     goto done;
                 }
                 CK(ls_apply(w.A, n, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
+                if (trace_on())
+                    fprintf(stderr, "glasso[fp64] cycle %d level %d pairs %lld F %.15g dF %.3e alpha %g trials %d "
+                            "inner %lld relkkt %.3e\n",
+                            k, l, (long long)np, FT, FT - F, alpha, lstrials, inner_iters, relkkt);
                 std::swap(w.L, w.T);
                 logdet = ldT;
                 trSA += alpha * trSD;

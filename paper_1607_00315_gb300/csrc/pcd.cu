@@ -25,10 +25,13 @@
 // plus, for the few coordinates set to an exact zero, the same two passes on
 // their corrections, so (W Delta W) is never recomputed from U = Delta W;
 // U is formed once at the end (SpMM of the final Delta).  The per-pair
-// vector work, the reductions and the exact step run in one CTA each
-// (k_pcd_dir, k_pcd_step); every kernel reads a device flag and returns at
-// once after the stopping rule fired, so the host launches iterations in
-// chunks and synchronises once per chunk.
+// vector work runs as grid-wide passes whose last CTA reduces the partials
+// and takes the scalar decisions (stop, CG coefficient, descent check, the
+// step's bound); the kink walk runs in one CTA.  Every kernel reads a device
+// flag and returns at once after the stopping rule fired, so the host
+// launches iterations in chunks and synchronises once per chunk.  At the
+// precision stop the coordinates whose own minimiser is zero take their
+// exact zero (the final shrinkage).
 //
 // Exact step: phi'(t) = g1 + g2 t + h(t), h(t+) = lambda sum_p w_p P_p
 // sign(c_p + t P_p) (sign(P_p) at a kink), is nondecreasing, so the minimiser
@@ -54,9 +57,13 @@ struct PcdState {
     int done;        // the stopping rule fired: every later kernel returns at once
     int it;          // iterations completed
     int has_corr;    // exact zeros this iteration: b needs their correction
+    int shrink;      // the precision stop fired: the final shrinkage is due
+    int reset;       // the CG direction did not descend: back to the PCD direction
+    int nk;          // kinks gathered in (0, R]
+    unsigned arrive; // CTAs finished with the current pass (the last one resets it)
     int pad;
     double d0max;    // max |d| of the first iteration
-    double beta, g1, t, kinkt;
+    double beta, g1, g2, h0, R, t, kinkt;
 };
 
 __device__ __forceinline__ double sgnd(double x) { return (double)((x > 0.0) - (x < 0.0)); }
@@ -65,7 +72,7 @@ __device__ __forceinline__ double soft(double x, double th) {
     return ax > 0.0 ? copysign(ax, x) : 0.0;
 }
 
-// Block-wide sum / max over PT threads (every thread gets the result).
+// Block-wide sum over PT threads (every thread gets the result).
 __device__ double block_sum(double v, double *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -81,22 +88,6 @@ __device__ double block_sum(double v, double *red) {
     __syncthreads();
     return red[32];
 }
-__device__ double block_max(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double x = red[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if (threadIdx.x == 0) red[32] = x;
-    }
-    __syncthreads();
-    return red[32];
-}
-
 // ---------------------------------------------------------------- CSR of the pairs
 // Row r lists every pair touching r: (r, j) for pairs (r, j) and (r, i) for
 // pairs (i, r), i < r, as (column, pair index); rows are sorted by column so
@@ -268,83 +259,209 @@ __global__ void k_pcd_addb(double *__restrict__ b, const double *__restrict__ ad
 }
 
 // ---------------------------------------------------------------- one iteration, vector part
-// Direction, stopping rule, CG coefficient, search direction and g1 (one CTA).
-// v: pair vectors (see PcdVec); w_p = 2 off the diagonal, 1 on it.
+// The per-pair work of an iteration is a sequence of grid-wide passes over
+// the pairs; each pass ends in per-CTA partial sums, and the last CTA to
+// finish combines them in CTA order (deterministic) and takes the pass's
+// scalar decision, which the next pass reads from the state.  Only the kink
+// walk runs in one CTA, on the kinks gathered by the pass before it.
 struct PcdVec {
     const int32_t *pi, *pj;
     const double *inva, *g, *aval;  // 1/a_p, G_p, A_p
     double *D, *b, *c, *d, *dprev, *P, *wpw, *corr;
     uint8_t *zt;
     int64_t np;
+    double *part;      // 4 partials per CTA of a pass
+    double *kt, *kj;   // gathered kinks: times and jumps (KCAP)
+    int *kp;           //                  pair indices
 };
 
-__global__ void __launch_bounds__(PT) k_pcd_dir(PcdVec v, double lam, int iters, int cg, double rtol,
+constexpr int GT = 256;  // threads of a pass CTA
+
+__device__ __forceinline__ double pair_w(const PcdVec &v, int64_t p) { return v.pi[p] == v.pj[p] ? 1.0 : 2.0; }
+
+// Reduce NV per-thread values (slot k a max when bit k of maxmask is set, else
+// a sum) over the grid; returns true in thread 0 of the last CTA to arrive,
+// with the totals in out.  Partials are combined in CTA order.
+template <int NV>
+__device__ bool pass_reduce(double (&v)[NV], unsigned maxmask, double *part, unsigned *arrive,
+                            double (&out)[NV]) {
+    __shared__ double sred[NV][GT / 32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (maxmask >> k) & 1u ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) sred[k][wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = sred[k][0];
+            for (int w = 1; w < GT / 32; ++w) x = (maxmask >> k) & 1u ? fmax(x, sred[k][w]) : x + sred[k][w];
+            part[blockIdx.x * NV + k] = x;
+        }
+        __threadfence();
+        last = atomicAdd(arrive, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || wid != 0) return false;
+    __threadfence();
+    // warp 0 of the last CTA: lane l combines partials l, l + 32, ... in order
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const bool mx = (maxmask >> k) & 1u;
+        double x = mx ? -INFINITY : 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const double y = __ldcg(part + b * NV + k);
+            x = mx ? fmax(x, y) : x + y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = mx ? fmax(x, y) : x + y;
+        }
+        out[k] = x;
+    }
+    if (lane == 0) *arrive = 0u;
+    return lane == 0;
+}
+
+// Pass 1: c, the PCD direction d, max|d| and the Polak-Ribiere sums; the
+// last CTA applies the stopping rule and sets beta.
+__global__ void __launch_bounds__(GT) k_pcd_dir(PcdVec v, double lam, int iters, int cg, double rtol,
                                                 PcdState *st) {
-    __shared__ double red[33];
     if (st->done) return;
     const int it = st->it;
     if (it >= iters) {
-        if (threadIdx.x == 0) st->done = 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 1;
         return;
     }
-    double dmax = 0.0, num = 0.0, den = 0.0;
-    for (int64_t p = threadIdx.x; p < v.np; p += PT) {
+    double r[3] = {0.0, 0.0, 0.0};  // max |d|, <d, d - d_prev>_w, <d_prev, d_prev>_w
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
         const double c = v.aval[p] + v.D[p];
         const double dp = soft(c - v.b[p] * v.inva[p], lam * v.inva[p]) - c;
         v.c[p] = c;
         v.d[p] = dp;
-        dmax = fmax(dmax, fabs(dp));
+        r[0] = fmax(r[0], fabs(dp));
         if (cg && it > 0) {
-            const double w = v.pi[p] == v.pj[p] ? 1.0 : 2.0, dq = v.dprev[p];
-            num += w * dp * (dp - dq);
-            den += w * dq * dq;
+            const double w = pair_w(v, p), dq = v.dprev[p];
+            r[1] += w * dp * (dp - dq);
+            r[2] += w * dq * dq;
         }
     }
-    dmax = block_max(dmax, red);
-    bool stop = dmax == 0.0;
-    if (!stop && it > 0 && rtol > 0.0 && dmax <= rtol * st->d0max) stop = true;
-    if (stop) {
-        if (threadIdx.x == 0) st->done = 1;
-        return;
+    double o[3];
+    if (!pass_reduce<3>(r, 1u, v.part, &st->arrive, o)) return;
+    const double dmax = o[0];
+    if (dmax == 0.0) {
+        st->done = 1;
+    } else if (it > 0 && rtol > 0.0 && dmax <= rtol * st->d0max) {
+        st->done = 1;
+        st->shrink = 1;  // the final shrinkage (k_pcd_shrink)
+    } else {
+        if (it == 0) st->d0max = dmax;
+        st->beta = (cg && it > 0 && o[2] > 0.0) ? fmax(0.0, o[1] / o[2]) : 0.0;
     }
-    double beta = 0.0;
-    if (cg && it > 0) {
-        num = block_sum(num, red);
-        den = block_sum(den, red);
-        beta = den > 0.0 ? fmax(0.0, num / den) : 0.0;
+}
+
+// At the precision stop: coordinates whose own minimiser is zero take their
+// exact zero.  Runs after the stop (gated on `shrink` alone).
+__global__ void __launch_bounds__(GT) k_pcd_shrink(PcdVec v, PcdState *st) {
+    if (!st->shrink) return;
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
+        const double c = v.c[p];
+        if (c != 0.0 && c + v.d[p] == 0.0) v.D[p] = -v.aval[p];
     }
-    double g1 = 0.0, h = 0.0;
-    for (int64_t p = threadIdx.x; p < v.np; p += PT) {
+}
+
+// Pass 2: P = d + beta P_prev, the zero flags, g1 = <b, P>_w and the slope h
+// of the l1 term at 0+; the last CTA checks descent.
+__global__ void __launch_bounds__(GT) k_pcd_dirP(PcdVec v, double lam, PcdState *st) {
+    if (st->done) return;
+    const double beta = st->beta;
+    double r[2] = {0.0, 0.0};
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
         const double dp = v.d[p], c = v.c[p];
         const double P = dp + beta * v.P[p];  // P holds the previous direction (0 at the start)
         v.P[p] = P;
         v.zt[p] = c + dp == 0.0;  // the coordinate's own minimiser is zero
-        const double w = v.pi[p] == v.pj[p] ? 1.0 : 2.0;
-        g1 += w * v.b[p] * P;
-        if (P != 0.0) h += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
+        const double w = pair_w(v, p);
+        r[0] += w * v.b[p] * P;
+        if (P != 0.0) r[1] += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
     }
-    g1 = block_sum(g1, red);
-    if (beta != 0.0) {
-        h = block_sum(h, red);
-        if (g1 + h >= 0.0) {  // not a descent direction: back to the PCD direction
-            g1 = 0.0;
-            for (int64_t p = threadIdx.x; p < v.np; p += PT) {
-                const double w = v.pi[p] == v.pj[p] ? 1.0 : 2.0;
-                v.P[p] = v.d[p];
-                g1 += w * v.b[p] * v.d[p];
-            }
-            g1 = block_sum(g1, red);
+    double o[2];
+    if (!pass_reduce<2>(r, 0u, v.part, &st->arrive, o)) return;
+    st->g1 = o[0];
+    st->reset = beta != 0.0 && o[0] + o[1] >= 0.0;  // not a descent direction
+}
+
+// Pass 2b (after a failed descent check): back to the PCD direction.
+__global__ void __launch_bounds__(GT) k_pcd_reset(PcdVec v, PcdState *st) {
+    if (st->done || !st->reset) return;
+    double r[1] = {0.0};
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
+        v.P[p] = v.d[p];
+        r[0] += pair_w(v, p) * v.b[p] * v.d[p];
+    }
+    double o[1];
+    if (!pass_reduce<1>(r, 0u, v.part, &st->arrive, o)) return;
+    st->g1 = o[0];
+    st->reset = 0;
+}
+
+// Pass 3 (after W P W): g2 = <P, W P W>_w and h(0+); the last CTA decides
+// whether the step is zero and sets the bound R = -(g1 + h(0+)) / g2 of the
+// minimiser.
+__global__ void __launch_bounds__(GT) k_pcd_g2(PcdVec v, double lam, PcdState *st) {
+    if (st->done) return;
+    double r[2] = {0.0, 0.0};
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
+        const double P = v.P[p];
+        if (P == 0.0) continue;
+        const double w = pair_w(v, p), c = v.c[p];
+        r[0] += w * P * v.wpw[p];
+        r[1] += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
+    }
+    double o[2];
+    if (!pass_reduce<2>(r, 0u, v.part, &st->arrive, o)) return;
+    const double g2 = o[0], h0 = o[1], g1 = st->g1;
+    st->g2 = g2;
+    st->h0 = h0;
+    st->nk = 0;
+    if (!(g2 > 0.0) || g1 + h0 >= 0.0) {
+        st->t = 0.0;
+        st->done = 1;  // no descent along P: the oracle's zero step ends the iteration
+    } else {
+        st->R = -(g1 + h0) / g2;
+    }
+}
+
+// Pass 4: gather the kinks t_p = -c_p / P_p in (0, R] (at most KCAP; the count
+// beyond that sends the walk to its fallback).
+__global__ void __launch_bounds__(GT) k_pcd_kinks(PcdVec v, double lam, PcdState *st) {
+    if (st->done) return;
+    const double R = st->R;
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
+        const double P = v.P[p], c = v.c[p];
+        if (P == 0.0 || c == 0.0 || sgnd(c) == sgnd(P)) continue;
+        const double tk = -c / P;
+        if (!(tk > 0.0 && tk <= R)) continue;
+        const int s = atomicAdd(&st->nk, 1);
+        if (s < KCAP) {
+            v.kt[s] = tk;
+            v.kj[s] = 2.0 * lam * pair_w(v, p) * fabs(P);
+            v.kp[s] = (int)p;
         }
-    }
-    if (threadIdx.x == 0) {
-        if (it == 0) st->d0max = dmax;
-        st->beta = beta;
-        st->g1 = g1;
     }
 }
 
 // lambda sum_p w_p P_p sign(c_p + t P_p) (sign(P_p) where c_p + t P_p = 0) and
-// the number of kinks t_p = -c_p / P_p in (L, R], for one thread's pairs.
+// the number of kinks in (L, R], over one thread's pairs (one-CTA kernel).
 __device__ __forceinline__ void slope_and_kinks(const PcdVec &v, double lam, double t, double L, double R,
                                                 double &h, double &cnt) {
     h = 0.0;
@@ -352,7 +469,7 @@ __device__ __forceinline__ void slope_and_kinks(const PcdVec &v, double lam, dou
     for (int64_t p = threadIdx.x; p < v.np; p += PT) {
         const double P = v.P[p];
         if (P == 0.0) continue;
-        const double c = v.c[p], w = v.pi[p] == v.pj[p] ? 1.0 : 2.0;
+        const double c = v.c[p], w = pair_w(v, p);
         const double x = c + t * P;
         h += lam * w * P * (x != 0.0 ? sgnd(x) : sgnd(P));
         if (c != 0.0 && sgnd(c) != sgnd(P)) {
@@ -362,43 +479,31 @@ __device__ __forceinline__ void slope_and_kinks(const PcdVec &v, double lam, dou
     }
 }
 
-// g2, the exact step, and the update of Delta and b (one CTA; dynamic shared
-// memory: KCAP keys, jumps and pair indices).
-__global__ void __launch_bounds__(PT) k_pcd_step(PcdVec v, double lam, PcdState *st) {
+// The exact step (one CTA; dynamic shared memory: KCAP keys, jumps and pair
+// indices): sort the kinks of (L, R] and walk them in increasing order from
+// h(L+).  L = 0 and the kinks gathered by k_pcd_kinks when they fit; else the
+// interval is first halved (bit-pattern bisection on the sign of phi') over
+// all pairs until its kinks fit, or until it holds a single kink value.
+__global__ void __launch_bounds__(PT) k_pcd_walk(PcdVec v, double lam, PcdState *st) {
     extern __shared__ __align__(16) unsigned char pcd_smem[];
     double *key = reinterpret_cast<double *>(pcd_smem);
     double *jmp = key + KCAP;
     int *kid = reinterpret_cast<int *>(jmp + KCAP);
     __shared__ double red[33];
     __shared__ int nkink;
-    __shared__ double res_t, res_kink;
     if (st->done) return;
-    const double g1 = st->g1;
-    double g2 = 0.0, h0 = 0.0;
-    for (int64_t p = threadIdx.x; p < v.np; p += PT) {
-        const double P = v.P[p];
-        if (P == 0.0) continue;
-        const double w = v.pi[p] == v.pj[p] ? 1.0 : 2.0, c = v.c[p];
-        g2 += w * P * v.wpw[p];
-        h0 += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
-    }
-    g2 = block_sum(g2, red);
-    h0 = block_sum(h0, red);
-    if (threadIdx.x == 0) {
-        res_t = 0.0;
-        res_kink = -1.0;
-    }
-    if (g2 > 0.0 && g1 + h0 < 0.0) {
-        // the minimiser lies in (L, R]; kinks at or below L are in HL = h(L+)
-        double L = 0.0, HL = h0, R = -(g1 + h0) / g2;
-        bool group = false;  // (L, R] holds too many kinks, all at R
-        // bisection on the bit patterns of the non-negative doubles (ordered as
-        // integers): at most 64 halvings before L and R are neighbours
+    const double g1 = st->g1, g2 = st->g2;
+    double L = 0.0, HL = st->h0, R = st->R;
+    bool group = false;  // (L, R] holds more than KCAP kinks, all at R
+    int m = st->nk;
+    if (m <= KCAP) {
+        for (int s = threadIdx.x; s < m; s += PT) {
+            key[s] = v.kt[s];
+            jmp[s] = v.kj[s];
+            kid[s] = v.kp[s];
+        }
+    } else {
         for (int round = 0; round < 70; ++round) {
-            double hh, cnt;
-            slope_and_kinks(v, lam, L, L, R, hh, cnt);
-            cnt = block_sum(cnt, red);
-            if (cnt <= (double)KCAP) break;
             const long long lb = __double_as_longlong(L), rb = __double_as_longlong(R);
             const double mid = __longlong_as_double(lb + (rb - lb) / 2);
             if (!(mid > L && mid < R)) {
@@ -414,6 +519,10 @@ __global__ void __launch_bounds__(PT) k_pcd_step(PcdVec v, double lam, PcdState 
                 L = mid;
                 HL = hm;
             }
+            double hh, cnt;
+            slope_and_kinks(v, lam, L, L, R, hh, cnt);
+            cnt = block_sum(cnt, red);
+            if (cnt <= (double)KCAP) break;
         }
         if (threadIdx.x == 0) nkink = 0;
         __syncthreads();
@@ -423,8 +532,7 @@ __global__ void __launch_bounds__(PT) k_pcd_step(PcdVec v, double lam, PcdState 
             if (P == 0.0 || c == 0.0 || sgnd(c) == sgnd(P)) continue;
             const double tk = -c / P;
             if (!(tk > L && tk <= R)) continue;
-            const double w = v.pi[p] == v.pj[p] ? 1.0 : 2.0;
-            const double j = 2.0 * lam * w * fabs(P);
+            const double j = 2.0 * lam * pair_w(v, p) * fabs(P);
             if (group) {
                 gjump += j;
             } else {
@@ -436,84 +544,86 @@ __global__ void __launch_bounds__(PT) k_pcd_step(PcdVec v, double lam, PcdState 
                 }
             }
         }
-        if (group) gjump = block_sum(gjump, red);
-        __syncthreads();
-        const int m = group ? 0 : min(nkink, KCAP);
-        // bitonic sort of (key, pair index) ascending, padded to a power of two
-        int m2 = 1;
-        while (m2 < m) m2 <<= 1;
-        for (int s = m + threadIdx.x; s < m2; s += PT) {
-            key[s] = INFINITY;
-            jmp[s] = 0.0;
-            kid[s] = 0x7fffffff;
-        }
-        __syncthreads();
-        for (int size = 2; size <= m2; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int s = threadIdx.x; s < m2; s += PT) {
-                    const int o = s ^ stride;
-                    if (o > s) {
-                        const bool up = (s & size) == 0;
-                        const bool gt = key[s] > key[o] || (key[s] == key[o] && kid[s] > kid[o]);
-                        if (gt == up) {
-                            const double tk = key[s], tj = jmp[s];
-                            const int ti = kid[s];
-                            key[s] = key[o]; jmp[s] = jmp[o]; kid[s] = kid[o];
-                            key[o] = tk; jmp[o] = tj; kid[o] = ti;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        if (threadIdx.x == 0) {
-            // the walk of the kinks in increasing order from h(L+)
-            double H = HL, t = NAN, kinkt = -1.0;
-            if (group) {
+        if (group) {
+            gjump = block_sum(gjump, red);
+            if (threadIdx.x == 0) {
+                double t = NAN, kinkt = -1.0, H = HL;
                 const double ts = -(g1 + H) / g2;
                 if (ts <= R) t = ts;
                 else if (g1 + g2 * R + H + gjump >= 0.0) t = kinkt = R;
-                else H += gjump;
-            } else {
-                int k = 0;
-                while (k < m) {
-                    const double tk = key[k];
-                    const double ts = -(g1 + H) / g2;
-                    if (ts <= tk) {
-                        t = ts;
-                        break;
-                    }
-                    double jump = 0.0;
-                    int k2 = k;
-                    while (k2 < m && key[k2] == tk) jump += jmp[k2++];
-                    if (g1 + g2 * tk + H + jump >= 0.0) {
-                        t = kinkt = tk;
-                        break;
-                    }
-                    H += jump;
-                    k = k2;
-                }
+                else t = -(g1 + H + gjump) / g2;
+                st->t = t;
+                st->kinkt = kinkt;
             }
-            if (isnan(t)) t = -(g1 + H) / g2;
-            res_t = t;
-            res_kink = kinkt;
+            return;
         }
+        __syncthreads();
+        m = min(nkink, KCAP);
     }
     __syncthreads();
-    const double t = res_t, kinkt = res_kink;
-    for (int64_t p = threadIdx.x; p < v.np; p += PT) v.dprev[p] = v.d[p];
-    if (t == 0.0) {
-        if (threadIdx.x == 0) {
-            st->done = 1;
-            st->t = 0.0;
-        }
-        return;
+    // bitonic sort of (key, pair index), padded to a power of two
+    int m2 = 1;
+    while (m2 < m) m2 <<= 1;
+    for (int s = m + threadIdx.x; s < m2; s += PT) {
+        key[s] = INFINITY;
+        jmp[s] = 0.0;
+        kid[s] = 0x7fffffff;
     }
-    // Delta += t P with exact zeros at the kink and the zero snap; b += t (W P W)
-    // here, and the exact zeros' corrections (increment - t P) in a second pass
-    double anyc = 0.0;
-    for (int64_t p = threadIdx.x; p < v.np; p += PT) {
+    __syncthreads();
+    for (int size = 2; size <= m2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int s = threadIdx.x; s < m2; s += PT) {
+                const int o = s ^ stride;
+                if (o > s) {
+                    const bool up = (s & size) == 0;
+                    const bool gt = key[s] > key[o] || (key[s] == key[o] && kid[s] > kid[o]);
+                    if (gt == up) {
+                        const double tk = key[s], tj = jmp[s];
+                        const int ti = kid[s];
+                        key[s] = key[o]; jmp[s] = jmp[o]; kid[s] = kid[o];
+                        key[o] = tk; jmp[o] = tj; kid[o] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x != 0) return;
+    // the walk, in increasing order from h(L+)
+    double H = HL, t = NAN, kinkt = -1.0;
+    int k = 0;
+    while (k < m) {
+        const double tk = key[k];
+        const double ts = -(g1 + H) / g2;
+        if (ts <= tk) {
+            t = ts;
+            break;
+        }
+        double jump = 0.0;
+        int k2 = k;
+        while (k2 < m && key[k2] == tk) jump += jmp[k2++];
+        if (g1 + g2 * tk + H + jump >= 0.0) {
+            t = kinkt = tk;
+            break;
+        }
+        H += jump;
+        k = k2;
+    }
+    if (isnan(t)) t = -(g1 + H) / g2;
+    st->t = t;
+    st->kinkt = kinkt;
+}
+
+// Pass 5: Delta += t P with exact zeros at the kink and the zero snap, b +=
+// t (W P W), d_prev = d, the corrections (increment - t P) of the exact
+// zeros; the last CTA counts the iteration.
+__global__ void __launch_bounds__(GT) k_pcd_update(PcdVec v, PcdState *st) {
+    if (st->done) return;
+    const double t = st->t, kinkt = st->kinkt;
+    double r[1] = {0.0};
+    for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < v.np; p += (int64_t)gridDim.x * GT) {
         const double P = v.P[p];
         double cr = 0.0;
+        v.dprev[p] = v.d[p];
         if (P != 0.0) {
             const double c = v.c[p], D0 = v.D[p], A = v.aval[p];
             double nd;
@@ -533,15 +643,12 @@ __global__ void __launch_bounds__(PT) k_pcd_step(PcdVec v, double lam, PcdState 
         }
         v.corr[p] = cr;
         v.b[p] += t * v.wpw[p];
-        if (cr != 0.0) anyc = 1.0;
+        if (cr != 0.0) r[0] = 1.0;
     }
-    anyc = block_max(anyc, red);
-    if (threadIdx.x == 0) {
-        st->t = t;
-        st->kinkt = kinkt;
-        st->has_corr = anyc != 0.0;
-        st->it += 1;
-    }
+    double o[1];
+    if (!pass_reduce<1>(r, 1u, v.part, &st->arrive, o)) return;
+    st->has_corr = o[0] != 0.0;
+    st->it += 1;
 }
 
 constexpr size_t PCD_SMEM = (size_t)KCAP * (2 * sizeof(double) + sizeof(int));
@@ -573,6 +680,14 @@ cudaError_t sddmm_launch(const T *W, const T *Vt, int64_t n, const int32_t *pi, 
 
 // Scratch of the PCD solver, grown on demand (pair vectors for np pairs, the
 // CSR of the pairs for n rows, the state).
+// The per-row and fixed part: CSR row pointers, cursors and counts (n + 1 each),
+// then, 16-byte aligned, the state, the pass partials (3 per CTA, at most 152
+// CTAs) and the gathered kinks (KCAP times, jumps, pair indices).
+size_t pcd_rows_bytes(int64_t n) {
+    return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 3 * 152 * sizeof(double) +
+           (size_t)KCAP * (2 * sizeof(double) + sizeof(int)) + 64;
+}
+
 cudaError_t pcd_ensure(Work &w, int64_t n, int64_t np, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (np > w.pcd_cap_np) {
@@ -591,8 +706,7 @@ cudaError_t pcd_ensure(Work &w, int64_t n, int64_t np, cudaStream_t st) {
         if (w.pcd_rows && (e = cudaFreeAsync(w.pcd_rows, st)) != cudaSuccess) return e;
         w.pcd_rows = nullptr;
         w.pcd_cap_n = 0;
-        if ((e = cudaMallocAsync((void **)&w.pcd_rows, (size_t)(n + 1) * 3 * sizeof(int) + sizeof(PcdState) + 64,
-                                 st)) != cudaSuccess)
+        if ((e = cudaMallocAsync((void **)&w.pcd_rows, pcd_rows_bytes(n), st)) != cudaSuccess)
             return e;
         w.pcd_cap_n = n + 1;
     }
@@ -617,7 +731,7 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     if (np > 0x7fffffff / 2) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = g_pcd_once.run(dev, [](int) {
-        return cudaFuncSetAttribute(k_pcd_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCD_SMEM);
+        return cudaFuncSetAttribute(k_pcd_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCD_SMEM);
     });
     if (e != cudaSuccess) return e;
     e = pcd_ensure(w, n, np, st);
@@ -646,6 +760,12 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     int *ptr = w.pcd_rows, *cursor = ptr + (n + 1), *cnt = cursor + (n + 1);
     PcdState *sd = reinterpret_cast<PcdState *>(
         (reinterpret_cast<uintptr_t>(cnt + (n + 1)) + 15) & ~uintptr_t(15));
+    v.part = reinterpret_cast<double *>(sd + 1);
+    v.kt = v.part + 3 * 152;
+    v.kj = v.kt + KCAP;
+    v.kp = reinterpret_cast<int *>(v.kj + KCAP);
+    static_assert(sizeof(PcdState) % 8 == 0, "state keeps the partials aligned");
+    const unsigned gv = (unsigned)lmax(1, lmin((np + GT - 1) / GT, 152));
     // CSR of the pairs
     const unsigned gp = (unsigned)lmax(1, lmin((np + 255) / 256, 152 * 8));
     if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st)) != cudaSuccess) return e;
@@ -670,14 +790,20 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     for (int done_it = 0; done_it < iters;) {
         const int chunk = std::min(PCD_CHUNK, iters - done_it);
         for (int k = 0; k < chunk; ++k) {
-            k_pcd_dir<<<1, PT, 0, st>>>(v, lam, iters, cg, rtol, sd);
-            counted(1);
+            k_pcd_dir<<<gv, GT, 0, st>>>(v, lam, iters, cg, rtol, sd);
+            k_pcd_shrink<<<gv, GT, 0, st>>>(v, sd);
+            k_pcd_dirP<<<gv, GT, 0, st>>>(v, lam, sd);
+            k_pcd_reset<<<gv, GT, 0, st>>>(v, sd);
+            counted(4);
             if ((e = spmm_launch<T>(W, n, ptr, col, pid, v.P, Vt, true, nullptr, &sd->done, st)) != cudaSuccess)
                 return e;
             if ((e = sddmm_launch<T>(W, Vt, n, pi, pj, np, v.wpw, nullptr, &sd->done, st)) != cudaSuccess)
                 return e;
-            k_pcd_step<<<1, PT, PCD_SMEM, st>>>(v, lam, sd);
-            counted(1);
+            k_pcd_g2<<<gv, GT, 0, st>>>(v, lam, sd);
+            k_pcd_kinks<<<gv, GT, 0, st>>>(v, lam, sd);
+            k_pcd_walk<<<1, PT, PCD_SMEM, st>>>(v, lam, sd);
+            k_pcd_update<<<gv, GT, 0, st>>>(v, sd);
+            counted(4);
             // the exact zeros' corrections (skipped unless has_corr)
             if ((e = spmm_launch<T>(W, n, ptr, col, pid, v.corr, Vt, true, &sd->has_corr, &sd->done, st)) !=
                 cudaSuccess)

@@ -82,8 +82,13 @@ def test_pcd_cg_matches_oracle(ctx, n, m, lam, seed, gen, cycles, iters):
     D = torch.zeros(len(fi), dtype=torch.float64, device="cuda")
     U = torch.full((n, n), np.nan, dtype=torch.float64, device="cuda")  # not read
     k = ctx.pcd(Sd, Wd, Ad, lam, pi, pj, iters, D, U, cg=True)
-    assert k == k_ref
     D, U = D.cpu().numpy(), U.cpu().numpy()
+    if k != k_ref:
+        # only once the LASSO is solved to rounding, where the stopping rule
+        # (d = 0, or a zero step) is decided by rounding noise: the oracle's own
+        # direction at the GPU's Delta then vanishes to rounding
+        d_chk, _ = oracle.pcd_direction(S, W, A, lam, fi, fj, D=D, U=U)
+        assert np.abs(d_chk).max() <= 1e-12 * np.abs(D_ref).max(), (k, k_ref)
     scale = max(np.abs(D_ref).max(), 1e-300)
     assert np.abs(D - D_ref).max() <= 1e-9 * scale
     assert np.abs(U - U_ref).max() <= 1e-9 * max(np.abs(U_ref).max(), 1e-300)
@@ -164,19 +169,26 @@ SOLVES = [
 def test_solve_with_pcd_cg_inner_matches_oracle(request, precision, gen, n, m, lam, seed):
     """Whole ML-cycle solves with PCD-CG as the Newton-direction solver (to
     Section 8's relative precision 1e-4) against the oracle's run of the same
-    method: the FP64 path makes the same relaxations; both reach the unique
-    minimiser (entries 1e-7, support up to the lambda border, objective 1e-9;
-    the mixed path's reported objective 1e-7, its A's objective 1e-9)."""
+    method.  To rel. KKT 1e-6 the FP64 path takes the oracle's relaxations and
+    ends at its objective.  To 1e-10 both paths reach the unique minimiser
+    (entries 1e-7, support up to the lambda border, objective 1e-9; the mixed
+    path's reported objective 1e-7, its A's objective 1e-9).  The relaxation
+    count to 1e-10 is not compared: near the minimiser the inner solver's
+    relative stopping rule can leave a coordinate a rounding-sized step past
+    its kink, and how many relaxations its removal takes depends on rounding."""
     c = request.getfixturevalue("mctx" if precision == "mixed" else "ctx")
     p = synth.random_problem(n, m, lam, seed, gen=gen)
     S = oracle.form_S(p.X)
+    if precision == "fp64":
+        A6, _, i6, _ = oracle.solve(S, lam, tol=1e-6, inner="pcd_cg")
+        B6, _, g6 = c.solve(S, lam, tol=1e-6, inner="pcd_cg")
+        assert g6["status"] == 0 and g6["relaxations"] == i6["relaxations"], (g6, i6)
+        assert abs(g6["objective"] - i6["objective"]) <= 1e-9 * abs(i6["objective"])
     A_ref, W_ref, info_ref, _ = oracle.solve(S, lam, tol=1e-10, inner="pcd_cg")
     assert info_ref["status"] == 0
     A, _, info = c.solve(S, lam, tol=1e-10, inner="pcd_cg")
     assert info["status"] == 0, info
-    assert info["inner_iters"] > 0
-    if precision == "fp64":
-        assert info["relaxations"] == info_ref["relaxations"]
+    assert info["inner_iters"] > 0 and info["rel_kkt"] <= 1e-10
     assert np.abs(A - A_ref).max() <= 1e-7
     border = np.abs(np.abs(S - W_ref) - lam) <= 1e-7
     assert not np.any(((A != 0) != (A_ref != 0)) & ~border)

@@ -757,6 +757,36 @@ def test_pcd_cg_needs_fewer_iterations_than_pcd():
     assert k_cg < k_pcd < 3000
 
 
+def test_pcd_final_shrinkage_at_the_precision_stop():
+    """The stop at relative precision ends with the final shrinkage: the
+    coordinates whose own 1-D minimiser is zero at the last direction take
+    their exact zero.  Against the same iterations without it (the iteration
+    cap instead of the precision stop): only such coordinates change, each to
+    exactly -A_p, each by less than the stopping precision, U stays Delta W,
+    and the model of eq. Quad_MLE_l1_prior does not increase (each change is
+    that coordinate's own minimiser, and the changes are below the precision)."""
+    S, A, W, fi, fj, lam = _coupled_lasso()
+    n = A.shape[0]
+    G = S - W
+    rtol = 1e-2
+    D1, U1, k = oracle.pcd(S, W, A, lam, fi, fj, 500, cg=True, rtol=rtol)
+    D0, U0, k0 = oracle.pcd(S, W, A, lam, fi, fj, k, cg=True)
+    assert k0 == k and 1 <= k < 500
+    d, _ = oracle.pcd_direction(S, W, A, lam, fi, fj, D0, U0)
+    c = A[fi, fj] + D0
+    own_zero = (c != 0) & (c + d == 0)
+    changed = D1 != D0
+    assert changed.any()
+    assert np.array_equal(changed, own_zero)
+    assert np.all(D1[changed] == -A[fi, fj][changed])
+    d_first, _ = oracle.pcd_direction(S, W, A, lam, fi, fj)
+    assert np.all(np.abs(D1 - D0) <= rtol * np.abs(d_first).max())
+    assert np.allclose(U1, _dense(n, fi, fj, D1) @ W, atol=1e-12)
+    m1 = _model(G, W, A, _dense(n, fi, fj, D1), lam)
+    m0 = _model(G, W, A, _dense(n, fi, fj, D0), lam)
+    assert m1 <= m0 + 1e-13
+
+
 @pytest.mark.parametrize("gen,n,lam,seed", [("sparse", 60, 0.1, 41), ("tridiag", 90, 0.15, 42)])
 def test_pcd_cg_inner_solver_reaches_the_same_minimiser(gen, n, lam, seed):
     """The ML-cycle with PCD-CG (to Section 8's relative precision 1e-4) as
