@@ -635,6 +635,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path whose solves/s is `value` (the other one is timed beside it)")
+    ap.add_argument("--inner", default="cd", choices=["cd", "pcd_cg"],
+                    help="Newton-direction solver of the timed solves (the other is timed beside it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=0,
@@ -697,7 +699,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        _, _, info = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out)
+        _, _, info = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner)
         return info
 
     for _ in range(max(args.warmup, 3)):
@@ -738,14 +740,14 @@ def main():
         octx.set_stream(stream.cuda_stream)
         oinfo = None
         for _ in range(2):
-            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out)
+            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner)
         olat = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out)
+            _, _, oinfo = octx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner)
             e1.record(stream)
             torch.cuda.synchronize()
             olat.append(e0.elapsed_time(e1))
@@ -782,7 +784,7 @@ def main():
                                 ("continuation", True, True)):
             linfo = None
             for _ in range(2):
-                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one,
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner, one_level=one,
                                         continuation=cont)
             llat = []
             for _ in range(args.steps):
@@ -790,7 +792,7 @@ def main():
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, one_level=one,
+                _, _, linfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner, one_level=one,
                                         continuation=cont)
                 e1.record(stream)
                 torch.cuda.synchronize()
@@ -803,41 +805,44 @@ def main():
         # in closed form, the other vertices as one sub-problem (same minimiser)
         sinfo = None
         for _ in range(2):
-            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, screen=True)
+            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner, screen=True)
         slat = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, screen=True)
+            _, _, sinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=args.inner, screen=True)
             e1.record(stream)
             torch.cuda.synchronize()
             slat.append(e0.elapsed_time(e1))
         compare["screened"] = {"ms_per_solve": float(np.mean(slat)), "components": sinfo["components"],
                                "max_block": sinfo["max_block"], "relaxations": sinfo["relaxations"],
                                "nnz": sinfo["nnz"], "objective": sinfo["objective"]}
-        # the Newton-direction solver: CD sweeps (the headline) against PCD-CG
-        # to Section 8's relative precision 1e-4, same input and protocol
+        # the Newton-direction solver: CD sweeps against PCD-CG to Section 8's
+        # relative precision 1e-4, same input and protocol (the timed one above,
+        # the other one here)
+        oinner = "pcd_cg" if args.inner == "cd" else "cd"
         pinfo = None
         for _ in range(2):
-            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner="pcd_cg")
+            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=oinner)
         plat = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner="pcd_cg")
+            _, _, pinfo = ctx.solve(S, p.lam, tol=p.tol, A_out=A_out, inner=oinner)
             e1.record(stream)
             torch.cuda.synchronize()
             plat.append(e0.elapsed_time(e1))
         compare["inner"] = {
-            "cd": {"ms_per_solve": total_ms / args.steps, "relaxations": infos[-1]["relaxations"],
-                   "inner_iters": infos[-1]["inner_iters"], "objective": infos[-1]["objective"]},
-            "pcd_cg": {"ms_per_solve": float(np.mean(plat)), "relaxations": pinfo["relaxations"],
-                       "inner_iters": pinfo["inner_iters"], "rel_kkt": pinfo["rel_kkt"],
-                       "objective": pinfo["objective"], "status": pinfo["status"]}}
+            args.inner: {"ms_per_solve": total_ms / args.steps, "relaxations": infos[-1]["relaxations"],
+                         "inner_iters": infos[-1]["inner_iters"], "rel_kkt": infos[-1]["rel_kkt"],
+                         "objective": infos[-1]["objective"], "timed": True},
+            oinner: {"ms_per_solve": float(np.mean(plat)), "relaxations": pinfo["relaxations"],
+                     "inner_iters": pinfo["inner_iters"], "rel_kkt": pinfo["rel_kkt"],
+                     "objective": pinfo["objective"], "status": pinfo["status"]}}
 
     # end to end through the public API with host buffers (pinned): S in, A out
     Sh = S.cpu().pin_memory().numpy()
@@ -845,7 +850,7 @@ def main():
     e2e = []
     for _ in range(args.e2e_steps if args.e2e_steps > 0 else args.steps):
         t0 = time.perf_counter()
-        ctx.solve(Sh, p.lam, tol=p.tol, A_out=Ah)
+        ctx.solve(Sh, p.lam, tol=p.tol, A_out=Ah, inner=args.inner)
         e2e.append(time.perf_counter() - t0)
     _, e2e_value = job_value(sum(e2e) * 1e3, len(e2e), world, dev)
 
@@ -911,7 +916,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol, "input": "S (fp64) given",
-                   "precision": args.precision, "l2": "flushed between timed steps (512 MB write)",
+                   "precision": args.precision, "inner": args.inner,
+                   "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(np.mean(lat))},

@@ -480,8 +480,13 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             if (sv.inner == GLASSO_INNER_PCD_CG) {
                 // PCD-CG to relative precision 1e-4 (Section 8); T is free until the line search
                 int its = 0;
-                CK(pcd(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1, kPcdRtol, w.D, w.U,
-                       w.T, false, w, st, &its));
+                const cudaError_t pe = pcd(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1,
+                                           kPcdRtol, w.D, w.U, w.T, false, w, st, &its);
+                if (pe == cudaErrorLaunchTimeout) {
+                    err = "PCD-CG: a bounded grid-barrier wait expired";
+                    return GLASSO_ETIMEOUT;
+                }
+                CK(pe);
                 inner_iters += its;
                 sv.mark_end(3, eb, (double)its * pcd_bytes(np, nd, 8.0));
             } else {
@@ -789,8 +794,13 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             if (sv.inner == GLASSO_INNER_PCD_CG) {
                 // PCD-CG with FP32 products (T's FP32 halves are free until the next refinement)
                 int its = 0;
-                CK(pcd32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1, kPcdRtol, w.D,
-                         U32, (float *)w.T, false, w, st, &its));
+                const cudaError_t pe = pcd32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1,
+                                             kPcdRtol, w.D, U32, (float *)w.T, false, w, st, &its);
+                if (pe == cudaErrorLaunchTimeout) {
+                    err = "PCD-CG: a bounded grid-barrier wait expired";
+                    return GLASSO_ETIMEOUT;
+                }
+                CK(pe);
                 inner_iters += its;
                 sv.mark_end(3, eb, (double)its * pcd_bytes(np, nd, 4.0));
             } else {
@@ -1791,12 +1801,22 @@ glasso_status glasso_pcd(glasso_ctx *ctx, const double *S, const double *W, cons
         float *W32 = reinterpret_cast<float *>(w.L), *U32 = reinterpret_cast<float *>(w.W);
         float *Vt = reinterpret_cast<float *>(w.T);
         CTX_CK(to_f32(W, W32, nn, st));
-        CTX_CK(pcd32(W32, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D, U32, Vt, true, w,
-                     st, &its));
+        const cudaError_t pe = pcd32(W32, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D,
+                                     U32, Vt, true, w, st, &its);
+        if (pe == cudaErrorLaunchTimeout) {
+            ctx->last_error = "PCD-CG: a bounded grid-barrier wait expired";
+            return GLASSO_ETIMEOUT;
+        }
+        CTX_CK(pe);
         CTX_CK(to_f64(U32, U, nn, st));
     } else {
-        CTX_CK(pcd(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D, U, w.T, true, w, st,
-                   &its));
+        const cudaError_t pe = pcd(W, n, lambda, pi, pj, np, w.p_inva, w.p_g, w.p_a, iters, cg, rtol, D, U, w.T,
+                                   true, w, st, &its);
+        if (pe == cudaErrorLaunchTimeout) {
+            ctx->last_error = "PCD-CG: a bounded grid-barrier wait expired";
+            return GLASSO_ETIMEOUT;
+        }
+        CTX_CK(pe);
     }
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;
