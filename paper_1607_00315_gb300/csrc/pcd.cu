@@ -48,7 +48,8 @@
 namespace glx {
 namespace {
 
-constexpr int PT = 256;           // threads of a CTA of the persistent kernel
+constexpr int PT = 512;           // threads of a CTA of the persistent kernel
+constexpr int PW = PT / 32;       // its warps
 constexpr int KCAP = 4096;        // kinks sorted in shared memory
 constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
@@ -179,7 +180,7 @@ __global__ void k_csr_sort(const int *__restrict__ ptr, int64_t n, int *__restri
 // is.  Zero values are skipped.  Tiles are taken from `first` in steps of
 // `step` (a grid-stride loop).
 template <typename T, bool TRANS>
-__device__ void spmm_tiles(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
+__device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
                            const int *__restrict__ col, const int *__restrict__ pid,
                            const double *__restrict__ x, T *__restrict__ out, int64_t first, int64_t step,
                            T (*tile)[SP_COLS + 1]) {
@@ -193,13 +194,24 @@ __device__ void spmm_tiles(const T *__restrict__ W, int64_t n, const int *__rest
 #pragma unroll
             for (int m = 0; m < SP_COLS / 32; ++m) acc[m] = T(0);
             if (r < n) {
-                for (int q = ptr[r], qe = ptr[r + 1]; q < qe; ++q) {
-                    const T v = (T)__ldcg(x + pid[q]);  // x may come from other CTAs of the launch
-                    if (v == T(0)) continue;
-                    const T *wr = W + (int64_t)col[q] * n + k0 + lane;
+                // four entries at a time, all their loads issued before the products
+                // (x may come from other CTAs of the launch: read through L2)
+                const int qb = ptr[r], qe = ptr[r + 1];
+                for (int q0 = qb; q0 < qe; q0 += 4) {
+                    T vv[4], wv[4][SP_COLS / 32];
 #pragma unroll
-                    for (int m = 0; m < SP_COLS / 32; ++m)
-                        if (k0 + lane + 32 * m < n) acc[m] = fma(v, wr[32 * m], acc[m]);
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u;
+                        vv[u] = q < qe ? (T)__ldcg(x + pid[q]) : T(0);
+                        const T *wr = W + (int64_t)(q < qe ? col[q] : 0) * n + k0 + lane;
+#pragma unroll
+                        for (int m = 0; m < SP_COLS / 32; ++m)
+                            wv[u][m] = (vv[u] != T(0) && k0 + lane + 32 * m < n) ? wr[32 * m] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int m = 0; m < SP_COLS / 32; ++m) acc[m] = fma(vv[u], wv[u][m], acc[m]);
                 }
             }
             if (TRANS) {
@@ -226,21 +238,25 @@ __device__ void spmm_tiles(const T *__restrict__ W, int64_t n, const int *__rest
 // out_p = W_{i,:} . Vt_{j,:} (= (W X W)_ij for Vt = (X W)^T): one warp per pair
 // (warps numbered w0, w0 + nw, ...), lanes over the row, sum in T.
 template <typename T>
-__device__ void sddmm_pairs(const T *__restrict__ W, const T *__restrict__ Vt, int64_t n,
+__device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__restrict__ Vt, int64_t n,
                             const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
                             double *__restrict__ out, int64_t w0, int64_t nw) {
     const int lane = threadIdx.x & 31;
     for (int64_t p = w0; p < np; p += nw) {
         const T *a = W + (int64_t)pi[p] * n, *b = Vt + (int64_t)pj[p] * n;
-        T s0 = T(0), s1 = T(0);
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         int64_t k = lane;
-        // (Vt may come from other CTAs of the launch: read through L2)
-        for (; k + 32 < n; k += 64) {
-            s0 = fma(a[k], __ldcg(b + k), s0);
-            s1 = fma(a[k + 32], __ldcg(b + k + 32), s1);
+        // four independent sums (Vt may come from other CTAs of the launch: read through L2)
+        for (; k + 96 < n; k += 128) {
+            const T a0 = a[k], a1 = a[k + 32], a2 = a[k + 64], a3 = a[k + 96];
+            const T b0 = __ldcg(b + k), b1 = __ldcg(b + k + 32), b2 = __ldcg(b + k + 64), b3 = __ldcg(b + k + 96);
+            s0 = fma(a0, b0, s0);
+            s1 = fma(a1, b1, s1);
+            s2 = fma(a2, b2, s2);
+            s3 = fma(a3, b3, s3);
         }
-        if (k < n) s0 = fma(a[k], __ldcg(b + k), s0);
-        T s = s0 + s1;
+        for (; k < n; k += 32) s0 = fma(a[k], __ldcg(b + k), s0);
+        T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) out[p] = (double)s;
@@ -338,15 +354,15 @@ __device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv,
             const double y = __shfl_xor_sync(0xffffffffu, x, o);
             x = mx ? fmax(x, y) : x + y;
         }
-        if (lane == 0) red[k * 8 + warp] = x;
+        if (lane == 0) red[k * PW + warp] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const bool mx = (maxmask >> k) & 1u;
-            double x = red[k * 8];
-            for (int w = 1; w < nwarp; ++w) x = mx ? fmax(x, red[k * 8 + w]) : x + red[k * 8 + w];
+            double x = red[k * PW];
+            for (int w = 1; w < nwarp; ++w) x = mx ? fmax(x, red[k * PW + w]) : x + red[k * PW + w];
             part[blockIdx.x * 4 + k] = x;
         }
     }
@@ -377,7 +393,7 @@ __device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv,
 // lambda sum_p w_p P_p sign(c_p + t P_p) (sign(P_p) where c_p + t P_p = 0) and
 // the number of kinks in (L, R], over one thread's share of all pairs (CTA 0's
 // fallback for more than KCAP kinks).
-__device__ void slope_and_kinks(const PcdVec &v, double lam, double t, double L, double R, double &h,
+__device__ __noinline__ void slope_and_kinks(const PcdVec &v, double lam, double t, double L, double R, double &h,
                                 double &cnt) {
     h = 0.0;
     cnt = 0.0;
@@ -399,7 +415,7 @@ __device__ void slope_and_kinks(const PcdVec &v, double lam, double t, double L,
 // h(L+).  L = 0 and the nk kinks gathered in (0, R] when they fit; else the
 // interval is first halved (bit-pattern bisection on the sign of phi') over
 // all pairs until its kinks fit, or until it holds a single kink value.
-__device__ void pcd_walk(const PcdVec &v, double lam, double g1, double g2, double h0, double R, int nk,
+__device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, double g2, double h0, double R, int nk,
                          double *key, double *jmp, int *kid, double *red, double &t_out, double &kink_out) {
     __shared__ int nkink;
     double L = 0.0, HL = h0;
@@ -530,12 +546,12 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
                                                         PcdVec v, int iters, int cg, double rtol, PcdState *st) {
     extern __shared__ __align__(16) unsigned char pcd_smem[];
     __shared__ T tile[SP_ROWS][SP_COLS + 1];
-    __shared__ double red[40], bc[4];
+    __shared__ double red[4 * PW + 8], bc[4];
     const unsigned G = gridDim.x;
     unsigned epoch = 0, nred = 0;
     const int64_t np = v.np;
     const int64_t lo = np * blockIdx.x / G, hi = np * (blockIdx.x + 1) / G;
-    const int64_t gw0 = (int64_t)blockIdx.x * (PT / 32) + (threadIdx.x >> 5), gnw = (int64_t)G * (PT / 32);
+    const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
     int it = 0;
     double d0max = 0.0;
     bool ok = true;
