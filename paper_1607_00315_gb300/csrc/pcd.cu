@@ -57,7 +57,7 @@ constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
 struct PcdState {
     int done;        // the stopping rule fired
     int it;          // iterations completed
-    int nk;          // kinks gathered in (0, R]
+    int pad0;
     int err;         // a bounded grid-barrier wait expired
     unsigned bar;    // grid barrier arrivals
     int pad;
@@ -240,7 +240,8 @@ __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, cons
 template <typename T>
 __device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__restrict__ Vt, int64_t n,
                             const int32_t *__restrict__ pi, const int32_t *__restrict__ pj, int64_t np,
-                            double *__restrict__ out, int64_t w0, int64_t nw) {
+                            double *__restrict__ out, int64_t w0, int64_t nw, const double *__restrict__ P,
+                            double *g2) {
     const int lane = threadIdx.x & 31;
     for (int64_t p = w0; p < np; p += nw) {
         const T *a = W + (int64_t)pi[p] * n, *b = Vt + (int64_t)pj[p] * n;
@@ -259,7 +260,11 @@ __device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__res
         T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out[p] = (double)s;
+        if (lane == 0) {
+            out[p] = (double)s;
+            // g2 += w_p P_p (W P W)_p, P from other CTAs of the launch (lane 0 only)
+            if (g2) *g2 += (pi[p] == pj[p] ? 1.0 : 2.0) * __ldcg(P + p) * (double)s;
+        }
     }
 }
 
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(256) k_pair_sddmm(const T *__restrict__ W, con
                                                     const int32_t *__restrict__ pj, int64_t np,
                                                     double *__restrict__ out) {
     sddmm_pairs<T>(W, Vt, n, pi, pj, np, out, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5),
-                   (int64_t)gridDim.x * 8);
+                   (int64_t)gridDim.x * 8, nullptr, nullptr);
 }
 
 __global__ void k_vec_add(double *__restrict__ b, const double *__restrict__ add, int64_t np) {
@@ -296,8 +301,6 @@ struct PcdVec {
     uint8_t *zt;
     int64_t np;
     double *part;      // 2 x 4 partials per CTA (alternating between reductions)
-    double *kt, *kj;   // gathered kinks: times and jumps (KCAP)
-    int *kp;           //                  pair indices
 };
 
 __device__ __forceinline__ double pair_w(const PcdVec &v, int64_t p) { return v.pi[p] == v.pj[p] ? 1.0 : 2.0; }
@@ -342,27 +345,31 @@ __device__ bool pcd_barrier(PcdState *st, unsigned G, unsigned &epoch) {
 // combines all partials in CTA order, so all take the same totals.
 template <int NV>
 __device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv, PcdState *st, unsigned G,
-                            unsigned &epoch, unsigned &nred, double *red, double *bc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+                            unsigned &epoch, unsigned &nred, double *red, double *bc, int nact) {
+    // only the first nact warps hold values (the others skip the FP64 shuffles,
+    // which cost a warp's issue slots on this GPU whatever the values)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *part = pv.part + (size_t)(nred++ & 1u) * 4 * G;
+    if (warp < nact) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const bool mx = (maxmask >> k) & 1u;
-        double x = v[k];
+        for (int k = 0; k < NV; ++k) {
+            const bool mx = (maxmask >> k) & 1u;
+            double x = v[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = mx ? fmax(x, y) : x + y;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = mx ? fmax(x, y) : x + y;
+            }
+            if (lane == 0) red[k * PW + warp] = x;
         }
-        if (lane == 0) red[k * PW + warp] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const bool mx = (maxmask >> k) & 1u;
-            double x = red[k * PW];
-            for (int w = 1; w < nwarp; ++w) x = mx ? fmax(x, red[k * PW + w]) : x + red[k * PW + w];
+            double x = mx ? 0.0 : 0.0;  // every max slot here is of non-negative values
+            for (int w = 0; w < nact; ++w) x = mx ? fmax(x, red[k * PW + w]) : x + red[k * PW + w];
             part[blockIdx.x * 4 + k] = x;
         }
     }
@@ -411,44 +418,18 @@ __device__ __noinline__ void slope_and_kinks(const PcdVec &v, double lam, double
 }
 
 // The exact step, in CTA 0 (dynamic shared memory: KCAP keys, jumps and pair
-// indices): sort the kinks of (L, R] and walk them in increasing order from
-// h(L+).  L = 0 and the nk kinks gathered in (0, R] when they fit; else the
-// interval is first halved (bit-pattern bisection on the sign of phi') over
-// all pairs until its kinks fit, or until it holds a single kink value.
-__device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, double g2, double h0, double R, int nk,
-                         double *key, double *jmp, int *kid, double *red, double &t_out, double &kink_out) {
+// indices): gather the kinks of (0, R] from all pairs, sort them and walk them
+// in increasing order from h(0+).  When more than KCAP lie in (0, R], the
+// interval (L, R] is first halved (bit-pattern bisection on the sign of
+// phi'(mid+)) until its kinks fit, or until it holds a single kink value, and
+// the walk starts from h(L+).
+__device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, double g2, double h0, double R,
+                                      double *key, double *jmp, int *kid, double *red, double &t_out,
+                                      double &kink_out) {
     __shared__ int nkink;
     double L = 0.0, HL = h0;
     bool group = false;  // (L, R] holds more than KCAP kinks, all at R
-    int m = nk;
-    if (m <= KCAP) {
-        for (int s = threadIdx.x; s < m; s += blockDim.x) {
-            key[s] = __ldcg(v.kt + s);
-            jmp[s] = __ldcg(v.kj + s);
-            kid[s] = __ldcg(v.kp + s);
-        }
-    } else {
-        for (int round = 0; round < 70; ++round) {
-            const long long lb = __double_as_longlong(L), rb = __double_as_longlong(R);
-            const double mid = __longlong_as_double(lb + (rb - lb) / 2);
-            if (!(mid > L && mid < R)) {
-                group = true;
-                break;
-            }
-            double hm, cm;
-            slope_and_kinks(v, lam, mid, mid, mid, hm, cm);
-            hm = block_sum(hm, red);
-            if (g1 + g2 * mid + hm >= 0.0) {
-                R = mid;
-            } else {
-                L = mid;
-                HL = hm;
-            }
-            double hh, cnt;
-            slope_and_kinks(v, lam, L, L, R, hh, cnt);
-            cnt = block_sum(cnt, red);
-            if (cnt <= (double)KCAP) break;
-        }
+    for (int pass = 0; pass < 2; ++pass) {
         if (threadIdx.x == 0) nkink = 0;
         __syncthreads();
         double gjump = 0.0;
@@ -484,9 +465,31 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
             return;
         }
         __syncthreads();
-        m = min(nkink, KCAP);
+        if (nkink <= KCAP) break;
+        // too many kinks: narrow (L, R], then gather again
+        for (int round = 0; round < 70; ++round) {
+            const long long lb = __double_as_longlong(L), rb = __double_as_longlong(R);
+            const double mid = __longlong_as_double(lb + (rb - lb) / 2);
+            if (!(mid > L && mid < R)) {
+                group = true;
+                break;
+            }
+            double hm, cm;
+            slope_and_kinks(v, lam, mid, mid, mid, hm, cm);
+            hm = block_sum(hm, red);
+            if (g1 + g2 * mid + hm >= 0.0) {
+                R = mid;
+            } else {
+                L = mid;
+                HL = hm;
+            }
+            double hh, cnt;
+            slope_and_kinks(v, lam, L, L, R, hh, cnt);
+            cnt = block_sum(cnt, red);
+            if (cnt <= (double)KCAP) break;
+        }
     }
-    __syncthreads();
+    const int m = min(nkink, KCAP);
     // bitonic sort of (key, pair index), padded to a power of two
     int m2 = 1;
     while (m2 < m) m2 <<= 1;
@@ -539,6 +542,10 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
 }
 
 // All PCD-CG iterations in one cooperative launch (see the top of the file).
+// Five grid barriers per iteration: the direction's reduction, the search
+// direction's, the SpMM, the SDDMM with g2, and the step from CTA 0.  The
+// corrections of an iteration's exact zeros are applied to b at the start of
+// the next one (only then are they needed).
 template <typename T>
 __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, T *__restrict__ Vt, int64_t n,
                                                         double lam, const int *__restrict__ ptr,
@@ -551,28 +558,45 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     unsigned epoch = 0, nred = 0;
     const int64_t np = v.np;
     const int64_t lo = np * blockIdx.x / G, hi = np * (blockIdx.x + 1) / G;
+    const int nact = (int)lmin(PW, (hi - lo + 31) / 32);  // warps holding pairs of this CTA's slice
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
     int it = 0;
     double d0max = 0.0;
-    bool ok = true;
+    bool corr_pending = false;  // this thread's pairs got corrections in the last update
     for (;;) {
         if (it >= iters) break;
-        // 1. direction, max |d| and the Polak-Ribiere sums
-        double r3[3] = {0.0, 0.0, 0.0};
-        for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
-            const double c = v.aval[p] + v.D[p];
-            const double dp = soft(c - v.b[p] * v.inva[p], lam * v.inva[p]) - c;
-            v.c[p] = c;
-            v.d[p] = dp;
-            r3[0] = fmax(r3[0], fabs(dp));
-            if (cg && it > 0) {
-                const double w = pair_w(v, p), dq = v.dprev[p];
-                r3[1] += w * dp * (dp - dq);
-                r3[2] += w * dq * dq;
+        // 1. direction, max |d| and the Polak-Ribiere sums (and whether the last
+        //    update left corrections of b to apply first)
+        double r4[4] = {0.0, 0.0, 0.0, corr_pending ? 1.0 : 0.0};
+        auto direction = [&](double (&r)[4]) {
+            for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
+                const double c = v.aval[p] + v.D[p];
+                const double dp = soft(c - v.b[p] * v.inva[p], lam * v.inva[p]) - c;
+                v.c[p] = c;
+                v.d[p] = dp;
+                r[0] = fmax(r[0], fabs(dp));
+                if (cg && it > 0) {
+                    const double w = pair_w(v, p), dq = v.dprev[p];
+                    r[1] += w * dp * (dp - dq);
+                    r[2] += w * dq * dq;
+                }
             }
+        };
+        direction(r4);
+        if (!grid_reduce<4>(r4, 9u, v, st, G, epoch, nred, red, bc, nact)) break;
+        if (r4[3] != 0.0) {
+            // b += (W C W) for the last update's corrections C, then the direction again
+            spmm_tiles<T, true>(W, n, ptr, col, pid, v.corr, Vt, blockIdx.x, G, tile);
+            if (!pcd_barrier(st, G, epoch)) break;
+            sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.tmp, gw0, gnw, nullptr, nullptr);
+            if (!pcd_barrier(st, G, epoch)) break;
+            for (int64_t p = lo + threadIdx.x; p < hi; p += PT) v.b[p] += __ldcg(v.tmp + p);
+            r4[0] = r4[1] = r4[2] = r4[3] = 0.0;
+            direction(r4);
+            if (!grid_reduce<4>(r4, 9u, v, st, G, epoch, nred, red, bc, nact)) break;
         }
-        if (!(ok = grid_reduce<3>(r3, 1u, v, st, G, epoch, nred, red, bc))) break;
-        const double dmax = r3[0];
+        corr_pending = false;
+        const double dmax = r4[0];
         if (dmax == 0.0) break;
         if (it > 0 && rtol > 0.0 && dmax <= rtol * d0max) {
             // the final shrinkage: own minimiser zero -> the exact zero
@@ -583,8 +607,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
             break;
         }
         if (it == 0) d0max = dmax;
-        const double beta = (cg && it > 0 && r3[2] > 0.0) ? fmax(0.0, r3[1] / r3[2]) : 0.0;
-        // 2. search direction, zero flags, g1 and the l1 slope at 0+
+        const double beta = (cg && it > 0 && r4[2] > 0.0) ? fmax(0.0, r4[1] / r4[2]) : 0.0;
+        // 2. search direction, zero flags, g1 and the l1 slope h(0+)
         double r2[2] = {0.0, 0.0};
         for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
             const double dp = v.d[p], c = v.c[p];
@@ -595,66 +619,41 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
             r2[0] += w * v.b[p] * P;
             if (P != 0.0) r2[1] += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
         }
-        if (!(ok = grid_reduce<2>(r2, 0u, v, st, G, epoch, nred, red, bc))) break;
-        double g1 = r2[0];
-        if (beta != 0.0 && g1 + r2[1] >= 0.0) {  // not a descent direction: the PCD direction
-            double r1[1] = {0.0};
+        if (!grid_reduce<2>(r2, 0u, v, st, G, epoch, nred, red, bc, nact)) break;
+        if (beta != 0.0 && r2[0] + r2[1] >= 0.0) {  // not a descent direction: the PCD direction
+            r2[0] = r2[1] = 0.0;
             for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
-                v.P[p] = v.d[p];
-                r1[0] += pair_w(v, p) * v.b[p] * v.d[p];
+                const double dp = v.d[p], c = v.c[p], w = pair_w(v, p);
+                v.P[p] = dp;
+                r2[0] += w * v.b[p] * dp;
+                if (dp != 0.0) r2[1] += lam * w * dp * (c != 0.0 ? sgnd(c) : sgnd(dp));
             }
-            if (!(ok = grid_reduce<1>(r1, 0u, v, st, G, epoch, nred, red, bc))) break;
-            g1 = r1[0];
+            if (!grid_reduce<2>(r2, 0u, v, st, G, epoch, nred, red, bc, nact)) break;
         }
-        // 3. (W P W) on the pairs
+        const double g1 = r2[0], h0 = r2[1];
+        // 3. (W P W) on the pairs, and g2 = <P, W P W>_w
         spmm_tiles<T, true>(W, n, ptr, col, pid, v.P, Vt, blockIdx.x, G, tile);
-        if (!(ok = pcd_barrier(st, G, epoch))) break;
-        sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.wpw, gw0, gnw);
-        if (!(ok = pcd_barrier(st, G, epoch))) break;
-        // 4. g2, h(0+), and the kinks below the bound R
-        r2[0] = r2[1] = 0.0;
-        for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
-            const double P = v.P[p];
-            if (P == 0.0) continue;
-            const double w = pair_w(v, p), c = v.c[p];
-            r2[0] += w * P * __ldcg(v.wpw + p);
-            r2[1] += lam * w * P * (c != 0.0 ? sgnd(c) : sgnd(P));
-        }
-        if (!(ok = grid_reduce<2>(r2, 0u, v, st, G, epoch, nred, red, bc))) break;
-        const double g2 = r2[0], h0 = r2[1];
+        if (!pcd_barrier(st, G, epoch)) break;
+        double r1[1] = {0.0};
+        sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.wpw, gw0, gnw, v.P, &r1[0]);
+        if (!grid_reduce<1>(r1, 0u, v, st, G, epoch, nred, red, bc, PW)) break;
+        const double g2 = r1[0];
         if (!(g2 > 0.0) || g1 + h0 >= 0.0) break;  // a zero step ends the iterations
-        const double R = -(g1 + h0) / g2;
-        for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
-            const double P = v.P[p], c = v.c[p];
-            if (P == 0.0 || c == 0.0 || sgnd(c) == sgnd(P)) continue;
-            const double tk = -c / P;
-            if (!(tk > 0.0 && tk <= R)) continue;
-            const int s = atomicAdd(&st->nk, 1);
-            if (s < KCAP) {
-                v.kt[s] = tk;
-                v.kj[s] = 2.0 * lam * pair_w(v, p) * fabs(P);
-                v.kp[s] = (int)p;
-            }
-        }
-        if (!(ok = pcd_barrier(st, G, epoch))) break;
-        // 5. the exact step (CTA 0)
+        // 4. the exact step (CTA 0)
         if (blockIdx.x == 0) {
             double *key = reinterpret_cast<double *>(pcd_smem);
             double *jmp = key + KCAP;
             int *kid = reinterpret_cast<int *>(jmp + KCAP);
-            const int nk = *reinterpret_cast<volatile int *>(&st->nk);
             double t, kinkt;
-            pcd_walk(v, lam, g1, g2, h0, R, nk, key, jmp, kid, red, t, kinkt);
+            pcd_walk(v, lam, g1, g2, h0, -(g1 + h0) / g2, key, jmp, kid, red, t, kinkt);
             if (threadIdx.x == 0) {
                 st->t = t;
                 st->kinkt = kinkt;
-                st->nk = 0;
             }
         }
-        if (!(ok = pcd_barrier(st, G, epoch))) break;
+        if (!pcd_barrier(st, G, epoch)) break;
         const double t = __ldcg(&st->t), kinkt = __ldcg(&st->kinkt);
-        // 6. Delta += t P with the exact zeros; b += t (W P W); corrections
-        double r1[1] = {0.0};
+        // 5. Delta += t P with the exact zeros; b += t (W P W); corrections
         for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
             const double P = v.P[p];
             double cr = 0.0;
@@ -678,19 +677,10 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
             }
             v.corr[p] = cr;
             v.b[p] += t * __ldcg(v.wpw + p);
-            if (cr != 0.0) r1[0] = 1.0;
+            if (cr != 0.0) corr_pending = true;
         }
-        if (!(ok = grid_reduce<1>(r1, 1u, v, st, G, epoch, nred, red, bc))) break;
         ++it;
-        if (r1[0] != 0.0) {  // b += (W C W) for the corrections C
-            spmm_tiles<T, true>(W, n, ptr, col, pid, v.corr, Vt, blockIdx.x, G, tile);
-            if (!(ok = pcd_barrier(st, G, epoch))) break;
-            sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.tmp, gw0, gnw);
-            if (!(ok = pcd_barrier(st, G, epoch))) break;
-            for (int64_t p = lo + threadIdx.x; p < hi; p += PT) v.b[p] += __ldcg(v.tmp + p);
-        }
     }
-    (void)ok;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->it = it;
         st->d0max = d0max;
@@ -704,13 +694,11 @@ OncePerDevice g_pcd_once[2];
 int g_pcd_nsm[2][kMaxDevices], g_pcd_occ[2][kMaxDevices];
 
 // The per-row and fixed part of the scratch: CSR row pointers, cursors and
-// counts (n + 1 each), then, 16-byte aligned, the state, the partials (2 x 4
-// per CTA, at most 152 x 4 CTAs) and the gathered kinks (KCAP times, jumps,
-// pair indices).
+// counts (n + 1 each), then, 16-byte aligned, the state and the partials (2 x 4
+// per CTA, at most 152 x 4 CTAs).
 constexpr int PCD_MAX_G = 152 * 4;
 size_t pcd_rows_bytes(int64_t n) {
-    return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 8 * PCD_MAX_G * sizeof(double) +
-           (size_t)KCAP * (2 * sizeof(double) + sizeof(int)) + 64;
+    return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 8 * PCD_MAX_G * sizeof(double) + 64;
 }
 
 cudaError_t pcd_ensure(Work &w, int64_t n, int64_t np, cudaStream_t st) {
@@ -794,9 +782,6 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
         (reinterpret_cast<uintptr_t>(cnt + (n + 1)) + 15) & ~uintptr_t(15));
     static_assert(sizeof(PcdState) % 8 == 0, "the state keeps the partials aligned");
     v.part = reinterpret_cast<double *>(sd + 1);
-    v.kt = v.part + 8 * PCD_MAX_G;
-    v.kj = v.kt + KCAP;
-    v.kp = reinterpret_cast<int *>(v.kj + KCAP);
     // CSR of the pairs
     const unsigned gp = (unsigned)lmax(1, lmin((np + 255) / 256, 152 * 8));
     if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st)) != cudaSuccess) return e;
