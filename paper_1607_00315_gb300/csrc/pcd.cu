@@ -53,11 +53,13 @@ constexpr int PW = PT / 32;       // its warps
 constexpr int KCAP = 4096;        // kinks sorted in shared memory
 constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
+constexpr int SP_RB = 8;          // rows of W held in shared memory by the persistent SpMM, at most
+constexpr size_t SP_WS_BYTES = 200 * 1024;  // shared memory for them
 
 struct PcdState {
     int done;        // the stopping rule fired
     int it;          // iterations completed
-    int pad0;
+    int nk;          // kinks gathered in (0, R]
     int err;         // a bounded grid-barrier wait expired
     unsigned bar;    // grid barrier arrivals
     int pad;
@@ -171,6 +173,24 @@ __global__ void k_csr_sort(const int *__restrict__ ptr, int64_t n, int *__restri
     }
 }
 
+// The CSR positions of each pair's entries: qi[p] in row pi[p], qj[p] in row
+// pj[p] (the same entry for a diagonal pair).
+__global__ void k_csr_pos(const int *__restrict__ ptr, int64_t n, const int *__restrict__ col,
+                          const int *__restrict__ pid, const int32_t *__restrict__ pi,
+                          const int32_t *__restrict__ pj, int *__restrict__ qi, int *__restrict__ qj) {
+    const int64_t nq = ptr[n];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int p = pid[q];
+        if (col[q] == pj[p]) {  // the entry in row pi[p]
+            qi[p] = (int)q;
+            if (pi[p] == pj[p]) qj[p] = (int)q;
+        } else {
+            qj[p] = (int)q;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- (W X W) on the pairs
 // V = X W for the symmetric X given on the pairs (values x, CSR pattern):
 // V_r = sum over the row's entries of x W_col.  A tile is a 32 x 128 block of
@@ -268,6 +288,54 @@ __device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__res
     }
 }
 
+// Vt = (X W)^T = W X with W held row by row in shared memory: Vt_{k,r} =
+// sum over row r's entries q of X_q W_{k, col_q}.  A CTA loads `rb` rows of W
+// (coalesced), then each thread forms Vt_{k, r} for its rows r and the rb
+// rows k from the entries' values vq (X in CSR entry order, so an entry's
+// column and value sit side by side) and shared-memory gathers; the stores
+// are coalesced along r.  Row blocks are taken from `first` in steps of
+// `step`.  (vq may come from other CTAs of the launch: read through L2.)
+template <typename T>
+__device__ __noinline__ void spmm_wrows(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
+                                        const int *__restrict__ col, const double *__restrict__ vq, T *__restrict__ Vt,
+                                        int rb, T *__restrict__ ws, int64_t first, int64_t step) {
+    const int64_t nrb = (n + rb - 1) / rb;
+    for (int64_t blk = first; blk < nrb; blk += step) {
+        const int64_t k0 = blk * rb;
+        const int nr = (int)lmin(rb, n - k0);
+        const T *src = W + k0 * n;
+        for (int64_t e = threadIdx.x; e < (int64_t)nr * n; e += blockDim.x) ws[e] = src[e];
+        __syncthreads();
+        for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+            T acc[SP_RB];
+#pragma unroll
+            for (int j = 0; j < SP_RB; ++j) acc[j] = T(0);
+            const int qb = ptr[r], qe = ptr[r + 1];
+            for (int q0 = qb; q0 < qe; q0 += 8) {
+                int cc[8];
+                T xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool in = q0 + u < qe;
+                    cc[u] = in ? col[q0 + u] : 0;
+                    xv[u] = in ? (T)__ldcg(vq + q0 + u) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (xv[u] == T(0)) continue;
+#pragma unroll
+                    for (int j = 0; j < SP_RB; ++j)
+                        if (j < nr) acc[j] = fma(xv[u], ws[(int64_t)j * n + cc[u]], acc[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < SP_RB; ++j)
+                if (j < nr) Vt[(k0 + j) * n + r] = acc[j];
+        }
+        __syncthreads();
+    }
+}
+
 // Stand-alone launches (the initial b from a given Delta, the final U).
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_pair_spmm(const T *__restrict__ W, int64_t n,
@@ -301,6 +369,10 @@ struct PcdVec {
     uint8_t *zt;
     int64_t np;
     double *part;      // 2 x 4 partials per CTA (alternating between reductions)
+    double *vq;        // the SpMM's values in CSR entry order (P, or the corrections)
+    const int *qi, *qj;  // each pair's two CSR positions
+    double *kt, *kj;   // kinks gathered in (0, R]: times and jumps (KCAP)
+    int *kp;           //                             pair indices
 };
 
 __device__ __forceinline__ double pair_w(const PcdVec &v, int64_t p) { return v.pi[p] == v.pj[p] ? 1.0 : 2.0; }
@@ -418,18 +490,27 @@ __device__ __noinline__ void slope_and_kinks(const PcdVec &v, double lam, double
 }
 
 // The exact step, in CTA 0 (dynamic shared memory: KCAP keys, jumps and pair
-// indices): gather the kinks of (0, R] from all pairs, sort them and walk them
-// in increasing order from h(0+).  When more than KCAP lie in (0, R], the
+// indices): sort the nk kinks of (0, R] gathered by all CTAs and walk them in
+// increasing order from h(0+).  When more than KCAP lie in (0, R], the
 // interval (L, R] is first halved (bit-pattern bisection on the sign of
-// phi'(mid+)) until its kinks fit, or until it holds a single kink value, and
-// the walk starts from h(L+).
+// phi'(mid+)) over all pairs until its kinks fit, or until it holds a single
+// kink value; they are gathered again and the walk starts from h(L+).
 __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, double g2, double h0, double R,
-                                      double *key, double *jmp, int *kid, double *red, double &t_out,
+                                      int nk, double *key, double *jmp, int *kid, double *red, double &t_out,
                                       double &kink_out) {
     __shared__ int nkink;
     double L = 0.0, HL = h0;
     bool group = false;  // (L, R] holds more than KCAP kinks, all at R
-    for (int pass = 0; pass < 2; ++pass) {
+    if (nk <= KCAP) {  // the kinks of (0, R], gathered by all CTAs
+        for (int s = threadIdx.x; s < nk; s += blockDim.x) {
+            key[s] = __ldcg(v.kt + s);
+            jmp[s] = __ldcg(v.kj + s);
+            kid[s] = __ldcg(v.kp + s);
+        }
+        if (threadIdx.x == 0) nkink = nk;
+        __syncthreads();
+    }
+    for (int pass = nk <= KCAP ? 2 : 0; pass < 2; ++pass) {
         if (threadIdx.x == 0) nkink = 0;
         __syncthreads();
         double gjump = 0.0;
@@ -542,17 +623,20 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
 }
 
 // All PCD-CG iterations in one cooperative launch (see the top of the file).
-// Five grid barriers per iteration: the direction's reduction, the search
-// direction's, the SpMM, the SDDMM with g2, and the step from CTA 0.  The
-// corrections of an iteration's exact zeros are applied to b at the start of
-// the next one (only then are they needed).
+// Six grid barriers per iteration: the direction's reduction, the search
+// direction's, the SpMM, the SDDMM with g2, the kink gather, and the step
+// from CTA 0.  The corrections of an iteration's exact zeros are applied to b
+// at the start of the next one (only then are they needed).  rb > 0: the
+// SpMM holds rb rows of W in shared memory (spmm_wrows); rb = 0 (rows too
+// long): the tiled SpMM.  The dynamic shared memory serves the SpMM and the
+// walk in turn.
 template <typename T>
 __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, T *__restrict__ Vt, int64_t n,
                                                         double lam, const int *__restrict__ ptr,
                                                         const int *__restrict__ col, const int *__restrict__ pid,
-                                                        PcdVec v, int iters, int cg, double rtol, PcdState *st) {
+                                                        PcdVec v, int iters, int cg, double rtol, int rb,
+                                                        PcdState *st) {
     extern __shared__ __align__(16) unsigned char pcd_smem[];
-    __shared__ T tile[SP_ROWS][SP_COLS + 1];
     __shared__ double red[4 * PW + 8], bc[4];
     const unsigned G = gridDim.x;
     unsigned epoch = 0, nred = 0;
@@ -560,6 +644,14 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     const int64_t lo = np * blockIdx.x / G, hi = np * (blockIdx.x + 1) / G;
     const int nact = (int)lmin(PW, (hi - lo + 31) / 32);  // warps holding pairs of this CTA's slice
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
+    T *ws = reinterpret_cast<T *>(pcd_smem);
+    auto spmm = [&](const double *xpair) {  // Vt = (X W)^T, X from vq (or the pair values)
+        if (rb > 0)
+            spmm_wrows<T>(W, n, ptr, col, v.vq, Vt, rb, ws, blockIdx.x, G);
+        else
+            spmm_tiles<T, true>(W, n, ptr, col, pid, xpair, Vt, blockIdx.x, G,
+                                reinterpret_cast<T(*)[SP_COLS + 1]>(pcd_smem));
+    };
     int it = 0;
     double d0max = 0.0;
     bool corr_pending = false;  // this thread's pairs got corrections in the last update
@@ -585,8 +677,9 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         direction(r4);
         if (!grid_reduce<4>(r4, 9u, v, st, G, epoch, nred, red, bc, nact)) break;
         if (r4[3] != 0.0) {
-            // b += (W C W) for the last update's corrections C, then the direction again
-            spmm_tiles<T, true>(W, n, ptr, col, pid, v.corr, Vt, blockIdx.x, G, tile);
+            // b += (W C W) for the last update's corrections C (in vq), then the
+            // direction again
+            spmm(v.corr);
             if (!pcd_barrier(st, G, epoch)) break;
             sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.tmp, gw0, gnw, nullptr, nullptr);
             if (!pcd_barrier(st, G, epoch)) break;
@@ -608,12 +701,15 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         }
         if (it == 0) d0max = dmax;
         const double beta = (cg && it > 0 && r4[2] > 0.0) ? fmax(0.0, r4[1] / r4[2]) : 0.0;
-        // 2. search direction, zero flags, g1 and the l1 slope h(0+)
+        // 2. search direction (also into vq for the SpMM), zero flags, g1 and
+        //    the l1 slope h(0+)
         double r2[2] = {0.0, 0.0};
         for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
             const double dp = v.d[p], c = v.c[p];
             const double P = dp + beta * v.P[p];
             v.P[p] = P;
+            v.vq[v.qi[p]] = P;
+            v.vq[v.qj[p]] = P;
             v.zt[p] = c + dp == 0.0;
             const double w = pair_w(v, p);
             r2[0] += w * v.b[p] * P;
@@ -625,6 +721,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
             for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
                 const double dp = v.d[p], c = v.c[p], w = pair_w(v, p);
                 v.P[p] = dp;
+                v.vq[v.qi[p]] = dp;
+                v.vq[v.qj[p]] = dp;
                 r2[0] += w * v.b[p] * dp;
                 if (dp != 0.0) r2[1] += lam * w * dp * (c != 0.0 ? sgnd(c) : sgnd(dp));
             }
@@ -632,28 +730,47 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         }
         const double g1 = r2[0], h0 = r2[1];
         // 3. (W P W) on the pairs, and g2 = <P, W P W>_w
-        spmm_tiles<T, true>(W, n, ptr, col, pid, v.P, Vt, blockIdx.x, G, tile);
+        spmm(v.P);
         if (!pcd_barrier(st, G, epoch)) break;
         double r1[1] = {0.0};
         sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.wpw, gw0, gnw, v.P, &r1[0]);
         if (!grid_reduce<1>(r1, 0u, v, st, G, epoch, nred, red, bc, PW)) break;
         const double g2 = r1[0];
         if (!(g2 > 0.0) || g1 + h0 >= 0.0) break;  // a zero step ends the iterations
-        // 4. the exact step (CTA 0)
+        const double R = -(g1 + h0) / g2;
+        // 4. the kinks t_p = -c_p / P_p in (0, R], gathered by all CTAs (a
+        //    division only for the candidates that a product test keeps)
+        for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
+            const double P = v.P[p], c = v.c[p];
+            if (P == 0.0 || c == 0.0 || sgnd(c) == sgnd(P)) continue;
+            if (fabs(c) > R * fabs(P) * (1.0 + 0x1p-40)) continue;
+            const double tk = -c / P;
+            if (!(tk > 0.0 && tk <= R)) continue;
+            const int s = atomicAdd(&st->nk, 1);
+            if (s < KCAP) {
+                v.kt[s] = tk;
+                v.kj[s] = 2.0 * lam * pair_w(v, p) * fabs(P);
+                v.kp[s] = (int)p;
+            }
+        }
+        if (!pcd_barrier(st, G, epoch)) break;
+        // 5. the exact step (CTA 0)
         if (blockIdx.x == 0) {
             double *key = reinterpret_cast<double *>(pcd_smem);
             double *jmp = key + KCAP;
             int *kid = reinterpret_cast<int *>(jmp + KCAP);
+            const int nk = *reinterpret_cast<volatile int *>(&st->nk);
             double t, kinkt;
-            pcd_walk(v, lam, g1, g2, h0, -(g1 + h0) / g2, key, jmp, kid, red, t, kinkt);
+            pcd_walk(v, lam, g1, g2, h0, R, nk, key, jmp, kid, red, t, kinkt);
             if (threadIdx.x == 0) {
                 st->t = t;
                 st->kinkt = kinkt;
+                st->nk = 0;
             }
         }
         if (!pcd_barrier(st, G, epoch)) break;
         const double t = __ldcg(&st->t), kinkt = __ldcg(&st->kinkt);
-        // 5. Delta += t P with the exact zeros; b += t (W P W); corrections
+        // 6. Delta += t P with the exact zeros; b += t (W P W); corrections (into vq)
         for (int64_t p = lo + threadIdx.x; p < hi; p += PT) {
             const double P = v.P[p];
             double cr = 0.0;
@@ -676,6 +793,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
                 if (special) cr = (nd - D0) - t * P;
             }
             v.corr[p] = cr;
+            v.vq[v.qi[p]] = cr;
+            v.vq[v.qj[p]] = cr;
             v.b[p] += t * __ldcg(v.wpw + p);
             if (cr != 0.0) corr_pending = true;
         }
@@ -689,29 +808,34 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
 }
 
 constexpr size_t PCD_SMEM = (size_t)KCAP * (2 * sizeof(double) + sizeof(int));
+constexpr size_t PCD_DYN_MAX = SP_WS_BYTES;  // the largest dynamic shared memory of k_pcd_persist
+static_assert(PCD_SMEM <= PCD_DYN_MAX, "the walk's arrays fit the dynamic shared memory");
 
 OncePerDevice g_pcd_once[2];
 int g_pcd_nsm[2][kMaxDevices], g_pcd_occ[2][kMaxDevices];
 
 // The per-row and fixed part of the scratch: CSR row pointers, cursors and
-// counts (n + 1 each), then, 16-byte aligned, the state and the partials (2 x 4
-// per CTA, at most 152 x 4 CTAs).
+// counts (n + 1 each), then, 16-byte aligned, the state, the partials (2 x 4
+// per CTA, at most 152 x 4 CTAs) and the gathered kinks (KCAP times, jumps,
+// pair indices).
 constexpr int PCD_MAX_G = 152 * 4;
 size_t pcd_rows_bytes(int64_t n) {
-    return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 8 * PCD_MAX_G * sizeof(double) + 64;
+    return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 8 * PCD_MAX_G * sizeof(double) +
+           (size_t)KCAP * (2 * sizeof(double) + sizeof(int)) + 64;
 }
 
 cudaError_t pcd_ensure(Work &w, int64_t n, int64_t np, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (np > w.pcd_cap_np) {
-        // 10 pair vectors of doubles (b, c, d, d_prev, P, W P W, corrections,
-        // scratch, spare x2), the CSR columns and pair indices (2 np ints each),
-        // the zero flags (np bytes)
+        // 8 pair vectors of doubles (b, c, d, d_prev, P, W P W, corrections,
+        // scratch), the SpMM's entry values (2 np doubles), the CSR columns
+        // and pair indices (2 np ints each), each pair's two CSR positions
+        // (np ints each), the zero flags (np bytes)
         const int64_t cap = std::max<int64_t>(np, 2 * w.pcd_cap_np);
         if (w.pcd_vec && (e = cudaFreeAsync(w.pcd_vec, st)) != cudaSuccess) return e;
         w.pcd_vec = nullptr;
         w.pcd_cap_np = 0;
-        const size_t bytes = (size_t)cap * (10 * sizeof(double) + 2 * 2 * sizeof(int) + 1) + 256;
+        const size_t bytes = (size_t)cap * (10 * sizeof(double) + 6 * sizeof(int) + 1) + 256;
         if ((e = cudaMallocAsync((void **)&w.pcd_vec, bytes, st)) != cudaSuccess) return e;
         w.pcd_cap_np = cap;
     }
@@ -745,11 +869,11 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     int dev = 0;
     cudaError_t e = g_pcd_once[which].run(dev, [&](int d) {
         cudaError_t e2 = cudaFuncSetAttribute(k_pcd_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)PCD_SMEM);
+                                              (int)PCD_DYN_MAX);
         if (e2 != cudaSuccess) return e2;
         e2 = cudaDeviceGetAttribute(&g_pcd_nsm[which][d], cudaDevAttrMultiProcessorCount, d);
         if (e2 != cudaSuccess) return e2;
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pcd_occ[which][d], k_pcd_persist<T>, PT, PCD_SMEM);
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pcd_occ[which][d], k_pcd_persist<T>, PT, PCD_DYN_MAX);
         if (e2 != cudaSuccess) return e2;
         return g_pcd_occ[which][d] < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
     });
@@ -773,15 +897,22 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     v.wpw = base + 5 * np;
     v.corr = base + 6 * np;
     v.tmp = base + 7 * np;
+    v.vq = base + 8 * np;
     int *col = reinterpret_cast<int *>(base + 10 * np);
     int *pid = col + 2 * np;
-    v.zt = reinterpret_cast<uint8_t *>(pid + 2 * np);
+    int *qi = pid + 2 * np, *qj = qi + np;
+    v.qi = qi;
+    v.qj = qj;
+    v.zt = reinterpret_cast<uint8_t *>(qj + np);
     v.np = np;
     int *ptr = w.pcd_rows, *cursor = ptr + (n + 1), *cnt = cursor + (n + 1);
     PcdState *sd = reinterpret_cast<PcdState *>(
         (reinterpret_cast<uintptr_t>(cnt + (n + 1)) + 15) & ~uintptr_t(15));
     static_assert(sizeof(PcdState) % 8 == 0, "the state keeps the partials aligned");
     v.part = reinterpret_cast<double *>(sd + 1);
+    v.kt = v.part + 8 * PCD_MAX_G;
+    v.kj = v.kt + KCAP;
+    v.kp = reinterpret_cast<int *>(v.kj + KCAP);
     // CSR of the pairs
     const unsigned gp = (unsigned)lmax(1, lmin((np + 255) / 256, 152 * 8));
     if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(int), st)) != cudaSuccess) return e;
@@ -789,7 +920,9 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     k_csr_scan<<<1, 1024, 0, st>>>(cnt, n, ptr, cursor);
     k_csr_fill<<<gp, 256, 0, st>>>(pi, pj, np, cursor, col, pid);
     k_csr_sort<<<(unsigned)lmax(1, lmin((n + 255) / 256, 152 * 8)), 256, 0, st>>>(ptr, n, col, pid);
-    counted(4);
+    k_csr_pos<<<(unsigned)lmax(1, lmin((2 * np + 255) / 256, 152 * 8)), 256, 0, st>>>(ptr, n, col, pid, pi, pj, qi,
+                                                                                     qj);
+    counted(5);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sd, 0, sizeof(PcdState), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(v.P, 0, (size_t)np * sizeof(double), st)) != cudaSuccess) return e;
@@ -805,9 +938,14 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     }
     // all iterations: one cooperative launch, as many CTAs as fit (one per SM)
     const int G = (int)lmax(1, lmin((int64_t)g_pcd_nsm[which][dev] * g_pcd_occ[which][dev], PCD_MAX_G));
+    // rows of W the SpMM holds in shared memory (0: rows too long, the tiled SpMM)
+    const int rb = (int)std::min<int64_t>(SP_RB, (int64_t)(SP_WS_BYTES / ((size_t)n * sizeof(T))));
+    const size_t dyn = std::max(std::max(PCD_SMEM, (size_t)rb * (size_t)n * sizeof(T)),
+                                (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(T));
     void *args[] = {(void *)&W, (void *)&Vt, (void *)&n, (void *)&lam, (void *)&ptr, (void *)&col,
-                    (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&sd};
-    e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, PCD_SMEM, st);
+                    (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&rb,
+                    (void *)&sd};
+    e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, dyn, st);
     counted(1);
     if (e != cudaSuccess) return e;
     // U = Delta W
