@@ -55,6 +55,7 @@ constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
 constexpr int SP_RB = 8;          // rows of W held in shared memory by the persistent SpMM, at most
 constexpr size_t SP_WS_BYTES = 200 * 1024;  // shared memory for them
+constexpr int PCD_MAX_G = 160;    // CTAs of the persistent kernel, at most (one per SM)
 
 struct PcdState {
     int done;        // the stopping rule fired
@@ -304,7 +305,34 @@ __device__ __noinline__ void spmm_wrows(const T *__restrict__ W, int64_t n, cons
         const int64_t k0 = blk * rb;
         const int nr = (int)lmin(rb, n - k0);
         const T *src = W + k0 * n;
-        for (int64_t e = threadIdx.x; e < (int64_t)nr * n; e += blockDim.x) ws[e] = src[e];
+        const int64_t ne = (int64_t)nr * n;
+        if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+            // 16-byte loads, four in flight per thread, then the scalar tail
+            const int64_t nv = ne * (int64_t)sizeof(T) / 16;
+            const int4 *s4 = reinterpret_cast<const int4 *>(src);
+            int4 *d4 = reinterpret_cast<int4 *>(ws);
+            for (int64_t e = threadIdx.x; e < nv; e += 4 * (int64_t)blockDim.x) {
+                int4 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (e + u * blockDim.x < nv) x[u] = s4[e + u * blockDim.x];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (e + u * blockDim.x < nv) d4[e + u * blockDim.x] = x[u];
+            }
+            for (int64_t e = nv * 16 / (int64_t)sizeof(T) + threadIdx.x; e < ne; e += blockDim.x) ws[e] = src[e];
+        } else {
+            // scalar loads, eight in flight per thread
+            for (int64_t e = threadIdx.x; e < ne; e += 8 * (int64_t)blockDim.x) {
+                T x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e + u * blockDim.x < ne) x[u] = src[e + u * blockDim.x];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e + u * blockDim.x < ne) ws[e + u * blockDim.x] = x[u];
+            }
+        }
         __syncthreads();
         for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
             T acc[SP_RB];
@@ -416,7 +444,7 @@ __device__ bool pcd_barrier(PcdState *st, unsigned G, unsigned &epoch) {
 // maxmask is set, else a sum): CTA partials, a barrier, then every CTA
 // combines all partials in CTA order, so all take the same totals.
 template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv, PcdState *st, unsigned G,
+__device__ __noinline__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv, PcdState *st, unsigned G,
                             unsigned &epoch, unsigned &nred, double *red, double *bc, int nact) {
     // only the first nact warps hold values (the others skip the FP64 shuffles,
     // which cost a warp's issue slots on this GPU whatever the values)
@@ -447,14 +475,22 @@ __device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, const PcdVec &pv,
     }
     if (!pcd_barrier(st, G, epoch)) return false;
     if (warp == 0) {
+        // every partial this lane combines, loaded before any is used (at most
+        // PCD_MAX_G / 32 per lane)
+        double pv[NV][PCD_MAX_G / 32];
+#pragma unroll
+        for (int u = 0; u < PCD_MAX_G / 32; ++u) {
+            const int b = lane + 32 * u;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) pv[k][u] = b < (int)G ? __ldcg(part + b * 4 + k) : 0.0;
+        }
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             const bool mx = (maxmask >> k) & 1u;
             double x = mx ? -INFINITY : 0.0;
-            for (int b = lane; b < (int)G; b += 32) {
-                const double y = __ldcg(part + b * 4 + k);
-                x = mx ? fmax(x, y) : x + y;
-            }
+#pragma unroll
+            for (int u = 0; u < PCD_MAX_G / 32; ++u)
+                if (lane + 32 * u < (int)G) x = mx ? fmax(x, pv[k][u]) : x + pv[k][u];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const double y = __shfl_xor_sync(0xffffffffu, x, o);
@@ -816,9 +852,8 @@ int g_pcd_nsm[2][kMaxDevices], g_pcd_occ[2][kMaxDevices];
 
 // The per-row and fixed part of the scratch: CSR row pointers, cursors and
 // counts (n + 1 each), then, 16-byte aligned, the state, the partials (2 x 4
-// per CTA, at most 152 x 4 CTAs) and the gathered kinks (KCAP times, jumps,
+// per CTA, at most PCD_MAX_G CTAs) and the gathered kinks (KCAP times, jumps,
 // pair indices).
-constexpr int PCD_MAX_G = 152 * 4;
 size_t pcd_rows_bytes(int64_t n) {
     return (size_t)(n + 1) * 3 * sizeof(int) + 16 + sizeof(PcdState) + 8 * PCD_MAX_G * sizeof(double) +
            (size_t)KCAP * (2 * sizeof(double) + sizeof(int)) + 64;
