@@ -53,8 +53,7 @@ constexpr int PW = PT / 32;       // its warps
 constexpr int KCAP = 4096;        // kinks sorted in shared memory
 constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
-constexpr int SP_RB = 8;          // rows of W held in shared memory by the persistent SpMM, at most
-constexpr size_t SP_WS_BYTES = 200 * 1024;  // shared memory for them
+constexpr int SP_GR = 16;         // rows of X per task of the persistent SpMM
 constexpr int PCD_MAX_G = 160;    // CTAs of the persistent kernel, at most (one per SM)
 
 struct PcdState {
@@ -289,78 +288,49 @@ __device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__res
     }
 }
 
-// Vt = (X W)^T = W X with W held row by row in shared memory: Vt_{k,r} =
-// sum over row r's entries q of X_q W_{k, col_q}.  A CTA loads `rb` rows of W
-// (coalesced), then each thread forms Vt_{k, r} for its rows r and the rb
-// rows k from the entries' values vq (X in CSR entry order, so an entry's
-// column and value sit side by side) and shared-memory gathers; the stores
-// are coalesced along r.  Row blocks are taken from `first` in steps of
-// `step`.  (vq may come from other CTAs of the launch: read through L2.)
+// Vt = (X W)^T for the persistent kernel: a task is a group of SP_GR rows r of
+// X and a chunk of blockDim.x columns k, one column per thread; the thread
+// sums X_q W_{col_q, k} over the group's entries q (entry columns and values
+// are the same for the whole CTA: broadcast loads; the W loads are coalesced
+// along k) and stores Vt_{k, r0 .. r0 + SP_GR - 1}, contiguous.  vq holds X in
+// CSR entry order, written by other CTAs of the launch: read through L2.
 template <typename T>
-__device__ __noinline__ void spmm_wrows(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
-                                        const int *__restrict__ col, const double *__restrict__ vq, T *__restrict__ Vt,
-                                        int rb, T *__restrict__ ws, int64_t first, int64_t step) {
-    const int64_t nrb = (n + rb - 1) / rb;
-    for (int64_t blk = first; blk < nrb; blk += step) {
-        const int64_t k0 = blk * rb;
-        const int nr = (int)lmin(rb, n - k0);
-        const T *src = W + k0 * n;
-        const int64_t ne = (int64_t)nr * n;
-        if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-            // 16-byte loads, four in flight per thread, then the scalar tail
-            const int64_t nv = ne * (int64_t)sizeof(T) / 16;
-            const int4 *s4 = reinterpret_cast<const int4 *>(src);
-            int4 *d4 = reinterpret_cast<int4 *>(ws);
-            for (int64_t e = threadIdx.x; e < nv; e += 4 * (int64_t)blockDim.x) {
-                int4 x[4];
+__device__ __noinline__ void spmm_groups(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
+                                         const int *__restrict__ col, const double *__restrict__ vq,
+                                         T *__restrict__ Vt, int64_t first, int64_t step) {
+    const int64_t ng = (n + SP_GR - 1) / SP_GR, nch = (n + blockDim.x - 1) / blockDim.x;
+    for (int64_t task = first; task < ng * nch; task += step) {
+        const int64_t r0 = (task / nch) * SP_GR, k = (task % nch) * blockDim.x + threadIdx.x;
+        const bool kin = k < n;
+        const T *wk = W + (kin ? k : 0);
+        T acc[SP_GR];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (e + u * blockDim.x < nv) x[u] = s4[e + u * blockDim.x];
+        for (int rl = 0; rl < SP_GR; ++rl) {
+            acc[rl] = T(0);
+            if (r0 + rl >= n) continue;
+            const int qb = ptr[r0 + rl], qe = ptr[r0 + rl + 1];
+            int q = qb;
+            for (; q + 3 < qe; q += 4) {
+                int c[4];
+                T x[4], w[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (e + u * blockDim.x < nv) d4[e + u * blockDim.x] = x[u];
-            }
-            for (int64_t e = nv * 16 / (int64_t)sizeof(T) + threadIdx.x; e < ne; e += blockDim.x) ws[e] = src[e];
-        } else {
-            // scalar loads, eight in flight per thread
-            for (int64_t e = threadIdx.x; e < ne; e += 8 * (int64_t)blockDim.x) {
-                T x[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (e + u * blockDim.x < ne) x[u] = src[e + u * blockDim.x];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (e + u * blockDim.x < ne) ws[e + u * blockDim.x] = x[u];
-            }
-        }
-        __syncthreads();
-        for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-            T acc[SP_RB];
-#pragma unroll
-            for (int j = 0; j < SP_RB; ++j) acc[j] = T(0);
-            const int qb = ptr[r], qe = ptr[r + 1];
-            for (int q0 = qb; q0 < qe; q0 += 8) {
-                int cc[8];
-                T xv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const bool in = q0 + u < qe;
-                    cc[u] = in ? col[q0 + u] : 0;
-                    xv[u] = in ? (T)__ldcg(vq + q0 + u) : T(0);
+                for (int u = 0; u < 4; ++u) {
+                    c[u] = col[q + u];
+                    x[u] = (T)__ldcg(vq + q + u);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (xv[u] == T(0)) continue;
+                for (int u = 0; u < 4; ++u) w[u] = wk[(int64_t)c[u] * n];
 #pragma unroll
-                    for (int j = 0; j < SP_RB; ++j)
-                        if (j < nr) acc[j] = fma(xv[u], ws[(int64_t)j * n + cc[u]], acc[j]);
-                }
+                for (int u = 0; u < 4; ++u) acc[rl] = fma(x[u], w[u], acc[rl]);
             }
-#pragma unroll
-            for (int j = 0; j < SP_RB; ++j)
-                if (j < nr) Vt[(k0 + j) * n + r] = acc[j];
+            for (; q < qe; ++q) acc[rl] = fma((T)__ldcg(vq + q), wk[(int64_t)col[q] * n], acc[rl]);
         }
-        __syncthreads();
+        if (kin) {
+            T *dst = Vt + k * n + r0;
+#pragma unroll
+            for (int rl = 0; rl < SP_GR; ++rl)
+                if (r0 + rl < n) dst[rl] = acc[rl];
+        }
     }
 }
 
@@ -662,15 +632,12 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
 // Six grid barriers per iteration: the direction's reduction, the search
 // direction's, the SpMM, the SDDMM with g2, the kink gather, and the step
 // from CTA 0.  The corrections of an iteration's exact zeros are applied to b
-// at the start of the next one (only then are they needed).  rb > 0: the
-// SpMM holds rb rows of W in shared memory (spmm_wrows); rb = 0 (rows too
-// long): the tiled SpMM.  The dynamic shared memory serves the SpMM and the
-// walk in turn.
+// at the start of the next one (only then are they needed).
 template <typename T>
 __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, T *__restrict__ Vt, int64_t n,
                                                         double lam, const int *__restrict__ ptr,
                                                         const int *__restrict__ col, const int *__restrict__ pid,
-                                                        PcdVec v, int iters, int cg, double rtol, int rb,
+                                                        PcdVec v, int iters, int cg, double rtol,
                                                         PcdState *st) {
     extern __shared__ __align__(16) unsigned char pcd_smem[];
     __shared__ double red[4 * PW + 8], bc[4];
@@ -680,14 +647,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     const int64_t lo = np * blockIdx.x / G, hi = np * (blockIdx.x + 1) / G;
     const int nact = (int)lmin(PW, (hi - lo + 31) / 32);  // warps holding pairs of this CTA's slice
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
-    T *ws = reinterpret_cast<T *>(pcd_smem);
-    auto spmm = [&](const double *xpair) {  // Vt = (X W)^T, X from vq (or the pair values)
-        if (rb > 0)
-            spmm_wrows<T>(W, n, ptr, col, v.vq, Vt, rb, ws, blockIdx.x, G);
-        else
-            spmm_tiles<T, true>(W, n, ptr, col, pid, xpair, Vt, blockIdx.x, G,
-                                reinterpret_cast<T(*)[SP_COLS + 1]>(pcd_smem));
-    };
+    auto spmm = [&]() { spmm_groups<T>(W, n, ptr, col, v.vq, Vt, blockIdx.x, G); };  // Vt = (X W)^T, X in vq
     int it = 0;
     double d0max = 0.0;
     bool corr_pending = false;  // this thread's pairs got corrections in the last update
@@ -715,7 +675,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         if (r4[3] != 0.0) {
             // b += (W C W) for the last update's corrections C (in vq), then the
             // direction again
-            spmm(v.corr);
+            spmm();
             if (!pcd_barrier(st, G, epoch)) break;
             sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.tmp, gw0, gnw, nullptr, nullptr);
             if (!pcd_barrier(st, G, epoch)) break;
@@ -766,7 +726,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         }
         const double g1 = r2[0], h0 = r2[1];
         // 3. (W P W) on the pairs, and g2 = <P, W P W>_w
-        spmm(v.P);
+        spmm();
         if (!pcd_barrier(st, G, epoch)) break;
         double r1[1] = {0.0};
         sddmm_pairs<T>(W, Vt, n, v.pi, v.pj, np, v.wpw, gw0, gnw, v.P, &r1[0]);
@@ -844,8 +804,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
 }
 
 constexpr size_t PCD_SMEM = (size_t)KCAP * (2 * sizeof(double) + sizeof(int));
-constexpr size_t PCD_DYN_MAX = SP_WS_BYTES;  // the largest dynamic shared memory of k_pcd_persist
-static_assert(PCD_SMEM <= PCD_DYN_MAX, "the walk's arrays fit the dynamic shared memory");
+constexpr size_t PCD_DYN_MAX = PCD_SMEM;  // the dynamic shared memory of k_pcd_persist (the walk's)
 
 OncePerDevice g_pcd_once[2];
 int g_pcd_nsm[2][kMaxDevices], g_pcd_occ[2][kMaxDevices];
@@ -973,14 +932,9 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     }
     // all iterations: one cooperative launch, as many CTAs as fit (one per SM)
     const int G = (int)lmax(1, lmin((int64_t)g_pcd_nsm[which][dev] * g_pcd_occ[which][dev], PCD_MAX_G));
-    // rows of W the SpMM holds in shared memory (0: rows too long, the tiled SpMM)
-    const int rb = (int)std::min<int64_t>(SP_RB, (int64_t)(SP_WS_BYTES / ((size_t)n * sizeof(T))));
-    const size_t dyn = std::max(std::max(PCD_SMEM, (size_t)rb * (size_t)n * sizeof(T)),
-                                (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(T));
     void *args[] = {(void *)&W, (void *)&Vt, (void *)&n, (void *)&lam, (void *)&ptr, (void *)&col,
-                    (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&rb,
-                    (void *)&sd};
-    e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, dyn, st);
+                    (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&sd};
+    e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, PCD_SMEM, st);
     counted(1);
     if (e != cudaSuccess) return e;
     // U = Delta W
