@@ -53,7 +53,6 @@ constexpr int PW = PT / 32;       // its warps
 constexpr int KCAP = 4096;        // kinks sorted in shared memory
 constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
-constexpr int SP_GR = 16;         // rows of X per task of the persistent SpMM
 constexpr int PCD_MAX_G = 160;    // CTAs of the persistent kernel, at most (one per SM)
 
 struct PcdState {
@@ -202,8 +201,8 @@ __global__ void k_csr_pos(const int *__restrict__ ptr, int64_t n, const int *__r
 template <typename T, bool TRANS>
 __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
                            const int *__restrict__ col, const int *__restrict__ pid,
-                           const double *__restrict__ x, T *__restrict__ out, int64_t first, int64_t step,
-                           T (*tile)[SP_COLS + 1]) {
+                           const double *__restrict__ x, const double *__restrict__ vq, T *__restrict__ out,
+                           int64_t first, int64_t step, T (*tile)[SP_COLS + 1]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int64_t tr = (n + SP_ROWS - 1) / SP_ROWS, tc = (n + SP_COLS - 1) / SP_COLS;
     for (int64_t tt = first; tt < tr * tc; tt += step) {
@@ -222,7 +221,7 @@ __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, cons
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int q = q0 + u;
-                        vv[u] = q < qe ? (T)__ldcg(x + pid[q]) : T(0);
+                        vv[u] = q < qe ? (T)__ldcg(vq ? vq + q : x + pid[q]) : T(0);
                         const T *wr = W + (int64_t)(q < qe ? col[q] : 0) * n + k0 + lane;
 #pragma unroll
                         for (int m = 0; m < SP_COLS / 32; ++m)
@@ -288,52 +287,6 @@ __device__ __noinline__ void sddmm_pairs(const T *__restrict__ W, const T *__res
     }
 }
 
-// Vt = (X W)^T for the persistent kernel: a task is a group of SP_GR rows r of
-// X and a chunk of blockDim.x columns k, one column per thread; the thread
-// sums X_q W_{col_q, k} over the group's entries q (entry columns and values
-// are the same for the whole CTA: broadcast loads; the W loads are coalesced
-// along k) and stores Vt_{k, r0 .. r0 + SP_GR - 1}, contiguous.  vq holds X in
-// CSR entry order, written by other CTAs of the launch: read through L2.
-template <typename T>
-__device__ __noinline__ void spmm_groups(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
-                                         const int *__restrict__ col, const double *__restrict__ vq,
-                                         T *__restrict__ Vt, int64_t first, int64_t step) {
-    const int64_t ng = (n + SP_GR - 1) / SP_GR, nch = (n + blockDim.x - 1) / blockDim.x;
-    for (int64_t task = first; task < ng * nch; task += step) {
-        const int64_t r0 = (task / nch) * SP_GR, k = (task % nch) * blockDim.x + threadIdx.x;
-        const bool kin = k < n;
-        const T *wk = W + (kin ? k : 0);
-        T acc[SP_GR];
-#pragma unroll
-        for (int rl = 0; rl < SP_GR; ++rl) {
-            acc[rl] = T(0);
-            if (r0 + rl >= n) continue;
-            const int qb = ptr[r0 + rl], qe = ptr[r0 + rl + 1];
-            int q = qb;
-            for (; q + 3 < qe; q += 4) {
-                int c[4];
-                T x[4], w[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    c[u] = col[q + u];
-                    x[u] = (T)__ldcg(vq + q + u);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) w[u] = wk[(int64_t)c[u] * n];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[rl] = fma(x[u], w[u], acc[rl]);
-            }
-            for (; q < qe; ++q) acc[rl] = fma((T)__ldcg(vq + q), wk[(int64_t)col[q] * n], acc[rl]);
-        }
-        if (kin) {
-            T *dst = Vt + k * n + r0;
-#pragma unroll
-            for (int rl = 0; rl < SP_GR; ++rl)
-                if (r0 + rl < n) dst[rl] = acc[rl];
-        }
-    }
-}
-
 // Stand-alone launches (the initial b from a given Delta, the final U).
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_pair_spmm(const T *__restrict__ W, int64_t n,
@@ -341,7 +294,7 @@ __global__ void __launch_bounds__(256) k_pair_spmm(const T *__restrict__ W, int6
                                                    const int *__restrict__ pid, const double *__restrict__ x,
                                                    T *__restrict__ out) {
     __shared__ T tile[SP_ROWS][SP_COLS + 1];
-    spmm_tiles<T, TRANS>(W, n, ptr, col, pid, x, out, blockIdx.x, gridDim.x, tile);
+    spmm_tiles<T, TRANS>(W, n, ptr, col, pid, x, nullptr, out, blockIdx.x, gridDim.x, tile);
 }
 
 template <typename T>
@@ -647,7 +600,11 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     const int64_t lo = np * blockIdx.x / G, hi = np * (blockIdx.x + 1) / G;
     const int nact = (int)lmin(PW, (hi - lo + 31) / 32);  // warps holding pairs of this CTA's slice
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
-    auto spmm = [&]() { spmm_groups<T>(W, n, ptr, col, v.vq, Vt, blockIdx.x, G); };  // Vt = (X W)^T, X in vq
+    // Vt = (X W)^T, X in vq (the tile in the dynamic shared memory, which the walk also uses)
+    auto spmm = [&]() {
+        spmm_tiles<T, true>(W, n, ptr, col, pid, nullptr, v.vq, Vt, blockIdx.x, G,
+                            reinterpret_cast<T(*)[SP_COLS + 1]>(pcd_smem));
+    };
     int it = 0;
     double d0max = 0.0;
     bool corr_pending = false;  // this thread's pairs got corrections in the last update
@@ -804,6 +761,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
 }
 
 constexpr size_t PCD_SMEM = (size_t)KCAP * (2 * sizeof(double) + sizeof(int));
+static_assert(PCD_SMEM >= (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(double), "the SpMM tile fits");
 constexpr size_t PCD_DYN_MAX = PCD_SMEM;  // the dynamic shared memory of k_pcd_persist (the walk's)
 
 OncePerDevice g_pcd_once[2];
