@@ -54,6 +54,9 @@ constexpr int KCAP = 4096;        // kinks sorted in shared memory
 constexpr int SP_ROWS = 32;       // rows of V per SpMM CTA
 constexpr int SP_COLS = 128;      // columns of V per SpMM CTA
 constexpr int PCD_MAX_G = 160;    // CTAs of the persistent kernel, at most (one per SM)
+// warp groups of the persistent SpMM: as many tiles in flight as fit the shared memory
+template <typename T>
+constexpr int SPLIT_NH = sizeof(T) == 4 ? 4 : 2;
 
 struct PcdState {
     int done;        // the stopping rule fired
@@ -251,6 +254,58 @@ __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, cons
             }
             __syncthreads();
         }
+    }
+}
+
+// The persistent kernel's SpMM: the CTA's warps split into NH groups, each
+// forming its own tiles (the CTA's tiles dealt round robin) with its own
+// shared-memory tile and named barrier, so NH tiles' load chains overlap.
+template <typename T, int NH>
+__device__ __noinline__ void spmm_tiles_split(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
+                                              const int *__restrict__ col, const double *__restrict__ vq,
+                                              T *__restrict__ out, int64_t first, int64_t step,
+                                              unsigned char *smem) {
+    const int lane = threadIdx.x & 31, nwh = (blockDim.x >> 5) / NH;  // warps per group
+    const int h = (threadIdx.x >> 5) / nwh, warp = (threadIdx.x >> 5) % nwh;
+    T(*tile)[SP_COLS + 1] = reinterpret_cast<T(*)[SP_COLS + 1]>(smem) + h * SP_ROWS;
+    const unsigned nthr = (unsigned)nwh * 32u;
+    const int64_t tr = (n + SP_ROWS - 1) / SP_ROWS, tc = (n + SP_COLS - 1) / SP_COLS;
+    for (int64_t tt = first + h * step; tt < tr * tc; tt += NH * step) {
+        const int64_t r0 = (tt / tc) * SP_ROWS, k0 = (tt % tc) * SP_COLS;
+        for (int rl = warp; rl < SP_ROWS; rl += nwh) {
+            const int64_t r = r0 + rl;
+            T acc[SP_COLS / 32];
+#pragma unroll
+            for (int m = 0; m < SP_COLS / 32; ++m) acc[m] = T(0);
+            if (r < n) {
+                const int qb = ptr[r], qe = ptr[r + 1];
+                for (int q0 = qb; q0 < qe; q0 += 4) {
+                    T vv[4], wv[4][SP_COLS / 32];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u;
+                        vv[u] = q < qe ? (T)__ldcg(vq + q) : T(0);
+                        const T *wr = W + (int64_t)(q < qe ? col[q] : 0) * n + k0 + lane;
+#pragma unroll
+                        for (int m = 0; m < SP_COLS / 32; ++m)
+                            wv[u][m] = (q < qe && k0 + lane + 32 * m < n) ? wr[32 * m] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int m = 0; m < SP_COLS / 32; ++m) acc[m] = fma(vv[u], wv[u][m], acc[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < SP_COLS / 32; ++m) tile[rl][lane + 32 * m] = acc[m];
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(nthr) : "memory");
+        for (int c = warp; c < SP_COLS; c += nwh) {
+            const int64_t k = k0 + c;
+            if (k >= n) break;
+            if (r0 + lane < n) out[k * n + r0 + lane] = tile[lane][c];
+        }
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(nthr) : "memory");
     }
 }
 
@@ -602,8 +657,8 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
     // Vt = (X W)^T, X in vq (the tile in the dynamic shared memory, which the walk also uses)
     auto spmm = [&]() {
-        spmm_tiles<T, true>(W, n, ptr, col, pid, nullptr, v.vq, Vt, blockIdx.x, G,
-                            reinterpret_cast<T(*)[SP_COLS + 1]>(pcd_smem));
+        spmm_tiles_split<T, SPLIT_NH<T>>(W, n, ptr, col, v.vq, Vt, blockIdx.x, G, pcd_smem);
+        __syncthreads();
     };
     int it = 0;
     double d0max = 0.0;
@@ -761,7 +816,9 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
 }
 
 constexpr size_t PCD_SMEM = (size_t)KCAP * (2 * sizeof(double) + sizeof(int));
-static_assert(PCD_SMEM >= (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(double), "the SpMM tile fits");
+static_assert(PCD_SMEM >= 4 * (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(float) &&
+                  PCD_SMEM >= 2 * (size_t)SP_ROWS * (SP_COLS + 1) * sizeof(double),
+              "the SpMM tiles fit");
 constexpr size_t PCD_DYN_MAX = PCD_SMEM;  // the dynamic shared memory of k_pcd_persist (the walk's)
 
 OncePerDevice g_pcd_once[2];
