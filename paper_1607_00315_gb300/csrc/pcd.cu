@@ -62,6 +62,7 @@ struct PcdState {
     int done;        // the stopping rule fired
     int it;          // iterations completed
     int nk;          // kinks gathered in (0, R]
+    unsigned tctr[2];  // SpMM tiles handed out (alternating between SpMM phases)
     int err;         // a bounded grid-barrier wait expired
     unsigned bar;    // grid barrier arrivals
     int pad;
@@ -263,14 +264,19 @@ __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, cons
 template <typename T, int NH>
 __device__ __noinline__ void spmm_tiles_split(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
                                               const int *__restrict__ col, const double *__restrict__ vq,
-                                              T *__restrict__ out, int64_t first, int64_t step,
-                                              unsigned char *smem) {
+                                              T *__restrict__ out, unsigned *ctr, unsigned char *smem) {
+    __shared__ unsigned grab[NH];
     const int lane = threadIdx.x & 31, nwh = (blockDim.x >> 5) / NH;  // warps per group
     const int h = (threadIdx.x >> 5) / nwh, warp = (threadIdx.x >> 5) % nwh;
     T(*tile)[SP_COLS + 1] = reinterpret_cast<T(*)[SP_COLS + 1]>(smem) + h * SP_ROWS;
     const unsigned nthr = (unsigned)nwh * 32u;
     const int64_t tr = (n + SP_ROWS - 1) / SP_ROWS, tc = (n + SP_COLS - 1) / SP_COLS;
-    for (int64_t tt = first + h * step; tt < tr * tc; tt += NH * step) {
+    for (;;) {
+        // the next tile, from a counter shared by every group of the grid
+        if (warp == 0 && lane == 0) grab[h] = atomicAdd(ctr, 1u);
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(nthr) : "memory");
+        const int64_t tt = grab[h];
+        if (tt >= tr * tc) break;
         const int64_t r0 = (tt / tc) * SP_ROWS, k0 = (tt % tc) * SP_COLS;
         for (int rl = warp; rl < SP_ROWS; rl += nwh) {
             const int64_t r = r0 + rl;
@@ -656,8 +662,14 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
     const int nact = (int)lmin(PW, (hi - lo + 31) / 32);  // warps holding pairs of this CTA's slice
     const int64_t gw0 = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), gnw = (int64_t)G * PW;
     // Vt = (X W)^T, X in vq (the tile in the dynamic shared memory, which the walk also uses)
+    unsigned nspmm = 0;
     auto spmm = [&]() {
-        spmm_tiles_split<T, SPLIT_NH<T>>(W, n, ptr, col, v.vq, Vt, blockIdx.x, G, pcd_smem);
+        // tiles handed out by st->tctr[nspmm & 1]; the other counter is cleared
+        // by CTA 0 for the next SpMM (which is at least one barrier away)
+        unsigned *ctr = &st->tctr[nspmm & 1u];
+        spmm_tiles_split<T, SPLIT_NH<T>>(W, n, ptr, col, v.vq, Vt, ctr, pcd_smem);
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->tctr[(nspmm + 1) & 1u] = 0u;
+        ++nspmm;
         __syncthreads();
     };
     int it = 0;
