@@ -293,7 +293,7 @@ def run_batched(args):
         for p in ps:
             for lam in synth.LAMBDA_PATH:
                 plist.append(glasso.Context.problem(p.X, lam, 1e-5, samples=True,
-                                                    screen=args.screen))
+                                                    screen=args.screen, inner=args.inner))
                 outs.append(np.empty((p.n, p.n)))
         return plist, outs
 
@@ -329,7 +329,7 @@ def run_batched(args):
         "config": {"workload": f"{args.instances} instances, n ~ U[32, 512], m = 2n, "
                                f"tridiagonal/sparse alternating, lambda path {list(synth.LAMBDA_PATH)} "
                                f"warm started, tol 1e-5, samples X (fp64) on the host",
-                   "screen": bool(args.screen), "solves": total, "wall_s": max_s,
+                   "screen": bool(args.screen), "inner": args.inner, "solves": total, "wall_s": max_s,
                    "parallelism": f"instances split over {world} ranks (greedy cost balance)"},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                        "mean": float(per.mean())},
@@ -374,7 +374,7 @@ def run_serving(args):
     ctx = glasso.Context(local, precision=glasso.MIXED, mem_budget_bytes=40 << 30)
     # warm-up: a few requests of the trace's sizes (outputs must outlive the poll)
     wouts = [np.empty((rows[k][1], rows[k][1])) for k in range(min(8, len(rows)))]
-    wt = [ctx.submit(glasso.Context.problem(xs[k], rows[k][2], 1e-5, samples=True), wouts[k])
+    wt = [ctx.submit(glasso.Context.problem(xs[k], rows[k][2], 1e-5, samples=True, inner=args.inner), wouts[k])
           for k in range(len(wouts))]
     for t in wt:
         while ctx.poll(t, 100000)[0] == glasso.EAGAIN:
@@ -410,7 +410,7 @@ def run_serving(args):
     for k, (arr, n, lam, _) in enumerate(rows):
         while time.perf_counter() - t0 < arr:
             time.sleep(0.0002)
-        prob = glasso.Context.problem(xs[k], lam, 1e-5, samples=True)
+        prob = glasso.Context.problem(xs[k], lam, 1e-5, samples=True, inner=args.inner)
         t = ctx.submit(prob, outs[k])
         with lock:
             tickets[k] = t
@@ -441,7 +441,7 @@ def run_serving(args):
         "config": {"workload": f"{len(trace)} Poisson arrivals at {args.rate}/s, n log-uniform in "
                                f"[64, 4096], m = n, lambda ~ U[0.05, 0.3], sparse generator, tol 1e-5, "
                                f"samples X (fp64) on the host, 40 GB device budget",
-                   "slots": int(os.environ.get("GLASSO_SERVE_SLOTS", "4")), "span_s": span,
+                   "slots": int(os.environ.get("GLASSO_SERVE_SLOTS", "4")), "inner": args.inner, "span_s": span,
                    "parallelism": f"requests routed over {world} ranks (least modelled work)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean()), "max": float(lat.max())},
@@ -467,27 +467,32 @@ def extra_workloads(args, local, dev):
         stream = torch.cuda.current_stream(dev)
         c3.set_stream(stream.cuda_stream)
         A3 = torch.empty((p3.n, p3.n), dtype=torch.float64, device=dev)
-        info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3)[2]  # warm-up
-        lat3 = []
-        for _ in range(3):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3)[2]
-            e1.record(stream)
-            torch.cuda.synchronize()
-            lat3.append(e0.elapsed_time(e1))
+        res3 = {}
+        for inner in (args.inner, "pcd_cg" if args.inner == "cd" else "cd"):
+            info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3, inner=inner)[2]  # warm-up
+            lat3 = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info3 = c3.solve(X3, p3.lam, tol=p3.tol, samples=True, A_out=A3, inner=inner)[2]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                lat3.append(e0.elapsed_time(e1))
+            ms3 = float(np.mean(lat3))
+            res3[inner] = {"ms_per_solve": ms3, "solves_per_s": 1e3 / ms3, "status": info3["status"],
+                           "relaxations": info3["relaxations"], "inner_iters": info3["inner_iters"],
+                           "rel_kkt": info3["rel_kkt"], "nnz": info3["nnz"]}
     del X3, A3
-    ms3 = float(np.mean(lat3))
-    out["n10000_fp32_samples"] = {
-        "workload": "sparse-Theta n=10000, X fp32 5000 x n on the device, S on the tensor cores "
-                    "inside the solve, lambda=0.08, mixed, to rel. KKT 1e-5",
-        "ms_per_solve": ms3, "solves_per_s": 1e3 / ms3, "status": info3["status"],
-        "relaxations": info3["relaxations"], "rel_kkt": info3["rel_kkt"], "nnz": info3["nnz"],
-        "inputs_larger_than_l2": True}
+    out["n10000_fp32_samples"] = dict(
+        workload="sparse-Theta n=10000, X fp32 5000 x n on the device, S on the tensor cores "
+                 "inside the solve, lambda=0.08, mixed, to rel. KKT 1e-5",
+        inputs_larger_than_l2=True, **res3[args.inner], inner=args.inner,
+        other_inner={k: v for k, v in res3.items() if k != args.inner})
     for name, extra in (("batched", []), ("serving", ["--requests", str(args.requests)])):
         try:
-            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name] + extra,
+            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name,
+                                "--inner", args.inner] + extra,
                                capture_output=True, text=True, timeout=600)
             line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
             out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config")
