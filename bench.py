@@ -293,7 +293,7 @@ def run_batched(args):
         for p in ps:
             for lam in synth.LAMBDA_PATH:
                 plist.append(glasso.Context.problem(p.X, lam, 1e-5, samples=True,
-                                                    screen=args.screen, inner=args.inner))
+                                                    screen=args.screen, inner=args.batch_inner))
                 outs.append(np.empty((p.n, p.n)))
         return plist, outs
 
@@ -329,7 +329,7 @@ def run_batched(args):
         "config": {"workload": f"{args.instances} instances, n ~ U[32, 512], m = 2n, "
                                f"tridiagonal/sparse alternating, lambda path {list(synth.LAMBDA_PATH)} "
                                f"warm started, tol 1e-5, samples X (fp64) on the host",
-                   "screen": bool(args.screen), "inner": args.inner, "solves": total, "wall_s": max_s,
+                   "screen": bool(args.screen), "inner": args.batch_inner, "solves": total, "wall_s": max_s,
                    "parallelism": f"instances split over {world} ranks (greedy cost balance)"},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                        "mean": float(per.mean())},
@@ -374,7 +374,8 @@ def run_serving(args):
     ctx = glasso.Context(local, precision=glasso.MIXED, mem_budget_bytes=40 << 30)
     # warm-up: a few requests of the trace's sizes (outputs must outlive the poll)
     wouts = [np.empty((rows[k][1], rows[k][1])) for k in range(min(8, len(rows)))]
-    wt = [ctx.submit(glasso.Context.problem(xs[k], rows[k][2], 1e-5, samples=True, inner=args.inner), wouts[k])
+    wt = [ctx.submit(glasso.Context.problem(xs[k], rows[k][2], 1e-5, samples=True, inner=args.batch_inner),
+                     wouts[k])
           for k in range(len(wouts))]
     for t in wt:
         while ctx.poll(t, 100000)[0] == glasso.EAGAIN:
@@ -410,7 +411,7 @@ def run_serving(args):
     for k, (arr, n, lam, _) in enumerate(rows):
         while time.perf_counter() - t0 < arr:
             time.sleep(0.0002)
-        prob = glasso.Context.problem(xs[k], lam, 1e-5, samples=True, inner=args.inner)
+        prob = glasso.Context.problem(xs[k], lam, 1e-5, samples=True, inner=args.batch_inner)
         t = ctx.submit(prob, outs[k])
         with lock:
             tickets[k] = t
@@ -441,7 +442,8 @@ def run_serving(args):
         "config": {"workload": f"{len(trace)} Poisson arrivals at {args.rate}/s, n log-uniform in "
                                f"[64, 4096], m = n, lambda ~ U[0.05, 0.3], sparse generator, tol 1e-5, "
                                f"samples X (fp64) on the host, 40 GB device budget",
-                   "slots": int(os.environ.get("GLASSO_SERVE_SLOTS", "4")), "inner": args.inner, "span_s": span,
+                   "slots": int(os.environ.get("GLASSO_SERVE_SLOTS", "4")), "inner": args.batch_inner,
+                   "span_s": span,
                    "parallelism": f"requests routed over {world} ranks (least modelled work)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean()), "max": float(lat.max())},
@@ -492,7 +494,7 @@ def extra_workloads(args, local, dev):
     for name, extra in (("batched", []), ("serving", ["--requests", str(args.requests)])):
         try:
             r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name,
-                                "--inner", args.inner] + extra,
+                                "--batch-inner", args.batch_inner] + extra,
                                capture_output=True, text=True, timeout=600)
             line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
             out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config")
@@ -640,8 +642,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path whose solves/s is `value` (the other one is timed beside it)")
-    ap.add_argument("--inner", default="cd", choices=["cd", "pcd_cg"],
-                    help="Newton-direction solver of the timed solves (the other is timed beside it)")
+    ap.add_argument("--inner", default="pcd_cg", choices=["cd", "pcd_cg"],
+                    help="Newton-direction solver of the single solves (the other is timed beside it): "
+                         "PCD-CG, Section 6.3's inner solver, by default")
+    ap.add_argument("--batch-inner", default="cd", choices=["cd", "pcd_cg"],
+                    help="Newton-direction solver of the batched and serving workloads (CD sweeps by default: "
+                         "many small solves run side by side, and PCD-CG's grid-wide launch would serialise them)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=0,

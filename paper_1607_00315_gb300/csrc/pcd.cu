@@ -957,8 +957,12 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
         k_vec_add<<<gp, 256, 0, st>>>(v.b, v.tmp, np);
         counted(3);
     }
-    // all iterations: one cooperative launch, as many CTAs as fit (one per SM)
-    const int G = (int)lmax(1, lmin((int64_t)g_pcd_nsm[which][dev] * g_pcd_occ[which][dev], PCD_MAX_G));
+    // all iterations: one cooperative launch, one CTA per SM at most, and no
+    // more than the SpMM tiles and the pairs can use (a small problem leaves
+    // the other SMs to the work beside it)
+    const int64_t tiles = ((n + SP_ROWS - 1) / SP_ROWS) * ((n + SP_COLS - 1) / SP_COLS);
+    const int64_t want = lmax(tiles / 2, (np + 127) / 128);
+    const int G = (int)lmax(1, lmin(lmin((int64_t)g_pcd_nsm[which][dev] * g_pcd_occ[which][dev], PCD_MAX_G), want));
     void *args[] = {(void *)&W, (void *)&Vt, (void *)&n, (void *)&lam, (void *)&ptr, (void *)&col,
                     (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&sd};
     e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, PCD_SMEM, st);
