@@ -589,6 +589,7 @@ def run_factor(args):
     n = args.factor_n
     p = synth.random_problem(n, max(n // 2, 2), 0.1, 9100 + n, gen="sparse")
     ctx = glasso.Context(local, precision=glasso.MIXED)
+    ctx.set_debug(glasso.DEBUG_TC_DAG_TILES, args.dag_tiles)
     stream = torch.cuda.current_stream(dev)
     ctx.set_stream(stream.cuda_stream)
     S = torch.empty((n, n), dtype=torch.float64, device=dev)
@@ -623,7 +624,7 @@ def run_factor(args):
             "value": tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "dtype": "split-tf32 (f32 storage)", "data": "synthetic",
-            "config": {"workload": f"cholinv_mixed n={n}", "n": n,
+            "config": {"workload": f"cholinv_mixed n={n}", "n": n, "dag_tiles": args.dag_tiles,
                        "l2": "flushed between timed calls (512 MB write)"},
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                          "frac": tf / peak,
@@ -656,6 +657,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (n=10000, batched, serving) reported beside the headline")
     ap.add_argument("--factor-n", type=int, default=2000, help="factor: matrix size")
+    ap.add_argument("--dag-tiles", type=int, default=0,
+                    help="largest diagonal block (in 128-row tiles) of one task-graph launch of the "
+                         "mixed factorisation: 0 the library default, 1 none (plain recursion)")
     ap.add_argument("--scan-n", type=int, default=2000, help="scan: matrix size")
     ap.add_argument("--workload", default="solve", choices=["solve", "batched", "serving", "factor", "scan"],
                     help="solve: the n=2000 single-solve metric (default); batched: lambda paths "
@@ -699,6 +703,7 @@ def main():
     p = synth.config_problem(CONFIG_ID, instance=rank)
     prec = glasso.FP64 if args.precision == "fp64" else glasso.MIXED
     ctx = glasso.Context(local, precision=prec)
+    ctx.set_debug(glasso.DEBUG_TC_DAG_TILES, args.dag_tiles)
     stream = torch.cuda.current_stream(dev)
     ctx.set_stream(stream.cuda_stream)
     # the workload's input is the FP64 covariance S (eq. cov_estimate), formed
@@ -927,7 +932,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD,
                    "n": p.n, "m": p.m, "lambda": p.lam, "tol": p.tol, "input": "S (fp64) given",
-                   "precision": args.precision, "inner": args.inner,
+                   "precision": args.precision, "inner": args.inner, "dag_tiles": args.dag_tiles,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -174,7 +174,7 @@ glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
 
 /* Code-path counters (all contexts, counted always, since the last reset):
  * which variant of a step the solves took. */
-#define GLASSO_PATHS 8
+#define GLASSO_PATHS 9
 enum {
     GLASSO_PATH_CD_LAG2 = 0,       /* FP32 sweeps by the pipelined chain-CTA kernel */
     GLASSO_PATH_CD_PERSIST32 = 1,  /* FP32 sweeps by the one-copy kernel (its matrices did not fit) */
@@ -183,7 +183,9 @@ enum {
     GLASSO_PATH_LS_SERIES6 = 4,    /* ... by the six-term series */
     GLASSO_PATH_TC_FACTOR = 5,     /* tensor-core factorisations (line-search trials and fresh W) */
     GLASSO_PATH_TC_LEAVES = 6,     /* diagonal leaves factored inside them */
-    GLASSO_PATH_NS_STEPS = 7       /* Newton-Schulz refinement GEMMs of W */
+    GLASSO_PATH_NS_STEPS = 7,      /* Newton-Schulz refinement GEMMs of W */
+    GLASSO_PATH_TC_DAG = 8         /* diagonal blocks (up to 32 x 128) factored and inverted by one
+                                      persistent task-graph launch inside them */
 };
 
 typedef struct {
@@ -216,11 +218,16 @@ enum {
     GLASSO_DEBUG_WAIT_UNREACHABLE = 2, /* nonzero: the CD sweep's grid barrier waits for one arrival more
                                           than the grid holds, so every wait runs to its limit; the sweep
                                           returns early and the call reports GLASSO_ETIMEOUT */
-    GLASSO_DEBUG_LS_REJECT = 3         /* nonzero: every line-search trial is rejected (Section 6.1.2's
+    GLASSO_DEBUG_LS_REJECT = 3,        /* nonzero: every line-search trial is rejected (Section 6.1.2's
                                           backtracking runs out of trials: GLASSO_ELINESEARCH) */
+    GLASSO_DEBUG_TC_DAG_TILES = 4      /* not a fault: the largest diagonal block, in 128-row tiles,
+                                          that the mixed factorisation hands to one persistent
+                                          task-graph launch (larger ones recurse): 0 the default (32),
+                                          1 none (recursion down to one-tile leaves), 2 .. 32 that
+                                          many; so every variant stays testable and comparable */
 };
 
-/* Set one knob.  GLASSO_EINVAL for an unknown knob or a negative wait limit. */
+/* Set one knob.  GLASSO_EINVAL for an unknown knob or a value out of its range. */
 glasso_status glasso_set_debug(glasso_ctx *ctx, int knob, int64_t value);
 
 /* ---- step-level entry points (device pointers) ----------------------- */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libglasso.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["api.cu", "dense.cu", "scan.cu", "hier.cu", "cd.cu", "mixed.cu", "tc.cu", "cholinv_tc.cu",
-           "screen.cu", "pcd.cu"]
+           "screen.cu", "pcd.cu", "chol_dag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,6 +45,7 @@ def _compile(src: str, obj: str, verbose: bool) -> None:
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     hdrs = [os.path.join(CSRC, "glasso_internal.h"), os.path.join(CSRC, "tc_ptx.h"),
+            os.path.join(CSRC, "leaf32.cuh"),
             os.path.join(ROOT, "include", "glasso.h")]
     newest = max(os.path.getmtime(p) for p in srcs + hdrs + [__file__])
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:

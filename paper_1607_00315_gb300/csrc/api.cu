@@ -649,7 +649,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     auto fresh_factor = [&]() -> glasso_status {
         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
         CK(ensure_side(w));
-        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles));
         glasso_status s2 = factor_wait();
         if (s2 != GLASSO_OK) return s2;
         if (h->info != 0) return GLASSO_ENOTPD;
@@ -879,7 +879,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                         sv.mark_begin(4, eb);
                         CK(ensure_side(w));
-        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles));
                         sv.mark_end(4, eb, 2.0 * nd * nd * nd / 3.0);
                         glasso_status s2 = factor_wait();
                         if (s2 != GLASSO_OK) return s2;
@@ -1478,6 +1478,10 @@ glasso_status glasso_set_debug(glasso_ctx *ctx, int knob, int64_t value) {
             return GLASSO_OK;
         case GLASSO_DEBUG_WAIT_UNREACHABLE: w.dbg_wait_unreachable = value != 0; return GLASSO_OK;
         case GLASSO_DEBUG_LS_REJECT: w.dbg_ls_reject = value != 0; return GLASSO_OK;
+        case GLASSO_DEBUG_TC_DAG_TILES:
+            if (value < 0 || value > 32) return GLASSO_EINVAL;
+            w.dbg_dag_tiles = (int)value;
+            return GLASSO_OK;
         default: return GLASSO_EINVAL;
     }
 }
@@ -1672,7 +1676,8 @@ glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, 
     CTX_CK(trial32(A, FA, n, ldf, nullptr, nullptr, nullptr, nullptr, 0, 0.0, ctx->stream));
     sv.mark_begin(4, eb);
     CTX_CK(ensure_side(w));
-    CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream, w.side, w.ev_a, w.ev_b));
+    CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream, w.side, w.ev_a, w.ev_b,
+                            w.dbg_dag_tiles));
     sv.mark_end(4, eb, 2.0 * (double)n * n * n / 3.0);
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;

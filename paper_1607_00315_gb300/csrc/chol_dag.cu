@@ -1,0 +1,747 @@
+// Persistent tiled Cholesky factorisation with its inverse factor (FP32,
+// split-TF32 tensor-core tile products) of a diagonal block [o, o + s) of the
+// mixed path's matrix: the positive-definiteness test and log det A of the
+// line search (Section 6.1.2) and X = L^{-1}, from which W = X^T X of
+// eq. gradHes follows.  One cooperative launch walks a task graph over the
+// T x T lower tiles (128 x 128) of the block:
+//
+//   LEAF(k)      factor and invert tile (k, k)          -> L_kk (implicit), X_kk, Xt_kk
+//   PANEL(i, k)  L_ik = A_ik X_kk^T                     (in place of A_ik)
+//   UPD(i, j, k) A_ij -= L_ik L_jk^T, k < j <= i        (right-looking)
+//   ZU(i, j, k)  Y_ij += L_ik X_kj, j <= k < i          (kept transposed in Xt_ji)
+//   XF(i, j)     X_ij = -X_ii Y_ij, and Xt_ji = X_ij^T
+//
+// X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj is forward substitution on L X = I
+// by block rows.  The host orders the tasks by a list schedule on the
+// critical path (a topological order); each CTA takes the next task from an
+// atomic counter and waits, bounded, until the task's inputs are final.  The
+// inputs are tracked by per-tile version counters: ver[i][j] counts the
+// completed writes of A's tile (updates k = 0 .. j - 1, then the leaf or the
+// panel), xver[i][j] those of Y_ij / X_ij (the i - j products, then XF; 1
+// for the leaf's X_ii).  A task waits only on tasks earlier in the order, and
+// every CTA of a cooperative launch is resident, so the lowest unfinished
+// task can always run: the walk cannot deadlock.  Every wait is bounded; on
+// expiry or a failed pivot the CTA raises a flag that stops every other CTA.
+//
+// Tile products: the k_tcx pipeline for one output tile per task (warp 0
+// issues the TMA loads of 128 x 32 FP32 tiles into a 3-stage ring, warps 2-5
+// split them into TF32 hi and lo parts, warp 1 issues the three MMAs per
+// 8-wide step into TMEM, warps 6-13 drain TMEM and write the tile), with the
+// mbarrier phases carried across the tasks of a CTA.  The products of the
+// factorisation (PANEL, UPD) sum their main hi hi terms outside the tensor
+// core, as k_tcx does for the log-det's accuracy; the inverse's products
+// (ZU, XF) accumulate in TMEM.
+#include <cuda.h>
+#include <math.h>
+
+#include <algorithm>
+#include <initializer_list>
+#include <map>
+#include <mutex>
+#include <queue>
+#include <utility>
+#include <vector>
+
+#include "glasso_internal.h"
+#include "leaf32.cuh"
+#include "tc_ptx.h"
+
+namespace glx {
+namespace {
+using namespace ptx;
+
+constexpr int DM = 128, DK = 32, DST = 3, DNB = 3, DNK = DM / DK;
+constexpr int DTHREADS = 448;
+constexpr uint32_t DTILE = DM * DK * 4;  // 16 KB
+constexpr int DAG_MAX_T = 32;            // tiles per side that one walk takes
+
+enum : int { T_LEAF = 0, T_PANEL = 1, T_UPD = 2, T_ZU = 3, T_XF = 4 };
+
+struct __align__(1024) DSmem {
+    union {
+        struct {
+            float a[DST][DM * DK];
+            float b[DST][DM * DK];
+            float alo[DST][DM * DK];
+            float blo[DST][DM * DK];
+        } g;
+        float leaf[leaf::LEAF_SMEM / sizeof(float)];
+    } u;
+    unsigned long long full[DST], conv[DST], empty[DST], done;
+    unsigned long long mfull[DNB], mfree[DNB];
+    uint32_t tmem;
+    int task, stop;
+    leaf::LeafShared lsh;
+};
+constexpr size_t DSMEM = sizeof(DSmem) + 1024;
+static_assert(DSMEM <= 227 * 1024, "shared memory of the persistent factorisation");
+
+struct DArgs {
+    const int4 *tasks;  // {kind, i, j, k}, in the order of the list schedule
+    int ntasks, T;
+    int64_t o, s, ld;   // the block [o, o + s) of n x n matrices with row stride ld
+    float *A, *X, *Xt;  // A: lower tiles overwritten (panels hold L); X lower, Xt upper
+    double *ldiag;
+    unsigned *ver, *xver, *next, *abort;  // zeroed before the launch
+    int *info, *err;
+    long long wait_cycles;
+};
+
+__device__ __forceinline__ float tf32_round_d(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void proxy_fence_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void proxy_fence_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait until *p >= target; false on expiry (err = code, abort raised)
+// or when another CTA raised abort.
+__device__ bool wait_ge(const unsigned *p, unsigned target, const DArgs &a, int code) {
+    if (ld_acquire(p) >= target) return true;
+    const long long t0 = cycles();
+    for (;;) {
+        __nanosleep(32);
+        if (ld_acquire(p) >= target) return true;
+        if (*(volatile unsigned *)a.abort) return false;
+        if (cycles() - t0 > a.wait_cycles) {
+            atomicCAS(a.err, 0, code);
+            atomicExch(a.abort, 1u);
+            return false;
+        }
+    }
+}
+
+// The inputs of task t are final (thread 0).
+__device__ bool wait_inputs(const int4 t, const DArgs &a) {
+    const int T = a.T, i = t.y, j = t.z, k = t.w;
+    const unsigned *ver = a.ver, *xver = a.xver;
+    switch (t.x) {
+    case T_LEAF:
+        return wait_ge(ver + k * T + k, (unsigned)k, a, 21);
+    case T_PANEL:
+        return wait_ge(ver + k * T + k, (unsigned)k + 1, a, 22) && wait_ge(ver + i * T + k, (unsigned)k, a, 22);
+    case T_UPD:
+        return wait_ge(ver + i * T + k, (unsigned)k + 1, a, 23) &&
+               wait_ge(ver + j * T + k, (unsigned)k + 1, a, 23) && wait_ge(ver + i * T + j, (unsigned)k, a, 23);
+    case T_ZU:
+        return wait_ge(xver + k * T + j, (unsigned)(k - j + 1), a, 24) &&
+               wait_ge(ver + i * T + k, (unsigned)k + 1, a, 24) &&
+               wait_ge(xver + i * T + j, (unsigned)(k - j), a, 24);
+    default:  // T_XF
+        return wait_ge(xver + i * T + j, (unsigned)(i - j), a, 25) && wait_ge(xver + i * T + i, 1u, a, 25);
+    }
+}
+
+// Publish task t's outputs (thread 0, after the CTA barrier that follows the
+// writes).
+__device__ void publish(const int4 t, const DArgs &a) {
+    const int T = a.T, i = t.y, j = t.z, k = t.w;
+    __threadfence();
+    switch (t.x) {
+    case T_LEAF:  // (ver[k][k] was published once X_kk was written)
+        atomicAdd(a.xver + k * T + k, 1u);
+        break;
+    case T_PANEL:
+        atomicAdd(a.ver + i * T + k, 1u);
+        break;
+    case T_UPD:
+        atomicAdd(a.ver + i * T + j, 1u);
+        break;
+    default:  // T_ZU, T_XF
+        atomicAdd(a.xver + i * T + j, 1u);
+        break;
+    }
+}
+
+// The operands, the depth offset and the output of a product task.
+struct GemmTask {
+    const CUtensorMap *p, *q;
+    int py, qy, kx;      // tile rows of P and Q, first column of the depth range
+    bool drain;
+    int mode;            // 0: out = alpha C, 1: out -= C, 2: out += C
+    bool lower_only;     // (mode 1 on a diagonal tile) only entries c <= r
+    float alpha;
+    float *out;          // the output tile's (0, 0)
+    float *outT;         // optional: outT[c][r] = alpha C[r][c]
+    int64_t rows, cols;  // valid rows / columns of the output tile
+};
+
+__device__ GemmTask gemm_of(const int4 t, const DArgs &a, const CUtensorMap *tA, const CUtensorMap *tX,
+                            const CUtensorMap *tXt) {
+    const int i = t.y, j = t.z, k = t.w;
+    const int64_t ld = a.ld, s = a.s;
+    float *A = a.A + a.o * ld + a.o, *X = a.X + a.o * ld + a.o, *Xt = a.Xt + a.o * ld + a.o;
+    GemmTask g;
+    g.outT = nullptr;
+    g.lower_only = false;
+    g.alpha = 1.f;
+    switch (t.x) {
+    case T_PANEL:  // L_ik = A_ik X_kk^T
+        g.p = tA; g.py = i; g.q = tX; g.qy = k; g.kx = k;
+        g.drain = true; g.mode = 0;
+        g.out = A + (int64_t)i * DM * ld + (int64_t)k * DM;
+        g.rows = s - (int64_t)i * DM; g.cols = s - (int64_t)k * DM;
+        break;
+    case T_UPD:  // A_ij -= L_ik L_jk^T
+        g.p = tA; g.py = i; g.q = tA; g.qy = j; g.kx = k;
+        g.drain = true; g.mode = 1; g.lower_only = i == j;
+        g.out = A + (int64_t)i * DM * ld + (int64_t)j * DM;
+        g.rows = s - (int64_t)i * DM; g.cols = s - (int64_t)j * DM;
+        break;
+    case T_ZU:  // Yt_ji (+)= Xt_jk L_ik^T  (= (L_ik X_kj)^T)
+        g.p = tXt; g.py = j; g.q = tA; g.qy = i; g.kx = k;
+        g.drain = false; g.mode = k == j ? 0 : 2;
+        g.out = Xt + (int64_t)j * DM * ld + (int64_t)i * DM;
+        g.rows = s - (int64_t)j * DM; g.cols = s - (int64_t)i * DM;
+        break;
+    default:  // T_XF: X_ij = -X_ii Y_ij = -X_ii Yt_ji^T, and Xt_ji = X_ij^T
+        g.p = tX; g.py = i; g.q = tXt; g.qy = j; g.kx = i;
+        g.drain = false; g.mode = 0; g.alpha = -1.f;
+        g.out = X + (int64_t)i * DM * ld + (int64_t)j * DM;
+        g.outT = Xt + (int64_t)j * DM * ld + (int64_t)i * DM;
+        g.rows = s - (int64_t)i * DM; g.cols = s - (int64_t)j * DM;
+        break;
+    }
+    g.rows = g.rows < DM ? g.rows : DM;
+    g.cols = g.cols < DM ? g.cols : DM;
+    return g;
+}
+
+// Per-CTA running counts that fix every mbarrier's phase: k-tiles loaded,
+// pairs of 8-wide steps drained, products completed.
+struct Phases {
+    unsigned kt, pairs, dones;
+};
+
+// One product task on the whole CTA.  Returns false if a bounded wait expired
+// (err set).
+__device__ bool run_gemm(DSmem &sm, uint32_t tmem, const GemmTask &g, Phases &ph, const DArgs &a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lw = warp & 3;
+    const uint32_t lane_off = (uint32_t)(lw * 32) << 16;
+    bool ok = true;
+    int issued = 0;
+    if (warp >= 6) {
+        constexpr int HC = DM / 2;
+        const uint32_t col0 = (uint32_t)(((warp - 6) >> 2) * HC);
+        float acc[HC];
+#pragma unroll
+        for (int c = 0; c < HC; ++c) acc[c] = 0.f;
+        if (g.drain) {
+            constexpr int npairs = DNK * (DK / 16);
+            for (int pr = 0; pr < npairs; ++pr) {
+                const unsigned P = ph.pairs + pr;
+                const int b = (int)(P % DNB);
+                const bool got = __all_sync(0xffffffffu, mbar_wait(&sm.mfull[b], (P / DNB) & 1));
+                if (!got) {
+                    if (lane == 0) atomicCAS(a.err, 0, 16);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t v0[32], v1[32];
+                tmem_ld32_issue(tmem + lane_off + 128u * (uint32_t)(b + 1) + col0, v0);
+                tmem_ld32_issue(tmem + lane_off + 128u * (uint32_t)(b + 1) + col0 + 32u, v1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    acc[c] += __uint_as_float(v0[c]);
+                    acc[32 + c] += __uint_as_float(v1[c]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) arrive(&sm.mfree[b]);
+            }
+        }
+        __syncwarp();
+        if (ok) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.done, ph.dones & 1));
+            if (!ok && lane == 0) atomicCAS(a.err, 0, 14);
+        }
+        tc_fence_after();
+        float(*Ct)[DM + 1] = reinterpret_cast<float(*)[DM + 1]>(&sm.u.g.a[0][0]);
+        if (ok) {
+            const int rl = lw * 32 + lane;
+#pragma unroll
+            for (int cb = 0; cb < HC / 32; ++cb) {
+                float v[32];
+                tmem_ld32(tmem + lane_off + col0 + (uint32_t)(cb * 32), v);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) Ct[rl][col0 + cb * 32 + c] = acc[cb * 32 + c] + v[c];
+            }
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (ok) {
+            const int wr = (threadIdx.x - 192) >> 5;  // 8 warps x 32 lanes
+            const int64_t ld = a.ld;
+            if (g.mode != 0) {
+                // read-modify-write through L2: four rows' loads before their stores
+                const float sg = g.mode == 1 ? -1.f : 1.f;
+#pragma unroll 1
+                for (int r0 = wr * 4; r0 < DM; r0 += 32) {
+                    float cur[4][DM / 32];
+                    bool act[4][DM / 32];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int p = 0; p < DM / 32; ++p) {
+                            const int r = r0 + u, c = lane + 32 * p;
+                            act[u][p] = r < g.rows && c < g.cols && (!g.lower_only || c <= r);
+                            cur[u][p] = act[u][p] ? __ldcg(g.out + r * ld + c) : 0.f;
+                        }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int p = 0; p < DM / 32; ++p)
+                            if (act[u][p]) {
+                                const int r = r0 + u, c = lane + 32 * p;
+                                g.out[r * ld + c] = fmaf(sg, Ct[r][c], cur[u][p]);
+                            }
+                }
+            } else {
+#pragma unroll 1
+                for (int r = wr; r < g.rows; r += 8)
+#pragma unroll
+                    for (int p = 0; p < DM / 32; ++p) {
+                        const int c = lane + 32 * p;
+                        if (c < g.cols) g.out[r * ld + c] = g.alpha * Ct[r][c];
+                    }
+            }
+            if (g.outT) {
+#pragma unroll 1
+                for (int c = wr; c < g.cols; c += 8)
+#pragma unroll
+                    for (int p = 0; p < DM / 32; ++p) {
+                        const int r = lane + 32 * p;
+                        if (r < g.rows) g.outT[c * ld + r] = g.alpha * Ct[r][c];
+                    }
+            }
+            proxy_fence_global();  // read by other CTAs' TMA loads
+        }
+    } else if (warp == 0) {
+        if (lane == 0) {
+            for (int kt = 0; kt < DNK; ++kt) {
+                const unsigned G = ph.kt + kt;
+                const int s = (int)(G % DST);
+                if (G >= DST && !mbar_wait(&sm.empty[s], ((G / DST) & 1) ^ 1)) {
+                    atomicCAS(a.err, 0, 11);
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&sm.full[s], 2 * DTILE);
+                const int x = (g.kx * DM) + kt * DK;
+                tma_2d(&sm.u.g.a[s][0], g.p, x, g.py * DM, &sm.full[s]);
+                tma_2d(&sm.u.g.b[s][0], g.q, x, g.qy * DM, &sm.full[s]);
+                ++issued;
+            }
+            if (ok) {
+                ok = mbar_wait(&sm.done, ph.dones & 1);
+                if (!ok) atomicCAS(a.err, 0, 17);
+            }
+            if (!ok) {
+                // let the copies still in flight land (bounded) before leaving
+                for (int kt = issued > DST ? issued - DST : 0; kt < issued; ++kt) {
+                    const unsigned G = ph.kt + kt;
+                    mbar_wait(&sm.full[G % DST], (G / DST) & 1);
+                }
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tf32_idesc(DM, DM);
+            for (int kt = 0; kt < DNK && ok; ++kt) {
+                const unsigned G = ph.kt + kt;
+                const int s = (int)(G % DST);
+                if (!mbar_wait(&sm.conv[s], (G / DST) & 1)) {
+                    atomicCAS(a.err, 0, 12);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned long long ah = sw128_desc(smem_u32(&sm.u.g.a[s][0]));
+                const unsigned long long bh = sw128_desc(smem_u32(&sm.u.g.b[s][0]));
+                const unsigned long long al = sw128_desc(smem_u32(&sm.u.g.alo[s][0]));
+                const unsigned long long bl = sw128_desc(smem_u32(&sm.u.g.blo[s][0]));
+#pragma unroll
+                for (int kk = 0; kk < DK / 8; ++kk) {
+                    const uint32_t first = (kt | kk) != 0;
+                    if (g.drain) {
+                        const int step = kt * (DK / 8) + kk;
+                        const unsigned P = ph.pairs + (unsigned)(step >> 1);
+                        const int b = (int)(P % DNB);
+                        if ((step & 1) == 0 && P >= DNB && !mbar_wait(&sm.mfree[b], ((P / DNB) & 1) ^ 1)) {
+                            atomicCAS(a.err, 0, 15);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        umma_tf32(tmem + 128u * (uint32_t)(b + 1), ah + 2ull * kk, bh + 2ull * kk, idesc,
+                                  (uint32_t)(step & 1));
+                        if (step & 1) umma_commit(&sm.mfull[b]);
+                        umma_tf32(tmem, ah + 2ull * kk, bl + 2ull * kk, idesc, first);
+                    } else {
+                        umma_tf32(tmem, ah + 2ull * kk, bh + 2ull * kk, idesc, first);
+                        umma_tf32(tmem, ah + 2ull * kk, bl + 2ull * kk, idesc, 1u);
+                    }
+                    umma_tf32(tmem, al + 2ull * kk, bh + 2ull * kk, idesc, 1u);
+                }
+                if (ok) umma_commit(&sm.empty[s]);
+            }
+            if (ok) umma_commit(&sm.done);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else {
+        // warps 2-5: split each landed stage into hi (in place) and lo
+        const int ct = threadIdx.x - 64;  // 0 .. 127
+        for (int kt = 0; kt < DNK; ++kt) {
+            const unsigned G = ph.kt + kt;
+            const int s = (int)(G % DST);
+            if (!__all_sync(0xffffffffu, mbar_wait(&sm.full[s], (G / DST) & 1))) {
+                if (lane == 0) atomicCAS(a.err, 0, 13);
+                ok = false;
+                break;
+            }
+            float4 *pa = reinterpret_cast<float4 *>(&sm.u.g.a[s][0]);
+            float4 *pb = reinterpret_cast<float4 *>(&sm.u.g.b[s][0]);
+            float4 *la = reinterpret_cast<float4 *>(&sm.u.g.alo[s][0]);
+            float4 *lb = reinterpret_cast<float4 *>(&sm.u.g.blo[s][0]);
+#pragma unroll
+            for (int r = 0; r < (DM * DK / 4) / 128; ++r) {
+                const int q = ct + 128 * r;
+                float4 v = pa[q], h;
+                h.x = tf32_round_d(v.x); h.y = tf32_round_d(v.y);
+                h.z = tf32_round_d(v.z); h.w = tf32_round_d(v.w);
+                pa[q] = h;
+                la[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                v = pb[q];
+                h.x = tf32_round_d(v.x); h.y = tf32_round_d(v.y);
+                h.z = tf32_round_d(v.z); h.w = tf32_round_d(v.w);
+                pb[q] = h;
+                lb[q] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            }
+            proxy_fence_shared();
+            __syncwarp();
+            if (lane == 0) arrive(&sm.conv[s]);
+        }
+        if (ok) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.done, ph.dones & 1));
+            if (!ok && lane == 0) atomicCAS(a.err, 0, 18);
+        }
+    }
+    ph.kt += DNK;
+    if (g.drain) ph.pairs += DNK * (DK / 16);
+    ph.dones += 1;
+    return ok;
+}
+
+__global__ void __launch_bounds__(DTHREADS, 1)
+    k_chol_dag(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tX,
+               const __grid_constant__ CUtensorMap tXt, const DArgs a) {
+    extern __shared__ unsigned char raw[];
+    DSmem &sm = *reinterpret_cast<DSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < DST; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.conv[s], 4);
+            mbar_init(&sm.empty[s], 1);
+        }
+        for (int b = 0; b < DNB; ++b) {
+            mbar_init(&sm.mfull[b], 1);
+            mbar_init(&sm.mfree[b], 8);
+        }
+        mbar_init(&sm.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tX) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tXt) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    Phases ph{0u, 0u, 0u};
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            int t = -1;
+            if (*(volatile int *)a.info != 0 || *(volatile unsigned *)a.abort) {
+                stop = 1;
+            } else {
+                t = (int)atomicAdd(a.next, 1u);
+                if (t >= a.ntasks) stop = 1;
+                else if (!wait_inputs(a.tasks[t], a)) stop = 1;
+                else proxy_fence_global();  // the inputs are read by TMA loads too
+            }
+            sm.task = t;
+            sm.stop = stop;
+        }
+        __syncthreads();
+        if (sm.stop) break;
+        const int4 t = a.tasks[sm.task];
+        bool ok = true;
+        if (t.x == T_LEAF) {
+            const int64_t d0 = a.o + (int64_t)t.w * DM;
+            const int sl = (int)min((int64_t)DM, a.s - (int64_t)t.w * DM);
+            const int f = leaf::leaf_factor(a.A, a.ld, d0, sl, a.X, a.ldiag, sm.u.leaf, &sm.lsh, a.wait_cycles);
+            if (f == 0) {
+                // X_kk is final: the panels of column k may start while Xt_kk
+                // (read only by the inverse's products) is written
+                proxy_fence_global();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    atomicAdd(a.ver + t.w * a.T + t.w, 1u);
+                }
+                leaf::leaf_store_xt(a.ld, d0, sl, a.Xt, sm.u.leaf);
+                proxy_fence_global();
+            } else {
+                ok = false;
+                if (threadIdx.x == 0) {
+                    if (f > 0) atomicCAS(a.info, 0, (int)(d0 + f));
+                    else atomicCAS(a.err, 0, 26);
+                }
+            }
+        } else {
+            const GemmTask g = gemm_of(t, a, &tA, &tX, &tXt);
+            ok = run_gemm(sm, tmem, g, ph, a);
+        }
+        proxy_fence_shared();  // this task's generic writes to shared memory precede the next TMA loads
+        tc_fence_before();
+        const int all_ok = __syncthreads_and(ok ? 1 : 0);
+        tc_fence_after();
+        if (threadIdx.x == 0) {
+            if (!all_ok) atomicExch(a.abort, 1u);  // a wait expired in this CTA: stop every CTA
+            else if (*(volatile int *)a.info == 0) publish(t, a);
+        }
+        if (!all_ok) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------- host side
+
+struct Plan {
+    int4 *dev = nullptr;
+    int ntasks = 0;
+    int width = 0;  // the most tasks the list schedule ran at once
+};
+
+// The task graph of T x T tiles and its order: a list schedule with G
+// workers, the ready task with the longest path to the end first (estimated
+// durations: leaf 10, product 3 units).  Start order is a topological order.
+std::vector<int4> plan_tasks(int T, int G, int *width) {
+    std::vector<int4> tk;
+    std::vector<std::vector<int>> deps;
+    auto id3 = [T](int i, int j, int k) { return ((int64_t)i * T + j) * T + k; };
+    std::vector<int> leaf(T, -1), panel((size_t)T * T, -1), xf((size_t)T * T, -1);
+    std::vector<int> upd((size_t)T * T * T, -1), zu((size_t)T * T * T, -1);
+    auto add = [&](int kind, int i, int j, int k, std::initializer_list<int> d) {
+        tk.push_back(make_int4(kind, i, j, k));
+        std::vector<int> dv;
+        for (int x : d)
+            if (x >= 0) dv.push_back(x);
+        deps.push_back(std::move(dv));
+        return (int)tk.size() - 1;
+    };
+    for (int k = 0; k < T; ++k) {
+        leaf[k] = add(T_LEAF, k, k, k, {k > 0 ? upd[id3(k, k, k - 1)] : -1});
+        for (int i = k + 1; i < T; ++i)
+            panel[i * T + k] = add(T_PANEL, i, k, k, {leaf[k], k > 0 ? upd[id3(i, k, k - 1)] : -1});
+        for (int j = k + 1; j < T; ++j)
+            for (int i = j; i < T; ++i)
+                upd[id3(i, j, k)] = add(T_UPD, i, j, k,
+                                        {panel[i * T + k], i != j ? panel[j * T + k] : -1,
+                                         k > 0 ? upd[id3(i, j, k - 1)] : -1});
+    }
+    for (int i = 1; i < T; ++i)
+        for (int j = 0; j < i; ++j) {
+            for (int k = j; k < i; ++k)
+                zu[id3(i, j, k)] = add(T_ZU, i, j, k, {k == j ? leaf[j] : xf[k * T + j], panel[i * T + k],
+                                                       k > j ? zu[id3(i, j, k - 1)] : -1});
+            xf[i * T + j] = add(T_XF, i, j, j, {zu[id3(i, j, i - 1)], leaf[i]});
+        }
+    const int N = (int)tk.size();
+    std::vector<double> dur(N), bl(N, 0.0);
+    std::vector<std::vector<int>> succ(N);
+    std::vector<int> indeg(N, 0);
+    for (int t = 0; t < N; ++t) {
+        dur[t] = tk[t].x == T_LEAF ? 10.0 : 3.0;
+        for (int d : deps[t]) {
+            succ[d].push_back(t);
+            ++indeg[t];
+        }
+    }
+    // bottom levels, in reverse creation order (every task is created after
+    // its dependencies)
+    for (int t = N - 1; t >= 0; --t) {
+        double m = 0.0;
+        for (int s2 : succ[t]) m = std::max(m, bl[s2]);
+        bl[t] = dur[t] + m;
+    }
+    // list schedule
+    using Ready = std::pair<double, int>;  // (priority, -id) max-heap
+    std::priority_queue<Ready> ready;
+    using Ev = std::pair<double, int>;  // (finish time, task), min-heap
+    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
+    std::vector<int> deg(indeg);
+    for (int t = 0; t < N; ++t)
+        if (deg[t] == 0) ready.push({bl[t], -t});
+    std::vector<int4> out;
+    out.reserve(N);
+    double now = 0.0;
+    int busy = 0, wmax = 0;
+    while ((int)out.size() < N) {
+        while (busy < G && !ready.empty()) {
+            const int t = -ready.top().second;
+            ready.pop();
+            out.push_back(tk[t]);
+            running.push({now + dur[t], t});
+            ++busy;
+        }
+        wmax = std::max(wmax, busy);
+        if (running.empty()) break;  // (cannot happen: the graph is acyclic)
+        const Ev e = running.top();
+        running.pop();
+        now = e.first;
+        --busy;
+        for (int s2 : succ[e.second])
+            if (--deg[s2] == 0) ready.push({bl[s2], -s2});
+    }
+    *width = wmax;
+    return out;
+}
+
+std::mutex g_plan_mu;
+std::map<std::pair<int, int>, Plan> g_plans;  // (device, T)
+OncePerDevice g_dag_once;
+
+cudaError_t get_plan(int dev, int T, int G, Plan *out) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find({dev, T});
+    if (it != g_plans.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    Plan p;
+    const std::vector<int4> tasks = plan_tasks(T, G, &p.width);
+    p.ntasks = (int)tasks.size();
+    cudaError_t e = cudaMalloc(&p.dev, tasks.size() * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(p.dev, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p.dev);
+        return e;
+    }
+    g_plans[{dev, T}] = p;
+    *out = p;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool chol_dag_fits(int64_t s, int max_tiles) {
+    const int64_t mt = max_tiles > 0 && max_tiles < DAG_MAX_T ? max_tiles : DAG_MAX_T;
+    return s > DM && (s + DM - 1) / DM <= mt;
+}
+
+// Factor the diagonal block [o, o + s) (o a multiple of 128, 128 < s <= 32 *
+// 128) of A (FP32, lower triangle, row stride ld, a multiple of 32) and invert
+// its factor: the block of X (lower) and Xt = X^T (upper) -- their tiles
+// outside the block's lower (upper) triangle are not written -- and the FP64
+// diagonal of L into ldiag[o ..].  A's block is overwritten.  scratch: 2 T^2
+// + 4 unsigned of device memory (T = ceil(s / 128)), zeroed here.  sc->info =
+// first failing pivot + 1; sc->tc_err = nonzero if a bounded wait expired.
+cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float *Xt, double *ldiag,
+                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles) {
+    if (!chol_dag_fits(s) || ld % 32 != 0 || o % DM != 0) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = g_dag_once.run(dev, [](int) {
+        return cudaFuncSetAttribute(k_chol_dag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DSMEM);
+    });
+    if (e != cudaSuccess) return e;
+    int nsm = 0, occ = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_chol_dag, DTHREADS, DSMEM);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int T = (int)((s + DM - 1) / DM);
+    Plan p;
+    e = get_plan(dev, T, nsm, &p);
+    if (e != cudaSuccess) return e;
+    const int G = std::max(1, std::min(nsm, p.width));
+    CUtensorMap mA, mX, mXt;
+    e = make_tmap(&mA, A + o * ld + o, s, s, ld);
+    if (e != cudaSuccess) return e;
+    e = make_tmap(&mX, X + o * ld + o, s, s, ld);
+    if (e != cudaSuccess) return e;
+    e = make_tmap(&mXt, Xt + o * ld + o, s, s, ld);
+    if (e != cudaSuccess) return e;
+    const size_t nctr = 2 * (size_t)T * T + 4;
+    e = cudaMemsetAsync(scratch, 0, nctr * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    DArgs a;
+    a.tasks = p.dev;
+    a.ntasks = p.ntasks;
+    a.T = T;
+    a.o = o;
+    a.s = s;
+    a.ld = ld;
+    a.A = A;
+    a.X = X;
+    a.Xt = Xt;
+    a.ldiag = ldiag;
+    a.ver = scratch;
+    a.xver = scratch + (size_t)T * T;
+    a.next = scratch + 2 * (size_t)T * T;
+    a.abort = a.next + 1;
+    a.info = &sc->info;
+    a.err = &sc->tc_err;
+    a.wait_cycles = wait_cycles > 0 ? wait_cycles : 2000000000ll;  // about 1 s
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(DTHREADS);
+    cfg.dynamicSmemBytes = DSMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_chol_dag, mA, mX, mXt, a);
+    counted(1);
+    if (e != cudaSuccess) return e;
+    path_hit(GLASSO_PATH_TC_DAG);
+    path_hit(GLASSO_PATH_TC_LEAVES, T);
+    return cudaGetLastError();
+}
+
+}  // namespace glx

@@ -14,6 +14,9 @@
 //   [L22, X22] = node(A22)
 //   Yt  = Xt11 L21^T  (= (L21 X11)^T) into scratch Z12
 //   X21 = -X22 Yt^T, and Xt12 = X21^T
+// A node of at most 32 tiles (s <= 4096; the caller may lower the bound or
+// ask for the plain recursion) is instead factored and inverted by one
+// persistent task-graph launch (chol_dag.cu).
 // Leaves (s <= 128) are factored and inverted by one CTA in shared memory
 // (FP32), which also records the FP64 diagonal of L for log det A.  Per
 // output tile the k range skips the zero triangles of X and Xt = X^T.
@@ -467,10 +470,16 @@ struct Rec {
     cudaStream_t st;
     cudaStream_t side;  // optional: Yt runs here, beside SYRK and the right subtree
     cudaEvent_t ev_a, ev_b;
+    int dag_tiles;      // largest block of one task-graph launch (0: default, 1: none)
 };
 
 cudaError_t node(const Rec &r, int64_t o, int64_t s) {
     if (s <= 128) return chol_leaf32(r.A, r.ld, o, (int)s, r.X, r.Xt, r.ldiag, r.sc, r.st);
+    // the task graph's counters use Z's diagonal block, which no enclosing
+    // node's scratch (Z21 below it, Z12 beside it) overlaps
+    if (r.dag_tiles != 1 && chol_dag_fits(s, r.dag_tiles))
+        return chol_dag(r.A, r.ld, o, s, r.X, r.Xt, r.ldiag, reinterpret_cast<unsigned *>(r.Z + o * r.ld + o),
+                        r.sc, r.st);
     const int64_t s1 = ((s / 2) + 127) / 128 * 128, s2 = s - s1;
     const int64_t ld = r.ld;
     int *err = &r.sc->tc_err;
@@ -529,12 +538,12 @@ cudaError_t node(const Rec &r, int64_t o, int64_t s) {
 // log det A (when info == 0), sc->tc_err = nonzero if a bounded wait expired.
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z,
                        double *ldiag, DevScalars *sc, cudaStream_t st, cudaStream_t side,
-                       cudaEvent_t ev_a, cudaEvent_t ev_b) {
+                       cudaEvent_t ev_a, cudaEvent_t ev_b, int dag_tiles) {
     if (ld % 32 != 0 || ld < n) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (side && (!ev_a || !ev_b)) return cudaErrorInvalidValue;
-    Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b};
+    Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b, dag_tiles};
     path_hit(GLASSO_PATH_TC_FACTOR);
     e = node(r, 0, n);
     if (e != cudaSuccess) return e;

@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "glasso_internal.h"
+#include "leaf32.cuh"
 
 namespace glx {
 namespace {
@@ -137,10 +138,7 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return r;
 }
 
-__device__ __forceinline__ float rsqrt_newton(float d) {
-    float r = rsqrtf(d);
-    return r * fmaf(-0.5f * d * r, r, 1.5f);
-}
+__device__ __forceinline__ float rsqrt_newton(float d) { return leaf::rsqrt_f32(d); }
 
 // One warp factors the kw x kw lower block B (shared, row-major, padded) in
 // place and writes Xs = L^{-1}, in the arithmetic of T.  (On this GPU one
@@ -372,331 +370,26 @@ __global__ void __launch_bounds__(TPB, 2) k_potrf_trail(T *__restrict__ A, int64
     }
 }
 
-// Leaf of the tensor-core factorisation (FP32): one CTA factors and inverts
-// the diagonal block [o, o + s), s <= 128, of A (row stride ld) in shared
-// memory, in 8-wide steps: one thread factors and inverts each 8 x 8 diagonal
-// block in registers (the serial path: 16 such blocks), then the CTA forms
-// the panel L_ib = A_ib X_kk^T and the trailing update.  X = L^{-1} then
-// follows from the 8 x 8 inverses by doubling the block size,
-//   [X11 0; X21 X22] with X21 = -X22 (L21 X11),
-// with L21 X11 parked in the free upper quarter.  Rows beyond s are
-// identity.  Writes the s x s blocks of X (lower, zeros above) and Xt = X^T
-// (upper, zeros below), the FP64 diagonal of L into ldiag[o ..], and the
-// first failing pivot + 1 (global index) into sc->info.  (Column-at-a-time
-// forms of 32-wide diagonal blocks -- one warp or the whole CTA -- took about
-// 18 us per block on this GPU: long dependent chains through shared memory.)
-constexpr int LB = 128, LP = LB + 4;  // rows padded to 16-byte multiples
-constexpr size_t LEAF_SMEM = 2 * LB * LP * sizeof(float);
-
-// One thread: Cholesky of the 8 x 8 lower block a (registers) in place;
-// rd[i] = 1 / L_ii.  Returns 0 or the failing pivot + 1.
-__device__ __forceinline__ int thread_chol8(float (&a)[8][8], float (&rd)[8]) {
-    int fail = 0;  // recorded, not branched on: the pivot chain stays straight-line
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float d = a[j][j];
-        if (fail == 0 && !(d > 0.f)) fail = j + 1;
-        d = d > 0.f ? d : 1.f;
-        const float r = rsqrt_newton(d);
-        rd[j] = r;
-        a[j][j] = d * r;
-#pragma unroll
-        for (int i = j + 1; i < 8; ++i) a[i][j] *= r;
-#pragma unroll
-        for (int i = j + 1; i < 8; ++i)
-#pragma unroll
-            for (int k = j + 1; k <= i; ++k) a[i][k] = fmaf(-a[i][j], a[k][j], a[i][k]);
-    }
-    return fail;
-}
-
-__global__ void __launch_bounds__(TPB, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
-                                                    int s, float *__restrict__ Xo,
-                                                    float *__restrict__ Xto, double *__restrict__ ldiag,
-                                                    DevScalars *sc) {
+// Leaf of the tensor-core factorisation as a kernel of its own: one CTA of
+// leaf::LT threads (see leaf32.cuh); a failing pivot goes to sc->info as its
+// global index + 1, an expired wait to sc->tc_err.
+__global__ void __launch_bounds__(leaf::LT, 1) k_leaf32(const float *__restrict__ A, int64_t ld, int64_t o,
+                                                        int s, float *__restrict__ Xo,
+                                                        float *__restrict__ Xto, double *__restrict__ ldiag,
+                                                        DevScalars *sc) {
     pdl_wait();  // the block comes from the preceding kernel
     pdl_trigger();
     if (sc->info != 0) return;
     extern __shared__ float lsm[];
-    float(*L)[LP] = reinterpret_cast<float(*)[LP]>(lsm);
-    float(*X)[LP] = reinterpret_cast<float(*)[LP]>(lsm + LB * LP);
-    __shared__ int fshare;
-    const int tid = threadIdx.x;
-    constexpr int NQ = LB * LB / 4 / TPB;  // 16-byte groups per thread
-    // 16-byte loads of the rows (the block starts at a multiple of 128 in a
-    // matrix whose row stride is a multiple of 32 floats), all issued before
-    // the first shared-memory store
-    {
-        float4 v[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-            v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < s && c4 <= r) {
-                const float *src = A + (o + r) * ld + o + c4;
-                if (c4 + 3 < s) {
-                    v[q] = *reinterpret_cast<const float4 *>(src);
-                } else {
-                    v[q].x = src[0];
-                    if (c4 + 1 < s) v[q].y = src[1];
-                    if (c4 + 2 < s) v[q].z = src[2];
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-            const float e[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-            float f[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int cc = c4 + k;
-                f[k] = (cc <= r && r < s) ? e[k] : (r == cc ? 1.f : 0.f);
-            }
-            *reinterpret_cast<float4 *>(&L[r][c4]) = make_float4(f[0], f[1], f[2], f[3]);
-            *reinterpret_cast<float4 *>(&X[r][c4]) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-    if (tid == 0) fshare = 0;
-    __syncthreads();
-    // one thread: factor and invert the 8 x 8 diagonal block at d (registers;
-    // the eight columns of the inverse are independent chains, so one thread
-    // keeps them all in flight)
-    auto diag8 = [&](int d) {
-        float a[8][8], x[8][8], rd[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a[i][j] = (j <= i) ? L[d + i][d + j] : 0.f;
-        const int f = thread_chol8(a, rd);
-        if (f) {
-            fshare = d + f;
-            return;
-        }
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (i < cc) {
-                    x[i][cc] = 0.f;
-                } else {
-                    float sum = (i == cc) ? 1.f : 0.f;
-#pragma unroll
-                    for (int t = cc; t < i; ++t) sum = fmaf(-a[i][t], x[t][cc], sum);
-                    x[i][cc] = sum * rd[i];
-                }
-            }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (j <= i) L[d + i][d + j] = a[i][j];
-                X[d + i][d + j] = x[i][j];  // zeros above the diagonal
-            }
-    };
-    auto dot8 = [](float4 p0, float4 p1, float4 q0, float4 q1) {
-        float a0 = p0.x * q0.x, a1 = p0.y * q0.y;
-        a0 = fmaf(p0.z, q0.z, a0);
-        a1 = fmaf(p0.w, q0.w, a1);
-        a0 = fmaf(p1.x, q1.x, a0);
-        a1 = fmaf(p1.y, q1.y, a1);
-        a0 = fmaf(p1.z, q1.z, a0);
-        a1 = fmaf(p1.w, q1.w, a1);
-        return a0 + a1;
-    };
-    if (tid == 0) diag8(0);
-    __syncthreads();
-    for (int d0 = 0; d0 < LB; d0 += 8) {
-        // diagonal block d0 is factored (look-ahead from the previous step)
-        if (fshare) {
-            if (tid == 0) atomicCAS(&sc->info, 0, (int)(o + fshare));
-            return;
-        }
-        const int R = LB - d0 - 8;  // rows below the diagonal block
-        if (R == 0) break;
-        // panel: L[r][d0 + c] = L[r][d0 .. d0 + 7] . X[d0 + c][d0 .. d0 + 7]
-        // (X's diagonal block is zero above its diagonal)
-        float pv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + TPB * q;
-            pv[q] = 0.f;
-            if (idx < R * 8) {
-                const int r = d0 + 8 + idx / 8, c = idx % 8;
-                pv[q] = dot8(*reinterpret_cast<const float4 *>(&L[r][d0]),
-                             *reinterpret_cast<const float4 *>(&L[r][d0 + 4]),
-                             *reinterpret_cast<const float4 *>(&X[d0 + c][d0]),
-                             *reinterpret_cast<const float4 *>(&X[d0 + c][d0 + 4]));
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + TPB * q;
-            if (idx < R * 8) L[d0 + 8 + idx / 8][d0 + idx % 8] = pv[q];
-        }
-        __syncthreads();
-        const int b0 = d0 + 8, g = tid >> 5, c = tid & 31;
-        if (g == 0) {
-            // look-ahead: warp 0 updates the next diagonal block (36 entries)
-            // and one lane factors it while warps 1..7 update the rest
-            {
-                // entries e = c and c + 32 (< 36) of the block's lower triangle
-                int ii[2], jj[2];
-                float4 a0[2], a1[2], q0[2], q1[2];
-                float cur[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int e = c + 32 * u < 36 ? c + 32 * u : 0;
-                    int i = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);  // row of entry e (j <= i)
-                    if ((i + 1) * (i + 2) / 2 <= e) ++i;
-                    if (i * (i + 1) / 2 > e) --i;
-                    ii[u] = i;
-                    jj[u] = e - i * (i + 1) / 2;
-                    a0[u] = *reinterpret_cast<const float4 *>(&L[b0 + i][d0]);
-                    a1[u] = *reinterpret_cast<const float4 *>(&L[b0 + i][d0 + 4]);
-                    q0[u] = *reinterpret_cast<const float4 *>(&L[b0 + jj[u]][d0]);
-                    q1[u] = *reinterpret_cast<const float4 *>(&L[b0 + jj[u]][d0 + 4]);
-                    cur[u] = L[b0 + i][b0 + jj[u]];
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-                    if (c + 32 * u < 36) L[b0 + ii[u]][b0 + jj[u]] = cur[u] - dot8(a0[u], a1[u], q0[u], q1[u]);
-            }
-            __syncwarp();
-            if (c == 0) diag8(b0);
-        } else {
-            // trailing update of the lower part outside the next diagonal
-            // block, 4 x 4 register tiles (I, J), J <= I, in units of 4 from
-            // b0; tiles 0..2 (the next diagonal block) are warp 0's
-            const int TI = R / 4, ntl = TI * (TI + 1) / 2;
-            for (int qq = 3 + (tid - 32); qq < ntl; qq += TPB - 32) {
-                int I = (int)((sqrtf(8.f * qq + 1.f) - 1.f) * 0.5f);
-                if ((I + 1) * (I + 2) / 2 <= qq) ++I;
-                if (I * (I + 1) / 2 > qq) --I;
-                const int J = qq - I * (I + 1) / 2;
-                const int i0 = b0 + 4 * I, j0 = b0 + 4 * J;
-                float4 p0[4], p1[4], r0[4], r1[4], cv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    p0[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][d0]);
-                    p1[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][d0 + 4]);
-                    r0[u] = *reinterpret_cast<const float4 *>(&L[j0 + u][d0]);
-                    r1[u] = *reinterpret_cast<const float4 *>(&L[j0 + u][d0 + 4]);
-                    cv[u] = *reinterpret_cast<const float4 *>(&L[i0 + u][j0]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    float o4[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (I != J || v <= u) o4[v] -= dot8(p0[u], p1[u], r0[v], r1[v]);
-                    *reinterpret_cast<float4 *>(&L[i0 + u][j0]) = make_float4(o4[0], o4[1], o4[2], o4[3]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    for (int r = tid; r < s; r += TPB) ldiag[o + r] = (double)L[r][r];
-    // X = L^{-1} from the 8 x 8 diagonal inverses by doubling: for blocks of
-    // size bs = 16, 32, 64, 128 with halves h, X21 = -X22 (L21 X11).  The
-    // product T = L21 X11 is parked in the block's upper-right quarter (above
-    // the diagonal, masked out of X below).  Each thread forms a 4 x 4 tile.
-#pragma unroll 1
-    for (int bs = 16; bs <= LB; bs *= 2) {
-        const int h = bs / 2, th = h / 4, tpp = th * th, ntile = (LB / bs) * tpp;
-        for (int it = tid; it < ntile; it += TPB) {
-            const int p = (it / tpp) * bs, tt = it % tpp, r0 = 4 * (tt / th), c0 = 4 * (tt % th);
-            float acc[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 4
-            for (int k = c0; k < h; ++k) {  // X11[k][c] = 0 for k < c
-                const float4 xq = *reinterpret_cast<const float4 *>(&X[p + k][p + c0]);
-                const float xv[4] = {k >= c0 ? xq.x : 0.f, k >= c0 + 1 ? xq.y : 0.f,
-                                     k >= c0 + 2 ? xq.z : 0.f, k >= c0 + 3 ? xq.w : 0.f};
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float lv = L[p + h + r0 + a][p + k];
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(lv, xv[b], acc[a][b]);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                *reinterpret_cast<float4 *>(&X[p + r0 + a][p + h + c0]) =
-                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-        }
-        __syncthreads();
-        for (int it = tid; it < ntile; it += TPB) {
-            const int p = (it / tpp) * bs, tt = it % tpp, r0 = 4 * (tt / th), c0 = 4 * (tt % th);
-            float acc[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-            const int kend = r0 + 4 < h ? r0 + 4 : h;
-#pragma unroll 4
-            for (int k = 0; k < kend; ++k) {  // X22[r][k] = 0 for k > r
-                const float4 tq = *reinterpret_cast<const float4 *>(&X[p + k][p + h + c0]);
-                const float tv[4] = {tq.x, tq.y, tq.z, tq.w};
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float xv = k <= r0 + a ? X[p + h + r0 + a][p + h + k] : 0.f;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv, tv[b], acc[a][b]);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                *reinterpret_cast<float4 *>(&X[p + h + r0 + a][p + c0]) =
-                    make_float4(-acc[a][0], -acc[a][1], -acc[a][2], -acc[a][3]);
-        }
-        __syncthreads();
-    }
-    // X rows with 16-byte stores (zeros above the diagonal); X^T staged in
-    // L's space with stride LB + 1 (conflict-free transposition), then rows
-    // of X^T with 16-byte stores
-    float *Lt = lsm;
-    constexpr int LTS = LB + 1;
-#pragma unroll 4
-    for (int q = 0; q < NQ; ++q) {
-        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-        const float4 v = *reinterpret_cast<const float4 *>(&X[r][c4]);
-        float e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (c4 + k > r) e[k] = 0.f;
-        if (r < s && c4 < s) {
-            if (c4 + 3 < s) {
-                *reinterpret_cast<float4 *>(Xo + (o + r) * ld + o + c4) = make_float4(e[0], e[1], e[2], e[3]);
-            } else {
-                for (int k = 0; k < 4 && c4 + k < s; ++k) Xo[(o + r) * ld + o + c4 + k] = e[k];
-            }
-        }
-    }
-    __syncthreads();  // L is free (ldiag was read before the inverse)
-#pragma unroll 4
-    for (int q = 0; q < LB * LB / TPB; ++q) {
-        const int idx = tid + TPB * q, r = idx / LB, cc = idx % LB;
-        Lt[cc * LTS + r] = (cc <= r) ? X[r][cc] : 0.f;  // Lt[c][r] = X[r][c] (lower X)
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int q = 0; q < NQ; ++q) {
-        const int idx = tid + TPB * q, r = idx / (LB / 4), c4 = 4 * (idx % (LB / 4));
-        if (r >= s || c4 >= s) continue;
-        const float *row = Lt + r * LTS + c4;
-        if (c4 + 3 < s) {
-            *reinterpret_cast<float4 *>(Xto + (o + r) * ld + o + c4) = make_float4(row[0], row[1], row[2], row[3]);
-        } else {
-            for (int k = 0; k < 4 && c4 + k < s; ++k) Xto[(o + r) * ld + o + c4 + k] = row[k];
-        }
+    __shared__ leaf::LeafShared lsh;
+    const int f = leaf::leaf_factor(A, ld, o, s, Xo, ldiag, lsm, &lsh, 2000000000ll);
+    if (f == 0) {
+        leaf::leaf_store_xt(ld, o, s, Xto, lsm);
+    } else if (threadIdx.x == 0) {
+        if (f > 0) atomicCAS(&sc->info, 0, (int)(o + f));
+        else atomicCAS(&sc->tc_err, 0, 19);
     }
 }
-
 
 // log det A = 2 sum_i log L_ii from the FP64 diagonal of the factor,
 // deterministic single-CTA reduction.
@@ -923,14 +616,14 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
     static OncePerDevice once;
     int dev = 0;
     cudaError_t ie = once.run(dev, [](int) {
-        return cudaFuncSetAttribute(k_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LEAF_SMEM);
+        return cudaFuncSetAttribute(k_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf::LEAF_SMEM);
     });
     if (ie != cudaSuccess) return ie;
-    if (s < 1 || s > LB) return cudaErrorInvalidValue;
+    if (s < 1 || s > leaf::LB) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};  // programmatic serialisation, as for the GEMMs
     cfg.gridDim = dim3(1);
-    cfg.blockDim = dim3(TPB);
-    cfg.dynamicSmemBytes = LEAF_SMEM;
+    cfg.blockDim = dim3(leaf::LT);
+    cfg.dynamicSmemBytes = leaf::LEAF_SMEM;
     cfg.stream = st;
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

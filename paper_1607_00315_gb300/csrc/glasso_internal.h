@@ -169,6 +169,7 @@ struct Work {
     long long dbg_wait_cycles = 0;  // CD grid-barrier wait limit in SM cycles (0: about 2 s)
     int dbg_wait_unreachable = 0;   // the barrier waits for one arrival more than the grid holds
     int dbg_ls_reject = 0;          // every line-search trial is rejected
+    int dbg_dag_tiles = 0;          // largest task-graph block in tiles (0: default, 1: none)
 };
 
 }  // namespace glx
@@ -285,7 +286,12 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
 cudaError_t logdet_from_diag(const double *ldiag, int64_t n, DevScalars *sc, cudaStream_t st);
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z, double *ldiag,
                        DevScalars *sc, cudaStream_t st, cudaStream_t side = nullptr,
-                       cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr);
+                       cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, int dag_tiles = 0);
+// one persistent task-graph launch for a diagonal block (chol_dag.cu); a
+// block fits when 128 < s <= max_tiles * 128 (max_tiles 0: the default 32)
+bool chol_dag_fits(int64_t s, int max_tiles = 0);
+cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float *Xt, double *ldiag,
+                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles = 0);
 cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t ldw, DevScalars *sc,
                      cudaStream_t st);
 cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,

@@ -11,6 +11,8 @@ W = A^{-1} is held to kappa(A) 2^-14 relative (max norm), which keeps
 ||I - A W|| far below the 0.9 at which the Newton-Schulz refinement of the
 solve would restart.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -20,8 +22,15 @@ from paper_1607_00315_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def mctx():
+# The factorisation's variants (glasso_set_debug GLASSO_DEBUG_TC_DAG_TILES):
+# diagonal blocks of up to 32 tiles in one persistent task-graph launch (the
+# default), the plain recursion down to one-tile leaves, and the recursion
+# handing blocks of at most 4 tiles (at offsets o > 0) to the task graph.
+VARIANTS = {"task_graph": 0, "recursion": 1, "task_graph_4": 4}
+
+
+@pytest.fixture(scope="module", params=list(VARIANTS))
+def mctx(request):
     import torch
 
     from paper_1607_00315_gb300 import build, glasso
@@ -29,8 +38,18 @@ def mctx():
     build.build()
     torch.cuda.init()
     c = glasso.Context(0, precision=glasso.MIXED)
+    c.set_debug(glasso.DEBUG_TC_DAG_TILES, VARIANTS[request.param])
+    c.variant = request.param
     yield c
     c.close()
+
+
+@functools.lru_cache(maxsize=None)
+def _reference(n, seed):
+    A = _spd(n, seed)
+    info_ref, L = oracle.cholesky(A)
+    assert info_ref == 0
+    return A, oracle.logdet_from_chol(L), oracle.inverse_from_chol(L)
 
 
 def _dev(a):
@@ -55,14 +74,11 @@ def _run(mctx, A):
 
 
 # 1: one leaf; 100/128: one ragged / one full leaf; 129, 200, 300: two to
-# three leaves with a ragged tail; 513, 1000: several recursion levels
-@pytest.mark.parametrize("n", [1, 5, 100, 128, 129, 200, 300, 513, 1000])
+# three tiles with a ragged tail; 513, 1000: several recursion levels (or
+# task-graph blocks); 2000: the n = 2000 workload's size, 16 tiles
+@pytest.mark.parametrize("n", [1, 5, 100, 128, 129, 200, 300, 513, 1000, 2000])
 def test_cholinv_matches_oracle(mctx, n):
-    A = _spd(n, 1000 + n)
-    info_ref, L = oracle.cholesky(A)
-    assert info_ref == 0
-    ld_ref = oracle.logdet_from_chol(L)
-    W_ref = oracle.inverse_from_chol(L)
+    A, ld_ref, W_ref = _reference(n, 1000 + n)
     info, ld, W = _run(mctx, A)
     assert info == 0
     assert abs(ld - ld_ref) <= n * 2.0 ** -20, (ld, ld_ref)
@@ -108,3 +124,29 @@ def test_cholinv_consecutive_calls_and_sizes(mctx):
         info_ref, L = oracle.cholesky(A)
         info, ld, W = _run(mctx, A)
         assert info == 0 and abs(ld - oracle.logdet_from_chol(L)) <= n * 2.0 ** -20
+
+
+def test_cholinv_largest_task_graph_block(mctx):
+    """n = 4019: 32 tiles with a ragged tail, the largest block one
+    task-graph launch takes (the recursion variant splits it)."""
+    if mctx.variant == "task_graph_4":
+        pytest.skip("the 4-tile cap is covered at n <= 2000")
+    n = 4019
+    A, ld_ref, W_ref = _reference(n, 4019)
+    info, ld, W = _run(mctx, A)
+    assert info == 0
+    assert abs(ld - ld_ref) <= n * 2.0 ** -20, (ld, ld_ref)
+    kappa = np.linalg.cond(A)
+    assert np.abs(W - W_ref).max() / np.abs(W_ref).max() <= kappa * 2.0 ** -16
+
+
+def test_cholinv_variant_paths(mctx):
+    """Which variant ran, from the code-path counters."""
+    A, _, _ = _reference(1000, 2000)
+    mctx.get_profile(reset=True)
+    info, _, _ = _run(mctx, A)
+    paths = mctx.get_profile(reset=True)["paths"]
+    assert info == 0 and paths["tc_factor"] == 1, paths
+    want = {"task_graph": 1, "recursion": 0, "task_graph_4": 2}[mctx.variant]  # 1000 = 512 + 488
+    assert paths["tc_dag"] == want, paths
+    assert paths["tc_leaves"] == 8, paths  # ceil(1000 / 128) diagonal tiles either way
