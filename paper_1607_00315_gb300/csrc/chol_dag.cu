@@ -288,29 +288,26 @@ __device__ bool run_gemm(DSmem &sm, uint32_t tmem, const GemmTask &g, Phases &ph
             const int wr = (threadIdx.x - 192) >> 5;  // 8 warps x 32 lanes
             const int64_t ld = a.ld;
             if (g.mode != 0) {
-                // read-modify-write through L2: four rows' loads before their stores
+                // read-modify-write through L2: each thread's 16 rows x 4
+                // columns are all loaded before any store (one round trip)
                 const float sg = g.mode == 1 ? -1.f : 1.f;
-#pragma unroll 1
-                for (int r0 = wr * 4; r0 < DM; r0 += 32) {
-                    float cur[4][DM / 32];
-                    bool act[4][DM / 32];
+                float cur[16][DM / 32];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 16; ++u)
 #pragma unroll
-                        for (int p = 0; p < DM / 32; ++p) {
-                            const int r = r0 + u, c = lane + 32 * p;
-                            act[u][p] = r < g.rows && c < g.cols && (!g.lower_only || c <= r);
-                            cur[u][p] = act[u][p] ? __ldcg(g.out + r * ld + c) : 0.f;
-                        }
+                    for (int p = 0; p < DM / 32; ++p) {
+                        const int r = wr * 16 + u, c = lane + 32 * p;
+                        const bool act = r < g.rows && c < g.cols && (!g.lower_only || c <= r);
+                        cur[u][p] = act ? __ldcg(g.out + r * ld + c) : 0.f;
+                    }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 16; ++u)
 #pragma unroll
-                        for (int p = 0; p < DM / 32; ++p)
-                            if (act[u][p]) {
-                                const int r = r0 + u, c = lane + 32 * p;
-                                g.out[r * ld + c] = fmaf(sg, Ct[r][c], cur[u][p]);
-                            }
-                }
+                    for (int p = 0; p < DM / 32; ++p) {
+                        const int r = wr * 16 + u, c = lane + 32 * p;
+                        if (r < g.rows && c < g.cols && (!g.lower_only || c <= r))
+                            g.out[r * ld + c] = fmaf(sg, Ct[r][c], cur[u][p]);
+                    }
             } else {
 #pragma unroll 1
                 for (int r = wr; r < g.rows; r += 8)
