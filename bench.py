@@ -194,14 +194,17 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_class):
-    """DRAM bytes per launch of the dominant class from a committed ncu summary,
-    or None when the summary is missing or was taken on other kernel sources."""
+def ncu_traffic(kernel_class, variant=None):
+    """DRAM bytes per launch of the dominant class from a committed ncu summary
+    (the entry "class:variant" when there is one, e.g. the inner solver of
+    cd_sweeps), or None when the summary is missing or was taken on other
+    kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    e = d.get(kernel_class)
+    e = d.get(f"{kernel_class}:{variant}") if variant else None
+    e = e or d.get(kernel_class)
     if not e or e.get("source_hash") != source_hash(e.get("sources", [])):
         return None
     return e.get("dram_bytes_per_launch")
@@ -907,7 +910,7 @@ def main():
     roof["kernel"] = dom
     roof["launch_ms"] = per_launch_ms
     roof["work_per_launch"] = work_per_launch
-    roof["traffic"] = ncu_traffic(dom)
+    roof["traffic"] = ncu_traffic(dom, args.inner if dom == "cd_sweeps" else None)
     share = {k: round(v["ms"] / sum(c["ms"] for c in classes.values()), 4) for k, v in classes.items()}
     # every timed class against its own roofline (the same arithmetic as above)
     per_class = {}
