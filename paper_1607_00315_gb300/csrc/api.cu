@@ -649,7 +649,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
     auto fresh_factor = [&]() -> glasso_status {
         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, 0, 0.0, st));
         CK(ensure_side(w));
-        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles, w.dag_share));
         glasso_status s2 = factor_wait();
         if (s2 != GLASSO_OK) return s2;
         if (h->info != 0) return GLASSO_ENOTPD;
@@ -879,7 +879,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
                         CK(trial32(w.A, FA, n, ldf, w.pi, w.pj, w.p_a, w.D, np, alpha, st));
                         sv.mark_begin(4, eb);
                         CK(ensure_side(w));
-        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles));
+        CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, sc, st, w.side, w.ev_a, w.ev_b, w.dbg_dag_tiles, w.dag_share));
                         sv.mark_end(4, eb, 2.0 * nd * nd * nd / 3.0);
                         glasso_status s2 = factor_wait();
                         if (s2 != GLASSO_OK) return s2;
@@ -1221,6 +1221,7 @@ void worker_main(Serve *sv) {
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     Work w;
+    w.dag_share = serve_slots();  // the slots' solves share the GPU
     std::string err;
     for (;;) {
         Request *r = nullptr;
@@ -1677,7 +1678,7 @@ glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, 
     sv.mark_begin(4, eb);
     CTX_CK(ensure_side(w));
     CTX_CK(cholinv_tc(FA, n, ldf, FX, FXt, FZ, w.ldiag, w.sc, ctx->stream, w.side, w.ev_a, w.ev_b,
-                            w.dbg_dag_tiles));
+                            w.dbg_dag_tiles, w.dag_share));
     sv.mark_end(4, eb, 2.0 * (double)n * n * n / 3.0);
     s = sync_ctx(ctx);
     if (s != GLASSO_OK) return s;

@@ -546,13 +546,15 @@ __global__ void __launch_bounds__(DTHREADS, 1)
 struct Plan {
     int4 *dev = nullptr;
     int ntasks = 0;
-    int width = 0;  // the most tasks the list schedule ran at once
+    int grid = 0;  // CTAs of the launch (the list schedule's workers)
 };
 
-// The task graph of T x T tiles and its order: a list schedule with G
-// workers, the ready task with the longest path to the end first (estimated
-// durations: leaf 10, product 3 units).  Start order is a topological order.
-std::vector<int4> plan_tasks(int T, int G, int *width) {
+// The task graph of T x T tiles and its order: a list schedule, the ready
+// task with the longest path to the end first (estimated durations: leaf
+// 10, product 3 units), on twice the fewest workers (<= G_max) that keep
+// the modelled makespan within 5% of G_max workers'; *grid = that count.
+// Start order is a topological order.
+std::vector<int4> plan_tasks(int T, int G_max, int *grid) {
     std::vector<int4> tk;
     std::vector<std::vector<int>> deps;
     auto id3 = [T](int i, int j, int k) { return ((int64_t)i * T + j) * T + k; };
@@ -601,36 +603,52 @@ std::vector<int4> plan_tasks(int T, int G, int *width) {
         for (int s2 : succ[t]) m = std::max(m, bl[s2]);
         bl[t] = dur[t] + m;
     }
-    // list schedule
-    using Ready = std::pair<double, int>;  // (priority, -id) max-heap
-    std::priority_queue<Ready> ready;
-    using Ev = std::pair<double, int>;  // (finish time, task), min-heap
-    std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
-    std::vector<int> deg(indeg);
-    for (int t = 0; t < N; ++t)
-        if (deg[t] == 0) ready.push({bl[t], -t});
-    std::vector<int4> out;
-    out.reserve(N);
-    double now = 0.0;
-    int busy = 0, wmax = 0;
-    while ((int)out.size() < N) {
-        while (busy < G && !ready.empty()) {
-            const int t = -ready.top().second;
-            ready.pop();
-            out.push_back(tk[t]);
-            running.push({now + dur[t], t});
-            ++busy;
+    // list schedule with G workers: the start order and its makespan
+    auto schedule = [&](int G, std::vector<int4> *order) {
+        using Ready = std::pair<double, int>;  // (priority, -id) max-heap
+        std::priority_queue<Ready> ready;
+        using Ev = std::pair<double, int>;  // (finish time, task), min-heap
+        std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> running;
+        std::vector<int> deg(indeg);
+        for (int t = 0; t < N; ++t)
+            if (deg[t] == 0) ready.push({bl[t], -t});
+        if (order) order->clear();
+        double now = 0.0;
+        int busy = 0, started = 0;
+        while (started < N || !running.empty()) {
+            while (busy < G && !ready.empty()) {
+                const int t = -ready.top().second;
+                ready.pop();
+                if (order) order->push_back(tk[t]);
+                running.push({now + dur[t], t});
+                ++busy;
+                ++started;
+            }
+            if (running.empty()) break;  // (cannot happen: the graph is acyclic)
+            const Ev e = running.top();
+            running.pop();
+            now = e.first;
+            --busy;
+            for (int s2 : succ[e.second])
+                if (--deg[s2] == 0) ready.push({bl[s2], -s2});
         }
-        wmax = std::max(wmax, busy);
-        if (running.empty()) break;  // (cannot happen: the graph is acyclic)
-        const Ev e = running.top();
-        running.pop();
-        now = e.first;
-        --busy;
-        for (int s2 : succ[e.second])
-            if (--deg[s2] == 0) ready.push({bl[s2], -s2});
+        return now;
+    };
+    // twice the fewest workers whose makespan is within 5% of G_max's (the
+    // modelled makespan has a sharp knee there; measured task times vary, so
+    // the launch keeps a margin): it leaves the other SMs to whatever runs
+    // beside it (concurrent solves)
+    const double best = schedule(G_max, nullptr);
+    int lo = 1, hi = G_max;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (schedule(mid, nullptr) <= 1.05 * best) hi = mid;
+        else lo = mid + 1;
     }
-    *width = wmax;
+    const int G = std::min(G_max, 2 * lo);
+    std::vector<int4> out;
+    schedule(G, &out);
+    *grid = G;
     return out;
 }
 
@@ -638,6 +656,10 @@ std::mutex g_plan_mu;
 std::map<std::pair<int, int>, Plan> g_plans;  // (device, T)
 OncePerDevice g_dag_once;
 
+// The plans of every T = 2 .. DAG_MAX_T for a device, built together on the
+// first call (about 1.4 MB of tasks in one allocation, host work of the
+// order of 0.1 s), so that no later call allocates device memory -- an
+// allocation can wait for other streams' work in flight.
 cudaError_t get_plan(int dev, int T, int G, Plan *out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find({dev, T});
@@ -645,18 +667,28 @@ cudaError_t get_plan(int dev, int T, int G, Plan *out) {
         *out = it->second;
         return cudaSuccess;
     }
-    Plan p;
-    const std::vector<int4> tasks = plan_tasks(T, G, &p.width);
-    p.ntasks = (int)tasks.size();
-    cudaError_t e = cudaMalloc(&p.dev, tasks.size() * sizeof(int4));
+    std::vector<int4> all;
+    std::vector<Plan> plans(DAG_MAX_T + 1);
+    std::vector<size_t> off(DAG_MAX_T + 1, 0);
+    for (int t = 2; t <= DAG_MAX_T; ++t) {
+        const std::vector<int4> tasks = plan_tasks(t, G, &plans[t].grid);
+        plans[t].ntasks = (int)tasks.size();
+        off[t] = all.size();
+        all.insert(all.end(), tasks.begin(), tasks.end());
+    }
+    int4 *dev_tasks = nullptr;
+    cudaError_t e = cudaMalloc(&dev_tasks, all.size() * sizeof(int4));
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(p.dev, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dev_tasks, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(p.dev);
+        cudaFree(dev_tasks);
         return e;
     }
-    g_plans[{dev, T}] = p;
-    *out = p;
+    for (int t = 2; t <= DAG_MAX_T; ++t) {
+        plans[t].dev = dev_tasks + off[t];
+        g_plans[{dev, t}] = plans[t];
+    }
+    *out = g_plans[{dev, T}];
     return cudaSuccess;
 }
 
@@ -674,8 +706,9 @@ bool chol_dag_fits(int64_t s, int max_tiles) {
 // diagonal of L into ldiag[o ..].  A's block is overwritten.  scratch: 2 T^2
 // + 4 unsigned of device memory (T = ceil(s / 128)), zeroed here.  sc->info =
 // first failing pivot + 1; sc->tc_err = nonzero if a bounded wait expired.
+// The launch takes at most 1 / share of the SMs (solves of concurrent slots).
 cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float *Xt, double *ldiag,
-                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles) {
+                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles, int share) {
     if (!chol_dag_fits(s) || ld % 32 != 0 || o % DM != 0) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -694,7 +727,9 @@ cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float
     Plan p;
     e = get_plan(dev, T, nsm, &p);
     if (e != cudaSuccess) return e;
-    const int G = std::max(1, std::min(nsm, p.width));
+    // the planned grid, within this launch's share of the SMs (any grid is
+    // safe: the walk takes tasks in order)
+    const int G = std::max(1, std::min(nsm * occ / std::max(1, share), p.grid));
     CUtensorMap mA, mX, mXt;
     e = make_tmap(&mA, A + o * ld + o, s, s, ld);
     if (e != cudaSuccess) return e;

@@ -471,6 +471,7 @@ struct Rec {
     cudaStream_t side;  // optional: Yt runs here, beside SYRK and the right subtree
     cudaEvent_t ev_a, ev_b;
     int dag_tiles;      // largest block of one task-graph launch (0: default, 1: none)
+    int dag_share;      // a task-graph launch takes at most 1 / dag_share of the SMs
 };
 
 cudaError_t node(const Rec &r, int64_t o, int64_t s) {
@@ -479,7 +480,7 @@ cudaError_t node(const Rec &r, int64_t o, int64_t s) {
     // node's scratch (Z21 below it, Z12 beside it) overlaps
     if (r.dag_tiles != 1 && chol_dag_fits(s, r.dag_tiles))
         return chol_dag(r.A, r.ld, o, s, r.X, r.Xt, r.ldiag, reinterpret_cast<unsigned *>(r.Z + o * r.ld + o),
-                        r.sc, r.st);
+                        r.sc, r.st, 0, r.dag_share);
     const int64_t s1 = ((s / 2) + 127) / 128 * 128, s2 = s - s1;
     const int64_t ld = r.ld;
     int *err = &r.sc->tc_err;
@@ -538,12 +539,12 @@ cudaError_t node(const Rec &r, int64_t o, int64_t s) {
 // log det A (when info == 0), sc->tc_err = nonzero if a bounded wait expired.
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z,
                        double *ldiag, DevScalars *sc, cudaStream_t st, cudaStream_t side,
-                       cudaEvent_t ev_a, cudaEvent_t ev_b, int dag_tiles) {
+                       cudaEvent_t ev_a, cudaEvent_t ev_b, int dag_tiles, int dag_share) {
     if (ld % 32 != 0 || ld < n) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(&sc->info, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     if (side && (!ev_a || !ev_b)) return cudaErrorInvalidValue;
-    Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b, dag_tiles};
+    Rec r{A, X, Xt, Z, ld, ldiag, sc, st, side, ev_a, ev_b, dag_tiles, dag_share};
     path_hit(GLASSO_PATH_TC_FACTOR);
     e = node(r, 0, n);
     if (e != cudaSuccess) return e;

@@ -170,6 +170,8 @@ struct Work {
     int dbg_wait_unreachable = 0;   // the barrier waits for one arrival more than the grid holds
     int dbg_ls_reject = 0;          // every line-search trial is rejected
     int dbg_dag_tiles = 0;          // largest task-graph block in tiles (0: default, 1: none)
+    int dag_share = 1;              // a task-graph launch takes at most 1 / dag_share of the SMs
+                                    // (the serving slots' solves run concurrently)
 };
 
 }  // namespace glx
@@ -286,12 +288,14 @@ cudaError_t chol_leaf32(const float *A, int64_t ld, int64_t o, int s, float *X, 
 cudaError_t logdet_from_diag(const double *ldiag, int64_t n, DevScalars *sc, cudaStream_t st);
 cudaError_t cholinv_tc(float *A, int64_t n, int64_t ld, float *X, float *Xt, float *Z, double *ldiag,
                        DevScalars *sc, cudaStream_t st, cudaStream_t side = nullptr,
-                       cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, int dag_tiles = 0);
+                       cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr, int dag_tiles = 0,
+                       int dag_share = 1);
 // one persistent task-graph launch for a diagonal block (chol_dag.cu); a
 // block fits when 128 < s <= max_tiles * 128 (max_tiles 0: the default 32)
 bool chol_dag_fits(int64_t s, int max_tiles = 0);
 cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float *Xt, double *ldiag,
-                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles = 0);
+                     unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles = 0,
+                     int share = 1);
 cudaError_t lauum_tc(const float *Xt, int64_t n, int64_t ld, float *W, int64_t ldw, DevScalars *sc,
                      cudaStream_t st);
 cudaError_t gemm_nt_split(const float *P, const float *Q, int64_t n, int64_t ld, float *C, int *err,
