@@ -114,3 +114,56 @@ def test_mixed_n1200_against_a_live_oracle_solve():
     assert paths["tc_factor"] >= 1 and paths["tc_leaves"] >= 10 * paths["tc_factor"], paths
     assert paths["ls_series2"] + paths["ls_series6"] >= 1, paths
     assert paths["ns_steps"] >= 1, paths
+
+
+@pytest.fixture(scope="module")
+def golden10k():
+    """The oracle's minimiser of the n = 10000 workload (configuration 3):
+    tests/golden/n10000_minimiser.json, written by the oracle at rel. KKT
+    1e-9 from S formed in FP64 from the FP32-rounded samples.  Here S is
+    formed by numpy's BLAS from the same samples (X^T X / m, uncentred, as
+    the oracle's a1): equal to the oracle's S to rounding, far inside the
+    1e-7 entry bar, and independent of the CUDA path."""
+    g = json.load(open(os.path.join(HERE, "golden", "n10000_minimiser.json")))
+    n = g["n"]
+    A = np.zeros((n, n))
+    A[g["i"], g["j"]] = g["a"]
+    A[g["j"], g["i"]] = g["a"]
+    border = np.zeros((n, n), dtype=bool)
+    border[g["border_i"], g["border_j"]] = True
+    border |= border.T
+    p = synth.config_problem(3)
+    X = p.X.astype(np.float32).astype(np.float64)
+    S = (X.T @ X) / X.shape[0]
+    assert p.n == n and p.lam == g["lambda"]
+    return g, A, border, S
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_n10000_matches_the_oracle_minimiser(golden10k, precision):
+    """Configuration 3 at its full size, n = 10000, against the oracle's
+    minimiser: entries to 1e-7, the support apart from the border pairs, the
+    reported objective (FP64 path 1e-9, mixed 1e-7), and the FP64 objective
+    of the returned A (log det by numpy's LAPACK factorisation) to 1e-9."""
+    g, A_ref, border, S = golden10k
+    F_ref = g["objective"]
+    ctx = _context(precision)
+    try:
+        ctx.get_profile(reset=True)
+        A, _, info = ctx.solve(S, g["lambda"], tol=g["tol"])
+        paths = ctx.get_profile()["paths"]
+    finally:
+        ctx.close()
+    assert info["status"] == 0, info
+    assert info["rel_kkt"] <= g["tol"]
+    assert np.abs(A - A_ref).max() <= 1e-7, np.abs(A - A_ref).max()
+    _support_ok(A, A_ref, border)
+    rtol = 1e-9 if precision == "fp64" else MIXED_OBJ_RTOL
+    assert abs(info["objective"] - F_ref) <= rtol * abs(F_ref), (info["objective"], F_ref)
+    sign, logdet = np.linalg.slogdet(A)
+    assert sign > 0
+    F = -logdet + float(np.sum(S * A)) + g["lambda"] * float(np.abs(A).sum())
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref), (F, F_ref)
+    if precision == "mixed":
+        # the recursion's top levels and the task-graph blocks ran
+        assert paths["tc_factor"] >= 1 and paths["tc_dag"] >= 2 * paths["tc_factor"], paths
