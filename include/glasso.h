@@ -174,7 +174,7 @@ glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
 
 /* Code-path counters (all contexts, counted always, since the last reset):
  * which variant of a step the solves took. */
-#define GLASSO_PATHS 9
+#define GLASSO_PATHS 10
 enum {
     GLASSO_PATH_CD_LAG2 = 0,       /* FP32 sweeps by the pipelined chain-CTA kernel */
     GLASSO_PATH_CD_PERSIST32 = 1,  /* FP32 sweeps by the one-copy kernel (its matrices did not fit) */
@@ -184,8 +184,10 @@ enum {
     GLASSO_PATH_TC_FACTOR = 5,     /* tensor-core factorisations (line-search trials and fresh W) */
     GLASSO_PATH_TC_LEAVES = 6,     /* diagonal leaves factored inside them */
     GLASSO_PATH_NS_STEPS = 7,      /* Newton-Schulz refinement GEMMs of W */
-    GLASSO_PATH_TC_DAG = 8         /* diagonal blocks (up to 32 x 128) factored and inverted by one
+    GLASSO_PATH_TC_DAG = 8,        /* diagonal blocks (up to 32 x 128) factored and inverted by one
                                       persistent task-graph launch inside them */
+    GLASSO_PATH_TC_TUNED = 9       /* task-graph launches timed by the grid autotuner (the first
+                                      call per block size; GLASSO_AUTOTUNE=0 turns it off) */
 };
 
 typedef struct {

@@ -39,6 +39,7 @@
 #include <map>
 #include <mutex>
 #include <queue>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -547,6 +548,7 @@ struct Plan {
     int4 *dev = nullptr;
     int ntasks = 0;
     int grid = 0;  // CTAs of the launch (the list schedule's workers)
+    int knee = 0;  // the fewest workers within 5% of the modelled best makespan
 };
 
 // The task graph of T x T tiles and its order: a list schedule, the ready
@@ -554,7 +556,7 @@ struct Plan {
 // 10, product 3 units), on twice the fewest workers (<= G_max) that keep
 // the modelled makespan within 5% of G_max workers'; *grid = that count.
 // Start order is a topological order.
-std::vector<int4> plan_tasks(int T, int G_max, int *grid) {
+std::vector<int4> plan_tasks(int T, int G_max, int *grid, int *knee) {
     std::vector<int4> tk;
     std::vector<std::vector<int>> deps;
     auto id3 = [T](int i, int j, int k) { return ((int64_t)i * T + j) * T + k; };
@@ -649,6 +651,7 @@ std::vector<int4> plan_tasks(int T, int G_max, int *grid) {
     std::vector<int4> out;
     schedule(G, &out);
     *grid = G;
+    *knee = lo;
     return out;
 }
 
@@ -671,7 +674,7 @@ cudaError_t get_plan(int dev, int T, int G, Plan *out) {
     std::vector<Plan> plans(DAG_MAX_T + 1);
     std::vector<size_t> off(DAG_MAX_T + 1, 0);
     for (int t = 2; t <= DAG_MAX_T; ++t) {
-        const std::vector<int4> tasks = plan_tasks(t, G, &plans[t].grid);
+        const std::vector<int4> tasks = plan_tasks(t, G, &plans[t].grid, &plans[t].knee);
         plans[t].ntasks = (int)tasks.size();
         off[t] = all.size();
         all.insert(all.end(), tasks.begin(), tasks.end());
@@ -692,6 +695,18 @@ cudaError_t get_plan(int dev, int T, int G, Plan *out) {
     return cudaSuccess;
 }
 
+// Grids picked by the autotuner, per (device, T, SM share).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+bool autotune_on() {
+    static const bool on = [] {
+        const char *e = getenv("GLASSO_AUTOTUNE");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 }  // namespace
 
 bool chol_dag_fits(int64_t s, int max_tiles) {
@@ -707,6 +722,10 @@ bool chol_dag_fits(int64_t s, int max_tiles) {
 // + 4 unsigned of device memory (T = ceil(s / 128)), zeroed here.  sc->info =
 // first failing pivot + 1; sc->tc_err = nonzero if a bounded wait expired.
 // The launch takes at most 1 / share of the SMs (solves of concurrent slots).
+// Its grid: on the first call for a (device, T, share), unless GLASSO_AUTOTUNE
+// is 0, each of 1, 2, 3, 4 times the modelled knee is timed on this input
+// (restored from a copy between runs) and the fastest kept for later calls;
+// otherwise twice the knee.  The result does not depend on the grid.
 cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float *Xt, double *ldiag,
                      unsigned *scratch, DevScalars *sc, cudaStream_t st, long long wait_cycles, int share) {
     if (!chol_dag_fits(s) || ld % 32 != 0 || o % DM != 0) return cudaErrorInvalidValue;
@@ -727,9 +746,10 @@ cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float
     Plan p;
     e = get_plan(dev, T, nsm, &p);
     if (e != cudaSuccess) return e;
-    // the planned grid, within this launch's share of the SMs (any grid is
-    // safe: the walk takes tasks in order)
-    const int G = std::max(1, std::min(nsm * occ / std::max(1, share), p.grid));
+    // any grid is safe (the walk takes tasks in order) and gives the same
+    // result bit for bit (each task's arithmetic does not depend on the CTA
+    // that runs it); a launch takes at most its share of the SMs
+    const int cap = std::max(2, nsm * occ / std::max(1, share));
     CUtensorMap mA, mX, mXt;
     e = make_tmap(&mA, A + o * ld + o, s, s, ld);
     if (e != cudaSuccess) return e;
@@ -738,8 +758,6 @@ cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float
     e = make_tmap(&mXt, Xt + o * ld + o, s, s, ld);
     if (e != cudaSuccess) return e;
     const size_t nctr = 2 * (size_t)T * T + 4;
-    e = cudaMemsetAsync(scratch, 0, nctr * sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
     DArgs a;
     a.tasks = p.dev;
     a.ntasks = p.ntasks;
@@ -758,19 +776,92 @@ cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float
     a.info = &sc->info;
     a.err = &sc->tc_err;
     a.wait_cycles = wait_cycles > 0 ? wait_cycles : 2000000000ll;  // about 1 s
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)G);
-    cfg.blockDim = dim3(DTHREADS);
-    cfg.dynamicSmemBytes = DSMEM;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_chol_dag, mA, mX, mXt, a);
-    counted(1);
-    if (e != cudaSuccess) return e;
+    auto launch = [&](int G) -> cudaError_t {
+        cudaError_t le = cudaMemsetAsync(scratch, 0, nctr * sizeof(unsigned), st);
+        if (le != cudaSuccess) return le;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)G);
+        cfg.blockDim = dim3(DTHREADS);
+        cfg.dynamicSmemBytes = DSMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        le = cudaLaunchKernelEx(&cfg, k_chol_dag, mA, mX, mXt, a);
+        counted(1);
+        return le;
+    };
+    const std::tuple<int, int, int> key(dev, T, share);
+    int G = std::min(cap, p.grid);
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            G = it->second;
+            tuned = true;
+        }
+    }
+    std::vector<int> cand;
+    if (!tuned && autotune_on())
+        for (int m = 1; m <= 4; ++m) {
+            const int g = std::max(2, std::min(cap, m * p.knee));
+            if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+        }
+    if (cand.size() > 1) {
+        // autotune: time each candidate grid on this very input (restored
+        // from a copy between runs), keep the fastest for (device, T, share),
+        // and leave the result of a run with it in place
+        float *bk = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        const size_t pitch = (size_t)s * sizeof(float), lpitch = (size_t)ld * sizeof(float);
+        float *blk = A + o * ld + o;
+        e = cudaMallocAsync(&bk, pitch * s, st);
+        if (e == cudaSuccess) e = cudaMemcpy2DAsync(bk, pitch, blk, lpitch, pitch, s, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        float best_ms = 0.f;
+        int best = G, last = -1;
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c) {
+            if (c > 0) e = cudaMemcpy2DAsync(blk, lpitch, bk, pitch, pitch, s, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch(cand[c]);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = cand[c];
+            }
+            last = cand[c];
+            path_hit(GLASSO_PATH_TC_TUNED);
+        }
+        if (e == cudaSuccess && best != last) {
+            e = cudaMemcpy2DAsync(blk, lpitch, bk, pitch, pitch, s, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = launch(best);
+        }
+        if (bk) cudaFreeAsync(bk, st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return e;
+        // keep the choice only if the runs were complete (a failed pivot or an
+        // expired wait ends a run early, whatever its grid)
+        int flags[2] = {1, 1};
+        e = cudaMemcpyAsync(&flags[0], &sc->info, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flags[1], &sc->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (flags[0] == 0 && flags[1] == 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = best;
+        }
+    } else {
+        e = launch(G);
+        if (e != cudaSuccess) return e;
+    }
     path_hit(GLASSO_PATH_TC_DAG);
     path_hit(GLASSO_PATH_TC_LEAVES, T);
     return cudaGetLastError();

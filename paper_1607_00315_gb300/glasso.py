@@ -62,9 +62,9 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PATHS = 9
+PATHS = 10
 PATH_NAMES = ("cd_lag2", "cd_persist32", "cd_chain64", "ls_series2", "ls_series6", "tc_factor",
-              "tc_leaves", "ns_steps", "tc_dag")
+              "tc_leaves", "ns_steps", "tc_dag", "tc_tuned")
 DEBUG_WAIT_CYCLES, DEBUG_WAIT_UNREACHABLE, DEBUG_LS_REJECT, DEBUG_TC_DAG_TILES = 1, 2, 3, 4
 
 

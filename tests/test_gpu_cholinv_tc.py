@@ -150,3 +150,27 @@ def test_cholinv_variant_paths(mctx):
     want = {"task_graph": 1, "recursion": 0, "task_graph_4": 2}[mctx.variant]  # 1000 = 512 + 488
     assert paths["tc_dag"] == want, paths
     assert paths["tc_leaves"] == 8, paths  # ceil(1000 / 128) diagonal tiles either way
+
+
+def test_grid_autotuner(mctx):
+    """The task graph's grid autotuner: the first factorisation of a block
+    size times candidate grids on its own input and keeps the fastest; the
+    next call reuses it.  Any grid gives the same result bit for bit, so the
+    two calls' W are equal, and the result meets the oracle bars above.
+    n = 1400 (11 tiles): a size no other test factors first."""
+    if mctx.variant != "task_graph":
+        pytest.skip("the autotuner picks the task graph's grid")
+    n = 1400
+    A, ld_ref, W_ref = _reference(n, 1400)
+    mctx.get_profile(reset=True)
+    info, ld1, W1 = _run(mctx, A)
+    p1 = mctx.get_profile(reset=True)["paths"]
+    info2, ld2, W2 = _run(mctx, A)
+    p2 = mctx.get_profile(reset=True)["paths"]
+    assert info == 0 and info2 == 0
+    assert p1["tc_tuned"] >= 2, p1
+    assert p2["tc_tuned"] == 0 and p2["tc_dag"] == 1, p2
+    assert np.array_equal(W1, W2) and ld1 == ld2
+    assert abs(ld1 - ld_ref) <= n * 2.0 ** -20
+    kappa = np.linalg.cond(A)
+    assert np.abs(W1 - W_ref).max() / np.abs(W_ref).max() <= kappa * 2.0 ** -16
