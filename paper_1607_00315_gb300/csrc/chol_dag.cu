@@ -657,41 +657,51 @@ std::vector<int4> plan_tasks(int T, int G_max, int *grid, int *knee) {
 
 std::mutex g_plan_mu;
 std::map<std::pair<int, int>, Plan> g_plans;  // (device, T)
+std::map<int, int4 *> g_plan_buf;              // device -> room for the plans of every T
 OncePerDevice g_dag_once;
 
-// The plans of every T = 2 .. DAG_MAX_T for a device, built together on the
-// first call (about 1.4 MB of tasks in one allocation, host work of the
-// order of 0.1 s), so that no later call allocates device memory -- an
-// allocation can wait for other streams' work in flight.
-cudaError_t get_plan(int dev, int T, int G, Plan *out) {
+// The number of tasks of the T x T graph: leaves, panels, updates, the
+// inverse's products and its final products.
+size_t task_count(int T) {
+    size_t c = (size_t)T + (size_t)T * (T - 1);  // LEAF, PANEL and XF
+    for (int k = 0; k < T; ++k) c += (size_t)(T - 1 - k) * (T - k) / 2;  // UPD
+    for (int i = 1; i < T; ++i)
+        for (int j = 0; j < i; ++j) c += (size_t)(i - j);  // ZU
+    return c;
+}
+
+// The plan of T for a device: scheduled on the host when T is first used and
+// copied (stream-ordered on st) into one device buffer that the first call
+// sized for every T, so that later calls allocate no device memory (an
+// allocation can wait for other streams' work in flight).
+cudaError_t get_plan(int dev, int T, int G, cudaStream_t st, Plan *out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find({dev, T});
     if (it != g_plans.end()) {
         *out = it->second;
         return cudaSuccess;
     }
-    std::vector<int4> all;
-    std::vector<Plan> plans(DAG_MAX_T + 1);
-    std::vector<size_t> off(DAG_MAX_T + 1, 0);
-    for (int t = 2; t <= DAG_MAX_T; ++t) {
-        const std::vector<int4> tasks = plan_tasks(t, G, &plans[t].grid, &plans[t].knee);
-        plans[t].ntasks = (int)tasks.size();
-        off[t] = all.size();
-        all.insert(all.end(), tasks.begin(), tasks.end());
+    auto bi = g_plan_buf.find(dev);
+    if (bi == g_plan_buf.end()) {
+        size_t total = 0;
+        for (int t = 2; t <= DAG_MAX_T; ++t) total += task_count(t);
+        int4 *buf = nullptr;
+        cudaError_t e = cudaMalloc(&buf, total * sizeof(int4));
+        if (e != cudaSuccess) return e;
+        bi = g_plan_buf.emplace(dev, buf).first;
     }
-    int4 *dev_tasks = nullptr;
-    cudaError_t e = cudaMalloc(&dev_tasks, all.size() * sizeof(int4));
+    size_t off = 0;
+    for (int t = 2; t < T; ++t) off += task_count(t);
+    Plan p;
+    const std::vector<int4> tasks = plan_tasks(T, G, &p.grid, &p.knee);
+    if (tasks.size() != task_count(T)) return cudaErrorInvalidValue;
+    p.ntasks = (int)tasks.size();
+    p.dev = bi->second + off;
+    // (from pageable memory: the call returns once the host data is staged)
+    cudaError_t e = cudaMemcpyAsync(p.dev, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(dev_tasks, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(dev_tasks);
-        return e;
-    }
-    for (int t = 2; t <= DAG_MAX_T; ++t) {
-        plans[t].dev = dev_tasks + off[t];
-        g_plans[{dev, t}] = plans[t];
-    }
-    *out = g_plans[{dev, T}];
+    g_plans[{dev, T}] = p;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -744,7 +754,7 @@ cudaError_t chol_dag(float *A, int64_t ld, int64_t o, int64_t s, float *X, float
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int T = (int)((s + DM - 1) / DM);
     Plan p;
-    e = get_plan(dev, T, nsm, &p);
+    e = get_plan(dev, T, nsm, st, &p);
     if (e != cudaSuccess) return e;
     // any grid is safe (the walk takes tasks in order) and gives the same
     // result bit for bit (each task's arithmetic does not depend on the CTA
