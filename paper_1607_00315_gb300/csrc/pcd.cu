@@ -264,21 +264,21 @@ __device__ __noinline__ void spmm_tiles(const T *__restrict__ W, int64_t n, cons
 template <typename T, int NH>
 __device__ __noinline__ void spmm_tiles_split(const T *__restrict__ W, int64_t n, const int *__restrict__ ptr,
                                               const int *__restrict__ col, const double *__restrict__ vq,
-                                              T *__restrict__ out, unsigned *ctr, unsigned char *smem) {
+                                              T *__restrict__ out, unsigned *ctr, unsigned char *smem, int sr) {
     __shared__ unsigned grab[NH];
     const int lane = threadIdx.x & 31, nwh = (blockDim.x >> 5) / NH;  // warps per group
     const int h = (threadIdx.x >> 5) / nwh, warp = (threadIdx.x >> 5) % nwh;
     T(*tile)[SP_COLS + 1] = reinterpret_cast<T(*)[SP_COLS + 1]>(smem) + h * SP_ROWS;
     const unsigned nthr = (unsigned)nwh * 32u;
-    const int64_t tr = (n + SP_ROWS - 1) / SP_ROWS, tc = (n + SP_COLS - 1) / SP_COLS;
+    const int64_t tr = (n + sr - 1) / sr, tc = (n + SP_COLS - 1) / SP_COLS;
     for (;;) {
         // the next tile, from a counter shared by every group of the grid
         if (warp == 0 && lane == 0) grab[h] = atomicAdd(ctr, 1u);
         asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(nthr) : "memory");
         const int64_t tt = grab[h];
         if (tt >= tr * tc) break;
-        const int64_t r0 = (tt / tc) * SP_ROWS, k0 = (tt % tc) * SP_COLS;
-        for (int rl = warp; rl < SP_ROWS; rl += nwh) {
+        const int64_t r0 = (tt / tc) * sr, k0 = (tt % tc) * SP_COLS;
+        for (int rl = warp; rl < sr; rl += nwh) {
             const int64_t r = r0 + rl;
             T acc[SP_COLS / 32];
 #pragma unroll
@@ -309,7 +309,7 @@ __device__ __noinline__ void spmm_tiles_split(const T *__restrict__ W, int64_t n
         for (int c = warp; c < SP_COLS; c += nwh) {
             const int64_t k = k0 + c;
             if (k >= n) break;
-            if (r0 + lane < n) out[k * n + r0 + lane] = tile[lane][c];
+            if (lane < sr && r0 + lane < n) out[k * n + r0 + lane] = tile[lane][c];
         }
         asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(nthr) : "memory");
     }
@@ -385,6 +385,7 @@ struct PcdVec {
     const int *qi, *qj;  // each pair's two CSR positions
     double *kt, *kj;   // kinks gathered in (0, R]: times and jumps (KCAP)
     int *kp;           //                             pair indices
+    int sr;            // rows per SpMM tile (<= SP_ROWS): fewer for a small n, so the grid has tiles to share
 };
 
 __device__ __forceinline__ double pair_w(const PcdVec &v, int64_t p) { return v.pi[p] == v.pj[p] ? 1.0 : 2.0; }
@@ -617,27 +618,60 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
             }
             __syncthreads();
         }
-    // the walk, in increasing order from h(L+) (every thread, the same steps)
-    double H = HL, t = NAN, kinkt = -1.0;
-    int k = 0;
-    while (k < m) {
+    // The walk in increasing order from h(L+): the slope phi'(t) = g1 + g2 t +
+    // h(t) rises at each kink group (equal times) by its jumps.  The walk stops
+    // at the first group whose slope just right of it is >= 0: inside the
+    // smooth piece before it (t = -(g1 + H) / g2, H the jumps before the
+    // group) if the slope is already >= 0 just left of it, else on the kink.
+    // In parallel: an inclusive scan of the jumps (each thread a contiguous
+    // chunk, then the chunks' totals), the first such group by a minimum.
+    __shared__ double wsum[PT / 32];
+    __shared__ int first;
+    const int nt = (int)blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int ch = (m + nt - 1) / nt, c0 = min(m, tid * ch), c1 = min(m, c0 + ch);
+    double run = 0.0;
+    for (int i = c0; i < c1; ++i) {
+        run += jmp[i];
+        jmp[i] = run;  // (the chunk's own prefix for now)
+    }
+    // exclusive prefix of the chunk totals: warp scan, then the warps' totals
+    double x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    if (tid == 0) first = 0x7fffffff;
+    __syncthreads();
+    double woff = 0.0;
+    for (int w = 0; w < wid; ++w) woff += wsum[w];
+    const double off = woff + (x - run);
+    for (int i = c0; i < c1; ++i) jmp[i] += off;  // S_i = jumps up to and including i
+    __syncthreads();
+    for (int i = c0; i < c1; ++i) {
+        if (i + 1 < m && key[i + 1] == key[i]) continue;  // not the group's last kink
+        if (g1 + g2 * key[i] + (HL + jmp[i]) >= 0.0) {
+            atomicMin(&first, i);
+            break;
+        }
+    }
+    __syncthreads();
+    double t, kinkt = -1.0;
+    if (first == 0x7fffffff) {
+        t = -(g1 + (HL + (m > 0 ? jmp[m - 1] : 0.0))) / g2;
+    } else {
+        int k = first;
         const double tk = key[k];
+        while (k > 0 && key[k - 1] == tk) --k;  // the group's first kink
+        const double H = HL + (k > 0 ? jmp[k - 1] : 0.0);
         const double ts = -(g1 + H) / g2;
         if (ts <= tk) {
             t = ts;
-            break;
-        }
-        double jump = 0.0;
-        int k2 = k;
-        while (k2 < m && key[k2] == tk) jump += jmp[k2++];
-        if (g1 + g2 * tk + H + jump >= 0.0) {
+        } else {
             t = kinkt = tk;
-            break;
         }
-        H += jump;
-        k = k2;
     }
-    if (isnan(t)) t = -(g1 + H) / g2;
     t_out = t;
     kink_out = kinkt;
 }
@@ -667,7 +701,7 @@ __global__ void __launch_bounds__(PT, 1) k_pcd_persist(const T *__restrict__ W, 
         // tiles handed out by st->tctr[nspmm & 1]; the other counter is cleared
         // by CTA 0 for the next SpMM (which is at least one barrier away)
         unsigned *ctr = &st->tctr[nspmm & 1u];
-        spmm_tiles_split<T, SPLIT_NH<T>>(W, n, ptr, col, v.vq, Vt, ctr, pcd_smem);
+        spmm_tiles_split<T, SPLIT_NH<T>>(W, n, ptr, col, v.vq, Vt, ctr, pcd_smem, v.sr);
         if (blockIdx.x == 0 && threadIdx.x == 0) st->tctr[(nspmm + 1) & 1u] = 0u;
         ++nspmm;
         __syncthreads();
@@ -963,6 +997,13 @@ cudaError_t pcd_t(const T *W, int64_t n, double lam, const int32_t *pi, const in
     const int64_t tiles = ((n + SP_ROWS - 1) / SP_ROWS) * ((n + SP_COLS - 1) / SP_COLS);
     const int64_t want = lmax(tiles / 2, (np + 127) / 128);
     const int G = (int)lmax(1, lmin(lmin((int64_t)g_pcd_nsm[which][dev] * g_pcd_occ[which][dev], PCD_MAX_G), want));
+    // rows per SpMM tile: halved (down to 8) while the grid's warp groups
+    // outnumber the tiles (at n = 494, 32-row tiles gave 64 tiles to 600
+    // groups, each tile a long chain of dependent row gathers)
+    const int64_t tcols = (n + SP_COLS - 1) / SP_COLS;
+    int sr = SP_ROWS;
+    while (sr > 8 && ((n + sr - 1) / sr) * tcols < (int64_t)G * SPLIT_NH<T>) sr /= 2;
+    v.sr = sr;
     void *args[] = {(void *)&W, (void *)&Vt, (void *)&n, (void *)&lam, (void *)&ptr, (void *)&col,
                     (void *)&pid, (void *)&v, (void *)&iters, (void *)&cg, (void *)&rtol, (void *)&sd};
     e = cudaLaunchCooperativeKernel((const void *)k_pcd_persist<T>, dim3(G), dim3(PT), args, PCD_SMEM, st);
