@@ -649,9 +649,10 @@ def main():
     ap.add_argument("--inner", default="pcd_cg", choices=["cd", "pcd_cg"],
                     help="Newton-direction solver of the single solves (the other is timed beside it): "
                          "PCD-CG, Section 6.3's inner solver, by default")
-    ap.add_argument("--batch-inner", default="cd", choices=["cd", "pcd_cg"],
-                    help="Newton-direction solver of the batched and serving workloads (CD sweeps by default: "
-                         "many small solves run side by side, and PCD-CG's grid-wide launch would serialise them)")
+    ap.add_argument("--batch-inner", default="auto", choices=["cd", "pcd_cg", "auto"],
+                    help="Newton-direction solver of the batched and serving workloads (auto by default: per "
+                         "relaxation PCD-CG when the CD sweeps' serial chain would be long, CD sweeps when the "
+                         "free set is small and PCD-CG's fixed cost would dominate)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=0,

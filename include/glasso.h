@@ -87,10 +87,14 @@ typedef struct {
                          isolated vertices' (objective, log det, nnz). */
     int inner;        /* Newton-direction solver of each relaxation: GLASSO_INNER_CD (0, the default):
                          CD sweeps, min(1 + floor(k/3), 10) in cycle k; GLASSO_INNER_PCD_CG (1): PCD-CG
-                         (glasso_pcd) to relative precision 1e-4 (Section 8), at most 500 iterations */
+                         (glasso_pcd) to relative precision 1e-4 (Section 8), at most 500 iterations;
+                         GLASSO_INNER_AUTO (2): per relaxation, PCD-CG when the CD sweeps would update
+                         at least GLASSO_AUTO_PCD_WORK coordinates in their serial chain (pairs x
+                         sweeps; the environment variable of that name overrides it), else CD sweeps */
 } glasso_problem;
 
-enum { GLASSO_INNER_CD = 0, GLASSO_INNER_PCD_CG = 1 };
+enum { GLASSO_INNER_CD = 0, GLASSO_INNER_PCD_CG = 1, GLASSO_INNER_AUTO = 2 };
+#define GLASSO_AUTO_PCD_WORK 20000
 
 typedef struct {
     int status;          /* glasso_status of this solve */

@@ -342,6 +342,24 @@ void prof_collect(Prof *prof) {
 // PCD-CG as the inner solver: Section 8's relative precision, and an
 // iteration cap that the precision normally reaches long before.
 constexpr int kPcdIters = 500;
+
+// The inner solver of one relaxation: GLASSO_INNER_AUTO takes PCD-CG when
+// the CD sweeps' serial chain would be long (pairs x sweeps coordinate
+// updates, each a dependent step of the chain) and CD sweeps otherwise,
+// where PCD-CG's fixed cost (the pair CSR and a persistent launch with grid
+// barriers) would dominate.
+int64_t auto_pcd_work() {
+    static const int64_t v = [] {
+        const char *ev = getenv("GLASSO_AUTO_PCD_WORK");
+        const long long x = ev ? atoll(ev) : 0;
+        return (int64_t)(x > 0 ? x : GLASSO_AUTO_PCD_WORK);
+    }();
+    return v;
+}
+bool pick_pcd(int inner, int64_t np, int nsweeps) {
+    if (inner == GLASSO_INNER_PCD_CG) return true;
+    return inner == GLASSO_INNER_AUTO && np * (int64_t)nsweeps >= auto_pcd_work();
+}
 constexpr double kPcdRtol = 1e-4;
 // Algorithmic bytes of one PCD-CG iteration with word size ws: the SpMM reads
 // the 2 np rows of W its pairs name and writes V^T (n^2), the SDDMM reads two
@@ -477,7 +495,7 @@ glasso_status solve_core(Solver &sv, int64_t n, double lam, double tol, int max_
             CK(cudaMemsetAsync(w.U, 0, (size_t)(n * n) * sizeof(double), st));
             CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
             sv.mark_begin(3, eb);
-            if (sv.inner == GLASSO_INNER_PCD_CG) {
+            if (pick_pcd(sv.inner, np, nsweeps)) {
                 // PCD-CG to relative precision 1e-4 (Section 8); T is free until the line search
                 int its = 0;
                 const cudaError_t pe = pcd(w.W, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1,
@@ -791,7 +809,7 @@ glasso_status solve_core_mixed(Solver &sv, int64_t n, double lam, double tol, in
             // once the relative KKT residual is small, where the Newton step must be
             // resolved to the gradient's FP64 accuracy
             // (the FP64 buffer T is free in this path: it holds the second copy of U)
-            if (sv.inner == GLASSO_INNER_PCD_CG) {
+            if (pick_pcd(sv.inner, np, nsweeps)) {
                 // PCD-CG with FP32 products (T's FP32 halves are free until the next refinement)
                 int its = 0;
                 const cudaError_t pe = pcd32(W32, n, lk, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1,
@@ -1021,7 +1039,8 @@ glasso_status validate(const glasso_problem *p) {
     if (p->input == GLASSO_INPUT_X && (p->m < 1 || (p->dtype != GLASSO_F64 && p->dtype != GLASSO_F32)))
         return GLASSO_EINVAL;
     if (p->n > 46340) return GLASSO_EINVAL;  // n^2 int32-indexed pair bound
-    if (p->inner != GLASSO_INNER_CD && p->inner != GLASSO_INNER_PCD_CG) return GLASSO_EINVAL;
+    if (p->inner != GLASSO_INNER_CD && p->inner != GLASSO_INNER_PCD_CG && p->inner != GLASSO_INNER_AUTO)
+        return GLASSO_EINVAL;
     return GLASSO_OK;
 }
 

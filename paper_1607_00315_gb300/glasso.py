@@ -24,7 +24,7 @@ PROF_CLASSES = 6
 PROF_NAMES = ("cholesky", "inverse", "scan", "cd_sweeps", "ls_cholesky", "ns_refine")
 
 _lib = None
-INNER = {"cd": 0, "pcd_cg": 1}
+INNER = {"cd": 0, "pcd_cg": 1, "auto": 2}
 
 
 def _inner_code(inner):

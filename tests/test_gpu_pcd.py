@@ -203,3 +203,26 @@ def test_solve_with_pcd_cg_inner_matches_oracle(request, precision, gen, n, m, l
     assert abs(info["objective"] - F_ref) <= rtol * abs(F_ref)
     _, F = oracle.objective(S, A, lam)
     assert abs(F - F_ref) <= 1e-9 * abs(F_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_with_auto_inner_reaches_the_minimiser(request, precision):
+    """inner = auto: each relaxation takes CD sweeps or PCD-CG by the length of
+    the CD chain (pairs x sweeps against GLASSO_AUTO_PCD_WORK).  n = 400 with
+    a small lambda: the coarse levels' small free sets and the level-0 dense
+    one.  Whatever the mix, the solve ends at the oracle's unique minimiser
+    (entries 1e-7, support up to the lambda border, objective 1e-9 / 1e-7)."""
+    c = request.getfixturevalue("mctx" if precision == "mixed" else "ctx")
+    p = synth.random_problem(400, 800, 0.04, 31, gen="sparse")
+    S = oracle.form_S(p.X)
+    A_ref, W_ref, info_ref, _ = oracle.solve(S, p.lam, tol=1e-10)
+    assert info_ref["status"] == 0
+    A, _, info = c.solve(S, p.lam, tol=1e-10, inner="auto")
+    assert info["status"] == 0, info
+    assert info["rel_kkt"] <= 1e-10
+    assert np.abs(A - A_ref).max() <= 1e-7
+    border = np.abs(np.abs(S - W_ref) - p.lam) <= 1e-7
+    assert not np.any(((A != 0) != (A_ref != 0)) & ~border)
+    F_ref = info_ref["objective"]
+    rtol = 1e-9 if precision == "fp64" else 1e-7
+    assert abs(info["objective"] - F_ref) <= rtol * abs(F_ref)
