@@ -618,58 +618,86 @@ __device__ __noinline__ void pcd_walk(const PcdVec &v, double lam, double g1, do
             }
             __syncthreads();
         }
-    // The walk in increasing order from h(L+): the slope phi'(t) = g1 + g2 t +
-    // h(t) rises at each kink group (equal times) by its jumps.  The walk stops
-    // at the first group whose slope just right of it is >= 0: inside the
-    // smooth piece before it (t = -(g1 + H) / g2, H the jumps before the
-    // group) if the slope is already >= 0 just left of it, else on the kink.
-    // In parallel: an inclusive scan of the jumps (each thread a contiguous
-    // chunk, then the chunks' totals), the first such group by a minimum.
-    __shared__ double wsum[PT / 32];
-    __shared__ int first;
-    const int nt = (int)blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int ch = (m + nt - 1) / nt, c0 = min(m, tid * ch), c1 = min(m, c0 + ch);
-    double run = 0.0;
-    for (int i = c0; i < c1; ++i) {
-        run += jmp[i];
-        jmp[i] = run;  // (the chunk's own prefix for now)
-    }
-    // exclusive prefix of the chunk totals: warp scan, then the warps' totals
-    double x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    if (tid == 0) first = 0x7fffffff;
-    __syncthreads();
-    double woff = 0.0;
-    for (int w = 0; w < wid; ++w) woff += wsum[w];
-    const double off = woff + (x - run);
-    for (int i = c0; i < c1; ++i) jmp[i] += off;  // S_i = jumps up to and including i
-    __syncthreads();
-    for (int i = c0; i < c1; ++i) {
-        if (i + 1 < m && key[i + 1] == key[i]) continue;  // not the group's last kink
-        if (g1 + g2 * key[i] + (HL + jmp[i]) >= 0.0) {
-            atomicMin(&first, i);
-            break;
+    // The walk in increasing order from h(L+).  A few kinks (the usual case at
+    // n = 2000): every thread takes the same serial steps.  Many (dense free
+    // sets): in parallel.  (The serial steps are a dependent FP64 chain: 31 us
+    // for 1200 kinks, against 12 us in parallel; below about a hundred kinks
+    // the serial walk is the faster.)
+    double t = NAN, kinkt = -1.0;
+    if (m <= 96) {
+        double H = HL;
+        int k = 0;
+        while (k < m) {
+            const double tk = key[k];
+            const double ts = -(g1 + H) / g2;
+            if (ts <= tk) {
+                t = ts;
+                break;
+            }
+            double jump = 0.0;
+            int k2 = k;
+            while (k2 < m && key[k2] == tk) jump += jmp[k2++];
+            if (g1 + g2 * tk + H + jump >= 0.0) {
+                t = kinkt = tk;
+                break;
+            }
+            H += jump;
+            k = k2;
         }
-    }
-    __syncthreads();
-    double t, kinkt = -1.0;
-    if (first == 0x7fffffff) {
-        t = -(g1 + (HL + (m > 0 ? jmp[m - 1] : 0.0))) / g2;
+        if (isnan(t)) t = -(g1 + H) / g2;
     } else {
-        int k = first;
-        const double tk = key[k];
-        while (k > 0 && key[k - 1] == tk) --k;  // the group's first kink
-        const double H = HL + (k > 0 ? jmp[k - 1] : 0.0);
-        const double ts = -(g1 + H) / g2;
-        if (ts <= tk) {
-            t = ts;
+        // The slope phi'(t) = g1 + g2 t + h(t) rises at each kink group (equal
+        // times) by its jumps.  The walk stops
+        // at the first group whose slope just right of it is >= 0: inside the
+        // smooth piece before it (t = -(g1 + H) / g2, H the jumps before the
+        // group) if the slope is already >= 0 just left of it, else on the kink.
+        // In parallel: an inclusive scan of the jumps (each thread a contiguous
+        // chunk, then the chunks' totals), the first such group by a minimum.
+        __shared__ double wsum[PT / 32];
+        __shared__ int first;
+        const int nt = (int)blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+        const int ch = (m + nt - 1) / nt, c0 = min(m, tid * ch), c1 = min(m, c0 + ch);
+        double run = 0.0;
+        for (int i = c0; i < c1; ++i) {
+            run += jmp[i];
+            jmp[i] = run;  // (the chunk's own prefix for now)
+        }
+        // exclusive prefix of the chunk totals: warp scan, then the warps' totals
+        double x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        if (tid == 0) first = 0x7fffffff;
+        __syncthreads();
+        double woff = 0.0;
+        for (int w = 0; w < wid; ++w) woff += wsum[w];
+        const double off = woff + (x - run);
+        for (int i = c0; i < c1; ++i) jmp[i] += off;  // S_i = jumps up to and including i
+        __syncthreads();
+        for (int i = c0; i < c1; ++i) {
+            if (i + 1 < m && key[i + 1] == key[i]) continue;  // not the group's last kink
+            if (g1 + g2 * key[i] + (HL + jmp[i]) >= 0.0) {
+                atomicMin(&first, i);
+                break;
+            }
+        }
+        __syncthreads();
+        if (first == 0x7fffffff) {
+            t = -(g1 + (HL + (m > 0 ? jmp[m - 1] : 0.0))) / g2;
         } else {
-            t = kinkt = tk;
+            int k = first;
+            const double tk = key[k];
+            while (k > 0 && key[k - 1] == tk) --k;  // the group's first kink
+            const double H = HL + (k > 0 ? jmp[k - 1] : 0.0);
+            const double ts = -(g1 + H) / g2;
+            if (ts <= tk) {
+                t = ts;
+            } else {
+                t = kinkt = tk;
+            }
         }
     }
     t_out = t;
