@@ -265,11 +265,14 @@ def _gen_serving(row):
 
 def run_batched(args):
     """Lambda paths of many small independent instances (n ~ U[32, 512], m = 2n,
-    tridiagonal / sparse generators alternating), each path warm started,
-    solved by one glasso_solve_batch call (paths run concurrently through the
-    serving slots).  Under torchrun the instances are split over the ranks
-    (shard.balanced_partition) and each rank solves its share; the time is the
-    slowest rank's.  value = solves/s over all instances x 4 lambdas."""
+    tridiagonal / sparse generators alternating), each path warm started.
+    Engine "fused" (default): one glasso_solve_batch_fused call, every solve in
+    one persistent launch (a CTA per path, FP64, all control on the device);
+    engine "slots": one glasso_solve_batch call, paths run concurrently
+    through the host-driven serving slots (mixed precision).  Under torchrun
+    the instances are split over the ranks (shard.balanced_partition) and each
+    rank solves its share; the time is the slowest rank's.  value = solves/s
+    over all instances x 4 lambdas (latency: each solve's own time)."""
     import torch
     import torch.distributed as dist
 
@@ -289,55 +292,71 @@ def run_batched(args):
     parts = shard.balanced_partition([shard.unit_cost(p.n, len(synth.LAMBDA_PATH)) for p in allp],
                                      world)
     probs = [allp[k] for k in parts[rank]]
+    fused = args.batch_engine == "fused"
     ctx = glasso.Context(local, precision=glasso.MIXED)
+    inner = "cd" if fused else args.batch_inner
+    run = ctx.solve_batch_fused if fused else ctx.solve_batch
 
     def make(ps):
         plist, outs = [], []
         for p in ps:
             for lam in synth.LAMBDA_PATH:
                 plist.append(glasso.Context.problem(p.X, lam, 1e-5, samples=True,
-                                                    screen=args.screen, inner=args.batch_inner))
+                                                    screen=args.screen and not fused, inner=inner))
                 outs.append(np.empty((p.n, p.n)))
         return plist, outs
 
     wp, wo = make(probs[:16])
-    ctx.solve_batch(wp, wo, warm_from_prev=True)  # warm-up
+    run(wp, wo, warm_from_prev=True)  # warm-up
     plist, outs = make(probs)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    s, infos = ctx.solve_batch(plist, outs, warm_from_prev=True)
+    s, infos = run(plist, outs, warm_from_prev=True)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
     ctx.close()
     max_s, total, value = batched_job_value(dt, len(plist), world, dev)
     lat = [i["seconds"] * 1e3 for i in infos]
     nfail = sum(1 for i in infos if i["status"] != 0)
+    fl = sum(i["flops"] for i in infos)
     if world > 1:
         gathered = [None] * world
-        dist.all_gather_object(gathered, (lat, nfail, int(s)))
+        dist.all_gather_object(gathered, (lat, nfail, int(s), fl))
         lat = [x for g in gathered for x in g[0]]
         nfail = sum(g[1] for g in gathered)
         s = next((g[2] for g in gathered if g[2] != 0), 0)
+        fl = sum(g[3] for g in gathered)
         dist.destroy_process_group()
     if rank != 0:
         return 0
     per = np.array(lat)
     line = {
-        "metric": "batched lambda paths: solves/sec (mixed), per-solve latency p50/p99",
+        "metric": "batched lambda paths: solves/sec, per-solve latency p50/p99",
         "value": value, "unit": "solves/s", "n_gpus": world, "higher_is_better": True,
         "scaling": "strong",  # the instance set is fixed; more ranks split it
-        "dtype": "mixed(f32/tf32+f64)", "data": "synthetic", "status": int(s),
+        "dtype": "f64" if fused else "mixed(f32/tf32+f64)", "data": "synthetic", "status": int(s),
         "config": {"workload": f"{args.instances} instances, n ~ U[32, 512], m = 2n, "
                                f"tridiagonal/sparse alternating, lambda path {list(synth.LAMBDA_PATH)} "
                                f"warm started, tol 1e-5, samples X (fp64) on the host",
-                   "screen": bool(args.screen), "inner": args.batch_inner, "solves": total, "wall_s": max_s,
+                   "engine": "one persistent launch (glasso_solve_batch_fused)" if fused
+                             else "host serving slots (glasso_solve_batch)",
+                   "screen": bool(args.screen) and not fused, "inner": inner, "solves": total, "wall_s": max_s,
                    "parallelism": f"instances split over {world} ranks (greedy cost balance)"},
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                        "mean": float(per.mean())},
         "failed": int(nfail),
     }
+    if fused:
+        # the fused kernel is bound by FP64 arithmetic (its dense steps); the
+        # pool measures no FP64 rate, so the peak is the nominal 1.25 TFLOP/s
+        ach = fl / max_s / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": 1.25 * world, "unit": "TFLOP/s",
+                            "frac": ach / (1.25 * world), "traffic": None,
+                            "peak_source": "nominal FP64 rate (no measured FP64 peak); achieved = the "
+                                           "solves' algorithmic FP64 operations / the call's wall time",
+                            "kernel": "k_fused_paths"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -500,8 +519,8 @@ def extra_workloads(args, local, dev):
                                 "--batch-inner", args.batch_inner] + extra,
                                capture_output=True, text=True, timeout=600)
             line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
-            out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config")
-                         if k in line}
+            out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config",
+                                              "roofline", "dtype") if k in line}
         except Exception as e:  # reported, not fatal: the headline stands on its own
             out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
     return out
@@ -653,6 +672,9 @@ def main():
                     help="Newton-direction solver of the batched and serving workloads (auto by default: per "
                          "relaxation PCD-CG when the CD sweeps' serial chain would be long, CD sweeps when the "
                          "free set is small and PCD-CG's fixed cost would dominate)")
+    ap.add_argument("--batch-engine", default="slots", choices=["fused", "slots"],
+                    help="batched workload: one persistent launch over all paths (fused) or the host-driven "
+                         "serving slots")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision path")
     ap.add_argument("--e2e-steps", type=int, default=0,

@@ -112,6 +112,9 @@ typedef struct {
     int64_t components;  /* screen: connected components of {|S_ij| > lambda}; 0 without screening */
     int64_t max_block;   /* screen: vertices in the largest component; 0 without screening */
     int64_t inner_iters; /* CD sweeps or PCD-CG iterations, summed over the relaxations */
+    double flops;        /* glasso_solve_batch_fused: the solve's algorithmic FP64 operations
+                            (n^3/3 per factorisation, 2n^3/3 per inverse, 2n per coordinate
+                            of a sweep + 2n per row it updates); 0 elsewhere */
 } glasso_info;
 
 /* ---- context -------------------------------------------------------- */
@@ -156,6 +159,28 @@ glasso_status glasso_solve(glasso_ctx *ctx, const glasso_problem *p, double *A_o
 glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int count,
                                  int warm_from_prev, double **A_out, glasso_info *infos);
 
+/* The batched solver in ONE persistent launch (many small problems, e.g.
+ * lambda paths of several subjects).  Same arguments and warm-start rule as
+ * glasso_solve_batch: A_out[k] (in p[k].location) receives the solution of
+ * p[k], infos[k] its statistics; with warm_from_prev a maximal run of
+ * problems on the same data (same n, input kind and data pointer, A0 NULL
+ * after the first) is one lambda path, each problem warm started from the
+ * previous solution (continuation, end of Section 2).
+ * Each CTA of the launch takes a path from a device-side queue (longest
+ * first) and runs every step of the ML-cycle of Algorithm 1 (hierarchy of
+ * Section 7, CD sweeps on the Newton LASSO of eq. Quad_MLE_l1_prior, the
+ * Armijo line search of Section 6.1.2, the Section 8 KKT stop) itself, in
+ * FP64, whatever the context's precision; no host round trip between steps,
+ * relaxations or problems.  infos[k].seconds is the solve's own device time.
+ * Requires 1 <= n <= GLASSO_FUSED_MAX_N, screen = 0, continuation = 0 and
+ * inner CD or AUTO (AUTO takes the CD sweeps here); otherwise GLASSO_EINVAL
+ * before any work.  GLASSO_ENOMEM when the launch's memory (inputs, outputs
+ * and one workspace of about 6 n_max^2 doubles per CTA) exceeds the budget.
+ * Returns the first non-OK status, or GLASSO_OK. */
+#define GLASSO_FUSED_MAX_N 512
+glasso_status glasso_solve_batch_fused(glasso_ctx *ctx, const glasso_problem *p, int count,
+                                       int warm_from_prev, double **A_out, glasso_info *infos);
+
 /* Asynchronous serving interface.  glasso_submit copies the problem's inputs
  * before returning (the caller may free them at once), queues the solve and
  * returns a ticket.  A_out must stay valid until glasso_poll reports the
@@ -178,7 +203,7 @@ glasso_status glasso_poll(glasso_ctx *ctx, uint64_t ticket, int64_t timeout_us,
 
 /* Code-path counters (all contexts, counted always, since the last reset):
  * which variant of a step the solves took. */
-#define GLASSO_PATHS 10
+#define GLASSO_PATHS 11
 enum {
     GLASSO_PATH_CD_LAG2 = 0,       /* FP32 sweeps by the pipelined chain-CTA kernel */
     GLASSO_PATH_CD_PERSIST32 = 1,  /* FP32 sweeps by the one-copy kernel (its matrices did not fit) */
@@ -191,7 +216,9 @@ enum {
     GLASSO_PATH_TC_DAG = 8,        /* diagonal blocks (up to 32 x 128) factored and inverted by one
                                       persistent task-graph launch inside them */
     GLASSO_PATH_TC_TUNED = 9       /* task-graph launches timed by the grid autotuner (the first
-                                      call per block size; GLASSO_AUTOTUNE=0 turns it off) */
+                                      call per block size; GLASSO_AUTOTUNE=0 turns it off) */,
+    GLASSO_PATH_FUSED = 10         /* problems solved inside a fused batched launch
+                                      (glasso_solve_batch_fused) */
 };
 
 typedef struct {

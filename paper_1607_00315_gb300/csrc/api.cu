@@ -1591,6 +1591,179 @@ glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int c
     return first;
 }
 
+// The batched solver in one persistent launch (fused.cu): the inputs of every
+// path are staged (S copied, or formed from X), the launch runs all solves,
+// then the solutions and statistics are copied out.
+glasso_status glasso_solve_batch_fused(glasso_ctx *ctx, const glasso_problem *p, int count,
+                                       int warm_from_prev, double **A_out, glasso_info *infos) {
+    if (!ctx || !p || count < 0 || (count > 0 && !A_out)) return GLASSO_EINVAL;
+    if (count == 0) return GLASSO_OK;
+    cudaSetDevice(ctx->device);
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    std::string &err = ctx->last_error;
+    auto fail_all = [&](glasso_status s) {
+        if (infos)
+            for (int k = 0; k < count; ++k) {
+                memset(&infos[k], 0, sizeof(glasso_info));
+                infos[k].status = s;
+            }
+        return s;
+    };
+    int nmax = 0;
+    for (int k = 0; k < count; ++k) {
+        const glasso_problem &q = p[k];
+        if (validate(&q) != GLASSO_OK || q.n > GLASSO_FUSED_MAX_N || q.screen || q.continuation ||
+            q.inner == GLASSO_INNER_PCD_CG || !A_out[k])
+            return fail_all(GLASSO_EINVAL);
+        nmax = std::max(nmax, (int)q.n);
+    }
+    // paths: maximal runs continuing one another (the rule of glasso_solve_batch)
+    auto continues = [&](int k) {
+        return warm_from_prev && k > 0 && p[k].A0 == nullptr && p[k].n == p[k - 1].n &&
+               p[k].data == p[k - 1].data && p[k].input == p[k - 1].input;
+    };
+    std::vector<int2> paths;
+    for (int k = 0; k < count; ++k) {
+        if (!continues(k)) paths.push_back(make_int2(k, k + 1));
+        else paths.back().y = k + 1;
+    }
+    const int npaths = (int)paths.size();
+    // longest first: the device queue hands them out in this order
+    std::stable_sort(paths.begin(), paths.end(), [&](const int2 &a, const int2 &b) {
+        const double ca = std::pow((double)p[a.x].n, 3.0) * (a.y - a.x);
+        const double cb = std::pow((double)p[b.x].n, 3.0) * (b.y - b.x);
+        return ca > cb;
+    });
+    int dev = 0, nsm = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(npaths, nsm);
+    // one device arena: S per path, A per problem (A0 staged there), the
+    // problem and result records, the paths, the queue counter, the slots
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t off = 0;
+    std::vector<size_t> s_off(npaths), a_off(count);
+    for (int c = 0; c < npaths; ++c) {
+        s_off[c] = off;
+        off += al((size_t)p[paths[c].x].n * p[paths[c].x].n * sizeof(double));
+    }
+    for (int k = 0; k < count; ++k) {
+        a_off[k] = off;
+        off += al((size_t)p[k].n * p[k].n * sizeof(double));
+    }
+    const size_t prob_off = off;
+    off += al((size_t)count * sizeof(FusedProblem));
+    const size_t res_off = off;
+    off += al((size_t)count * sizeof(FusedResult));
+    const size_t path_off = off;
+    off += al((size_t)npaths * sizeof(int2));
+    const size_t next_off = off;
+    off += 256;
+    const size_t slot = fused_slot_bytes(nmax);
+    const size_t arena_off = off;
+    off += (size_t)grid * slot;
+    if (ctx->budget && off > ctx->budget) return fail_all(GLASSO_ENOMEM);
+    glasso_status s0 = work_ensure(w, 1, st, err);
+    if (s0 != GLASSO_OK) return fail_all(s0);
+    char *base = nullptr;
+    if (cudaMallocAsync((void **)&base, off, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_all(GLASSO_ENOMEM);
+    }
+    struct Free {
+        char *p;
+        cudaStream_t st;
+        ~Free() { cudaFreeAsync(p, st); }
+    } guard{base, st};
+    // stage the inputs
+    for (int c = 0; c < npaths; ++c) {
+        const glasso_problem &q = p[paths[c].x];
+        const int64_t n = q.n;
+        double *Sd = (double *)(base + s_off[c]);
+        const cudaMemcpyKind kind = q.location == GLASSO_HOST ? cudaMemcpyHostToDevice
+                                                              : cudaMemcpyDeviceToDevice;
+        if (q.input == GLASSO_INPUT_S) {
+            CK(cudaMemcpyAsync(Sd, q.data, (size_t)(n * n) * sizeof(double), kind, st));
+            glasso_status s = check_symmetric(w, Sd, n, st, err);
+            if (s != GLASSO_OK) return fail_all(s);
+        } else {
+            const int xb = q.dtype == GLASSO_F32 ? 4 : 8;
+            glasso_status s = work_ensure_x(w, q.m, n, xb, st, err);
+            if (s != GLASSO_OK) return fail_all(s);
+            const void *X = q.data;
+            if (q.location == GLASSO_HOST) {
+                CK(cudaMemcpyAsync(w.Xraw, q.data, (size_t)(q.m * n) * xb, kind, st));
+                X = w.Xraw;
+            }
+            CK(form_S(X, q.dtype, q.m, n, q.center, Sd, w.Xin, st));
+        }
+    }
+    std::vector<FusedProblem> fp(count);
+    for (int c = 0; c < npaths; ++c)
+        for (int k = paths[c].x; k < paths[c].y; ++k) {
+            const glasso_problem &q = p[k];
+            FusedProblem &f = fp[k];
+            f.S = (const double *)(base + s_off[c]);
+            f.A_out = (double *)(base + a_off[k]);
+            f.A0 = nullptr;
+            if (q.A0) {
+                const cudaMemcpyKind kind = q.location == GLASSO_HOST ? cudaMemcpyHostToDevice
+                                                                      : cudaMemcpyDeviceToDevice;
+                CK(cudaMemcpyAsync(f.A_out, q.A0, (size_t)q.n * q.n * sizeof(double), kind, st));
+                glasso_status s = check_symmetric(w, f.A_out, q.n, st, err);
+                if (s != GLASSO_OK) return fail_all(s);
+                f.A0 = f.A_out;
+            }
+            f.lambda = q.lambda;
+            f.tol = q.tol;
+            f.n = (int)q.n;
+            f.max_cycles = q.max_cycles > 0 ? q.max_cycles : 200;
+            f.one_level = q.one_level != 0;
+            f.pad = 0;
+        }
+    FusedProblem *dprob = (FusedProblem *)(base + prob_off);
+    FusedResult *dres = (FusedResult *)(base + res_off);
+    int2 *dpath = (int2 *)(base + path_off);
+    CK(cudaMemcpyAsync(dprob, fp.data(), (size_t)count * sizeof(FusedProblem), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dpath, paths.data(), (size_t)npaths * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(dres, 0, (size_t)count * sizeof(FusedResult), st));
+    CK(fused_paths(dprob, dres, dpath, npaths, (int *)(base + next_off), base + arena_off, slot, nmax, grid,
+                   st));
+    path_hit(GLASSO_PATH_FUSED, count);
+    std::vector<FusedResult> res(count);
+    CK(cudaMemcpyAsync(res.data(), dres, (size_t)count * sizeof(FusedResult), cudaMemcpyDeviceToHost, st));
+    for (int k = 0; k < count; ++k) {
+        const cudaMemcpyKind kind = p[k].location == GLASSO_HOST ? cudaMemcpyDeviceToHost
+                                                                 : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(A_out[k], base + a_off[k], (size_t)p[k].n * p[k].n * sizeof(double), kind, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    glasso_status first = GLASSO_OK;
+    for (int k = 0; k < count; ++k) {
+        const FusedResult &r = res[k];
+        if (infos) {
+            glasso_info &inf = infos[k];
+            memset(&inf, 0, sizeof(glasso_info));
+            inf.status = r.status;
+            inf.cycles = r.cycles;
+            inf.relaxations = r.relaxations;
+            inf.ls_trials = r.ls_trials;
+            inf.objective = r.objective;
+            inf.rel_kkt = r.rel_kkt;
+            inf.max_kkt = r.max_kkt;
+            inf.logdet = r.logdet;
+            inf.seconds = r.t1 >= r.t0 ? (double)(r.t1 - r.t0) * 1e-9 : 0.0;
+            inf.nnz = r.nnz;
+            inf.max_nnz = r.max_nnz;
+            inf.inner_iters = r.sweeps;
+            inf.flops = r.flops;
+        }
+        if (r.status != GLASSO_OK && first == GLASSO_OK) first = (glasso_status)r.status;
+    }
+    return first;
+}
+
 glasso_status glasso_submit(glasso_ctx *ctx, const glasso_problem *p, double *A_out,
                             uint64_t *ticket) {
     return submit_chain(ctx, p, 1, &A_out, ticket);

@@ -327,4 +327,31 @@ cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi
                         const double *aval, int nsweeps, double *D, float *U, Work &w,
                         bool chain64, cudaStream_t st, float *U2 = nullptr);
 
+// ---- the batched solver (fused.cu) ----
+// One problem of a fused launch: S and A_out are n x n FP64 on the device,
+// A0 (optional) too; n <= GLASSO_FUSED_MAX_N.
+constexpr int FUSED_THREADS = GLASSO_FUSED_MAX_N;  // one thread per column of a row
+struct FusedProblem {
+    const double *S;
+    const double *A0;
+    double *A_out;
+    double lambda, tol;
+    int n, max_cycles, one_level, pad;
+};
+struct FusedResult {
+    int status, cycles, relaxations, ls_trials;
+    double objective, rel_kkt, max_kkt, logdet;
+    long long nnz, max_nnz, sweeps;
+    double flops;               // algorithmic FP64 operations of the dense steps and the sweeps
+    unsigned long long t0, t1;  // device global timer (ns) at the solve's start and end
+};
+// Workspace bytes of one CTA slot for problems of size <= nmax.
+size_t fused_slot_bytes(int nmax);
+// One persistent launch of `grid` CTAs over the paths (int2 {first, end}: a
+// run of problems, each after the first warm started from its predecessor);
+// next: one device int (zeroed here); arena: grid * slot_bytes.
+cudaError_t fused_paths(const FusedProblem *probs, FusedResult *res, const int2 *paths, int npaths,
+                        int *next, char *arena, size_t slot_bytes, int nmax, int grid,
+                        cudaStream_t st);
+
 }  // namespace glx

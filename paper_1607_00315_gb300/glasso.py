@@ -56,15 +56,16 @@ class Info(C.Structure):
                 ("ls_trials", C.c_int), ("objective", C.c_double), ("rel_kkt", C.c_double),
                 ("max_kkt", C.c_double), ("logdet", C.c_double), ("seconds", C.c_double),
                 ("nnz", C.c_int64), ("max_nnz", C.c_int64), ("components", C.c_int64),
-                ("max_block", C.c_int64), ("inner_iters", C.c_int64)]
+                ("max_block", C.c_int64), ("inner_iters", C.c_int64), ("flops", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-PATHS = 10
+PATHS = 11
 PATH_NAMES = ("cd_lag2", "cd_persist32", "cd_chain64", "ls_series2", "ls_series6", "tc_factor",
-              "tc_leaves", "ns_steps", "tc_dag", "tc_tuned")
+              "tc_leaves", "ns_steps", "tc_dag", "tc_tuned", "fused")
+FUSED_MAX_N = 512
 DEBUG_WAIT_CYCLES, DEBUG_WAIT_UNREACHABLE, DEBUG_LS_REJECT, DEBUG_TC_DAG_TILES = 1, 2, 3, 4
 
 
@@ -95,6 +96,8 @@ def load():
     L.glasso_solve.argtypes = [vp, C.POINTER(Problem), vp, vp, C.POINTER(Info)]
     L.glasso_solve_batch.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                      C.POINTER(Info)]
+    L.glasso_solve_batch_fused.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
+                                           C.POINTER(Info)]
     L.glasso_submit.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(C.c_uint64)]
     L.glasso_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Info)]
     L.glasso_set_profiling.argtypes = [vp, i32]
@@ -253,6 +256,16 @@ class Context:
         s = self.L.glasso_solve_batch(self.h, arr, k, int(warm_from_prev), ptrs, infos)
         return s, [infos[i].as_dict() for i in range(k)]
 
+    def solve_batch_fused(self, problems, outs, warm_from_prev=False):
+        """glasso_solve_batch_fused (all solves in one persistent launch, n <= 512);
+        returns (status, info dicts)."""
+        k = len(problems)
+        arr = (Problem * k)(*problems)
+        ptrs = (C.c_void_p * k)(*[_ptr(o) for o in outs])
+        infos = (Info * k)()
+        s = self.L.glasso_solve_batch_fused(self.h, arr, k, int(warm_from_prev), ptrs, infos)
+        return s, [infos[i].as_dict() for i in range(k)]
+
     def submit(self, problem, A_out):
         t = C.c_uint64()
         self._check(self.L.glasso_submit(self.h, C.byref(problem), _ptr(A_out), C.byref(t)),
@@ -356,7 +369,8 @@ def free_set_noalloc(S, W, A, lam, oi, oj, absg=None, stream=None):
 
 EXPORTED = (
     "glasso_create", "glasso_destroy", "glasso_set_stream", "glasso_strerror",
-    "glasso_last_error", "glasso_solve", "glasso_solve_batch", "glasso_submit", "glasso_poll",
+    "glasso_last_error", "glasso_solve", "glasso_solve_batch", "glasso_solve_batch_fused",
+    "glasso_submit", "glasso_poll",
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
