@@ -309,6 +309,9 @@ def run_batched(args):
     wp, wo = make(probs[:16])
     run(wp, wo, warm_from_prev=True)  # warm-up
     plist, outs = make(probs)
+    if fused:
+        ctx.set_profiling(True)  # the fused kernel's own per-step clocks (no events)
+        ctx.get_profile(reset=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -316,6 +319,13 @@ def run_batched(args):
     s, infos = run(plist, outs, warm_from_prev=True)
     torch.cuda.synchronize(dev)
     dt = time.perf_counter() - t0
+    share = None
+    if fused:
+        prof = ctx.get_profile()
+        names = ("factorisations", "inverses", "scans_and_hierarchy", "cd_sweeps", "line_searches")
+        cls = [prof[glasso.PROF_NAMES[c]]["ms"] for c in range(len(names))]
+        tot = sum(cls)
+        share = {nm: (v / tot if tot > 0 else 0.0) for nm, v in zip(names, cls)}
     ctx.close()
     max_s, total, value = batched_job_value(dt, len(plist), world, dev)
     lat = [i["seconds"] * 1e3 for i in infos]
@@ -357,6 +367,7 @@ def run_batched(args):
                             "peak_source": "nominal FP64 rate (no measured FP64 peak); achieved = the "
                                            "solves' algorithmic FP64 operations / the call's wall time",
                             "kernel": "k_fused_paths"}
+        line["time_share"] = share  # of the CTAs' summed device time, by step
     print(json.dumps(line), flush=True)
     return 0
 
@@ -520,7 +531,7 @@ def extra_workloads(args, local, dev):
                                capture_output=True, text=True, timeout=600)
             line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
             out[name] = {k: line[k] for k in ("metric", "value", "unit", "latency_ms", "failed", "config",
-                                              "roofline", "dtype") if k in line}
+                                              "roofline", "dtype", "time_share") if k in line}
         except Exception as e:  # reported, not fatal: the headline stands on its own
             out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
     return out
@@ -672,7 +683,7 @@ def main():
                     help="Newton-direction solver of the batched and serving workloads (auto by default: per "
                          "relaxation PCD-CG when the CD sweeps' serial chain would be long, CD sweeps when the "
                          "free set is small and PCD-CG's fixed cost would dominate)")
-    ap.add_argument("--batch-engine", default="slots", choices=["fused", "slots"],
+    ap.add_argument("--batch-engine", default="fused", choices=["fused", "slots"],
                     help="batched workload: one persistent launch over all paths (fused) or the host-driven "
                          "serving slots")
     ap.add_argument("--no-compare", action="store_true",

@@ -171,7 +171,11 @@ glasso_status glasso_solve_batch(glasso_ctx *ctx, const glasso_problem *p, int c
  * Section 7, CD sweeps on the Newton LASSO of eq. Quad_MLE_l1_prior, the
  * Armijo line search of Section 6.1.2, the Section 8 KKT stop) itself, in
  * FP64, whatever the context's precision; no host round trip between steps,
- * relaxations or problems.  infos[k].seconds is the solve's own device time.
+ * relaxations or problems.  infos[k].seconds is the solve's own device time;
+ * with profiling on (glasso_set_profiling), the kernel classes of
+ * glasso_get_profile receive the CTAs' summed device time per step: 0 the
+ * factorisations of the iterate, 1 the inverses, 2 the free-set scans and the
+ * hierarchy, 3 the CD sweeps, 4 the line searches.
  * Requires 1 <= n <= GLASSO_FUSED_MAX_N, screen = 0, continuation = 0 and
  * inner CD or AUTO (AUTO takes the CD sweeps here); otherwise GLASSO_EINVAL
  * before any work.  GLASSO_ENOMEM when the launch's memory (inputs, outputs

@@ -1739,6 +1739,12 @@ glasso_status glasso_solve_batch_fused(glasso_ctx *ctx, const glasso_problem *p,
         CK(cudaMemcpyAsync(A_out[k], base + a_off[k], (size_t)p[k].n * p[k].n * sizeof(double), kind, st));
     }
     CK(cudaStreamSynchronize(st));
+    // with profiling on, the step classes receive the CTAs' summed device time
+    if (ctx->prof && ((Prof *)ctx->prof)->on) {
+        Prof *pr = (Prof *)ctx->prof;
+        for (int k = 0; k < count; ++k)
+            for (int c = 0; c < FUSED_CLASSES; ++c) pr->ms[c] += res[k].cls_ns[c] * 1e-6;
+    }
     glasso_status first = GLASSO_OK;
     for (int k = 0; k < count; ++k) {
         const FusedResult &r = res[k];

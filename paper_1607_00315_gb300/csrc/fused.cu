@@ -47,6 +47,8 @@ struct FShared {
     double dbc[2];      // broadcast doubles
     int ibc;
     int fail;
+    double cls[FUSED_CLASSES];  // device time per step class of the current solve (thread 0)
+    unsigned long long tmark;
     double dg[PNB][PLD];  // a diagonal block of the factor
     double dx[PNB][PLD];  // its inverse
     double panel[GLASSO_FUSED_MAX_N * PLD];
@@ -126,6 +128,16 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Thread 0 charges the time since the last mark to step class c (each step
+// ends at a CTA barrier, so thread 0's clock stands for the CTA's).
+__device__ __forceinline__ void lap(FShared &sm, int c) {
+    if (threadIdx.x == 0) {
+        const unsigned long long now = globaltimer();
+        sm.cls[c] += (double)(now - sm.tmark);
+        sm.tmark = now;
+    }
 }
 
 // T <- the lower triangle of A (the upper triangle of T is not written).
@@ -750,6 +762,10 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
     const double *S = P.S;
     const int nn = n * n;
     const unsigned long long t0 = globaltimer();
+    if (t == 0) {
+        for (int c = 0; c < FUSED_CLASSES; ++c) sm.cls[c] = 0.0;
+        sm.tmark = t0;
+    }
     int status = GLASSO_EMAXITER, cycles = 0, relax = 0, lstrials = 0;
     long long sweeps = 0;
     double F = 0.0, logdet = 0.0, relkkt = INFINITY, maxkkt = INFINITY, trSA = 0.0, l1 = 0.0;
@@ -788,18 +804,22 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
         status = GLASSO_ENOTPD;
         goto out;
     }
+    lap(sm, 0);
     chol_ok = true;
     cta_trtri(ws.T, ws.X, n, sm);
     cta_xtx(ws.X, ws.W, n);
     __syncthreads();
+    lap(sm, 1);
     flops += 2.0 * n3 / 3.0;
     W_ok = true;
     nf = cta_scan_full(S, ws.W, ws.A, n, lam, 1, ws.fi, ws.fj, ws.fabsg, o5, sm);
+    lap(sm, 2);
 
     for (int k = 0; k < P.max_cycles; ++k) {
         cycles = k + 1;
         const int nsweeps = min(1 + k / 3, 10);
         int Lv = cta_hierarchy(ws.fabsg, ws.fi, ws.fj, ws.A, n, nf, ws.ftag, ws.fsup, sm);
+        lap(sm, 2);
         if (P.one_level) Lv = 0;
         for (int l = Lv; l >= 0; --l) {
             fresh = false;
@@ -811,6 +831,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                     status = GLASSO_ENOTPD;
                     goto out;
                 }
+                lap(sm, 0);
                 chol_ok = true;
             }
             if (!W_ok) {
@@ -818,6 +839,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                 cta_xtx(ws.X, ws.W, n);
                 __syncthreads();
                 flops += 2.0 * n3 / 3.0;
+                lap(sm, 1);
                 W_ok = true;
             }
             int np;
@@ -835,6 +857,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                 qi = ws.fi;
                 qj = ws.fj;
                 fresh = true;
+                lap(sm, 2);
                 if (relkkt <= P.tol) {
                     status = GLASSO_OK;
                     goto out;
@@ -845,6 +868,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                 np = cta_scan_cand(S, ws.W, ws.A, n, lam, ws.fi, ws.fj, ws.ftag, l, nf, ws.pi, ws.pj, sm);
                 qi = ws.pi;
                 qj = ws.pj;
+                lap(sm, 2);
             }
             // Newton direction from Delta = 0
             for (int e = t; e < nn; e += FT) ws.Ut[e] = 0.0;
@@ -855,6 +879,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                 cta_cd(ws.W, n, qi, qj, np, nsweeps, ws.pg, ws.pinva, ws.plia, ws.pa, ws.D, ws.Ut, sm);
             sweeps += nsweeps;
             flops += 2.0 * n * ((double)np * nsweeps + (double)rows);
+            lap(sm, 3);
             double mv = 0.0;
             for (int p = t; p < np; p += FT) mv += ws.D[p] != 0.0 ? 1.0 : 0.0;
             if (cta_sum(mv, sm) != 0.0) {
@@ -863,6 +888,7 @@ __device__ void fused_solve(const FusedProblem &P, FusedResult &R, const FSlot &
                                                trSA, l1, tr, sm);
                 lstrials += tr;
                 flops += tr * n3 / 3.0;
+                lap(sm, 4);
                 if (rc != GLASSO_OK) {
                     chol_ok = false;  // T holds a rejected trial
                     status = rc;
@@ -916,6 +942,8 @@ out:
         R.max_nnz = (long long)max_nnz;
         R.sweeps = sweeps;
         R.flops = flops;
+        lap(sm, 2);  // the closing evaluation and the copy out
+        for (int c = 0; c < FUSED_CLASSES; ++c) R.cls_ns[c] = sm.cls[c];
         R.t0 = t0;
         R.t1 = globaltimer();
     }

@@ -331,6 +331,10 @@ cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi
 // One problem of a fused launch: S and A_out are n x n FP64 on the device,
 // A0 (optional) too; n <= GLASSO_FUSED_MAX_N.
 constexpr int FUSED_THREADS = GLASSO_FUSED_MAX_N;  // one thread per column of a row
+// device time of a fused solve per step class, indexed like the profile
+// classes: 0 factorisations of the iterate, 1 inverses, 2 free-set scans and
+// hierarchy, 3 CD sweeps, 4 line searches
+constexpr int FUSED_CLASSES = 5;
 struct FusedProblem {
     const double *S;
     const double *A0;
@@ -343,6 +347,7 @@ struct FusedResult {
     double objective, rel_kkt, max_kkt, logdet;
     long long nnz, max_nnz, sweeps;
     double flops;               // algorithmic FP64 operations of the dense steps and the sweeps
+    double cls_ns[FUSED_CLASSES];  // device time per step class (ns)
     unsigned long long t0, t1;  // device global timer (ns) at the solve's start and end
 };
 // Workspace bytes of one CTA slot for problems of size <= nmax.
