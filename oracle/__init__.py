@@ -87,6 +87,15 @@ def lib():
         L.orc_pcd.restype = C.c_int
         L.orc_components.restype = C.c_int64
         L.orc_continuation_lambdas.restype = C.c_int
+        L.orc_bcd_logdet.argtypes = [_d, C.c_int64, _i32, _i32, C.c_int64, _d, _u8, C.c_double, _d]
+        L.orc_bcd_logdet.restype = C.c_int
+        L.orc_bcd_iteration.argtypes = [_d, _d, C.c_int64, C.c_double, C.c_int64, _i32, _i32, C.c_int64,
+                                        C.c_int, C.c_int, C.c_int, _d, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]
+        L.orc_bcd_iteration.restype = C.c_int
+        L.orc_solve_bcd.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d,
+                                    C.POINTER(Info), C.c_int64, C.c_int, C.c_int, C.c_int]
+        L.orc_solve_bcd.restype = C.c_int
         _lib = L
     return _lib
 
@@ -281,3 +290,63 @@ def solve(S, lam, tol=1e-8, max_cycles=200, A0=None, trace_cap=0, one_level=Fals
                     1 if continuation else 0, 1 if inner == "pcd_cg" else 0)
     d = {k: getattr(info, k) for k, _ in Info._fields_}
     return A, W, d, tr[: info.ntrace].copy()
+
+
+# ---- NEXT-4: BCD-IC (Section 6, Algorithm 2) ----------------------------------
+
+_RULES = {"armijo": 0, "paper": 1}
+
+
+def bcd_logdet(A, pi, pj, D, inI, alpha):
+    """log det(A + alpha Delta) by the Schur complement on the index set I
+    (eq. logdet_blocks); Delta on the pairs (pi <= pj) must vanish outside
+    the rows/columns of I.  Returns (code, log det): code 0, 1 (A_22 not
+    positive definite), 2 (the small matrix not), -1 (Delta on the 22 block)."""
+    A = _f64(A)
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    D = _f64(D)
+    m = np.ascontiguousarray(inI, dtype=np.uint8)
+    ld = C.c_double(0.0)
+    rc = lib().orc_bcd_logdet(_p(A), A.shape[0], _p(pi, _i32), _p(pj, _i32), len(pi), _p(D),
+                              _p(m, _u8), alpha, C.byref(ld))
+    return rc, ld.value
+
+
+def bcd_iteration(S, A, lam, block, cand=None, inner="pcd_cg", nsweeps=1, rule="paper"):
+    """One BCD-IC iteration (Algorithm 2) over the column blocks of `block`
+    columns; cand = (ci, cj) restricts the block free sets to candidates.
+    Returns (status, A_new, F(A_new), line-search evaluations, blocks moved)."""
+    S = _f64(S)
+    A = _f64(A).copy()
+    n = A.shape[0]
+    if cand is None:
+        ci = cj = None
+        nc = 0
+    else:
+        ci = np.ascontiguousarray(cand[0], dtype=np.int32)
+        cj = np.ascontiguousarray(cand[1], dtype=np.int32)
+        nc = len(ci)
+    F = C.c_double(0.0)
+    tr, mv = C.c_int(0), C.c_int(0)
+    rc = lib().orc_bcd_iteration(_p(S), _p(A), n, lam, int(block),
+                                 None if ci is None else _p(ci, _i32), None if cj is None else _p(cj, _i32),
+                                 nc, 1 if inner == "pcd_cg" else 0, nsweeps, _RULES[rule], C.byref(F),
+                                 C.byref(tr), C.byref(mv))
+    return rc, A, F.value, tr.value, mv.value
+
+
+def solve_bcd(S, lam, tol=1e-8, block=None, max_cycles=200, A0=None, inner="pcd_cg", rule="paper",
+              one_level=False):
+    """ML-BCD: the ML-cycle with one BCD-IC iteration (blocks of `block`
+    columns, default all n) as the relaxation on each level; one_level: BCD-IC
+    alone.  Returns (A, info dict)."""
+    S = _f64(S)
+    n = S.shape[0]
+    A = np.empty((n, n))
+    info = Info()
+    a0 = None if A0 is None else _f64(A0)
+    lib().orc_solve_bcd(_p(S), n, lam, tol, max_cycles, None if a0 is None else _p(a0), _p(A),
+                        C.byref(info), int(block or n), 1 if inner == "pcd_cg" else 0, _RULES[rule],
+                        1 if one_level else 0)
+    return A, {k: getattr(info, k) for k, _ in Info._fields_}

@@ -16,6 +16,11 @@
  * upper-triangle index pairs (i <= j) in row-major order (i ascending, then j
  * ascending); a pair (i, j) stands for both A_ij and A_ji.
  *
+ * Functions: a1-a8 (the dense ML-cycle: S, Cholesky, inverse, free set and
+ * KKT residual, hierarchy, CD sweeps, PCD / PCD-CG, line search, solve),
+ * continuation and screening, and NEXT-4: BCD-IC (Section 6, Algorithm 2) with
+ * its Schur-complement log det and ML-BCD (the ML-cycle over BCD-IC).
+ *
  * Readings of points the paper leaves open are marked READING.
  * Parity pins: every function here is pinned by the CPU test suite against
  * closed forms, library routines, brute force on tiny inputs or the paper's
@@ -839,3 +844,340 @@ int64_t orc_components(const double *S, int64_t n, double lam, int32_t *comp) {
 
 /* Relaxation count of trace entries written (for callers sizing buffers). */
 int64_t orc_max_pairs(int64_t n) { return n * (n + 1) / 2; }
+
+/* ---------------------------------------------------------------------- */
+/* NEXT-4. BCD-IC (Section 6, Algorithm 2): the paper's relaxation for n
+ * beyond dense memory, written here from its definitions on dense matrices.
+ * The cheaper routes the paper takes at scale (only the columns I_j and N_j
+ * of W, its appendix's formulas for the B_i from those columns) are not
+ * taken: every quantity is formed from its definition.                     */
+
+/* x = M^{-1} b for M = L L^T (L lower triangular, m x m). */
+static void chol_solve(const double *L, int64_t m, const double *b, double *x) {
+    for (int64_t i = 0; i < m; ++i) {
+        double s = b[i];
+        for (int64_t k = 0; k < i; ++k) s -= L[i * m + k] * x[k];
+        x[i] = s / L[i * m + i];
+    }
+    for (int64_t i = m - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t k = i + 1; k < m; ++k) s -= L[k * m + i] * x[k];
+        x[i] = s / L[i * m + i];
+    }
+}
+
+/* Schur-complement log det (eq. Schurs_lemma, eq. logdet_blocks, eq.
+ * Schurs_PDness).  The block "1" is the index set I (mask inI), "2" its
+ * complement; Delta (pairs pi <= pj with values D, mirrored) must vanish on
+ * the 22 block, as a block update's direction does:
+ *   log det(A + alpha Delta) = log det A_22 + log det(B_0 + alpha B_1 + alpha^2 B_2),
+ *   B_0 = A_11 - A_12 A_22^{-1} A_21,
+ *   B_1 = Delta_11 - Delta_12 A_22^{-1} A_21 - A_12 A_22^{-1} Delta_21,
+ *   B_2 = -Delta_12 A_22^{-1} Delta_21,
+ * and A + alpha Delta is positive definite iff A_22 and the small matrix are.
+ * A_22^{-1} A_21 and A_22^{-1} Delta_21 come from Cholesky solves with A_22.
+ * Returns 0 with *ld set; 1 when A_22, 2 when the small matrix is not
+ * positive definite; -1 when Delta is nonzero on the 22 block.             */
+int orc_bcd_logdet(const double *A, int64_t n, const int32_t *pi, const int32_t *pj, int64_t np,
+                   const double *D, const uint8_t *inI, double alpha, double *ld) {
+    int64_t m1 = 0, m2 = 0;
+    int64_t *i1 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *i2 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        if (inI[i]) i1[m1++] = i;
+        else i2[m2++] = i;
+    }
+    double *Dl = (double *)calloc((size_t)(n * n), sizeof(double));
+    const size_t s1 = (size_t)(m1 > 0 ? m1 : 1), s2 = (size_t)(m2 > 0 ? m2 : 1);
+    double *A22 = (double *)malloc(s2 * s2 * sizeof(double));
+    double *L22 = (double *)malloc(s2 * s2 * sizeof(double));
+    double *Y = (double *)malloc(s2 * s1 * sizeof(double)); /* A_22^{-1} A_21, column c at Y[c m2] */
+    double *Z = (double *)malloc(s2 * s1 * sizeof(double)); /* A_22^{-1} Delta_21 */
+    double *rhs = (double *)malloc(s2 * sizeof(double));
+    double *M = (double *)malloc(s1 * s1 * sizeof(double));
+    double *LM = (double *)malloc(s1 * s1 * sizeof(double));
+    int rc = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        const int64_t i = pi[p], j = pj[p];
+        if (!inI[i] && !inI[j] && D[p] != 0.0) { rc = -1; goto out; }
+        Dl[i * n + j] = D[p];
+        Dl[j * n + i] = D[p];
+    }
+    double ld22 = 0.0;
+    if (m2 > 0) {
+        for (int64_t a = 0; a < m2; ++a)
+            for (int64_t c = 0; c < m2; ++c) A22[a * m2 + c] = A[i2[a] * n + i2[c]];
+        if (orc_cholesky(A22, m2, L22) != 0) { rc = 1; goto out; }
+        ld22 = orc_logdet_from_chol(L22, m2);
+        for (int64_t c = 0; c < m1; ++c) {
+            for (int64_t a = 0; a < m2; ++a) rhs[a] = A[i2[a] * n + i1[c]];
+            chol_solve(L22, m2, rhs, Y + c * m2);
+            for (int64_t a = 0; a < m2; ++a) rhs[a] = Dl[i2[a] * n + i1[c]];
+            chol_solve(L22, m2, rhs, Z + c * m2);
+        }
+    }
+    for (int64_t a = 0; a < m1; ++a)
+        for (int64_t c = 0; c < m1; ++c) {
+            const int64_t ia = i1[a], ic = i1[c];
+            double b0 = A[ia * n + ic], b1 = Dl[ia * n + ic], b2 = 0.0;
+            for (int64_t k = 0; k < m2; ++k) {
+                const double a12 = A[ia * n + i2[k]], d12 = Dl[ia * n + i2[k]];
+                b0 -= a12 * Y[c * m2 + k];
+                b1 -= d12 * Y[c * m2 + k] + a12 * Z[c * m2 + k];
+                b2 -= d12 * Z[c * m2 + k];
+            }
+            M[a * m1 + c] = b0 + alpha * b1 + alpha * alpha * b2;
+        }
+    if (m1 > 0 && orc_cholesky(M, m1, LM) != 0) { rc = 2; goto out; }
+    *ld = ld22 + (m1 > 0 ? orc_logdet_from_chol(LM, m1) : 0.0);
+out:
+    free(i1); free(i2); free(Dl); free(A22); free(L22); free(Y); free(Z); free(rhs); free(M); free(LM);
+    return rc;
+}
+
+/* One BCD-IC iteration (Algorithm 2) at lambda.  The columns are split into
+ * the blocks I_j = [j b, min((j + 1) b, n)), treated in order (READING: the
+ * paper clusters the columns with METIS, an external library, and allows any
+ * partition; consecutive index ranges are the partition its Figure
+ * fig:BCD_Sweep draws).  For each block, at the current iterate A:
+ *   1. W = A^{-1} from the Cholesky factor (the algorithm solves linear
+ *      systems for the columns I_j and N_j of W; all of W contains them);
+ *   2. the block's free set (eq. active_set_j): the free pairs (eq.
+ *      active_set, at the current A) with a row or a column in I_j, taken
+ *      from the candidate list when one is given (Section 7: within C_l),
+ *      else from all upper-triangle pairs;
+ *   3. the Newton direction on those pairs from Delta = 0 (eq.
+ *      sub_Quad_MLE_l1_prior): PCD-CG to the relative precision 1e-4 (the
+ *      paper's block solver; inner = 1) or nsweeps CD sweeps (inner = 0);
+ *   4. the line search along it, log det by eq. logdet_blocks, over the
+ *      samples alpha_i = beta^i (beta = 1/2, at most 30):
+ *      rule 1 (Section 6.1.2: the sample minimising F subject to positive
+ *      definiteness): the first positive-definite alpha_i with F(alpha_i)
+ *      <= F(A) + eps_F whose successor is not lower, F(alpha_{i+1}) >=
+ *      F(alpha_i) (READING: F is convex along the ray, so the samples fall
+ *      until the one before the first rise, the best of them);
+ *      rule 0: the dense relaxation's Armijo test (orc_line_search), so that
+ *      with one block holding every index the iteration is exactly the
+ *      dense relaxation (Section 6.2: QUIC is BCD-IC with a single block).
+ *      eps_F = 1e-12 max(|F(A)|, n) as there.
+ * F_out: F of the final iterate.  Returns 0, ORC_ENOTPD (A not positive
+ * definite) or ORC_ELINESEARCH; *moved = blocks with a nonzero direction;
+ * *trials = objective evaluations of the line searches.                    */
+int orc_bcd_iteration(const double *S, double *A, int64_t n, double lam, int64_t b,
+                      const int32_t *cand_i, const int32_t *cand_j, int64_t ncand, int inner,
+                      int nsweeps, int rule, double *F_out, int *trials, int *moved) {
+    if (b < 1) b = n;
+    const size_t nn = (size_t)(n * n);
+    const int64_t maxp = cand_i ? (ncand > 0 ? ncand : 1) : n * (n + 1) / 2;
+    double *L = (double *)malloc(nn * sizeof(double));
+    double *W = (double *)malloc(nn * sizeof(double));
+    double *U = (double *)malloc(nn * sizeof(double));
+    double *T = (double *)malloc(nn * sizeof(double));
+    int32_t *pi = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *pj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    double *D = (double *)malloc((size_t)maxp * sizeof(double));
+    uint8_t *inI = (uint8_t *)malloc((size_t)n);
+    int rc = ORC_OK, ntr = 0, nmv = 0;
+    double F = 0.0;
+    for (int64_t j0 = 0; j0 < n; j0 += b) {
+        const int64_t j1 = j0 + b < n ? j0 + b : n;
+        for (int64_t i = 0; i < n; ++i) inI[i] = i >= j0 && i < j1;
+        if (orc_cholesky(A, n, L) != 0) { rc = ORC_ENOTPD; goto out; }
+        orc_inverse_from_chol(L, n, W);
+        double tr, l1;
+        trace_and_l1(S, A, n, &tr, &l1);
+        F = -orc_logdet_from_chol(L, n) + tr + lam * l1;
+        int64_t np = 0;
+        if (cand_i) {
+            for (int64_t p = 0; p < ncand; ++p) {
+                const int64_t i = cand_i[p], j = cand_j[p];
+                if (!inI[i] && !inI[j]) continue;
+                if (A[i * n + j] != 0.0 || fabs(S[i * n + j] - W[i * n + j]) > lam) {
+                    pi[np] = (int32_t)i; pj[np] = (int32_t)j; ++np;
+                }
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = i; j < n; ++j) {
+                    if (!inI[i] && !inI[j]) continue;
+                    if (A[i * n + j] != 0.0 || fabs(S[i * n + j] - W[i * n + j]) > lam) {
+                        pi[np] = (int32_t)i; pj[np] = (int32_t)j; ++np;
+                    }
+                }
+        }
+        memset(U, 0, nn * sizeof(double));
+        memset(D, 0, (size_t)(np > 0 ? np : 1) * sizeof(double));
+        if (inner == 1)
+            orc_pcd(S, W, A, n, lam, pi, pj, np, 500, 1, 1e-4, D, U);
+        else
+            orc_cd_sweeps(S, W, A, n, lam, pi, pj, np, nsweeps, D, U);
+        int mv = 0;
+        for (int64_t p = 0; p < np; ++p) mv |= D[p] != 0.0;
+        if (!mv) continue;
+        ++nmv;
+        const double epsF = 1e-12 * (fabs(F) > (double)n ? fabs(F) : (double)n);
+        double delta = 0.0;
+        for (int64_t p = 0; p < np; ++p) {
+            const int64_t i = pi[p], j = pj[p];
+            const double mult = i == j ? 1.0 : 2.0, aij = A[i * n + j];
+            delta += mult * ((S[i * n + j] - W[i * n + j]) * D[p] + lam * (fabs(aij + D[p]) - fabs(aij)));
+        }
+        /* F(A + alpha Delta) by eq. logdet_blocks; +inf when not positive definite */
+        double alpha = 1.0, a_acc = 0.0, F_acc = 0.0, prevF = INFINITY, prevA = 0.0;
+        int ok = 0;
+        for (int t = 0; t < 30 && !ok; ++t, alpha *= 0.5) {
+            memcpy(T, A, nn * sizeof(double));
+            for (int64_t p = 0; p < np; ++p) {
+                const int64_t i = pi[p], j = pj[p];
+                T[i * n + j] = A[i * n + j] + alpha * D[p];
+                T[j * n + i] = T[i * n + j];
+            }
+            double ldT = 0.0, Ft = INFINITY;
+            ++ntr;
+            if (orc_bcd_logdet(A, n, pi, pj, np, D, inI, alpha, &ldT) == 0) {
+                double trT, l1T;
+                trace_and_l1(S, T, n, &trT, &l1T);
+                Ft = -ldT + trT + lam * l1T;
+            }
+            if (rule == 0) {
+                if (Ft <= F + 1e-4 * alpha * delta + epsF) { ok = 1; a_acc = alpha; F_acc = Ft; }
+            } else {
+                if (prevF < INFINITY && prevF <= F + epsF && Ft >= prevF) { ok = 1; a_acc = prevA; F_acc = prevF; }
+                prevF = Ft;
+                prevA = alpha;
+            }
+        }
+        if (!ok && rule != 0 && prevF <= F + epsF) {
+            /* the samples fell to the last one: it is the best */
+            ok = 1;
+            a_acc = prevA;
+            F_acc = prevF;
+        }
+        if (!ok) { rc = ORC_ELINESEARCH; goto out; }
+        for (int64_t p = 0; p < np; ++p) {
+            const int64_t i = pi[p], j = pj[p];
+            A[i * n + j] = A[i * n + j] + a_acc * D[p];
+            A[j * n + i] = A[i * n + j];
+        }
+        F = F_acc;
+    }
+    if (orc_cholesky(A, n, L) != 0) { rc = ORC_ENOTPD; goto out; }
+    {
+        double tr, l1;
+        trace_and_l1(S, A, n, &tr, &l1);
+        F = -orc_logdet_from_chol(L, n) + tr + lam * l1;
+    }
+out:
+    if (F_out) *F_out = F;
+    if (trials) *trials = ntr;
+    if (moved) *moved = nmv;
+    free(L); free(W); free(U); free(T); free(pi); free(pj); free(D); free(inI);
+    return rc;
+}
+
+/* ML-BCD: the ML-cycle of orc_solve (Algorithm 1 with nu = nu_c = 1, the
+ * hierarchy of Section 7, the Section 8 KKT stop) with one BCD-IC iteration
+ * (orc_bcd_iteration, blocks of b columns) as the relaxation on C_l, the
+ * combination the paper measures (Section 7: BCD-IC as the relaxation, the
+ * block free sets within C_l).  At level 0 the block free sets come from all
+ * pairs; at level l > 0 from the candidates of C_l (the previous fine free
+ * set's pairs with tag >= l).  inner, rule: as in orc_bcd_iteration; CD
+ * sweeps take nsweeps = min(1 + floor(k/3), 10) in cycle k as orc_solve does.
+ * one_level != 0: the level-0 relaxation only (BCD-IC alone).              */
+int orc_solve_bcd(const double *S, int64_t n, double lam, double tol, int max_cycles,
+                  const double *A0, double *A, orc_info *info, int64_t b, int inner, int rule,
+                  int one_level) {
+    if (n < 1 || !(lam > 0.0)) return ORC_EINVAL;
+    const size_t nn = (size_t)(n * n);
+    const int64_t maxp = n * (n + 1) / 2;
+    double *L = (double *)malloc(nn * sizeof(double));
+    double *W = (double *)malloc(nn * sizeof(double));
+    int32_t *fi = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *fj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *ci = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    int32_t *cj = (int32_t *)malloc((size_t)maxp * sizeof(int32_t));
+    double *absg = (double *)malloc((size_t)maxp * sizeof(double));
+    uint8_t *insupp = (uint8_t *)malloc((size_t)maxp);
+    uint8_t *tag = (uint8_t *)malloc((size_t)maxp);
+    int status = ORC_EMAXITER, relax = 0, lstrials = 0, cycles = 0;
+    int64_t max_nnz = 0, nf = 0;
+    double F = 0.0, relkkt = INFINITY, maxkkt = INFINITY, logdet = 0.0;
+    if (A0) {
+        memcpy(A, A0, nn * sizeof(double));
+    } else {
+        memset(A, 0, nn * sizeof(double));
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(S[i * n + i] + lam > 0.0)) { status = ORC_ENOTPD; goto done; }
+            A[i * n + i] = 1.0 / (S[i * n + i] + lam);
+        }
+    }
+    if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
+    orc_inverse_from_chol(L, n, W);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i; j < n; ++j)
+            if (fabs(S[i * n + j]) > lam || A[i * n + j] != 0.0) {
+                fi[nf] = (int32_t)i; fj[nf] = (int32_t)j;
+                absg[nf] = fabs(S[i * n + j] - W[i * n + j]);
+                ++nf;
+            }
+    for (int k = 0; k < max_cycles; ++k) {
+        cycles = k + 1;
+        int nsweeps = 1 + k / 3;
+        if (nsweeps > 10) nsweeps = 10;
+        for (int64_t p = 0; p < nf; ++p) insupp[p] = A[fi[p] * n + fj[p]] != 0.0;
+        int L_levels = 1;
+        orc_hierarchy(absg, insupp, nf, tag, &L_levels);
+        if (one_level) L_levels = 0;
+        for (int l = L_levels; l >= 0; --l) {
+            const int32_t *qi = NULL, *qj = NULL;
+            int64_t nq = 0;
+            if (l == 0) {
+                if (orc_cholesky(A, n, L) != 0) { status = ORC_ENOTPD; goto done; }
+                orc_inverse_from_chol(L, n, W);
+                const int64_t z = count_nnz(A, nn);
+                if (z > max_nnz) max_nnz = z;
+                nf = orc_free_set(S, W, A, n, lam, NULL, NULL, 0, fi, fj);
+                for (int64_t p = 0; p < nf; ++p) absg[p] = fabs(S[fi[p] * n + fj[p]] - W[fi[p] * n + fj[p]]);
+                relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
+                if (relkkt <= tol) { status = ORC_OK; goto done; }
+            } else {
+                for (int64_t p = 0; p < nf; ++p)
+                    if (tag[p] >= l) { ci[nq] = fi[p]; cj[nq] = fj[p]; ++nq; }
+                qi = ci;
+                qj = cj;
+            }
+            int tr = 0, mv = 0;
+            const int rc = orc_bcd_iteration(S, A, n, lam, b, qi, qj, nq, inner, nsweeps, rule, &F, &tr, &mv);
+            lstrials += tr;
+            if (rc != ORC_OK) { status = rc; goto done; }
+            ++relax;
+        }
+    }
+done:
+    if (status == ORC_OK || status == ORC_EMAXITER || status == ORC_ELINESEARCH) {
+        if (orc_cholesky(A, n, L) == 0) {
+            logdet = orc_logdet_from_chol(L, n);
+            orc_inverse_from_chol(L, n, W);
+            double tr, l1;
+            trace_and_l1(S, A, n, &tr, &l1);
+            F = -logdet + tr + lam * l1;
+            relkkt = orc_rel_kkt(S, W, A, n, lam, &maxkkt);
+        }
+    }
+    if (info) {
+        const int64_t nnz = count_nnz(A, nn);
+        info->status = status;
+        info->cycles = cycles;
+        info->relaxations = relax;
+        info->ls_trials = lstrials;
+        info->objective = F;
+        info->rel_kkt = relkkt;
+        info->max_kkt = maxkkt;
+        info->logdet = logdet;
+        info->nnz = nnz;
+        info->ntrace = 0;
+        info->max_nnz = nnz > max_nnz ? nnz : max_nnz;
+    }
+    free(L); free(W); free(fi); free(fj); free(ci); free(cj); free(absg); free(insupp); free(tag);
+    return status;
+}
