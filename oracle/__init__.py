@@ -96,6 +96,8 @@ def lib():
         L.orc_solve_bcd.argtypes = [_d, C.c_int64, C.c_double, C.c_double, C.c_int, _d, _d,
                                     C.POINTER(Info), C.c_int64, C.c_int, C.c_int, C.c_int]
         L.orc_solve_bcd.restype = C.c_int
+        L.orc_bcd_w11.argtypes = [_d, C.c_int64, _u8, _u8, _d, _d]
+        L.orc_bcd_w11.restype = C.c_int
         _lib = L
     return _lib
 
@@ -350,3 +352,17 @@ def solve_bcd(S, lam, tol=1e-8, block=None, max_cycles=200, A0=None, inner="pcd_
                         C.byref(info), int(block or n), 1 if inner == "pcd_cg" else 0, _RULES[rule],
                         1 if one_level else 0)
     return A, {k: getattr(info, k) for k, _ in Info._fields_}
+
+
+def bcd_w11(A, inI, inN, WN):
+    """W_11 = (A^{-1})_{II} from the columns of A^{-1} in the neighbourhood N
+    only (the appendix's reduced inversion): W_11 = A_11^{-1} (I - A_12 W_21).
+    Returns (code, W_11): 0, 1 (A_11 not positive definite), -1 (A_12 nonzero
+    outside N)."""
+    A, WN = _f64(A), _f64(WN)
+    mI = np.ascontiguousarray(inI, dtype=np.uint8)
+    mN = np.ascontiguousarray(inN, dtype=np.uint8)
+    m1 = int(mI.sum())
+    W11 = np.zeros((max(m1, 1), max(m1, 1)))
+    rc = lib().orc_bcd_w11(_p(A), A.shape[0], _p(mI, _u8), _p(mN, _u8), _p(WN), _p(W11))
+    return rc, W11[:m1, :m1]

@@ -1181,3 +1181,51 @@ done:
     free(L); free(W); free(fi); free(fj); free(ci); free(cj); free(absg); free(insupp); free(tag);
     return status;
 }
+
+/* The diagonal block W_11 = (A^{-1})_{I I} of a block from the columns of W
+ * in the block's C-neighbourhood only (appendix sec:reducingGradient, eq.
+ * reducingGradients1-2): block row I of A W = I reads A_11 W_11 + K = I with
+ * K = A_12 W_21, and A_12 is nonzero only in the neighbourhood's columns when
+ * supp(A) lies in C, so
+ *     K_ac = sum_{k in N} A_{a k} W_{k c}   (W_{k c} = W_{c k}: column k of W),
+ *     W_11 = A_11^{-1} (I - K)              (Cholesky solves with A_11).
+ * READING: the neighbourhood N = {k not in I : (i, k) in C for some i in I}
+ * (the printed eq. extended_set_C quantifies over the wrong index: read
+ * literally it holds every index outside I through the diagonal pairs).
+ * inN: the mask of N; WN: an n x n array whose columns k in N hold column k
+ * of A^{-1} (other columns are not read).  W11: m1 x m1 in the order of I.
+ * Returns 0; 1 when A_11 is not positive definite; -1 when A_12 has a
+ * nonzero outside N (the support is not within C).                         */
+int orc_bcd_w11(const double *A, int64_t n, const uint8_t *inI, const uint8_t *inN, const double *WN,
+                double *W11) {
+    int64_t m1 = 0;
+    int64_t *i1 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i)
+        if (inI[i]) i1[m1++] = i;
+    const size_t s1 = (size_t)(m1 > 0 ? m1 : 1);
+    double *A11 = (double *)malloc(s1 * s1 * sizeof(double));
+    double *L11 = (double *)malloc(s1 * s1 * sizeof(double));
+    double *rhs = (double *)malloc(s1 * sizeof(double));
+    double *x = (double *)malloc(s1 * sizeof(double));
+    int rc = 0;
+    for (int64_t a = 0; a < m1; ++a)
+        for (int64_t k = 0; k < n; ++k)
+            if (!inI[k] && !inN[k] && A[i1[a] * n + k] != 0.0) { rc = -1; goto out; }
+    for (int64_t a = 0; a < m1; ++a)
+        for (int64_t c = 0; c < m1; ++c) A11[a * m1 + c] = A[i1[a] * n + i1[c]];
+    if (m1 > 0 && orc_cholesky(A11, m1, L11) != 0) { rc = 1; goto out; }
+    for (int64_t c = 0; c < m1; ++c) {
+        /* column c of I - K */
+        for (int64_t a = 0; a < m1; ++a) {
+            double kac = 0.0;
+            for (int64_t k = 0; k < n; ++k)
+                if (inN[k]) kac += A[i1[a] * n + k] * WN[i1[c] * n + k];
+            rhs[a] = (a == c ? 1.0 : 0.0) - kac;
+        }
+        chol_solve(L11, m1, rhs, x);
+        for (int64_t a = 0; a < m1; ++a) W11[a * m1 + c] = x[a];
+    }
+out:
+    free(i1); free(A11); free(L11); free(rhs); free(x);
+    return rc;
+}

@@ -160,3 +160,38 @@ def test_ml_bcd_reaches_the_minimiser(block, inner, one_level):
     W = np.linalg.inv(A_ref)
     border = np.abs(np.abs(S - W) - lam) <= 1e-7
     assert not np.any(((A != 0) != (A_ref != 0)) & ~border)
+
+
+def _sparse_spd(n, seed, density=0.15):
+    """A positive definite A whose off-diagonal support is a random pattern C."""
+    r = np.random.default_rng(seed)
+    C = np.triu(r.random((n, n)) < density, 1)
+    C = C | C.T
+    A = np.where(C, r.uniform(-0.3, 0.3, (n, n)), 0.0)
+    A = (A + A.T) / 2
+    A[np.arange(n), np.arange(n)] = np.abs(A).sum(1) + 0.5
+    return A, C
+
+
+@pytest.mark.parametrize("n,I,seed", [(20, [3, 4, 5, 6], 1), (30, [0, 29], 2), (25, list(range(10, 22)), 3)])
+def test_reduced_inversion_from_the_neighbourhood(n, I, seed):
+    """The appendix's W_11 = A_11^{-1}(I - A_12 W_21) from the neighbourhood's
+    columns of W alone equals the corresponding block of the dense inverse."""
+    A, C = _sparse_spd(n, seed)
+    inI = np.zeros(n, dtype=np.uint8)
+    inI[I] = 1
+    inN = np.zeros(n, dtype=np.uint8)
+    for k in range(n):
+        if not inI[k] and C[np.array(I), k].any():
+            inN[k] = 1
+    W = np.linalg.inv(A)
+    WN = np.full((n, n), np.nan)  # only the neighbourhood's columns are available
+    WN[:, inN.astype(bool)] = W[:, inN.astype(bool)]
+    rc, W11 = oracle.bcd_w11(A, inI, inN, WN)
+    assert rc == 0
+    assert np.abs(W11 - W[np.ix_(I, I)]).max() <= 1e-12 * np.abs(W).max()
+    # a support outside C (A_12 nonzero outside N) is refused
+    out = next(k for k in range(n) if not inI[k] and not inN[k])
+    B = A.copy()
+    B[I[0], out] = B[out, I[0]] = 0.01
+    assert oracle.bcd_w11(B, inI, inN, WN)[0] == -1
