@@ -392,6 +392,25 @@ glasso_status glasso_components(glasso_ctx *ctx, const double *S, int64_t n, dou
 glasso_status glasso_objective(glasso_ctx *ctx, const double *S, const double *A, int64_t n,
                                double lambda, double *F, int *info);
 
+/* BCD-IC's line-search log det (Section 6, the update of Algorithm 2;
+ * eq. Schurs_lemma, eq. logdet_blocks, eq. Schurs_PDness): for a block I and
+ * a direction Delta that vanishes outside the rows and columns of I,
+ *   log det(A + alpha Delta) = log det A_22 + log det(B_0 + alpha B_1 + alpha^2 B_2)
+ * with B_0 = A_11 - A_12 A_22^{-1} A_21, B_1 = Delta_11 - Delta_12 A_22^{-1} A_21
+ * - A_12 A_22^{-1} Delta_21, B_2 = -Delta_12 A_22^{-1} Delta_21 ("1" = I, "2"
+ * the other indices); A + alpha Delta is positive definite iff A_22 and the
+ * |I| x |I| matrix are.  FP64 on the device in any context.
+ * A: n x n FP64, device, symmetric (A_22 is read from it); pi, pj, D: the np
+ * pairs of Delta (i <= j, device); inI: n bytes on the device, nonzero for
+ * the indices of I.  *code (host): 0 with *logdet set; 1 when A_22, 2 when
+ * the small matrix is not positive definite; -1 when Delta has a nonzero
+ * pair outside the rows and columns of I.  GLASSO_EINVAL for bad arguments
+ * or a pair index outside [0, n).  Allocates its scratch on the context's
+ * stream and synchronises it. */
+glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, const int32_t *pi,
+                                const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
+                                double alpha, double *logdet, int *code);
+
 /* ---- allocation-free entry point ------------------------------------- */
 
 /* Largest n accepted by glasso_free_set_noalloc. */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libglasso.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["api.cu", "dense.cu", "scan.cu", "hier.cu", "cd.cu", "mixed.cu", "tc.cu", "cholinv_tc.cu",
-           "screen.cu", "pcd.cu", "chol_dag.cu", "fused.cu"]
+           "screen.cu", "pcd.cu", "chol_dag.cu", "fused.cu", "bcd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1855,6 +1855,91 @@ glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double
     return GLASSO_OK;
 }
 
+// BCD-IC's Schur-complement line-search log det (bcd.cu pieces, dense.cu's
+// FP64 factorisation and inverse).
+glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, const int32_t *pi,
+                                const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
+                                double alpha, double *logdet, int *code) {
+    if (!ctx || !A || !inI || !code || n < 1 || np < 0 || (np > 0 && (!pi || !pj || !D)) ||
+        !isfinite(alpha))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    glasso_status s = work_ensure(w, n, st, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    // the block's index lists
+    std::vector<uint8_t> mask((size_t)n);
+    CTX_CK(cudaMemcpyAsync(mask.data(), inI, (size_t)n, cudaMemcpyDeviceToHost, st));
+    CTX_CK(cudaStreamSynchronize(st));
+    std::vector<int32_t> i1, i2;
+    for (int64_t i = 0; i < n; ++i) (mask[i] ? i1 : i2).push_back((int32_t)i);
+    const int64_t m1 = (int64_t)i1.size(), m2 = (int64_t)i2.size();
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t nn = (size_t)n * n;
+    const size_t o_dl = 0, o_a22 = o_dl + al(nn * 8), o_inv = o_a22 + al((size_t)(m2 * m2) * 8),
+                 o_y = o_inv + al((size_t)(m2 * m2) * 8), o_z = o_y + al((size_t)(m2 * m1) * 8),
+                 o_m = o_z + al((size_t)(m2 * m1) * 8), o_i1 = o_m + al((size_t)(m1 * m1) * 8),
+                 o_i2 = o_i1 + al((size_t)m1 * 4), o_bad = o_i2 + al((size_t)m2 * 4), total = o_bad + 256;
+    char *base = nullptr;
+    if (cudaMallocAsync((void **)&base, total, st) != cudaSuccess) {
+        cudaGetLastError();
+        return GLASSO_ENOMEM;
+    }
+    struct Free {
+        char *p;
+        cudaStream_t st;
+        ~Free() { cudaFreeAsync(p, st); }
+    } guard{base, st};
+    double *Dl = (double *)(base + o_dl), *A22 = (double *)(base + o_a22), *Ainv = (double *)(base + o_inv);
+    double *Y = (double *)(base + o_y), *Z = (double *)(base + o_z), *M = (double *)(base + o_m);
+    int32_t *d1 = (int32_t *)(base + o_i1), *d2 = (int32_t *)(base + o_i2);
+    int *bad = (int *)(base + o_bad);
+    CTX_CK(cudaMemsetAsync(Dl, 0, nn * 8, st));
+    CTX_CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    if (m1) CTX_CK(cudaMemcpyAsync(d1, i1.data(), (size_t)m1 * 4, cudaMemcpyHostToDevice, st));
+    if (m2) CTX_CK(cudaMemcpyAsync(d2, i2.data(), (size_t)m2 * 4, cudaMemcpyHostToDevice, st));
+    CTX_CK(bcd_scatter(pi, pj, D, np, n, inI, Dl, bad, st));
+    int hbad = 0;
+    CTX_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CTX_CK(cudaStreamSynchronize(st));
+    if (hbad == 2) return GLASSO_EINVAL;
+    if (hbad == 1) {
+        *code = -1;
+        return GLASSO_OK;
+    }
+    double ld22 = 0.0;
+    if (m2 > 0) {
+        CTX_CK(bcd_gather(A, n, d2, m2, A22, st));
+        CTX_CK(potrf(A22, m2, w.xd, w.ldiag, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (w.sc_host->info != 0) {
+            *code = 1;
+            return GLASSO_OK;
+        }
+        ld22 = w.sc_host->logdet;
+        CTX_CK(inverse(A22, m2, Ainv, w.T, w.U, st));
+        CTX_CK(bcd_solve(Ainv, m2, A, Dl, n, d1, m1, d2, Y, Z, st));
+    }
+    double ld = ld22;
+    if (m1 > 0) {
+        CTX_CK(bcd_assemble(A, Dl, n, d1, m1, d2, m2, Y, Z, alpha, M, st));
+        CTX_CK(potrf(M, m1, w.xd, w.ldiag, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (w.sc_host->info != 0) {
+            *code = 2;
+            return GLASSO_OK;
+        }
+        ld += w.sc_host->logdet;
+    }
+    CTX_CK(cudaStreamSynchronize(st));
+    *code = 0;
+    if (logdet) *logdet = ld;
+    return GLASSO_OK;
+}
+
 glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, double *W, int *info,
                                    double *logdet) {
     if (!ctx || !A || !W || n < 1) return GLASSO_EINVAL;

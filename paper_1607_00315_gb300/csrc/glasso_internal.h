@@ -327,6 +327,21 @@ cudaError_t cd_sweeps32(const float *W, int64_t n, double lam, const int32_t *pi
                         const double *aval, int nsweeps, double *D, float *U, Work &w,
                         bool chain64, cudaStream_t st, float *U2 = nullptr);
 
+// ---- BCD-IC's Schur-complement line-search pieces (bcd.cu) ----
+// Dl (n x n, zeroed by the caller) <- Delta from its pairs; *bad = 1 for a
+// nonzero pair outside the block's rows and columns, 2 for an index outside [0, n).
+cudaError_t bcd_scatter(const int32_t *pi, const int32_t *pj, const double *D, int64_t np, int64_t n,
+                        const uint8_t *inI, double *Dl, int *bad, cudaStream_t st);
+// out (m x m) = A[idx, idx]
+cudaError_t bcd_gather(const double *A, int64_t n, const int32_t *idx, int64_t m, double *out, cudaStream_t st);
+// Y = A_22^{-1} A_21, Z = A_22^{-1} Delta_21 (column c at offset c m2) from Ainv = A_22^{-1}
+cudaError_t bcd_solve(const double *Ainv, int64_t m2, const double *A, const double *Dl, int64_t n,
+                      const int32_t *idx1, int64_t m1, const int32_t *idx2, double *Y, double *Z, cudaStream_t st);
+// M = B_0 + alpha B_1 + alpha^2 B_2 (m1 x m1)
+cudaError_t bcd_assemble(const double *A, const double *Dl, int64_t n, const int32_t *idx1, int64_t m1,
+                         const int32_t *idx2, int64_t m2, const double *Y, const double *Z, double alpha,
+                         double *M, cudaStream_t st);
+
 // ---- the batched solver (fused.cu) ----
 // One problem of a fused launch: S and A_out are n x n FP64 on the device,
 // A0 (optional) too; n <= GLASSO_FUSED_MAX_N.

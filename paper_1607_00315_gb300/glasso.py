@@ -96,6 +96,7 @@ def load():
     L.glasso_solve.argtypes = [vp, C.POINTER(Problem), vp, vp, C.POINTER(Info)]
     L.glasso_solve_batch.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                      C.POINTER(Info)]
+    L.glasso_bcd_logdet.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, d, C.POINTER(d), C.POINTER(i32)]
     L.glasso_solve_batch_fused.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                            C.POINTER(Info)]
     L.glasso_submit.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(C.c_uint64)]
@@ -266,6 +267,16 @@ class Context:
         s = self.L.glasso_solve_batch_fused(self.h, arr, k, int(warm_from_prev), ptrs, infos)
         return s, [infos[i].as_dict() for i in range(k)]
 
+    def bcd_logdet(self, A, pi, pj, D, inI, alpha):
+        """glasso_bcd_logdet (BCD-IC's Schur-complement log det) on CUDA tensors:
+        A (n x n float64), pi/pj (int32) and D (float64) the pairs of Delta,
+        inI (uint8) the block mask.  Returns (code, log det)."""
+        ld, code = C.c_double(0.0), C.c_int(0)
+        self._check(self.L.glasso_bcd_logdet(self.h, _ptr(A), A.shape[0], _ptr(pi), _ptr(pj), len(pi),
+                                             _ptr(D), _ptr(inI), float(alpha), C.byref(ld), C.byref(code)),
+                    "bcd_logdet")
+        return code.value, ld.value
+
     def submit(self, problem, A_out):
         t = C.c_uint64()
         self._check(self.L.glasso_submit(self.h, C.byref(problem), _ptr(A_out), C.byref(t)),
@@ -374,5 +385,5 @@ EXPORTED = (
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
-    "glasso_set_debug", "glasso_pcd",
+    "glasso_set_debug", "glasso_pcd", "glasso_bcd_logdet",
 )
