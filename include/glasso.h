@@ -411,6 +411,26 @@ glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, con
                                 const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
                                 double alpha, double *logdet, int *code);
 
+/* One BCD-IC iteration (Section 6, Algorithm 2) on the device, A updated in
+ * place.  The columns are split into consecutive blocks of `block` columns
+ * (0: one block), treated in order; for each, at the current iterate: W from
+ * the FP64 factorisation, the block's free set (eq. active_set_j: free pairs
+ * with a row or column in the block), the Newton direction on it
+ * (eq. sub_Quad_MLE_l1_prior) by nsweeps CD sweeps (inner = GLASSO_INNER_CD)
+ * or PCD-CG to relative precision 1e-4 (GLASSO_INNER_PCD_CG), and the line
+ * search over alpha = 2^-t (t < 30) with log det(A + alpha Delta) from the
+ * Schur complement (glasso_bcd_logdet).  rule 1: the sample minimising F
+ * subject to positive definiteness (Section 6.1.2: the first sample not
+ * improved on by the next); rule 0: Armijo (sigma = 1e-4).  Both accept only
+ * F(A + alpha Delta) <= F(A) + 1e-12 max(|F(A)|, n).  S, A: n x n FP64 on the
+ * device.  *F (optional): F of the result; *moved: blocks with a nonzero
+ * direction; *trials: samples evaluated.  GLASSO_ENOTPD when A is not
+ * positive definite, GLASSO_ELINESEARCH when no sample passes (A keeps the
+ * blocks done so far). */
+glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, int64_t n, double lambda,
+                                   int64_t block, int inner, int nsweeps, int rule, double *F,
+                                   int *moved, int *trials);
+
 /* ---- allocation-free entry point ------------------------------------- */
 
 /* Largest n accepted by glasso_free_set_noalloc. */

@@ -1856,24 +1856,15 @@ glasso_status glasso_inverse(glasso_ctx *ctx, const double *L, int64_t n, double
 }
 
 // BCD-IC's Schur-complement line-search log det (bcd.cu pieces, dense.cu's
-// FP64 factorisation and inverse).
-glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, const int32_t *pi,
-                                const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
-                                double alpha, double *logdet, int *code) {
-    if (!ctx || !A || !inI || !code || n < 1 || np < 0 || (np > 0 && (!pi || !pj || !D)) ||
-        !isfinite(alpha))
-        return GLASSO_EINVAL;
-    cudaSetDevice(ctx->device);
+// FP64 factorisation and inverse) for the block with index lists i1 (I) and
+// i2 (the others); inI: the block's mask on the device.  Uses w.T, w.U, w.xd,
+// w.ldiag and w.sc; synchronises the stream.
+static glasso_status bcd_logdet_dev(glasso_ctx *ctx, const double *A, int64_t n, const int32_t *pi,
+                                    const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
+                                    const std::vector<int32_t> &i1, const std::vector<int32_t> &i2,
+                                    double alpha, double *logdet, int *code) {
     Work &w = ctx->w;
     cudaStream_t st = ctx->stream;
-    glasso_status s = work_ensure(w, n, st, ctx->last_error);
-    if (s != GLASSO_OK) return s;
-    // the block's index lists
-    std::vector<uint8_t> mask((size_t)n);
-    CTX_CK(cudaMemcpyAsync(mask.data(), inI, (size_t)n, cudaMemcpyDeviceToHost, st));
-    CTX_CK(cudaStreamSynchronize(st));
-    std::vector<int32_t> i1, i2;
-    for (int64_t i = 0; i < n; ++i) (mask[i] ? i1 : i2).push_back((int32_t)i);
     const int64_t m1 = (int64_t)i1.size(), m2 = (int64_t)i2.size();
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t nn = (size_t)n * n;
@@ -1909,6 +1900,7 @@ glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, con
         return GLASSO_OK;
     }
     double ld22 = 0.0;
+    glasso_status s;
     if (m2 > 0) {
         CTX_CK(bcd_gather(A, n, d2, m2, A22, st));
         CTX_CK(potrf(A22, m2, w.xd, w.ldiag, w.sc, st));
@@ -1937,6 +1929,169 @@ glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, con
     CTX_CK(cudaStreamSynchronize(st));
     *code = 0;
     if (logdet) *logdet = ld;
+    return GLASSO_OK;
+}
+
+glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, const int32_t *pi,
+                                const int32_t *pj, int64_t np, const double *D, const uint8_t *inI,
+                                double alpha, double *logdet, int *code) {
+    if (!ctx || !A || !inI || !code || n < 1 || np < 0 || (np > 0 && (!pi || !pj || !D)) ||
+        !isfinite(alpha))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    glasso_status s = work_ensure(ctx->w, n, ctx->stream, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    std::vector<uint8_t> mask((size_t)n);
+    CTX_CK(cudaMemcpyAsync(mask.data(), inI, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CTX_CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> i1, i2;
+    for (int64_t i = 0; i < n; ++i) (mask[i] ? i1 : i2).push_back((int32_t)i);
+    return bcd_logdet_dev(ctx, A, n, pi, pj, np, D, inI, i1, i2, alpha, logdet, code);
+}
+
+// One BCD-IC iteration (Algorithm 2) with every block step on the device: per
+// block of consecutive columns, W from the FP64 factorisation, the block's
+// free set by the candidate scan over its pairs, the Newton direction (CD
+// sweeps or PCD-CG), the line search over the samples alpha = 2^-t with log
+// det(A + alpha Delta) from the Schur complement.  The block loop and the
+// sample decisions run on the host.
+glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, int64_t n, double lambda,
+                                   int64_t block, int inner, int nsweeps, int rule, double *F_out,
+                                   int *moved, int *trials) {
+    if (!ctx || !S || !A || n < 1 || n > 46340 || !finite_pos(lambda) || block < 0 ||
+        (inner != GLASSO_INNER_CD && inner != GLASSO_INNER_PCD_CG) || (rule != 0 && rule != 1) ||
+        (inner == GLASSO_INNER_CD && nsweeps < 1))
+        return GLASSO_EINVAL;
+    if (block == 0 || block > n) block = n;
+    cudaSetDevice(ctx->device);
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    glasso_status s = work_ensure(w, n, st, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    uint8_t *dmask = nullptr;
+    if (cudaMallocAsync((void **)&dmask, (size_t)n, st) != cudaSuccess) {
+        cudaGetLastError();
+        return GLASSO_ENOMEM;
+    }
+    struct Free {
+        uint8_t *p;
+        cudaStream_t st;
+        ~Free() { cudaFreeAsync(p, st); }
+    } guard{dmask, st};
+    int nmv = 0, ntr = 0;
+    std::vector<uint8_t> mask((size_t)n);
+    std::vector<int32_t> ci, cj, i1, i2;
+    for (int64_t j0 = 0; j0 < n; j0 += block) {
+        const int64_t j1 = std::min(j0 + block, n);
+        i1.clear();
+        i2.clear();
+        for (int64_t i = 0; i < n; ++i) {
+            mask[i] = i >= j0 && i < j1;
+            (mask[i] ? i1 : i2).push_back((int32_t)i);
+        }
+        // F(A), log det A and W = A^{-1} at the current iterate
+        double FA = 0.0;
+        int info = 0;
+        s = glasso_objective(ctx, S, A, n, lambda, &FA, &info);
+        if (s != GLASSO_OK) return s;
+        if (info != 0) return GLASSO_ENOTPD;
+        CTX_CK(cudaMemcpyAsync(w.L, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CTX_CK(potrf(w.L, n, w.xd, w.ldiag, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        const double ldA = w.sc_host->logdet;
+        CTX_CK(inverse(w.L, n, w.W, w.T, w.U, st));
+        // the block's candidates: upper-triangle pairs with a row or a column in I, row-major
+        ci.clear();
+        cj.clear();
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = i; j < n; ++j)
+                if (mask[i] || mask[j]) {
+                    ci.push_back((int32_t)i);
+                    cj.push_back((int32_t)j);
+                }
+        const int64_t nc = (int64_t)ci.size();
+        CTX_CK(cudaMemcpyAsync(w.fi, ci.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
+        CTX_CK(cudaMemcpyAsync(w.fj, cj.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
+        CTX_CK(cudaMemcpyAsync(dmask, mask.data(), (size_t)n, cudaMemcpyHostToDevice, st));
+        CTX_CK(scan_cand(S, w.W, A, n, lambda, w.fi, w.fj, nullptr, 0, nc, w, w.pi, w.pj, nullptr, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        const int64_t np = w.sc_host->count;
+        if (np == 0) continue;
+        CTX_CK(pair_prep(S, w.W, A, n, lambda, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, w.p_s, st));
+        CTX_CK(cudaMemsetAsync(w.U, 0, (size_t)(n * n) * sizeof(double), st));
+        CTX_CK(cudaMemsetAsync(w.D, 0, np * sizeof(double), st));
+        if (inner == GLASSO_INNER_PCD_CG) {
+            int its = 0;
+            const cudaError_t pe = pcd(w.W, n, lambda, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, kPcdIters, 1,
+                                       kPcdRtol, w.D, w.U, w.T, false, w, st, &its);
+            if (pe == cudaErrorLaunchTimeout) {
+                ctx->last_error = "PCD-CG: a bounded grid-barrier wait expired";
+                return GLASSO_ETIMEOUT;
+            }
+            CTX_CK(pe);
+        } else {
+            CTX_CK(cd_sweeps(w.W, n, lambda, w.pi, w.pj, np, w.p_inva, w.p_g, w.p_a, nsweeps, w.D, w.U, w, st));
+        }
+        CTX_CK(ls_delta(w.p_g, w.p_a, w.p_s, w.D, w.pi, w.pj, np, lambda, w, w.sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (w.sc_host->bar_err) {
+            ctx->last_error = "CD sweep: a bounded grid-barrier wait expired";
+            return GLASSO_ETIMEOUT;
+        }
+        if (!w.sc_host->moved) continue;
+        ++nmv;
+        const double delta = w.sc_host->delta, trSD = w.sc_host->trSD;
+        const double epsF = 1e-12 * std::max(fabs(FA), (double)n);
+        double alpha = 1.0, a_acc = 0.0, prevF = INFINITY, prevA = 0.0;
+        bool ok = false;
+        for (int t = 0; t < 30 && !ok; ++t, alpha *= 0.5) {
+            double ldT = 0.0;
+            int code = 0;
+            s = bcd_logdet_dev(ctx, A, n, w.pi, w.pj, np, w.D, dmask, i1, i2, alpha, &ldT, &code);
+            if (s != GLASSO_OK) return s;
+            CTX_CK(ls_dl1(w.p_a, w.D, w.pi, w.pj, np, alpha, w, w.sc, st));
+            s = sync_ctx(ctx);
+            if (s != GLASSO_OK) return s;
+            ++ntr;
+            const double Ft =
+                code == 0 ? FA - (ldT - ldA) + alpha * trSD + lambda * w.sc_host->dl1 : INFINITY;
+            if (rule == 0) {
+                if (Ft <= FA + 1e-4 * alpha * delta + epsF) {
+                    ok = true;
+                    a_acc = alpha;
+                }
+            } else {
+                if (prevF < INFINITY && prevF <= FA + epsF && Ft >= prevF) {
+                    ok = true;
+                    a_acc = prevA;
+                }
+                prevF = Ft;
+                prevA = alpha;
+            }
+        }
+        if (!ok && rule == 1 && prevF <= FA + epsF) {
+            ok = true;  // the samples fell to the last one
+            a_acc = prevA;
+        }
+        if (!ok) {
+            if (moved) *moved = nmv;
+            if (trials) *trials = ntr;
+            return GLASSO_ELINESEARCH;
+        }
+        CTX_CK(ls_apply(A, n, w.pi, w.pj, w.p_a, w.D, np, a_acc, st));
+        CTX_CK(cudaStreamSynchronize(st));
+    }
+    if (F_out) {
+        int info = 0;
+        s = glasso_objective(ctx, S, A, n, lambda, F_out, &info);
+        if (s != GLASSO_OK) return s;
+        if (info != 0) return GLASSO_ENOTPD;
+    }
+    if (moved) *moved = nmv;
+    if (trials) *trials = ntr;
     return GLASSO_OK;
 }
 

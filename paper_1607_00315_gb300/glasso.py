@@ -97,6 +97,8 @@ def load():
     L.glasso_solve_batch.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                      C.POINTER(Info)]
     L.glasso_bcd_logdet.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, d, C.POINTER(d), C.POINTER(i32)]
+    L.glasso_bcd_iteration.argtypes = [vp, vp, vp, i64, d, i64, i32, i32, i32, C.POINTER(d),
+                                       C.POINTER(i32), C.POINTER(i32)]
     L.glasso_solve_batch_fused.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                            C.POINTER(Info)]
     L.glasso_submit.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(C.c_uint64)]
@@ -277,6 +279,16 @@ class Context:
                     "bcd_logdet")
         return code.value, ld.value
 
+    def bcd_iteration(self, S, A, lam, block, inner="cd", nsweeps=1, rule="paper"):
+        """glasso_bcd_iteration on CUDA float64 tensors (A updated in place);
+        returns (F, blocks moved, samples evaluated)."""
+        F, mv, tr = C.c_double(0.0), C.c_int(0), C.c_int(0)
+        self._check(self.L.glasso_bcd_iteration(self.h, _ptr(S), _ptr(A), A.shape[0], float(lam), int(block),
+                                                _inner_code(inner), int(nsweeps),
+                                                {"armijo": 0, "paper": 1}[rule], C.byref(F), C.byref(mv),
+                                                C.byref(tr)), "bcd_iteration")
+        return F.value, mv.value, tr.value
+
     def submit(self, problem, A_out):
         t = C.c_uint64()
         self._check(self.L.glasso_submit(self.h, C.byref(problem), _ptr(A_out), C.byref(t)),
@@ -385,5 +397,5 @@ EXPORTED = (
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
-    "glasso_set_debug", "glasso_pcd", "glasso_bcd_logdet",
+    "glasso_set_debug", "glasso_pcd", "glasso_bcd_logdet", "glasso_bcd_iteration",
 )

@@ -100,3 +100,48 @@ def test_bcd_logdet_other_codes(ctx):
         ctx.bcd_logdet(dA, dpi3, dpj, dD, dI, 0.5)
     code, ld = ctx.bcd_logdet(dA, dpi, dpj, dD, dI, 0.5)
     assert code == 0 and abs(ld - oracle.bcd_logdet(A, pi, pj, D, inI, 0.5)[1]) <= 1e-10 * abs(ld)
+
+
+def _problem(n, lam, seed):
+    from paper_1607_00315_gb300 import synth
+
+    p = synth.random_problem(n, 2 * n, lam, seed, gen="sparse")
+    return oracle.form_S(p.X)
+
+
+@pytest.mark.parametrize("n,block,nsweeps,rule", [(40, 40, 2, "armijo"), (40, 7, 1, "paper"),
+                                                  (130, 33, 2, "paper"), (64, 1, 1, "paper")])
+def test_bcd_iteration_matches_oracle(ctx, n, block, nsweeps, rule):
+    """Two BCD-IC iterations with CD sweeps, step by step against the oracle's
+    orc_bcd_iteration: the same blocks moved, the same samples, the iterate to
+    1e-10 (a single block with the Armijo rule is the dense relaxation)."""
+    lam = 0.1
+    S = _problem(n, lam, 500 + n + block)
+    A_ref = np.diag(1.0 / (np.diag(S) + lam))
+    dS, dA = _dev(S, A_ref)
+    for _ in range(2):
+        rc, A_ref, F_ref, tr_ref, mv_ref = oracle.bcd_iteration(S, A_ref, lam, block, inner="cd",
+                                                                nsweeps=nsweeps, rule=rule)
+        F, mv, tr = ctx.bcd_iteration(dS, dA, lam, block, "cd", nsweeps, rule)
+        assert rc == 0
+        A = dA.cpu().numpy()
+        assert np.abs(A - A_ref).max() <= 1e-10, np.abs(A - A_ref).max()
+        assert abs(F - F_ref) <= 1e-10 * abs(F_ref)
+        assert (mv, tr) == (mv_ref, tr_ref)
+
+
+def test_bcd_iterations_with_pcd_cg_reach_the_minimiser(ctx):
+    """BCD-IC alone (PCD-CG in each block, the paper's step rule) iterated on
+    the device reaches the oracle's minimiser."""
+    n, lam = 40, 0.1
+    S = _problem(n, lam, 11)
+    A_ref = oracle.solve(S, lam, tol=1e-11)[0]
+    dS, dA = _dev(S, np.diag(1.0 / (np.diag(S) + lam)))
+    F_prev = np.inf
+    for _ in range(8):
+        F, _, _ = ctx.bcd_iteration(dS, dA, lam, 10, "pcd_cg")
+        assert F <= F_prev + 1e-12 * abs(F)
+        F_prev = F
+    A = dA.cpu().numpy()
+    assert np.abs(A - A_ref).max() <= 1e-7
+    assert oracle.rel_kkt(S, np.linalg.inv(A), A, lam)[0] <= 1e-8
