@@ -431,6 +431,19 @@ glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, 
                                    int64_t block, int inner, int nsweeps, int rule, double *F,
                                    int *moved, int *trials);
 
+/* ML-BCD (Sections 6-7): the ML-cycle of Algorithm 1 (hierarchy of Section 7,
+ * the Section 8 KKT stop at tol) with one BCD-IC iteration (as
+ * glasso_bcd_iteration, blocks of `block` columns) as the relaxation on each
+ * level, the block free sets taken within C_l; from A0 = diag(1/(S_ii +
+ * lambda)); nsweeps = min(1 + floor(k/3), 10) CD sweeps in cycle k (inner =
+ * GLASSO_INNER_CD) or PCD-CG; one_level != 0: BCD-IC alone.  The control runs
+ * on the host, every step on the device.  S (input) and A (output): n x n
+ * FP64 on the device.  info (optional): status, cycles, relaxations, samples
+ * (ls_trials), objective, KKT residuals, log det, nnz.  Returns the status. */
+glasso_status glasso_solve_bcd(glasso_ctx *ctx, const double *S, int64_t n, double lambda, double tol,
+                               int max_cycles, int64_t block, int inner, int rule, int one_level, double *A,
+                               glasso_info *info);
+
 /* ---- allocation-free entry point ------------------------------------- */
 
 /* Largest n accepted by glasso_free_set_noalloc. */

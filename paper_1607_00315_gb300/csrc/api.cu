@@ -1955,29 +1955,34 @@ glasso_status glasso_bcd_logdet(glasso_ctx *ctx, const double *A, int64_t n, con
 // sweeps or PCD-CG), the line search over the samples alpha = 2^-t with log
 // det(A + alpha Delta) from the Schur complement.  The block loop and the
 // sample decisions run on the host.
-glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, int64_t n, double lambda,
-                                   int64_t block, int inner, int nsweeps, int rule, double *F_out,
-                                   int *moved, int *trials) {
-    if (!ctx || !S || !A || n < 1 || n > 46340 || !finite_pos(lambda) || block < 0 ||
-        (inner != GLASSO_INNER_CD && inner != GLASSO_INNER_PCD_CG) || (rule != 0 && rule != 1) ||
-        (inner == GLASSO_INNER_CD && nsweeps < 1))
-        return GLASSO_EINVAL;
+// The iteration itself.  cand_i/cand_j (host, optional): the candidates the
+// block free sets are taken from (the ML-cycle's C_l), else all pairs.  The
+// block's candidates live in buffers of their own, so the fine free set and
+// the level tags of the workspace are left untouched.
+static glasso_status bcd_iteration_impl(glasso_ctx *ctx, const double *S, double *A, int64_t n, double lambda,
+                                        int64_t block, int inner, int nsweeps, int rule,
+                                        const std::vector<int32_t> *cand_i, const std::vector<int32_t> *cand_j,
+                                        double *F_out, int *moved, int *trials) {
     if (block == 0 || block > n) block = n;
-    cudaSetDevice(ctx->device);
     Work &w = ctx->w;
     cudaStream_t st = ctx->stream;
     glasso_status s = work_ensure(w, n, st, ctx->last_error);
     if (s != GLASSO_OK) return s;
-    uint8_t *dmask = nullptr;
-    if (cudaMallocAsync((void **)&dmask, (size_t)n, st) != cudaSuccess) {
+    // the mask and two candidate lists of at most block * n pairs
+    const size_t capc = (size_t)block * (size_t)n + 1;
+    char *base = nullptr;
+    const size_t o_c1 = ((size_t)n + 255) & ~(size_t)255, o_c2 = o_c1 + ((capc * 4 + 255) & ~(size_t)255);
+    if (cudaMallocAsync((void **)&base, o_c2 + capc * 4, st) != cudaSuccess) {
         cudaGetLastError();
         return GLASSO_ENOMEM;
     }
     struct Free {
-        uint8_t *p;
+        char *p;
         cudaStream_t st;
         ~Free() { cudaFreeAsync(p, st); }
-    } guard{dmask, st};
+    } guard{base, st};
+    uint8_t *dmask = (uint8_t *)base;
+    int32_t *dci = (int32_t *)(base + o_c1), *dcj = (int32_t *)(base + o_c2);
     int nmv = 0, ntr = 0;
     std::vector<uint8_t> mask((size_t)n);
     std::vector<int32_t> ci, cj, i1, i2;
@@ -2001,20 +2006,32 @@ glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, 
         if (s != GLASSO_OK) return s;
         const double ldA = w.sc_host->logdet;
         CTX_CK(inverse(w.L, n, w.W, w.T, w.U, st));
-        // the block's candidates: upper-triangle pairs with a row or a column in I, row-major
+        // the block's candidates: pairs with a row or a column in I, from the
+        // given candidates (in their order) or from all upper-triangle pairs (row-major)
         ci.clear();
         cj.clear();
-        for (int64_t i = 0; i < n; ++i)
-            for (int64_t j = i; j < n; ++j)
+        if (cand_i) {
+            for (size_t p = 0; p < cand_i->size(); ++p) {
+                const int32_t i = (*cand_i)[p], j = (*cand_j)[p];
                 if (mask[i] || mask[j]) {
-                    ci.push_back((int32_t)i);
-                    cj.push_back((int32_t)j);
+                    ci.push_back(i);
+                    cj.push_back(j);
                 }
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = i; j < n; ++j)
+                    if (mask[i] || mask[j]) {
+                        ci.push_back((int32_t)i);
+                        cj.push_back((int32_t)j);
+                    }
+        }
         const int64_t nc = (int64_t)ci.size();
-        CTX_CK(cudaMemcpyAsync(w.fi, ci.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
-        CTX_CK(cudaMemcpyAsync(w.fj, cj.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
+        if (nc == 0) continue;
+        CTX_CK(cudaMemcpyAsync(dci, ci.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
+        CTX_CK(cudaMemcpyAsync(dcj, cj.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
         CTX_CK(cudaMemcpyAsync(dmask, mask.data(), (size_t)n, cudaMemcpyHostToDevice, st));
-        CTX_CK(scan_cand(S, w.W, A, n, lambda, w.fi, w.fj, nullptr, 0, nc, w, w.pi, w.pj, nullptr, w.sc, st));
+        CTX_CK(scan_cand(S, w.W, A, n, lambda, dci, dcj, nullptr, 0, nc, w, w.pi, w.pj, nullptr, w.sc, st));
         s = sync_ctx(ctx);
         if (s != GLASSO_OK) return s;
         const int64_t np = w.sc_host->count;
@@ -2093,6 +2110,164 @@ glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, 
     if (moved) *moved = nmv;
     if (trials) *trials = ntr;
     return GLASSO_OK;
+}
+
+glasso_status glasso_bcd_iteration(glasso_ctx *ctx, const double *S, double *A, int64_t n, double lambda,
+                                   int64_t block, int inner, int nsweeps, int rule, double *F_out,
+                                   int *moved, int *trials) {
+    if (!ctx || !S || !A || n < 1 || n > 46340 || !finite_pos(lambda) || block < 0 ||
+        (inner != GLASSO_INNER_CD && inner != GLASSO_INNER_PCD_CG) || (rule != 0 && rule != 1) ||
+        (inner == GLASSO_INNER_CD && nsweeps < 1))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    return bcd_iteration_impl(ctx, S, A, n, lambda, block, inner, nsweeps, rule, nullptr, nullptr, F_out, moved,
+                              trials);
+}
+
+// ML-BCD: Algorithm 1's control (hierarchy of Section 7, the Section 8 KKT
+// stop) on the host, each relaxation one BCD-IC iteration on C_l.
+glasso_status glasso_solve_bcd(glasso_ctx *ctx, const double *S, int64_t n, double lambda, double tol,
+                               int max_cycles, int64_t block, int inner, int rule, int one_level, double *A,
+                               glasso_info *info) {
+    if (!ctx || !S || !A || n < 1 || n > 46340 || !finite_pos(lambda) || !(tol >= 0.0) || block < 0 ||
+        (inner != GLASSO_INNER_CD && inner != GLASSO_INNER_PCD_CG) || (rule != 0 && rule != 1))
+        return GLASSO_EINVAL;
+    cudaSetDevice(ctx->device);
+    Work &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    glasso_status s = work_ensure(w, n, st, ctx->last_error);
+    if (s != GLASSO_OK) return s;
+    DevScalars *sc = w.sc, *h = w.sc_host;
+    const int mc = max_cycles > 0 ? max_cycles : 200;
+    const auto t0 = std::chrono::steady_clock::now();
+    glasso_status status = GLASSO_EMAXITER;
+    int cycles = 0, relax = 0, lstrials = 0;
+    double relkkt = INFINITY, maxkkt = INFINITY, F = 0.0, logdet = 0.0;
+    long long nnz = 0, max_nnz = 0;
+    bool fresh = false;
+    int64_t nf = 0;
+    std::vector<int32_t> hfi, hfj, ci, cj;
+    std::vector<uint8_t> htag;
+    CTX_CK(cudaMemsetAsync(sc, 0, sizeof(DevScalars), st));
+    CTX_CK(init_diag(S, n, lambda, A, sc, st));
+    CTX_CK(cudaMemcpyAsync(w.L, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CTX_CK(potrf(w.L, n, w.xd, w.ldiag, sc, st));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    if (h->err || h->info != 0) return GLASSO_ENOTPD;
+    CTX_CK(inverse(w.L, n, w.W, w.T, w.U, st));
+    // initial free set (Section 7 footnote) with |G| on it
+    CTX_CK(scan_full(S, w.W, A, n, lambda, 1, w, w.fi, w.fj, w.fabsg, sc, st));
+    s = sync_ctx(ctx);
+    if (s != GLASSO_OK) return s;
+    nf = h->count;
+    for (int k = 0; k < mc; ++k) {
+        cycles = k + 1;
+        const int nsweeps = std::min(1 + k / 3, 10);
+        int Lv = 0;
+        if (!one_level) {
+            CTX_CK(support_flags(A, n, w.fi, w.fj, nf, w.fsupp, st));
+            CTX_CK(hierarchy(w.fabsg, w.fsupp, nf, w.ftag, sc, st));
+            s = sync_ctx(ctx);
+            if (s != GLASSO_OK) return s;
+            Lv = h->levels;
+        }
+        if (Lv > 0) {
+            hfi.resize((size_t)nf);
+            hfj.resize((size_t)nf);
+            htag.resize((size_t)nf);
+            CTX_CK(cudaMemcpyAsync(hfi.data(), w.fi, (size_t)nf * 4, cudaMemcpyDeviceToHost, st));
+            CTX_CK(cudaMemcpyAsync(hfj.data(), w.fj, (size_t)nf * 4, cudaMemcpyDeviceToHost, st));
+            CTX_CK(cudaMemcpyAsync(htag.data(), w.ftag, (size_t)nf, cudaMemcpyDeviceToHost, st));
+            CTX_CK(cudaStreamSynchronize(st));
+        }
+        for (int l = Lv; l >= 0; --l) {
+            fresh = false;
+            const std::vector<int32_t> *pci = nullptr, *pcj = nullptr;
+            if (l == 0) {
+                // the fine free set at the current iterate, the KKT stop
+                CTX_CK(cudaMemcpyAsync(w.L, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                CTX_CK(potrf(w.L, n, w.xd, w.ldiag, sc, st));
+                s = sync_ctx(ctx);
+                if (s != GLASSO_OK) return s;
+                if (h->info != 0) return GLASSO_ENOTPD;
+                logdet = h->logdet;
+                CTX_CK(inverse(w.L, n, w.W, w.T, w.U, st));
+                CTX_CK(scan_full(S, w.W, A, n, lambda, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+                s = sync_ctx(ctx);
+                if (s != GLASSO_OK) return s;
+                const int64_t np = h->count;
+                relkkt = h->kkt_sum / h->l1;
+                maxkkt = h->kkt_max;
+                nnz = h->nnz;
+                max_nnz = std::max(max_nnz, nnz);
+                F = -logdet + h->trSA + lambda * h->l1;
+                CTX_CK(cudaMemcpyAsync(w.fi, w.pi, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CTX_CK(cudaMemcpyAsync(w.fj, w.pj, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+                CTX_CK(cudaMemcpyAsync(w.fabsg, w.pabsg, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                nf = np;
+                fresh = true;
+                if (relkkt <= tol) {
+                    status = GLASSO_OK;
+                    goto done;
+                }
+            } else {
+                ci.clear();
+                cj.clear();
+                for (size_t p = 0; p < hfi.size(); ++p)
+                    if (htag[p] >= l) {
+                        ci.push_back(hfi[p]);
+                        cj.push_back(hfj[p]);
+                    }
+                pci = &ci;
+                pcj = &cj;
+            }
+            int tr = 0, mv = 0;
+            s = bcd_iteration_impl(ctx, S, A, n, lambda, block, inner, nsweeps, rule, pci, pcj, nullptr, &mv, &tr);
+            lstrials += tr;
+            if (s == GLASSO_ELINESEARCH) {
+                status = s;
+                goto done;
+            }
+            if (s != GLASSO_OK) return s;
+            if (mv) fresh = false;
+            ++relax;
+        }
+    }
+done:
+    if (!fresh) {
+        CTX_CK(cudaMemcpyAsync(w.L, A, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CTX_CK(potrf(w.L, n, w.xd, w.ldiag, sc, st));
+        s = sync_ctx(ctx);
+        if (s != GLASSO_OK) return s;
+        if (h->info == 0) {
+            logdet = h->logdet;
+            CTX_CK(inverse(w.L, n, w.W, w.T, w.U, st));
+            CTX_CK(scan_full(S, w.W, A, n, lambda, 0, w, w.pi, w.pj, w.pabsg, sc, st));
+            s = sync_ctx(ctx);
+            if (s != GLASSO_OK) return s;
+            relkkt = h->kkt_sum / h->l1;
+            maxkkt = h->kkt_max;
+            nnz = h->nnz;
+            F = -logdet + h->trSA + lambda * h->l1;
+        }
+    }
+    max_nnz = std::max(max_nnz, nnz);
+    if (info) {
+        memset(info, 0, sizeof(glasso_info));
+        info->status = status;
+        info->cycles = cycles;
+        info->relaxations = relax;
+        info->ls_trials = lstrials;
+        info->objective = F;
+        info->rel_kkt = relkkt;
+        info->max_kkt = maxkkt;
+        info->logdet = logdet;
+        info->nnz = nnz;
+        info->max_nnz = max_nnz;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return status;
 }
 
 glasso_status glasso_cholinv_mixed(glasso_ctx *ctx, const double *A, int64_t n, double *W, int *info,

@@ -99,6 +99,7 @@ def load():
     L.glasso_bcd_logdet.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, d, C.POINTER(d), C.POINTER(i32)]
     L.glasso_bcd_iteration.argtypes = [vp, vp, vp, i64, d, i64, i32, i32, i32, C.POINTER(d),
                                        C.POINTER(i32), C.POINTER(i32)]
+    L.glasso_solve_bcd.argtypes = [vp, vp, i64, d, d, i32, i64, i32, i32, i32, vp, C.POINTER(Info)]
     L.glasso_solve_batch_fused.argtypes = [vp, C.POINTER(Problem), i32, i32, C.POINTER(vp),
                                            C.POINTER(Info)]
     L.glasso_submit.argtypes = [vp, C.POINTER(Problem), vp, C.POINTER(C.c_uint64)]
@@ -289,6 +290,19 @@ class Context:
                                                 C.byref(tr)), "bcd_iteration")
         return F.value, mv.value, tr.value
 
+    def solve_bcd(self, S, lam, tol=1e-8, block=0, inner="cd", rule="paper", one_level=False, max_cycles=0,
+                  A_out=None):
+        """glasso_solve_bcd (ML-BCD) on a CUDA float64 S; returns (status, A, info dict)."""
+        import torch
+
+        n = S.shape[0]
+        A = torch.empty((n, n), dtype=torch.float64, device=S.device) if A_out is None else A_out
+        info = Info()
+        s = self.L.glasso_solve_bcd(self.h, _ptr(S), n, float(lam), float(tol), int(max_cycles), int(block),
+                                    _inner_code(inner), {"armijo": 0, "paper": 1}[rule], int(bool(one_level)),
+                                    _ptr(A), C.byref(info))
+        return s, A, info.as_dict()
+
     def submit(self, problem, A_out):
         t = C.c_uint64()
         self._check(self.L.glasso_submit(self.h, C.byref(problem), _ptr(A_out), C.byref(t)),
@@ -397,5 +411,5 @@ EXPORTED = (
     "glasso_set_profiling", "glasso_get_profile", "glasso_form_S", "glasso_potrf",
     "glasso_inverse", "glasso_cholinv_mixed", "glasso_free_set", "glasso_hierarchy", "glasso_cd_sweeps",
     "glasso_line_search", "glasso_objective", "glasso_free_set_noalloc", "glasso_components",
-    "glasso_set_debug", "glasso_pcd", "glasso_bcd_logdet", "glasso_bcd_iteration",
+    "glasso_set_debug", "glasso_pcd", "glasso_bcd_logdet", "glasso_bcd_iteration", "glasso_solve_bcd",
 )

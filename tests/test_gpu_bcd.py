@@ -145,3 +145,23 @@ def test_bcd_iterations_with_pcd_cg_reach_the_minimiser(ctx):
     A = dA.cpu().numpy()
     assert np.abs(A - A_ref).max() <= 1e-7
     assert oracle.rel_kkt(S, np.linalg.inv(A), A, lam)[0] <= 1e-8
+
+
+def test_ml_bcd_matches_oracle(ctx):
+    """ML-BCD (the ML-cycle over BCD-IC iterations, PCD-CG in the blocks) on
+    the device against the oracle's orc_solve_bcd: the minimiser to the FP64
+    bar.  PCD-CG stops at a relative precision, and the device's and the
+    oracle's inner solves may stop an iteration apart, so the two trajectories
+    differ (measured: 9 relaxations against 11); the count is held to a
+    quarter of the oracle's."""
+    n, block, lam = 40, 10, 0.1
+    S = _problem(n, lam, 700 + n)
+    A_ref, info_ref = oracle.solve_bcd(S, lam, tol=1e-10, block=block, inner="pcd_cg")
+    assert info_ref["status"] == 0
+    (dS,) = _dev(S)
+    s, dA, info = ctx.solve_bcd(dS, lam, 1e-10, block, "pcd_cg")
+    assert s == 0 and info["status"] == 0 and info["rel_kkt"] <= 1e-10, info
+    A = dA.cpu().numpy()
+    assert np.abs(A - A_ref).max() <= 1e-7
+    assert abs(info["objective"] - info_ref["objective"]) <= 1e-9 * abs(info_ref["objective"])
+    assert abs(info["relaxations"] - info_ref["relaxations"]) <= max(2, info_ref["relaxations"] // 4)
