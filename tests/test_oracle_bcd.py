@@ -195,3 +195,16 @@ def test_reduced_inversion_from_the_neighbourhood(n, I, seed):
     B = A.copy()
     B[I[0], out] = B[out, I[0]] = 0.01
     assert oracle.bcd_w11(B, inI, inN, WN)[0] == -1
+
+
+@pytest.mark.parametrize("n,seed,one_level", [(30, 3, False), (45, 8, False), (30, 3, True)])
+def test_one_block_ml_bcd_is_the_dense_ml_cycle(n, seed, one_level):
+    """With a single block holding every index, CD sweeps and the Armijo rule,
+    ML-BCD takes exactly the steps of the dense ML-cycle (Section 6.2's
+    equivalence of QUIC with single-block BCD-IC, over whole solves): the same
+    cycles, relaxations and trials, and the same iterate bit for bit."""
+    S, lam = _problem(n, 0.1, seed)
+    A1, _, i1, _ = oracle.solve(S, lam, tol=1e-10, one_level=one_level)
+    A2, i2 = oracle.solve_bcd(S, lam, tol=1e-10, block=n, inner="cd", rule="armijo", one_level=one_level)
+    assert (i1["cycles"], i1["relaxations"], i1["ls_trials"]) == (i2["cycles"], i2["relaxations"], i2["ls_trials"])
+    assert np.array_equal(A1, A2)
